@@ -1,0 +1,205 @@
+/*
+ * wr.h -- exact rank of large sparse integer matrices modulo a prime p, by
+ * block Wiedemann, on one GB300 GPU (sm_103a).
+ *
+ * Method (Dumas, Elbaz-Vincent, Giorgi, Urbanska, "Parallel computation of the
+ * rank of large sparse matrices from algebraic K-theory", PASCO 2007):
+ * Section 2.4, "Block Wiedemann Rank Algorithm":
+ *   1. form A~ from A with preconditioners of the form A^T A (Section 2.3):
+ *      A~ = D1 A^T D2 A D1 (N = cols) or D1 A D2 A^T D1 (N = rows), D1, D2
+ *      random nonsingular diagonals;
+ *   2. the sequence S_i = X^T A~^i Y, i = 0 .. L-1 (Section 2.1, Coppersmith's
+ *      block Wiedemann), L = ceil(N/m) + ceil(N/n) + 2 by default;
+ *   3. the minimal matrix generator F of {S_i} through a sigma-basis
+ *      (Section 2.3, "sigma-basis computations"; M-Basis of Giorgi, Jeannerod,
+ *      Villard);
+ *   4. r = deg det F - codeg det F.
+ * Rank over Q: the maximum of the ranks modulo several primes (Section 2.4,
+ * last paragraph).
+ *
+ * Conventions for every call:
+ *   - every function returns wr_status (WR_OK = 0, errors < 0) or a plain
+ *     value documented with it; no call aborts or traps; wr_last_error()
+ *     gives a message for the last failing call of the calling thread;
+ *   - host pointers are read (or written) during the call only and stay
+ *     owned by the caller; device pointers (names starting with d_) must be
+ *     memory of the context's device, also owned by the caller;
+ *   - matrices, results and servers are opaque and owned by the library
+ *     until the matching *_free / *_stop call;
+ *   - residues are uint32 in [0, p); blocks are row-major; the sequence is
+ *     laid out [i][a][b] (L x m x n); generator coefficients [k][row][col];
+ *   - all work is queued on the context's stream; calls that return host
+ *     values synchronise that stream.
+ */
+#ifndef WR_H
+#define WR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WR_OK = 0,
+    WR_EINVAL = -1,      /* bad argument (null pointer, size, block width ...)      */
+    WR_ENOMEM = -2,      /* device or host allocation failed                        */
+    WR_EDEVICE = -3,     /* CUDA error; message from the runtime                    */
+    WR_ETIMEDOUT = -4,   /* a bounded device or host wait ran out                   */
+    WR_ENOTPRIME = -5,   /* p is not a prime with 2 < p < 2^31                       */
+    WR_EOVERFLOW = -6,   /* an entry or a size does not fit the exact formats       */
+    WR_EPROBFAIL = -7,   /* Monte Carlo failure detected (singular generator ...);   */
+                         /* retry with another seed                                 */
+    WR_EBUSY = -8        /* server queue full / resource busy                       */
+} wr_status;
+
+enum { WR_PROJ_GENERIC = 0, WR_PROJ_SYMMETRIC = 1 };
+enum { WR_SIDE_AUTO = -1, WR_SIDE_COLS = 0, WR_SIDE_ROWS = 1 };
+enum { WR_WANT_SEQUENCE = 1, WR_WANT_GENERATOR = 2 };
+
+typedef struct wr_ctx wr_ctx;
+typedef struct wr_matrix wr_matrix;
+typedef struct wr_result wr_result;
+typedef struct wr_server wr_server;
+
+/* Parameters of one rank computation; copied on call. */
+typedef struct {
+    uint32_t prime;      /* 2 < p < 2^31, checked by deterministic Miller-Rabin           */
+    uint32_t m, n;       /* block sizes, 1..32 each; m = n = 1 is scalar Wiedemann        */
+    uint64_t seed;       /* derives X, Y, D1, D2: h(seed, tag, idx) = sm(sm(seed ^ tag*G) */
+                         /* + idx) with sm = SplitMix64 output, G = 0x9E3779B97F4A7C15;   */
+                         /* X, Y entries h mod p (tags 1, 2; idx = row*width + col);      */
+                         /* D1, D2 entries 1 + h mod (p - 1) (tags 3, 4; idx = row)       */
+    int32_t projection;  /* WR_PROJ_GENERIC (X independent) or WR_PROJ_SYMMETRIC (X = Y,  */
+                         /* m = n; Section 2.2)                                           */
+    int32_t side;        /* WR_SIDE_AUTO (N = min(rows, cols)), WR_SIDE_COLS, WR_SIDE_ROWS */
+    uint64_t seq_len;    /* 0: L = ceil(N/m) + ceil(N/n) + 2                               */
+    uint32_t want;       /* WR_WANT_SEQUENCE | WR_WANT_GENERATOR: keep them in the result */
+} wr_params;
+
+/* Phase times of the last wr_rank on a context (milliseconds, CUDA events). */
+typedef struct {
+    double setup_ms;     /* X, Y, D1, D2 derivation and preconditioning set-up             */
+    double sequence_ms;  /* the L - 1 black-box applications and projections               */
+    double sigma_ms;     /* sigma-basis                                                   */
+    double readout_ms;   /* generator selection, det valuations, rank                     */
+    double total_ms;
+    double spmm_ms;      /* when profiling is on: summed duration of the sampled SpMM      */
+    int64_t spmm_launches; /* launches those samples cover                                  */
+    double spmm_bytes;   /* algorithmic bytes of those launches                            */
+} wr_timings;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * queue work on (for example a torch stream), or NULL for a stream owned by
+ * the context.  (The paper's Section 3.1 runs one process per column of Y; on
+ * one GPU every column of the block goes through one kernel pass instead.) */
+wr_status wr_create(wr_ctx **out, int device, void *cuda_stream);
+void wr_destroy(wr_ctx *ctx);
+/* Message of the last failing call made by this thread ("" if none). */
+const char *wr_last_error(void);
+/* Turn per-kernel CUDA-event sampling of the SpMM passes on (1) or off (0). */
+wr_status wr_set_profiling(wr_ctx *ctx, int on);
+wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out);
+
+/* ---------------------------------------------------------------- matrices */
+
+/* Ingest a CSR matrix (Section 2.4 step 1 operates on it as a black box).
+ * rowptr: rows + 1 int64, nondecreasing, rowptr[0] = 0; colidx: int32 in
+ * [0, cols); vals: small signed integers, |v| <= 127 (the paper's boundary
+ * matrices hold 0, +-1 and small integers).  cols < 2^24 and every row and
+ * column < 2^24 entries (exact int64 accumulation), else WR_EOVERFLOW.
+ * Builds SELL-C-sigma layouts of A and A^T on the device. */
+wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
+                             const int32_t *colidx, const int32_t *vals, wr_matrix **out);
+/* Same, from arrays already in device memory (nnz = rowptr[rows]). */
+wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz,
+                                    const int64_t *d_rowptr, const int32_t *d_colidx,
+                                    const int32_t *d_vals, wr_matrix **out);
+/* rows, cols, nnz, and the padded slot counts of the A and A^T layouts. */
+wr_status wr_matrix_info(const wr_matrix *mat, int64_t *rows, int64_t *cols, int64_t *nnz,
+                         int64_t *slots_a, int64_t *slots_at);
+void wr_matrix_free(wr_matrix *mat);
+
+/* ---------------------------------------------------------------- rank */
+
+/* Rank of the matrix modulo params->prime (Section 2.4 steps 1-4). */
+wr_status wr_rank(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out);
+
+/* Many jobs in one call (matrices may repeat with different primes or seeds):
+ * jobs that share a matrix share its passes over the matrix; the sequence
+ * loops of all jobs run interleaved on the device.  outs[j] receives job j's
+ * result (NULL when that job failed; the call then returns its status). */
+wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *const *mats,
+                        const wr_params *params, wr_result **outs);
+
+uint64_t wr_result_rank(const wr_result *res);
+/* deg det F, codeg det F = v_x(det F), sum of the generator's column degrees,
+ * and the sequence length used. */
+wr_status wr_result_info(const wr_result *res, int64_t *deg_det, int64_t *codeg,
+                         int64_t *sum_delta, int64_t *seq_len);
+/* Copy the sequence (L*m*n residues, [i][a][b]) to host memory dst (cap_elems
+ * entries).  Needs WR_WANT_SEQUENCE. */
+wr_status wr_result_sequence(const wr_result *res, uint32_t *dst, size_t cap_elems);
+/* Copy the generator F ((dmax+1)*n*n residues, [k][row][col], dmax = max column
+ * degree) and its column degrees (n).  Needs WR_WANT_GENERATOR. */
+wr_status wr_result_generator(const wr_result *res, uint32_t *coeffs, size_t cap_elems,
+                              int32_t *col_degrees);
+void wr_result_free(wr_result *res);
+
+/* ------------------------------------------- step-level calls (device data) */
+
+/* One application of the preconditioned black box (Section 2.3):
+ * d_out = A~ d_in, d_in, d_out: N x width residues (width 1..32), N and D1, D2
+ * from params (side, seed, prime).  d_in and d_out may alias. */
+wr_status wr_blackbox_apply_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                   const uint32_t *d_in, uint32_t *d_out, int64_t width);
+/* The sequence S_i = X^T A~^i Y, i < L (Section 2.4 step 2) into d_S (L*m*n). */
+wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                             uint32_t *d_S, uint64_t L);
+/* Order-L sigma-basis of [S(x) | -I_m] with shift (0^n, 1^m) (Section 2.3):
+ * writes its first n rows (the P part) as d_P ((Dcap+1) x n x (m+n), [t][r][c])
+ * and the shifted column degrees d_deg (m + n).  d_S: L*m*n residues. */
+wr_status wr_sigma_basis_device(wr_ctx *ctx, const uint32_t *d_S, uint64_t L, uint32_t m,
+                                uint32_t n, uint32_t prime, uint32_t *d_P, int32_t *d_deg,
+                                int64_t Dcap);
+/* x-adic valuation of det G for G (T x n x n, [t][i][j], residues) given by
+ * its first T coefficients (Section 2.4 step 4, codeg).  *val = -1 when the
+ * precision T does not determine it. */
+wr_status wr_det_valuation_device(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T,
+                                  uint32_t prime, int64_t *val);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct {
+    int32_t max_slots;        /* requests resident on the device at once                 */
+    uint64_t hbm_budget;      /* bytes of device memory the admitted requests may hold   */
+    int32_t queue_cap;        /* pending requests before wr_submit returns WR_EBUSY      */
+} wr_server_cfg;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    double p50_ms, p99_ms;    /* latency submit -> result                                */
+    double throughput_rps;    /* completed / (last completion - first submission)         */
+    int32_t max_resident;     /* most requests resident at once                          */
+} wr_stats;
+
+/* Continuous-batching rank server: requests are admitted as slots and device
+ * memory free up, and their sequence iterations run interleaved with those of
+ * the requests already resident. */
+wr_status wr_server_start(wr_ctx *ctx, const wr_server_cfg *cfg, wr_server **out);
+/* Queue a rank request; the matrix must stay alive until its result is taken. */
+wr_status wr_submit(wr_server *srv, const wr_matrix *mat, const wr_params *params,
+                    uint64_t *ticket);
+/* Wait up to timeout_ms for a ticket's result (WR_ETIMEDOUT if not ready). */
+wr_status wr_wait(wr_server *srv, uint64_t ticket, uint32_t timeout_ms, wr_result **out);
+wr_status wr_server_stats(wr_server *srv, wr_stats *out);
+void wr_server_stop(wr_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WR_H */

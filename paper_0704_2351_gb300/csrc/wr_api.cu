@@ -1,0 +1,434 @@
+// The C ABI of libwr (include/wr.h): contexts, matrices, the rank call,
+// results and the step-level calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wr_internal.cuh"
+
+namespace wr {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+wr_status fail(wr_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+wr_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return WR_EDEVICE;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+wr_status dev_alloc(wr_ctx *ctx, DevBuf &b, size_t bytes) {
+    b.release();
+    if (bytes == 0) bytes = 1;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WR_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                   " bytes failed: " + cudaGetErrorString(e));
+    }
+    b.ptr = p;
+    b.bytes = bytes;
+    b.stream = ctx->stream;
+    return WR_OK;
+}
+
+ModP make_modp(uint32_t p) {
+    ModP m;
+    m.p = p;
+    m.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
+    uint64_t k = ((uint64_t(1) << 62) + p - 1) / p;
+    m.off = (int64_t)(k * (uint64_t)p);
+    uint64_t pm1 = (uint64_t)p - 1;
+    unsigned __int128 room = ((unsigned __int128)1 << 64) - 1 - p;
+    uint64_t lazy = pm1 ? (uint64_t)(room / ((unsigned __int128)pm1 * pm1)) : 1024;
+    m.lazy = (uint32_t)std::min<uint64_t>(lazy, 1024);
+    return m;
+}
+
+static uint64_t host_powmod(uint64_t a, uint64_t e, uint64_t n) {
+    unsigned __int128 r = 1 % n, b = a % n;
+    while (e) {
+        if (e & 1) r = r * b % n;
+        b = b * b % n;
+        e >>= 1;
+    }
+    return (uint64_t)r;
+}
+
+// deterministic Miller-Rabin for n < 2^32 (bases 2, 7, 61)
+bool is_prime_u32(uint64_t n) {
+    if (n < 2) return false;
+    for (uint64_t sp : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull, 19ull, 23ull, 29ull, 31ull, 37ull}) {
+        if (n == sp) return true;
+        if (n % sp == 0) return false;
+    }
+    uint64_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; s++; }
+    for (uint64_t a : {2ull, 7ull, 61ull}) {
+        uint64_t x = host_powmod(a % n, d, n);
+        if (a % n == 0 || x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; r++) {
+            x = (uint64_t)((unsigned __int128)x * x % n);
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+int padded_width(int n) {
+    int nv = 1;
+    while (nv < n) nv <<= 1;
+    return nv;
+}
+
+wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r) {
+    if (!mat || !prm) return fail(WR_EINVAL, "null matrix or params");
+    if (prm->prime <= 2 || prm->prime >= (1u << 31) || !is_prime_u32(prm->prime))
+        return fail(WR_ENOTPRIME, "prime must be a prime p with 2 < p < 2^31");
+    if (prm->m < 1 || prm->m > 32 || prm->n < 1 || prm->n > 32)
+        return fail(WR_EINVAL, "block sizes m, n must be in 1..32");
+    if (prm->projection != WR_PROJ_GENERIC && prm->projection != WR_PROJ_SYMMETRIC)
+        return fail(WR_EINVAL, "unknown projection mode");
+    if (prm->projection == WR_PROJ_SYMMETRIC && prm->m != prm->n)
+        return fail(WR_EINVAL, "the symmetric projection needs m = n");
+    r.p = prm->prime;
+    r.m = (int)prm->m;
+    r.n = (int)prm->n;
+    r.nv = padded_width(r.n);
+    int side = prm->side;
+    if (side == WR_SIDE_AUTO) side = mat->rows >= mat->cols ? WR_SIDE_COLS : WR_SIDE_ROWS;
+    if (side != WR_SIDE_COLS && side != WR_SIDE_ROWS) return fail(WR_EINVAL, "unknown side");
+    r.side = side;
+    r.N = side == WR_SIDE_COLS ? mat->cols : mat->rows;
+    r.M = side == WR_SIDE_COLS ? mat->rows : mat->cols;
+    r.L = prm->seq_len ? (int64_t)prm->seq_len : (r.N + r.m - 1) / r.m + (r.N + r.n - 1) / r.n + 2;
+    r.symmetric = prm->projection == WR_PROJ_SYMMETRIC;
+    r.seed = prm->seed;
+    return WR_OK;
+}
+
+}  // namespace wr
+
+using namespace wr;
+
+// ------------------------------------------------------------------ context
+
+extern "C" wr_status wr_create(wr_ctx **out, int device, void *cuda_stream) {
+    if (!out) return fail(WR_EINVAL, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(WR_EDEVICE, "no CUDA device available");
+    }
+    if (device < 0 || device >= ndev) return fail(WR_EINVAL, "device index out of range");
+    WR_CUDA(cudaSetDevice(device));
+    wr_ctx *c = new wr_ctx();
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
+        c->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)optin;
+    *out = c;
+    return WR_OK;
+}
+
+extern "C" void wr_destroy(wr_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" const char *wr_last_error(void) { return g_err.c_str(); }
+
+extern "C" wr_status wr_set_profiling(wr_ctx *ctx, int on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->profiling = on != 0;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out) {
+    if (!ctx || !out) return fail(WR_EINVAL, "null argument");
+    *out = ctx->last;
+    return WR_OK;
+}
+
+// ------------------------------------------------------------------ matrices
+
+static wr_status load_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                             const int32_t *d_colidx, const int32_t *d_vals, wr_matrix **out) {
+    if (!ctx || !out) return fail(WR_EINVAL, "null argument");
+    *out = nullptr;
+    if (rows < 0 || cols < 0 || nnz < 0) return fail(WR_EINVAL, "negative size");
+    if (rows >= (int64_t(1) << 31) || cols >= (int64_t(1) << 24))
+        return fail(WR_EOVERFLOW, "rows must be < 2^31 and cols < 2^24");
+    if (nnz > 0 && (!d_colidx || !d_vals)) return fail(WR_EINVAL, "null column or value array");
+    if (!d_rowptr) return fail(WR_EINVAL, "null row pointer array");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    WR_TRY(validate_csr(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals));
+    wr_matrix *m = new wr_matrix();
+    m->ctx = ctx;
+    m->rows = rows;
+    m->cols = cols;
+    m->nnz = nnz;
+    wr_status st = build_sell(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, m->a);
+    if (st == WR_OK) {
+        DevBuf rpt, cit, vat;
+        st = transpose_csr(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, rpt, cit, vat);
+        if (st == WR_OK)
+            st = build_sell(ctx, cols, rows, nnz, rpt.as<int64_t>(), cit.as<int32_t>(), vat.as<int32_t>(), m->at);
+    }
+    if (st != WR_OK) {
+        delete m;
+        return st;
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "matrix build");
+    }
+    *out = m;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz,
+                                               const int64_t *d_rowptr, const int32_t *d_colidx,
+                                               const int32_t *d_vals, wr_matrix **out) {
+    return load_device(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, out);
+}
+
+extern "C" wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
+                                        const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
+    if (!ctx || !out || !rowptr) return fail(WR_EINVAL, "null argument");
+    if (rows < 0 || cols < 0) return fail(WR_EINVAL, "negative size");
+    const int64_t nnz = rowptr[rows];
+    if (nnz < 0) return fail(WR_EINVAL, "negative nnz");
+    if (nnz > 0 && (!colidx || !vals)) return fail(WR_EINVAL, "null column or value array");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    DevBuf rp, ci, va;
+    WR_TRY(dev_alloc(ctx, rp, sizeof(int64_t) * (rows + 1)));
+    WR_TRY(dev_alloc(ctx, ci, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    WR_TRY(dev_alloc(ctx, va, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    WR_CUDA(cudaMemcpyAsync(rp.ptr, rowptr, sizeof(int64_t) * (rows + 1), cudaMemcpyHostToDevice, ctx->stream));
+    if (nnz > 0) {
+        WR_CUDA(cudaMemcpyAsync(ci.ptr, colidx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
+        WR_CUDA(cudaMemcpyAsync(va.ptr, vals, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return load_device(ctx, rows, cols, nnz, rp.as<int64_t>(), ci.as<int32_t>(), va.as<int32_t>(), out);
+}
+
+extern "C" wr_status wr_matrix_info(const wr_matrix *mat, int64_t *rows, int64_t *cols, int64_t *nnz,
+                                    int64_t *slots_a, int64_t *slots_at) {
+    if (!mat) return fail(WR_EINVAL, "null matrix");
+    if (rows) *rows = mat->rows;
+    if (cols) *cols = mat->cols;
+    if (nnz) *nnz = mat->nnz;
+    if (slots_a) *slots_a = mat->a.nslots;
+    if (slots_at) *slots_at = mat->at.nslots;
+    return WR_OK;
+}
+
+extern "C" void wr_matrix_free(wr_matrix *mat) {
+    if (!mat) return;
+    cudaSetDevice(mat->ctx->device);
+    cudaStreamSynchronize(mat->ctx->stream);
+    delete mat;
+}
+
+// ------------------------------------------------------------------ rank
+
+namespace wr {
+
+wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out) {
+    if (!ctx || !mat || !params || !out) return fail(WR_EINVAL, "null argument");
+    *out = nullptr;
+    Resolved r;
+    WR_TRY(resolve(mat, params, r));
+    WR_CUDA(cudaSetDevice(ctx->device));
+    ctx->last = wr_timings{};
+    auto t_start = std::chrono::steady_clock::now();
+    wr_result *res = new wr_result();
+    res->prime = r.p;
+    res->m = (uint32_t)r.m;
+    res->n = (uint32_t)r.n;
+    res->seq_len = r.L;
+    if (r.N == 0) {
+        res->rank = 0;
+        *out = res;
+        return WR_OK;
+    }
+    const int64_t L = r.L;
+    const int q = r.m + r.n;
+    const int64_t Dcap = L + 1;
+    DevBuf dS, dP, ddeg;
+    wr_status st = dev_alloc(ctx, dS, sizeof(uint32_t) * L * r.m * r.n);
+    if (st == WR_OK) st = dev_alloc(ctx, dP, sizeof(uint32_t) * (Dcap + 1) * r.n * q);
+    if (st == WR_OK) st = dev_alloc(ctx, ddeg, sizeof(int32_t) * q);
+    double setup_ms = 0, seq_ms = 0;
+    if (st == WR_OK) st = run_sequence(ctx, mat, *params, L, dS.as<uint32_t>(), &setup_ms, &seq_ms);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (st == WR_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventCreate(&e2);
+        cudaEventRecord(e0, ctx->stream);
+        st = sigma_basis(ctx, dS.as<uint32_t>(), L, r.m, r.n, r.p, dP.as<uint32_t>(), ddeg.as<int32_t>(), Dcap);
+    }
+    Readout ro;
+    if (st == WR_OK) {
+        cudaEventRecord(e1, ctx->stream);
+        st = rank_readout(ctx, dP.as<uint32_t>(), ddeg.as<int32_t>(), r.m, r.n, r.p, Dcap, ro,
+                          (params->want & WR_WANT_GENERATOR) ? &res->gen : nullptr);
+    }
+    if (st == WR_OK) {
+        cudaEventRecord(e2, ctx->stream);
+        cudaEventSynchronize(e2);
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&b, e1, e2);
+        ctx->last.setup_ms = setup_ms;
+        ctx->last.sequence_ms = seq_ms;
+        ctx->last.sigma_ms = a;
+        ctx->last.readout_ms = b;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
+    if (st == WR_OK && (params->want & WR_WANT_SEQUENCE)) {
+        res->seq.resize((size_t)L * r.m * r.n);
+        cudaError_t e = cudaMemcpyAsync(res->seq.data(), dS.ptr, sizeof(uint32_t) * res->seq.size(),
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy sequence");
+    }
+    if (st != WR_OK) {
+        delete res;
+        return st;
+    }
+    res->rank = ro.rank;
+    res->deg_det = ro.deg_det;
+    res->codeg = ro.codeg;
+    res->sum_delta = ro.sum_delta;
+    if (params->want & WR_WANT_GENERATOR) {
+        res->gen_deg = ro.delta;
+        res->gen_dmax = ro.dmax;
+    }
+    ctx->last.total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    *out = res;
+    return WR_OK;
+}
+
+}  // namespace wr
+
+extern "C" wr_status wr_rank(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out) {
+    return rank_one(ctx, mat, params, out);
+}
+
+extern "C" uint64_t wr_result_rank(const wr_result *res) { return res ? (uint64_t)res->rank : 0; }
+
+extern "C" wr_status wr_result_info(const wr_result *res, int64_t *deg_det, int64_t *codeg, int64_t *sum_delta,
+                                    int64_t *seq_len) {
+    if (!res) return fail(WR_EINVAL, "null result");
+    if (deg_det) *deg_det = res->deg_det;
+    if (codeg) *codeg = res->codeg;
+    if (sum_delta) *sum_delta = res->sum_delta;
+    if (seq_len) *seq_len = res->seq_len;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_result_sequence(const wr_result *res, uint32_t *dst, size_t cap_elems) {
+    if (!res || !dst) return fail(WR_EINVAL, "null argument");
+    if (res->seq.empty() && res->seq_len > 0 && res->m > 0)
+        return fail(WR_EINVAL, "the sequence was not kept (WR_WANT_SEQUENCE)");
+    if (cap_elems < res->seq.size()) return fail(WR_EINVAL, "destination too small");
+    std::memcpy(dst, res->seq.data(), sizeof(uint32_t) * res->seq.size());
+    return WR_OK;
+}
+
+extern "C" wr_status wr_result_generator(const wr_result *res, uint32_t *coeffs, size_t cap_elems,
+                                         int32_t *col_degrees) {
+    if (!res) return fail(WR_EINVAL, "null result");
+    if (res->gen_dmax < 0) return fail(WR_EINVAL, "the generator was not kept (WR_WANT_GENERATOR)");
+    if (coeffs) {
+        if (cap_elems < res->gen.size()) return fail(WR_EINVAL, "destination too small");
+        std::memcpy(coeffs, res->gen.data(), sizeof(uint32_t) * res->gen.size());
+    }
+    if (col_degrees) std::memcpy(col_degrees, res->gen_deg.data(), sizeof(int32_t) * res->gen_deg.size());
+    return WR_OK;
+}
+
+extern "C" void wr_result_free(wr_result *res) { delete res; }
+
+// ------------------------------------------------------------------ step-level calls
+
+extern "C" wr_status wr_blackbox_apply_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                              const uint32_t *d_in, uint32_t *d_out, int64_t width) {
+    if (!ctx || !mat || !params || !d_in || !d_out) return fail(WR_EINVAL, "null argument");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    return blackbox_apply(ctx, mat, *params, d_in, d_out, width);
+}
+
+extern "C" wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                        uint32_t *d_S, uint64_t L) {
+    if (!ctx || !mat || !params || !d_S) return fail(WR_EINVAL, "null argument");
+    Resolved r;
+    WR_TRY(resolve(mat, params, r));
+    WR_CUDA(cudaSetDevice(ctx->device));
+    ctx->last = wr_timings{};
+    if (r.N == 0) {
+        WR_CUDA(cudaMemsetAsync(d_S, 0, sizeof(uint32_t) * L * r.m * r.n, ctx->stream));
+        return WR_OK;
+    }
+    double a = 0, b = 0;
+    WR_TRY(run_sequence(ctx, mat, *params, (int64_t)L, d_S, &a, &b));
+    ctx->last.setup_ms = a;
+    ctx->last.sequence_ms = b;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_sigma_basis_device(wr_ctx *ctx, const uint32_t *d_S, uint64_t L, uint32_t m, uint32_t n,
+                                           uint32_t prime, uint32_t *d_P, int32_t *d_deg, int64_t Dcap) {
+    if (!ctx || !d_S || !d_P || !d_deg) return fail(WR_EINVAL, "null argument");
+    if (prime <= 2 || prime >= (1u << 31) || !is_prime_u32(prime)) return fail(WR_ENOTPRIME, "bad prime");
+    if (Dcap < (int64_t)L + 1) return fail(WR_EINVAL, "Dcap must be at least L + 1");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    return sigma_basis(ctx, d_S, (int64_t)L, (int)m, (int)n, prime, d_P, d_deg, Dcap);
+}
+
+extern "C" wr_status wr_det_valuation_device(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T, uint32_t prime,
+                                             int64_t *val) {
+    if (!ctx || !d_G || !val) return fail(WR_EINVAL, "null argument");
+    if (prime <= 2 || prime >= (1u << 31) || !is_prime_u32(prime)) return fail(WR_ENOTPRIME, "bad prime");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    return det_valuation(ctx, d_G, n, T, prime, val);
+}

@@ -1,0 +1,419 @@
+// Matrix ingest on the device: CSR validation, exclusive scans, CSR
+// transpose, and the SELL-C-sigma layout the SpMM kernels read.
+//
+// The paper reads its boundary matrices once and keeps them for the whole
+// sequence (Section 2.6.4 reduces them at read time; Section 3.1 broadcasts
+// A to every process).  Here the matrix is laid out once per load, in device
+// memory, for both A and A^T (the two sparse passes of A~ = D1 A^T D2 A D1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "wr_internal.cuh"
+
+namespace wr {
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+enum : int { ERR_ROWPTR = 1, ERR_COL = 2, ERR_VAL = 4, ERR_ROWLEN = 8 };
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t &excl) {
+    __shared__ int64_t warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < (int)(blockDim.x / 32) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int64_t warp_prefix = warp > 0 ? warp_sums[warp - 1] : 0;
+    int64_t total = warp_sums[blockDim.x / 32 - 1];
+    excl = warp_prefix + x - v;
+    __syncthreads();
+    return total;
+}
+
+__global__ void k_tile_sums(const int64_t *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int64_t s = 0;
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+        if (i < n) s += in[i];
+    }
+    int64_t excl;
+    int64_t tot = block_exclusive_scan(s, excl);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_tile_scan(const int64_t *__restrict__ in, int64_t n, const int64_t *__restrict__ offs,
+                            int64_t *__restrict__ out) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int64_t loc[SCAN_ITEMS];
+    int64_t s = 0;
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+        loc[k] = i < n ? in[i] : 0;
+        s += loc[k];
+    }
+    int64_t excl;
+    int64_t tot = block_exclusive_scan(s, excl);
+    int64_t run = excl + (offs ? offs[blockIdx.x] : 0);
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+        if (i < n) out[i] = run;
+        run += loc[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+        (void)tot;
+        out[n] = run;  // total
+    }
+}
+
+// --- validation
+
+__global__ void k_validate(int64_t rows, int64_t cols, int64_t nnz, const int64_t *__restrict__ rowptr,
+                           const int32_t *__restrict__ colidx, const int32_t *__restrict__ vals,
+                           int *__restrict__ err) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int e = 0;
+    for (int64_t i = tid; i < rows; i += stride) {
+        int64_t a = rowptr[i], b = rowptr[i + 1];
+        if (b < a || a < 0 || b > nnz) e |= ERR_ROWPTR;
+        else if (b - a >= (int64_t(1) << 24)) e |= ERR_ROWLEN;
+    }
+    if (tid == 0 && (rowptr[0] != 0 || rowptr[rows] != nnz)) e |= ERR_ROWPTR;
+    for (int64_t k = tid; k < nnz; k += stride) {
+        int32_t c = colidx[k];
+        int32_t v = vals[k];
+        if (c < 0 || c >= cols) e |= ERR_COL;
+        if (v < -127 || v > 127) e |= ERR_VAL;
+    }
+    if (e) atomicOr(err, e);
+}
+
+// --- transpose
+
+__global__ void k_count_cols(int64_t nnz, const int32_t *__restrict__ colidx, int64_t *__restrict__ cnt) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = tid; k < nnz; k += stride)
+        atomicAdd((unsigned long long *)&cnt[colidx[k]], 1ull);
+}
+
+__global__ void k_scatter_transpose(int64_t rows, const int64_t *__restrict__ rowptr,
+                                    const int32_t *__restrict__ colidx, const int32_t *__restrict__ vals,
+                                    const int64_t *__restrict__ rowptr_t, int64_t *__restrict__ fill,
+                                    int32_t *__restrict__ colidx_t, int32_t *__restrict__ vals_t) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < rows; i += stride) {
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            int32_t c = colidx[k];
+            int64_t pos = rowptr_t[c] + (int64_t)atomicAdd((unsigned long long *)&fill[c], 1ull);
+            colidx_t[pos] = (int32_t)i;
+            vals_t[pos] = vals[k];
+        }
+    }
+}
+
+// --- SELL build
+
+__global__ void k_count_segments(int64_t rows, const int64_t *__restrict__ rowptr,
+                                 int64_t *__restrict__ nseg, int64_t *__restrict__ is_split,
+                                 int *__restrict__ err) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < rows; i += stride) {
+        int64_t len = rowptr[i + 1] - rowptr[i];
+        if (len >= (int64_t(1) << 24)) atomicOr(err, ERR_ROWLEN);
+        int64_t s = len > 0 ? (len + SEG - 1) / SEG : 1;
+        nseg[i] = s;
+        is_split[i] = s > 1 ? 1 : 0;
+    }
+}
+
+__global__ void k_make_vrows(int64_t rows, const int64_t *__restrict__ rowptr,
+                             const int64_t *__restrict__ vstart, const int64_t *__restrict__ split_id,
+                             const int64_t *__restrict__ is_split, int32_t *__restrict__ vr_row,
+                             int32_t *__restrict__ vr_len, int64_t *__restrict__ vr_start,
+                             int32_t *__restrict__ split_row, int *__restrict__ hist) {
+    __shared__ int sh[SEG + 1];
+    for (int b = threadIdx.x; b <= SEG; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < rows; i += stride) {
+        int64_t a = rowptr[i], len = rowptr[i + 1] - a;
+        int64_t v0 = vstart[i], ns = vstart[i + 1] - v0;
+        for (int64_t s = 0; s < ns; s++) {
+            int64_t l = len - s * SEG;
+            l = l < 0 ? 0 : (l > SEG ? SEG : l);
+            vr_row[v0 + s] = (int32_t)i;
+            vr_len[v0 + s] = (int32_t)l;
+            vr_start[v0 + s] = a + s * SEG;
+            atomicAdd(&sh[l], 1);
+        }
+        if (is_split[i]) split_row[split_id[i]] = (int32_t)i;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b <= SEG; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+}
+
+// bucket b (length b) starts after all longer buckets
+__global__ void k_bucket_starts(const int *__restrict__ hist, int64_t *__restrict__ start) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int b = SEG; b >= 0; b--) {
+            start[b] = run;
+            run += hist[b];
+        }
+    }
+}
+
+__global__ void k_bucket_scatter(int64_t nv, const int32_t *__restrict__ vr_len,
+                                 const int64_t *__restrict__ start, unsigned long long *__restrict__ fill,
+                                 int32_t *__restrict__ sorted) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = tid; v < nv; v += stride) {
+        int l = vr_len[v];
+        int64_t pos = start[l] + (int64_t)atomicAdd(&fill[l], 1ull);
+        sorted[pos] = (int32_t)v;
+    }
+}
+
+__global__ void k_chunk_slots(int64_t nchunks, int64_t nv, const int32_t *__restrict__ sorted,
+                              const int32_t *__restrict__ vr_len, int32_t *__restrict__ chunk_len,
+                              int64_t *__restrict__ slots) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = tid; c < nchunks; c += stride) {
+        // sorted by length descending: the chunk's first virtual row is its longest
+        int l = vr_len[sorted[c * SELL_C]];
+        chunk_len[c] = l;
+        slots[c] = (int64_t)l * SELL_C;
+    }
+    (void)nv;
+}
+
+__global__ void k_fill_sell(int64_t nchunks, int64_t nv, const int32_t *__restrict__ sorted,
+                            const int32_t *__restrict__ vr_row, const int32_t *__restrict__ vr_len,
+                            const int64_t *__restrict__ vr_start, const int64_t *__restrict__ is_split,
+                            const int64_t *__restrict__ split_id, const int32_t *__restrict__ colidx,
+                            const int32_t *__restrict__ vals, const int64_t *__restrict__ chunk_off,
+                            const int32_t *__restrict__ chunk_len, uint32_t *__restrict__ entries,
+                            uint32_t *__restrict__ vrow) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t pos = tid; pos < nchunks * SELL_C; pos += stride) {
+        int64_t c = pos / SELL_C;
+        int lane = (int)(pos % SELL_C);
+        int clen = chunk_len[c];
+        uint32_t *dst = entries + chunk_off[c] + lane;
+        if (pos < nv) {
+            int32_t v = sorted[pos];
+            int32_t r = vr_row[v];
+            int l = vr_len[v];
+            int64_t s = vr_start[v];
+            for (int j = 0; j < clen; j++) {
+                uint32_t w = 0;
+                if (j < l) w = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
+                dst[(int64_t)j * SELL_C] = w;
+            }
+            vrow[pos] = is_split[r] ? (VROW_SPLIT | (uint32_t)split_id[r]) : (uint32_t)r;
+        } else {
+            for (int j = 0; j < clen; j++) dst[(int64_t)j * SELL_C] = 0;
+            vrow[pos] = VROW_EMPTY;
+        }
+    }
+}
+
+int grid_for(wr_ctx *ctx, int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)ctx->num_sms * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+wr_status read_err(wr_ctx *ctx, int *d_err, int *h_err) {
+    WR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    WR_CUDA(cudaStreamSynchronize(ctx->stream));
+    return WR_OK;
+}
+
+}  // namespace
+
+wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n) {
+    if (n <= 0) {
+        WR_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int64_t), ctx->stream));
+        return WR_OK;
+    }
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 1) {
+        k_tile_scan<<<1, SCAN_THREADS, 0, ctx->stream>>>(d_in, n, nullptr, d_out);
+        WR_CUDA(cudaGetLastError());
+        return WR_OK;
+    }
+    DevBuf sums, offs;
+    WR_TRY(dev_alloc(ctx, sums, sizeof(int64_t) * tiles));
+    WR_TRY(dev_alloc(ctx, offs, sizeof(int64_t) * (tiles + 1)));
+    k_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(d_in, n, sums.as<int64_t>());
+    WR_CUDA(cudaGetLastError());
+    WR_TRY(exclusive_scan_i64(ctx, sums.as<int64_t>(), offs.as<int64_t>(), tiles));
+    k_tile_scan<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(d_in, n, offs.as<int64_t>(), d_out);
+    WR_CUDA(cudaGetLastError());
+    // the last tile wrote out[n]; keep the stream ordered for the caller
+    return WR_OK;
+}
+
+wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                       const int32_t *d_colidx, const int32_t *d_vals) {
+    DevBuf err;
+    WR_TRY(dev_alloc(ctx, err, sizeof(int)));
+    WR_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), ctx->stream));
+    int threads = 256;
+    k_validate<<<grid_for(ctx, std::max(rows, nnz), threads), threads, 0, ctx->stream>>>(
+        rows, cols, nnz, d_rowptr, d_colidx, d_vals, err.as<int>());
+    WR_CUDA(cudaGetLastError());
+    int h = 0;
+    WR_TRY(read_err(ctx, err.as<int>(), &h));
+    if (h & ERR_ROWPTR) return fail(WR_EINVAL, "rowptr is not a valid CSR row pointer array");
+    if (h & ERR_COL) return fail(WR_EINVAL, "column index out of range");
+    if (h & ERR_VAL) return fail(WR_EOVERFLOW, "matrix entry outside [-127, 127]");
+    if (h & ERR_ROWLEN) return fail(WR_EOVERFLOW, "a row holds 2^24 or more entries");
+    return WR_OK;
+}
+
+wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                        const int32_t *d_colidx, const int32_t *d_vals, DevBuf &rowptr_t,
+                        DevBuf &colidx_t, DevBuf &vals_t) {
+    DevBuf cnt, fill;
+    WR_TRY(dev_alloc(ctx, cnt, sizeof(int64_t) * (cols + 1)));
+    WR_TRY(dev_alloc(ctx, fill, sizeof(int64_t) * (cols + 1)));
+    WR_TRY(dev_alloc(ctx, rowptr_t, sizeof(int64_t) * (cols + 1)));
+    WR_TRY(dev_alloc(ctx, colidx_t, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    WR_TRY(dev_alloc(ctx, vals_t, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    WR_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int64_t) * (cols + 1), ctx->stream));
+    WR_CUDA(cudaMemsetAsync(fill.ptr, 0, sizeof(int64_t) * (cols + 1), ctx->stream));
+    int threads = 256;
+    if (nnz > 0) {
+        k_count_cols<<<grid_for(ctx, nnz, threads), threads, 0, ctx->stream>>>(nnz, d_colidx,
+                                                                               cnt.as<int64_t>());
+        WR_CUDA(cudaGetLastError());
+    }
+    WR_TRY(exclusive_scan_i64(ctx, cnt.as<int64_t>(), rowptr_t.as<int64_t>(), cols));
+    if (nnz > 0) {
+        k_scatter_transpose<<<grid_for(ctx, rows, threads), threads, 0, ctx->stream>>>(
+            rows, d_rowptr, d_colidx, d_vals, rowptr_t.as<int64_t>(), fill.as<int64_t>(),
+            colidx_t.as<int32_t>(), vals_t.as<int32_t>());
+        WR_CUDA(cudaGetLastError());
+    }
+    return WR_OK;
+}
+
+wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                     const int32_t *d_colidx, const int32_t *d_vals, Sell &out) {
+    out.nrows = rows;
+    out.ncols = cols;
+    const int threads = 256;
+    cudaStream_t st = ctx->stream;
+    DevBuf nseg, is_split, vstart, split_id, err;
+    int64_t R1 = rows + 1;
+    WR_TRY(dev_alloc(ctx, nseg, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, is_split, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, vstart, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, split_id, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, err, sizeof(int)));
+    WR_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), st));
+    if (rows > 0) {
+        k_count_segments<<<grid_for(ctx, rows, threads), threads, 0, st>>>(
+            rows, d_rowptr, nseg.as<int64_t>(), is_split.as<int64_t>(), err.as<int>());
+        WR_CUDA(cudaGetLastError());
+    }
+    WR_TRY(exclusive_scan_i64(ctx, nseg.as<int64_t>(), vstart.as<int64_t>(), rows));
+    WR_TRY(exclusive_scan_i64(ctx, is_split.as<int64_t>(), split_id.as<int64_t>(), rows));
+    int64_t tot[2] = {0, 0};
+    int herr = 0;
+    WR_CUDA(cudaMemcpyAsync(&tot[0], vstart.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaMemcpyAsync(&tot[1], split_id.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaStreamSynchronize(st));
+    if (herr & ERR_ROWLEN) return fail(WR_EOVERFLOW, "a row or column holds 2^24 or more entries");
+    const int64_t nv = tot[0];
+    out.nvrows = nv;
+    out.nsplit = tot[1];
+    out.nchunks = (nv + SELL_C - 1) / SELL_C;
+
+    DevBuf vr_row, vr_len, vr_start, hist, bstart, bfill, sorted, slots;
+    WR_TRY(dev_alloc(ctx, vr_row, sizeof(int32_t) * std::max<int64_t>(nv, 1)));
+    WR_TRY(dev_alloc(ctx, vr_len, sizeof(int32_t) * std::max<int64_t>(nv, 1)));
+    WR_TRY(dev_alloc(ctx, vr_start, sizeof(int64_t) * std::max<int64_t>(nv, 1)));
+    WR_TRY(dev_alloc(ctx, out.split_row, sizeof(int32_t) * std::max<int64_t>(out.nsplit, 1)));
+    WR_TRY(dev_alloc(ctx, hist, sizeof(int) * (SEG + 1)));
+    WR_TRY(dev_alloc(ctx, bstart, sizeof(int64_t) * (SEG + 1)));
+    WR_TRY(dev_alloc(ctx, bfill, sizeof(unsigned long long) * (SEG + 1)));
+    WR_TRY(dev_alloc(ctx, sorted, sizeof(int32_t) * std::max<int64_t>(out.nchunks * SELL_C, 1)));
+    WR_TRY(dev_alloc(ctx, slots, sizeof(int64_t) * (out.nchunks + 1)));
+    WR_TRY(dev_alloc(ctx, out.chunk_off, sizeof(int64_t) * (out.nchunks + 1)));
+    WR_TRY(dev_alloc(ctx, out.chunk_len, sizeof(int32_t) * std::max<int64_t>(out.nchunks, 1)));
+    WR_TRY(dev_alloc(ctx, out.vrow, sizeof(uint32_t) * std::max<int64_t>(out.nchunks * SELL_C, 1)));
+    WR_CUDA(cudaMemsetAsync(hist.ptr, 0, sizeof(int) * (SEG + 1), st));
+    WR_CUDA(cudaMemsetAsync(bfill.ptr, 0, sizeof(unsigned long long) * (SEG + 1), st));
+    if (out.nchunks == 0) {
+        WR_CUDA(cudaMemsetAsync(out.chunk_off.ptr, 0, sizeof(int64_t), st));
+        WR_TRY(dev_alloc(ctx, out.entries, sizeof(uint32_t)));
+        out.nslots = 0;
+        return WR_OK;
+    }
+    k_make_vrows<<<grid_for(ctx, rows, threads), threads, 0, st>>>(
+        rows, d_rowptr, vstart.as<int64_t>(), split_id.as<int64_t>(), is_split.as<int64_t>(),
+        vr_row.as<int32_t>(), vr_len.as<int32_t>(), vr_start.as<int64_t>(), out.split_row.as<int32_t>(),
+        hist.as<int>());
+    WR_CUDA(cudaGetLastError());
+    k_bucket_starts<<<1, 32, 0, st>>>(hist.as<int>(), bstart.as<int64_t>());
+    WR_CUDA(cudaGetLastError());
+    k_bucket_scatter<<<grid_for(ctx, nv, threads), threads, 0, st>>>(
+        nv, vr_len.as<int32_t>(), bstart.as<int64_t>(), bfill.as<unsigned long long>(), sorted.as<int32_t>());
+    WR_CUDA(cudaGetLastError());
+    k_chunk_slots<<<grid_for(ctx, out.nchunks, threads), threads, 0, st>>>(
+        out.nchunks, nv, sorted.as<int32_t>(), vr_len.as<int32_t>(), out.chunk_len.as<int32_t>(),
+        slots.as<int64_t>());
+    WR_CUDA(cudaGetLastError());
+    WR_TRY(exclusive_scan_i64(ctx, slots.as<int64_t>(), out.chunk_off.as<int64_t>(), out.nchunks));
+    int64_t nslots = 0;
+    WR_CUDA(cudaMemcpyAsync(&nslots, out.chunk_off.as<int64_t>() + out.nchunks, sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaStreamSynchronize(st));
+    out.nslots = nslots;
+    WR_TRY(dev_alloc(ctx, out.entries, sizeof(uint32_t) * std::max<int64_t>(nslots, 1)));
+    k_fill_sell<<<grid_for(ctx, out.nchunks * SELL_C, threads), threads, 0, st>>>(
+        out.nchunks, nv, sorted.as<int32_t>(), vr_row.as<int32_t>(), vr_len.as<int32_t>(),
+        vr_start.as<int64_t>(), is_split.as<int64_t>(), split_id.as<int64_t>(), d_colidx, d_vals,
+        out.chunk_off.as<int64_t>(), out.chunk_len.as<int32_t>(), out.entries.as<uint32_t>(),
+        out.vrow.as<uint32_t>());
+    WR_CUDA(cudaGetLastError());
+    WR_CUDA(cudaStreamSynchronize(st));  // temporaries are freed on return
+    return WR_OK;
+}
+
+}  // namespace wr

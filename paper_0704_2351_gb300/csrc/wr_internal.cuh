@@ -1,0 +1,267 @@
+// Internal definitions shared by the CUDA translation units of libwr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/wr.h"
+
+namespace wr {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string &msg);
+wr_status fail(wr_status st, const std::string &msg);
+wr_status cuda_fail(cudaError_t e, const char *what);
+
+#define WR_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::wr::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define WR_TRY(call)                              \
+    do {                                          \
+        wr_status s_ = (call);                    \
+        if (s_ != WR_OK) return s_;               \
+    } while (0)
+
+// ------------------------------------------------------------------ arithmetic mod p
+//
+// Residues are uint32 in [0, p), p < 2^31.  Reduction of a 64-bit value uses
+// Barrett's method with mu = floor(2^64 / p): q = hi64(x * mu) is at most 2
+// below floor(x / p), so r = x - q p < 3 p needs at most two corrections.
+// Signed sums (|s| < 2^62) are shifted by off, a multiple of p >= 2^62.
+
+struct ModP {
+    uint32_t p;
+    uint32_t lazy;   // products (p-1)^2 that fit on top of a value < p in a uint64
+    uint64_t mu;     // floor(2^64 / p)
+    int64_t off;     // multiple of p in [2^62, 2^62 + p)
+};
+
+ModP make_modp(uint32_t p);
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t red64(uint64_t x, const ModP &m) {
+    uint64_t q = mulhi64(x, m.mu);
+    uint64_t r = x - q * (uint64_t)m.p;
+    if (r >= m.p) r -= m.p;
+    if (r >= m.p) r -= m.p;
+    return (uint32_t)r;
+}
+
+__host__ __device__ __forceinline__ uint32_t red_s64(int64_t s, const ModP &m) {
+    return red64((uint64_t)s + (uint64_t)m.off, m);  // |s| < 2^62: the sum is in [0, 2^64)
+}
+
+__host__ __device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, const ModP &m) {
+    return red64((uint64_t)a * b, m);
+}
+
+__host__ __device__ __forceinline__ uint32_t addm(uint32_t a, uint32_t b, const ModP &m) {
+    uint32_t s = a + b;  // < 2^32 since a, b < 2^31
+    return s >= m.p ? s - m.p : s;
+}
+
+__host__ __device__ __forceinline__ uint32_t subm(uint32_t a, uint32_t b, const ModP &m) {
+    return a >= b ? a - b : a + m.p - b;
+}
+
+__host__ __device__ __forceinline__ uint32_t powm(uint32_t a, uint32_t e, const ModP &m) {
+    uint32_t r = 1 % m.p;
+    while (e) {
+        if (e & 1) r = mulm(r, a, m);
+        a = mulm(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// inverse of a != 0 by Fermat's little theorem
+__host__ __device__ __forceinline__ uint32_t invm(uint32_t a, const ModP &m) {
+    return powm(a, m.p - 2, m);
+}
+
+// ------------------------------------------------------------------ random draws
+//
+// SplitMix64 (Steele, Lea, Flood 2014): output for state x is the mix of
+// x + 0x9E3779B97F4A7C15.  Entry idx of the stream with tag t under seed s is
+// h = sm(sm(s ^ t * GOLDEN) + idx).
+
+constexpr uint64_t GOLDEN = 0x9E3779B97F4A7C15ULL;
+
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t x) {
+    uint64_t z = x + GOLDEN;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t stream_hash(uint64_t seed, uint64_t tag, uint64_t idx) {
+    return sm64(sm64(seed ^ (tag * GOLDEN)) + idx);
+}
+
+enum { TAG_X = 1, TAG_Y = 2, TAG_D1 = 3, TAG_D2 = 4 };
+
+bool is_prime_u32(uint64_t n);
+
+// ------------------------------------------------------------------ device memory
+
+// Device allocation in stream order on the context's stream
+// (cudaMallocAsync / cudaFreeAsync): a buffer released at scope exit is
+// freed after the work already queued on that stream.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), bytes(o.bytes), stream(o.stream) { o.ptr = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); ptr = o.ptr; bytes = o.bytes; stream = o.stream; o.ptr = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// ------------------------------------------------------------------ SELL-C-sigma layout
+//
+// Rows are cut into segments ("virtual rows") of at most SEG entries; virtual
+// rows are sorted by length (descending) and packed by chunks of 32.  Chunk c
+// holds its entries slot-major: entry j of the chunk's lane r is at
+// entries[off[c] + 32 j + r], a packed word (col << 8) | (uint8)val.  Padding
+// words are 0 (column 0, value 0).  vrow[32 c + r] is the output row, or
+// SPLIT | split_id for a segment of a row that was cut (its partial sums are
+// added exactly into an int64 accumulator and finished by a second kernel),
+// or EMPTY past the last virtual row.
+
+constexpr int SELL_C = 32;
+constexpr int SEG = 256;
+constexpr uint32_t VROW_SPLIT = 0x80000000u;
+constexpr uint32_t VROW_EMPTY = 0xFFFFFFFFu;
+
+struct Sell {
+    int64_t nrows = 0;     // output rows
+    int64_t ncols = 0;     // gathered dimension
+    int64_t nvrows = 0;
+    int64_t nchunks = 0;
+    int64_t nslots = 0;    // entries incl. padding
+    int64_t nsplit = 0;    // rows that were cut into segments
+    DevBuf entries;        // uint32 [nslots]
+    DevBuf chunk_off;      // int64  [nchunks + 1]
+    DevBuf chunk_len;      // int32  [nchunks]
+    DevBuf vrow;           // uint32 [nchunks * 32]
+    DevBuf split_row;      // int32  [nsplit]
+};
+
+struct SellView {
+    int64_t nrows, ncols, nchunks, nsplit;
+    const uint32_t *entries;
+    const int64_t *chunk_off;
+    const int32_t *chunk_len;
+    const uint32_t *vrow;
+    const int32_t *split_row;
+};
+
+inline SellView view(const Sell &s) {
+    return SellView{s.nrows, s.ncols, s.nchunks, s.nsplit, s.entries.as<uint32_t>(),
+                    s.chunk_off.as<int64_t>(), s.chunk_len.as<int32_t>(), s.vrow.as<uint32_t>(),
+                    s.split_row.as<int32_t>()};
+}
+
+}  // namespace wr
+
+// ------------------------------------------------------------------ opaque handles
+
+struct wr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    bool profiling = false;
+    wr_timings last{};
+};
+
+struct wr_matrix {
+    wr_ctx *ctx = nullptr;
+    int64_t rows = 0, cols = 0, nnz = 0;
+    wr::Sell a;    // rows of A
+    wr::Sell at;   // rows of A^T
+};
+
+struct wr_result {
+    uint32_t prime = 0, m = 0, n = 0;
+    int64_t rank = 0, deg_det = 0, codeg = 0, sum_delta = 0, seq_len = 0;
+    std::vector<uint32_t> seq;       // L*m*n (when wanted)
+    std::vector<uint32_t> gen;       // (dmax+1)*n*n (when wanted)
+    std::vector<int32_t> gen_deg;    // n
+    int64_t gen_dmax = -1;
+};
+
+namespace wr {
+
+wr_status dev_alloc(wr_ctx *ctx, DevBuf &b, size_t bytes);
+
+// format (wr_format.cu)
+wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                     const int32_t *d_colidx, const int32_t *d_vals, Sell &out);
+wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                        const int32_t *d_colidx, const int32_t *d_vals, DevBuf &rowptr_t,
+                        DevBuf &colidx_t, DevBuf &vals_t);
+wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
+                       const int32_t *d_colidx, const int32_t *d_vals);
+wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n);
+
+// sequence (wr_spmm.cu)
+struct SeqPlan;
+wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
+                       uint32_t *d_S, double *setup_ms, double *seq_ms);
+wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
+                         const uint32_t *d_in, uint32_t *d_out, int64_t width);
+
+// sigma-basis and readout (wr_sigma.cu)
+wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n, uint32_t p,
+                      uint32_t *d_P, int32_t *d_deg, int64_t Dcap);
+wr_status det_valuation(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T, uint32_t p,
+                        int64_t *val);
+struct Readout {
+    int64_t rank, deg_det, codeg, sum_delta, vP, dmax;
+    std::vector<int32_t> delta;
+};
+wr_status rank_readout(wr_ctx *ctx, const uint32_t *d_P, const int32_t *d_deg, int m, int n,
+                       uint32_t p, int64_t Dcap, Readout &out, std::vector<uint32_t> *gen);
+
+// parameters
+struct Resolved {
+    uint32_t p;
+    int m, n;            // block sizes
+    int nv;              // padded block width (1, 2, 4, 8, 16, 32)
+    int side;            // 0: N = cols, 1: N = rows
+    int64_t N, M;        // dimension of A~ and the other dimension
+    int64_t L;
+    bool symmetric;
+    uint64_t seed;
+};
+wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r);
+
+int padded_width(int n);
+
+}  // namespace wr

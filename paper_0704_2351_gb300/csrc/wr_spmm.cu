@@ -1,0 +1,512 @@
+// The block Wiedemann sequence on the device (Section 2.4 step 2 of the paper;
+// Section 2.1 for the block sequence X^T A~^i Y; Section 2.3 for A~).
+//
+// With T_k = D1 A~^k Y (stored, N x nv residues) the recurrence is
+//   W       = D2 (A T_k)                    SpMM pass 1 (rows of A, or of A^T)
+//   T_{k+1} = D1^2 (A^T W)                  SpMM pass 2 (the other layout)
+//   S_{k+1} = Xh^T T_{k+1},  Xh = D1^{-1} X (so that S_k = X^T A~^k Y)
+// Every row sum of a pass is exact in int64 (|a| <= 127, residues < 2^31,
+// < 2^24 terms) and reduced once; the diagonal scaling is the epilogue.
+// The paper's one-process-per-column scheme (Section 3.1) becomes the block
+// width: all n columns of T ride on one pass over the matrix, each gathered
+// row of T being one vector load of n residues.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "wr_internal.cuh"
+
+namespace wr {
+
+namespace {
+
+template <int NV>
+struct Lanes {
+    static constexpr int G = NV >= 4 ? NV / 4 : 1;  // lanes per row
+    static constexpr int W = NV / G;                 // residues per lane (1, 2 or 4)
+    static constexpr int RPW = 32 / G;               // rows per warp pass
+};
+
+template <int W>
+__device__ __forceinline__ void ldv(const uint32_t *p, uint32_t (&v)[W]);
+template <>
+__device__ __forceinline__ void ldv<1>(const uint32_t *p, uint32_t (&v)[1]) { v[0] = __ldg(p); }
+template <>
+__device__ __forceinline__ void ldv<2>(const uint32_t *p, uint32_t (&v)[2]) {
+    uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+}
+template <>
+__device__ __forceinline__ void ldv<4>(const uint32_t *p, uint32_t (&v)[4]) {
+    uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+template <int W>
+__device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&v)[W]);
+template <>
+__device__ __forceinline__ void stv<1>(uint32_t *p, const uint32_t (&v)[1]) { p[0] = v[0]; }
+template <>
+__device__ __forceinline__ void stv<2>(uint32_t *p, const uint32_t (&v)[2]) {
+    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void stv<4>(uint32_t *p, const uint32_t (&v)[4]) {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+__device__ __forceinline__ int entry_val(uint32_t e) { return (int)(int8_t)(e & 0xFFu); }
+
+// One warp per SELL chunk of 32 virtual rows; G lanes share a row and each
+// holds W of its NV residues, so every gathered row of x is one coalesced
+// NV*4-byte access.  y[row] = scale[row] * (sum_j a_j x[col_j]) mod p.
+template <int NV>
+__global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__restrict__ x,
+                                              uint32_t *__restrict__ y,
+                                              const uint32_t *__restrict__ scale,
+                                              unsigned long long *__restrict__ acc64, ModP mp,
+                                              int *__restrict__ term_counter) {
+    using Ln = Lanes<NV>;
+    constexpr int W = Ln::W;
+    if (term_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(term_counter, 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (chunk >= A.nchunks) return;
+    const int64_t base = A.chunk_off[chunk];
+    const int len = A.chunk_len[chunk];
+    const int sub = lane / Ln::G, part = lane % Ln::G;
+    const uint32_t *xb = x + part * W;
+#pragma unroll 1
+    for (int pass = 0; pass < Ln::G; pass++) {
+        const int r = pass * Ln::RPW + sub;
+        const uint32_t *e = A.entries + base + r;
+        int64_t acc[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) acc[w] = 0;
+        int j = 0;
+        for (; j + 4 <= len; j += 4) {
+            const uint32_t e0 = __ldg(e + (j + 0) * SELL_C);
+            const uint32_t e1 = __ldg(e + (j + 1) * SELL_C);
+            const uint32_t e2 = __ldg(e + (j + 2) * SELL_C);
+            const uint32_t e3 = __ldg(e + (j + 3) * SELL_C);
+            uint32_t v0[W], v1[W], v2[W], v3[W];
+            ldv<W>(xb + (e0 >> 8) * NV, v0);
+            ldv<W>(xb + (e1 >> 8) * NV, v1);
+            ldv<W>(xb + (e2 >> 8) * NV, v2);
+            ldv<W>(xb + (e3 >> 8) * NV, v3);
+            const int a0 = entry_val(e0), a1 = entry_val(e1), a2 = entry_val(e2), a3 = entry_val(e3);
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                acc[w] += (int64_t)a0 * (int32_t)v0[w];
+                acc[w] += (int64_t)a1 * (int32_t)v1[w];
+                acc[w] += (int64_t)a2 * (int32_t)v2[w];
+                acc[w] += (int64_t)a3 * (int32_t)v3[w];
+            }
+        }
+        for (; j < len; j++) {
+            const uint32_t e0 = __ldg(e + j * SELL_C);
+            uint32_t v0[W];
+            ldv<W>(xb + (e0 >> 8) * NV, v0);
+            const int a0 = entry_val(e0);
+#pragma unroll
+            for (int w = 0; w < W; w++) acc[w] += (int64_t)a0 * (int32_t)v0[w];
+        }
+        const uint32_t vr = A.vrow[chunk * SELL_C + r];
+        if (vr == VROW_EMPTY) continue;
+        if (vr & VROW_SPLIT) {
+            unsigned long long *dst = acc64 + (size_t)(vr & ~VROW_SPLIT) * NV + part * W;
+#pragma unroll
+            for (int w = 0; w < W; w++) atomicAdd(dst + w, (unsigned long long)acc[w]);
+        } else {
+            const uint32_t s = __ldg(scale + vr);
+            uint32_t o[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) o[w] = mulm(s, red_s64(acc[w], mp), mp);
+            stv<W>(y + (size_t)vr * NV + part * W, o);
+        }
+    }
+}
+
+// Rows that were cut into segments: their exact int64 sums were added into
+// acc64; reduce, scale, store, and clear the accumulator for the next pass.
+__global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restrict__ split_row,
+                                 unsigned long long *__restrict__ acc64, uint32_t *__restrict__ y,
+                                 const uint32_t *__restrict__ scale, ModP mp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsplit * nv) return;
+    int64_t sid = i / nv;
+    int b = (int)(i % nv);
+    int32_t r = split_row[sid];
+    unsigned long long s = acc64[i];
+    acc64[i] = 0;
+    y[(size_t)r * nv + b] = mulm(scale[r], red_s64((int64_t)s, mp), mp);
+}
+
+// S_raw[k] += Xh^T T (m x n block), k read from the term counter.  Partial
+// sums are reduced mod p before the exact uint64 atomics, so the sum over
+// blocks cannot overflow and its value does not depend on the order.
+constexpr int PROJ_THREADS = 256;
+constexpr int PROJ_TILE = 64;
+
+template <int KLAZY>
+__global__ void __launch_bounds__(PROJ_THREADS)
+    k_project(int64_t N, int m, int n, int nv, const uint32_t *__restrict__ xh,
+              const uint32_t *__restrict__ t, unsigned long long *__restrict__ s_raw,
+              const int *__restrict__ term_counter, ModP mp) {
+    __shared__ uint32_t xs[PROJ_TILE * 32];
+    __shared__ uint32_t ts[PROJ_TILE * 32];
+    __shared__ unsigned long long red[PROJ_THREADS];
+    const int E = m * n;
+    const int groups = E >= PROJ_THREADS ? 1 : PROJ_THREADS / E;
+    const int tid = threadIdx.x;
+    const int g = E >= PROJ_THREADS ? 0 : tid / E;
+    const bool active = E >= PROJ_THREADS || g < groups;
+    unsigned long long acc[4] = {0, 0, 0, 0};
+    const int64_t ntiles = (N + PROJ_TILE - 1) / PROJ_TILE;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * PROJ_TILE;
+        const int rows = (int)min64(PROJ_TILE, N - r0);
+        __syncthreads();
+        for (int i = tid; i < rows * m; i += PROJ_THREADS) xs[i] = xh[r0 * m + i];
+        for (int i = tid; i < rows * n; i += PROJ_THREADS) {
+            int rr = i / n, b = i % n;
+            ts[i] = t[(r0 + rr) * nv + b];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int k = 0; k < 4; k++) {
+            const int e = E >= PROJ_THREADS ? tid + k * PROJ_THREADS : (k == 0 ? tid % E : -1);
+            if (e < 0 || e >= E) break;
+            const int a = e / n, b = e % n;
+            unsigned long long s = acc[k];
+            int cnt = 0;
+            for (int rr = g; rr < rows; rr += groups) {
+                s += (unsigned long long)xs[rr * m + a] * ts[rr * n + b];
+                if (++cnt == KLAZY) { s = red64(s, mp); cnt = 0; }
+            }
+            acc[k] = red64(s, mp);
+        }
+    }
+    const int k_term = *term_counter;
+    unsigned long long *dst = s_raw + (size_t)k_term * E;
+    if (E >= PROJ_THREADS) {
+        for (int k = 0; k < 4; k++) {
+            const int e = tid + k * PROJ_THREADS;
+            if (e < E && acc[k]) atomicAdd(dst + e, acc[k]);
+        }
+    } else {
+        red[tid] = active ? acc[0] : 0;
+        __syncthreads();
+        if (tid < E) {
+            unsigned long long s = 0;
+            for (int gg = 0; gg < groups; gg++) s += red[gg * E + tid];
+            if (s) atomicAdd(dst + tid, s);
+        }
+    }
+}
+
+__global__ void k_reduce_seq(int64_t count, const unsigned long long *__restrict__ s_raw,
+                             uint32_t *__restrict__ S, ModP mp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) S[i] = red64(s_raw[i], mp);
+}
+
+// random draws (tags: X 1, Y 2, D1 3, D2 4)
+__global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t p,
+                              uint32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = (uint32_t)(1 + stream_hash(seed, tag, (uint64_t)i) % (uint64_t)(p - 1));
+}
+
+// T0 = D1 Y (padded to nv columns with zeros), Xh = D1^{-1} X, d1sq = D1^2.
+__global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, int symmetric,
+                          const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
+                          uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, ModP mp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t d = d1[i];
+    const uint32_t dinv = invm(d, mp);
+    d1sq[i] = mulm(d, d, mp);
+    for (int b = 0; b < nv; b++) {
+        uint32_t yv = 0;
+        if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, (uint64_t)i * n + b) % mp.p);
+        t0[i * nv + b] = mulm(d, yv, mp);
+    }
+    for (int a = 0; a < m; a++) {
+        uint64_t tag = symmetric ? TAG_Y : TAG_X;
+        uint64_t width = symmetric ? (uint64_t)n : (uint64_t)m;
+        uint32_t xv = (uint32_t)(stream_hash(seed, tag, (uint64_t)i * width + a) % mp.p);
+        xh[i * m + a] = mulm(dinv, xv, mp);
+    }
+}
+
+// out (N x nv, padded) = D1 in (N x width)
+__global__ void k_scale_pad(int64_t N, int width, int nv, const uint32_t *__restrict__ in,
+                            const uint32_t *__restrict__ d1, uint32_t *__restrict__ out, ModP mp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * nv) return;
+    int64_t r = i / nv;
+    int b = (int)(i % nv);
+    out[i] = b < width ? mulm(d1[r], in[r * width + b], mp) : 0;
+}
+
+__global__ void k_unpad(int64_t N, int width, int nv, const uint32_t *__restrict__ in,
+                        uint32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * width) return;
+    int64_t r = i / width;
+    int b = (int)(i % width);
+    out[i] = in[r * nv + b];
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <int NV>
+wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y,
+                        const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
+                        int *term_counter) {
+    if (A.nchunks > 0) {
+        int64_t threads = A.nchunks * 32;
+        k_spmm<NV><<<blocks_for(threads, 256), 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp,
+                                                                      term_counter);
+        WR_CUDA(cudaGetLastError());
+    } else if (term_counter) {
+        // keep the term counter moving even for an empty matrix
+        k_spmm<NV><<<1, 32, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter);
+        WR_CUDA(cudaGetLastError());
+    }
+    if (A.nsplit > 0) {
+        int64_t cnt = A.nsplit * NV;
+        k_finalize_split<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
+                                                                       y, scale, mp);
+        WR_CUDA(cudaGetLastError());
+    }
+    return WR_OK;
+}
+
+wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
+                      const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
+                      int *term_counter) {
+    switch (nv) {
+        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        default: return fail(WR_EINVAL, "unsupported padded block width");
+    }
+}
+
+wr_status launch_project(wr_ctx *ctx, int64_t N, int m, int n, int nv, const uint32_t *xh,
+                         const uint32_t *t, unsigned long long *s_raw, const int *term_counter,
+                         const ModP &mp) {
+    int64_t ntiles = (N + PROJ_TILE - 1) / PROJ_TILE;
+    int64_t grid = std::min<int64_t>(std::max<int64_t>(ntiles, 1), (int64_t)ctx->num_sms * 4);
+    if (mp.lazy >= 16)
+        k_project<16><<<(unsigned)grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, nv, xh, t, s_raw,
+                                                                         term_counter, mp);
+    else
+        k_project<4><<<(unsigned)grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, nv, xh, t, s_raw,
+                                                                        term_counter, mp);
+    WR_CUDA(cudaGetLastError());
+    return WR_OK;
+}
+
+}  // namespace
+
+// State of one sequence run (device buffers), shared by wr_rank and the
+// step-level entry points.
+struct SeqState {
+    Resolved r;
+    ModP mp;
+    const Sell *first = nullptr;   // pass 1 layout (output in the other space)
+    const Sell *second = nullptr;  // pass 2 layout (output in N-space)
+    DevBuf T, Wb, D1, D2, d1sq, xh, acc1, acc2, s_raw, counter;
+};
+
+static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r, SeqState &st,
+                           bool want_projection) {
+    st.r = r;
+    st.mp = make_modp(r.p);
+    st.first = r.side == 0 ? &mat->a : &mat->at;
+    st.second = r.side == 0 ? &mat->at : &mat->a;
+    const int nv = r.nv;
+    WR_TRY(dev_alloc(ctx, st.T, sizeof(uint32_t) * std::max<int64_t>(r.N * nv, 1)));
+    WR_TRY(dev_alloc(ctx, st.Wb, sizeof(uint32_t) * std::max<int64_t>(r.M * nv, 1)));
+    WR_TRY(dev_alloc(ctx, st.D1, sizeof(uint32_t) * std::max<int64_t>(r.N, 1)));
+    WR_TRY(dev_alloc(ctx, st.D2, sizeof(uint32_t) * std::max<int64_t>(r.M, 1)));
+    WR_TRY(dev_alloc(ctx, st.d1sq, sizeof(uint32_t) * std::max<int64_t>(r.N, 1)));
+    WR_TRY(dev_alloc(ctx, st.xh, sizeof(uint32_t) * std::max<int64_t>(r.N * r.m, 1)));
+    WR_TRY(dev_alloc(ctx, st.acc1, sizeof(unsigned long long) * std::max<int64_t>(st.first->nsplit * nv, 1)));
+    WR_TRY(dev_alloc(ctx, st.acc2, sizeof(unsigned long long) * std::max<int64_t>(st.second->nsplit * nv, 1)));
+    WR_TRY(dev_alloc(ctx, st.counter, sizeof(int)));
+    cudaStream_t s = ctx->stream;
+    WR_CUDA(cudaMemsetAsync(st.acc1.ptr, 0, st.acc1.bytes, s));
+    WR_CUDA(cudaMemsetAsync(st.acc2.ptr, 0, st.acc2.bytes, s));
+    WR_CUDA(cudaMemsetAsync(st.counter.ptr, 0, sizeof(int), s));
+    if (r.N > 0)
+        k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, st.D1.as<uint32_t>());
+    if (r.M > 0)
+        k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, st.D2.as<uint32_t>());
+    WR_CUDA(cudaGetLastError());
+    if (want_projection && r.N > 0) {
+        k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, nv, r.seed, r.symmetric ? 1 : 0,
+                                                      st.D1.as<uint32_t>(), st.T.as<uint32_t>(),
+                                                      st.xh.as<uint32_t>(), st.d1sq.as<uint32_t>(), st.mp);
+        WR_CUDA(cudaGetLastError());
+    }
+    return WR_OK;
+}
+
+// One iteration: T <- D1^2 A^T D2 A T (or the rows-side analogue), then the
+// projection of the new T into S_raw[counter].
+static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
+    const int nv = st.r.nv;
+    SellView f = view(*st.first), sc = view(*st.second);
+    if (ev) WR_CUDA(cudaEventRecord(ev[0], ctx->stream));
+    WR_TRY(launch_spmm(ctx, nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
+                       st.acc1.as<unsigned long long>(), st.mp, st.counter.as<int>()));
+    if (ev) WR_CUDA(cudaEventRecord(ev[1], ctx->stream));
+    WR_TRY(launch_spmm(ctx, nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.d1sq.as<uint32_t>(),
+                       st.acc2.as<unsigned long long>(), st.mp, nullptr));
+    if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
+    WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
+                          st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp));
+    return WR_OK;
+}
+
+static double spmm_pass_bytes(const Sell &s, int nv, int64_t nnz) {
+    // packed entries (4 B each), gathered block read once, output written
+    // once, one scale residue per output row
+    return 4.0 * (double)nnz + 4.0 * nv * (double)(s.ncols + s.nrows) + 4.0 * (double)s.nrows;
+}
+
+wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
+                       uint32_t *d_S, double *setup_ms, double *seq_ms) {
+    Resolved r;
+    WR_TRY(resolve(mat, &prm, r));
+    r.L = L;
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0, e1, e2;
+    WR_CUDA(cudaEventCreate(&e0));
+    WR_CUDA(cudaEventCreate(&e1));
+    WR_CUDA(cudaEventCreate(&e2));
+    WR_CUDA(cudaEventRecord(e0, s));
+    SeqState st;
+    WR_TRY(seq_setup(ctx, mat, r, st, true));
+    const int64_t E = (int64_t)r.m * r.n;
+    WR_TRY(dev_alloc(ctx, st.s_raw, sizeof(unsigned long long) * std::max<int64_t>(L * E, 1)));
+    WR_CUDA(cudaMemsetAsync(st.s_raw.ptr, 0, st.s_raw.bytes, s));
+    if (L > 0)
+        WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp));
+    WR_CUDA(cudaEventRecord(e1, s));
+
+    // profiling: every PROF_EVERY-th group of iterations is launched eagerly
+    // with CUDA events around the two SpMM passes
+    const int64_t iters = std::max<int64_t>(L - 1, 0);
+    const int64_t G = 64;
+    const int PROF_EVERY = 8;
+    std::vector<cudaEvent_t> pev;
+    if (ctx->profiling) {
+        pev.resize(3 * G);
+        for (auto &e : pev) WR_CUDA(cudaEventCreate(&e));
+    }
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    if (iters >= G) {
+        WR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        wr_status cst = WR_OK;
+        for (int64_t i = 0; i < G && cst == WR_OK; i++) cst = seq_iteration(ctx, st, nullptr);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (cst != WR_OK) { if (graph) cudaGraphDestroy(graph); return cst; }
+        WR_CUDA(ce);
+        WR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    int64_t done = 0, group = 0;
+    wr_status loop_st = WR_OK;
+    while (done < iters && loop_st == WR_OK) {
+        const int64_t todo = std::min(G, iters - done);
+        if (todo == G && exec && !(ctx->profiling && group % PROF_EVERY == 0)) {
+            cudaError_t ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) loop_st = cuda_fail(ce, "cudaGraphLaunch");
+        } else {
+            const bool prof = ctx->profiling;
+            for (int64_t i = 0; i < todo && loop_st == WR_OK; i++)
+                loop_st = seq_iteration(ctx, st, prof ? &pev[3 * i] : nullptr);
+            if (prof && loop_st == WR_OK) {
+                cudaError_t ce = cudaEventSynchronize(pev[3 * (todo - 1) + 2]);
+                if (ce != cudaSuccess) loop_st = cuda_fail(ce, "cudaEventSynchronize");
+                for (int64_t i = 0; i < todo && loop_st == WR_OK; i++) {
+                    float a = 0, b = 0;
+                    cudaEventElapsedTime(&a, pev[3 * i], pev[3 * i + 1]);
+                    cudaEventElapsedTime(&b, pev[3 * i + 1], pev[3 * i + 2]);
+                    prof_ms += a + b;
+                    prof_launches += 2;
+                    ctx->last.spmm_bytes += spmm_pass_bytes(*st.first, r.nv, mat->nnz) +
+                                            spmm_pass_bytes(*st.second, r.nv, mat->nnz);
+                }
+            }
+        }
+        done += todo;
+        group++;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto &e : pev) cudaEventDestroy(e);
+    WR_TRY(loop_st);
+    if (L * E > 0) {
+        k_reduce_seq<<<blocks_for(L * E, 256), 256, 0, s>>>(L * E, st.s_raw.as<unsigned long long>(), d_S,
+                                                           st.mp);
+        WR_CUDA(cudaGetLastError());
+    }
+    WR_CUDA(cudaEventRecord(e2, s));
+    WR_CUDA(cudaEventSynchronize(e2));
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    if (setup_ms) *setup_ms = a;
+    if (seq_ms) *seq_ms = b;
+    ctx->last.spmm_ms += prof_ms;
+    ctx->last.spmm_launches += prof_launches;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    return WR_OK;
+}
+
+wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, const uint32_t *d_in,
+                         uint32_t *d_out, int64_t width) {
+    if (width < 1 || width > 32) return fail(WR_EINVAL, "width must be in 1..32");
+    wr_params p2 = prm;
+    p2.n = (uint32_t)width;
+    p2.m = 1;
+    Resolved r;
+    WR_TRY(resolve(mat, &p2, r));
+    SeqState st;
+    WR_TRY(seq_setup(ctx, mat, r, st, false));
+    cudaStream_t s = ctx->stream;
+    if (r.N > 0) {
+        k_scale_pad<<<blocks_for(r.N * r.nv, 256), 256, 0, s>>>(r.N, (int)width, r.nv, d_in,
+                                                               st.D1.as<uint32_t>(), st.T.as<uint32_t>(), st.mp);
+        WR_CUDA(cudaGetLastError());
+    }
+    SellView f = view(*st.first), sc = view(*st.second);
+    WR_TRY(launch_spmm(ctx, r.nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
+                       st.acc1.as<unsigned long long>(), st.mp, nullptr));
+    // second pass scaled by D1 (not D1^2): out = D1 A^T D2 A D1 in
+    WR_TRY(launch_spmm(ctx, r.nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.D1.as<uint32_t>(),
+                       st.acc2.as<unsigned long long>(), st.mp, nullptr));
+    if (r.N > 0) {
+        k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out);
+        WR_CUDA(cudaGetLastError());
+    }
+    WR_CUDA(cudaStreamSynchronize(s));
+    return WR_OK;
+}
+
+}  // namespace wr

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libwr (include/wr.h), same names as the C ABI.
+
+Argument marshalling only: every step of the rank path runs in libwr's CUDA
+kernels.  Device pointers may be given as integers or as objects with a
+data_ptr() method (for example torch tensors on the context's device).
+Errors raise WrError with the library's status and message.  There is no
+fallback: if libwr.so is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwr.so")
+
+WR_OK, WR_EINVAL, WR_ENOMEM, WR_EDEVICE, WR_ETIMEDOUT = 0, -1, -2, -3, -4
+WR_ENOTPRIME, WR_EOVERFLOW, WR_EPROBFAIL, WR_EBUSY = -5, -6, -7, -8
+WR_PROJ_GENERIC, WR_PROJ_SYMMETRIC = 0, 1
+WR_SIDE_AUTO, WR_SIDE_COLS, WR_SIDE_ROWS = -1, 0, 1
+WR_WANT_SEQUENCE, WR_WANT_GENERATOR = 1, 2
+
+
+class WrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("wr status %d: %s" % (status, message))
+        self.status = status
+        self.message = message
+
+
+class wr_params(ctypes.Structure):
+    _fields_ = [("prime", ctypes.c_uint32), ("m", ctypes.c_uint32), ("n", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("projection", ctypes.c_int32), ("side", ctypes.c_int32),
+                ("seq_len", ctypes.c_uint64), ("want", ctypes.c_uint32)]
+
+
+class wr_timings(ctypes.Structure):
+    _fields_ = [("setup_ms", ctypes.c_double), ("sequence_ms", ctypes.c_double),
+                ("sigma_ms", ctypes.c_double), ("readout_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("spmm_ms", ctypes.c_double),
+                ("spmm_launches", ctypes.c_int64), ("spmm_bytes", ctypes.c_double)]
+
+
+class wr_server_cfg(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64), ("queue_cap", ctypes.c_int32)]
+
+
+class wr_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("throughput_rps", ctypes.c_double), ("max_resident", ctypes.c_int32)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libwr.so is not built (run __graft_entry__.build()); there is no fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+vp, i64, u64, u32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+P = ctypes.POINTER
+_sig = {
+    "wr_create": ([P(vp), ctypes.c_int, vp], ctypes.c_int),
+    "wr_destroy": ([vp], None),
+    "wr_last_error": ([], ctypes.c_char_p),
+    "wr_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
+    "wr_last_timings": ([vp, P(wr_timings)], ctypes.c_int),
+    "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
+    "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
+    "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
+    "wr_matrix_free": ([vp], None),
+    "wr_rank": ([vp, vp, P(wr_params), P(vp)], ctypes.c_int),
+    "wr_rank_batch": ([vp, ctypes.c_size_t, P(vp), P(wr_params), P(vp)], ctypes.c_int),
+    "wr_result_rank": ([vp], u64),
+    "wr_result_info": ([vp, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
+    "wr_result_sequence": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
+    "wr_result_generator": ([vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
+    "wr_result_free": ([vp], None),
+    "wr_blackbox_apply_device": ([vp, vp, P(wr_params), vp, vp, i64], ctypes.c_int),
+    "wr_sequence_device": ([vp, vp, P(wr_params), vp, u64], ctypes.c_int),
+    "wr_sigma_basis_device": ([vp, vp, u64, u32, u32, u32, vp, vp, i64], ctypes.c_int),
+    "wr_det_valuation_device": ([vp, vp, i64, i64, u32, P(i64)], ctypes.c_int),
+    "wr_server_start": ([vp, P(wr_server_cfg), P(vp)], ctypes.c_int),
+    "wr_submit": ([vp, vp, P(wr_params), P(u64)], ctypes.c_int),
+    "wr_wait": ([vp, u64, u32, P(vp)], ctypes.c_int),
+    "wr_server_stats": ([vp, P(wr_stats)], ctypes.c_int),
+    "wr_server_stop": ([vp], None),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _check(st: int):
+    if st != WR_OK:
+        raise WrError(st, _lib.wr_last_error().decode(errors="replace"))
+
+
+def _dptr(x) -> int:
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def make_params(prime: int, m: int, n: int, seed: int, projection: int = WR_PROJ_GENERIC,
+                side: int = WR_SIDE_AUTO, seq_len: int = 0, want: int = 0) -> wr_params:
+    return wr_params(prime, m, n, seed & 0xFFFFFFFFFFFFFFFF, projection, side, seq_len, want)
+
+
+# ------------------------------------------------------------------ context
+
+def wr_create(device: int = 0, stream=None) -> int:
+    h = vp()
+    _check(_lib.wr_create(ctypes.byref(h), device, vp(_dptr(stream) if stream is not None else None)))
+    return h.value
+
+
+def wr_destroy(ctx: int) -> None:
+    _lib.wr_destroy(vp(ctx))
+
+
+def wr_last_error() -> str:
+    return _lib.wr_last_error().decode(errors="replace")
+
+
+def wr_set_profiling(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_profiling(vp(ctx), 1 if on else 0))
+
+
+def wr_last_timings(ctx: int) -> dict:
+    t = wr_timings()
+    _check(_lib.wr_last_timings(vp(ctx), ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in wr_timings._fields_}
+
+
+# ------------------------------------------------------------------ matrices
+
+def wr_matrix_load_csr(ctx: int, rows: int, cols: int, rowptr, colidx, vals) -> int:
+    rp = _np(rowptr, np.int64)
+    ci = _np(colidx, np.int32)
+    va = _np(vals, np.int32)
+    h = vp()
+    _check(_lib.wr_matrix_load_csr(vp(ctx), rows, cols, rp.ctypes.data, ci.ctypes.data, va.ctypes.data,
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def wr_matrix_load_csr_device(ctx: int, rows: int, cols: int, nnz: int, d_rowptr, d_colidx, d_vals) -> int:
+    h = vp()
+    _check(_lib.wr_matrix_load_csr_device(vp(ctx), rows, cols, nnz, vp(_dptr(d_rowptr)), vp(_dptr(d_colidx)),
+                                          vp(_dptr(d_vals)), ctypes.byref(h)))
+    return h.value
+
+
+def wr_matrix_info(mat: int) -> dict:
+    v = [i64() for _ in range(5)]
+    _check(_lib.wr_matrix_info(vp(mat), *[ctypes.byref(x) for x in v]))
+    return dict(zip(["rows", "cols", "nnz", "slots_a", "slots_at"], [x.value for x in v]))
+
+
+def wr_matrix_free(mat: int) -> None:
+    _lib.wr_matrix_free(vp(mat))
+
+
+# ------------------------------------------------------------------ rank
+
+def wr_rank(ctx: int, mat: int, params: wr_params) -> int:
+    h = vp()
+    _check(_lib.wr_rank(vp(ctx), vp(mat), ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def wr_rank_batch(ctx: int, mats: Sequence[int], params: Sequence[wr_params]) -> list:
+    n = len(mats)
+    marr = (vp * n)(*[vp(m) for m in mats])
+    parr = (wr_params * n)(*params)
+    outs = (vp * n)()
+    _check(_lib.wr_rank_batch(vp(ctx), n, marr, parr, outs))
+    return [o for o in outs]
+
+
+def wr_result_rank(res: int) -> int:
+    return int(_lib.wr_result_rank(vp(res)))
+
+
+def wr_result_info(res: int) -> dict:
+    v = [i64() for _ in range(4)]
+    _check(_lib.wr_result_info(vp(res), *[ctypes.byref(x) for x in v]))
+    return dict(zip(["deg_det", "codeg", "sum_delta", "seq_len"], [x.value for x in v]))
+
+
+def wr_result_sequence(res: int, m: int, n: int) -> np.ndarray:
+    L = wr_result_info(res)["seq_len"]
+    out = np.empty(L * m * n, dtype=np.uint32)
+    _check(_lib.wr_result_sequence(vp(res), out.ctypes.data, out.size))
+    return out.reshape(L, m, n)
+
+
+def wr_result_generator(res: int, n: int):
+    deg = np.empty(n, dtype=np.int32)
+    _check(_lib.wr_result_generator(vp(res), None, 0, deg.ctypes.data))
+    dmax = int(deg.max()) if n else 0
+    coeffs = np.empty((dmax + 1) * n * n, dtype=np.uint32)
+    _check(_lib.wr_result_generator(vp(res), coeffs.ctypes.data, coeffs.size, deg.ctypes.data))
+    return coeffs.reshape(dmax + 1, n, n), deg
+
+
+def wr_result_free(res: int) -> None:
+    _lib.wr_result_free(vp(res))
+
+
+# ------------------------------------------------------------------ step-level calls
+
+def wr_blackbox_apply_device(ctx: int, mat: int, params: wr_params, d_in, d_out, width: int) -> None:
+    _check(_lib.wr_blackbox_apply_device(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_in)),
+                                         vp(_dptr(d_out)), width))
+
+
+def wr_sequence_device(ctx: int, mat: int, params: wr_params, d_S, L: int) -> None:
+    _check(_lib.wr_sequence_device(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_S)), L))
+
+
+def wr_sigma_basis_device(ctx: int, d_S, L: int, m: int, n: int, prime: int, d_P, d_deg, Dcap: int) -> None:
+    _check(_lib.wr_sigma_basis_device(vp(ctx), vp(_dptr(d_S)), L, m, n, prime, vp(_dptr(d_P)),
+                                      vp(_dptr(d_deg)), Dcap))
+
+
+def wr_det_valuation_device(ctx: int, d_G, n: int, T: int, prime: int) -> int:
+    v = i64()
+    _check(_lib.wr_det_valuation_device(vp(ctx), vp(_dptr(d_G)), n, T, prime, ctypes.byref(v)))
+    return v.value
+
+
+# ------------------------------------------------------------------ serving
+
+def wr_server_start(ctx: int, max_slots: int = 8, hbm_budget: int = 0, queue_cap: int = 0) -> int:
+    cfg = wr_server_cfg(max_slots, hbm_budget, queue_cap)
+    h = vp()
+    _check(_lib.wr_server_start(vp(ctx), ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def wr_submit(srv: int, mat: int, params: wr_params) -> int:
+    t = u64()
+    _check(_lib.wr_submit(vp(srv), vp(mat), ctypes.byref(params), ctypes.byref(t)))
+    return t.value
+
+
+def wr_wait(srv: int, ticket: int, timeout_ms: int) -> int:
+    h = vp()
+    _check(_lib.wr_wait(vp(srv), ticket, timeout_ms, ctypes.byref(h)))
+    return h.value
+
+
+def wr_server_stats(srv: int) -> dict:
+    s = wr_stats()
+    _check(_lib.wr_server_stats(vp(srv), ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in wr_stats._fields_}
+
+
+def wr_server_stop(srv: int) -> None:
+    _lib.wr_server_stop(vp(srv))

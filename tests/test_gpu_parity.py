@@ -1,0 +1,351 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work, so the bar is bit-exactness: sequences, sigma-bases, generator
+degrees, valuations and ranks must equal the oracle's.  Sizes span several
+SELL chunks, split (heavy) rows, ragged tails and padded block widths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0704_2351_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRIMES = [65521, 1073741789, 2147483629]
+
+
+@pytest.fixture(scope="module")
+def wr():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_0704_2351_gb300 import _build
+    _build.build()
+    from paper_0704_2351_gb300 import wr as w
+    return w
+
+
+@pytest.fixture(scope="module")
+def ctx(wr):
+    c = wr.wr_create(0)
+    yield c
+    wr.wr_destroy(c)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def from_dev(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def heavy_matrix(R, C, seed, heavy=3, heavy_len=700, per_row=5):
+    """Random sparse matrix plus a few rows and columns longer than one SELL
+    segment (256 entries), to exercise the split-row path in both passes."""
+    rng = np.random.default_rng(seed)
+    base = synth.random_sparse(R, C, per_row, seed=seed)
+    r = [np.repeat(np.arange(R), np.diff(base.rowptr))]
+    c = [base.colidx.astype(np.int64)]
+    v = [base.vals.astype(np.int64)]
+    for _ in range(heavy):
+        row = int(rng.integers(0, R))
+        cols = rng.choice(C, size=min(heavy_len, C), replace=False)
+        r.append(np.full(len(cols), row)); c.append(cols); v.append(rng.choice([-1, 1, 2, -3], size=len(cols)))
+        col = int(rng.integers(0, C))
+        rows = rng.choice(R, size=min(heavy_len, R), replace=False)
+        r.append(rows); c.append(np.full(len(rows), col)); v.append(rng.choice([-1, 1, 3], size=len(rows)))
+    return synth.csr_from_coo(R, C, np.concatenate(r), np.concatenate(c), np.concatenate(v))
+
+
+def load(wr, ctx, A):
+    return wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+
+
+# ------------------------------------------------------------------ black box (A4, A5)
+
+@pytest.mark.parametrize("p", PRIMES)
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("width", [1, 3, 8, 16, 32])
+def test_blackbox_parity(wr, ctx, p, side, width):
+    A = heavy_matrix(1100, 900, seed=width * 7 + side)
+    mat = load(wr, ctx, A)
+    seed = 99 + width
+    N = A.cols if side == 0 else A.rows
+    Mo = A.rows if side == 0 else A.cols
+    rng = np.random.default_rng(width)
+    v = rng.integers(0, p, size=(N, width)).astype(np.uint32)
+    prm = wr.make_params(p, 1, width, seed, side=side)
+    dout = torch.empty((N, width), dtype=torch.int32, device="cuda")
+    wr.wr_blackbox_apply_device(ctx, mat, prm, to_dev(v), dout, width)
+    d1 = oracle.derive_diag(seed, oracle.TAG_D1, N, p)
+    d2 = oracle.derive_diag(seed, oracle.TAG_D2, Mo, p)
+    ref = oracle.blackbox_apply(A, p, side, d1, d2, v)
+    assert np.array_equal(from_dev(dout), ref)
+    wr.wr_matrix_free(mat)
+
+
+def test_blackbox_tiny_and_ragged(wr, ctx):
+    p = 65521
+    for (R, C, k) in [(1, 1, 1), (3, 70, 2), (33, 31, 4), (65, 2, 1)]:
+        A = synth.random_sparse(R, C, k, seed=R * C)
+        mat = load(wr, ctx, A)
+        for side in [0, 1]:
+            N = A.cols if side == 0 else A.rows
+            Mo = A.rows if side == 0 else A.cols
+            v = np.random.default_rng(1).integers(0, p, size=(N, 2)).astype(np.uint32)
+            prm = wr.make_params(p, 1, 2, 5, side=side)
+            dout = torch.empty((N, 2), dtype=torch.int32, device="cuda")
+            wr.wr_blackbox_apply_device(ctx, mat, prm, to_dev(v), dout, 2)
+            ref = oracle.blackbox_apply(A, p, side, oracle.derive_diag(5, 3, N, p),
+                                        oracle.derive_diag(5, 4, Mo, p), v)
+            assert np.array_equal(from_dev(dout), ref)
+        wr.wr_matrix_free(mat)
+
+
+# ------------------------------------------------------------------ sequence (A2, A3, A6, A7)
+
+def gpu_sequence(wr, ctx, A, p, m, n, seed, L, side=-1, symmetric=False):
+    mat = load(wr, ctx, A)
+    prm = wr.make_params(p, m, n, seed, side=side,
+                         projection=wr.WR_PROJ_SYMMETRIC if symmetric else wr.WR_PROJ_GENERIC)
+    dS = torch.empty((L, m, n), dtype=torch.int32, device="cuda")
+    wr.wr_sequence_device(ctx, mat, prm, dS, L)
+    S = from_dev(dS)
+    wr.wr_matrix_free(mat)
+    return S
+
+
+def test_sequence_config0_scalar_full(wr, ctx):
+    A = synth.config0()
+    p = synth.PRIME_C0
+    st = oracle.Setup(A, p, 1, 1, seed=synth.SEED_BASE)
+    L = oracle.seq_length(st.N, 1, 1)
+    S_ref = oracle.sequence(A, st, L)
+    S = gpu_sequence(wr, ctx, A, p, 1, 1, synth.SEED_BASE, L)
+    assert np.array_equal(S, S_ref)
+
+
+@pytest.mark.parametrize("m,n", [(2, 2), (3, 5), (8, 8), (4, 16), (32, 32), (1, 7)])
+@pytest.mark.parametrize("p", [65521, 2147483629])
+def test_sequence_block_parity(wr, ctx, m, n, p):
+    A = heavy_matrix(700, 620, seed=m * 100 + n, heavy=2, heavy_len=400)
+    st = oracle.Setup(A, p, m, n, seed=3)
+    L = min(oracle.seq_length(st.N, m, n), 300)
+    S_ref = oracle.sequence(A, st, L)
+    S = gpu_sequence(wr, ctx, A, p, m, n, 3, L)
+    assert np.array_equal(S, S_ref)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_sequence_sides_and_symmetric(wr, ctx, side):
+    p = 1073741789
+    A = heavy_matrix(500, 560, seed=17 + side, heavy=2, heavy_len=300)
+    for sym in [False, True]:
+        st = oracle.Setup(A, p, 4, 4, seed=21, side=side, symmetric=sym)
+        S_ref = oracle.sequence(A, st, 150)
+        S = gpu_sequence(wr, ctx, A, p, 4, 4, 21, 150, side=side, symmetric=sym)
+        assert np.array_equal(S, S_ref)
+        if sym:
+            assert all(np.array_equal(S[i], S[i].T) for i in range(len(S)))
+
+
+# ------------------------------------------------------------------ sigma-basis (A8)
+
+def gpu_sigma(wr, ctx, S, p):
+    L, m, n = S.shape
+    q = m + n
+    Dcap = L + 1
+    dP = torch.empty(((Dcap + 1), n, q), dtype=torch.int32, device="cuda")
+    ddeg = torch.empty(q, dtype=torch.int32, device="cuda")
+    wr.wr_sigma_basis_device(ctx, to_dev(S), L, m, n, p, dP, ddeg, Dcap)
+    return from_dev(dP), ddeg.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,L", [(1, 1, 50), (2, 3, 77), (3, 2, 130), (8, 8, 200), (5, 5, 65),
+                                   (16, 16, 70), (32, 32, 40)])
+@pytest.mark.parametrize("p", [65521, 2147483629])
+def test_sigma_basis_random_sequence(wr, ctx, m, n, L, p):
+    rng = np.random.default_rng(m * 1000 + n * 10 + L)
+    S = rng.integers(0, p, size=(L, m, n)).astype(np.uint32)
+    M, deg = oracle.mbasis(S, p)
+    P, dg = gpu_sigma(wr, ctx, S, p)
+    assert np.array_equal(dg, deg)
+    D = M.shape[0] - 1
+    assert np.array_equal(P[: D + 1], M[:, :n, :])
+    assert not P[D + 1:].any()
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (4, 4), (2, 6)])
+def test_sigma_basis_wiedemann_sequence(wr, ctx, m, n):
+    """Structured (rank-deficient) sequences: degenerate discrepancies."""
+    p = 65521
+    A = synth.planted_sparse(300, 260, 170, row_len=5, seed=m + n)
+    st = oracle.Setup(A, p, m, n, seed=4)
+    S = oracle.sequence(A, st)
+    M, deg = oracle.mbasis(S, p)
+    P, dg = gpu_sigma(wr, ctx, S, p)
+    assert np.array_equal(dg, deg)
+    assert np.array_equal(P[: M.shape[0]], M[:, :n, :])
+
+
+def test_sigma_basis_degenerate_sequences(wr, ctx):
+    p = 1073741789
+    for S in [np.zeros((20, 2, 2), np.uint32),
+              np.concatenate([np.ones((1, 3, 3), np.uint32), np.zeros((30, 3, 3), np.uint32)]),
+              np.tile(np.eye(2, dtype=np.uint32)[None], (25, 1, 1))]:
+        M, deg = oracle.mbasis(S, p)
+        P, dg = gpu_sigma(wr, ctx, S, p)
+        n = S.shape[2]
+        assert np.array_equal(dg, deg)
+        assert np.array_equal(P[: M.shape[0]], M[:, :n, :])
+
+
+# ------------------------------------------------------------------ det valuation (A9)
+
+def test_det_valuation_parity(wr, ctx):
+    p = 65521
+    rng = np.random.default_rng(5)
+    for t in range(20):
+        n = int(rng.integers(1, 9))
+        e = rng.integers(0, 3, size=n)
+        U = rng.integers(0, p, size=(2, n, n))
+        V = rng.integers(0, p, size=(2, n, n))
+        U[0] = np.triu(U[0], 1) + np.eye(n, dtype=np.int64)
+        V[0] = np.tril(V[0], -1) + np.eye(n, dtype=np.int64)
+        Dg = np.zeros((int(e.max()) + 1, n, n), dtype=np.int64)
+        for i in range(n):
+            Dg[int(e[i]), i, i] = 1
+        G = oracle.polymat_mul(oracle.polymat_mul(U, Dg, p), V, p).astype(np.uint32)
+        T = G.shape[0]
+        v = wr.wr_det_valuation_device(ctx, to_dev(G), n, T, p)
+        assert v == oracle.det_valuation(G, p) == int(e.sum())
+
+
+# ------------------------------------------------------------------ rank (A1-A9)
+
+def gpu_rank(wr, ctx, A, p, m, n, seed, want=0, side=-1, symmetric=False):
+    mat = load(wr, ctx, A)
+    prm = wr.make_params(p, m, n, seed, side=side, want=want,
+                         projection=wr.WR_PROJ_SYMMETRIC if symmetric else wr.WR_PROJ_GENERIC)
+    res = wr.wr_rank(ctx, mat, prm)
+    out = dict(rank=wr.wr_result_rank(res), **wr.wr_result_info(res))
+    if want & wr.WR_WANT_SEQUENCE:
+        out["S"] = wr.wr_result_sequence(res, m, n)
+    if want & wr.WR_WANT_GENERATOR:
+        out["F"], out["delta"] = wr.wr_result_generator(res, n)
+    wr.wr_result_free(res)
+    wr.wr_matrix_free(mat)
+    return out
+
+
+def test_rank_config0_scalar(wr, ctx):
+    A = synth.config0()
+    p = synth.PRIME_C0
+    ref = oracle.rank_wiedemann(A, p, 1, 1, seed=synth.SEED_BASE)
+    g = gpu_rank(wr, ctx, A, p, 1, 1, synth.SEED_BASE, want=3)
+    assert g["rank"] == ref["rank"] == 1500
+    assert (g["deg_det"], g["codeg"]) == (ref["deg_det"], ref["codeg"])
+    assert np.array_equal(g["S"], ref["S"])
+    assert np.array_equal(g["delta"], ref["delta"])
+    assert np.array_equal(g["F"], ref["F"])
+
+
+@pytest.mark.parametrize("m,n", [(2, 2), (4, 4), (8, 8), (3, 5)])
+@pytest.mark.parametrize("p", PRIMES)
+def test_rank_planted_block(wr, ctx, m, n, p):
+    for t in range(3):
+        rng = np.random.default_rng(t * 31 + m)
+        R, C = int(rng.integers(50, 400)), int(rng.integers(50, 400))
+        r = int(rng.integers(1, min(R, C)))
+        A = synth.planted_sparse(R, C, r, row_len=int(rng.integers(2, 9)), seed=t + 100 * m)
+        ref = oracle.rank_wiedemann(A, p, m, n, seed=t)
+        g = gpu_rank(wr, ctx, A, p, m, n, t, want=3)
+        assert g["rank"] == ref["rank"] == r
+        assert (g["deg_det"], g["codeg"], g["sum_delta"]) == (ref["deg_det"], ref["codeg"], ref["sum_delta"])
+        assert np.array_equal(g["F"], ref["F"])
+
+
+def test_rank_edge_cases(wr, ctx):
+    p = 65521
+    Z = synth.csr_from_coo(5, 4, np.zeros(0), np.zeros(0), np.zeros(0))
+    assert gpu_rank(wr, ctx, Z, p, 2, 2, 1)["rank"] == 0
+    one = synth.dense_to_csr(np.array([[0, 1], [0, 0]]))
+    assert gpu_rank(wr, ctx, one, p, 1, 1, 1)["rank"] == 1
+    eye = synth.dense_to_csr(np.eye(40, dtype=np.int64))
+    assert gpu_rank(wr, ctx, eye, p, 4, 4, 1)["rank"] == 40
+    big = synth.dense_to_csr(np.array([[127, -127, 5], [-128 + 1, 3, 0]]))
+    assert gpu_rank(wr, ctx, big, 2147483629, 1, 1, 3)["rank"] == oracle.rank_dense(big.to_dense(), 2147483629)
+    # heavy rows and columns in a planted matrix
+    H = heavy_matrix(900, 800, seed=3)
+    ref = oracle.rank_sparse(H, 1073741789)
+    assert gpu_rank(wr, ctx, H, 1073741789, 8, 8, 2)["rank"] == ref
+
+
+def test_rank_chain_complex_pair(wr, ctx):
+    d_n, d_n1 = synth.chain_pair(2500, seed=8, homology=3)
+    p = 1073741783
+    rn = gpu_rank(wr, ctx, d_n, p, 8, 8, 5)["rank"]
+    rn1 = gpu_rank(wr, ctx, d_n1, p, 8, 8, 6)["rank"]
+    assert rn == d_n.rank and rn1 == d_n1.rank
+    assert rn + rn1 <= 2500
+
+
+def test_errors_are_reported(wr, ctx):
+    A = synth.random_sparse(10, 10, 2, seed=1)
+    with pytest.raises(wr.WrError) as ei:
+        gpu_rank(wr, ctx, A, 65520, 1, 1, 1)
+    assert ei.value.status == wr.WR_ENOTPRIME
+    bad = synth.CSR(2, 2, np.array([0, 1, 2]), np.array([0, 5], np.int32), np.array([1, 1], np.int32))
+    with pytest.raises(wr.WrError) as ei:
+        load(wr, ctx, bad)
+    assert ei.value.status == wr.WR_EINVAL
+    big = synth.CSR(1, 1, np.array([0, 1]), np.array([0], np.int32), np.array([300], np.int32))
+    with pytest.raises(wr.WrError) as ei:
+        load(wr, ctx, big)
+    assert ei.value.status == wr.WR_EOVERFLOW
+
+
+# ------------------------------------------------------------------ full size: config 1
+
+def _annihilates(S, F, delta, p, i):
+    """sum_k S[i+k] F[k][:, j] = 0 mod p for each column j with i + delta_j < L."""
+    L, m, n = S.shape
+    for j in range(n):
+        dj = int(delta[j])
+        if i + dj >= L:
+            continue
+        Sk = S[i: i + dj + 1].astype(np.uint64)            # (dj+1, m, n)
+        f = F[: dj + 1, :, j].astype(np.uint64)              # (dj+1, n)
+        lo, hi = f & 0x7FFF, f >> 15
+        acc_lo = np.einsum("kar,kr->a", Sk, lo)
+        acc_hi = np.einsum("kar,kr->a", Sk, hi)
+        tot = [(int(a) + (int(b) % p) * (1 << 15)) % p for a, b in zip(acc_lo, acc_hi)]
+        if any(tot):
+            return False
+    return True
+
+
+def test_config1_full_size(wr, ctx):
+    """200,000 x 180,000, block 8 x 8, p = 1073741789: planted rank, the first
+    terms against the oracle, the generator annihilates the sequence at
+    sampled offsets, and one black-box application at full size."""
+    A = synth.config1()
+    p, m, n, seed = synth.PRIME_C1, 8, 8, synth.SEED_BASE + 1
+    g = gpu_rank(wr, ctx, A, p, m, n, seed, want=3)
+    assert g["rank"] == A.rank == 170000
+    assert g["seq_len"] == 45002
+    st = oracle.Setup(A, p, m, n, seed)
+    S_ref = oracle.sequence(A, st, L=6)
+    assert np.array_equal(g["S"][:6], S_ref)
+    rng = np.random.default_rng(0)
+    for i in [0, 1] + list(rng.integers(0, 22000, size=3)):
+        assert _annihilates(g["S"], g["F"], g["delta"], p, int(i))
+    mat = load(wr, ctx, A)
+    v = rng.integers(0, p, size=(A.cols, n)).astype(np.uint32)
+    dout = torch.empty((A.cols, n), dtype=torch.int32, device="cuda")
+    wr.wr_blackbox_apply_device(ctx, mat, wr.make_params(p, 1, n, seed), to_dev(v), dout, n)
+    ref = oracle.blackbox_apply(A, p, 0, st.D1, st.D2, v)
+    assert np.array_equal(from_dev(dout), ref)
+    wr.wr_matrix_free(mat)
