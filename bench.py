@@ -1,0 +1,288 @@
+"""Benchmark of the block Wiedemann rank path on GB300.
+
+A step is one pass of the whole path over one synthetic matrix: CSR ingest
+and SELL-C-sigma layout on the device, preconditioner set-up, the L - 1
+black-box applications with their projections, the sigma-basis and the rank
+readout.  The workload is the 200,000 x 180,000 power-law matrix of planted
+rank 170,000, block 8 x 8, p = 1073741789 (L = 45,002 terms).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wr|reference]
+
+One JSON line on rank 0.  value = SpMM nnz*vec processed per second over the
+whole step (2 passes x nnz x n per term); ms_per_step = time to rank.
+--impl reference times the CPU oracle on the host cores on a bounded sample
+of the same workload (first terms of the sequence).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mod-p SpMM nnz·vec/s, %HBM peak; batched/served vs plain time-to-rank (exact)"
+UNIT = "nnz*vec/s"
+
+
+def workload(rank: int):
+    from paper_0704_2351_gb300 import synth
+    seed = synth.SEED_BASE + 1 + 1000 * rank
+    A = synth.config1(seed=seed)
+    return A, dict(p=synth.PRIME_C1, m=8, n=8, seed=seed, name=(
+        "power-law sparse matrix 200000x180000, %d nnz (20/row base, alpha 2.1 column degrees), planted rank "
+        "170000; block Wiedemann m=n=8 mod p=1073741789, L=45002" % A.nnz))
+
+
+def nnzvec_per_step(A, n, L):
+    return 2.0 * A.nnz * n * (L - 1)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def start_clock_sampler(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        return subprocess.Popen(cmd, stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def stop_clock_sampler(proc, path, device):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or f[0] != str(device):
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def cpu_baseline(A, cfg, budget_s=12.0, terms_cap=400):
+    """The oracle as it stands, on the host's cores, over the first terms of
+    the same sequence (each term = one black-box application = 2 SpMM passes)."""
+    import oracle
+    st = oracle.Setup(A, cfg["p"], cfg["m"], cfg["n"], cfg["seed"])
+    t = time.perf_counter()
+    oracle.sequence(A, st, L=3)
+    per = max((time.perf_counter() - t) / 2, 1e-4)
+    terms = int(min(terms_cap, max(3, budget_s / per)))
+    t = time.perf_counter()
+    oracle.sequence(A, st, L=terms)
+    el = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0))
+    v = 2.0 * A.nnz * cfg["n"] * (terms - 1) / el
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d terms of the same sequence (%d black-box applications, 2 sparse passes "
+                      "each, %.1f s)" % (terms, terms - 1, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A, cfg = workload(0)
+    import oracle
+    oracle.load()
+    st = oracle.Setup(A, cfg["p"], cfg["m"], cfg["n"], cfg["seed"])
+    terms = 6
+    for _ in range(args.warmup):
+        oracle.sequence(A, st, L=2)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sequence(A, st, L=terms)
+    el = time.perf_counter() - t
+    work = 2.0 * A.nnz * cfg["n"] * (terms - 1) * args.steps
+    v = work / el
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": cfg["name"], "step": "first %d terms of the sequence "
+                                            "on the CPU oracle" % terms},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d terms per step, %d steps" % (terms, args.steps)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wr", choices=["wr", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_0704_2351_gb300 import wr
+
+    A, cfg = workload(rank)
+    p, m, n = cfg["p"], cfg["m"], cfg["n"]
+    L = -(-A.cols // m) + -(-A.cols // n) + 2
+    work = nnzvec_per_step(A, n, L)
+    stream = torch.cuda.Stream()
+    ctx = wr.wr_create(local, stream.cuda_stream)
+    params = wr.make_params(p, m, n, cfg["seed"])
+    d_rp = torch.from_numpy(A.rowptr.astype(np.int64)).to("cuda")
+    d_ci = torch.from_numpy(A.colidx.astype(np.int32)).to("cuda")
+    d_va = torch.from_numpy(A.vals.astype(np.int32)).to("cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    torch.cuda.synchronize()
+
+    def step():
+        mat = wr.wr_matrix_load_csr_device(ctx, A.rows, A.cols, A.nnz, d_rp, d_ci, d_va)
+        res = wr.wr_rank(ctx, mat, params)
+        r = wr.wr_result_rank(res)
+        wr.wr_result_free(res)
+        wr.wr_matrix_free(mat)
+        return r
+
+    for _ in range(args.warmup):
+        r = step()
+        assert r == A.rank, "rank %d != planted %d" % (r, A.rank)
+
+    wr.wr_set_profiling(ctx, True)
+    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % rank)
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    sampler = start_clock_sampler(clk_path)
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    spmm_ms = spmm_bytes = 0.0
+    spmm_launches = 0
+    phases = []
+    launches0 = wr.wr_last_timings(ctx)["kernel_launches"]
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step()
+        e1.record(stream)
+        e1.synchronize()
+        assert r == A.rank
+        total_ms += e0.elapsed_time(e1)
+        tm = wr.wr_last_timings(ctx)
+        spmm_ms += tm["spmm_ms"]
+        spmm_bytes += tm["spmm_bytes"]
+        spmm_launches += tm["spmm_launches"]
+        phases.append({k: round(tm[k], 3) for k in ["setup_ms", "sequence_ms", "sigma_ms", "readout_ms"]})
+    torch.cuda.synchronize()
+    launches = wr.wr_last_timings(ctx)["kernel_launches"] - launches0
+    clocks = stop_clock_sampler(sampler, clk_path, local)
+    wr.wr_set_profiling(ctx, False)
+    t_max = total_ms
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = work * args.steps * world / (t_max * 1e-3)
+
+    # end to end through the C ABI from pinned host buffers
+    h_rp = torch.from_numpy(A.rowptr.astype(np.int64)).pin_memory()
+    h_ci = torch.from_numpy(A.colidx.astype(np.int32)).pin_memory()
+    h_va = torch.from_numpy(A.vals.astype(np.int32)).pin_memory()
+    from paper_0704_2351_gb300.wr import _lib, vp, _check
+    import ctypes
+    e2e_ms = 0.0
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h = vp()
+        _check(_lib.wr_matrix_load_csr(vp(ctx), A.rows, A.cols, vp(h_rp.data_ptr()), vp(h_ci.data_ptr()),
+                                       vp(h_va.data_ptr()), ctypes.byref(h)))
+        res = wr.wr_rank(ctx, h.value, params)
+        r = wr.wr_result_rank(res)
+        wr.wr_result_free(res)
+        wr.wr_matrix_free(h.value)
+        e2e_ms += 1e3 * (time.perf_counter() - t)
+        assert r == A.rank
+    e2e_steps = max(1, min(args.steps, 2))
+    e2e_value = work * world / (e2e_ms / e2e_steps * 1e-3)
+    h2d = 8 * (A.rows + 1) + 8 * A.nnz
+    d2h = 4 * n + 2 * 8 + 8 + 3 * 8  # column degrees, valuations, layout sizes, rank
+
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    roof = None
+    if spmm_launches:
+        avg_s = spmm_ms / spmm_launches * 1e-3
+        per_launch = spmm_bytes / spmm_launches
+        ach = per_launch / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak if peak else 6800.0, "unit": "GB/s",
+                "frac": ach / (peak if peak else 6800.0), "traffic": None,
+                "peak_source": "measured" if peak else "fallback",
+                "kernel": "k_spmm (both passes of the black box)", "avg_launch_us": avg_s * 1e6,
+                "bytes_per_launch": per_launch, "sampled_launches": spmm_launches}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "block": [m, n], "prime": p, "seq_len": L,
+                       "per_rank": "independent matrix per rank (seeded by rank), no collective on the data path",
+                       "l2": "working set below L2; a 256 MB buffer is written between timed steps",
+                       "phases_ms": phases},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms / e2e_steps},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    wr.wr_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -88,6 +88,8 @@ typedef struct {
     double spmm_ms;      /* when profiling is on: summed duration of the sampled SpMM      */
     int64_t spmm_launches; /* launches those samples cover                                  */
     double spmm_bytes;   /* algorithmic bytes of those launches                            */
+    int64_t kernel_launches; /* kernels launched through this context since its creation  */
+                             /* (each replay of a captured graph counts its kernel nodes)    */
 } wr_timings;
 
 /* ---------------------------------------------------------------- context */

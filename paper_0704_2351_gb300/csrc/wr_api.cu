@@ -179,6 +179,7 @@ extern "C" wr_status wr_set_profiling(wr_ctx *ctx, int on) {
 extern "C" wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out) {
     if (!ctx || !out) return fail(WR_EINVAL, "null argument");
     *out = ctx->last;
+    out->kernel_launches = ctx->launches;
     return WR_OK;
 }
 

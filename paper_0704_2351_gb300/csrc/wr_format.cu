@@ -271,17 +271,17 @@ wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, i
     int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 1) {
         k_tile_scan<<<1, SCAN_THREADS, 0, ctx->stream>>>(d_in, n, nullptr, d_out);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
         return WR_OK;
     }
     DevBuf sums, offs;
     WR_TRY(dev_alloc(ctx, sums, sizeof(int64_t) * tiles));
     WR_TRY(dev_alloc(ctx, offs, sizeof(int64_t) * (tiles + 1)));
     k_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(d_in, n, sums.as<int64_t>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     WR_TRY(exclusive_scan_i64(ctx, sums.as<int64_t>(), offs.as<int64_t>(), tiles));
     k_tile_scan<<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(d_in, n, offs.as<int64_t>(), d_out);
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     // the last tile wrote out[n]; keep the stream ordered for the caller
     return WR_OK;
 }
@@ -294,7 +294,7 @@ wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, con
     int threads = 256;
     k_validate<<<grid_for(ctx, std::max(rows, nnz), threads), threads, 0, ctx->stream>>>(
         rows, cols, nnz, d_rowptr, d_colidx, d_vals, err.as<int>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     int h = 0;
     WR_TRY(read_err(ctx, err.as<int>(), &h));
     if (h & ERR_ROWPTR) return fail(WR_EINVAL, "rowptr is not a valid CSR row pointer array");
@@ -319,14 +319,14 @@ wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, co
     if (nnz > 0) {
         k_count_cols<<<grid_for(ctx, nnz, threads), threads, 0, ctx->stream>>>(nnz, d_colidx,
                                                                                cnt.as<int64_t>());
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     WR_TRY(exclusive_scan_i64(ctx, cnt.as<int64_t>(), rowptr_t.as<int64_t>(), cols));
     if (nnz > 0) {
         k_scatter_transpose<<<grid_for(ctx, rows, threads), threads, 0, ctx->stream>>>(
             rows, d_rowptr, d_colidx, d_vals, rowptr_t.as<int64_t>(), fill.as<int64_t>(),
             colidx_t.as<int32_t>(), vals_t.as<int32_t>());
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     return WR_OK;
 }
@@ -348,7 +348,7 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
     if (rows > 0) {
         k_count_segments<<<grid_for(ctx, rows, threads), threads, 0, st>>>(
             rows, d_rowptr, nseg.as<int64_t>(), is_split.as<int64_t>(), err.as<int>());
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     WR_TRY(exclusive_scan_i64(ctx, nseg.as<int64_t>(), vstart.as<int64_t>(), rows));
     WR_TRY(exclusive_scan_i64(ctx, is_split.as<int64_t>(), split_id.as<int64_t>(), rows));
@@ -389,16 +389,16 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
         rows, d_rowptr, vstart.as<int64_t>(), split_id.as<int64_t>(), is_split.as<int64_t>(),
         vr_row.as<int32_t>(), vr_len.as<int32_t>(), vr_start.as<int64_t>(), out.split_row.as<int32_t>(),
         hist.as<int>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     k_bucket_starts<<<1, 32, 0, st>>>(hist.as<int>(), bstart.as<int64_t>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     k_bucket_scatter<<<grid_for(ctx, nv, threads), threads, 0, st>>>(
         nv, vr_len.as<int32_t>(), bstart.as<int64_t>(), bfill.as<unsigned long long>(), sorted.as<int32_t>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     k_chunk_slots<<<grid_for(ctx, out.nchunks, threads), threads, 0, st>>>(
         out.nchunks, nv, sorted.as<int32_t>(), vr_len.as<int32_t>(), out.chunk_len.as<int32_t>(),
         slots.as<int64_t>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     WR_TRY(exclusive_scan_i64(ctx, slots.as<int64_t>(), out.chunk_off.as<int64_t>(), out.nchunks));
     int64_t nslots = 0;
     WR_CUDA(cudaMemcpyAsync(&nslots, out.chunk_off.as<int64_t>() + out.nchunks, sizeof(int64_t),
@@ -411,7 +411,7 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
         vr_start.as<int64_t>(), is_split.as<int64_t>(), split_id.as<int64_t>(), d_colidx, d_vals,
         out.chunk_off.as<int64_t>(), out.chunk_len.as<int32_t>(), out.entries.as<uint32_t>(),
         out.vrow.as<uint32_t>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     WR_CUDA(cudaStreamSynchronize(st));  // temporaries are freed on return
     return WR_OK;
 }

@@ -23,6 +23,14 @@ wr_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::wr::cuda_fail(e_, #call);  \
     } while (0)
 
+// after a kernel launch: count it on the context and check the launch
+#define WR_LAUNCHED(ctx)                                                   \
+    do {                                                                   \
+        (ctx)->launches++;                                                 \
+        cudaError_t e_ = cudaGetLastError();                               \
+        if (e_ != cudaSuccess) return ::wr::cuda_fail(e_, "kernel launch"); \
+    } while (0)
+
 #define WR_TRY(call)                              \
     do {                                          \
         wr_status s_ = (call);                    \
@@ -197,6 +205,7 @@ struct wr_ctx {
     int num_sms = 0;
     size_t smem_optin = 0;
     bool profiling = false;
+    int64_t launches = 0;   // kernels launched through this context (graph replays: nodes per replay)
     wr_timings last{};
 };
 

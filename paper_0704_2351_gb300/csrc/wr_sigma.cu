@@ -192,6 +192,23 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
                 uint32_t v = (j == pc[t]) ? 0u : mulm(Tff[j * q + pc[t]], sinv[j], mp);
                 Tp[t * q + j] = v;
             }
+            __syncwarp();
+            // local degree bounds: column j now also holds multiples of the
+            // pivot columns added to it, which may have a larger local degree
+            int dnew[2];
+            for (int k = 0; k < 2; k++) {
+                const int j = lane + 32 * k;
+                dnew[k] = 0;
+                if (j < q) {
+                    int d = degl[j];
+                    for (int t = 0; t < np; t++)
+                        if (Tp[t * q + j]) d = max(d, degl[pc[t]]);
+                    dnew[k] = d;
+                }
+            }
+            __syncwarp();
+            for (int k = 0; k < 2; k++)
+                if (lane + 32 * k < q) degl[lane + 32 * k] = dnew[k];
         }
         __syncthreads();
         const int np = *npiv;
@@ -444,7 +461,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     WR_TRY(dev_alloc(ctx, degl, sizeof(int32_t) * q));
     WR_TRY(dev_alloc(ctx, dmax, sizeof(int)));
     k_init_basis<<<1, 256, 0, s>>>(d_P, n, q, d_deg, qtop.as<uint32_t>(), m, dmax.as<int>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
 
     // chunk size: the local kernel's shared memory must fit
     const size_t budget = std::min<size_t>(ctx->smem_optin, 227 * 1024) - 1024;
@@ -487,17 +504,17 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
             dim3 grid((unsigned)((std::min(Dbound, k0 + bb - 1) + TT) / TT), (unsigned)((q + CT - 1) / CT));
             kwin<<<grid, 256, window_bytes(TT, bb), s>>>(d_S, L, m, n, q, Pcur, k0, bb, TT, CT,
                                                           dmax.as<int>(), Eacc.as<unsigned long long>(), mp);
-            WR_CUDA(cudaGetLastError());
+            WR_LAUNCHED(ctx);
         }
         k_local<<<1, LOCAL_THREADS, local_bytes(bb), s>>>(m, n, q, bb, Eacc.as<unsigned long long>(),
                                                          qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
                                                          degl.as<int32_t>(), dmax.as<int>(), mp);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
         const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
         kapp<<<(unsigned)((Dnew + TA) / TA), 256, apply_bytes(TA, bb), s>>>(
             Pcur, Pnext, n, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, mp);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
         std::swap(Pcur, Pnext);
         Dbound = Dnew;
     }
@@ -519,7 +536,7 @@ wr_status det_valuation(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T, 
     WR_CUDA(cudaFuncSetAttribute(k_valuation, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
     k_valuation<<<1, VAL_THREADS, smem, ctx->stream>>>(d_G, g.as<uint32_t>(), (int)n, (int)T,
                                                        out.as<int64_t>(), mp);
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     WR_CUDA(cudaMemcpyAsync(val, out.ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     WR_CUDA(cudaStreamSynchronize(ctx->stream));
     return WR_OK;
@@ -533,7 +550,7 @@ wr_status rank_readout(wr_ctx *ctx, const uint32_t *d_P, const int32_t *d_deg, i
     WR_TRY(dev_alloc(ctx, sel, sizeof(int32_t) * n));
     WR_TRY(dev_alloc(ctx, delta, sizeof(int32_t) * n));
     k_select<<<1, 64, 0, s>>>(d_deg, q, n, sel.as<int32_t>(), delta.as<int32_t>());
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     out.delta.assign(n, 0);
     WR_CUDA(cudaMemcpyAsync(out.delta.data(), delta.ptr, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     WR_CUDA(cudaStreamSynchronize(s));
@@ -555,7 +572,7 @@ wr_status rank_readout(wr_ctx *ctx, const uint32_t *d_P, const int32_t *d_deg, i
             WR_TRY(dev_alloc(ctx, G, sizeof(uint32_t) * T * n * n));
             k_extract<<<blocks_for(T * n * n, 256), 256, 0, s>>>(d_P, n, q, sel.as<int32_t>(), delta.as<int32_t>(),
                                                                  T, which, Dcap, G.as<uint32_t>());
-            WR_CUDA(cudaGetLastError());
+            WR_LAUNCHED(ctx);
             int64_t v = -1;
             WR_TRY(det_valuation(ctx, G.as<uint32_t>(), n, T, p, &v));
             if (v >= 0) { vals[which] = v; break; }
@@ -574,7 +591,7 @@ wr_status rank_readout(wr_ctx *ctx, const uint32_t *d_P, const int32_t *d_deg, i
         WR_TRY(dev_alloc(ctx, G, sizeof(uint32_t) * T * n * n));
         k_extract<<<blocks_for(T * n * n, 256), 256, 0, s>>>(d_P, n, q, sel.as<int32_t>(), delta.as<int32_t>(),
                                                              T, 1, Dcap, G.as<uint32_t>());
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
         gen->resize((size_t)T * n * n);
         WR_CUDA(cudaMemcpyAsync(gen->data(), G.ptr, sizeof(uint32_t) * gen->size(), cudaMemcpyDeviceToHost, s));
         WR_CUDA(cudaStreamSynchronize(s));

@@ -270,17 +270,17 @@ wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
         int64_t threads = A.nchunks * 32;
         k_spmm<NV><<<blocks_for(threads, 256), 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp,
                                                                       term_counter);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     } else if (term_counter) {
         // keep the term counter moving even for an empty matrix
         k_spmm<NV><<<1, 32, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     if (A.nsplit > 0) {
         int64_t cnt = A.nsplit * NV;
         k_finalize_split<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
                                                                        y, scale, mp);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     return WR_OK;
 }
@@ -310,7 +310,7 @@ wr_status launch_project(wr_ctx *ctx, int64_t N, int m, int n, int nv, const uin
     else
         k_project<4><<<(unsigned)grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, nv, xh, t, s_raw,
                                                                         term_counter, mp);
-    WR_CUDA(cudaGetLastError());
+    WR_LAUNCHED(ctx);
     return WR_OK;
 }
 
@@ -346,16 +346,19 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
     WR_CUDA(cudaMemsetAsync(st.acc1.ptr, 0, st.acc1.bytes, s));
     WR_CUDA(cudaMemsetAsync(st.acc2.ptr, 0, st.acc2.bytes, s));
     WR_CUDA(cudaMemsetAsync(st.counter.ptr, 0, sizeof(int), s));
-    if (r.N > 0)
+    if (r.N > 0) {
         k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, st.D1.as<uint32_t>());
-    if (r.M > 0)
+        WR_LAUNCHED(ctx);
+    }
+    if (r.M > 0) {
         k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, st.D2.as<uint32_t>());
-    WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
+    }
     if (want_projection && r.N > 0) {
         k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, nv, r.seed, r.symmetric ? 1 : 0,
                                                       st.D1.as<uint32_t>(), st.T.as<uint32_t>(),
                                                       st.xh.as<uint32_t>(), st.d1sq.as<uint32_t>(), st.mp);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     return WR_OK;
 }
@@ -418,11 +421,15 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
     int64_t prof_launches = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    int64_t graph_launches = 0;  // kernel nodes in one replay
     if (iters >= G) {
+        const int64_t before = ctx->launches;
         WR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         wr_status cst = WR_OK;
         for (int64_t i = 0; i < G && cst == WR_OK; i++) cst = seq_iteration(ctx, st, nullptr);
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        graph_launches = ctx->launches - before;
+        ctx->launches = before;
         if (cst != WR_OK) { if (graph) cudaGraphDestroy(graph); return cst; }
         WR_CUDA(ce);
         WR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -434,6 +441,7 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
         if (todo == G && exec && !(ctx->profiling && group % PROF_EVERY == 0)) {
             cudaError_t ce = cudaGraphLaunch(exec, s);
             if (ce != cudaSuccess) loop_st = cuda_fail(ce, "cudaGraphLaunch");
+            ctx->launches += graph_launches;
         } else {
             const bool prof = ctx->profiling;
             for (int64_t i = 0; i < todo && loop_st == WR_OK; i++)
@@ -462,7 +470,7 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
     if (L * E > 0) {
         k_reduce_seq<<<blocks_for(L * E, 256), 256, 0, s>>>(L * E, st.s_raw.as<unsigned long long>(), d_S,
                                                            st.mp);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     WR_CUDA(cudaEventRecord(e2, s));
     WR_CUDA(cudaEventSynchronize(e2));
@@ -493,7 +501,7 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
     if (r.N > 0) {
         k_scale_pad<<<blocks_for(r.N * r.nv, 256), 256, 0, s>>>(r.N, (int)width, r.nv, d_in,
                                                                st.D1.as<uint32_t>(), st.T.as<uint32_t>(), st.mp);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     SellView f = view(*st.first), sc = view(*st.second);
     WR_TRY(launch_spmm(ctx, r.nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
@@ -503,7 +511,7 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
                        st.acc2.as<unsigned long long>(), st.mp, nullptr));
     if (r.N > 0) {
         k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out);
-        WR_CUDA(cudaGetLastError());
+        WR_LAUNCHED(ctx);
     }
     WR_CUDA(cudaStreamSynchronize(s));
     return WR_OK;

@@ -41,7 +41,8 @@ class wr_timings(ctypes.Structure):
     _fields_ = [("setup_ms", ctypes.c_double), ("sequence_ms", ctypes.c_double),
                 ("sigma_ms", ctypes.c_double), ("readout_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("spmm_ms", ctypes.c_double),
-                ("spmm_launches", ctypes.c_int64), ("spmm_bytes", ctypes.c_double)]
+                ("spmm_launches", ctypes.c_int64), ("spmm_bytes", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 class wr_server_cfg(ctypes.Structure):

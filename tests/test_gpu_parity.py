@@ -218,8 +218,14 @@ def test_det_valuation_parity(wr, ctx):
         for i in range(n):
             Dg[int(e[i]), i, i] = 1
         G = oracle.polymat_mul(oracle.polymat_mul(U, Dg, p), V, p).astype(np.uint32)
-        T = G.shape[0]
-        v = wr.wr_det_valuation_device(ctx, to_dev(G), n, T, p)
+        # same precision on both sides (coefficients past the degree are 0);
+        # the short one may legitimately not determine the valuation (-1)
+        for T in [G.shape[0], 2 * G.shape[0] + 2 * n]:
+            Gp = np.zeros((T, n, n), dtype=np.uint32)
+            Gp[: G.shape[0]] = G
+            v = wr.wr_det_valuation_device(ctx, to_dev(Gp), n, T, p)
+            ref = oracle.load().or_det_valuation(oracle._p(Gp), n, T, p)
+            assert v == ref
         assert v == oracle.det_valuation(G, p) == int(e.sum())
 
 
