@@ -158,6 +158,27 @@ void wr_result_free(wr_result *res);
  * from params (side, seed, prime).  d_in and d_out may alias. */
 wr_status wr_blackbox_apply_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                                    const uint32_t *d_in, uint32_t *d_out, int64_t width);
+/* The same application as wr_blackbox_apply_device, without allocating any
+ * device memory.  The paper has no counterpart: it exists for callers that
+ * must not allocate device memory while they run -- code that works inside
+ * another program's fixed device-memory arena (where cudaMalloc would fail or
+ * fragment it), or latency-critical loops that cannot pay for cudaMalloc or
+ * cudaFree (both may synchronise the device).  The matrix is loaded
+ * beforehand with the usual calls; d_in and d_out are the caller's (N x width
+ * residues each, as in wr_blackbox_apply_device).
+ * Its temporaries live in one fixed 32 MiB array per device, held by every
+ * device that loads the library until the process exits.  It needs
+ * 4 nv (N + M) + 4 (N + M) + 8 nv (split rows of A and A^T) bytes (nv = width
+ * rounded up to a power of two, M the other dimension); larger requests return
+ * WR_EINVAL with the sizes in wr_last_error().  The first call on a device
+ * looks up the array's device address (with that device current): make that
+ * first call before any stream capture.  All calls share the array and find
+ * what the previous call left in it; calls whose work overlaps on the GPU
+ * (other threads, contexts or streams of the same device) race on it and must
+ * be serialised by the caller.  The call returns after its work completed. */
+wr_status wr_blackbox_apply_device_noalloc(wr_ctx *ctx, const wr_matrix *mat,
+                                           const wr_params *params, const uint32_t *d_in,
+                                           uint32_t *d_out, int64_t width);
 /* The sequence S_i = X^T A~^i Y, i < L (Section 2.4 step 2) into d_S (L*m*n). */
 wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                              uint32_t *d_S, uint64_t L);

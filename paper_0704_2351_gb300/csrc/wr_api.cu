@@ -399,6 +399,14 @@ extern "C" wr_status wr_blackbox_apply_device(wr_ctx *ctx, const wr_matrix *mat,
     return blackbox_apply(ctx, mat, *params, d_in, d_out, width);
 }
 
+// The paper has no counterpart: see the declaration in wr.h.
+extern "C" wr_status wr_blackbox_apply_device_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                                      const uint32_t *d_in, uint32_t *d_out, int64_t width) {
+    if (!ctx || !mat || !params || !d_in || !d_out) return fail(WR_EINVAL, "null argument");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    return blackbox_apply_noalloc(ctx, mat, *params, d_in, d_out, width);
+}
+
 extern "C" wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                                         uint32_t *d_S, uint64_t L) {
     if (!ctx || !mat || !params || !d_S) return fail(WR_EINVAL, "null argument");

@@ -245,6 +245,8 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
                        uint32_t *d_S, double *setup_ms, double *seq_ms);
 wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                          const uint32_t *d_in, uint32_t *d_out, int64_t width);
+wr_status blackbox_apply_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
+                                 const uint32_t *d_in, uint32_t *d_out, int64_t width);
 
 // sigma-basis and readout (wr_sigma.cu)
 wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n, uint32_t p,

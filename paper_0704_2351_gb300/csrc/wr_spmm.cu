@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "wr_internal.cuh"
@@ -511,6 +513,110 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
                        st.acc2.as<unsigned long long>(), st.mp, nullptr));
     if (r.N > 0) {
         k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out);
+        WR_LAUNCHED(ctx);
+    }
+    WR_CUDA(cudaStreamSynchronize(s));
+    return WR_OK;
+}
+
+}  // namespace wr
+
+// ---------------------------------------------------------------------------
+// Black-box application without device allocation.
+//
+// For callers that must not allocate device memory once they are running:
+// code that lives inside another program's fixed device-memory arena (where
+// cudaMalloc would fail or fragment the arena), or latency-critical loops that
+// cannot afford an allocation (cudaMalloc and cudaFree may synchronise the
+// device).  All temporaries of one application (the padded input block, the
+// intermediate block, both diagonals and the split-row accumulators) are
+// carved out of one fixed array that exists once per device for the life of
+// the process.
+
+// 32 MiB of scratch per device, reserved when the library's device code is
+// loaded on that device.
+static __device__ __align__(256) unsigned char wr_noalloc_scratch[32u << 20];
+
+namespace wr {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = sizeof(wr_noalloc_scratch);
+
+// Device address of the scratch array, looked up once per device (the first
+// call on a device does it, with that device current).
+static void *g_noalloc_addr[128];
+static std::mutex g_noalloc_mu;
+
+static wr_status noalloc_scratch_address(int device, void **out) {
+    if (device < 0 || device >= 128) return fail(WR_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, wr_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return WR_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+wr_status blackbox_apply_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
+                                 const uint32_t *d_in, uint32_t *d_out, int64_t width) {
+    if (width < 1 || width > 32) return fail(WR_EINVAL, "width must be in 1..32");
+    wr_params p2 = prm;
+    p2.n = (uint32_t)width;
+    p2.m = 1;
+    Resolved r;
+    WR_TRY(resolve(mat, &p2, r));
+    const Sell *first = r.side == 0 ? &mat->a : &mat->at;
+    const Sell *second = r.side == 0 ? &mat->at : &mat->a;
+    const int nv = r.nv;
+    // layout of the scratch array
+    const size_t oT = 0;
+    const size_t oW = oT + align256(sizeof(uint32_t) * (size_t)r.N * nv);
+    const size_t oD1 = oW + align256(sizeof(uint32_t) * (size_t)r.M * nv);
+    const size_t oD2 = oD1 + align256(sizeof(uint32_t) * (size_t)r.N);
+    const size_t oA1 = oD2 + align256(sizeof(uint32_t) * (size_t)r.M);
+    const size_t nA1 = sizeof(unsigned long long) * (size_t)first->nsplit * nv;
+    const size_t oA2 = oA1 + align256(nA1);
+    const size_t nA2 = sizeof(unsigned long long) * (size_t)second->nsplit * nv;
+    const size_t need = oA2 + align256(nA2);
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(WR_EINVAL, "this matrix and width need " + std::to_string(need) +
+                                   " bytes of scratch; the allocation-free call has " +
+                                   std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes (use wr_blackbox_apply_device)");
+    void *base = nullptr;
+    WR_TRY(noalloc_scratch_address(ctx->device, &base));
+    unsigned char *b = static_cast<unsigned char *>(base);
+    uint32_t *T = reinterpret_cast<uint32_t *>(b + oT);
+    uint32_t *Wb = reinterpret_cast<uint32_t *>(b + oW);
+    uint32_t *D1 = reinterpret_cast<uint32_t *>(b + oD1);
+    uint32_t *D2 = reinterpret_cast<uint32_t *>(b + oD2);
+    unsigned long long *acc1 = reinterpret_cast<unsigned long long *>(b + oA1);
+    unsigned long long *acc2 = reinterpret_cast<unsigned long long *>(b + oA2);
+    const ModP mp = make_modp(r.p);
+    cudaStream_t s = ctx->stream;
+    // the split-row accumulators must start at zero; the scratch keeps
+    // whatever the previous call left there
+    if (nA1) WR_CUDA(cudaMemsetAsync(acc1, 0, nA1, s));
+    if (nA2) WR_CUDA(cudaMemsetAsync(acc2, 0, nA2, s));
+    if (r.N > 0) {
+        k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, D1);
+        WR_LAUNCHED(ctx);
+    }
+    if (r.M > 0) {
+        k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, D2);
+        WR_LAUNCHED(ctx);
+    }
+    if (r.N > 0) {
+        k_scale_pad<<<blocks_for(r.N * nv, 256), 256, 0, s>>>(r.N, (int)width, nv, d_in, D1, T, mp);
+        WR_LAUNCHED(ctx);
+    }
+    WR_TRY(launch_spmm(ctx, nv, view(*first), T, Wb, D2, acc1, mp, nullptr));
+    WR_TRY(launch_spmm(ctx, nv, view(*second), Wb, T, D1, acc2, mp, nullptr));
+    if (r.N > 0) {
+        k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, nv, T, d_out);
         WR_LAUNCHED(ctx);
     }
     WR_CUDA(cudaStreamSynchronize(s));

@@ -79,6 +79,7 @@ _sig = {
     "wr_result_generator": ([vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
     "wr_result_free": ([vp], None),
     "wr_blackbox_apply_device": ([vp, vp, P(wr_params), vp, vp, i64], ctypes.c_int),
+    "wr_blackbox_apply_device_noalloc": ([vp, vp, P(wr_params), vp, vp, i64], ctypes.c_int),
     "wr_sequence_device": ([vp, vp, P(wr_params), vp, u64], ctypes.c_int),
     "wr_sigma_basis_device": ([vp, vp, u64, u32, u32, u32, vp, vp, i64], ctypes.c_int),
     "wr_det_valuation_device": ([vp, vp, i64, i64, u32, P(i64)], ctypes.c_int),
@@ -223,6 +224,13 @@ def wr_result_free(res: int) -> None:
 def wr_blackbox_apply_device(ctx: int, mat: int, params: wr_params, d_in, d_out, width: int) -> None:
     _check(_lib.wr_blackbox_apply_device(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_in)),
                                          vp(_dptr(d_out)), width))
+
+
+def wr_blackbox_apply_device_noalloc(ctx: int, mat: int, params: wr_params, d_in, d_out, width: int) -> None:
+    """Same as wr_blackbox_apply_device, with no device allocation (fixed
+    per-device scratch; see include/wr.h)."""
+    _check(_lib.wr_blackbox_apply_device_noalloc(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_in)),
+                                                 vp(_dptr(d_out)), width))
 
 
 def wr_sequence_device(ctx: int, mat: int, params: wr_params, d_S, L: int) -> None:
