@@ -58,6 +58,11 @@ ModP make_modp(uint32_t p) {
     unsigned __int128 room = ((unsigned __int128)1 << 64) - 1 - p;
     uint64_t lazy = pm1 ? (uint64_t)(room / ((unsigned __int128)pm1 * pm1)) : 1024;
     m.lazy = (uint32_t)std::min<uint64_t>(lazy, 1024);
+    uint32_t inv = p;  // Newton iteration for p^{-1} mod 2^32 (p odd)
+    for (int i = 0; i < 5; i++) inv *= 2u - p * inv;
+    m.pneg = 0u - inv;
+    m.r1 = (uint32_t)((uint64_t(1) << 32) % p);
+    m.r2 = (uint32_t)((uint64_t)m.r1 * m.r1 % p);
     return m;
 }
 

@@ -134,116 +134,136 @@ __global__ void k_scatter_transpose(int64_t rows, const int64_t *__restrict__ ro
     }
 }
 
-// --- SELL build
+// --- layout build
+//
+// Light rows (at most LIGHT_MAX entries, empty rows included) go to the SELL
+// part: sorted by length (descending), 32 per chunk, slot-major.  Longer rows
+// go to the vector part: their entries are copied contiguously and cut into
+// segments of at most VSEG entries; a row with more than one segment is a
+// split row (exact int64 partial sums, finished by a second kernel).
 
-__global__ void k_count_segments(int64_t rows, const int64_t *__restrict__ rowptr,
-                                 int64_t *__restrict__ nseg, int64_t *__restrict__ is_split,
-                                 int *__restrict__ err) {
+__global__ void k_classify(int64_t rows, const int64_t *__restrict__ rowptr, int64_t *__restrict__ nseg,
+                           int64_t *__restrict__ vlen, int64_t *__restrict__ is_split, int *__restrict__ hist,
+                           int *__restrict__ err) {
+    __shared__ int sh[LIGHT_MAX + 1];
+    for (int b = threadIdx.x; b <= LIGHT_MAX; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = tid; i < rows; i += stride) {
-        int64_t len = rowptr[i + 1] - rowptr[i];
+        const int64_t len = rowptr[i + 1] - rowptr[i];
         if (len >= (int64_t(1) << 24)) atomicOr(err, ERR_ROWLEN);
-        int64_t s = len > 0 ? (len + SEG - 1) / SEG : 1;
-        nseg[i] = s;
-        is_split[i] = s > 1 ? 1 : 0;
-    }
-}
-
-__global__ void k_make_vrows(int64_t rows, const int64_t *__restrict__ rowptr,
-                             const int64_t *__restrict__ vstart, const int64_t *__restrict__ split_id,
-                             const int64_t *__restrict__ is_split, int32_t *__restrict__ vr_row,
-                             int32_t *__restrict__ vr_len, int64_t *__restrict__ vr_start,
-                             int32_t *__restrict__ split_row, int *__restrict__ hist) {
-    __shared__ int sh[SEG + 1];
-    for (int b = threadIdx.x; b <= SEG; b += blockDim.x) sh[b] = 0;
-    __syncthreads();
-    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < rows; i += stride) {
-        int64_t a = rowptr[i], len = rowptr[i + 1] - a;
-        int64_t v0 = vstart[i], ns = vstart[i + 1] - v0;
-        for (int64_t s = 0; s < ns; s++) {
-            int64_t l = len - s * SEG;
-            l = l < 0 ? 0 : (l > SEG ? SEG : l);
-            vr_row[v0 + s] = (int32_t)i;
-            vr_len[v0 + s] = (int32_t)l;
-            vr_start[v0 + s] = a + s * SEG;
-            atomicAdd(&sh[l], 1);
+        if (len <= LIGHT_MAX) {
+            nseg[i] = 0;
+            vlen[i] = 0;
+            is_split[i] = 0;
+            atomicAdd(&sh[len], 1);
+        } else {
+            const int64_t ns = (len + VSEG - 1) / VSEG;
+            nseg[i] = ns;
+            vlen[i] = len;
+            is_split[i] = ns > 1 ? 1 : 0;
         }
-        if (is_split[i]) split_row[split_id[i]] = (int32_t)i;
     }
     __syncthreads();
-    for (int b = threadIdx.x; b <= SEG; b += blockDim.x)
+    for (int b = threadIdx.x; b <= LIGHT_MAX; b += blockDim.x)
         if (sh[b]) atomicAdd(&hist[b], sh[b]);
 }
 
-// bucket b (length b) starts after all longer buckets
+// bucket b (rows of length b) starts after all longer buckets
 __global__ void k_bucket_starts(const int *__restrict__ hist, int64_t *__restrict__ start) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int64_t run = 0;
-        for (int b = SEG; b >= 0; b--) {
+        for (int b = LIGHT_MAX; b >= 0; b--) {
             start[b] = run;
             run += hist[b];
         }
+        start[LIGHT_MAX + 1] = run;  // number of light rows
     }
 }
 
-__global__ void k_bucket_scatter(int64_t nv, const int32_t *__restrict__ vr_len,
+__global__ void k_bucket_scatter(int64_t rows, const int64_t *__restrict__ rowptr,
                                  const int64_t *__restrict__ start, unsigned long long *__restrict__ fill,
                                  int32_t *__restrict__ sorted) {
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = tid; v < nv; v += stride) {
-        int l = vr_len[v];
-        int64_t pos = start[l] + (int64_t)atomicAdd(&fill[l], 1ull);
-        sorted[pos] = (int32_t)v;
+    for (int64_t i = tid; i < rows; i += stride) {
+        const int64_t len = rowptr[i + 1] - rowptr[i];
+        if (len > LIGHT_MAX) continue;
+        const int64_t pos = start[len] + (int64_t)atomicAdd(&fill[len], 1ull);
+        sorted[pos] = (int32_t)i;
     }
 }
 
-__global__ void k_chunk_slots(int64_t nchunks, int64_t nv, const int32_t *__restrict__ sorted,
-                              const int32_t *__restrict__ vr_len, int32_t *__restrict__ chunk_len,
+__global__ void k_chunk_slots(int64_t nchunks, const int32_t *__restrict__ sorted,
+                              const int64_t *__restrict__ rowptr, int32_t *__restrict__ chunk_len,
                               int64_t *__restrict__ slots) {
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = tid; c < nchunks; c += stride) {
-        // sorted by length descending: the chunk's first virtual row is its longest
-        int l = vr_len[sorted[c * SELL_C]];
+        // sorted by length descending: the chunk's first row is its longest
+        const int32_t r = sorted[c * SELL_C];
+        const int l = (int)(rowptr[r + 1] - rowptr[r]);
         chunk_len[c] = l;
         slots[c] = (int64_t)l * SELL_C;
     }
-    (void)nv;
 }
 
-__global__ void k_fill_sell(int64_t nchunks, int64_t nv, const int32_t *__restrict__ sorted,
-                            const int32_t *__restrict__ vr_row, const int32_t *__restrict__ vr_len,
-                            const int64_t *__restrict__ vr_start, const int64_t *__restrict__ is_split,
-                            const int64_t *__restrict__ split_id, const int32_t *__restrict__ colidx,
-                            const int32_t *__restrict__ vals, const int64_t *__restrict__ chunk_off,
-                            const int32_t *__restrict__ chunk_len, uint32_t *__restrict__ entries,
-                            uint32_t *__restrict__ vrow) {
+__global__ void k_fill_light(int64_t nchunks, int64_t nlight, const int32_t *__restrict__ sorted,
+                             const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                             const int32_t *__restrict__ vals, const int64_t *__restrict__ chunk_off,
+                             const int32_t *__restrict__ chunk_len, uint32_t *__restrict__ entries,
+                             uint32_t *__restrict__ vrow) {
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t pos = tid; pos < nchunks * SELL_C; pos += stride) {
-        int64_t c = pos / SELL_C;
-        int lane = (int)(pos % SELL_C);
-        int clen = chunk_len[c];
+        const int64_t c = pos / SELL_C;
+        const int lane = (int)(pos % SELL_C);
+        const int clen = chunk_len[c];
         uint32_t *dst = entries + chunk_off[c] + lane;
-        if (pos < nv) {
-            int32_t v = sorted[pos];
-            int32_t r = vr_row[v];
-            int l = vr_len[v];
-            int64_t s = vr_start[v];
+        if (pos < nlight) {
+            const int32_t r = sorted[pos];
+            const int64_t s = rowptr[r];
+            const int l = (int)(rowptr[r + 1] - s);
             for (int j = 0; j < clen; j++) {
                 uint32_t w = 0;
                 if (j < l) w = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
                 dst[(int64_t)j * SELL_C] = w;
             }
-            vrow[pos] = is_split[r] ? (VROW_SPLIT | (uint32_t)split_id[r]) : (uint32_t)r;
+            vrow[pos] = (uint32_t)r;
         } else {
             for (int j = 0; j < clen; j++) dst[(int64_t)j * SELL_C] = 0;
             vrow[pos] = VROW_EMPTY;
         }
+    }
+}
+
+// one warp per long row: copy its entries contiguously and write its segments
+__global__ void k_fill_vector(int64_t rows, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                              const int32_t *__restrict__ vals, const int64_t *__restrict__ vlen,
+                              const int64_t *__restrict__ voff, const int64_t *__restrict__ segbase,
+                              const int64_t *__restrict__ is_split, const int64_t *__restrict__ split_id,
+                              uint32_t *__restrict__ ventries, int64_t *__restrict__ seg_start,
+                              int32_t *__restrict__ seg_len, uint32_t *__restrict__ seg_row,
+                              int32_t *__restrict__ split_row) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < rows; i += nwarps) {
+        const int64_t len = vlen[i];
+        if (len == 0) continue;
+        const int64_t s = rowptr[i], o = voff[i];
+        for (int64_t j = lane; j < len; j += 32)
+            ventries[o + j] = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
+        const int64_t ns = (len + VSEG - 1) / VSEG;
+        const uint32_t tgt = is_split[i] ? (VROW_SPLIT | (uint32_t)split_id[i]) : (uint32_t)i;
+        for (int64_t k = lane; k < ns; k += 32) {
+            const int64_t g = segbase[i] + k;
+            seg_start[g] = o + k * VSEG;
+            seg_len[g] = (int32_t)min64(VSEG, len - k * VSEG);
+            seg_row[g] = tgt;
+        }
+        if (lane == 0 && is_split[i]) split_row[split_id[i]] = (int32_t)i;
     }
 }
 
@@ -333,71 +353,85 @@ wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, co
 
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
                      const int32_t *d_colidx, const int32_t *d_vals, Sell &out) {
+    (void)nnz;
     out.nrows = rows;
     out.ncols = cols;
     const int threads = 256;
     cudaStream_t st = ctx->stream;
-    DevBuf nseg, is_split, vstart, split_id, err;
-    int64_t R1 = rows + 1;
+    const int64_t R1 = rows + 1;
+    DevBuf nseg, vlen, is_split, segbase, voff, split_id, hist, bstart, bfill, err;
     WR_TRY(dev_alloc(ctx, nseg, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, vlen, sizeof(int64_t) * R1));
     WR_TRY(dev_alloc(ctx, is_split, sizeof(int64_t) * R1));
-    WR_TRY(dev_alloc(ctx, vstart, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, segbase, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, voff, sizeof(int64_t) * R1));
     WR_TRY(dev_alloc(ctx, split_id, sizeof(int64_t) * R1));
+    WR_TRY(dev_alloc(ctx, hist, sizeof(int) * (LIGHT_MAX + 1)));
+    WR_TRY(dev_alloc(ctx, bstart, sizeof(int64_t) * (LIGHT_MAX + 2)));
+    WR_TRY(dev_alloc(ctx, bfill, sizeof(unsigned long long) * (LIGHT_MAX + 1)));
     WR_TRY(dev_alloc(ctx, err, sizeof(int)));
     WR_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), st));
+    WR_CUDA(cudaMemsetAsync(hist.ptr, 0, hist.bytes, st));
+    WR_CUDA(cudaMemsetAsync(bfill.ptr, 0, bfill.bytes, st));
     if (rows > 0) {
-        k_count_segments<<<grid_for(ctx, rows, threads), threads, 0, st>>>(
-            rows, d_rowptr, nseg.as<int64_t>(), is_split.as<int64_t>(), err.as<int>());
+        k_classify<<<grid_for(ctx, rows, threads), threads, 0, st>>>(rows, d_rowptr, nseg.as<int64_t>(),
+                                                                    vlen.as<int64_t>(), is_split.as<int64_t>(),
+                                                                    hist.as<int>(), err.as<int>());
         WR_LAUNCHED(ctx);
     }
-    WR_TRY(exclusive_scan_i64(ctx, nseg.as<int64_t>(), vstart.as<int64_t>(), rows));
+    WR_TRY(exclusive_scan_i64(ctx, nseg.as<int64_t>(), segbase.as<int64_t>(), rows));
+    WR_TRY(exclusive_scan_i64(ctx, vlen.as<int64_t>(), voff.as<int64_t>(), rows));
     WR_TRY(exclusive_scan_i64(ctx, is_split.as<int64_t>(), split_id.as<int64_t>(), rows));
-    int64_t tot[2] = {0, 0};
+    k_bucket_starts<<<1, 32, 0, st>>>(hist.as<int>(), bstart.as<int64_t>());
+    WR_LAUNCHED(ctx);
+    int64_t tot[4] = {0, 0, 0, 0};
     int herr = 0;
-    WR_CUDA(cudaMemcpyAsync(&tot[0], vstart.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    WR_CUDA(cudaMemcpyAsync(&tot[1], split_id.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaMemcpyAsync(&tot[0], segbase.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaMemcpyAsync(&tot[1], voff.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaMemcpyAsync(&tot[2], split_id.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaMemcpyAsync(&tot[3], bstart.as<int64_t>() + LIGHT_MAX + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     WR_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
     WR_CUDA(cudaStreamSynchronize(st));
     if (herr & ERR_ROWLEN) return fail(WR_EOVERFLOW, "a row or column holds 2^24 or more entries");
-    const int64_t nv = tot[0];
-    out.nvrows = nv;
-    out.nsplit = tot[1];
-    out.nchunks = (nv + SELL_C - 1) / SELL_C;
+    out.nseg = tot[0];
+    out.nvent = tot[1];
+    out.nsplit = tot[2];
+    out.nlight = tot[3];
+    out.nchunks = (out.nlight + SELL_C - 1) / SELL_C;
 
-    DevBuf vr_row, vr_len, vr_start, hist, bstart, bfill, sorted, slots;
-    WR_TRY(dev_alloc(ctx, vr_row, sizeof(int32_t) * std::max<int64_t>(nv, 1)));
-    WR_TRY(dev_alloc(ctx, vr_len, sizeof(int32_t) * std::max<int64_t>(nv, 1)));
-    WR_TRY(dev_alloc(ctx, vr_start, sizeof(int64_t) * std::max<int64_t>(nv, 1)));
+    // vector part
+    WR_TRY(dev_alloc(ctx, out.ventries, sizeof(uint32_t) * std::max<int64_t>(out.nvent, 1)));
+    WR_TRY(dev_alloc(ctx, out.seg_start, sizeof(int64_t) * std::max<int64_t>(out.nseg, 1)));
+    WR_TRY(dev_alloc(ctx, out.seg_len, sizeof(int32_t) * std::max<int64_t>(out.nseg, 1)));
+    WR_TRY(dev_alloc(ctx, out.seg_row, sizeof(uint32_t) * std::max<int64_t>(out.nseg, 1)));
     WR_TRY(dev_alloc(ctx, out.split_row, sizeof(int32_t) * std::max<int64_t>(out.nsplit, 1)));
-    WR_TRY(dev_alloc(ctx, hist, sizeof(int) * (SEG + 1)));
-    WR_TRY(dev_alloc(ctx, bstart, sizeof(int64_t) * (SEG + 1)));
-    WR_TRY(dev_alloc(ctx, bfill, sizeof(unsigned long long) * (SEG + 1)));
+    if (out.nseg > 0) {
+        k_fill_vector<<<grid_for(ctx, rows * 32, threads), threads, 0, st>>>(
+            rows, d_rowptr, d_colidx, d_vals, vlen.as<int64_t>(), voff.as<int64_t>(), segbase.as<int64_t>(),
+            is_split.as<int64_t>(), split_id.as<int64_t>(), out.ventries.as<uint32_t>(), out.seg_start.as<int64_t>(),
+            out.seg_len.as<int32_t>(), out.seg_row.as<uint32_t>(), out.split_row.as<int32_t>());
+        WR_LAUNCHED(ctx);
+    }
+
+    // light part
+    DevBuf sorted, slots;
     WR_TRY(dev_alloc(ctx, sorted, sizeof(int32_t) * std::max<int64_t>(out.nchunks * SELL_C, 1)));
     WR_TRY(dev_alloc(ctx, slots, sizeof(int64_t) * (out.nchunks + 1)));
     WR_TRY(dev_alloc(ctx, out.chunk_off, sizeof(int64_t) * (out.nchunks + 1)));
     WR_TRY(dev_alloc(ctx, out.chunk_len, sizeof(int32_t) * std::max<int64_t>(out.nchunks, 1)));
     WR_TRY(dev_alloc(ctx, out.vrow, sizeof(uint32_t) * std::max<int64_t>(out.nchunks * SELL_C, 1)));
-    WR_CUDA(cudaMemsetAsync(hist.ptr, 0, sizeof(int) * (SEG + 1), st));
-    WR_CUDA(cudaMemsetAsync(bfill.ptr, 0, sizeof(unsigned long long) * (SEG + 1), st));
     if (out.nchunks == 0) {
         WR_CUDA(cudaMemsetAsync(out.chunk_off.ptr, 0, sizeof(int64_t), st));
         WR_TRY(dev_alloc(ctx, out.entries, sizeof(uint32_t)));
         out.nslots = 0;
+        WR_CUDA(cudaStreamSynchronize(st));
         return WR_OK;
     }
-    k_make_vrows<<<grid_for(ctx, rows, threads), threads, 0, st>>>(
-        rows, d_rowptr, vstart.as<int64_t>(), split_id.as<int64_t>(), is_split.as<int64_t>(),
-        vr_row.as<int32_t>(), vr_len.as<int32_t>(), vr_start.as<int64_t>(), out.split_row.as<int32_t>(),
-        hist.as<int>());
-    WR_LAUNCHED(ctx);
-    k_bucket_starts<<<1, 32, 0, st>>>(hist.as<int>(), bstart.as<int64_t>());
-    WR_LAUNCHED(ctx);
-    k_bucket_scatter<<<grid_for(ctx, nv, threads), threads, 0, st>>>(
-        nv, vr_len.as<int32_t>(), bstart.as<int64_t>(), bfill.as<unsigned long long>(), sorted.as<int32_t>());
+    k_bucket_scatter<<<grid_for(ctx, rows, threads), threads, 0, st>>>(
+        rows, d_rowptr, bstart.as<int64_t>(), bfill.as<unsigned long long>(), sorted.as<int32_t>());
     WR_LAUNCHED(ctx);
     k_chunk_slots<<<grid_for(ctx, out.nchunks, threads), threads, 0, st>>>(
-        out.nchunks, nv, sorted.as<int32_t>(), vr_len.as<int32_t>(), out.chunk_len.as<int32_t>(),
-        slots.as<int64_t>());
+        out.nchunks, sorted.as<int32_t>(), d_rowptr, out.chunk_len.as<int32_t>(), slots.as<int64_t>());
     WR_LAUNCHED(ctx);
     WR_TRY(exclusive_scan_i64(ctx, slots.as<int64_t>(), out.chunk_off.as<int64_t>(), out.nchunks));
     int64_t nslots = 0;
@@ -406,13 +440,11 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
     WR_CUDA(cudaStreamSynchronize(st));
     out.nslots = nslots;
     WR_TRY(dev_alloc(ctx, out.entries, sizeof(uint32_t) * std::max<int64_t>(nslots, 1)));
-    k_fill_sell<<<grid_for(ctx, out.nchunks * SELL_C, threads), threads, 0, st>>>(
-        out.nchunks, nv, sorted.as<int32_t>(), vr_row.as<int32_t>(), vr_len.as<int32_t>(),
-        vr_start.as<int64_t>(), is_split.as<int64_t>(), split_id.as<int64_t>(), d_colidx, d_vals,
-        out.chunk_off.as<int64_t>(), out.chunk_len.as<int32_t>(), out.entries.as<uint32_t>(),
-        out.vrow.as<uint32_t>());
+    k_fill_light<<<grid_for(ctx, out.nchunks * SELL_C, threads), threads, 0, st>>>(
+        out.nchunks, out.nlight, sorted.as<int32_t>(), d_rowptr, d_colidx, d_vals, out.chunk_off.as<int64_t>(),
+        out.chunk_len.as<int32_t>(), out.entries.as<uint32_t>(), out.vrow.as<uint32_t>());
     WR_LAUNCHED(ctx);
-    WR_CUDA(cudaStreamSynchronize(st));  // temporaries are freed on return
+    WR_CUDA(cudaStreamSynchronize(st));
     return WR_OK;
 }
 

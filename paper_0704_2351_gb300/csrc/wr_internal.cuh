@@ -49,6 +49,9 @@ struct ModP {
     uint32_t lazy;   // products (p-1)^2 that fit on top of a value < p in a uint64
     uint64_t mu;     // floor(2^64 / p)
     int64_t off;     // multiple of p in [2^62, 2^62 + p)
+    uint32_t pneg;   // -p^{-1} mod 2^32 (Montgomery, R = 2^32)
+    uint32_t r1;     // R mod p: the Montgomery form of 1
+    uint32_t r2;     // R^2 mod p
 };
 
 ModP make_modp(uint32_t p);
@@ -91,6 +94,29 @@ __host__ __device__ __forceinline__ uint32_t powm(uint32_t a, uint32_t e, const 
     while (e) {
         if (e & 1) r = mulm(r, a, m);
         a = mulm(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Montgomery product with R = 2^32: a b R^{-1} mod p for a, b < p < 2^31.
+// t + m p < 2^62 + 2^63, and the result is < 2p before the correction.
+__host__ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const ModP &m) {
+    const uint64_t t = (uint64_t)a * b;
+    const uint32_t k = (uint32_t)t * m.pneg;
+    const uint32_t u = (uint32_t)((t + (uint64_t)k * m.p) >> 32);
+    return u >= m.p ? u - m.p : u;
+}
+
+__host__ __device__ __forceinline__ uint32_t to_mont(uint32_t a, const ModP &m) { return mont_mul(a, m.r2, m); }
+__host__ __device__ __forceinline__ uint32_t from_mont(uint32_t a, const ModP &m) { return mont_mul(a, 1u, m); }
+
+// (a R)^{-1} R = a^{-1} R in Montgomery form, by Fermat's little theorem
+__host__ __device__ __forceinline__ uint32_t mont_inv(uint32_t am, const ModP &m) {
+    uint32_t r = m.r1, b = am, e = m.p - 2;
+    while (e) {
+        if (e & 1) r = mont_mul(r, b, m);
+        b = mont_mul(b, b, m);
         e >>= 1;
     }
     return r;
@@ -149,49 +175,66 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(ptr); }
 };
 
-// ------------------------------------------------------------------ SELL-C-sigma layout
+// ------------------------------------------------------------------ sparse layout
 //
-// Rows are cut into segments ("virtual rows") of at most SEG entries; virtual
-// rows are sorted by length (descending) and packed by chunks of 32.  Chunk c
-// holds its entries slot-major: entry j of the chunk's lane r is at
-// entries[off[c] + 32 j + r], a packed word (col << 8) | (uint8)val.  Padding
-// words are 0 (column 0, value 0).  vrow[32 c + r] is the output row, or
-// SPLIT | split_id for a segment of a row that was cut (its partial sums are
-// added exactly into an int64 accumulator and finished by a second kernel),
-// or EMPTY past the last virtual row.
+// Two parts per matrix (one for A, one for A^T):
+//  * SELL-C-sigma part for light rows (at most LIGHT_MAX entries, empty rows
+//    included): rows sorted by length (descending), packed by chunks of 32,
+//    slot-major: entry j of lane r of chunk c is at entries[off[c] + 32 j + r],
+//    a packed word (col << 8) | (uint8)val; padding words are 0.  vrow[32 c + r]
+//    is the output row, or EMPTY past the last light row.
+//  * vector part for longer rows: entries copied contiguously (ventries) and
+//    cut into segments of at most VSEG entries, one warp per segment.
+//    seg_row is the output row, or SPLIT | split_id for rows with more than one
+//    segment: those add exact int64 partial sums into an accumulator that a
+//    second kernel reduces, scales and stores.
 
 constexpr int SELL_C = 32;
-constexpr int SEG = 256;
+constexpr int LIGHT_MAX = 32;
+constexpr int VSEG = 256;
 constexpr uint32_t VROW_SPLIT = 0x80000000u;
 constexpr uint32_t VROW_EMPTY = 0xFFFFFFFFu;
 
 struct Sell {
     int64_t nrows = 0;     // output rows
     int64_t ncols = 0;     // gathered dimension
-    int64_t nvrows = 0;
+    // light part
+    int64_t nlight = 0;
     int64_t nchunks = 0;
     int64_t nslots = 0;    // entries incl. padding
-    int64_t nsplit = 0;    // rows that were cut into segments
     DevBuf entries;        // uint32 [nslots]
     DevBuf chunk_off;      // int64  [nchunks + 1]
     DevBuf chunk_len;      // int32  [nchunks]
     DevBuf vrow;           // uint32 [nchunks * 32]
+    // vector part
+    int64_t nseg = 0;
+    int64_t nvent = 0;
+    DevBuf ventries;       // uint32 [nvent]
+    DevBuf seg_start;      // int64  [nseg]
+    DevBuf seg_len;        // int32  [nseg]
+    DevBuf seg_row;        // uint32 [nseg]
+    int64_t nsplit = 0;    // rows with more than one segment
     DevBuf split_row;      // int32  [nsplit]
 };
 
 struct SellView {
-    int64_t nrows, ncols, nchunks, nsplit;
+    int64_t nrows, ncols, nchunks, nseg, nsplit;
     const uint32_t *entries;
     const int64_t *chunk_off;
     const int32_t *chunk_len;
     const uint32_t *vrow;
+    const uint32_t *ventries;
+    const int64_t *seg_start;
+    const int32_t *seg_len;
+    const uint32_t *seg_row;
     const int32_t *split_row;
 };
 
 inline SellView view(const Sell &s) {
-    return SellView{s.nrows, s.ncols, s.nchunks, s.nsplit, s.entries.as<uint32_t>(),
+    return SellView{s.nrows, s.ncols, s.nchunks, s.nseg, s.nsplit, s.entries.as<uint32_t>(),
                     s.chunk_off.as<int64_t>(), s.chunk_len.as<int32_t>(), s.vrow.as<uint32_t>(),
-                    s.split_row.as<int32_t>()};
+                    s.ventries.as<uint32_t>(), s.seg_start.as<int64_t>(), s.seg_len.as<int32_t>(),
+                    s.seg_row.as<uint32_t>(), s.split_row.as<int32_t>()};
 }
 
 }  // namespace wr

@@ -47,60 +47,87 @@ __global__ void k_init_basis(uint32_t *__restrict__ P, int n, int q, int32_t *__
     if (threadIdx.x == 0) *dmax = 1;
 }
 
-// E_acc[(i*m + a)*q + c] += sum_{t in tile} sum_r S[k0+i-t][a][r] P[t][r][c]
+// ---- window.  Block b takes coefficients t in [b tper, (b+1) tper) and
+// writes its partial E_i = sum_t S[k0+i-t] P[t] (mod p) for all i < bb into
+// Epart[b]; the local kernel adds the partials.  Work item = one (a, c) pair
+// and WIN_IB consecutive orders i, held in registers across the range.
+constexpr int WIN_THREADS = 256;
+constexpr int WIN_IB = 16;
+
 template <int KLAZY>
-__global__ void k_window(const uint32_t *__restrict__ S, int64_t L, int m, int n, int q,
-                         const uint32_t *__restrict__ P, int64_t k0, int bb, int TT, int CT,
-                         const int *__restrict__ dmax_dev, unsigned long long *__restrict__ E_acc,
-                         ModP mp) {
+__global__ void __launch_bounds__(WIN_THREADS)
+    k_window(const uint32_t *__restrict__ S, int64_t L, int m, int n, int q, const uint32_t *__restrict__ P,
+             int64_t k0, int bb, int TT, int64_t tper, const int *__restrict__ dmax_dev,
+             uint32_t *__restrict__ Epart, ModP mp) {
     extern __shared__ uint32_t sm[];
-    const int64_t t0 = (int64_t)blockIdx.x * TT;
-    const int c0 = blockIdx.y * CT;
-    const int ct = min(CT, q - c0);
-    const int dmax = *dmax_dev;
-    if (t0 > dmax || t0 > k0 + bb - 1) return;
-    const int tt_n = (int)min64(TT, min64(dmax + 1, k0 + bb) - t0);
-    uint32_t *Ps = sm;                          // [TT][n][CT]
-    uint32_t *Ss = sm + (size_t)TT * n * CT;    // [bb + TT - 1][m][n]
-    const int mn = m * n;
-    for (int i = threadIdx.x; i < tt_n * n * ct; i += blockDim.x) {
-        int tl = i / (n * ct), rem = i % (n * ct), r = rem / ct, cl = rem % ct;
-        Ps[(tl * n + r) * CT + cl] = P[((size_t)(t0 + tl) * n + r) * q + c0 + cl];
-    }
-    const int64_t smin = k0 - t0 - tt_n + 1;
-    const int scount = bb + tt_n - 1;
-    for (int i = threadIdx.x; i < scount * mn; i += blockDim.x) {
-        int64_t s = smin + i / mn;
-        Ss[i] = (s >= 0 && s < L) ? S[(size_t)s * mn + i % mn] : 0u;
-    }
-    __syncthreads();
-    const int nout = bb * m * ct;
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int i = o / (m * ct), a = (o / ct) % m, cl = o % ct;
-        unsigned long long acc = 0;
+    const int mn = m * n, nq = n * q, mq = m * q;
+    const int nib = (bb + WIN_IB - 1) / WIN_IB;
+    const int items = mq * nib;
+    uint32_t *out = Epart + (size_t)blockIdx.x * bb * mq;
+    const int64_t tmax = min64((int64_t)*dmax_dev, k0 + bb - 1);
+    const int64_t tb0 = (int64_t)blockIdx.x * tper;
+    const int64_t tb1 = min64(tb0 + tper, tmax + 1);
+    uint32_t *Ps = sm;                          // [TT][n][q]
+    uint32_t *Ss = sm + (size_t)TT * nq;        // [nib*WIN_IB + TT - 1][m][n]
+    for (int round = 0; round * WIN_THREADS < items; round++) {
+        const int it = round * WIN_THREADS + threadIdx.x;
+        const bool act = it < items;
+        const int pair = act ? it % mq : 0;
+        const int a = pair / q, c = pair % q;
+        const int i0 = act ? (it / mq) * WIN_IB : 0;
+        unsigned long long acc[WIN_IB];
+#pragma unroll
+        for (int k = 0; k < WIN_IB; k++) acc[k] = 0;
         int cnt = 0;
-        for (int tl = 0; tl < tt_n; tl++) {
-            const int64_t s = k0 + i - (t0 + tl);
-            if (s < 0) break;
-            const uint32_t *srow = Ss + (size_t)(s - smin) * mn + a * n;
-            const uint32_t *pcol = Ps + (size_t)tl * n * CT + cl;
-            for (int r = 0; r < n; r++) {
-                acc += (unsigned long long)srow[r] * pcol[r * CT];
-                if (++cnt == KLAZY) { acc = red64(acc, mp); cnt = 0; }
+        for (int64_t t0 = tb0; t0 < tb1; t0 += TT) {
+            const int tt_n = (int)min64(TT, tb1 - t0);
+            const int64_t smin = k0 - (t0 + tt_n - 1);
+            const int srows = nib * WIN_IB + tt_n - 1;
+            __syncthreads();
+            for (int x = threadIdx.x; x < tt_n * nq; x += WIN_THREADS) Ps[x] = P[(size_t)t0 * nq + x];
+            for (int x = threadIdx.x; x < srows * mn; x += WIN_THREADS) {
+                const int64_t sidx = smin + x / mn;
+                Ss[x] = (sidx >= 0 && sidx < L) ? S[(size_t)sidx * mn + x % mn] : 0u;
+            }
+            __syncthreads();
+            if (!act) continue;
+            for (int tl = 0; tl < tt_n; tl++) {
+                // order i, coefficient t0+tl -> S index k0 + i - t0 - tl = smin + (i + tt_n - 1 - tl)
+                const uint32_t *srow = Ss + (size_t)(i0 + tt_n - 1 - tl) * mn + a * n;
+                const uint32_t *pcol = Ps + (size_t)tl * nq + c;
+                for (int r = 0; r < n; r++) {
+                    const unsigned long long pv = pcol[r * q];
+#pragma unroll
+                    for (int k = 0; k < WIN_IB; k++) acc[k] += pv * srow[k * mn + r];
+                    if (++cnt == KLAZY) {
+#pragma unroll
+                        for (int k = 0; k < WIN_IB; k++) acc[k] = red64(acc[k], mp);
+                        cnt = 0;
+                    }
+                }
             }
         }
-        acc = red64(acc, mp);
-        if (acc) atomicAdd(&E_acc[((size_t)i * m + a) * q + c0 + cl], acc);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < WIN_IB; k++) {
+                const int i = i0 + k;
+                if (i < bb) out[(size_t)(i * m + a) * q + c] = red64(acc[k], mp);
+            }
+        }
     }
 }
 
-// Local M-Basis over the window: one block.
-// Shared layout: Es [bb][m][q], Ml [bb+1][q][q], D [m][q], Tff [q][q],
-// Tp [m][q], and small vectors.
-constexpr int LOCAL_THREADS = 512;
+// ---- local M-Basis over the window: one block, bb orders.
+// Shared layout: Es [bb][m][q] (normal form), Ml [bb+1][q][q], D [m][q] and
+// Tff [q][q] (Montgomery form), Tp [m][q] (normal form), small vectors.
+// The elimination is fraction-free in Montgomery form; the transform of the
+// order (normalised by the inverse column scales) is then applied row by row
+// to the rest of the window and to Ml with lazy uint64 accumulation.
+constexpr int LOCAL_THREADS = 1024;
 
+template <int KLAZY>
 __global__ void __launch_bounds__(LOCAL_THREADS)
-    k_local(int m, int n, int q, int bb, unsigned long long *__restrict__ E_acc,
+    k_local(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
             uint32_t *__restrict__ qtop, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
             int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, ModP mp) {
     extern __shared__ uint32_t sm[];
@@ -116,40 +143,47 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
     int *ord = degl + q;                                 // q
     int *pc = ord + q;                                   // m
     int *pr = pc + m;                                    // m
-    int *isp = pr + m;                                   // q (pivot flag)
+    int *isp = pr + m;                                   // q
     int *npiv = isp + q;                                 // 1
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    const int E = bb * m * q;
 
-    for (int i = tid; i < bb * m * q; i += nth) {
-        unsigned long long v = E_acc[i];
-        E_acc[i] = 0;
+    for (int x = tid; x < E; x += nth) {
+        unsigned long long v = 0;
+        for (int b = 0; b < nparts; b++) v += Epart[(size_t)b * E + x];
         uint32_t e = red64(v, mp);
-        if (i < m * q) e = subm(e, qtop[i], mp);
-        Es[i] = e;
+        if (x < m * q) e = subm(e, qtop[x], mp);
+        Es[x] = e;
     }
-    for (int i = tid; i < (bb + 1) * q * q; i += nth) {
-        int s = i / (q * q), rem = i % (q * q);
-        Ml[i] = (s == 0 && rem / q == rem % q) ? 1u : 0u;
+    for (int x = tid; x < (bb + 1) * q * q; x += nth) {
+        const int s = x / (q * q), rem = x % (q * q);
+        Ml[x] = (s == 0 && rem / q == rem % q) ? 1u : 0u;
     }
     for (int c = tid; c < q; c += nth) {
         deg[c] = deg_g[c];
         degl[c] = 0;
     }
     __syncthreads();
+    // rows of the transform step: q <= 32 -> 32/W2 rows per warp, W2 = pow2 >= q
+    int W2 = 1;
+    while (W2 < q && W2 < 32) W2 <<= 1;
+    const int rpw = 32 / W2;
+    const int grp = lane / W2, col = lane % W2;
+    const unsigned gmask = (W2 == 32) ? 0xffffffffu : (((1u << W2) - 1u) << (grp * W2));
 
     for (int i = 0; i < bb; i++) {
-        // ---- elimination on Delta = Es[i] (warp 0)
+        // ---- elimination on Delta = Es[i] (warp 0), fraction-free, Montgomery form
         if (warp == 0) {
-            for (int x = lane; x < m * q; x += 32) D[x] = Es[(size_t)i * m * q + x];
+            for (int x = lane; x < m * q; x += 32) D[x] = to_mont(Es[(size_t)i * m * q + x], mp);
             for (int c = lane; c < q; c += 32) {
                 int rk = 0;
                 for (int c2 = 0; c2 < q; c2++)
                     rk += (deg[c2] < deg[c] || (deg[c2] == deg[c] && c2 < c)) ? 1 : 0;
                 ord[rk] = c;
-                scl[c] = 1;
+                scl[c] = mp.r1;
                 isp[c] = 0;
-                for (int x = 0; x < q; x++) Tff[c * q + x] = (x == c) ? 1u : 0u;
+                for (int x = 0; x < q; x++) Tff[c * q + x] = (x == c) ? mp.r1 : 0u;
             }
             __syncwarp();
             int np = 0;
@@ -161,18 +195,15 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
                     if (dj == 0) continue;
                     const uint32_t dc = D[r * q + c];
                     __syncwarp();
-                    for (int a = lane; a < m; a += 32)
-                        D[a * q + j] = subm(mulm(dc, D[a * q + j], mp), mulm(dj, D[a * q + c], mp), mp);
+                    for (int aa = lane; aa < m; aa += 32)
+                        D[aa * q + j] = subm(mont_mul(dc, D[aa * q + j], mp), mont_mul(dj, D[aa * q + c], mp), mp);
                     for (int x = lane; x < q; x += 32)
-                        Tff[j * q + x] = subm(mulm(dc, Tff[j * q + x], mp), mulm(dj, Tff[c * q + x], mp), mp);
-                    if (lane == 0) scl[j] = mulm(scl[j], dc, mp);
+                        Tff[j * q + x] = subm(mont_mul(dc, Tff[j * q + x], mp), mont_mul(dj, Tff[c * q + x], mp), mp);
+                    if (lane == 0) scl[j] = mont_mul(scl[j], dc, mp);
                     __syncwarp();
                 }
-                bool nzr = false;
-                for (int a = lane; a < m; a += 32) nzr |= D[a * q + j] != 0;
                 // first nonzero row (m <= 32: one row per lane)
-                unsigned bal = __ballot_sync(0xffffffffu, lane < m && D[lane * q + j] != 0);
-                (void)nzr;
+                const unsigned bal = __ballot_sync(0xffffffffu, lane < m && D[lane * q + j] != 0);
                 if (bal) {
                     if (lane == 0) {
                         pc[np] = j;
@@ -184,21 +215,21 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
                 __syncwarp();
             }
             if (lane == 0) *npiv = np;
-            for (int c = lane; c < q; c += 32) sinv[c] = invm(scl[c], mp);
+            // normal-form inverse of each column scale: from_mont((s R)^{-1} R) = s^{-1}
+            for (int c = lane; c < q; c += 32) sinv[c] = from_mont(mont_inv(scl[c], mp), mp);
             __syncwarp();
-            // normalised transform restricted to pivot rows: Tp[t][j] = T[pc[t]][j]
+            // Tp[t][j] = T[pc[t]][j] = Tff[j][pc[t]] / s_j  (Tff is in Montgomery form:
+            // mont_mul(x R, y) = x y)
             for (int x = lane; x < np * q; x += 32) {
-                int t = x / q, j = x % q;
-                uint32_t v = (j == pc[t]) ? 0u : mulm(Tff[j * q + pc[t]], sinv[j], mp);
-                Tp[t * q + j] = v;
+                const int t = x / q, j = x % q;
+                Tp[t * q + j] = (j == pc[t]) ? 0u : mont_mul(Tff[j * q + pc[t]], sinv[j], mp);
             }
             __syncwarp();
-            // local degree bounds: column j now also holds multiples of the
-            // pivot columns added to it, which may have a larger local degree
-            int dnew[2];
+            // local degree bounds: column j now also holds multiples of the pivot
+            // columns added to it, which may have a larger local degree
+            int dnew[2] = {0, 0};
             for (int k = 0; k < 2; k++) {
                 const int j = lane + 32 * k;
-                dnew[k] = 0;
                 if (j < q) {
                     int d = degl[j];
                     for (int t = 0; t < np; t++)
@@ -212,31 +243,47 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
         }
         __syncthreads();
         const int np = *npiv;
-        // ---- apply the transform to the rest of the window and to Ml (row-wise)
-        //      new[j] = old[j] + sum_t Tp[t][j] old[pc[t]]
+        // ---- apply: new[j] = old[j] + sum_t Tp[t][j] old[pc[t]] on the rest
+        //      of the window (orders i..bb-1) and on Ml (coefficients <= max degl)
         {
-            const int erows = (bb - i) * m;        // rows (i', a), i' in [i, bb)
+            const int erows = (bb - i) * m;
             int dl = 0;
             for (int c = 0; c < q; c++) dl = max(dl, degl[c]);
-            const int mrows = (dl + 1) * q;        // rows (s, x) of Ml, s <= max degl
-            const int nrows = erows + mrows;
-            for (int row = warp; row < nrows; row += nth / 32) {
-                uint32_t *base = row < erows ? Es + ((size_t)i * m + row) * q
-                                             : Ml + (size_t)(row - erows) * q;
-                uint32_t v0 = lane < q ? base[lane] : 0u;
-                uint32_t v1 = lane + 32 < q ? base[lane + 32] : 0u;
-                uint32_t n0 = v0, n1 = v1;
-                for (int t = 0; t < np; t++) {
-                    const int c = pc[t];
-                    const uint32_t oc = c < 32 ? __shfl_sync(0xffffffffu, v0, c)
-                                               : __shfl_sync(0xffffffffu, v1, c - 32);
-                    if (oc == 0) continue;
-                    if (lane < q) n0 = addm(n0, mulm(Tp[t * q + lane], oc, mp), mp);
-                    if (lane + 32 < q) n1 = addm(n1, mulm(Tp[t * q + lane + 32], oc, mp), mp);
+            const int nrows = erows + (dl + 1) * q;
+            if (q <= 32) {
+                for (int row0 = warp * rpw; row0 < nrows; row0 += nwarps * rpw) {
+                    const int row = row0 + grp;
+                    const bool ok = row < nrows && col < q;
+                    uint32_t *base = row < erows ? Es + ((size_t)i * m + row) * q : Ml + (size_t)(row - erows) * q;
+                    const uint32_t v = ok ? base[col] : 0u;
+                    unsigned long long acc = v;
+                    int cnt = 0;
+                    for (int t = 0; t < np; t++) {
+                        const uint32_t oc = __shfl_sync(0xffffffffu, v, grp * W2 + pc[t]);
+                        if (ok) acc += (unsigned long long)Tp[t * q + col] * oc;
+                        if (++cnt == KLAZY) { acc = red64(acc, mp); cnt = 0; }
+                    }
+                    if (ok) base[col] = red64(acc, mp);
                 }
-                if (lane < q) base[lane] = n0;
-                if (lane + 32 < q) base[lane + 32] = n1;
+            } else {
+                for (int row = warp; row < nrows; row += nwarps) {
+                    uint32_t *base = row < erows ? Es + ((size_t)i * m + row) * q : Ml + (size_t)(row - erows) * q;
+                    const uint32_t v0 = base[lane];
+                    const uint32_t v1 = lane + 32 < q ? base[lane + 32] : 0u;
+                    unsigned long long a0 = v0, a1 = v1;
+                    int cnt = 0;
+                    for (int t = 0; t < np; t++) {
+                        const int c = pc[t];
+                        const uint32_t oc = c < 32 ? __shfl_sync(0xffffffffu, v0, c) : __shfl_sync(0xffffffffu, v1, c - 32);
+                        a0 += (unsigned long long)Tp[t * q + lane] * oc;
+                        if (lane + 32 < q) a1 += (unsigned long long)Tp[t * q + lane + 32] * oc;
+                        if (++cnt == KLAZY) { a0 = red64(a0, mp); a1 = red64(a1, mp); cnt = 0; }
+                    }
+                    base[lane] = red64(a0, mp);
+                    if (lane + 32 < q) base[lane + 32] = red64(a1, mp);
+                }
             }
+            (void)gmask;
         }
         __syncthreads();
         // ---- multiply pivot columns by x: shift in the window and in Ml
@@ -244,13 +291,12 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
             const int t = w / (m + q), k = w % (m + q);
             const int c = pc[t];
             if (k < m) {
-                const int a = k;
                 for (int ii = bb - 1; ii > i; ii--)
-                    Es[((size_t)ii * m + a) * q + c] = Es[((size_t)(ii - 1) * m + a) * q + c];
+                    Es[((size_t)ii * m + k) * q + c] = Es[((size_t)(ii - 1) * m + k) * q + c];
             } else {
                 const int x = k - m;
-                for (int s = degl[c] + 1; s > 0; s--)
-                    Ml[((size_t)s * q + x) * q + c] = Ml[((size_t)(s - 1) * q + x) * q + c];
+                for (int s2 = degl[c] + 1; s2 > 0; s2--)
+                    Ml[((size_t)s2 * q + x) * q + c] = Ml[((size_t)(s2 - 1) * q + x) * q + c];
                 Ml[(size_t)x * q + c] = 0;
             }
         }
@@ -263,12 +309,9 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
     }
     // ---- Qtop <- Qtop * Ml[bb]; write back
     for (int x = tid; x < m * q; x += nth) {
-        const int a = x / q, c = x % q;
+        const int aa = x / q, c = x % q;
         unsigned long long acc = 0;
-        for (int y = 0; y < q; y++) {
-            acc += (unsigned long long)qtop[a * q + y] * Ml[((size_t)bb * q + y) * q + c];
-            acc = red64(acc, mp);
-        }
+        for (int y = 0; y < q; y++) acc = red64(acc + (unsigned long long)qtop[aa * q + y] * Ml[((size_t)bb * q + y) * q + c], mp);
         D[x] = (uint32_t)acc;
     }
     __syncthreads();
@@ -285,11 +328,16 @@ __global__ void __launch_bounds__(LOCAL_THREADS)
     }
 }
 
-// P_new[t][r][c] = sum_{s <= min(t, degl[c])} sum_x P[t-s][r][x] Ml[s][x][c]
+// ---- apply: P_new[t][r][c] = sum_{s <= degl[c]} sum_x P[t-s][r][x] Ml[s][x][c]
+// Block: TA coefficients; work item = (r, c, APP_TB consecutive coefficients).
+constexpr int APP_THREADS = 256;
+constexpr int APP_TB = 8;
+
 template <int KLAZY>
-__global__ void k_apply(const uint32_t *__restrict__ P, uint32_t *__restrict__ Pn, int n, int q,
-                        const uint32_t *__restrict__ Ml_g, const int32_t *__restrict__ degl_g, int bb,
-                        int64_t Dbound, int TA, ModP mp) {
+__global__ void __launch_bounds__(APP_THREADS)
+    k_apply(const uint32_t *__restrict__ P, uint32_t *__restrict__ Pn, int n, int q,
+            const uint32_t *__restrict__ Ml_g, const int32_t *__restrict__ degl_g, int bb, int64_t Dbound,
+            int TA, ModP mp) {
     extern __shared__ uint32_t sm[];
     uint32_t *Mls = sm;                               // (bb+1)*q*q
     uint32_t *Pss = Mls + (size_t)(bb + 1) * q * q;   // (TA + bb) * n * q
@@ -297,30 +345,45 @@ __global__ void k_apply(const uint32_t *__restrict__ P, uint32_t *__restrict__ P
     const int64_t t0 = (int64_t)blockIdx.x * TA;
     if (t0 > Dbound) return;
     const int ta = (int)min64(TA, Dbound + 1 - t0);
-    for (int i = threadIdx.x; i < (bb + 1) * q * q; i += blockDim.x) Mls[i] = Ml_g[i];
-    for (int i = threadIdx.x; i < q; i += blockDim.x) degl[i] = degl_g[i];
-    const int64_t pbase = t0 - bb;  // Pss[u] holds P[pbase + u]
     const int nq = n * q;
-    for (int i = threadIdx.x; i < (ta + bb) * nq; i += blockDim.x) {
-        int64_t t = pbase + i / nq;
-        Pss[i] = t >= 0 ? P[(size_t)t * nq + i % nq] : 0u;
+    for (int x = threadIdx.x; x < (bb + 1) * q * q; x += APP_THREADS) Mls[x] = Ml_g[x];
+    for (int x = threadIdx.x; x < q; x += APP_THREADS) degl[x] = degl_g[x];
+    const int64_t pbase = t0 - bb;  // Pss[u] holds P[pbase + u]
+    for (int x = threadIdx.x; x < (ta + bb) * nq; x += APP_THREADS) {
+        const int64_t t = pbase + x / nq;
+        Pss[x] = t >= 0 ? P[(size_t)t * nq + x % nq] : 0u;
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < ta * nq; o += blockDim.x) {
-        const int tl = o / nq, r = (o / q) % n, c = o % q;
-        const int64_t t = t0 + tl;
-        unsigned long long acc = 0;
+    const int ntb = (ta + APP_TB - 1) / APP_TB;
+    for (int it = threadIdx.x; it < nq * ntb; it += APP_THREADS) {
+        const int rc = it % nq, tb = it / nq;
+        const int r = rc / q, c = rc % q;
+        const int tl0 = tb * APP_TB;
+        unsigned long long acc[APP_TB];
+#pragma unroll
+        for (int k = 0; k < APP_TB; k++) acc[k] = 0;
         int cnt = 0;
-        const int smax = (int)min64(degl[c], t);
-        for (int s = 0; s <= smax; s++) {
-            const uint32_t *prow = Pss + (size_t)(t - s - pbase) * nq + r * q;
-            const uint32_t *mcol = Mls + (size_t)s * q * q + c;
+        const int smax = degl[c];
+        for (int s2 = 0; s2 <= smax; s2++) {
+            // P[t0 + tl0 + k - s2] = Pss[tl0 + k + bb - s2]
+            const uint32_t *prow = Pss + (size_t)(tl0 + bb - s2) * nq + r * q;
+            const uint32_t *mcol = Mls + (size_t)s2 * q * q + c;
             for (int x = 0; x < q; x++) {
-                acc += (unsigned long long)prow[x] * mcol[x * q];
-                if (++cnt == KLAZY) { acc = red64(acc, mp); cnt = 0; }
+                const unsigned long long mv = mcol[x * q];
+#pragma unroll
+                for (int k = 0; k < APP_TB; k++) acc[k] += mv * prow[(size_t)k * nq + x];
+                if (++cnt == KLAZY) {
+#pragma unroll
+                    for (int k = 0; k < APP_TB; k++) acc[k] = red64(acc[k], mp);
+                    cnt = 0;
+                }
             }
         }
-        Pn[(size_t)t * nq + r * q + c] = red64(acc, mp);
+#pragma unroll
+        for (int k = 0; k < APP_TB; k++) {
+            const int tl = tl0 + k;
+            if (tl < ta) Pn[(size_t)(t0 + tl) * nq + rc] = red64(acc[k], mp);
+        }
     }
 }
 
@@ -454,7 +517,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     cudaStream_t s = ctx->stream;
     const size_t nq = (size_t)n * q;
     WR_CUDA(cudaMemsetAsync(d_P, 0, sizeof(uint32_t) * (Dcap + 1) * nq, s));
-    DevBuf P2, qtop, Ml, degl, dmax, Eacc;
+    DevBuf P2, qtop, Ml, degl, dmax, Epart;
     WR_TRY(dev_alloc(ctx, P2, sizeof(uint32_t) * (Dcap + 1) * nq));
     WR_CUDA(cudaMemsetAsync(P2.ptr, 0, P2.bytes, s));
     WR_TRY(dev_alloc(ctx, qtop, sizeof(uint32_t) * m * q));
@@ -463,56 +526,55 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     k_init_basis<<<1, 256, 0, s>>>(d_P, n, q, d_deg, qtop.as<uint32_t>(), m, dmax.as<int>());
     WR_LAUNCHED(ctx);
 
-    // chunk size: the local kernel's shared memory must fit
+    // chunk size b and tiles: every kernel's shared memory must fit
     const size_t budget = std::min<size_t>(ctx->smem_optin, 227 * 1024) - 1024;
     auto local_bytes = [&](int b) {
         return sizeof(uint32_t) * ((size_t)b * m * q + (size_t)(b + 1) * q * q + m * q + q * q + m * q + 2 * q) +
-               sizeof(int) * (3 * q + 2 * m + q + 1);
+               sizeof(int) * (4 * q + 2 * m + 1);
     };
-    int bmax = 64;
-    while (bmax > 1 && local_bytes(bmax) > budget) bmax /= 2;
-    // window tiles
-    const int CT = std::min(q, 16);
     auto window_bytes = [&](int TT, int b) {
-        return sizeof(uint32_t) * ((size_t)TT * n * CT + (size_t)(b + TT - 1) * m * n);
+        const int nib = (b + WIN_IB - 1) / WIN_IB;
+        return sizeof(uint32_t) * ((size_t)TT * nq + (size_t)(nib * WIN_IB + TT - 1) * m * n);
     };
-    int TT = 64;
-    while (TT > 1 && window_bytes(TT, bmax) > budget) TT /= 2;
-    int TA = 16;
-    auto apply_bytes = [&](int ta, int b) {
-        return sizeof(uint32_t) * ((size_t)(b + 1) * q * q + (size_t)(ta + b) * nq);
-    };
-    while (TA > 1 && apply_bytes(TA, bmax) > budget) TA /= 2;
-    if (apply_bytes(TA, bmax) > budget) return fail(WR_EINVAL, "block sizes too large for shared memory");
-
+    auto apply_bytes = [&](int ta, int b) { return sizeof(uint32_t) * ((size_t)(b + 1) * q * q + (size_t)(ta + b) * nq); };
+    int bmax = 64, TT = 32, TA = 64;
+    for (;;) {
+        while (TT > 4 && window_bytes(TT, bmax) > budget) TT /= 2;
+        while (TA > APP_TB && apply_bytes(TA, bmax) > budget) TA /= 2;
+        if (local_bytes(bmax) <= budget && window_bytes(TT, bmax) <= budget && apply_bytes(TA, bmax) <= budget) break;
+        if (bmax == 1) return fail(WR_EINVAL, "block sizes too large for shared memory");
+        bmax /= 2;
+        TT = 32;
+        TA = 64;
+    }
+    const int nparts_max = std::max(1, 2 * ctx->num_sms);
     WR_TRY(dev_alloc(ctx, Ml, sizeof(uint32_t) * (bmax + 1) * q * q));
-    WR_TRY(dev_alloc(ctx, Eacc, sizeof(unsigned long long) * (size_t)bmax * m * q));
-    WR_CUDA(cudaMemsetAsync(Eacc.ptr, 0, Eacc.bytes, s));
+    WR_TRY(dev_alloc(ctx, Epart, sizeof(uint32_t) * (size_t)nparts_max * bmax * m * q));
     const bool lazy16 = mp.lazy >= 16;
     auto *kwin = lazy16 ? k_window<16> : k_window<4>;
+    auto *kloc = lazy16 ? k_local<16> : k_local<4>;
     auto *kapp = lazy16 ? k_apply<16> : k_apply<4>;
     WR_CUDA(cudaFuncSetAttribute(kwin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
-    WR_CUDA(cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+    WR_CUDA(cudaFuncSetAttribute(kloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     WR_CUDA(cudaFuncSetAttribute(kapp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
 
     uint32_t *Pcur = d_P, *Pnext = P2.as<uint32_t>();
     int64_t Dbound = 1;
     for (int64_t k0 = 0; k0 < L; k0 += bmax) {
         const int bb = (int)std::min<int64_t>(bmax, L - k0);
-        // window
-        {
-            dim3 grid((unsigned)((std::min(Dbound, k0 + bb - 1) + TT) / TT), (unsigned)((q + CT - 1) / CT));
-            kwin<<<grid, 256, window_bytes(TT, bb), s>>>(d_S, L, m, n, q, Pcur, k0, bb, TT, CT,
-                                                          dmax.as<int>(), Eacc.as<unsigned long long>(), mp);
-            WR_LAUNCHED(ctx);
-        }
-        k_local<<<1, LOCAL_THREADS, local_bytes(bb), s>>>(m, n, q, bb, Eacc.as<unsigned long long>(),
-                                                         qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
-                                                         degl.as<int32_t>(), dmax.as<int>(), mp);
+        // window: split coefficients [0, min(Dbound, k0 + bb - 1)] over the blocks
+        const int64_t tspan = std::min<int64_t>(Dbound, k0 + bb - 1) + 1;
+        const int nparts = (int)std::min<int64_t>(nparts_max, std::max<int64_t>(1, (tspan + TT - 1) / TT));
+        const int64_t tper = (tspan + nparts - 1) / nparts;
+        kwin<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, n, q, Pcur, k0, bb, TT, tper,
+                                                                dmax.as<int>(), Epart.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
-        const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
+        kloc<<<1, LOCAL_THREADS, local_bytes(bb), s>>>(m, n, q, bb, nparts, Epart.as<uint32_t>(), qtop.as<uint32_t>(),
+                                                        d_deg, Ml.as<uint32_t>(), degl.as<int32_t>(), dmax.as<int>(), mp);
+        WR_LAUNCHED(ctx);
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
-        kapp<<<(unsigned)((Dnew + TA) / TA), 256, apply_bytes(TA, bb), s>>>(
+        const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
+        kapp<<<(unsigned)((Dnew + TA) / TA), APP_THREADS, apply_bytes(TA, bb), s>>>(
             Pcur, Pnext, n, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, mp);
         WR_LAUNCHED(ctx);
         std::swap(Pcur, Pnext);

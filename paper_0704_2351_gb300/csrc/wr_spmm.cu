@@ -23,110 +23,158 @@ namespace wr {
 
 namespace {
 
+// W residues (at most 16 bytes) per lane, G lanes per gathered row: one
+// warp-wide gather then touches 32/G rows, each one contiguous 4*NV-byte
+// run, so the L1 handles one tag lookup per row instead of one per lane.
 template <int NV>
 struct Lanes {
-    static constexpr int G = NV >= 4 ? NV / 4 : 1;  // lanes per row
-    static constexpr int W = NV / G;                 // residues per lane (1, 2 or 4)
-    static constexpr int RPW = 32 / G;               // rows per warp pass
+    static constexpr int W = NV < 4 ? NV : 4;  // residues per lane
+    static constexpr int G = NV / W;           // lanes per row (1, 2, 4, 8)
+    static constexpr int RPW = 32 / G;         // rows (light) or entries (vector) per warp step
 };
 
 template <int W>
-__device__ __forceinline__ void ldv(const uint32_t *p, uint32_t (&v)[W]);
-template <>
-__device__ __forceinline__ void ldv<1>(const uint32_t *p, uint32_t (&v)[1]) { v[0] = __ldg(p); }
-template <>
-__device__ __forceinline__ void ldv<2>(const uint32_t *p, uint32_t (&v)[2]) {
-    uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-    v[0] = t.x; v[1] = t.y;
-}
-template <>
-__device__ __forceinline__ void ldv<4>(const uint32_t *p, uint32_t (&v)[4]) {
-    uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+__device__ __forceinline__ void ldv(const uint32_t *p, uint32_t (&v)[W]) {
+    if constexpr (W == 1) {
+        v[0] = __ldg(p);
+    } else if constexpr (W == 2) {
+        uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < W / 4; k++) {
+            uint4 t = __ldg(reinterpret_cast<const uint4 *>(p) + k);
+            v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+        }
+    }
 }
 
 template <int W>
-__device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&v)[W]);
-template <>
-__device__ __forceinline__ void stv<1>(uint32_t *p, const uint32_t (&v)[1]) { p[0] = v[0]; }
-template <>
-__device__ __forceinline__ void stv<2>(uint32_t *p, const uint32_t (&v)[2]) {
-    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
-}
-template <>
-__device__ __forceinline__ void stv<4>(uint32_t *p, const uint32_t (&v)[4]) {
-    *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+__device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&v)[W]) {
+    if constexpr (W == 1) {
+        p[0] = v[0];
+    } else if constexpr (W == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < W / 4; k++)
+            reinterpret_cast<uint4 *>(p)[k] = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
 }
 
 __device__ __forceinline__ int entry_val(uint32_t e) { return (int)(int8_t)(e & 0xFFu); }
 
-// One warp per SELL chunk of 32 virtual rows; G lanes share a row and each
-// holds W of its NV residues, so every gathered row of x is one coalesced
-// NV*4-byte access.  y[row] = scale[row] * (sum_j a_j x[col_j]) mod p.
+template <int W>
+__device__ __forceinline__ void mac(int64_t (&acc)[W], uint32_t e, const uint32_t (&v)[W]) {
+    const int a = entry_val(e);
+#pragma unroll
+    for (int w = 0; w < W; w++) acc[w] += (int64_t)a * (int32_t)v[w];
+}
+
+// Epilogue of a finished row: y[row] = scale[row] * (sum mod p), or, for a
+// row cut into segments, the exact partial sums added into acc64.
+template <int W>
+__device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], uint32_t *y,
+                                        const uint32_t *scale, unsigned long long *acc64, int nv,
+                                        int col0, const ModP &mp) {
+    if (tgt & VROW_SPLIT) {
+        unsigned long long *dst = acc64 + (size_t)(tgt & ~VROW_SPLIT) * nv + col0;
+#pragma unroll
+        for (int w = 0; w < W; w++) atomicAdd(dst + w, (unsigned long long)acc[w]);
+    } else {
+        const uint32_t s = __ldg(scale + tgt);
+        uint32_t o[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) o[w] = mulm(s, red_s64(acc[w], mp), mp);
+        stv<W>(y + (size_t)tgt * nv + col0, o);
+    }
+}
+
+// One SpMM pass, y = scale * (A x) mod p, exact int64 row sums.
+// Blocks [0, vblocks): one warp per segment of a long row; its lanes stride
+// over the segment's contiguous entries, then a shuffle reduction.
+// Blocks [vblocks, ...): G warps per SELL chunk of 32 light rows; warp q of
+// the chunk takes rows [q*RPW, (q+1)*RPW), G lanes per row.
 template <int NV>
 __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__restrict__ x,
                                               uint32_t *__restrict__ y,
                                               const uint32_t *__restrict__ scale,
                                               unsigned long long *__restrict__ acc64, ModP mp,
-                                              int *__restrict__ term_counter) {
+                                              int *__restrict__ term_counter, int64_t vblocks) {
     using Ln = Lanes<NV>;
-    constexpr int W = Ln::W;
+    constexpr int W = Ln::W, G = Ln::G, RPW = Ln::RPW;
     if (term_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(term_counter, 1);
-    const int lane = threadIdx.x & 31;
-    const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / G, part = lane % G;
+    const uint32_t *xb = x + part * W;
+    if ((int64_t)blockIdx.x < vblocks) {
+        const int64_t seg = (int64_t)blockIdx.x * 8 + warp;
+        if (seg >= A.nseg) return;
+        const uint32_t *e = A.ventries + A.seg_start[seg];
+        const int len = A.seg_len[seg];
+        int64_t acc[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) acc[w] = 0;
+        int j = sub;
+        for (; j + 3 * RPW < len; j += 4 * RPW) {
+            const uint32_t e0 = __ldg(e + j), e1 = __ldg(e + j + RPW);
+            const uint32_t e2 = __ldg(e + j + 2 * RPW), e3 = __ldg(e + j + 3 * RPW);
+            uint32_t v0[W], v1[W], v2[W], v3[W];
+            ldv<W>(xb + (e0 >> 8) * NV, v0);
+            ldv<W>(xb + (e1 >> 8) * NV, v1);
+            ldv<W>(xb + (e2 >> 8) * NV, v2);
+            ldv<W>(xb + (e3 >> 8) * NV, v3);
+            mac<W>(acc, e0, v0);
+            mac<W>(acc, e1, v1);
+            mac<W>(acc, e2, v2);
+            mac<W>(acc, e3, v3);
+        }
+        for (; j < len; j += RPW) {
+            const uint32_t e0 = __ldg(e + j);
+            uint32_t v0[W];
+            ldv<W>(xb + (e0 >> 8) * NV, v0);
+            mac<W>(acc, e0, v0);
+        }
+#pragma unroll
+        for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+            for (int w = 0; w < W; w++) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], off);
+        if (sub == 0) row_out<W>(A.seg_row[seg], acc, y, scale, acc64, NV, part * W, mp);
+        return;
+    }
+    const int64_t lw = ((int64_t)blockIdx.x - vblocks) * 8 + warp;
+    const int64_t chunk = lw / G;
     if (chunk >= A.nchunks) return;
     const int64_t base = A.chunk_off[chunk];
     const int len = A.chunk_len[chunk];
-    const int sub = lane / Ln::G, part = lane % Ln::G;
-    const uint32_t *xb = x + part * W;
-#pragma unroll 1
-    for (int pass = 0; pass < Ln::G; pass++) {
-        const int r = pass * Ln::RPW + sub;
+    {
+        const int r = (int)(lw % G) * RPW + sub;
         const uint32_t *e = A.entries + base + r;
         int64_t acc[W];
 #pragma unroll
         for (int w = 0; w < W; w++) acc[w] = 0;
         int j = 0;
         for (; j + 4 <= len; j += 4) {
-            const uint32_t e0 = __ldg(e + (j + 0) * SELL_C);
-            const uint32_t e1 = __ldg(e + (j + 1) * SELL_C);
-            const uint32_t e2 = __ldg(e + (j + 2) * SELL_C);
-            const uint32_t e3 = __ldg(e + (j + 3) * SELL_C);
+            const uint32_t e0 = __ldg(e + (j + 0) * SELL_C), e1 = __ldg(e + (j + 1) * SELL_C);
+            const uint32_t e2 = __ldg(e + (j + 2) * SELL_C), e3 = __ldg(e + (j + 3) * SELL_C);
             uint32_t v0[W], v1[W], v2[W], v3[W];
             ldv<W>(xb + (e0 >> 8) * NV, v0);
             ldv<W>(xb + (e1 >> 8) * NV, v1);
             ldv<W>(xb + (e2 >> 8) * NV, v2);
             ldv<W>(xb + (e3 >> 8) * NV, v3);
-            const int a0 = entry_val(e0), a1 = entry_val(e1), a2 = entry_val(e2), a3 = entry_val(e3);
-#pragma unroll
-            for (int w = 0; w < W; w++) {
-                acc[w] += (int64_t)a0 * (int32_t)v0[w];
-                acc[w] += (int64_t)a1 * (int32_t)v1[w];
-                acc[w] += (int64_t)a2 * (int32_t)v2[w];
-                acc[w] += (int64_t)a3 * (int32_t)v3[w];
-            }
+            mac<W>(acc, e0, v0);
+            mac<W>(acc, e1, v1);
+            mac<W>(acc, e2, v2);
+            mac<W>(acc, e3, v3);
         }
         for (; j < len; j++) {
             const uint32_t e0 = __ldg(e + j * SELL_C);
             uint32_t v0[W];
             ldv<W>(xb + (e0 >> 8) * NV, v0);
-            const int a0 = entry_val(e0);
-#pragma unroll
-            for (int w = 0; w < W; w++) acc[w] += (int64_t)a0 * (int32_t)v0[w];
+            mac<W>(acc, e0, v0);
         }
         const uint32_t vr = A.vrow[chunk * SELL_C + r];
-        if (vr == VROW_EMPTY) continue;
-        if (vr & VROW_SPLIT) {
-            unsigned long long *dst = acc64 + (size_t)(vr & ~VROW_SPLIT) * NV + part * W;
-#pragma unroll
-            for (int w = 0; w < W; w++) atomicAdd(dst + w, (unsigned long long)acc[w]);
-        } else {
-            const uint32_t s = __ldg(scale + vr);
-            uint32_t o[W];
-#pragma unroll
-            for (int w = 0; w < W; w++) o[w] = mulm(s, red_s64(acc[w], mp), mp);
-            stv<W>(y + (size_t)vr * NV + part * W, o);
-        }
+        if (vr != VROW_EMPTY) row_out<W>(vr, acc, y, scale, acc64, NV, part * W, mp);
     }
 }
 
@@ -145,66 +193,53 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
     y[(size_t)r * nv + b] = mulm(scale[r], red_s64((int64_t)s, mp), mp);
 }
 
-// S_raw[k] += Xh^T T (m x n block), k read from the term counter.  Partial
-// sums are reduced mod p before the exact uint64 atomics, so the sum over
-// blocks cannot overflow and its value does not depend on the order.
+// S_raw[k] += Xh^T T (m x n), k read from the term counter.  m threads per
+// row (one per row of the block Xh^T), NV register accumulators each; rows are
+// streamed over the grid.  Partials are reduced mod p before the exact uint64
+// atomics, so their sum cannot overflow and does not depend on the order.
 constexpr int PROJ_THREADS = 256;
-constexpr int PROJ_TILE = 64;
 
-template <int KLAZY>
+template <int NV, int KLAZY>
 __global__ void __launch_bounds__(PROJ_THREADS)
-    k_project(int64_t N, int m, int n, int nv, const uint32_t *__restrict__ xh,
-              const uint32_t *__restrict__ t, unsigned long long *__restrict__ s_raw,
-              const int *__restrict__ term_counter, ModP mp) {
-    __shared__ uint32_t xs[PROJ_TILE * 32];
-    __shared__ uint32_t ts[PROJ_TILE * 32];
-    __shared__ unsigned long long red[PROJ_THREADS];
-    const int E = m * n;
-    const int groups = E >= PROJ_THREADS ? 1 : PROJ_THREADS / E;
+    k_project(int64_t N, int m, int n, const uint32_t *__restrict__ xh, const uint32_t *__restrict__ t,
+              unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, ModP mp) {
+    __shared__ unsigned long long red[32 * NV];
     const int tid = threadIdx.x;
-    const int g = E >= PROJ_THREADS ? 0 : tid / E;
-    const bool active = E >= PROJ_THREADS || g < groups;
-    unsigned long long acc[4] = {0, 0, 0, 0};
-    const int64_t ntiles = (N + PROJ_TILE - 1) / PROJ_TILE;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * PROJ_TILE;
-        const int rows = (int)min64(PROJ_TILE, N - r0);
-        __syncthreads();
-        for (int i = tid; i < rows * m; i += PROJ_THREADS) xs[i] = xh[r0 * m + i];
-        for (int i = tid; i < rows * n; i += PROJ_THREADS) {
-            int rr = i / n, b = i % n;
-            ts[i] = t[(r0 + rr) * nv + b];
-        }
-        __syncthreads();
-        if (!active) continue;
-        for (int k = 0; k < 4; k++) {
-            const int e = E >= PROJ_THREADS ? tid + k * PROJ_THREADS : (k == 0 ? tid % E : -1);
-            if (e < 0 || e >= E) break;
-            const int a = e / n, b = e % n;
-            unsigned long long s = acc[k];
-            int cnt = 0;
-            for (int rr = g; rr < rows; rr += groups) {
-                s += (unsigned long long)xs[rr * m + a] * ts[rr * n + b];
-                if (++cnt == KLAZY) { s = red64(s, mp); cnt = 0; }
+    for (int i = tid; i < m * NV; i += PROJ_THREADS) red[i] = 0;
+    const int per = PROJ_THREADS / m;  // rows per block step
+    const int a = tid % m, slot = tid / m;
+    unsigned long long acc[NV];
+#pragma unroll
+    for (int b = 0; b < NV; b++) acc[b] = 0;
+    if (slot < per) {
+        int cnt = 0;
+        for (int64_t r = (int64_t)blockIdx.x * per + slot; r < N; r += (int64_t)gridDim.x * per) {
+            const unsigned long long xv = __ldg(xh + r * m + a);
+            uint32_t tv[NV];
+            ldv<NV>(t + r * NV, tv);
+#pragma unroll
+            for (int b = 0; b < NV; b++) acc[b] += xv * tv[b];
+            if (++cnt == KLAZY) {
+#pragma unroll
+                for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
+                cnt = 0;
             }
-            acc[k] = red64(s, mp);
         }
+#pragma unroll
+        for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
     }
+    __syncthreads();
+    if (slot < per) {
+#pragma unroll
+        for (int b = 0; b < NV; b++)
+            if (b < n && acc[b]) atomicAdd(&red[a * NV + b], acc[b]);
+    }
+    __syncthreads();
     const int k_term = *term_counter;
-    unsigned long long *dst = s_raw + (size_t)k_term * E;
-    if (E >= PROJ_THREADS) {
-        for (int k = 0; k < 4; k++) {
-            const int e = tid + k * PROJ_THREADS;
-            if (e < E && acc[k]) atomicAdd(dst + e, acc[k]);
-        }
-    } else {
-        red[tid] = active ? acc[0] : 0;
-        __syncthreads();
-        if (tid < E) {
-            unsigned long long s = 0;
-            for (int gg = 0; gg < groups; gg++) s += red[gg * E + tid];
-            if (s) atomicAdd(dst + tid, s);
-        }
+    unsigned long long *dst = s_raw + (size_t)k_term * m * n;
+    for (int e = tid; e < m * n; e += PROJ_THREADS) {
+        const unsigned long long v = red[(e / n) * NV + e % n];
+        if (v) atomicAdd(dst + e, v);
     }
 }
 
@@ -268,14 +303,11 @@ template <int NV>
 wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y,
                         const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
                         int *term_counter) {
-    if (A.nchunks > 0) {
-        int64_t threads = A.nchunks * 32;
-        k_spmm<NV><<<blocks_for(threads, 256), 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp,
-                                                                      term_counter);
-        WR_LAUNCHED(ctx);
-    } else if (term_counter) {
-        // keep the term counter moving even for an empty matrix
-        k_spmm<NV><<<1, 32, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter);
+    const int64_t vblocks = (A.nseg + 7) / 8;
+    const int64_t lblocks = (A.nchunks * Lanes<NV>::G + 7) / 8;
+    const int64_t blocks = std::max<int64_t>(vblocks + lblocks, term_counter ? 1 : 0);
+    if (blocks > 0) {
+        k_spmm<NV><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter, vblocks);
         WR_LAUNCHED(ctx);
     }
     if (A.nsplit > 0) {
@@ -301,17 +333,30 @@ wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x,
     }
 }
 
+template <int NV>
+void launch_project_t(wr_ctx *ctx, unsigned grid, int64_t N, int m, int n, const uint32_t *xh,
+                      const uint32_t *t, unsigned long long *s_raw, const int *term_counter, const ModP &mp) {
+    if (mp.lazy >= 16)
+        k_project<NV, 16><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, mp);
+    else
+        k_project<NV, 4><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, mp);
+}
+
 wr_status launch_project(wr_ctx *ctx, int64_t N, int m, int n, int nv, const uint32_t *xh,
                          const uint32_t *t, unsigned long long *s_raw, const int *term_counter,
                          const ModP &mp) {
-    int64_t ntiles = (N + PROJ_TILE - 1) / PROJ_TILE;
-    int64_t grid = std::min<int64_t>(std::max<int64_t>(ntiles, 1), (int64_t)ctx->num_sms * 4);
-    if (mp.lazy >= 16)
-        k_project<16><<<(unsigned)grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, nv, xh, t, s_raw,
-                                                                         term_counter, mp);
-    else
-        k_project<4><<<(unsigned)grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, nv, xh, t, s_raw,
-                                                                        term_counter, mp);
+    const int per = PROJ_THREADS / m;
+    const int64_t need = std::max<int64_t>((N + per - 1) / per, 1);
+    const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ctx->num_sms * 4);
+    switch (nv) {
+        case 1: launch_project_t<1>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        case 2: launch_project_t<2>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        case 4: launch_project_t<4>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        case 8: launch_project_t<8>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        case 16: launch_project_t<16>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        case 32: launch_project_t<32>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        default: return fail(WR_EINVAL, "unsupported padded block width");
+    }
     WR_LAUNCHED(ctx);
     return WR_OK;
 }
