@@ -90,6 +90,9 @@ typedef struct {
     double spmm_bytes;   /* algorithmic bytes of those launches                            */
     int64_t kernel_launches; /* kernels launched through this context since its creation  */
                              /* (each replay of a captured graph counts its kernel nodes)    */
+    double sigma_window_ms;  /* when profiling is on: sigma-basis time in the discrepancy    */
+    double sigma_local_ms;   /* windows, the per-chunk M-Basis and the transform products    */
+    double sigma_apply_ms;
 } wr_timings;
 
 /* ---------------------------------------------------------------- context */

@@ -108,6 +108,13 @@ __host__ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, co
     return u >= m.p ? u - m.p : u;
 }
 
+// Montgomery reduction of a 64-bit T < p 2^32: T R^{-1} mod p.
+__host__ __device__ __forceinline__ uint32_t mont_redc(uint64_t t, const ModP &m) {
+    const uint32_t k = (uint32_t)t * m.pneg;
+    const uint32_t u = (uint32_t)((t + (uint64_t)k * m.p) >> 32);
+    return u >= m.p ? u - m.p : u;
+}
+
 __host__ __device__ __forceinline__ uint32_t to_mont(uint32_t a, const ModP &m) { return mont_mul(a, m.r2, m); }
 __host__ __device__ __forceinline__ uint32_t from_mont(uint32_t a, const ModP &m) { return mont_mul(a, 1u, m); }
 
@@ -190,7 +197,7 @@ struct DevBuf {
 //    second kernel reduces, scales and stores.
 
 constexpr int SELL_C = 32;
-constexpr int LIGHT_MAX = 32;
+constexpr int LIGHT_MAX = 64;
 constexpr int VSEG = 256;
 constexpr uint32_t VROW_SPLIT = 0x80000000u;
 constexpr uint32_t VROW_EMPTY = 0xFFFFFFFFu;

@@ -118,205 +118,249 @@ __global__ void __launch_bounds__(WIN_THREADS)
 }
 
 // ---- local M-Basis over the window: one block, bb orders.
-// Shared layout: Es [bb][m][q] (normal form), Ml [bb+1][q][q], D [m][q] and
-// Tff [q][q] (Montgomery form), Tp [m][q] (normal form), small vectors.
-// The elimination is fraction-free in Montgomery form; the transform of the
-// order (normalised by the inverse column scales) is then applied row by row
-// to the rest of the window and to Ml with lazy uint64 accumulation.
+//
+// Shared memory: the window Es (bb x m x q, normal form), the chunk transform
+// Ml ((2 bb + 1) x q x q), Tp (m x q: T[pc[t]][j], normal form), small vectors.
+// Multiplying column c by x moves no data: window column c is read at row
+// i' - sh[c] (sh = shifts so far in the chunk), and Ml column c holds its
+// coefficient s at row base[c] + s, base[c] decreasing by one per shift.
+//
+// Per order, warp 0 eliminates the discrepancy with one column per lane
+// (two for q > 32), right-looking and fraction-free in Montgomery form: when
+// the current column (in (degree, index) order) is nonzero it becomes a pivot
+// and every later column is reduced by it at once.  Each column is reduced by
+// exactly the pivots created before it, so the reduced columns and the
+// transform are the unique ones of the order-by-order rule.  All threads
+// then apply the normalised transform new[j] = old[j] + sum_t Tp[t][j]
+// old[pc[t]] to the rest of the window and to Ml.
 constexpr int LOCAL_THREADS = 1024;
 
-template <int KLAZY>
-__global__ void __launch_bounds__(LOCAL_THREADS)
+template <int MM, int CPL, int KLAZY>
+__global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
     k_local(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
             uint32_t *__restrict__ qtop, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
             int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, ModP mp) {
     extern __shared__ uint32_t sm[];
+    const int mq = m * q, qq = q * q;
+    const int mlrows = 2 * bb + 1;
     uint32_t *Es = sm;                                   // bb*m*q
-    uint32_t *Ml = Es + (size_t)bb * m * q;              // (bb+1)*q*q
-    uint32_t *D = Ml + (size_t)(bb + 1) * q * q;         // m*q
-    uint32_t *Tff = D + m * q;                           // q*q  (row j: transform of column j)
-    uint32_t *Tp = Tff + q * q;                          // m*q  (Tp[t][j] = T[pc[t]][j])
-    uint32_t *scl = Tp + m * q;                          // q
-    uint32_t *sinv = scl + q;                            // q
-    int *deg = (int *)(sinv + q);                        // q
+    uint32_t *Ml = Es + (size_t)bb * mq;                 // (2bb+1)*q*q
+    uint32_t *Tp = Ml + (size_t)mlrows * qq;             // m*q
+    uint32_t *tmp = Tp + mq;                             // m*q
+    int *deg = (int *)(tmp + mq);                        // q
     int *degl = deg + q;                                 // q
-    int *ord = degl + q;                                 // q
-    int *pc = ord + q;                                   // m
-    int *pr = pc + m;                                    // m
-    int *isp = pr + m;                                   // q
-    int *npiv = isp + q;                                 // 1
+    int *sh = degl + q;                                  // q
+    int *base = sh + q;                                  // q
+    int *pc = base + q;                                  // m
+    int *npiv = pc + m;                                  // 1
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    const int E = bb * m * q;
+    const int E = bb * mq;
 
     for (int x = tid; x < E; x += nth) {
         unsigned long long v = 0;
         for (int b = 0; b < nparts; b++) v += Epart[(size_t)b * E + x];
         uint32_t e = red64(v, mp);
-        if (x < m * q) e = subm(e, qtop[x], mp);
+        if (x < mq) e = subm(e, qtop[x], mp);
         Es[x] = e;
     }
-    for (int x = tid; x < (bb + 1) * q * q; x += nth) {
-        const int s = x / (q * q), rem = x % (q * q);
-        Ml[x] = (s == 0 && rem / q == rem % q) ? 1u : 0u;
+    for (int x = tid; x < mlrows * qq; x += nth) {
+        const int s2 = x / qq, rem = x % qq;
+        Ml[x] = (s2 == bb && rem / q == rem % q) ? 1u : 0u;  // logical coefficient 0 at row base = bb
     }
     for (int c = tid; c < q; c += nth) {
         deg[c] = deg_g[c];
         degl[c] = 0;
+        sh[c] = 0;
+        base[c] = bb;
     }
     __syncthreads();
-    // rows of the transform step: q <= 32 -> 32/W2 rows per warp, W2 = pow2 >= q
     int W2 = 1;
     while (W2 < q && W2 < 32) W2 <<= 1;
     const int rpw = 32 / W2;
     const int grp = lane / W2, col = lane % W2;
-    const unsigned gmask = (W2 == 32) ? 0xffffffffu : (((1u << W2) - 1u) << (grp * W2));
 
     for (int i = 0; i < bb; i++) {
-        // ---- elimination on Delta = Es[i] (warp 0), fraction-free, Montgomery form
         if (warp == 0) {
-            for (int x = lane; x < m * q; x += 32) D[x] = to_mont(Es[(size_t)i * m * q + x], mp);
-            for (int c = lane; c < q; c += 32) {
-                int rk = 0;
-                for (int c2 = 0; c2 < q; c2++)
-                    rk += (deg[c2] < deg[c] || (deg[c2] == deg[c] && c2 < c)) ? 1 : 0;
-                ord[rk] = c;
-                scl[c] = mp.r1;
-                isp[c] = 0;
-                for (int x = 0; x < q; x++) Tff[c * q + x] = (x == c) ? mp.r1 : 0u;
+            // column j = lane + 32 k of this lane
+            uint32_t d[CPL][MM], tp[CPL][MM], sc[CPL];
+            int rk[CPL];
+#pragma unroll
+            for (int k = 0; k < CPL; k++) {
+                const int j = lane + 32 * k;
+                const bool v = j < q;
+                sc[k] = mp.r1;
+                rk[k] = 1 << 20;
+                if (v) {
+                    int r0 = 0;
+                    for (int c2 = 0; c2 < q; c2++)
+                        r0 += (deg[c2] < deg[j] || (deg[c2] == deg[j] && c2 < j)) ? 1 : 0;
+                    rk[k] = r0;
+                }
+                const uint32_t *er = Es + (size_t)(i - (v ? sh[j] : 0)) * mq + (v ? j : 0);
+#pragma unroll
+                for (int a2 = 0; a2 < MM; a2++) {
+                    d[k][a2] = (v && a2 < m) ? to_mont(er[a2 * q], mp) : 0u;
+                    tp[k][a2] = 0u;
+                }
             }
-            __syncwarp();
             int np = 0;
-            for (int oi = 0; oi < q; oi++) {
-                const int j = ord[oi];
-                for (int t = 0; t < np; t++) {
-                    const int c = pc[t], r = pr[t];
-                    const uint32_t dj = D[r * q + j];
-                    if (dj == 0) continue;
-                    const uint32_t dc = D[r * q + c];
-                    __syncwarp();
-                    for (int aa = lane; aa < m; aa += 32)
-                        D[aa * q + j] = subm(mont_mul(dc, D[aa * q + j], mp), mont_mul(dj, D[aa * q + c], mp), mp);
-                    for (int x = lane; x < q; x += 32)
-                        Tff[j * q + x] = subm(mont_mul(dc, Tff[j * q + x], mp), mont_mul(dj, Tff[c * q + x], mp), mp);
-                    if (lane == 0) scl[j] = mont_mul(scl[j], dc, mp);
-                    __syncwarp();
+            for (int step = 0; step < q; step++) {
+                // the current column: the one of rank `step`
+                int mine = -1;
+#pragma unroll
+                for (int k = 0; k < CPL; k++)
+                    if (rk[k] == step) mine = k;
+                const unsigned who = __ballot_sync(0xffffffffu, mine >= 0);
+                const int src = __ffs(who) - 1;
+                // its first nonzero row (or -1)
+                int fr = -1;
+                uint32_t sc_cur = 0;
+                if (mine >= 0) {
+#pragma unroll
+                    for (int k = 0; k < CPL; k++)
+                        if (k == mine) {
+                            sc_cur = sc[k];
+#pragma unroll
+                            for (int a2 = MM - 1; a2 >= 0; a2--)
+                                if (d[k][a2] != 0) fr = a2;
+                        }
                 }
-                // first nonzero row (m <= 32: one row per lane)
-                const unsigned bal = __ballot_sync(0xffffffffu, lane < m && D[lane * q + j] != 0);
-                if (bal) {
-                    if (lane == 0) {
-                        pc[np] = j;
-                        pr[np] = __ffs(bal) - 1;
-                        isp[j] = 1;
+                fr = __shfl_sync(0xffffffffu, fr, src);
+                if (fr < 0) continue;  // zero column: no pivot
+                const int jcur = __shfl_sync(0xffffffffu, lane + 32 * (mine >= 0 ? mine : 0), src);
+                sc_cur = __shfl_sync(0xffffffffu, sc_cur, src);
+                // broadcast the pivot column and its transform coefficients
+                uint32_t pv[MM], pt[MM];
+#pragma unroll
+                for (int a2 = 0; a2 < MM; a2++) {
+                    uint32_t x0 = 0, x1 = 0;
+#pragma unroll
+                    for (int k = 0; k < CPL; k++)
+                        if (k == mine) { x0 = d[k][a2]; x1 = tp[k][a2]; }
+                    pv[a2] = __shfl_sync(0xffffffffu, x0, src);
+                    pt[a2] = __shfl_sync(0xffffffffu, x1, src);
+                }
+                uint32_t dc = 0;
+#pragma unroll
+                for (int a2 = 0; a2 < MM; a2++)
+                    if (a2 == fr) dc = pv[a2];
+                // reduce every later column: col <- dc col - dj pivot (fraction-free)
+#pragma unroll
+                for (int k = 0; k < CPL; k++) {
+                    if (rk[k] > step && rk[k] < (1 << 20)) {
+                        uint32_t dj = 0;
+#pragma unroll
+                        for (int a2 = 0; a2 < MM; a2++)
+                            if (a2 == fr) dj = d[k][a2];
+                        if (dj != 0) {
+#pragma unroll
+                            for (int a2 = 0; a2 < MM; a2++)
+                                d[k][a2] = subm(mont_mul(dc, d[k][a2], mp), mont_mul(dj, pv[a2], mp), mp);
+#pragma unroll
+                            for (int t = 0; t < MM; t++) {
+                                if (t < np) tp[k][t] = subm(mont_mul(dc, tp[k][t], mp), mont_mul(dj, pt[t], mp), mp);
+                                else if (t == np) tp[k][t] = subm(0u, mont_mul(dj, sc_cur, mp), mp);
+                            }
+                            sc[k] = mont_mul(sc[k], dc, mp);
+                        }
                     }
-                    np++;
                 }
-                __syncwarp();
+                if (lane == 0) pc[np] = jcur;
+                np++;
             }
-            if (lane == 0) *npiv = np;
-            // normal-form inverse of each column scale: from_mont((s R)^{-1} R) = s^{-1}
-            for (int c = lane; c < q; c += 32) sinv[c] = from_mont(mont_inv(scl[c], mp), mp);
+            // normalise: Tp[t][j] = tp_j[t] / s_j (normal form), and the local
+            // degree bounds of the columns that absorbed pivot columns
             __syncwarp();
-            // Tp[t][j] = T[pc[t]][j] = Tff[j][pc[t]] / s_j  (Tff is in Montgomery form:
-            // mont_mul(x R, y) = x y)
-            for (int x = lane; x < np * q; x += 32) {
-                const int t = x / q, j = x % q;
-                Tp[t * q + j] = (j == pc[t]) ? 0u : mont_mul(Tff[j * q + pc[t]], sinv[j], mp);
-            }
-            __syncwarp();
-            // local degree bounds: column j now also holds multiples of the pivot
-            // columns added to it, which may have a larger local degree
-            int dnew[2] = {0, 0};
-            for (int k = 0; k < 2; k++) {
+#pragma unroll
+            for (int k = 0; k < CPL; k++) {
                 const int j = lane + 32 * k;
                 if (j < q) {
-                    int d = degl[j];
-                    for (int t = 0; t < np; t++)
-                        if (Tp[t * q + j]) d = max(d, degl[pc[t]]);
-                    dnew[k] = d;
+                    const uint32_t sinv = from_mont(mont_inv(sc[k], mp), mp);
+                    int dl = degl[j];
+#pragma unroll
+                    for (int t = 0; t < MM; t++)
+                        if (t < np) {
+                            const uint32_t v = mont_mul(tp[k][t], sinv, mp);
+                            Tp[t * q + j] = v;
+                            if (v) dl = max(dl, degl[pc[t]]);
+                        }
+                    tmp[j] = (uint32_t)dl;
                 }
             }
             __syncwarp();
-            for (int k = 0; k < 2; k++)
-                if (lane + 32 * k < q) degl[lane + 32 * k] = dnew[k];
+            for (int j = lane; j < q; j += 32) degl[j] = (int)tmp[j];
+            if (lane == 0) *npiv = np;
         }
         __syncthreads();
         const int np = *npiv;
-        // ---- apply: new[j] = old[j] + sum_t Tp[t][j] old[pc[t]] on the rest
-        //      of the window (orders i..bb-1) and on Ml (coefficients <= max degl)
+        // ---- apply the transform to window orders i..bb-1 and to Ml
         {
             const int erows = (bb - i) * m;
             int dl = 0;
             for (int c = 0; c < q; c++) dl = max(dl, degl[c]);
             const int nrows = erows + (dl + 1) * q;
-            if (q <= 32) {
-                for (int row0 = warp * rpw; row0 < nrows; row0 += nwarps * rpw) {
-                    const int row = row0 + grp;
-                    const bool ok = row < nrows && col < q;
-                    uint32_t *base = row < erows ? Es + ((size_t)i * m + row) * q : Ml + (size_t)(row - erows) * q;
-                    const uint32_t v = ok ? base[col] : 0u;
-                    unsigned long long acc = v;
-                    int cnt = 0;
-                    for (int t = 0; t < np; t++) {
-                        const uint32_t oc = __shfl_sync(0xffffffffu, v, grp * W2 + pc[t]);
-                        if (ok) acc += (unsigned long long)Tp[t * q + col] * oc;
-                        if (++cnt == KLAZY) { acc = red64(acc, mp); cnt = 0; }
+            for (int row0 = warp * rpw; row0 < nrows; row0 += nwarps * rpw) {
+                const int row = row0 + grp;
+                const bool rowok = row < nrows;
+                // each lane: column j = col (q <= 32) or lane, lane + 32 (q > 32)
+                uint32_t *p0 = nullptr, *p1 = nullptr;
+                uint32_t v0 = 0, v1 = 0;
+                const int j0 = q <= 32 ? col : lane;
+                const int j1 = q <= 32 ? -1 : lane + 32;
+                if (rowok) {
+                    if (row < erows) {
+                        const int ip = i + row / m, a2 = row % m;
+                        if (j0 < q) p0 = Es + ((size_t)(ip - sh[j0]) * m + a2) * q + j0;
+                        if (j1 >= 0 && j1 < q) p1 = Es + ((size_t)(ip - sh[j1]) * m + a2) * q + j1;
+                    } else {
+                        const int s2 = (row - erows) / q, x = (row - erows) % q;
+                        if (j0 < q) p0 = Ml + ((size_t)(base[j0] + s2) * q + x) * q + j0;
+                        if (j1 >= 0 && j1 < q) p1 = Ml + ((size_t)(base[j1] + s2) * q + x) * q + j1;
                     }
-                    if (ok) base[col] = red64(acc, mp);
                 }
-            } else {
-                for (int row = warp; row < nrows; row += nwarps) {
-                    uint32_t *base = row < erows ? Es + ((size_t)i * m + row) * q : Ml + (size_t)(row - erows) * q;
-                    const uint32_t v0 = base[lane];
-                    const uint32_t v1 = lane + 32 < q ? base[lane + 32] : 0u;
-                    unsigned long long a0 = v0, a1 = v1;
-                    int cnt = 0;
-                    for (int t = 0; t < np; t++) {
-                        const int c = pc[t];
-                        const uint32_t oc = c < 32 ? __shfl_sync(0xffffffffu, v0, c) : __shfl_sync(0xffffffffu, v1, c - 32);
-                        a0 += (unsigned long long)Tp[t * q + lane] * oc;
-                        if (lane + 32 < q) a1 += (unsigned long long)Tp[t * q + lane + 32] * oc;
-                        if (++cnt == KLAZY) { a0 = red64(a0, mp); a1 = red64(a1, mp); cnt = 0; }
-                    }
-                    base[lane] = red64(a0, mp);
-                    if (lane + 32 < q) base[lane + 32] = red64(a1, mp);
+                if (p0) v0 = *p0;
+                if (p1) v1 = *p1;
+                unsigned long long a0 = v0, a1 = v1;
+                int cnt = 0;
+                for (int t = 0; t < np; t++) {
+                    const int c = pc[t];
+                    uint32_t oc;
+                    if (q <= 32) oc = __shfl_sync(0xffffffffu, v0, grp * W2 + c);
+                    else oc = c < 32 ? __shfl_sync(0xffffffffu, v0, c) : __shfl_sync(0xffffffffu, v1, c - 32);
+                    if (p0) a0 += (unsigned long long)Tp[t * q + j0] * oc;
+                    if (p1) a1 += (unsigned long long)Tp[t * q + j1] * oc;
+                    if (++cnt == KLAZY) { a0 = red64(a0, mp); a1 = red64(a1, mp); cnt = 0; }
                 }
-            }
-            (void)gmask;
-        }
-        __syncthreads();
-        // ---- multiply pivot columns by x: shift in the window and in Ml
-        for (int w = tid; w < np * (m + q); w += nth) {
-            const int t = w / (m + q), k = w % (m + q);
-            const int c = pc[t];
-            if (k < m) {
-                for (int ii = bb - 1; ii > i; ii--)
-                    Es[((size_t)ii * m + k) * q + c] = Es[((size_t)(ii - 1) * m + k) * q + c];
-            } else {
-                const int x = k - m;
-                for (int s2 = degl[c] + 1; s2 > 0; s2--)
-                    Ml[((size_t)s2 * q + x) * q + c] = Ml[((size_t)(s2 - 1) * q + x) * q + c];
-                Ml[(size_t)x * q + c] = 0;
+                if (p0) *p0 = red64(a0, mp);
+                if (p1) *p1 = red64(a1, mp);
             }
         }
         __syncthreads();
+        // ---- multiply the pivot columns by x
         for (int t = tid; t < np; t += nth) {
-            deg[pc[t]] += 1;
-            degl[pc[t]] += 1;
+            const int c = pc[t];
+            deg[c] += 1;
+            degl[c] += 1;
+            sh[c] += 1;
+            base[c] -= 1;
         }
         __syncthreads();
     }
-    // ---- Qtop <- Qtop * Ml[bb]; write back
-    for (int x = tid; x < m * q; x += nth) {
+    // ---- Qtop <- Qtop * Ml[bb]; write back Ml in logical layout
+    for (int x = tid; x < mq; x += nth) {
         const int aa = x / q, c = x % q;
         unsigned long long acc = 0;
-        for (int y = 0; y < q; y++) acc = red64(acc + (unsigned long long)qtop[aa * q + y] * Ml[((size_t)bb * q + y) * q + c], mp);
-        D[x] = (uint32_t)acc;
+        for (int y = 0; y < q; y++)
+            acc = red64(acc + (unsigned long long)qtop[aa * q + y] * Ml[((size_t)(base[c] + bb) * q + y) * q + c], mp);
+        tmp[x] = (uint32_t)acc;
     }
     __syncthreads();
-    for (int x = tid; x < m * q; x += nth) qtop[x] = D[x];
-    for (int x = tid; x < (bb + 1) * q * q; x += nth) Ml_g[x] = Ml[x];
+    for (int x = tid; x < mq; x += nth) qtop[x] = tmp[x];
+    for (int x = tid; x < (bb + 1) * qq; x += nth) {
+        const int s2 = x / qq, c = x % q, y = (x / q) % q;
+        Ml_g[x] = Ml[((size_t)(base[c] + s2) * q + y) * q + c];
+    }
     for (int c = tid; c < q; c += nth) {
         deg_g[c] = deg[c];
         degl_g[c] = degl[c];
@@ -529,8 +573,8 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     // chunk size b and tiles: every kernel's shared memory must fit
     const size_t budget = std::min<size_t>(ctx->smem_optin, 227 * 1024) - 1024;
     auto local_bytes = [&](int b) {
-        return sizeof(uint32_t) * ((size_t)b * m * q + (size_t)(b + 1) * q * q + m * q + q * q + m * q + 2 * q) +
-               sizeof(int) * (4 * q + 2 * m + 1);
+        return sizeof(uint32_t) * ((size_t)b * m * q + (size_t)(2 * b + 1) * q * q + 2 * m * q) +
+               sizeof(int) * (4 * q + m + 1);
     };
     auto window_bytes = [&](int TT, int b) {
         const int nib = (b + WIN_IB - 1) / WIN_IB;
@@ -552,7 +596,13 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     WR_TRY(dev_alloc(ctx, Epart, sizeof(uint32_t) * (size_t)nparts_max * bmax * m * q));
     const bool lazy16 = mp.lazy >= 16;
     auto *kwin = lazy16 ? k_window<16> : k_window<4>;
-    auto *kloc = lazy16 ? k_local<16> : k_local<4>;
+    using LocalFn = void (*)(int, int, int, int, int, const uint32_t *, uint32_t *, int32_t *, uint32_t *,
+                             int32_t *, int *, ModP);
+    LocalFn kloc;
+    if (m <= 8)
+        kloc = q <= 32 ? (lazy16 ? k_local<8, 1, 16> : k_local<8, 1, 4>) : (lazy16 ? k_local<8, 2, 16> : k_local<8, 2, 4>);
+    else
+        kloc = q <= 32 ? (lazy16 ? k_local<32, 1, 16> : k_local<32, 1, 4>) : (lazy16 ? k_local<32, 2, 16> : k_local<32, 2, 4>);
     auto *kapp = lazy16 ? k_apply<16> : k_apply<4>;
     WR_CUDA(cudaFuncSetAttribute(kwin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     WR_CUDA(cudaFuncSetAttribute(kloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
@@ -560,8 +610,16 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
 
     uint32_t *Pcur = d_P, *Pnext = P2.as<uint32_t>();
     int64_t Dbound = 1;
+    // profiling: events around the three kernels of every 16th chunk
+    cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
+    double pw = 0, pl = 0, pa = 0;
+    int64_t nchunks = (L + bmax - 1) / bmax, sampled = 0;
+    if (ctx->profiling)
+        for (auto &e : pe) WR_CUDA(cudaEventCreate(&e));
     for (int64_t k0 = 0; k0 < L; k0 += bmax) {
         const int bb = (int)std::min<int64_t>(bmax, L - k0);
+        const bool prof = ctx->profiling && ((k0 / bmax) % 16 == 0);
+        if (prof) WR_CUDA(cudaEventRecord(pe[0], s));
         // window: split coefficients [0, min(Dbound, k0 + bb - 1)] over the blocks
         const int64_t tspan = std::min<int64_t>(Dbound, k0 + bb - 1) + 1;
         const int nparts = (int)std::min<int64_t>(nparts_max, std::max<int64_t>(1, (tspan + TT - 1) / TT));
@@ -569,16 +627,37 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         kwin<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, n, q, Pcur, k0, bb, TT, tper,
                                                                 dmax.as<int>(), Epart.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
-        kloc<<<1, LOCAL_THREADS, local_bytes(bb), s>>>(m, n, q, bb, nparts, Epart.as<uint32_t>(), qtop.as<uint32_t>(),
+        if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
+        kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(m, n, q, bb, nparts, Epart.as<uint32_t>(), qtop.as<uint32_t>(),
                                                         d_deg, Ml.as<uint32_t>(), degl.as<int32_t>(), dmax.as<int>(), mp);
         WR_LAUNCHED(ctx);
+        if (prof) WR_CUDA(cudaEventRecord(pe[2], s));
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
         const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
         kapp<<<(unsigned)((Dnew + TA) / TA), APP_THREADS, apply_bytes(TA, bb), s>>>(
             Pcur, Pnext, n, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, mp);
         WR_LAUNCHED(ctx);
+        if (prof) {
+            WR_CUDA(cudaEventRecord(pe[3], s));
+            WR_CUDA(cudaEventSynchronize(pe[3]));
+            float a = 0, b = 0, c = 0;
+            cudaEventElapsedTime(&a, pe[0], pe[1]);
+            cudaEventElapsedTime(&b, pe[1], pe[2]);
+            cudaEventElapsedTime(&c, pe[2], pe[3]);
+            pw += a;
+            pl += b;
+            pa += c;
+            sampled++;
+        }
         std::swap(Pcur, Pnext);
         Dbound = Dnew;
+    }
+    if (ctx->profiling) {
+        for (auto &e : pe) cudaEventDestroy(e);
+        const double scale = sampled ? (double)nchunks / sampled : 0.0;  // extrapolate the samples
+        ctx->last.sigma_window_ms = pw * scale;
+        ctx->last.sigma_local_ms = pl * scale;
+        ctx->last.sigma_apply_ms = pa * scale;
     }
     if (Pcur != d_P)
         WR_CUDA(cudaMemcpyAsync(d_P, Pcur, sizeof(uint32_t) * (Dbound + 1) * nq, cudaMemcpyDeviceToDevice, s));

@@ -73,6 +73,10 @@ __device__ __forceinline__ void mac(int64_t (&acc)[W], uint32_t e, const uint32_
 
 // Epilogue of a finished row: y[row] = scale[row] * (sum mod p), or, for a
 // row cut into segments, the exact partial sums added into acc64.
+// A direct row has at most VSEG entries, so |sum| < 2^15 p and
+// T = sum + 2^15 p lies in [0, 2^16 p), below p R: one Montgomery reduction
+// gives T R^{-1}; with the scale taken to scale R^2 mod p (two Montgomery
+// products), mont_mul(T R^{-1}, scale R^2) = sum * scale mod p.
 template <int W>
 __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], uint32_t *y,
                                         const uint32_t *scale, unsigned long long *acc64, int nv,
@@ -82,10 +86,11 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
 #pragma unroll
         for (int w = 0; w < W; w++) atomicAdd(dst + w, (unsigned long long)acc[w]);
     } else {
-        const uint32_t s = __ldg(scale + tgt);
+        const uint32_t s2 = to_mont(to_mont(__ldg(scale + tgt), mp), mp);
+        const uint64_t off = (uint64_t)mp.p << 15;
         uint32_t o[W];
 #pragma unroll
-        for (int w = 0; w < W; w++) o[w] = mulm(s, red_s64(acc[w], mp), mp);
+        for (int w = 0; w < W; w++) o[w] = mont_mul(mont_redc((uint64_t)acc[w] + off, mp), s2, mp);
         stv<W>(y + (size_t)tgt * nv + col0, o);
     }
 }
@@ -154,6 +159,16 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
 #pragma unroll
         for (int w = 0; w < W; w++) acc[w] = 0;
         int j = 0;
+        for (; j + 8 <= len; j += 8) {
+            uint32_t ee[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) ee[u] = __ldg(e + (j + u) * SELL_C);
+            uint32_t vv[8][W];
+#pragma unroll
+            for (int u = 0; u < 8; u++) ldv<W>(xb + (ee[u] >> 8) * NV, vv[u]);
+#pragma unroll
+            for (int u = 0; u < 8; u++) mac<W>(acc, ee[u], vv[u]);
+        }
         for (; j + 4 <= len; j += 4) {
             const uint32_t e0 = __ldg(e + (j + 0) * SELL_C), e1 = __ldg(e + (j + 1) * SELL_C);
             const uint32_t e2 = __ldg(e + (j + 2) * SELL_C), e3 = __ldg(e + (j + 3) * SELL_C);
@@ -203,9 +218,12 @@ template <int NV, int KLAZY>
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project(int64_t N, int m, int n, const uint32_t *__restrict__ xh, const uint32_t *__restrict__ t,
               unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, ModP mp) {
+    // red32[w][a][b]: per-warp sums reduced mod p (m divides 32); red: one
+    // shared row of atomically added sums (other m)
+    __shared__ uint32_t red32[(PROJ_THREADS / 32) * 32 * NV];
     __shared__ unsigned long long red[32 * NV];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < m * NV; i += PROJ_THREADS) red[i] = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool pow2 = (32 % m) == 0;
     const int per = PROJ_THREADS / m;  // rows per block step
     const int a = tid % m, slot = tid / m;
     unsigned long long acc[NV];
@@ -228,18 +246,39 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
         for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
     }
-    __syncthreads();
-    if (slot < per) {
+    if (pow2) {
+        // lanes of a warp with the same a hold the same (a, b) entries:
+        // butterfly over the slot bits (offsets m, 2m, ..., 16)
+        for (int off = m; off < 32; off <<= 1)
 #pragma unroll
-        for (int b = 0; b < NV; b++)
-            if (b < n && acc[b]) atomicAdd(&red[a * NV + b], acc[b]);
-    }
-    __syncthreads();
-    const int k_term = *term_counter;
-    unsigned long long *dst = s_raw + (size_t)k_term * m * n;
-    for (int e = tid; e < m * n; e += PROJ_THREADS) {
-        const unsigned long long v = red[(e / n) * NV + e % n];
-        if (v) atomicAdd(dst + e, v);
+            for (int b = 0; b < NV; b++) acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], off);
+        if (lane < m)
+#pragma unroll
+            for (int b = 0; b < NV; b++) red32[(warp * m + lane) * NV + b] = red64(acc[b], mp);
+        __syncthreads();
+        const int k_term = *term_counter;
+        unsigned long long *dst = s_raw + (size_t)k_term * m * n;
+        for (int e = tid; e < m * n; e += PROJ_THREADS) {
+            const int aa = e / n, b = e % n;
+            unsigned long long v = 0;
+            for (int w = 0; w < PROJ_THREADS / 32; w++) v += red32[(w * m + aa) * NV + b];
+            if (v) atomicAdd(dst + e, v);
+        }
+    } else {
+        for (int i = tid; i < m * NV; i += PROJ_THREADS) red[i] = 0;
+        __syncthreads();
+        if (slot < per) {
+#pragma unroll
+            for (int b = 0; b < NV; b++)
+                if (b < n && acc[b]) atomicAdd(&red[a * NV + b], acc[b]);
+        }
+        __syncthreads();
+        const int k_term = *term_counter;
+        unsigned long long *dst = s_raw + (size_t)k_term * m * n;
+        for (int e = tid; e < m * n; e += PROJ_THREADS) {
+            const unsigned long long v = red[(e / n) * NV + e % n];
+            if (v) atomicAdd(dst + e, v);
+        }
     }
 }
 

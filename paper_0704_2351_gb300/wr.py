@@ -42,7 +42,8 @@ class wr_timings(ctypes.Structure):
                 ("sigma_ms", ctypes.c_double), ("readout_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("spmm_ms", ctypes.c_double),
                 ("spmm_launches", ctypes.c_int64), ("spmm_bytes", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("sigma_window_ms", ctypes.c_double),
+                ("sigma_local_ms", ctypes.c_double), ("sigma_apply_ms", ctypes.c_double)]
 
 
 class wr_server_cfg(ctypes.Structure):
