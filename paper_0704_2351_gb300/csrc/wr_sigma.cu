@@ -119,53 +119,143 @@ __global__ void __launch_bounds__(WIN_THREADS)
 
 // ---- local M-Basis over the window: one block, bb orders.
 //
-// Shared memory: the window Es (bb x m x q, normal form), the chunk transform
-// Ml ((2 bb + 1) x q x q), Tp (m x q: T[pc[t]][j], normal form), small vectors.
-// Multiplying column c by x moves no data: window column c is read at row
-// i' - sh[c] (sh = shifts so far in the chunk), and Ml column c holds its
-// coefficient s at row base[c] + s, base[c] decreasing by one per shift.
+// The device keeps the basis in fraction-free form, M_g = M diag(S): the
+// elimination of a discrepancy whose columns are scaled by nonzero constants
+// picks the same pivots and yields the same reduced columns up to column
+// scales, so M_g stays a column-scaled copy of the order-by-order basis.  S
+// (per column, product of the scales of all orders) is divided out of P once
+// at the end.
 //
-// Per order, warp 0 eliminates the discrepancy with one column per lane
-// (two for q > 32), right-looking and fraction-free in Montgomery form: when
-// the current column (in (degree, index) order) is nonzero it becomes a pivot
-// and every later column is reduced by it at once.  Each column is reduced by
-// exactly the pivots created before it, so the reduced columns and the
-// transform are the unique ones of the order-by-order rule.  All threads
-// then apply the normalised transform new[j] = old[j] + sum_t Tp[t][j]
-// old[pc[t]] to the rest of the window and to Ml.
+// Warp 0 runs the critical path: per order it eliminates the discrepancy with
+// one column per lane (two for q > 32), right-looking and fraction-free in
+// Montgomery form -- when the current column (in (degree, index) order) is
+// nonzero it becomes a pivot and every later column is reduced by it at once,
+// so each column is reduced by exactly the pivots created before it.  It
+// publishes the order's transform, new[j] = s_j old[j] + sum_t F[t][j]
+// old[pc[t]], and keeps the degree bookkeeping.  The other warps apply the
+// transform: first to window rows i and i+1 (the next discrepancy; warp 0
+// waits for these), then to rows i+2.., to Qtop (coefficient x^k of the last
+// m rows of M) and to the chunk transform Ml.  Named barriers hand the orders
+// over: T_i (transform i published; warp 0 arrives, the others wait) and RR_i
+// (rows i, i+1 done; the others arrive, warp 0 waits).  Phases alternate
+// between two ids per barrier, so a barrier is reused only after its previous
+// phase completed: the arrivals of phase k + 2 are ordered after a wait that
+// needs phase k complete.  There is no spin-wait.  Multiplying column c by x
+// moves no data: window column c is read at row i' - sh[c], and Ml column c
+// holds its coefficient s at row base[c] + s; the other warps use per-order
+// snapshots of sh and base.
 constexpr int LOCAL_THREADS = 1024;
+constexpr int BAR_T0 = 1, BAR_RR0 = 3;  // ids BAR_T0 + (i & 1), BAR_RR0 + (i & 1)
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+    __threadfence_block();
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The transform of one order held in registers by each lane: for its
+// column(s) j, the diagonal dg[j], the coefficients F[t][j] and where the
+// pivot columns of the same row live.  apply() computes new[j] = dg[j] old[j]
+// + sum_t F[t][j] old[pc[t]] for one row whose column j sits at p[0] (and
+// column j + 32 at p[1] when CPL = 2, that is q > 32, one row per warp).
+template <int MM, int CPL, int KLAZY>
+struct RowTransform {
+    uint32_t f[CPL][MM], d[CPL];
+    int src[MM];  // CPL = 1: lane holding pc[t]; CPL = 2: pc[t] itself
+    int np;
+
+    __device__ __forceinline__ void load(const uint32_t *F, const uint32_t *dg, const int *pcs, int np_, int q,
+                                         int W2, int grp, int col, int lane) {
+        np = np_;
+#pragma unroll
+        for (int k = 0; k < CPL; k++) {
+            const int j = CPL == 1 ? col : lane + 32 * k;
+            d[k] = j < q ? dg[j] : 0u;
+#pragma unroll
+            for (int t = 0; t < MM; t++) f[k][t] = (t < np && j < q) ? F[t * q + j] : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < MM; t++) {
+            const int c = t < np ? pcs[t] : 0;
+            src[t] = CPL == 1 ? grp * W2 + c : c;
+        }
+    }
+
+    __device__ __forceinline__ void apply(uint32_t *const (&ptr)[CPL], const ModP &mp) const {
+        uint32_t v[CPL];
+        unsigned long long a[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; k++) {
+            v[k] = ptr[k] ? *ptr[k] : 0u;
+            a[k] = (unsigned long long)d[k] * v[k];
+        }
+#pragma unroll
+        for (int t = 0; t < MM; t++) {
+            if (t < np) {
+                uint32_t oc;
+                if (CPL == 1) {
+                    oc = __shfl_sync(0xffffffffu, v[0], src[t]);
+                } else {
+                    const uint32_t x0 = __shfl_sync(0xffffffffu, v[0], src[t] & 31);
+                    const uint32_t x1 = __shfl_sync(0xffffffffu, v[CPL - 1], src[t] & 31);
+                    oc = src[t] >= 32 ? x1 : x0;
+                }
+#pragma unroll
+                for (int k = 0; k < CPL; k++) a[k] += (unsigned long long)f[k][t] * oc;
+                // at most KLAZY products (plus a reduced residue) between reductions
+                if (MM + 1 > KLAZY && (t + 2) % KLAZY == 0) {
+#pragma unroll
+                    for (int k = 0; k < CPL; k++) a[k] = red64(a[k], mp);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CPL; k++)
+            if (ptr[k]) *ptr[k] = red64(a[k], mp);
+    }
+};
 
 template <int MM, int CPL, int KLAZY>
 __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
     k_local(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
-            uint32_t *__restrict__ qtop, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
-            int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, ModP mp) {
+            uint32_t *__restrict__ qtop_g, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
+            int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, uint32_t *__restrict__ scale_g, ModP mp) {
     extern __shared__ uint32_t sm[];
     const int mq = m * q, qq = q * q;
     const int mlrows = 2 * bb + 1;
+    const int tw = mq + q;                               // transform: F (m x q) then diagonal (q)
     uint32_t *Es = sm;                                   // bb*m*q
     uint32_t *Ml = Es + (size_t)bb * mq;                 // (2bb+1)*q*q
-    uint32_t *Tp = Ml + (size_t)mlrows * qq;             // m*q
-    uint32_t *tmp = Tp + mq;                             // m*q
-    int *deg = (int *)(tmp + mq);                        // q
+    uint32_t *Tb = Ml + (size_t)mlrows * qq;             // 2 * tw (double buffer)
+    uint32_t *qt = Tb + 2 * tw;                          // m*q
+    int *deg = (int *)(qt + mq);                         // q
     int *degl = deg + q;                                 // q
     int *sh = degl + q;                                  // q
     int *base = sh + q;                                  // q
-    int *pc = base + q;                                  // m
-    int *npiv = pc + m;                                  // 1
+    int *snap = base + q;                                // 2 * snapw: sh, base, isp, pc, np, dl
+    const int snapw = 3 * q + m + 2;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
     const int E = bb * mq;
+    (void)n;
 
+    for (int x = tid; x < mq; x += nth) qt[x] = qtop_g[x];
+    __syncthreads();
     for (int x = tid; x < E; x += nth) {
         unsigned long long v = 0;
-        for (int b = 0; b < nparts; b++) v += Epart[(size_t)b * E + x];
+        int b = 0;
+        for (; b + 4 <= nparts; b += 4)
+            v += (unsigned long long)Epart[(size_t)b * E + x] + Epart[(size_t)(b + 1) * E + x] +
+                 Epart[(size_t)(b + 2) * E + x] + Epart[(size_t)(b + 3) * E + x];
+        for (; b < nparts; b++) v += Epart[(size_t)b * E + x];
         uint32_t e = red64(v, mp);
-        if (x < mq) e = subm(e, qtop[x], mp);
+        if (x < mq) e = subm(e, qt[x], mp);
         Es[x] = e;
     }
     for (int x = tid; x < mlrows * qq; x += nth) {
-        const int s2 = x / qq, rem = x % qq;
+        const int s2 = x / qq, rem = x - s2 * qq;
         Ml[x] = (s2 == bb && rem / q == rem % q) ? 1u : 0u;  // logical coefficient 0 at row base = bb
     }
     for (int c = tid; c < q; c += nth) {
@@ -180,9 +270,16 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
     const int rpw = 32 / W2;
     const int grp = lane / W2, col = lane % W2;
 
-    for (int i = 0; i < bb; i++) {
-        if (warp == 0) {
-            // column j = lane + 32 k of this lane
+    if (warp == 0) {
+        uint32_t scum[CPL];  // cumulative column scales over the chunk (Montgomery form)
+#pragma unroll
+        for (int k = 0; k < CPL; k++) scum[k] = mp.r1;
+        for (int i = 0; i < bb; i++) {
+            uint32_t *F = Tb + (i & 1) * tw;
+            uint32_t *dg = F + mq;
+            int *sn = snap + (i & 1) * snapw;
+            int *s_sh = sn, *s_base = sn + q, *s_isp = sn + 2 * q, *s_pc = sn + 3 * q;
+            // ---- elimination of order i
             uint32_t d[CPL][MM], tp[CPL][MM], sc[CPL];
             int rk[CPL];
 #pragma unroll
@@ -196,6 +293,9 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
                     for (int c2 = 0; c2 < q; c2++)
                         r0 += (deg[c2] < deg[j] || (deg[c2] == deg[j] && c2 < j)) ? 1 : 0;
                     rk[k] = r0;
+                    s_isp[j] = 0;
+                    s_sh[j] = sh[j];
+                    s_base[j] = base[j];
                 }
                 const uint32_t *er = Es + (size_t)(i - (v ? sh[j] : 0)) * mq + (v ? j : 0);
 #pragma unroll
@@ -206,14 +306,12 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
             }
             int np = 0;
             for (int step = 0; step < q; step++) {
-                // the current column: the one of rank `step`
                 int mine = -1;
 #pragma unroll
                 for (int k = 0; k < CPL; k++)
                     if (rk[k] == step) mine = k;
                 const unsigned who = __ballot_sync(0xffffffffu, mine >= 0);
                 const int src = __ffs(who) - 1;
-                // its first nonzero row (or -1)
                 int fr = -1;
                 uint32_t sc_cur = 0;
                 if (mine >= 0) {
@@ -227,10 +325,9 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
                         }
                 }
                 fr = __shfl_sync(0xffffffffu, fr, src);
-                if (fr < 0) continue;  // zero column: no pivot
+                if (fr < 0) continue;
                 const int jcur = __shfl_sync(0xffffffffu, lane + 32 * (mine >= 0 ? mine : 0), src);
                 sc_cur = __shfl_sync(0xffffffffu, sc_cur, src);
-                // broadcast the pivot column and its transform coefficients
                 uint32_t pv[MM], pt[MM];
 #pragma unroll
                 for (int a2 = 0; a2 < MM; a2++) {
@@ -245,7 +342,8 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
 #pragma unroll
                 for (int a2 = 0; a2 < MM; a2++)
                     if (a2 == fr) dc = pv[a2];
-                // reduce every later column: col <- dc col - dj pivot (fraction-free)
+                // col <- dc col - dj pivot: one Montgomery reduction of
+                // dc*x + (p - dj)*y < 2 p^2 < p 2^32 per entry
 #pragma unroll
                 for (int k = 0; k < CPL; k++) {
                     if (rk[k] > step && rk[k] < (1 << 20)) {
@@ -254,122 +352,199 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
                         for (int a2 = 0; a2 < MM; a2++)
                             if (a2 == fr) dj = d[k][a2];
                         if (dj != 0) {
+                            const uint64_t ndj = mp.p - dj;
 #pragma unroll
                             for (int a2 = 0; a2 < MM; a2++)
-                                d[k][a2] = subm(mont_mul(dc, d[k][a2], mp), mont_mul(dj, pv[a2], mp), mp);
+                                d[k][a2] = mont_redc((uint64_t)dc * d[k][a2] + ndj * pv[a2], mp);
 #pragma unroll
                             for (int t = 0; t < MM; t++) {
-                                if (t < np) tp[k][t] = subm(mont_mul(dc, tp[k][t], mp), mont_mul(dj, pt[t], mp), mp);
-                                else if (t == np) tp[k][t] = subm(0u, mont_mul(dj, sc_cur, mp), mp);
+                                if (t < np) tp[k][t] = mont_redc((uint64_t)dc * tp[k][t] + ndj * pt[t], mp);
+                                else if (t == np) tp[k][t] = mont_redc(ndj * sc_cur, mp);
                             }
                             sc[k] = mont_mul(sc[k], dc, mp);
                         }
                     }
                 }
-                if (lane == 0) pc[np] = jcur;
+                if (lane == 0) {
+                    s_pc[np] = jcur;
+                    s_isp[jcur] = 1;
+                }
                 np++;
             }
-            // normalise: Tp[t][j] = tp_j[t] / s_j (normal form), and the local
-            // degree bounds of the columns that absorbed pivot columns
             __syncwarp();
+            // publish the transform (normal form) and the local degree bounds
+            int dln[CPL];
 #pragma unroll
             for (int k = 0; k < CPL; k++) {
                 const int j = lane + 32 * k;
+                dln[k] = 0;
                 if (j < q) {
-                    const uint32_t sinv = from_mont(mont_inv(sc[k], mp), mp);
                     int dl = degl[j];
 #pragma unroll
                     for (int t = 0; t < MM; t++)
                         if (t < np) {
-                            const uint32_t v = mont_mul(tp[k][t], sinv, mp);
-                            Tp[t * q + j] = v;
-                            if (v) dl = max(dl, degl[pc[t]]);
+                            const uint32_t v = from_mont(tp[k][t], mp);
+                            F[t * q + j] = v;
+                            if (v) dl = max(dl, degl[s_pc[t]]);
                         }
-                    tmp[j] = (uint32_t)dl;
+                    dg[j] = from_mont(sc[k], mp);
+                    scum[k] = mont_mul(scum[k], sc[k], mp);
+                    dln[k] = dl;
                 }
+            }
+            int dmx = 0;
+#pragma unroll
+            for (int k = 0; k < CPL; k++) dmx = max(dmx, dln[k]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) dmx = max(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
+            if (lane == 0) {
+                sn[3 * q + m] = np;
+                sn[3 * q + m + 1] = dmx;
             }
             __syncwarp();
-            for (int j = lane; j < q; j += 32) degl[j] = (int)tmp[j];
-            if (lane == 0) *npiv = np;
+            named_arrive(BAR_T0 + (i & 1), nth);
+            // ---- bookkeeping of order i: local degrees, pivots times x
+#pragma unroll
+            for (int k = 0; k < CPL; k++)
+                if (lane + 32 * k < q) degl[lane + 32 * k] = dln[k];
+            __syncwarp();
+            for (int t = lane; t < np; t += 32) {
+                const int c = s_pc[t];
+                deg[c] += 1;
+                degl[c] += 1;
+                sh[c] += 1;
+                base[c] -= 1;
+            }
+            __syncwarp();
+            // ---- the next discrepancy (rows i, i+1) must be done
+            named_sync(BAR_RR0 + (i & 1), nth);
         }
-        __syncthreads();
-        const int np = *npiv;
-        // ---- apply the transform to window orders i..bb-1 and to Ml
-        {
-            const int erows = (bb - i) * m;
-            int dl = 0;
-            for (int c = 0; c < q; c++) dl = max(dl, degl[c]);
-            const int nrows = erows + (dl + 1) * q;
-            for (int row0 = warp * rpw; row0 < nrows; row0 += nwarps * rpw) {
-                const int row = row0 + grp;
-                const bool rowok = row < nrows;
-                // each lane: column j = col (q <= 32) or lane, lane + 32 (q > 32)
-                uint32_t *p0 = nullptr, *p1 = nullptr;
-                uint32_t v0 = 0, v1 = 0;
-                const int j0 = q <= 32 ? col : lane;
-                const int j1 = q <= 32 ? -1 : lane + 32;
-                if (rowok) {
-                    if (row < erows) {
-                        const int ip = i + row / m, a2 = row % m;
-                        if (j0 < q) p0 = Es + ((size_t)(ip - sh[j0]) * m + a2) * q + j0;
-                        if (j1 >= 0 && j1 < q) p1 = Es + ((size_t)(ip - sh[j1]) * m + a2) * q + j1;
-                    } else {
-                        const int s2 = (row - erows) / q, x = (row - erows) % q;
-                        if (j0 < q) p0 = Ml + ((size_t)(base[j0] + s2) * q + x) * q + j0;
-                        if (j1 >= 0 && j1 < q) p1 = Ml + ((size_t)(base[j1] + s2) * q + x) * q + j1;
+        // cumulative scales of this chunk into the running product
+#pragma unroll
+        for (int k = 0; k < CPL; k++) {
+            const int j = lane + 32 * k;
+            if (j < q) scale_g[j] = mont_mul(scale_g[j], scum[k], mp);
+        }
+    } else {
+        // warps on warp 0's SM sub-partition (w % 4 == 0) take no rows, so
+        // the elimination keeps its issue slots
+        const bool worker = (warp & 3) != 0;
+        const int ow = warp - 1 - (warp >> 2), nw = nwarps - nwarps / 4;
+        const int NG = nw * rpw;        // row groups over all worker warps
+        const int gg = ow * rpw + grp;  // this lane group's first row
+        int jc[CPL];
+        bool cok[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; k++) {
+            jc[k] = CPL == 1 ? col : lane + 32 * k;
+            cok[k] = jc[k] < q;
+        }
+        RowTransform<MM, CPL, KLAZY> tr;
+        for (int i = 0; i < bb; i++) {
+            named_sync(BAR_T0 + (i & 1), nth);
+            const uint32_t *F = Tb + (i & 1) * tw;
+            const uint32_t *dg = F + mq;
+            const int *sn = snap + (i & 1) * snapw;
+            const int *s_sh = sn, *s_base = sn + q, *s_isp = sn + 2 * q, *s_pc = sn + 3 * q;
+            const int np = sn[3 * q + m], dl = sn[3 * q + m + 1];
+            if (worker) tr.load(F, dg, s_pc, np, q, W2, grp, col, lane);
+            int shc[CPL], bsc[CPL];
+#pragma unroll
+            for (int k = 0; k < CPL; k++) {
+                shc[k] = cok[k] ? s_sh[jc[k]] : 0;
+                bsc[k] = cok[k] ? s_base[jc[k]] : 0;
+            }
+            // window row (ip, a2) of column j sits at Es[((ip - sh[j]) m + a2) q + j]
+            auto es = [&](bool ok, int ip, int a2, uint32_t *(&ptr)[CPL]) {
+#pragma unroll
+                for (int k = 0; k < CPL; k++)
+                    ptr[k] = (ok && cok[k]) ? Es + ((size_t)(ip - shc[k]) * m + a2) * q + jc[k] : nullptr;
+            };
+            // rows i and i+1 first (the next discrepancy)
+            if (worker) {
+                const int r1 = (i + 1 < bb ? 2 : 1) * m;
+                for (int row0 = ow * rpw; row0 < r1; row0 += NG) {
+                    const int row = row0 + grp;
+                    uint32_t *ptr[CPL];
+                    es(row < r1, i + (row >= m ? 1 : 0), row - (row >= m ? m : 0), ptr);
+                    tr.apply(ptr, mp);
+                }
+            }
+            named_arrive(BAR_RR0 + (i & 1), nth);
+            if (worker && np > 0) {
+                // window orders i+2 .. bb-1: rows gg, gg + NG, ... walked incrementally
+                const int wr = (bb - i - 2) > 0 ? (bb - i - 2) * m : 0;
+                {
+                    const int stepi = NG / m, stepa = NG - (NG / m) * m;
+                    int ip = i + 2 + gg / m, a2 = gg - (gg / m) * m;
+                    for (int row0 = ow * rpw; row0 < wr; row0 += NG) {
+                        uint32_t *ptr[CPL];
+                        es(row0 + grp < wr, ip, a2, ptr);
+                        tr.apply(ptr, mp);
+                        ip += stepi;
+                        a2 += stepa;
+                        if (a2 >= m) { a2 -= m; ip++; }
                     }
                 }
-                if (p0) v0 = *p0;
-                if (p1) v1 = *p1;
-                unsigned long long a0 = v0, a1 = v1;
-                int cnt = 0;
-                for (int t = 0; t < np; t++) {
-                    const int c = pc[t];
-                    uint32_t oc;
-                    if (q <= 32) oc = __shfl_sync(0xffffffffu, v0, grp * W2 + c);
-                    else oc = c < 32 ? __shfl_sync(0xffffffffu, v0, c) : __shfl_sync(0xffffffffu, v1, c - 32);
-                    if (p0) a0 += (unsigned long long)Tp[t * q + j0] * oc;
-                    if (p1) a1 += (unsigned long long)Tp[t * q + j1] * oc;
-                    if (++cnt == KLAZY) { a0 = red64(a0, mp); a1 = red64(a1, mp); cnt = 0; }
+                // Qtop rows; the next Qtop keeps the pivot columns of Qtop T
+                for (int row0 = ow * rpw; row0 < m; row0 += NG) {
+                    const int a2 = row0 + grp;
+                    uint32_t *ptr[CPL];
+#pragma unroll
+                    for (int k = 0; k < CPL; k++) ptr[k] = (a2 < m && cok[k]) ? qt + a2 * q + jc[k] : nullptr;
+                    tr.apply(ptr, mp);
+#pragma unroll
+                    for (int k = 0; k < CPL; k++)
+                        if (ptr[k] && !s_isp[jc[k]]) *ptr[k] = 0;
                 }
-                if (p0) *p0 = red64(a0, mp);
-                if (p1) *p1 = red64(a1, mp);
+                // Ml coefficients 0..dl: rows (s2, x) walked incrementally
+                {
+                    const int mrows = (dl + 1) * q;
+                    const int steps2 = NG / q, stepx = NG - (NG / q) * q;
+                    int s2 = gg / q, x = gg - (gg / q) * q;
+                    for (int row0 = ow * rpw; row0 < mrows; row0 += NG) {
+                        const bool ok = row0 + grp < mrows;
+                        uint32_t *ptr[CPL];
+#pragma unroll
+                        for (int k = 0; k < CPL; k++)
+                            ptr[k] = (ok && cok[k]) ? Ml + ((size_t)(bsc[k] + s2) * q + x) * q + jc[k] : nullptr;
+                        tr.apply(ptr, mp);
+                        s2 += steps2;
+                        x += stepx;
+                        if (x >= q) { x -= q; s2++; }
+                    }
+                }
             }
+            if (np == 0)  // no pivot: the next Qtop is zero
+                for (int x = tid - 32; x < mq; x += nth - 32) qt[x] = 0;
         }
-        __syncthreads();
-        // ---- multiply the pivot columns by x
-        for (int t = tid; t < np; t += nth) {
-            const int c = pc[t];
-            deg[c] += 1;
-            degl[c] += 1;
-            sh[c] += 1;
-            base[c] -= 1;
-        }
-        __syncthreads();
-    }
-    // ---- Qtop <- Qtop * Ml[bb]; write back Ml in logical layout
-    for (int x = tid; x < mq; x += nth) {
-        const int aa = x / q, c = x % q;
-        unsigned long long acc = 0;
-        for (int y = 0; y < q; y++)
-            acc = red64(acc + (unsigned long long)qtop[aa * q + y] * Ml[((size_t)(base[c] + bb) * q + y) * q + c], mp);
-        tmp[x] = (uint32_t)acc;
     }
     __syncthreads();
-    for (int x = tid; x < mq; x += nth) qtop[x] = tmp[x];
     for (int x = tid; x < (bb + 1) * qq; x += nth) {
         const int s2 = x / qq, c = x % q, y = (x / q) % q;
         Ml_g[x] = Ml[((size_t)(base[c] + s2) * q + y) * q + c];
     }
+    for (int x = tid; x < mq; x += nth) qtop_g[x] = qt[x];
     for (int c = tid; c < q; c += nth) {
         deg_g[c] = deg[c];
         degl_g[c] = degl[c];
     }
     if (tid == 0) {
-        int d = 0;
-        for (int c = 0; c < q; c++) d = max(d, deg[c]);
-        *dmax_g = d;
+        int dmx = 0;
+        for (int c = 0; c < q; c++) dmx = max(dmx, deg[c]);
+        *dmax_g = dmx;
     }
+}
+
+// P[t][r][c] /= S[c] (S in Montgomery form), t <= D
+__global__ void k_unscale(uint32_t *__restrict__ P, int n, int q, int64_t D, const uint32_t *__restrict__ scale_g,
+                          ModP mp) {
+    __shared__ uint32_t inv[64];
+    for (int c = threadIdx.x; c < q; c += blockDim.x) inv[c] = from_mont(mont_inv(scale_g[c], mp), mp);
+    __syncthreads();
+    const int64_t nq = (int64_t)n * q;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (D + 1) * nq; x += (int64_t)gridDim.x * blockDim.x)
+        P[x] = mulm(P[x], inv[x % q], mp);
 }
 
 // ---- apply: P_new[t][r][c] = sum_{s <= degl[c]} sum_x P[t-s][r][x] Ml[s][x][c]
@@ -561,11 +736,10 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     cudaStream_t s = ctx->stream;
     const size_t nq = (size_t)n * q;
     WR_CUDA(cudaMemsetAsync(d_P, 0, sizeof(uint32_t) * (Dcap + 1) * nq, s));
-    DevBuf P2, qtop, Ml, degl, dmax, Epart;
+    DevBuf P2, qtop, dmax, Epart, Ml, degl, scale;
     WR_TRY(dev_alloc(ctx, P2, sizeof(uint32_t) * (Dcap + 1) * nq));
     WR_CUDA(cudaMemsetAsync(P2.ptr, 0, P2.bytes, s));
     WR_TRY(dev_alloc(ctx, qtop, sizeof(uint32_t) * m * q));
-    WR_TRY(dev_alloc(ctx, degl, sizeof(int32_t) * q));
     WR_TRY(dev_alloc(ctx, dmax, sizeof(int)));
     k_init_basis<<<1, 256, 0, s>>>(d_P, n, q, d_deg, qtop.as<uint32_t>(), m, dmax.as<int>());
     WR_LAUNCHED(ctx);
@@ -573,8 +747,8 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     // chunk size b and tiles: every kernel's shared memory must fit
     const size_t budget = std::min<size_t>(ctx->smem_optin, 227 * 1024) - 1024;
     auto local_bytes = [&](int b) {
-        return sizeof(uint32_t) * ((size_t)b * m * q + (size_t)(2 * b + 1) * q * q + 2 * m * q) +
-               sizeof(int) * (4 * q + m + 1);
+        return sizeof(uint32_t) * ((size_t)b * m * q + (size_t)(2 * b + 1) * q * q + 3 * (size_t)m * q + 2 * q) +
+               sizeof(int) * (4 * q + 2 * (3 * q + m + 2));
     };
     auto window_bytes = [&](int TT, int b) {
         const int nib = (b + WIN_IB - 1) / WIN_IB;
@@ -592,18 +766,25 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         TA = 64;
     }
     const int nparts_max = std::max(1, 2 * ctx->num_sms);
-    WR_TRY(dev_alloc(ctx, Ml, sizeof(uint32_t) * (bmax + 1) * q * q));
     WR_TRY(dev_alloc(ctx, Epart, sizeof(uint32_t) * (size_t)nparts_max * bmax * m * q));
+    WR_TRY(dev_alloc(ctx, Ml, sizeof(uint32_t) * (size_t)(bmax + 1) * q * q));
+    WR_TRY(dev_alloc(ctx, degl, sizeof(int32_t) * q));
+    WR_TRY(dev_alloc(ctx, scale, sizeof(uint32_t) * q));
+    {
+        std::vector<uint32_t> one(q, mp.r1);  // Montgomery form of 1
+        WR_CUDA(cudaMemcpyAsync(scale.ptr, one.data(), sizeof(uint32_t) * q, cudaMemcpyHostToDevice, s));
+        WR_CUDA(cudaStreamSynchronize(s));
+    }
     const bool lazy16 = mp.lazy >= 16;
     auto *kwin = lazy16 ? k_window<16> : k_window<4>;
-    using LocalFn = void (*)(int, int, int, int, int, const uint32_t *, uint32_t *, int32_t *, uint32_t *,
-                             int32_t *, int *, ModP);
+    auto *kapp = lazy16 ? k_apply<16> : k_apply<4>;
+    using LocalFn = void (*)(int, int, int, int, int, const uint32_t *, uint32_t *, int32_t *, uint32_t *, int32_t *,
+                             int *, uint32_t *, ModP);
     LocalFn kloc;
     if (m <= 8)
         kloc = q <= 32 ? (lazy16 ? k_local<8, 1, 16> : k_local<8, 1, 4>) : (lazy16 ? k_local<8, 2, 16> : k_local<8, 2, 4>);
     else
         kloc = q <= 32 ? (lazy16 ? k_local<32, 1, 16> : k_local<32, 1, 4>) : (lazy16 ? k_local<32, 2, 16> : k_local<32, 2, 4>);
-    auto *kapp = lazy16 ? k_apply<16> : k_apply<4>;
     WR_CUDA(cudaFuncSetAttribute(kwin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     WR_CUDA(cudaFuncSetAttribute(kloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     WR_CUDA(cudaFuncSetAttribute(kapp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
@@ -628,8 +809,9 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
                                                                 dmax.as<int>(), Epart.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
         if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
-        kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(m, n, q, bb, nparts, Epart.as<uint32_t>(), qtop.as<uint32_t>(),
-                                                        d_deg, Ml.as<uint32_t>(), degl.as<int32_t>(), dmax.as<int>(), mp);
+        kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(
+            m, n, q, bb, nparts, Epart.as<uint32_t>(), qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
+            degl.as<int32_t>(), dmax.as<int>(), scale.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
         if (prof) WR_CUDA(cudaEventRecord(pe[2], s));
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
@@ -661,6 +843,10 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     }
     if (Pcur != d_P)
         WR_CUDA(cudaMemcpyAsync(d_P, Pcur, sizeof(uint32_t) * (Dbound + 1) * nq, cudaMemcpyDeviceToDevice, s));
+    // divide the cumulative column scales out of P
+    k_unscale<<<(unsigned)std::min<int64_t>(((Dbound + 1) * nq + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, s>>>(
+        d_P, n, q, Dbound, scale.as<uint32_t>(), mp);
+    WR_LAUNCHED(ctx);
     WR_CUDA(cudaStreamSynchronize(s));
     return WR_OK;
 }
