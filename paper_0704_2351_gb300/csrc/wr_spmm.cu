@@ -211,16 +211,22 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
     y[(size_t)r * nv + b] = mulm(scale[r], red_s64((int64_t)s, mp), mp);
 }
 
-// S_raw[k] += Xh^T T (m x n), k read from the term counter.  m threads per
-// row (one per row of the block Xh^T), NV register accumulators each; rows are
-// streamed over the grid.  Partials are reduced mod p before the exact uint64
-// atomics, so their sum cannot overflow and does not depend on the order.
+// S_raw[k] += Xh^T T (m x n), k = tmul * (term counter) + toff, skipped
+// unless 0 <= k < L.  m threads per row (one per row of the block Xh^T), NV
+// register accumulators each; rows are streamed over the grid.  Partials are
+// reduced mod p before the exact uint64 atomics, so their sum cannot overflow
+// and does not depend on the order.
+// GRAM: the weighted Gram matrix sum_r wt[r] T[r]^T T[r] (m = n) instead; the
+// symmetric projection X = Y turns every term into one (Section 2.2).
 constexpr int PROJ_THREADS = 256;
 
-template <int NV, int KLAZY>
+template <int NV, int KLAZY, bool GRAM>
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project(int64_t N, int m, int n, const uint32_t *__restrict__ xh, const uint32_t *__restrict__ t,
-              unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, ModP mp) {
+              unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, int tmul, int toff,
+              int64_t L, ModP mp) {
+    const int64_t k_term = (int64_t)tmul * *term_counter + toff;
+    if (k_term < 0 || k_term >= L) return;  // the same for every thread
     // red32[w][a][b]: per-warp sums reduced mod p (m divides 32); red: one
     // shared row of atomically added sums (other m)
     __shared__ uint32_t red32[(PROJ_THREADS / 32) * 32 * NV];
@@ -235,7 +241,8 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     if (slot < per) {
         int cnt = 0;
         for (int64_t r = (int64_t)blockIdx.x * per + slot; r < N; r += (int64_t)gridDim.x * per) {
-            const unsigned long long xv = __ldg(xh + r * m + a);
+            const unsigned long long xv =
+                GRAM ? mulm(__ldg(xh + r), __ldg(t + r * NV + a), mp) : __ldg(xh + r * m + a);
             uint32_t tv[NV];
             ldv<NV>(t + r * NV, tv);
 #pragma unroll
@@ -259,7 +266,6 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
             for (int b = 0; b < NV; b++) red32[(warp * m + lane) * NV + b] = red64(acc[b], mp);
         __syncthreads();
-        const int k_term = *term_counter;
         unsigned long long *dst = s_raw + (size_t)k_term * m * n;
         for (int e = tid; e < m * n; e += PROJ_THREADS) {
             const int aa = e / n, b = e % n;
@@ -276,7 +282,6 @@ __global__ void __launch_bounds__(PROJ_THREADS)
                 if (b < n && acc[b]) atomicAdd(&red[a * NV + b], acc[b]);
         }
         __syncthreads();
-        const int k_term = *term_counter;
         unsigned long long *dst = s_raw + (size_t)k_term * m * n;
         for (int e = tid; e < m * n; e += PROJ_THREADS) {
             const unsigned long long v = red[(e / n) * NV + e % n];
@@ -298,7 +303,9 @@ __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t
     if (i < len) out[i] = (uint32_t)(1 + stream_hash(seed, tag, (uint64_t)i) % (uint64_t)(p - 1));
 }
 
-// T0 = D1 Y (padded to nv columns with zeros), Xh = D1^{-1} X, d1sq = D1^2.
+// T0 = D1 Y (padded to nv columns with zeros), d1sq = D1^2, and
+// Xh = D1^{-1} X (generic projection) or the Gram weights D1^{-2} (symmetric
+// projection X = Y: S_2k = V_k^T V_k with T_k = D1 V_k).
 __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, int symmetric,
                           const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
                           uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, ModP mp) {
@@ -312,12 +319,21 @@ __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, int sy
         if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, (uint64_t)i * n + b) % mp.p);
         t0[i * nv + b] = mulm(d, yv, mp);
     }
+    if (symmetric) {
+        xh[i] = mulm(dinv, dinv, mp);
+        return;
+    }
     for (int a = 0; a < m; a++) {
-        uint64_t tag = symmetric ? TAG_Y : TAG_X;
-        uint64_t width = symmetric ? (uint64_t)n : (uint64_t)m;
-        uint32_t xv = (uint32_t)(stream_hash(seed, tag, (uint64_t)i * width + a) % mp.p);
+        uint32_t xv = (uint32_t)(stream_hash(seed, TAG_X, (uint64_t)i * m + a) % mp.p);
         xh[i * m + a] = mulm(dinv, xv, mp);
     }
+}
+
+// out = d^{-1}, elementwise (the Gram weights D2^{-1} of the odd terms of
+// the symmetric projection: S_2k+1 = W^T D2^{-1} W with W = D2 A D1 V_k)
+__global__ void k_inv_diag(int64_t len, const uint32_t *__restrict__ d, uint32_t *__restrict__ out, ModP mp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = invm(d[i], mp);
 }
 
 // out (N x nv, padded) = D1 in (N x width)
@@ -375,30 +391,44 @@ wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x,
     }
 }
 
-template <int NV>
+template <int NV, bool GRAM>
 void launch_project_t(wr_ctx *ctx, unsigned grid, int64_t N, int m, int n, const uint32_t *xh,
-                      const uint32_t *t, unsigned long long *s_raw, const int *term_counter, const ModP &mp) {
+                      const uint32_t *t, unsigned long long *s_raw, const int *term_counter, int tmul, int toff,
+                      int64_t L, const ModP &mp) {
     if (mp.lazy >= 16)
-        k_project<NV, 16><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, mp);
+        k_project<NV, 16, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
+                                                                         toff, L, mp);
     else
-        k_project<NV, 4><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, mp);
+        k_project<NV, 4, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
+                                                                        toff, L, mp);
 }
 
+// gram = false: S_raw[k] += xh^T t (xh: N x m).  gram = true: S_raw[k] +=
+// sum_r xh[r] t[r]^T t[r] (xh: N weights, m = n).  k = tmul * counter + toff.
 wr_status launch_project(wr_ctx *ctx, int64_t N, int m, int n, int nv, const uint32_t *xh,
                          const uint32_t *t, unsigned long long *s_raw, const int *term_counter,
-                         const ModP &mp) {
+                         const ModP &mp, bool gram = false, int tmul = 1, int toff = 0,
+                         int64_t L = INT64_MAX) {
     const int per = PROJ_THREADS / m;
     const int64_t need = std::max<int64_t>((N + per - 1) / per, 1);
     const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ctx->num_sms * 4);
+#define WR_PROJ_CASE(NVV)                                                                                    \
+    case NVV:                                                                                                \
+        if (gram)                                                                                            \
+            launch_project_t<NVV, true>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, tmul, toff, L, mp);  \
+        else                                                                                                 \
+            launch_project_t<NVV, false>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, tmul, toff, L, mp); \
+        break;
     switch (nv) {
-        case 1: launch_project_t<1>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
-        case 2: launch_project_t<2>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
-        case 4: launch_project_t<4>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
-        case 8: launch_project_t<8>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
-        case 16: launch_project_t<16>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
-        case 32: launch_project_t<32>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, mp); break;
+        WR_PROJ_CASE(1)
+        WR_PROJ_CASE(2)
+        WR_PROJ_CASE(4)
+        WR_PROJ_CASE(8)
+        WR_PROJ_CASE(16)
+        WR_PROJ_CASE(32)
         default: return fail(WR_EINVAL, "unsupported padded block width");
     }
+#undef WR_PROJ_CASE
     WR_LAUNCHED(ctx);
     return WR_OK;
 }
@@ -412,7 +442,7 @@ struct SeqState {
     ModP mp;
     const Sell *first = nullptr;   // pass 1 layout (output in the other space)
     const Sell *second = nullptr;  // pass 2 layout (output in N-space)
-    DevBuf T, Wb, D1, D2, d1sq, xh, acc1, acc2, s_raw, counter;
+    DevBuf T, Wb, D1, D2, d1sq, xh, w2, acc1, acc2, s_raw, counter;
 };
 
 static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r, SeqState &st,
@@ -449,11 +479,27 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
                                                       st.xh.as<uint32_t>(), st.d1sq.as<uint32_t>(), st.mp);
         WR_LAUNCHED(ctx);
     }
+    if (want_projection && r.symmetric && r.M > 0) {
+        WR_TRY(dev_alloc(ctx, st.w2, sizeof(uint32_t) * r.M));
+        k_inv_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.M, st.D2.as<uint32_t>(), st.w2.as<uint32_t>(), st.mp);
+        WR_LAUNCHED(ctx);
+    }
     return WR_OK;
 }
 
-// One iteration: T <- D1^2 A^T D2 A T (or the rows-side analogue), then the
-// projection of the new T into S_raw[counter].
+// Terms produced by k black-box applications: one each (generic projection),
+// two each with the symmetric projection, where Ã = D1 A^T D2 A D1 is
+// symmetric and V_k = Ã^k Y gives S_2k = V_k^T V_k and
+// S_2k+1 = (A D1 V_k)^T D2 (A D1 V_k).
+static int64_t seq_applications(const Resolved &r, int64_t L) {
+    const int64_t terms = std::max<int64_t>(L - 1, 0);
+    return r.symmetric ? (terms + 1) / 2 : terms;
+}
+
+// One iteration: W = D2 A T, T <- D1^2 A^T W (or the rows-side analogue),
+// then the projections: the new T into S_raw[counter] (generic), or W and the
+// new T into S_raw[2 counter - 1] and S_raw[2 counter] (symmetric; terms past
+// L - 1 are skipped).
 static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
     const int nv = st.r.nv;
     SellView f = view(*st.first), sc = view(*st.second);
@@ -464,8 +510,18 @@ static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
     WR_TRY(launch_spmm(ctx, nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.d1sq.as<uint32_t>(),
                        st.acc2.as<unsigned long long>(), st.mp, nullptr));
     if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
-    WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
-                          st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp));
+    if (st.r.symmetric) {
+        WR_TRY(launch_project(ctx, st.r.M, st.r.m, st.r.n, nv, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(),
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, -1,
+                              st.r.L));
+        WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, 0,
+                              st.r.L));
+    } else {
+        WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, false, 1, 0,
+                              st.r.L));
+    }
     return WR_OK;
 }
 
@@ -493,12 +549,13 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
     WR_CUDA(cudaMemsetAsync(st.s_raw.ptr, 0, st.s_raw.bytes, s));
     if (L > 0)
         WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
-                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp));
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.symmetric,
+                              r.symmetric ? 2 : 1, 0, L));
     WR_CUDA(cudaEventRecord(e1, s));
 
     // profiling: every PROF_EVERY-th group of iterations is launched eagerly
     // with CUDA events around the two SpMM passes
-    const int64_t iters = std::max<int64_t>(L - 1, 0);
+    const int64_t iters = seq_applications(r, L);
     const int64_t G = 64;
     const int PROF_EVERY = 8;
     std::vector<cudaEvent_t> pev;

@@ -151,6 +151,36 @@ def test_sequence_sides_and_symmetric(wr, ctx, side):
             assert all(np.array_equal(S[i], S[i].T) for i in range(len(S)))
 
 
+@pytest.mark.parametrize("n,L,side", [(1, 41, 0), (1, 40, 1), (8, 97, 0), (8, 96, 1), (32, 33, 0), (4, 1, 0),
+                                      (4, 2, 1), (4, 3, 0)])
+@pytest.mark.parametrize("p", [65521, 2147483629])
+def test_sequence_symmetric_two_terms_per_application(wr, ctx, n, L, side, p):
+    """X = Y: the GPU takes S_2k = V_k^T V_k and S_2k+1 = (A D1 V_k)^T D2 (A D1 V_k)
+    from one application of A~ per two terms; the oracle applies A~ once per
+    term.  Odd and even L (the last application's second term is dropped when
+    it would be S_L), L = 1 and 2, and both sides."""
+    A = heavy_matrix(640, 590, seed=n * 7 + L, heavy=2, heavy_len=350)
+    st = oracle.Setup(A, p, n, n, seed=40 + n, side=side, symmetric=True)
+    S_ref = oracle.sequence(A, st, L)
+    S = gpu_sequence(wr, ctx, A, p, n, n, 40 + n, L, side=side, symmetric=True)
+    assert np.array_equal(S, S_ref)
+
+
+@pytest.mark.parametrize("m", [1, 4, 8])
+def test_rank_planted_symmetric(wr, ctx, m):
+    p = 1073741789
+    for t in range(3):
+        rng = np.random.default_rng(t * 17 + m)
+        R, C = int(rng.integers(60, 500)), int(rng.integers(60, 500))
+        r = int(rng.integers(1, min(R, C)))
+        A = synth.planted_sparse(R, C, r, row_len=int(rng.integers(3, 9)), seed=t + 300 * m)
+        ref = oracle.rank_wiedemann(A, p, m, m, seed=t, symmetric=True)
+        g = gpu_rank(wr, ctx, A, p, m, m, t, want=3, symmetric=True)
+        assert g["rank"] == ref["rank"] == r
+        assert np.array_equal(g["S"], ref["S"])
+        assert np.array_equal(g["F"], ref["F"])
+
+
 # ------------------------------------------------------------------ sigma-basis (A8)
 
 def gpu_sigma(wr, ctx, S, p):
