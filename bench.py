@@ -7,9 +7,13 @@ readout.  The workload is the 200,000 x 180,000 power-law matrix of planted
 rank 170,000, block 8 x 8, p = 1073741789 (L = 45,002 terms).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wr|reference]
+                    [--projection generic|symmetric]
 
 One JSON line on rank 0.  value = SpMM nnz*vec processed per second over the
-whole step (2 passes x nnz x n per term); ms_per_step = time to rank.
+whole step (2 passes x nnz x n per black-box application); ms_per_step = time
+to rank.  The generic projection (independent X) applies the black box L - 1
+times; the symmetric one (X = Y) takes two terms per application, so it
+applies it ceil((L - 1) / 2) times and its value counts only those.
 --impl reference times the CPU oracle on the host cores on a bounded sample
 of the same workload (first terms of the sequence).
 """
@@ -41,8 +45,12 @@ def workload(rank: int):
         "170000; block Wiedemann m=n=8 mod p=1073741789, L=45002" % A.nnz))
 
 
-def nnzvec_per_step(A, n, L):
-    return 2.0 * A.nnz * n * (L - 1)
+def applications(L, symmetric):
+    return (L // 2) if symmetric else (L - 1)
+
+
+def nnzvec_per_step(A, n, L, symmetric=False):
+    return 2.0 * A.nnz * n * applications(L, symmetric)
 
 
 def measured_peaks():
@@ -95,7 +103,7 @@ def cpu_baseline(A, cfg, budget_s=12.0, terms_cap=400):
     """The oracle as it stands, on the host's cores, over the first terms of
     the same sequence (each term = one black-box application = 2 SpMM passes)."""
     import oracle
-    st = oracle.Setup(A, cfg["p"], cfg["m"], cfg["n"], cfg["seed"])
+    st = oracle.Setup(A, cfg["p"], cfg["m"], cfg["n"], cfg["seed"], symmetric=cfg.get("symmetric", False))
     t = time.perf_counter()
     oracle.sequence(A, st, L=3)
     per = max((time.perf_counter() - t) / 2, 1e-4)
@@ -108,6 +116,62 @@ def cpu_baseline(A, cfg, budget_s=12.0, terms_cap=400):
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d terms of the same sequence (%d black-box applications, 2 sparse passes "
                       "each, %.1f s)" % (terms, terms - 1, el)}
+
+
+def gather_reference(A, n, reps=20):
+    """The same gather pattern through a library kernel: a float32 gather-sum
+    (torch.nn.functional.embedding_bag, mode "sum") of rows of the same width,
+    once over the rows of A (pass 1 shape) and once over the rows of A^T (pass
+    2 shape), timed with CUDA events after warm-up (inputs L2-resident, as in
+    the loop)."""
+    import torch
+    import torch.nn.functional as F
+    At = A.transpose()
+    out = {}
+    for name, M, cols in [("pass1", A, A.cols), ("pass2", At, At.cols)]:
+        tab = torch.rand(cols, n, device="cuda", dtype=torch.float32)
+        idx = torch.from_numpy(M.colidx.astype(np.int64)).cuda()
+        off = torch.from_numpy(M.rowptr[:-1].astype(np.int64)).cuda()
+        for _ in range(3):
+            F.embedding_bag(idx, tab, off, mode="sum")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            F.embedding_bag(idx, tab, off, mode="sum")
+        e1.record()
+        e1.synchronize()
+        out[name + "_us"] = 1e3 * e0.elapsed_time(e1) / reps
+    out["impl"] = "torch.nn.functional.embedding_bag, mode sum, float32 rows of %d values, same index pattern" % n
+    return out
+
+
+def run_blackbox_only(args):
+    """A few black-box applications on the bench workload (for profiler
+    captures of the SpMM passes): matrix ingest, then W + K applications."""
+    import torch
+    from paper_0704_2351_gb300 import wr
+    A, cfg = workload(0)
+    p, n = cfg["p"], cfg["n"]
+    ctx = wr.wr_create(0)
+    mat = wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+    g = torch.Generator().manual_seed(cfg["seed"])
+    v = torch.randint(0, p, (A.cols, n), generator=g, dtype=torch.int64).to(torch.int32).cuda()
+    out = torch.empty_like(v)
+    prm = wr.make_params(p, 1, n, cfg["seed"])
+    for _ in range(args.warmup):
+        wr.wr_blackbox_apply_device(ctx, mat, prm, v, out, n)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        wr.wr_blackbox_apply_device(ctx, mat, prm, v, out, n)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t) / max(args.steps, 1)
+    print(json.dumps({"only": "blackbox", "workload": cfg["name"], "steps": args.steps,
+                      "ms_per_application_wall": ms}), flush=True)
+    wr.wr_matrix_free(mat)
+    wr.wr_destroy(ctx)
+    return 0
 
 
 def run_reference(args):
@@ -147,9 +211,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wr", choices=["wr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--projection", default="generic", choices=["generic", "symmetric"])
+    ap.add_argument("--only-blackbox", action="store_true",
+                    help="only ingest + black-box applications (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_blackbox:
+        return run_blackbox_only(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,11 +233,14 @@ def main():
 
     A, cfg = workload(rank)
     p, m, n = cfg["p"], cfg["m"], cfg["n"]
+    sym = args.projection == "symmetric"
+    cfg["symmetric"] = sym
     L = -(-A.cols // m) + -(-A.cols // n) + 2
-    work = nnzvec_per_step(A, n, L)
+    work = nnzvec_per_step(A, n, L, sym)
     stream = torch.cuda.Stream()
     ctx = wr.wr_create(local, stream.cuda_stream)
-    params = wr.make_params(p, m, n, cfg["seed"])
+    params = wr.make_params(p, m, n, cfg["seed"],
+                            projection=wr.WR_PROJ_SYMMETRIC if sym else wr.WR_PROJ_GENERIC)
     d_rp = torch.from_numpy(A.rowptr.astype(np.int64)).to("cuda")
     d_ci = torch.from_numpy(A.colidx.astype(np.int32)).to("cuda")
     d_va = torch.from_numpy(A.vals.astype(np.int32)).to("cuda")
@@ -267,6 +339,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": cfg["name"], "block": [m, n], "prime": p, "seq_len": L,
+                       "projection": args.projection, "applications": applications(L, sym),
                        "per_rank": "independent matrix per rank (seeded by rank), no collective on the data path",
                        "l2": "working set below L2; a 256 MB buffer is written between timed steps",
                        "phases_ms": phases},
@@ -276,6 +349,10 @@ def main():
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, cfg)
+    if rank == 0 and world == 1 and spmm_launches:
+        gref = gather_reference(A, n)
+        gref["k_spmm_avg_pass_us"] = spmm_ms / spmm_launches * 1e3
+        line["gather_ref"] = gref
     if rank == 0:
         print(json.dumps(line), flush=True)
     wr.wr_destroy(ctx)
