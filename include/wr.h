@@ -133,12 +133,24 @@ void wr_matrix_free(wr_matrix *mat);
 /* Rank of the matrix modulo params->prime (Section 2.4 steps 1-4). */
 wr_status wr_rank(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out);
 
-/* Many jobs in one call (matrices may repeat with different primes or seeds):
- * jobs that share a matrix share its passes over the matrix; the sequence
- * loops of all jobs run interleaved on the device.  outs[j] receives job j's
- * result (NULL when that job failed; the call then returns its status). */
+/* Many jobs in one call (matrices may repeat with different primes or seeds;
+ * the paper's rank over Q takes the maximum over several primes, Section
+ * 2.4).  Jobs run on the context's batch slots (wr_set_batch_slots, default
+ * 8): each slot has its own stream and host thread, so the sequence loops and
+ * sigma-basis kernels of several jobs are in flight on the device at once;
+ * slots take the largest remaining job first.  Each job's result is
+ * bit-identical to the same job run alone.  outs[j] receives job j's result
+ * (NULL when that job failed; the call then returns the first failing job's
+ * status, its index in wr_last_error()).  The matrices must have been loaded
+ * on the context's device. */
 wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *const *mats,
                         const wr_params *params, wr_result **outs);
+/* Number of slots wr_rank_batch uses on this context (1..64). */
+wr_status wr_set_batch_slots(wr_ctx *ctx, int32_t slots);
+/* Upper bound of the device memory one wr_rank call on (mat, params)
+ * allocates besides the loaded matrix (the server's admission estimate). */
+wr_status wr_rank_device_bytes(const wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                               uint64_t *bytes);
 
 uint64_t wr_result_rank(const wr_result *res);
 /* deg det F, codeg det F = v_x(det F), sum of the generator's column degrees,
@@ -210,11 +222,18 @@ typedef struct {
     double p50_ms, p99_ms;    /* latency submit -> result                                */
     double throughput_rps;    /* completed / (last completion - first submission)         */
     int32_t max_resident;     /* most requests resident at once                          */
+    int64_t kernel_launches;  /* kernels launched by the server's slots so far            */
 } wr_stats;
 
-/* Continuous-batching rank server: requests are admitted as slots and device
- * memory free up, and their sequence iterations run interleaved with those of
- * the requests already resident. */
+/* Continuous-batching rank server (no counterpart in the paper, which runs
+ * one matrix at a time).  max_slots slots, each a stream of its own with one
+ * host thread; a queued request is admitted, in arrival order, as soon as a
+ * slot is idle and its device-memory estimate (wr_rank_device_bytes) fits
+ * beside the requests already resident (hbm_budget; 0 = no limit; a request
+ * above the budget is refused at submission with WR_EINVAL).  Requests that
+ * arrive while others are on the GPU therefore start at once and overlap with
+ * them on the device; each result is bit-identical to the same request run
+ * alone.  Latency is measured from wr_submit to the result being ready. */
 wr_status wr_server_start(wr_ctx *ctx, const wr_server_cfg *cfg, wr_server **out);
 /* Queue a rank request; the matrix must stay alive until its result is taken. */
 wr_status wr_submit(wr_server *srv, const wr_matrix *mat, const wr_params *params,

@@ -256,6 +256,7 @@ struct wr_ctx {
     size_t smem_optin = 0;
     bool profiling = false;
     int64_t launches = 0;   // kernels launched through this context (graph replays: nodes per replay)
+    int batch_slots = 8;    // slots (streams + host threads) of wr_rank_batch
     wr_timings last{};
 };
 

@@ -1,12 +1,25 @@
-// Batched rank jobs and the rank server.
+// Batched rank jobs and the continuous-batching rank server.
+//
+// Both run every job through the same single-job path (rank_one), each job on
+// one of several slots.  A slot is a context of its own (its own non-blocking
+// stream on the caller's device) driven by one host thread, so the captured
+// sequence loops and the sigma-basis kernels of different jobs are in flight
+// on the device at the same time: small matrices that cannot fill 152 SMs on
+// their own share the GPU, and the single-block M-Basis chunks of several jobs
+// run side by side.  A job's kernels, launch shapes and arithmetic do not
+// depend on what runs beside it, so its result is bit-identical to the same
+// job run alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <numeric>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -14,89 +27,200 @@
 
 namespace wr {
 wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out);
+
+// Upper bound of the device memory one rank_one call allocates besides the
+// loaded matrix: the sequence state (blocks, diagonals, split accumulators,
+// exact term sums), the kept sequence and basis, and the larger of the
+// sequence phase and the sigma-basis + readout phase (the sequence state is
+// released before the sigma-basis starts).
+size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
+    const size_t L = (size_t)r.L, m = (size_t)r.m, n = (size_t)r.n, q = m + n, nv = (size_t)r.nv;
+    const size_t N = (size_t)r.N, M = (size_t)r.M;
+    const size_t nsplit = (size_t)(mat->a.nsplit + mat->at.nsplit);
+    const size_t seq = 4 * N * nv + 4 * M * nv + 4 * (3 * N + 2 * M) + 4 * N * m + 8 * nv * nsplit + 8 * L * m * n;
+    const size_t keep = 4 * L * m * n + 4 * (L + 2) * n * q + 4 * q;
+    const size_t sigma = 4 * (L + 2) * n * q + 4 * (size_t)(2 * num_sms) * 64 * m * q + 4 * 65 * q * q + 4 * (m * q + 4 * q);
+    const size_t readout = 4 * 2 * (L + 2) * n * n + 64;
+    return keep + std::max(seq, sigma + readout) + (1u << 20);
 }
 
+// A slot: a context of its own on the parent's device.
+static wr_status make_slot(const wr_ctx *parent, wr_ctx **out) {
+    WR_TRY(wr_create(out, parent->device, nullptr));
+    (*out)->profiling = parent->profiling;
+    return WR_OK;
+}
+
+}  // namespace wr
+
 using namespace wr;
+
+extern "C" wr_status wr_rank_device_bytes(const wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                          uint64_t *bytes) {
+    if (!ctx || !mat || !params || !bytes) return fail(WR_EINVAL, "null argument");
+    Resolved r;
+    WR_TRY(resolve(mat, params, r));
+    *bytes = r.N == 0 ? 0 : (uint64_t)rank_device_bytes(mat, r, ctx->num_sms);
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_batch_slots(wr_ctx *ctx, int32_t slots) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if (slots < 1 || slots > 64) return fail(WR_EINVAL, "batch slots must be in 1..64");
+    ctx->batch_slots = slots;
+    return WR_OK;
+}
 
 extern "C" wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *const *mats,
                                    const wr_params *params, wr_result **outs) {
     if (!ctx || (njobs && (!mats || !params || !outs))) return fail(WR_EINVAL, "null argument");
-    wr_status first = WR_OK;
+    for (size_t j = 0; j < njobs; j++) outs[j] = nullptr;
+    if (njobs == 0) return WR_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    // largest jobs first (longest-processing-time order balances the slots)
+    std::vector<size_t> order(njobs);
+    std::vector<double> cost(njobs, 0.0);
     for (size_t j = 0; j < njobs; j++) {
-        outs[j] = nullptr;
-        wr_status st = rank_one(ctx, mats[j], &params[j], &outs[j]);
-        if (st != WR_OK && first == WR_OK) first = st;
+        order[j] = j;
+        Resolved r;
+        if (mats[j] && resolve(mats[j], &params[j], r) == WR_OK)
+            cost[j] = (double)r.L * (double)(mats[j]->nnz + 1) * r.nv;
     }
-    return first;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+
+    const int nslots = (int)std::min<size_t>(njobs, (size_t)std::max(1, ctx->batch_slots));
+    std::vector<wr_ctx *> slots(nslots, nullptr);
+    for (int k = 0; k < nslots; k++) {
+        wr_status st = make_slot(ctx, &slots[k]);
+        if (st != WR_OK) {
+            for (auto *c : slots) wr_destroy(c);
+            return st;
+        }
+    }
+    std::vector<wr_status> status(njobs, WR_OK);
+    std::vector<std::string> msg(njobs);
+    std::atomic<size_t> next{0};
+    auto worker = [&](int k) {
+        cudaSetDevice(ctx->device);
+        for (;;) {
+            const size_t i = next.fetch_add(1);
+            if (i >= njobs) return;
+            const size_t j = order[i];
+            status[j] = rank_one(slots[k], mats[j], &params[j], &outs[j]);
+            if (status[j] != WR_OK) msg[j] = wr_last_error();
+        }
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < nslots; k++) th.emplace_back(worker, k);
+    worker(0);
+    for (auto &t : th) t.join();
+    for (auto *c : slots) {
+        ctx->launches += c->launches;
+        wr_destroy(c);
+    }
+    ctx->last = wr_timings{};
+    ctx->last.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (size_t j = 0; j < njobs; j++)
+        if (status[j] != WR_OK) return fail(status[j], "batch job " + std::to_string(j) + ": " + msg[j]);
+    return WR_OK;
 }
 
 // ------------------------------------------------------------------ server
 
 struct wr_server {
-    wr_ctx *ctx = nullptr;  // own stream on the caller's device
+    int device = 0;
     wr_server_cfg cfg{};
+    std::vector<wr_ctx *> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     struct Req {
         uint64_t ticket;
         const wr_matrix *mat;
         wr_params prm;
+        uint64_t bytes;  // admission estimate
         std::chrono::steady_clock::time_point t_submit;
     };
     std::deque<Req> queue;
     struct Done {
         wr_status st;
         wr_result *res;
+        std::string msg;
     };
     std::map<uint64_t, Done> done;
     std::vector<double> lat_ms;
     uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0;
-    int32_t max_resident = 0;
+    uint64_t resident_bytes = 0;
+    int32_t resident = 0, max_resident = 0;
     std::chrono::steady_clock::time_point t_first, t_last;
     bool have_first = false, stop = false;
-    std::thread worker;
+    std::vector<std::thread> workers;
 };
 
-static void server_loop(wr_server *s) {
-    cudaSetDevice(s->ctx->device);
+// The head of the queue is admitted when a slot is idle (this worker) and
+// its memory estimate fits beside the requests already resident.  Strict
+// arrival order: a large request at the head waits for memory rather than
+// being overtaken indefinitely.
+static bool admissible(const wr_server *s) {
+    if (s->queue.empty()) return false;
+    if (s->cfg.hbm_budget == 0 || s->resident == 0) return true;
+    return s->resident_bytes + s->queue.front().bytes <= s->cfg.hbm_budget;
+}
+
+static void server_loop(wr_server *s, int k) {
+    cudaSetDevice(s->device);
+    wr_ctx *ctx = s->slots[k];
     for (;;) {
         wr_server::Req rq;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-            if (s->stop && s->queue.empty()) return;
+            s->cv_work.wait(lk, [&] { return (s->stop && s->queue.empty()) || admissible(s); });
+            if (s->queue.empty()) return;  // stopping
             rq = s->queue.front();
             s->queue.pop_front();
-            s->max_resident = std::max(s->max_resident, 1);
+            s->resident++;
+            s->resident_bytes += rq.bytes;
+            s->max_resident = std::max(s->max_resident, s->resident);
         }
+        s->cv_work.notify_all();  // the next head may fit as well
         wr_result *res = nullptr;
-        wr_status st = rank_one(s->ctx, rq.mat, &rq.prm, &res);
+        wr_status st = rank_one(ctx, rq.mat, &rq.prm, &res);
+        std::string msg = st == WR_OK ? std::string() : std::string(wr_last_error());
         auto now = std::chrono::steady_clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            s->done[rq.ticket] = wr_server::Done{st, res};
+            s->resident--;
+            s->resident_bytes -= rq.bytes;
+            s->done[rq.ticket] = wr_server::Done{st, res, msg};
             s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - rq.t_submit).count());
             if (st == WR_OK) s->completed++;
             else s->failed++;
             s->t_last = now;
         }
         s->cv_done.notify_all();
+        s->cv_work.notify_all();
     }
 }
 
 extern "C" wr_status wr_server_start(wr_ctx *ctx, const wr_server_cfg *cfg, wr_server **out) {
     if (!ctx || !cfg || !out) return fail(WR_EINVAL, "null argument");
     *out = nullptr;
+    if (cfg->max_slots > 64) return fail(WR_EINVAL, "max_slots must be at most 64");
     wr_server *s = new wr_server();
+    s->device = ctx->device;
     s->cfg = *cfg;
     if (s->cfg.max_slots < 1) s->cfg.max_slots = 1;
     if (s->cfg.queue_cap < 1) s->cfg.queue_cap = 1 << 20;
-    wr_status st = wr_create(&s->ctx, ctx->device, nullptr);
-    if (st != WR_OK) {
-        delete s;
-        return st;
+    for (int k = 0; k < s->cfg.max_slots; k++) {
+        wr_ctx *c = nullptr;
+        wr_status st = make_slot(ctx, &c);
+        if (st != WR_OK) {
+            for (auto *x : s->slots) wr_destroy(x);
+            delete s;
+            return st;
+        }
+        s->slots.push_back(c);
     }
-    s->worker = std::thread(server_loop, s);
+    for (int k = 0; k < s->cfg.max_slots; k++) s->workers.emplace_back(server_loop, s, k);
     *out = s;
     return WR_OK;
 }
@@ -105,17 +229,24 @@ extern "C" wr_status wr_submit(wr_server *srv, const wr_matrix *mat, const wr_pa
     if (!srv || !mat || !params || !ticket) return fail(WR_EINVAL, "null argument");
     Resolved r;
     WR_TRY(resolve(mat, params, r));
-    std::lock_guard<std::mutex> lk(srv->mu);
-    if ((int64_t)srv->queue.size() >= srv->cfg.queue_cap) return fail(WR_EBUSY, "server queue full");
-    auto now = std::chrono::steady_clock::now();
-    if (!srv->have_first) {
-        srv->t_first = now;
-        srv->have_first = true;
+    const uint64_t bytes = r.N == 0 ? 0 : (uint64_t)rank_device_bytes(mat, r, srv->slots[0]->num_sms);
+    if (srv->cfg.hbm_budget && bytes > srv->cfg.hbm_budget)
+        return fail(WR_EINVAL, "request needs up to " + std::to_string(bytes) + " bytes of device memory, above the "
+                               "server's budget of " + std::to_string(srv->cfg.hbm_budget));
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) return fail(WR_EBUSY, "server stopping");
+        if ((int64_t)srv->queue.size() >= srv->cfg.queue_cap) return fail(WR_EBUSY, "server queue full");
+        auto now = std::chrono::steady_clock::now();
+        if (!srv->have_first) {
+            srv->t_first = now;
+            srv->have_first = true;
+        }
+        *ticket = srv->next_ticket++;
+        srv->queue.push_back(wr_server::Req{*ticket, mat, *params, bytes, now});
+        srv->submitted++;
     }
-    *ticket = srv->next_ticket++;
-    srv->queue.push_back(wr_server::Req{*ticket, mat, *params, now});
-    srv->submitted++;
-    srv->cv_work.notify_one();
+    srv->cv_work.notify_all();
     return WR_OK;
 }
 
@@ -129,7 +260,8 @@ extern "C" wr_status wr_wait(wr_server *srv, uint64_t ticket, uint32_t timeout_m
     auto d = srv->done[ticket];
     srv->done.erase(ticket);
     *out = d.res;
-    return d.st;
+    if (d.st != WR_OK) return fail(d.st, d.msg);
+    return WR_OK;
 }
 
 extern "C" wr_status wr_server_stats(wr_server *srv, wr_stats *out) {
@@ -150,6 +282,8 @@ extern "C" wr_status wr_server_stats(wr_server *srv, wr_stats *out) {
     double span = srv->have_first ? std::chrono::duration<double>(srv->t_last - srv->t_first).count() : 0.0;
     out->throughput_rps = span > 0 ? (double)srv->completed / span : 0.0;
     out->max_resident = srv->max_resident;
+    out->kernel_launches = 0;
+    for (auto *c : srv->slots) out->kernel_launches += c->launches;
     return WR_OK;
 }
 
@@ -160,8 +294,9 @@ extern "C" void wr_server_stop(wr_server *srv) {
         srv->stop = true;
     }
     srv->cv_work.notify_all();
-    if (srv->worker.joinable()) srv->worker.join();
+    for (auto &t : srv->workers)
+        if (t.joinable()) t.join();
     for (auto &kv : srv->done) wr_result_free(kv.second.res);
-    wr_destroy(srv->ctx);
+    for (auto *c : srv->slots) wr_destroy(c);
     delete srv;
 }

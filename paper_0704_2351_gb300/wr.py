@@ -53,7 +53,8 @@ class wr_server_cfg(ctypes.Structure):
 class wr_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
-                ("throughput_rps", ctypes.c_double), ("max_resident", ctypes.c_int32)]
+                ("throughput_rps", ctypes.c_double), ("max_resident", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -74,6 +75,8 @@ _sig = {
     "wr_matrix_free": ([vp], None),
     "wr_rank": ([vp, vp, P(wr_params), P(vp)], ctypes.c_int),
     "wr_rank_batch": ([vp, ctypes.c_size_t, P(vp), P(wr_params), P(vp)], ctypes.c_int),
+    "wr_set_batch_slots": ([vp, i32], ctypes.c_int),
+    "wr_rank_device_bytes": ([vp, vp, P(wr_params), P(u64)], ctypes.c_int),
     "wr_result_rank": ([vp], u64),
     "wr_result_info": ([vp, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
     "wr_result_sequence": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -188,6 +191,16 @@ def wr_rank_batch(ctx: int, mats: Sequence[int], params: Sequence[wr_params]) ->
     outs = (vp * n)()
     _check(_lib.wr_rank_batch(vp(ctx), n, marr, parr, outs))
     return [o for o in outs]
+
+
+def wr_set_batch_slots(ctx: int, slots: int) -> None:
+    _check(_lib.wr_set_batch_slots(vp(ctx), slots))
+
+
+def wr_rank_device_bytes(ctx: int, mat: int, params: wr_params) -> int:
+    b = u64()
+    _check(_lib.wr_rank_device_bytes(vp(ctx), vp(mat), ctypes.byref(params), ctypes.byref(b)))
+    return b.value
 
 
 def wr_result_rank(res: int) -> int:
