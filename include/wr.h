@@ -197,6 +197,16 @@ wr_status wr_blackbox_apply_device_noalloc(wr_ctx *ctx, const wr_matrix *mat,
 /* The sequence S_i = X^T A~^i Y, i < L (Section 2.4 step 2) into d_S (L*m*n). */
 wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                              uint32_t *d_S, uint64_t L);
+/* Columns [col0, col0 + ncols) of that sequence, S_i = X^T A~^i Y[:, col0:col0+ncols]
+ * (L x m x ncols residues into d_S), with X, Y, D1, D2 drawn exactly as for
+ * the whole sequence (params->n is the width of the whole Y).  The paper
+ * gives every process one column of Y and gathers the column sequences before
+ * the sigma-basis (Section 3.1); one GPU per column slab is the same split, and
+ * the slabs of all GPUs, concatenated in column order, equal
+ * wr_sequence_device's result.  With the symmetric projection X is the whole
+ * Y and one term is computed per application. */
+wr_status wr_sequence_slab_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                  uint32_t col0, uint32_t ncols, uint32_t *d_S, uint64_t L);
 /* Order-L sigma-basis of [S(x) | -I_m] with shift (0^n, 1^m) (Section 2.3):
  * writes its first n rows (the P part) as d_P ((Dcap+1) x n x (m+n), [t][r][c])
  * and the shifted column degrees d_deg (m + n).  d_S: L*m*n residues. */

@@ -128,6 +128,11 @@ wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r) {
     r.L = prm->seq_len ? (int64_t)prm->seq_len : (r.N + r.m - 1) / r.m + (r.N + r.n - 1) / r.n + 2;
     r.symmetric = prm->projection == WR_PROJ_SYMMETRIC;
     r.seed = prm->seed;
+    r.ystride = r.n;
+    r.ycol0 = 0;
+    r.xtag = r.symmetric ? TAG_Y : TAG_X;
+    r.xwidth = r.symmetric ? r.n : r.m;
+    r.gram = r.symmetric;
     return WR_OK;
 }
 
@@ -425,6 +430,30 @@ extern "C" wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const
     }
     double a = 0, b = 0;
     WR_TRY(run_sequence(ctx, mat, *params, (int64_t)L, d_S, &a, &b));
+    ctx->last.setup_ms = a;
+    ctx->last.sequence_ms = b;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_sequence_slab_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                             uint32_t col0, uint32_t ncols, uint32_t *d_S, uint64_t L) {
+    if (!ctx || !mat || !params || !d_S) return fail(WR_EINVAL, "null argument");
+    Resolved r;
+    WR_TRY(resolve(mat, params, r));
+    if (ncols < 1 || (uint64_t)col0 + ncols > (uint64_t)params->n)
+        return fail(WR_EINVAL, "column slab [col0, col0 + ncols) must lie in [0, n) and be nonempty");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    ctx->last = wr_timings{};
+    r.n = (int)ncols;
+    r.nv = padded_width(r.n);
+    r.ycol0 = (int)col0;
+    r.gram = false;  // one term per application: X spans the whole Y, the right block is a slab
+    if (r.N == 0) {
+        WR_CUDA(cudaMemsetAsync(d_S, 0, sizeof(uint32_t) * L * r.m * r.n, ctx->stream));
+        return WR_OK;
+    }
+    double a = 0, b = 0;
+    WR_TRY(run_sequence_resolved(ctx, mat, r, (int64_t)L, d_S, &a, &b));
     ctx->last.setup_ms = a;
     ctx->last.sequence_ms = b;
     return WR_OK;

@@ -321,8 +321,17 @@ struct Resolved {
     int64_t L;
     bool symmetric;
     uint64_t seed;
+    // the columns of Y this run carries: entry (i, b) of the block is
+    // Y[i][ycol0 + b] of a Y with ystride columns (a column slab when
+    // ycol0 > 0 or n < ystride); X entry (i, a) draws tag xtag at i*xwidth + a
+    int ystride, ycol0;
+    uint64_t xtag;
+    int xwidth;
+    bool gram;  // two terms per application (symmetric projection, whole Y)
 };
 wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r);
+wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,
+                                double *setup_ms, double *seq_ms);
 
 int padded_width(int n);
 

@@ -303,11 +303,12 @@ __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t
     if (i < len) out[i] = (uint32_t)(1 + stream_hash(seed, tag, (uint64_t)i) % (uint64_t)(p - 1));
 }
 
-// T0 = D1 Y (padded to nv columns with zeros), d1sq = D1^2, and
-// Xh = D1^{-1} X (generic projection) or the Gram weights D1^{-2} (symmetric
-// projection X = Y: S_2k = V_k^T V_k with T_k = D1 V_k).
-__global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, int symmetric,
-                          const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
+// T0 = D1 Y (padded to nv columns with zeros; columns ycol0.. of a Y with
+// ystride columns), d1sq = D1^2, and Xh = D1^{-1} X (X drawn with tag xtag,
+// xwidth columns) or the Gram weights D1^{-2} (symmetric projection X = Y
+// over the whole Y: S_2k = V_k^T V_k with T_k = D1 V_k).
+__global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64_t xtag, int xwidth, int ystride,
+                          int ycol0, int gram, const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
                           uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, ModP mp) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -316,15 +317,15 @@ __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, int sy
     d1sq[i] = mulm(d, d, mp);
     for (int b = 0; b < nv; b++) {
         uint32_t yv = 0;
-        if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, (uint64_t)i * n + b) % mp.p);
+        if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, (uint64_t)i * ystride + ycol0 + b) % mp.p);
         t0[i * nv + b] = mulm(d, yv, mp);
     }
-    if (symmetric) {
+    if (gram) {
         xh[i] = mulm(dinv, dinv, mp);
         return;
     }
     for (int a = 0; a < m; a++) {
-        uint32_t xv = (uint32_t)(stream_hash(seed, TAG_X, (uint64_t)i * m + a) % mp.p);
+        uint32_t xv = (uint32_t)(stream_hash(seed, xtag, (uint64_t)i * xwidth + a) % mp.p);
         xh[i * m + a] = mulm(dinv, xv, mp);
     }
 }
@@ -474,12 +475,13 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
         WR_LAUNCHED(ctx);
     }
     if (want_projection && r.N > 0) {
-        k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, nv, r.seed, r.symmetric ? 1 : 0,
-                                                      st.D1.as<uint32_t>(), st.T.as<uint32_t>(),
-                                                      st.xh.as<uint32_t>(), st.d1sq.as<uint32_t>(), st.mp);
+        k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, nv, r.seed, r.xtag, r.xwidth, r.ystride,
+                                                      r.ycol0, r.gram ? 1 : 0, st.D1.as<uint32_t>(),
+                                                      st.T.as<uint32_t>(), st.xh.as<uint32_t>(),
+                                                      st.d1sq.as<uint32_t>(), st.mp);
         WR_LAUNCHED(ctx);
     }
-    if (want_projection && r.symmetric && r.M > 0) {
+    if (want_projection && r.gram && r.M > 0) {
         WR_TRY(dev_alloc(ctx, st.w2, sizeof(uint32_t) * r.M));
         k_inv_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.M, st.D2.as<uint32_t>(), st.w2.as<uint32_t>(), st.mp);
         WR_LAUNCHED(ctx);
@@ -493,7 +495,7 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
 // S_2k+1 = (A D1 V_k)^T D2 (A D1 V_k).
 static int64_t seq_applications(const Resolved &r, int64_t L) {
     const int64_t terms = std::max<int64_t>(L - 1, 0);
-    return r.symmetric ? (terms + 1) / 2 : terms;
+    return r.gram ? (terms + 1) / 2 : terms;
 }
 
 // One iteration: W = D2 A T, T <- D1^2 A^T W (or the rows-side analogue),
@@ -510,7 +512,7 @@ static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
     WR_TRY(launch_spmm(ctx, nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.d1sq.as<uint32_t>(),
                        st.acc2.as<unsigned long long>(), st.mp, nullptr));
     if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
-    if (st.r.symmetric) {
+    if (st.r.gram) {
         WR_TRY(launch_project(ctx, st.r.M, st.r.m, st.r.n, nv, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(),
                               st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, -1,
                               st.r.L));
@@ -535,6 +537,11 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
                        uint32_t *d_S, double *setup_ms, double *seq_ms) {
     Resolved r;
     WR_TRY(resolve(mat, &prm, r));
+    return run_sequence_resolved(ctx, mat, r, L, d_S, setup_ms, seq_ms);
+}
+
+wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,
+                                double *setup_ms, double *seq_ms) {
     r.L = L;
     cudaStream_t s = ctx->stream;
     cudaEvent_t e0, e1, e2;
@@ -549,8 +556,8 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
     WR_CUDA(cudaMemsetAsync(st.s_raw.ptr, 0, st.s_raw.bytes, s));
     if (L > 0)
         WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
-                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.symmetric,
-                              r.symmetric ? 2 : 1, 0, L));
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.gram,
+                              r.gram ? 2 : 1, 0, L));
     WR_CUDA(cudaEventRecord(e1, s));
 
     // profiling: every PROF_EVERY-th group of iterations is launched eagerly

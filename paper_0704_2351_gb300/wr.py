@@ -85,6 +85,7 @@ _sig = {
     "wr_blackbox_apply_device": ([vp, vp, P(wr_params), vp, vp, i64], ctypes.c_int),
     "wr_blackbox_apply_device_noalloc": ([vp, vp, P(wr_params), vp, vp, i64], ctypes.c_int),
     "wr_sequence_device": ([vp, vp, P(wr_params), vp, u64], ctypes.c_int),
+    "wr_sequence_slab_device": ([vp, vp, P(wr_params), u32, u32, vp, u64], ctypes.c_int),
     "wr_sigma_basis_device": ([vp, vp, u64, u32, u32, u32, vp, vp, i64], ctypes.c_int),
     "wr_det_valuation_device": ([vp, vp, i64, i64, u32, P(i64)], ctypes.c_int),
     "wr_server_start": ([vp, P(wr_server_cfg), P(vp)], ctypes.c_int),
@@ -249,6 +250,11 @@ def wr_blackbox_apply_device_noalloc(ctx: int, mat: int, params: wr_params, d_in
 
 def wr_sequence_device(ctx: int, mat: int, params: wr_params, d_S, L: int) -> None:
     _check(_lib.wr_sequence_device(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_S)), L))
+
+
+def wr_sequence_slab_device(ctx: int, mat: int, params: wr_params, col0: int, ncols: int, d_S, L: int) -> None:
+    _check(_lib.wr_sequence_slab_device(vp(ctx), vp(mat), ctypes.byref(params), col0, ncols,
+                                        vp(_dptr(d_S)), L))
 
 
 def wr_sigma_basis_device(ctx: int, d_S, L: int, m: int, n: int, prime: int, d_P, d_deg, Dcap: int) -> None:

@@ -181,6 +181,51 @@ def test_rank_planted_symmetric(wr, ctx, m):
         assert np.array_equal(g["F"], ref["F"])
 
 
+@pytest.mark.parametrize("sym", [False, True])
+def test_sequence_column_slabs_concatenate_to_the_whole(wr, ctx, sym):
+    """Column slabs of Y (the multi-GPU split, computed here one after the
+    other on one GPU): uneven widths, concatenated in column order, equal the
+    whole sequence; each slab equals the oracle on its slab of Y."""
+    p, m, n, seed, L = 1073741789, 8, 8, 12, 90
+    A = heavy_matrix(520, 480, seed=23, heavy=2, heavy_len=260)
+    mat = load(wr, ctx, A)
+    prm = wr.make_params(p, m, n, seed,
+                         projection=wr.WR_PROJ_SYMMETRIC if sym else wr.WR_PROJ_GENERIC)
+    st = oracle.Setup(A, p, m, n, seed, symmetric=sym)
+    S_ref = oracle.sequence(A, st, L)
+    parts = []
+    for c0, w in [(0, 3), (3, 1), (4, 4)]:
+        d = torch.empty((L, m, w), dtype=torch.int32, device="cuda")
+        wr.wr_sequence_slab_device(ctx, mat, prm, c0, w, d, L)
+        parts.append(from_dev(d).reshape(L, m, w))
+    assert np.array_equal(np.concatenate(parts, axis=2), S_ref)
+    with pytest.raises(wr.WrError):
+        wr.wr_sequence_slab_device(ctx, mat, prm, 6, 3, torch.empty((L, m, 3), dtype=torch.int32,
+                                                                   device="cuda"), L)
+    wr.wr_matrix_free(mat)
+
+
+def test_sharded_sequence_single_rank_gpu(wr, ctx):
+    """The shard module's GPU slab function with a one-rank gloo group."""
+    import torch.distributed as dist
+    from paper_0704_2351_gb300 import shard
+    import socket
+    s = socket.socket(); s.bind(("127.0.0.1", 0)); port = s.getsockname()[1]; s.close()
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    try:
+        p, m, n, seed, L = 65521, 4, 6, 3, 40
+        A = heavy_matrix(300, 280, seed=5, heavy=1, heavy_len=120)
+        mat = load(wr, ctx, A)
+        prm = wr.make_params(p, m, n, seed)
+        f = shard.gpu_slab(ctx, mat, prm, L)
+        S = shard.sharded_sequence(lambda c0, w: f(c0, w).cpu(), n, 0, 1)
+        ref = oracle.sequence(A, oracle.Setup(A, p, m, n, seed), L)
+        assert np.array_equal(S.numpy().view(np.uint32), ref)
+        wr.wr_matrix_free(mat)
+    finally:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------ sigma-basis (A8)
 
 def gpu_sigma(wr, ctx, S, p):
