@@ -329,6 +329,37 @@ def run_serve(args):
     return 0
 
 
+def run_sigma_only(args):
+    """The sigma-basis alone on a random sequence with the bench workload's
+    shape (L = 45,002 terms of 8 x 8 residues mod 1073741789; a random
+    sequence has the generic degree profile of a full-rank one), W + K times
+    (for profiler captures and timing of the sigma-basis kernels)."""
+    import torch
+    from paper_0704_2351_gb300 import wr
+    p, m, n, L = 1073741789, 8, 8, 45002
+    g = torch.Generator().manual_seed(7)
+    S = torch.randint(0, p, (L, m, n), generator=g, dtype=torch.int64).to(torch.int32).cuda()
+    q = m + n
+    P = torch.empty((L + 2, n, q), dtype=torch.int32, device="cuda")
+    deg = torch.empty(q, dtype=torch.int32, device="cuda")
+    ctx = wr.wr_create(0)
+    wr.wr_set_profiling(ctx, True)
+    for _ in range(args.warmup):
+        wr.wr_sigma_basis_device(ctx, S, L, m, n, p, P, deg, L + 1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        wr.wr_sigma_basis_device(ctx, S, L, m, n, p, P, deg, L + 1)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t) / max(args.steps, 1)
+    tm = wr.wr_last_timings(ctx)
+    print(json.dumps({"only": "sigma", "L": L, "block": [m, n], "ms_per_sigma_basis": ms,
+                      "window_ms": tm["sigma_window_ms"], "local_ms": tm["sigma_local_ms"],
+                      "apply_ms": tm["sigma_apply_ms"]}), flush=True)
+    wr.wr_destroy(ctx)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -369,6 +400,8 @@ def main():
     ap.add_argument("--projection", default="generic", choices=["generic", "symmetric"])
     ap.add_argument("--only-blackbox", action="store_true",
                     help="only ingest + black-box applications (for profiler captures)")
+    ap.add_argument("--only-sigma", action="store_true",
+                    help="only the sigma-basis on a random sequence of the workload's shape")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the one-matrix time-to-rank line (default); batch / serve: batched or "
                          "served against plain time-to-rank")
@@ -384,6 +417,8 @@ def main():
         return run_reference(args)
     if args.only_blackbox:
         return run_blackbox_only(args)
+    if args.only_sigma:
+        return run_sigma_only(args)
     if args.workload == "batch":
         args.block = args.block or 8
         return run_batch(args)

@@ -49,20 +49,81 @@ __global__ void k_init_basis(uint32_t *__restrict__ P, int n, int q, int32_t *__
 
 // ---- window.  Block b takes coefficients t in [b tper, (b+1) tper) and
 // writes its partial E_i = sum_t S[k0+i-t] P[t] (mod p) for all i < bb into
-// Epart[b]; the local kernel adds the partials.  Work item = one (a, c) pair
-// and WIN_IB consecutive orders i, held in registers across the range.
+// Epart[b]; k_sum_parts adds the partials.
 constexpr int WIN_THREADS = 256;
-constexpr int WIN_IB = 16;
+constexpr int WIN_IB = 8;  // orders per thread
+constexpr int WIN_CB = 4;  // columns per thread
+static_assert(WIN_IB == 8 && WIN_CB == 4, "the register window and 16-byte loads assume an 8 x 4 tile");
 
-template <int KLAZY>
-__global__ void __launch_bounds__(WIN_THREADS)
+// x = hi 2^32 + lo is congruent to hi (2^32 mod p) + lo; folded twice a 64-bit
+// accumulator drops below 2^60 + 2^33 (p < 2^30) or 2^62 + 2^33 (p < 2^31),
+// leaving room for FOLDK = 14 (or 2) more products below p^2 before the next
+// fold.  Two 32x32+64-bit multiply-adds instead of a reduction mod p.
+// d = a b + c in one 32x32 -> 64-bit multiply-add
+__device__ __forceinline__ unsigned long long madw(uint32_t a, uint32_t b, unsigned long long c) {
+    unsigned long long d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fold2(unsigned long long x, uint32_t c) {
+    x = madw((uint32_t)(x >> 32), c, (unsigned long long)(uint32_t)x);
+    return madw((uint32_t)(x >> 32), c, (unsigned long long)(uint32_t)x);
+}
+
+// A 64-bit accumulator kept as two 32-bit words: (hi, lo) += a b as two
+// multiply-adds chained through the carry flag.
+struct Acc2 {
+    uint32_t lo, hi;
+};
+__device__ __forceinline__ void mac2(Acc2 &acc, uint32_t a, uint32_t b) {
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
+        : "+r"(acc.lo), "+r"(acc.hi)
+        : "r"(a), "r"(b));
+}
+__device__ __forceinline__ unsigned long long acc2_u64(const Acc2 &a) {
+    return ((unsigned long long)a.hi << 32) | a.lo;
+}
+// fold2 on the two-word form
+__device__ __forceinline__ void fold2w(Acc2 &a, uint32_t c) {
+    const unsigned long long x = fold2(acc2_u64(a), c);
+    a.lo = (uint32_t)x;
+    a.hi = (uint32_t)(x >> 32);
+}
+
+
+// Four consecutive residues from shared memory (one 16-byte load when VEC),
+// zero where the column is out of range.
+template <bool VEC>
+__device__ __forceinline__ void ld4(const uint32_t *p, const bool (&cv)[4], uint32_t (&v)[4]) {
+    if constexpr (VEC) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = cv[u] ? p[u] : 0u;
+    }
+}
+
+// Discrepancies of one chunk: E_i = sum_t S_{k0+i-t} P_t for orders
+// i < bb (m x q each), the coefficients t of P split over the blocks (each
+// writes its partial sums, reduced mod p, to Epart[block]).  A thread owns a
+// WIN_IB x WIN_CB tile (orders i0.. x columns c0..) of one row a.  For a fixed
+// r it walks the coefficients t of the tile: the S residues the tile needs at
+// step t+1 are those of step t shifted by one order, so they live in a
+// circular register window that takes one new shared-memory load per step
+// (slot indices are compile-time in an 8-fold unrolled loop), and the
+// WIN_CB residues of P are one 16-byte load (VEC: q a multiple of 4).
+template <int FOLDK, bool VEC>
+__global__ void __launch_bounds__(WIN_THREADS, 1)
     k_window(const uint32_t *__restrict__ S, int64_t L, int m, int n, int q, const uint32_t *__restrict__ P,
              int64_t k0, int bb, int TT, int64_t tper, const int *__restrict__ dmax_dev,
              uint32_t *__restrict__ Epart, ModP mp) {
     extern __shared__ uint32_t sm[];
     const int mn = m * n, nq = n * q, mq = m * q;
-    const int nib = (bb + WIN_IB - 1) / WIN_IB;
-    const int items = mq * nib;
+    const int nib = (bb + WIN_IB - 1) / WIN_IB, ncb = (q + WIN_CB - 1) / WIN_CB;
+    const int items = nib * m * ncb;
+    const uint32_t fc = mp.r1;  // 2^32 mod p
     uint32_t *out = Epart + (size_t)blockIdx.x * bb * mq;
     const int64_t tmax = min64((int64_t)*dmax_dev, k0 + bb - 1);
     const int64_t tb0 = (int64_t)blockIdx.x * tper;
@@ -72,12 +133,18 @@ __global__ void __launch_bounds__(WIN_THREADS)
     for (int round = 0; round * WIN_THREADS < items; round++) {
         const int it = round * WIN_THREADS + threadIdx.x;
         const bool act = it < items;
-        const int pair = act ? it % mq : 0;
-        const int a = pair / q, c = pair % q;
-        const int i0 = act ? (it / mq) * WIN_IB : 0;
-        unsigned long long acc[WIN_IB];
+        const int cb = act ? it % ncb : 0;
+        const int a = act ? (it / ncb) % m : 0;
+        const int i0 = act ? (it / (ncb * m)) * WIN_IB : 0;
+        const int c0 = cb * WIN_CB;
+        bool cv[WIN_CB];
 #pragma unroll
-        for (int k = 0; k < WIN_IB; k++) acc[k] = 0;
+        for (int u = 0; u < WIN_CB; u++) cv[u] = c0 + u < q;
+        Acc2 acc[WIN_IB][WIN_CB];
+#pragma unroll
+        for (int k = 0; k < WIN_IB; k++)
+#pragma unroll
+            for (int u = 0; u < WIN_CB; u++) acc[k][u] = Acc2{0u, 0u};
         int cnt = 0;
         for (int64_t t0 = tb0; t0 < tb1; t0 += TT) {
             const int tt_n = (int)min64(TT, tb1 - t0);
@@ -91,18 +158,34 @@ __global__ void __launch_bounds__(WIN_THREADS)
             }
             __syncthreads();
             if (!act) continue;
-            for (int tl = 0; tl < tt_n; tl++) {
-                // order i, coefficient t0+tl -> S index k0 + i - t0 - tl = smin + (i + tt_n - 1 - tl)
-                const uint32_t *srow = Ss + (size_t)(i0 + tt_n - 1 - tl) * mn + a * n;
-                const uint32_t *pcol = Ps + (size_t)tl * nq + c;
-                for (int r = 0; r < n; r++) {
-                    const unsigned long long pv = pcol[r * q];
+            // order i0+k at coefficient t0+s reads S row smin + (i0 + k + tt_n - 1 - s) = row top - s + k
+            const int top = i0 + tt_n - 1;
+            for (int r = 0; r < n; r++) {
+                const uint32_t *scol = Ss + a * n + r;      // row u at scol[u * mn]
+                const uint32_t *pcol = Ps + r * q + c0;     // coefficient s at pcol[s * nq]
+                uint32_t sw[WIN_IB];                        // row top - s + k in slot (k - s) & 7
 #pragma unroll
-                    for (int k = 0; k < WIN_IB; k++) acc[k] += pv * srow[k * mn + r];
-                    if (++cnt == KLAZY) {
+                for (int k = 0; k < WIN_IB; k++) sw[k] = scol[(size_t)(top + k) * mn];
+                for (int s0 = 0; s0 < tt_n; s0 += 8) {
 #pragma unroll
-                        for (int k = 0; k < WIN_IB; k++) acc[k] = red64(acc[k], mp);
-                        cnt = 0;
+                    for (int j = 0; j < 8; j++) {
+                        const int st = s0 + j;
+                        if (st < tt_n) {
+                            if (st > 0) sw[(8 - j) & 7] = scol[(size_t)(top - st) * mn];
+                            uint32_t pv[WIN_CB];
+                            ld4<VEC>(pcol + (size_t)st * nq, cv, pv);
+#pragma unroll
+                            for (int k = 0; k < WIN_IB; k++)
+#pragma unroll
+                                for (int u = 0; u < WIN_CB; u++) mac2(acc[k][u], sw[(k - j) & 7], pv[u]);
+                            if (++cnt == FOLDK) {
+#pragma unroll
+                                for (int k = 0; k < WIN_IB; k++)
+#pragma unroll
+                                    for (int u = 0; u < WIN_CB; u++) fold2w(acc[k][u], fc);
+                                cnt = 0;
+                            }
+                        }
                     }
                 }
             }
@@ -111,9 +194,30 @@ __global__ void __launch_bounds__(WIN_THREADS)
 #pragma unroll
             for (int k = 0; k < WIN_IB; k++) {
                 const int i = i0 + k;
-                if (i < bb) out[(size_t)(i * m + a) * q + c] = red64(acc[k], mp);
+#pragma unroll
+                for (int u = 0; u < WIN_CB; u++)
+                    if (i < bb && cv[u]) out[(size_t)(i * m + a) * q + c0 + u] = red64(acc2_u64(acc[k][u]), mp);
             }
         }
+    }
+}
+
+// Esum[x] = sum over the window blocks of Epart[b][x], mod p: 32 entries per
+// block, 8 groups of blocks per entry, then a shared-memory sum.
+__global__ void __launch_bounds__(256)
+    k_sum_parts(int nparts, int64_t E, const uint32_t *__restrict__ Epart, uint32_t *__restrict__ Esum, ModP mp) {
+    __shared__ unsigned long long red[8][32];
+    const int lx = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t x = (int64_t)blockIdx.x * 32 + lx;
+    unsigned long long v = 0;  // < 2^31 * nparts
+    if (x < E)
+        for (int b = g; b < nparts; b += 8) v += __ldg(Epart + (size_t)b * E + x);
+    red[g][lx] = v;
+    __syncthreads();
+    if (g == 0 && x < E) {
+#pragma unroll
+        for (int k = 1; k < 8; k++) v += red[k][lx];
+        Esum[x] = red64(v, mp);
     }
 }
 
@@ -548,23 +652,35 @@ __global__ void k_unscale(uint32_t *__restrict__ P, int n, int q, int64_t D, con
 }
 
 // ---- apply: P_new[t][r][c] = sum_{s <= degl[c]} sum_x P[t-s][r][x] Ml[s][x][c]
-// Block: TA coefficients; work item = (r, c, APP_TB consecutive coefficients).
 constexpr int APP_THREADS = 256;
-constexpr int APP_TB = 8;
+constexpr int APP_TB = 8;  // coefficients per thread
+constexpr int APP_CB = 4;  // columns per thread
+static_assert(APP_TB == 8 && APP_CB == 4, "the register window and 16-byte loads assume an 8 x 4 tile");
 
-template <int KLAZY>
+// P' = P Ml (the chunk transform, logical layout: coefficient s of column c
+// at Ml[s][.][c], zero above degl[c]), coefficients t0 .. t0 + TA - 1 of P' per
+// block.  Coefficients above the new maximal column degree (*dmax_dev) are
+// zero in P' and already zero in the target buffer (it held an older basis of
+// no larger degree), so blocks beyond it return at once.  A thread owns a
+// APP_TB x APP_CB tile (coefficients x columns) of one row r of P'.  For a
+// fixed x it walks s: the P residues of step s+1 are those of step s shifted
+// by one coefficient (circular register window, one new load per step), and
+// the APP_CB residues of Ml are one 16-byte load (VEC).
+template <int FOLDK, bool VEC>
 __global__ void __launch_bounds__(APP_THREADS)
     k_apply(const uint32_t *__restrict__ P, uint32_t *__restrict__ Pn, int n, int q,
             const uint32_t *__restrict__ Ml_g, const int32_t *__restrict__ degl_g, int bb, int64_t Dbound,
-            int TA, ModP mp) {
+            int TA, const int *__restrict__ dmax_dev, ModP mp) {
     extern __shared__ uint32_t sm[];
     uint32_t *Mls = sm;                               // (bb+1)*q*q
     uint32_t *Pss = Mls + (size_t)(bb + 1) * q * q;   // (TA + bb) * n * q
     __shared__ int degl[64];
+    const int64_t dlim = min64(Dbound, (int64_t)*dmax_dev);
     const int64_t t0 = (int64_t)blockIdx.x * TA;
-    if (t0 > Dbound) return;
-    const int ta = (int)min64(TA, Dbound + 1 - t0);
+    if (t0 > dlim) return;
+    const int ta = (int)min64(TA, dlim + 1 - t0);
     const int nq = n * q;
+    const uint32_t fc = mp.r1;  // 2^32 mod p
     for (int x = threadIdx.x; x < (bb + 1) * q * q; x += APP_THREADS) Mls[x] = Ml_g[x];
     for (int x = threadIdx.x; x < q; x += APP_THREADS) degl[x] = degl_g[x];
     const int64_t pbase = t0 - bb;  // Pss[u] holds P[pbase + u]
@@ -573,35 +689,60 @@ __global__ void __launch_bounds__(APP_THREADS)
         Pss[x] = t >= 0 ? P[(size_t)t * nq + x % nq] : 0u;
     }
     __syncthreads();
-    const int ntb = (ta + APP_TB - 1) / APP_TB;
-    for (int it = threadIdx.x; it < nq * ntb; it += APP_THREADS) {
-        const int rc = it % nq, tb = it / nq;
-        const int r = rc / q, c = rc % q;
-        const int tl0 = tb * APP_TB;
-        unsigned long long acc[APP_TB];
+    const int ntb = (ta + APP_TB - 1) / APP_TB, ncb = (q + APP_CB - 1) / APP_CB;
+    for (int it = threadIdx.x; it < ntb * n * ncb; it += APP_THREADS) {
+        const int cb = it % ncb, r = (it / ncb) % n, tb = it / (ncb * n);
+        const int c0 = cb * APP_CB, tl0 = tb * APP_TB;
+        bool cv[APP_CB];
+        int smax = 0;
 #pragma unroll
-        for (int k = 0; k < APP_TB; k++) acc[k] = 0;
+        for (int u = 0; u < APP_CB; u++) {
+            cv[u] = c0 + u < q;
+            if (cv[u]) smax = max(smax, degl[c0 + u]);
+        }
+        Acc2 acc[APP_TB][APP_CB];
+#pragma unroll
+        for (int k = 0; k < APP_TB; k++)
+#pragma unroll
+            for (int u = 0; u < APP_CB; u++) acc[k][u] = Acc2{0u, 0u};
         int cnt = 0;
-        const int smax = degl[c];
-        for (int s2 = 0; s2 <= smax; s2++) {
-            // P[t0 + tl0 + k - s2] = Pss[tl0 + k + bb - s2]
-            const uint32_t *prow = Pss + (size_t)(tl0 + bb - s2) * nq + r * q;
-            const uint32_t *mcol = Mls + (size_t)s2 * q * q + c;
-            for (int x = 0; x < q; x++) {
-                const unsigned long long mv = mcol[x * q];
+        // coefficient t0 + tl0 + k - s of P is Pss row top - s + k
+        const int top = tl0 + bb;
+        for (int x = 0; x < q; x++) {
+            const uint32_t *pc = Pss + r * q + x;          // row u at pc[u * nq]
+            const uint32_t *mc = Mls + (size_t)x * q + c0;  // coefficient s at mc[s * q * q]
+            uint32_t pw[APP_TB];                            // row top - s + k in slot (k - s) & 7
 #pragma unroll
-                for (int k = 0; k < APP_TB; k++) acc[k] += mv * prow[(size_t)k * nq + x];
-                if (++cnt == KLAZY) {
+            for (int k = 0; k < APP_TB; k++) pw[k] = pc[(size_t)(top + k) * nq];
+            for (int s0 = 0; s0 <= smax; s0 += 8) {
 #pragma unroll
-                    for (int k = 0; k < APP_TB; k++) acc[k] = red64(acc[k], mp);
-                    cnt = 0;
+                for (int j = 0; j < 8; j++) {
+                    const int st = s0 + j;
+                    if (st <= smax) {
+                        if (st > 0) pw[(8 - j) & 7] = pc[(size_t)(top - st) * nq];
+                        uint32_t mv[APP_CB];
+                        ld4<VEC>(mc + (size_t)st * q * q, cv, mv);
+#pragma unroll
+                        for (int k = 0; k < APP_TB; k++)
+#pragma unroll
+                            for (int u = 0; u < APP_CB; u++) mac2(acc[k][u], pw[(k - j) & 7], mv[u]);
+                        if (++cnt == FOLDK) {
+#pragma unroll
+                            for (int k = 0; k < APP_TB; k++)
+#pragma unroll
+                                for (int u = 0; u < APP_CB; u++) fold2w(acc[k][u], fc);
+                            cnt = 0;
+                        }
+                    }
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < APP_TB; k++) {
             const int tl = tl0 + k;
-            if (tl < ta) Pn[(size_t)(t0 + tl) * nq + rc] = red64(acc[k], mp);
+#pragma unroll
+            for (int u = 0; u < APP_CB; u++)
+                if (tl < ta && cv[u]) Pn[(size_t)(t0 + tl) * nq + r * q + c0 + u] = red64(acc2_u64(acc[k][u]), mp);
         }
     }
 }
@@ -776,8 +917,13 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         WR_CUDA(cudaStreamSynchronize(s));
     }
     const bool lazy16 = mp.lazy >= 16;
-    auto *kwin = lazy16 ? k_window<16> : k_window<4>;
-    auto *kapp = lazy16 ? k_apply<16> : k_apply<4>;
+    const bool vec = q % 4 == 0;
+    auto *kwin = lazy16 ? (vec ? k_window<14, true> : k_window<14, false>)
+                        : (vec ? k_window<2, true> : k_window<2, false>);
+    auto *kapp = lazy16 ? (vec ? k_apply<14, true> : k_apply<14, false>)
+                        : (vec ? k_apply<2, true> : k_apply<2, false>);
+    DevBuf Esum;
+    WR_TRY(dev_alloc(ctx, Esum, sizeof(uint32_t) * (size_t)bmax * m * q));
     using LocalFn = void (*)(int, int, int, int, int, const uint32_t *, uint32_t *, int32_t *, uint32_t *, int32_t *,
                              int *, uint32_t *, ModP);
     LocalFn kloc;
@@ -808,16 +954,24 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         kwin<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, n, q, Pcur, k0, bb, TT, tper,
                                                                 dmax.as<int>(), Epart.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
+        const uint32_t *Ewin = Epart.as<uint32_t>();
+        if (nparts > 1) {
+            const int64_t E = (int64_t)bb * m * q;
+            k_sum_parts<<<(unsigned)((E + 31) / 32), 256, 0, s>>>(nparts, E, Epart.as<uint32_t>(),
+                                                                  Esum.as<uint32_t>(), mp);
+            WR_LAUNCHED(ctx);
+            Ewin = Esum.as<uint32_t>();
+        }
         if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
         kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(
-            m, n, q, bb, nparts, Epart.as<uint32_t>(), qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
+            m, n, q, bb, 1, Ewin, qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
             degl.as<int32_t>(), dmax.as<int>(), scale.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
         if (prof) WR_CUDA(cudaEventRecord(pe[2], s));
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
         const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
         kapp<<<(unsigned)((Dnew + TA) / TA), APP_THREADS, apply_bytes(TA, bb), s>>>(
-            Pcur, Pnext, n, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, mp);
+            Pcur, Pnext, n, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, dmax.as<int>(), mp);
         WR_LAUNCHED(ctx);
         if (prof) {
             WR_CUDA(cudaEventRecord(pe[3], s));
