@@ -239,19 +239,43 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
     for (int b = 0; b < NV; b++) acc[b] = 0;
     if (slot < per) {
+        // U rows in flight per thread; at most KLAZY products per accumulator
+        // between reductions (acc < p after one)
+        constexpr int U = NV <= 8 ? 4 : (NV <= 16 ? 2 : 1);
+        const int64_t stride = (int64_t)gridDim.x * per;
+        int64_t r = (int64_t)blockIdx.x * per + slot;
         int cnt = 0;
-        for (int64_t r = (int64_t)blockIdx.x * per + slot; r < N; r += (int64_t)gridDim.x * per) {
-            const unsigned long long xv =
-                GRAM ? mulm(__ldg(xh + r), __ldg(t + r * NV + a), mp) : __ldg(xh + r * m + a);
-            uint32_t tv[NV];
-            ldv<NV>(t + r * NV, tv);
+        for (; r + (U - 1) * stride < N; r += U * stride) {
+            uint32_t xs[U], tv[U][NV];
 #pragma unroll
-            for (int b = 0; b < NV; b++) acc[b] += xv * tv[b];
-            if (++cnt == KLAZY) {
+            for (int u = 0; u < U; u++) {
+                const int64_t ru = r + u * stride;
+                xs[u] = GRAM ? mulm(__ldg(xh + ru), __ldg(t + ru * NV + a), mp) : __ldg(xh + ru * m + a);
+                ldv<NV>(t + ru * NV, tv[u]);
+            }
+            if (cnt + U > KLAZY) {
 #pragma unroll
                 for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
                 cnt = 0;
             }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int b = 0; b < NV; b++) acc[b] += (unsigned long long)xs[u] * tv[u][b];
+            cnt += U;
+        }
+        for (; r < N; r += stride) {
+            const uint32_t xv = GRAM ? mulm(__ldg(xh + r), __ldg(t + r * NV + a), mp) : __ldg(xh + r * m + a);
+            uint32_t tv[NV];
+            ldv<NV>(t + r * NV, tv);
+            if (cnt + 1 > KLAZY) {
+#pragma unroll
+                for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
+                cnt = 0;
+            }
+#pragma unroll
+            for (int b = 0; b < NV; b++) acc[b] += (unsigned long long)xv * tv[b];
+            cnt++;
         }
 #pragma unroll
         for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
@@ -412,7 +436,7 @@ wr_status launch_project(wr_ctx *ctx, int64_t N, int m, int n, int nv, const uin
                          int64_t L = INT64_MAX) {
     const int per = PROJ_THREADS / m;
     const int64_t need = std::max<int64_t>((N + per - 1) / per, 1);
-    const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ctx->num_sms * 4);
+    const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ctx->num_sms * 2);
 #define WR_PROJ_CASE(NVV)                                                                                    \
     case NVV:                                                                                                \
         if (gram)                                                                                            \
