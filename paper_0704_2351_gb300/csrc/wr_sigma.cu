@@ -55,43 +55,6 @@ constexpr int WIN_IB = 8;  // orders per thread
 constexpr int WIN_CB = 4;  // columns per thread
 static_assert(WIN_IB == 8 && WIN_CB == 4, "the register window and 16-byte loads assume an 8 x 4 tile");
 
-// x = hi 2^32 + lo is congruent to hi (2^32 mod p) + lo; folded twice a 64-bit
-// accumulator drops below 2^60 + 2^33 (p < 2^30) or 2^62 + 2^33 (p < 2^31),
-// leaving room for FOLDK = 14 (or 2) more products below p^2 before the next
-// fold.  Two 32x32+64-bit multiply-adds instead of a reduction mod p.
-// d = a b + c in one 32x32 -> 64-bit multiply-add
-__device__ __forceinline__ unsigned long long madw(uint32_t a, uint32_t b, unsigned long long c) {
-    unsigned long long d;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return d;
-}
-
-__device__ __forceinline__ unsigned long long fold2(unsigned long long x, uint32_t c) {
-    x = madw((uint32_t)(x >> 32), c, (unsigned long long)(uint32_t)x);
-    return madw((uint32_t)(x >> 32), c, (unsigned long long)(uint32_t)x);
-}
-
-// A 64-bit accumulator kept as two 32-bit words: (hi, lo) += a b as two
-// multiply-adds chained through the carry flag.
-struct Acc2 {
-    uint32_t lo, hi;
-};
-__device__ __forceinline__ void mac2(Acc2 &acc, uint32_t a, uint32_t b) {
-    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
-        : "+r"(acc.lo), "+r"(acc.hi)
-        : "r"(a), "r"(b));
-}
-__device__ __forceinline__ unsigned long long acc2_u64(const Acc2 &a) {
-    return ((unsigned long long)a.hi << 32) | a.lo;
-}
-// fold2 on the two-word form
-__device__ __forceinline__ void fold2w(Acc2 &a, uint32_t c) {
-    const unsigned long long x = fold2(acc2_u64(a), c);
-    a.lo = (uint32_t)x;
-    a.hi = (uint32_t)(x >> 32);
-}
-
-
 // Four consecutive residues from shared memory (one 16-byte load when VEC),
 // zero where the column is out of range.
 template <bool VEC>

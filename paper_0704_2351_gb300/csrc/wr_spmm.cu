@@ -220,7 +220,7 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
 // symmetric projection X = Y turns every term into one (Section 2.2).
 constexpr int PROJ_THREADS = 256;
 
-template <int NV, int KLAZY, bool GRAM>
+template <int NV, int FOLDK, bool GRAM>
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project(int64_t N, int m, int n, const uint32_t *__restrict__ xh, const uint32_t *__restrict__ t,
               unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, int tmul, int toff,
@@ -235,50 +235,54 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     const bool pow2 = (32 % m) == 0;
     const int per = PROJ_THREADS / m;  // rows per block step
     const int a = tid % m, slot = tid / m;
+    const uint32_t fc = mp.r1;  // 2^32 mod p
     unsigned long long acc[NV];
+    {
+        // two-word accumulators, folded by 2^32 mod p every FOLDK products
+        Acc2 ac[NV];
 #pragma unroll
-    for (int b = 0; b < NV; b++) acc[b] = 0;
-    if (slot < per) {
-        // U rows in flight per thread; at most KLAZY products per accumulator
-        // between reductions (acc < p after one)
-        constexpr int U = NV <= 8 ? 4 : (NV <= 16 ? 2 : 1);
-        const int64_t stride = (int64_t)gridDim.x * per;
-        int64_t r = (int64_t)blockIdx.x * per + slot;
-        int cnt = 0;
-        for (; r + (U - 1) * stride < N; r += U * stride) {
-            uint32_t xs[U], tv[U][NV];
+        for (int b = 0; b < NV; b++) ac[b] = Acc2{0u, 0u};
+        if (slot < per) {
+            // U rows in flight per thread.  GRAM: xh holds the weights in
+            // Montgomery form, so mont_mul(xh[r], T[r][a]) = w_r T[r][a].
+            constexpr int U = NV <= 8 ? 4 : (NV <= 16 ? 2 : 1);
+            const int64_t stride = (int64_t)gridDim.x * per;
+            int64_t r = (int64_t)blockIdx.x * per + slot;
+            int cnt = 0;
+            for (; r + (U - 1) * stride < N; r += U * stride) {
+                uint32_t xs[U], tv[U][NV];
 #pragma unroll
-            for (int u = 0; u < U; u++) {
-                const int64_t ru = r + u * stride;
-                xs[u] = GRAM ? mulm(__ldg(xh + ru), __ldg(t + ru * NV + a), mp) : __ldg(xh + ru * m + a);
-                ldv<NV>(t + ru * NV, tv[u]);
+                for (int u = 0; u < U; u++) {
+                    const int64_t ru = r + u * stride;
+                    xs[u] = GRAM ? mont_mul(__ldg(xh + ru), __ldg(t + ru * NV + a), mp) : __ldg(xh + ru * m + a);
+                    ldv<NV>(t + ru * NV, tv[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+#pragma unroll
+                    for (int b = 0; b < NV; b++) mac2(ac[b], xs[u], tv[u][b]);
+                    if (++cnt == FOLDK) {
+#pragma unroll
+                        for (int b = 0; b < NV; b++) fold2w(ac[b], fc);
+                        cnt = 0;
+                    }
+                }
             }
-            if (cnt + U > KLAZY) {
+            for (; r < N; r += stride) {
+                const uint32_t xv = GRAM ? mont_mul(__ldg(xh + r), __ldg(t + r * NV + a), mp) : __ldg(xh + r * m + a);
+                uint32_t tv[NV];
+                ldv<NV>(t + r * NV, tv);
 #pragma unroll
-                for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
-                cnt = 0;
+                for (int b = 0; b < NV; b++) mac2(ac[b], xv, tv[b]);
+                if (++cnt == FOLDK) {
+#pragma unroll
+                    for (int b = 0; b < NV; b++) fold2w(ac[b], fc);
+                    cnt = 0;
+                }
             }
-#pragma unroll
-            for (int u = 0; u < U; u++)
-#pragma unroll
-                for (int b = 0; b < NV; b++) acc[b] += (unsigned long long)xs[u] * tv[u][b];
-            cnt += U;
         }
-        for (; r < N; r += stride) {
-            const uint32_t xv = GRAM ? mulm(__ldg(xh + r), __ldg(t + r * NV + a), mp) : __ldg(xh + r * m + a);
-            uint32_t tv[NV];
-            ldv<NV>(t + r * NV, tv);
-            if (cnt + 1 > KLAZY) {
 #pragma unroll
-                for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
-                cnt = 0;
-            }
-#pragma unroll
-            for (int b = 0; b < NV; b++) acc[b] += (unsigned long long)xv * tv[b];
-            cnt++;
-        }
-#pragma unroll
-        for (int b = 0; b < NV; b++) acc[b] = red64(acc[b], mp);
+        for (int b = 0; b < NV; b++) acc[b] = red64(acc2_u64(ac[b]), mp);
     }
     if (pow2) {
         // lanes of a warp with the same a hold the same (a, b) entries:
@@ -330,7 +334,7 @@ __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t
 // T0 = D1 Y (padded to nv columns with zeros; columns ycol0.. of a Y with
 // ystride columns), d1sq = D1^2, and Xh = D1^{-1} X (X drawn with tag xtag,
 // xwidth columns) or the Gram weights D1^{-2} (symmetric projection X = Y
-// over the whole Y: S_2k = V_k^T V_k with T_k = D1 V_k).
+// over the whole Y: S_2k = V_k^T V_k with T_k = D1 V_k; Montgomery form).
 __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64_t xtag, int xwidth, int ystride,
                           int ycol0, int gram, const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
                           uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, ModP mp) {
@@ -345,7 +349,7 @@ __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64
         t0[i * nv + b] = mulm(d, yv, mp);
     }
     if (gram) {
-        xh[i] = mulm(dinv, dinv, mp);
+        xh[i] = to_mont(mulm(dinv, dinv, mp), mp);  // Montgomery form for the Gram projection
         return;
     }
     for (int a = 0; a < m; a++) {
@@ -354,11 +358,11 @@ __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64
     }
 }
 
-// out = d^{-1}, elementwise (the Gram weights D2^{-1} of the odd terms of
+// out = d^{-1} R mod p, elementwise (the Gram weights D2^{-1} of the odd terms of
 // the symmetric projection: S_2k+1 = W^T D2^{-1} W with W = D2 A D1 V_k)
 __global__ void k_inv_diag(int64_t len, const uint32_t *__restrict__ d, uint32_t *__restrict__ out, ModP mp) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < len) out[i] = invm(d[i], mp);
+    if (i < len) out[i] = to_mont(invm(d[i], mp), mp);  // Montgomery form for the Gram projection
 }
 
 // out (N x nv, padded) = D1 in (N x width)
@@ -420,11 +424,11 @@ template <int NV, bool GRAM>
 void launch_project_t(wr_ctx *ctx, unsigned grid, int64_t N, int m, int n, const uint32_t *xh,
                       const uint32_t *t, unsigned long long *s_raw, const int *term_counter, int tmul, int toff,
                       int64_t L, const ModP &mp) {
-    if (mp.lazy >= 16)
-        k_project<NV, 16, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
+    if (mp.lazy >= 16)  // p < 2^30
+        k_project<NV, 14, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
                                                                          toff, L, mp);
     else
-        k_project<NV, 4, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
+        k_project<NV, 2, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
                                                                         toff, L, mp);
 }
 
