@@ -12,6 +12,7 @@ paper defines it:
 
 * sequence()            S_i = X^T A~^i Y mod p, i < L           (Section 2.1; Section 2.4 step 2)
 * blackbox_apply()      A~ = D1 A^T D2 A D1 (or D1 A D2 A^T D1)   (Section 2.3, Section 2.4 step 1)
+* blackbox_apply_rows() selected rows of A~ v, one at a time      (same; spot checks at full size)
 * mbasis()              sigma-basis of [S(x) | -I]               (Section 2.3 "sigma-basis computations")
 * generator()           minimal right matrix generator F          (Section 2.4 step 3)
 * rank_readout()        r = deg det F - codeg det F              (Section 2.4 step 4)
@@ -199,6 +200,54 @@ def blackbox_apply(A, p: int, side: int, d1: np.ndarray, d2: np.ndarray, v: np.n
     d2 = _c(d2, np.uint32)
     load().or_blackbox_apply(A.rows, A.cols, _p(rp), _p(ci), _p(va), p, side, _p(d1), _p(d2), w, _p(v))
     return v.reshape(N, w)
+
+
+def blackbox_apply_rows(A, p: int, side: int, d1: np.ndarray, d2: np.ndarray, v: np.ndarray,
+                        rows) -> np.ndarray:
+    """Selected output rows of A~ v (Section 2.3's preconditioned black box),
+    each computed on its own from the definition, for spot checks of full-size
+    applications.  side 1 (N = rows): A~ = D1 A D2 A^T D1, so
+    (A~ v)[x] = d1[x] sum_{y in row x of A} A[x,y] d2[y] sum_{z in col y} A[z,y] d1[z] v[z];
+    side 0 (N = cols): the same with A^T in place of A.  Plain numpy, one
+    residue product reduced mod p at a time."""
+    v = np.asarray(v, dtype=np.uint64)
+    if v.ndim == 1:
+        v = v[:, None]
+    d1 = np.asarray(d1, dtype=np.uint64)
+    d2 = np.asarray(d2, dtype=np.uint64)
+    rp = np.asarray(A.rowptr, dtype=np.int64)
+    ci = np.asarray(A.colidx, dtype=np.int64)
+    va = np.asarray(A.vals, dtype=np.int64)
+    ri = np.repeat(np.arange(A.rows, dtype=np.int64), np.diff(rp))
+    order = np.argsort(ci, kind="stable")  # column-major view of A
+    cp = np.zeros(A.cols + 1, dtype=np.int64)
+    np.add.at(cp, ci + 1, 1)
+    cp = np.cumsum(cp)
+    c_rows, c_vals = ri[order], va[order]
+
+    def row_of_A(x):
+        return ci[rp[x]:rp[x + 1]], va[rp[x]:rp[x + 1]]
+
+    def col_of_A(y):
+        return c_rows[cp[y]:cp[y + 1]], c_vals[cp[y]:cp[y + 1]]
+
+    # M = A (side 1) or A^T (side 0): rows of M and columns of M
+    m_row, m_col = (row_of_A, col_of_A) if side == 1 else (col_of_A, row_of_A)
+    P = np.uint64(p)
+    out = np.zeros((len(rows), v.shape[1]), dtype=np.uint64)
+    for k, x in enumerate(rows):
+        ys, ay = m_row(int(x))
+        acc = np.zeros(v.shape[1], dtype=np.uint64)
+        for y, a in zip(ys, ay):
+            zs, az = m_col(int(y))
+            u = np.zeros(v.shape[1], dtype=np.uint64)
+            for z, b in zip(zs, az):
+                t = (d1[z] * v[z]) % P                          # d1[z] v[z]
+                u = (u + (np.uint64(int(b) % p) * t) % P) % P   # + A[z,y] d1[z] v[z]
+            w = (d2[y] * u) % P
+            acc = (acc + (np.uint64(int(a) % p) * w) % P) % P
+        out[k] = (d1[x] * acc) % P
+    return out.astype(np.uint32)
 
 
 def sequence(A, setup: Setup, L: Optional[int] = None, return_last: bool = False):

@@ -430,3 +430,29 @@ def test_config1_full_size(wr, ctx):
     ref = oracle.blackbox_apply(A, p, 0, st.D1, st.D2, v)
     assert np.array_equal(from_dev(dout), ref)
     wr.wr_matrix_free(mat)
+
+
+# ------------------------------------------------------------------ full size: config 2
+
+def test_config2_full_size_spot_checks(wr, ctx):
+    """1,900,000 x 1,950,000, ~37M nnz, block 32 x 32, p = 2147483629 (rows
+    side, N = 1.9M): one black-box application at full size checked on 64
+    sampled output rows computed one by one, and the first two terms of the
+    sequence against the oracle's literal loop."""
+    A = synth.config2()
+    p, m, n, seed = 2147483629, 32, 32, synth.SEED_BASE + 2
+    st = oracle.Setup(A, p, m, n, seed)
+    assert st.side == 1 and st.N == 1900000
+    mat = load(wr, ctx, A)
+    rng = np.random.default_rng(2)
+    v = rng.integers(0, p, size=(st.N, n)).astype(np.uint32)
+    dout = torch.empty((st.N, n), dtype=torch.int32, device="cuda")
+    wr.wr_blackbox_apply_device(ctx, mat, wr.make_params(p, 1, n, seed), to_dev(v), dout, n)
+    got = from_dev(dout)
+    rows = np.sort(rng.choice(st.N, 64, replace=False))
+    assert np.array_equal(got[rows], oracle.blackbox_apply_rows(A, p, st.side, st.D1, st.D2, v, rows))
+    L = 2
+    dS = torch.empty((L, m, n), dtype=torch.int32, device="cuda")
+    wr.wr_sequence_device(ctx, mat, wr.make_params(p, m, n, seed), dS, L)
+    assert np.array_equal(from_dev(dS).reshape(L, m, n), oracle.sequence(A, st, L))
+    wr.wr_matrix_free(mat)

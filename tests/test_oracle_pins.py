@@ -500,3 +500,20 @@ def test_table_rtime_iteration_rule():
         if r % pp == 0:
             assert oracle.seq_length(r, pp, pp) == itp
     assert oracle.seq_length(1800, 1, 1) == 3602
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_blackbox_apply_rows_equals_full_application(side):
+    """The row-by-row spot check equals the whole application (itself pinned
+    to dense products), on both sides, with heavy rows and columns."""
+    p = 2147483629
+    A = synth.planted_sparse(140, 120, 100, row_len=6, seed=13 + side)
+    rng = np.random.default_rng(side)
+    N = A.cols if side == 0 else A.rows
+    M = A.rows if side == 0 else A.cols
+    d1 = oracle.derive_diag(9, 3, N, p)
+    d2 = oracle.derive_diag(9, 4, M, p)
+    v = rng.integers(0, p, size=(N, 5)).astype(np.uint32)
+    full = oracle.blackbox_apply(A, p, side, d1, d2, v)
+    rows = rng.choice(N, 25, replace=False)
+    assert np.array_equal(oracle.blackbox_apply_rows(A, p, side, d1, d2, v, rows), full[rows])
