@@ -344,6 +344,7 @@ def run_sigma_only(args):
     deg = torch.empty(q, dtype=torch.int32, device="cuda")
     ctx = wr.wr_create(0)
     wr.wr_set_profiling(ctx, True)
+    wr.wr_set_sigma_chunk(ctx, args.sigma_chunk)
     for _ in range(args.warmup):
         wr.wr_sigma_basis_device(ctx, S, L, m, n, p, P, deg, L + 1)
     torch.cuda.synchronize()
@@ -353,7 +354,7 @@ def run_sigma_only(args):
     torch.cuda.synchronize()
     ms = 1e3 * (time.perf_counter() - t) / max(args.steps, 1)
     tm = wr.wr_last_timings(ctx)
-    print(json.dumps({"only": "sigma", "L": L, "block": [m, n], "ms_per_sigma_basis": ms,
+    print(json.dumps({"only": "sigma", "L": L, "block": [m, n], "chunk": args.sigma_chunk, "ms_per_sigma_basis": ms,
                       "window_ms": tm["sigma_window_ms"], "local_ms": tm["sigma_local_ms"],
                       "apply_ms": tm["sigma_apply_ms"]}), flush=True)
     wr.wr_destroy(ctx)
@@ -402,6 +403,7 @@ def main():
                     help="only ingest + black-box applications (for profiler captures)")
     ap.add_argument("--only-sigma", action="store_true",
                     help="only the sigma-basis on a random sequence of the workload's shape")
+    ap.add_argument("--sigma-chunk", type=int, default=0, help="orders per sigma-basis chunk (0: automatic)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the one-matrix time-to-rank line (default); batch / serve: batched or "
                          "served against plain time-to-rank")

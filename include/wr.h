@@ -108,6 +108,12 @@ const char *wr_last_error(void);
 /* Turn per-kernel CUDA-event sampling of the SpMM passes on (1) or off (0). */
 wr_status wr_set_profiling(wr_ctx *ctx, int on);
 wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out);
+/* Orders per chunk of the blocked sigma-basis (1..64; 0 = automatic).  The
+ * result does not depend on it; the time does: each chunk runs its M-Basis
+ * steps in one thread block, whose work per order grows with the chunk, while
+ * the discrepancy and product kernels around it do the same total work for
+ * any chunk size and cost a few launches per chunk. */
+wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
 
 /* ---------------------------------------------------------------- matrices */
 

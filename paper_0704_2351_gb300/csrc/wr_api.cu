@@ -186,6 +186,13 @@ extern "C" wr_status wr_set_profiling(wr_ctx *ctx, int on) {
     return WR_OK;
 }
 
+extern "C" wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if (orders < 0 || orders > 64) return fail(WR_EINVAL, "sigma-basis chunk must be in 0..64 (0: automatic)");
+    ctx->sigma_chunk = orders;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out) {
     if (!ctx || !out) return fail(WR_EINVAL, "null argument");
     *out = ctx->last;

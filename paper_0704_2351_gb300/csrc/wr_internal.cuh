@@ -297,6 +297,7 @@ struct wr_ctx {
     bool profiling = false;
     int64_t launches = 0;   // kernels launched through this context (graph replays: nodes per replay)
     int batch_slots = 8;    // slots (streams + host threads) of wr_rank_batch
+    int sigma_chunk = 0;    // orders per sigma-basis chunk (0: automatic)
     wr_timings last{};
 };
 

@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(256)
 // holds its coefficient s at row base[c] + s; the other warps use per-order
 // snapshots of sh and base.
 constexpr int LOCAL_THREADS = 1024;
+// orders per chunk unless the context sets it (wr_set_sigma_chunk)
+constexpr int SIGMA_CHUNK_DEFAULT = 64;
 constexpr int BAR_T0 = 1, BAR_RR0 = 3;  // ids BAR_T0 + (i & 1), BAR_RR0 + (i & 1)
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
@@ -859,7 +861,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         return sizeof(uint32_t) * ((size_t)TT * nq + (size_t)(nib * WIN_IB + TT - 1) * m * n);
     };
     auto apply_bytes = [&](int ta, int b) { return sizeof(uint32_t) * ((size_t)(b + 1) * q * q + (size_t)(ta + b) * nq); };
-    int bmax = 64, TT = 32, TA = 64;
+    int bmax = ctx->sigma_chunk > 0 ? std::min(ctx->sigma_chunk, 64) : SIGMA_CHUNK_DEFAULT, TT = 32, TA = 64;
     for (;;) {
         while (TT > 4 && window_bytes(TT, bmax) > budget) TT /= 2;
         while (TA > APP_TB && apply_bytes(TA, bmax) > budget) TA /= 2;
