@@ -286,6 +286,145 @@ struct RowTransform {
     }
 };
 
+// Warp 0 of k_local when q <= 16: two lanes per column.  Lane L holds
+// column j = L & 15 and half h = L >> 4 of it: discrepancy rows
+// h*MM/2 .. h*MM/2 + MM/2 - 1 and the same range of its transform row, so a
+// pivot step costs each lane half the Montgomery updates of the one-lane
+// layout.  The elimination, the published transform and the bookkeeping are
+// those of the one-lane path (same pivots, same fraction-free values).
+template <int MM>
+__device__ __forceinline__ void local_warp0_two_lane(int m, int q, int bb, const uint32_t *Es, uint32_t *Tb, int tw,
+                                                     int *snap, int snapw, int *deg, int *degl, int *sh, int *base,
+                                                     uint32_t *scale_g, int nth, const ModP &mp) {
+    constexpr int HM = MM / 2;
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 15, h = lane >> 4;
+    const bool v = j < q;
+    const int mq = m * q;
+    uint32_t scum = mp.r1;  // cumulative column scale over the chunk (Montgomery form)
+    for (int i = 0; i < bb; i++) {
+        uint32_t *F = Tb + (i & 1) * tw;
+        uint32_t *dg = F + mq;
+        int *sn = snap + (i & 1) * snapw;
+        int *s_sh = sn, *s_base = sn + q, *s_isp = sn + 2 * q, *s_pc = sn + 3 * q;
+        uint32_t d[HM], tp[HM], sc = mp.r1;
+        int rk = 1 << 20;
+        if (v) {
+            int r0 = 0;
+            const int dj = deg[j];
+            for (int c2 = 0; c2 < q; c2++) {
+                const int dc2 = deg[c2];
+                r0 += (dc2 < dj || (dc2 == dj && c2 < j)) ? 1 : 0;
+            }
+            rk = r0;
+            if (h == 0) {
+                s_isp[j] = 0;
+                s_sh[j] = sh[j];
+                s_base[j] = base[j];
+            }
+        }
+        {
+            const uint32_t *er = Es + (size_t)(i - (v ? sh[j] : 0)) * mq + (v ? j : 0);
+#pragma unroll
+            for (int r = 0; r < HM; r++) {
+                const int a2 = h * HM + r;
+                d[r] = (v && a2 < m) ? to_mont(er[a2 * q], mp) : 0u;
+                tp[r] = 0u;
+            }
+        }
+        int np = 0;
+        for (int step = 0; step < q; step++) {
+            const bool mine = rk == step;
+            const unsigned who = __ballot_sync(0xffffffffu, mine);
+            const int src0 = __ffs(who) - 1;  // the h = 0 lane of the current column
+            int frl = -1;
+            if (mine) {
+#pragma unroll
+                for (int r = HM - 1; r >= 0; r--)
+                    if (d[r] != 0) frl = h * HM + r;
+            }
+            const int fr0 = __shfl_sync(0xffffffffu, frl, src0);
+            const int fr1 = __shfl_sync(0xffffffffu, frl, src0 + 16);
+            const int fr = fr0 >= 0 ? fr0 : fr1;
+            if (fr < 0) continue;
+            const int hp = fr / HM, rp = fr - hp * HM;
+            const uint32_t sc_cur = __shfl_sync(0xffffffffu, sc, src0);
+            uint32_t pv[HM], pt[HM];
+#pragma unroll
+            for (int r = 0; r < HM; r++) {
+                pv[r] = __shfl_sync(0xffffffffu, d[r], src0 + 16 * h);
+                pt[r] = __shfl_sync(0xffffffffu, tp[r], src0 + 16 * h);
+            }
+            uint32_t x = 0;  // this lane's residue at pivot row offset rp
+#pragma unroll
+            for (int r = 0; r < HM; r++)
+                if (r == rp) x = d[r];
+            const uint32_t dc = __shfl_sync(0xffffffffu, x, src0 + 16 * hp);
+            const uint32_t dj = __shfl_sync(0xffffffffu, x, j + 16 * hp);
+            if (rk > step && rk < (1 << 20) && dj != 0) {
+                // col <- dc col - dj pivot: one Montgomery reduction of
+                // dc*x + (p - dj)*y < 2 p^2 < p 2^32 per entry
+                const uint64_t ndj = mp.p - dj;
+#pragma unroll
+                for (int r = 0; r < HM; r++) d[r] = mont_redc((uint64_t)dc * d[r] + ndj * pv[r], mp);
+#pragma unroll
+                for (int r = 0; r < HM; r++) {
+                    const int t = h * HM + r;
+                    if (t < np) tp[r] = mont_redc((uint64_t)dc * tp[r] + ndj * pt[r], mp);
+                    else if (t == np) tp[r] = mont_redc(ndj * sc_cur, mp);
+                }
+                sc = mont_mul(sc, dc, mp);
+            }
+            if (lane == 0) {
+                s_pc[np] = src0;
+                s_isp[src0] = 1;
+            }
+            np++;
+        }
+        __syncwarp();
+        // publish the transform (normal form) and the local degree bounds
+        int dl = 0;
+        if (v) {
+            dl = degl[j];
+#pragma unroll
+            for (int r = 0; r < HM; r++) {
+                const int t = h * HM + r;
+                if (t < np) {
+                    const uint32_t val = from_mont(tp[r], mp);
+                    F[t * q + j] = val;
+                    if (val) dl = max(dl, degl[s_pc[t]]);
+                }
+            }
+            if (h == 0) dg[j] = from_mont(sc, mp);
+            scum = mont_mul(scum, sc, mp);
+        }
+        dl = max(dl, __shfl_xor_sync(0xffffffffu, dl, 16));  // both halves of the column
+        int dmx = dl;
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) dmx = max(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
+        if (lane == 0) {
+            sn[3 * q + m] = np;
+            sn[3 * q + m + 1] = dmx;
+        }
+        __syncwarp();
+        named_arrive(BAR_T0 + (i & 1), nth);
+        // ---- bookkeeping of order i: local degrees, pivots times x
+        if (v && h == 0) degl[j] = dl;
+        __syncwarp();
+        for (int t = lane; t < np; t += 32) {
+            const int c = s_pc[t];
+            deg[c] += 1;
+            degl[c] += 1;
+            sh[c] += 1;
+            base[c] -= 1;
+        }
+        __syncwarp();
+        // ---- the next discrepancy (rows i, i+1) must be done
+        named_sync(BAR_RR0 + (i & 1), nth);
+    }
+    if (v && h == 0) scale_g[j] = mont_mul(scale_g[j], scum, mp);
+}
+
 template <int MM, int CPL, int KLAZY>
 __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
     k_local(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
@@ -339,7 +478,9 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
     const int rpw = 32 / W2;
     const int grp = lane / W2, col = lane % W2;
 
-    if (warp == 0) {
+    if (warp == 0 && CPL == 1 && q <= 16) {
+        local_warp0_two_lane<MM>(m, q, bb, Es, Tb, tw, snap, snapw, deg, degl, sh, base, scale_g, nth, mp);
+    } else if (warp == 0) {
         uint32_t scum[CPL];  // cumulative column scales over the chunk (Montgomery form)
 #pragma unroll
         for (int k = 0; k < CPL; k++) scum[k] = mp.r1;
