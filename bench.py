@@ -285,7 +285,7 @@ def run_serve(args):
         srv = wr.wr_server_start(ctx, max_slots=args.slots, hbm_budget=args.hbm_budget, queue_cap=1 << 20)
         t0 = time.perf_counter()
         tickets = []
-        for a, h, prm in zip(arrivals, handles, params):
+        for a, h, prm in zip(arrivals, handles[:len(arrivals)], params[:len(arrivals)]):
             d = a - (time.perf_counter() - t0)
             if d > 0:
                 time.sleep(d)
@@ -297,21 +297,24 @@ def run_serve(args):
             wr.wr_result_free(res)
         st = wr.wr_server_stats(srv)
         wr.wr_server_stop(srv)
-        assert got == ranks, "served ranks differ from the plain ones"
+        assert got == ranks[:len(arrivals)], "served ranks differ from the plain ones"
         return st
 
     arr = [r["t"] for r in trace]
     out = {}
     for name, scale in [("trace_rate", 1.0), ("rate_0.7x_plain_capacity", None)]:
         if scale is None:
+            # the first quarter of the trace, arrivals stretched to 0.7x the
+            # plain capacity (the whole trace would take n / (0.7 capacity))
+            k = max(20, len(arr) // 4)
             lam = 0.7 * cap_plain
-            a = [x * args.rate / lam for x in arr]
+            a = [x * args.rate / lam for x in arr[:k]]
         else:
             lam = args.rate
             a = arr
         st = served(a)
         lat, thr = plain_latency(a)
-        out[name] = {"arrival_rate_rps": lam,
+        out[name] = {"arrival_rate_rps": lam, "requests": len(a),
                      "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                                 "throughput_rps": st["throughput_rps"], "max_resident": st["max_resident"]},
                      "plain": dict(_latency_stats(lat), throughput_rps=thr)}
