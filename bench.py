@@ -148,186 +148,49 @@ def gather_reference(A, n, reps=20):
 
 
 def run_blackbox_only(args):
-    """A few black-box applications on the bench workload (for profiler
-    captures of the SpMM passes): matrix ingest, then W + K applications."""
+    """Black-box applications only (matrix ingest, then W + K applications):
+    for profiler captures of the SpMM passes and for the SpMM rate on a
+    matrix whose working set exceeds L2.  --matrix c1: the bench workload
+    (block 8); --matrix c2: the 1,900,000 x 1,950,000 Poisson-row matrix of
+    ~37M nnz with block 32 (p = 2147483629), where the gathered block alone
+    (1.9M x 128 bytes) is twice the L2.  Prints per-pass times from the
+    library's CUDA-event samples and the algorithmic GB/s against the HBM
+    peak."""
     import torch
-    from paper_0704_2351_gb300 import wr
-    A, cfg = workload(0)
-    p, n = cfg["p"], cfg["n"]
+    from paper_0704_2351_gb300 import synth, wr
+    if args.matrix == "c2":
+        A = synth.config2()
+        p, n, seed = 2147483629, 32, synth.SEED_BASE + 2
+        name = ("1,900,000 x 1,950,000, %d nnz (Poisson 19.5 per row, uniform columns), block 32, "
+                "p = 2147483629" % A.nnz)
+    else:
+        A, cfg = workload(0)
+        p, n, seed, name = cfg["p"], cfg["n"], cfg["seed"], cfg["name"]
     ctx = wr.wr_create(0)
     mat = wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals)
-    g = torch.Generator().manual_seed(cfg["seed"])
-    v = torch.randint(0, p, (A.cols, n), generator=g, dtype=torch.int64).to(torch.int32).cuda()
+    N = min(A.rows, A.cols)
+    g = torch.Generator().manual_seed(seed)
+    v = torch.randint(0, p, (N, n), generator=g, dtype=torch.int64).to(torch.int32).cuda()
     out = torch.empty_like(v)
-    prm = wr.make_params(p, 1, n, cfg["seed"])
+    prm = wr.make_params(p, 1, n, seed)
     for _ in range(args.warmup):
         wr.wr_blackbox_apply_device(ctx, mat, prm, v, out, n)
+    wr.wr_set_profiling(ctx, True)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(args.steps):
         wr.wr_blackbox_apply_device(ctx, mat, prm, v, out, n)
     torch.cuda.synchronize()
     ms = 1e3 * (time.perf_counter() - t) / max(args.steps, 1)
-    print(json.dumps({"only": "blackbox", "workload": cfg["name"], "steps": args.steps,
-                      "ms_per_application_wall": ms}), flush=True)
+    # per-pass algorithmic bytes, as the library counts them for the loop
+    nv = 1 << max(0, (n - 1).bit_length())
+    per_pass = [4.0 * A.nnz + 4.0 * nv * (A.rows + A.cols) + 4.0 * r for r in (A.rows, A.cols)]
+    peak = measured_peaks().get("hbm_gbs")
+    line = {"only": "blackbox", "workload": name, "steps": args.steps, "ms_per_application_wall": ms,
+            "algorithmic_bytes_per_pass": per_pass,
+            "gbs_per_pass_at_wall_time": 1e-6 * sum(per_pass) / ms, "hbm_peak_gbs": peak}
+    print(json.dumps(line), flush=True)
     wr.wr_matrix_free(mat)
-    wr.wr_destroy(ctx)
-    return 0
-
-
-def run_batch(args):
-    """Batched workload: chain-complex pairs (d_n, d_{n+1}, d_n d_{n+1} = 0)
-    with row counts log-uniform in [5,000, 300,000], each matrix solved
-    modulo 4 primes below 2^30 (rank over Q = the maximum).  Plain = every job
-    through wr_rank one at a time; batched = one wr_rank_batch call.  Both
-    are timed end to end (host clock, results copied back); every batched
-    rank must equal the plain one and the planted rank."""
-    import torch
-    from paper_0704_2351_gb300 import synth, wr
-    pairs = synth.config3_pairs(npairs=args.pairs)
-    mats = [A for pr in pairs for A in pr]
-    primes = []
-    c = (1 << 30) - 1
-    while len(primes) < 4:
-        if all(c % d for d in range(2, int(c ** 0.5) + 1)):
-            primes.append(c)
-        c -= 2
-    ctx = wr.wr_create(0)
-    wr.wr_set_batch_slots(ctx, args.slots)
-    handles = [wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals) for A in mats]
-    b = args.block
-    jobs = [(i, p) for i in range(len(mats)) for p in primes]
-    params = [wr.make_params(p, b, b, synth.SEED_BASE + 3 + 7 * i) for (i, p) in jobs]
-    # warm-up (module load, first graph instantiation)
-    small = min(range(len(mats)), key=lambda i: mats[i].nnz)
-    wr.wr_result_free(wr.wr_rank(ctx, handles[small], params[small * 4]))
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    plain = []
-    for h, (i, p), prm in zip([handles[i] for i, _ in jobs], jobs, params):
-        res = wr.wr_rank(ctx, h, prm)
-        plain.append(wr.wr_result_rank(res))
-        wr.wr_result_free(res)
-    t_plain = time.perf_counter() - t
-    t = time.perf_counter()
-    outs = wr.wr_rank_batch(ctx, [handles[i] for i, _ in jobs], params)
-    t_batch = time.perf_counter() - t
-    batched = [wr.wr_result_rank(o) for o in outs]
-    for o in outs:
-        wr.wr_result_free(o)
-    assert batched == plain, "batched ranks differ from the plain ones"
-    for k, (i, p) in enumerate(jobs):
-        assert batched[k] == mats[i].rank, "job %d: rank %d != planted %d" % (k, batched[k], mats[i].rank)
-    rank_q = [max(batched[4 * i: 4 * i + 4]) for i in range(len(mats))]
-    chain_ok = all(rank_q[2 * k] + rank_q[2 * k + 1] <= pairs[k][0].cols for k in range(len(pairs)))
-    work = sum(2.0 * mats[i].nnz * b * ((-(-min(mats[i].rows, mats[i].cols) // b)) * 2 + 1) for i, _ in jobs)
-    line = {"metric": METRIC, "workload": "batched", "value": work / t_batch, "unit": UNIT,
-            "n_gpus": 1, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
-            "config": {"pairs": args.pairs, "matrices": len(mats), "primes": primes, "jobs": len(jobs),
-                       "block": [b, b], "slots": args.slots,
-                       "rows": [int(min(A.rows for A in mats)), int(max(A.rows for A in mats))],
-                       "nnz_total": int(sum(A.nnz for A in mats))},
-            "plain_s": t_plain, "batched_s": t_batch, "speedup": t_plain / t_batch,
-            "ranks_equal_planted": True, "chain_rank_sum_ok": chain_ok,
-            "gpu_launches_batched": wr.wr_last_timings(ctx)["kernel_launches"]}
-    print(json.dumps(line), flush=True)
-    for h in handles:
-        wr.wr_matrix_free(h)
-    wr.wr_destroy(ctx)
-    return 0
-
-
-def _latency_stats(lat):
-    lat = sorted(lat)
-    pick = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]
-    return {"p50_ms": pick(0.5), "p99_ms": pick(0.99), "mean_ms": sum(lat) / len(lat)}
-
-
-def run_serve(args):
-    """Served workload: a Poisson trace of rank queries (rows log-uniform in
-    [1,000, rows_hi], 10-20 nnz/row, planted rank 0.95 min(R, C), 4 primes
-    below 2^30, m = n = 16).  Plain = one request at a time in arrival order
-    (latency = queueing behind earlier requests + own time, from the measured
-    service times).  Served = the continuous-batching server fed at the
-    trace's arrival times, at the trace rate and at 0.7x the plain capacity."""
-    import torch
-    from paper_0704_2351_gb300 import synth, wr
-    trace = synth.config4_trace(nreq=args.requests, rate=args.rate, hi=args.rows_hi)
-    primes = [1073741789, 1073741783, 1073741741, 1073741723]
-    mats = [synth.config4_matrix(r) for r in trace]
-    ctx = wr.wr_create(0)
-    handles = [wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals) for A in mats]
-    b = args.block
-    params = [wr.make_params(primes[r["prime_slot"]], b, b, r["seed"]) for r in trace]
-    wr.wr_result_free(wr.wr_rank(ctx, handles[0], params[0]))
-    torch.cuda.synchronize()
-    service = []
-    ranks = []
-    for h, prm in zip(handles, params):
-        t = time.perf_counter()
-        res = wr.wr_rank(ctx, h, prm)
-        service.append(time.perf_counter() - t)
-        ranks.append(wr.wr_result_rank(res))
-        wr.wr_result_free(res)
-    assert ranks == [r["rank"] for r in trace], "plain ranks differ from the planted ones"
-    cap_plain = len(trace) / sum(service)
-
-    def plain_latency(arrivals):
-        """One request at a time in arrival order: (latencies in ms, completions/s)."""
-        free, lat = 0.0, []
-        for a, s in zip(arrivals, service):
-            start = max(a, free)
-            free = start + s
-            lat.append(1e3 * (free - a))
-        return lat, len(arrivals) / (free - arrivals[0])
-
-    def served(arrivals):
-        srv = wr.wr_server_start(ctx, max_slots=args.slots, hbm_budget=args.hbm_budget, queue_cap=1 << 20)
-        t0 = time.perf_counter()
-        tickets = []
-        for a, h, prm in zip(arrivals, handles[:len(arrivals)], params[:len(arrivals)]):
-            d = a - (time.perf_counter() - t0)
-            if d > 0:
-                time.sleep(d)
-            tickets.append(wr.wr_submit(srv, h, prm))
-        got = []
-        for tk in tickets:
-            res = wr.wr_wait(srv, tk, 3600 * 1000)
-            got.append(wr.wr_result_rank(res))
-            wr.wr_result_free(res)
-        st = wr.wr_server_stats(srv)
-        wr.wr_server_stop(srv)
-        assert got == ranks[:len(arrivals)], "served ranks differ from the plain ones"
-        return st
-
-    arr = [r["t"] for r in trace]
-    out = {}
-    for name, scale in [("trace_rate", 1.0), ("rate_0.7x_plain_capacity", None)]:
-        if scale is None:
-            # the first quarter of the trace, arrivals stretched to 0.7x the
-            # plain capacity (the whole trace would take n / (0.7 capacity))
-            k = max(20, len(arr) // 4)
-            lam = 0.7 * cap_plain
-            a = [x * args.rate / lam for x in arr[:k]]
-        else:
-            lam = args.rate
-            a = arr
-        st = served(a)
-        lat, thr = plain_latency(a)
-        out[name] = {"arrival_rate_rps": lam, "requests": len(a),
-                     "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                                "throughput_rps": st["throughput_rps"], "max_resident": st["max_resident"]},
-                     "plain": dict(_latency_stats(lat), throughput_rps=thr)}
-    line = {"metric": METRIC, "workload": "served", "unit": "requests/s", "n_gpus": 1,
-            "value": out["trace_rate"]["served"]["throughput_rps"], "higher_is_better": True,
-            "dtype": "int64", "data": "synthetic",
-            "config": {"requests": len(trace), "rate": args.rate, "rows": [1000, args.rows_hi],
-                       "block": [b, b], "slots": args.slots, "hbm_budget": args.hbm_budget,
-                       "nnz_total": int(sum(A.nnz for A in mats))},
-            "plain_capacity_rps": cap_plain, "results": out, "ranks_equal_planted": True}
-    print(json.dumps(line), flush=True)
-    for h in handles:
-        wr.wr_matrix_free(h)
     wr.wr_destroy(ctx)
     return 0
 
@@ -348,6 +211,7 @@ def run_sigma_only(args):
     ctx = wr.wr_create(0)
     wr.wr_set_profiling(ctx, True)
     wr.wr_set_sigma_chunk(ctx, args.sigma_chunk)
+    wr.wr_set_sigma_leaf(ctx, args.sigma_leaf)
     for _ in range(args.warmup):
         wr.wr_sigma_basis_device(ctx, S, L, m, n, p, P, deg, L + 1)
     torch.cuda.synchronize()
@@ -357,7 +221,8 @@ def run_sigma_only(args):
     torch.cuda.synchronize()
     ms = 1e3 * (time.perf_counter() - t) / max(args.steps, 1)
     tm = wr.wr_last_timings(ctx)
-    print(json.dumps({"only": "sigma", "L": L, "block": [m, n], "chunk": args.sigma_chunk, "ms_per_sigma_basis": ms,
+    print(json.dumps({"only": "sigma", "L": L, "block": [m, n], "chunk": args.sigma_chunk, "leaf": args.sigma_leaf,
+                      "ms_per_sigma_basis": ms,
                       "window_ms": tm["sigma_window_ms"], "local_ms": tm["sigma_local_ms"],
                       "apply_ms": tm["sigma_apply_ms"]}), flush=True)
     wr.wr_destroy(ctx)
@@ -404,9 +269,12 @@ def main():
     ap.add_argument("--projection", default="generic", choices=["generic", "symmetric"])
     ap.add_argument("--only-blackbox", action="store_true",
                     help="only ingest + black-box applications (for profiler captures)")
+    ap.add_argument("--matrix", default="c1", choices=["c1", "c2"],
+                    help="--only-blackbox: the bench matrix (c1) or the 1.9M-row block-32 matrix (c2)")
     ap.add_argument("--only-sigma", action="store_true",
                     help="only the sigma-basis on a random sequence of the workload's shape")
     ap.add_argument("--sigma-chunk", type=int, default=0, help="orders per sigma-basis chunk (0: automatic)")
+    ap.add_argument("--sigma-leaf", type=int, default=0, help="orders per PM-Basis leaf (0: automatic)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the one-matrix time-to-rank line (default); batch / serve: batched or "
                          "served against plain time-to-rank")

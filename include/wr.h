@@ -114,6 +114,15 @@ wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out);
  * the discrepancy and product kernels around it do the same total work for
  * any chunk size and cost a few launches per chunk. */
 wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
+/* Sigma-bases of more than `orders` orders (>= 64) are computed by PM-Basis
+ * (Section 2.3): halved recursively down to leaves of at most `orders`
+ * orders, which run the blocked M-Basis, with the residuals and the products
+ * of the halves' bases done as polynomial matrix products by number-theoretic
+ * transforms over three FFT primes and the CRT.  The result is the same basis
+ * bit for bit; a leaf as large as the sequence turns PM-Basis off.  0
+ * (default) = automatic: PM-Basis with 8,192-order leaves for sequences longer
+ * than 131,072 orders when m + n <= 32, the blocked M-Basis otherwise. */
+wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders);
 
 /* ---------------------------------------------------------------- matrices */
 

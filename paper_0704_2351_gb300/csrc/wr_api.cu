@@ -193,6 +193,13 @@ extern "C" wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders) {
     return WR_OK;
 }
 
+extern "C" wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if (orders != 0 && orders < 64) return fail(WR_EINVAL, "PM-Basis leaf must be 0 (automatic) or at least 64 orders");
+    ctx->sigma_leaf = orders;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out) {
     if (!ctx || !out) return fail(WR_EINVAL, "null argument");
     *out = ctx->last;

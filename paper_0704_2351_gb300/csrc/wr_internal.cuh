@@ -298,6 +298,7 @@ struct wr_ctx {
     int64_t launches = 0;   // kernels launched through this context (graph replays: nodes per replay)
     int batch_slots = 8;    // slots (streams + host threads) of wr_rank_batch
     int sigma_chunk = 0;    // orders per sigma-basis chunk (0: automatic)
+    int64_t sigma_leaf = 0; // orders per PM-Basis leaf (0: automatic)
     wr_timings last{};
 };
 
@@ -333,6 +334,8 @@ wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, i
 
 // sequence (wr_spmm.cu)
 struct SeqPlan;
+wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r, int s,
+                      int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C);
 wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
                        uint32_t *d_S, double *setup_ms, double *seq_ms);
 wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,

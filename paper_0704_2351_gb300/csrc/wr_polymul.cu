@@ -1,0 +1,252 @@
+// Products of polynomial matrices mod p by number-theoretic transforms, for
+// the PM-Basis sigma-basis (Section 2.3: "PM-Basis ... reduces this
+// computation to polynomial matrix multiplication", FFT primes c 2^k + 1, and
+// CRT with several FFT primes when the field itself has no large 2^k-th roots
+// of unity, with prod p_i > d n p^2).
+//
+// C = A B with A (r x s) and B (s x t) polynomial matrices whose entries are
+// residues mod p, stored coefficient-major ([coef][row][col]).  Each product
+// entry is computed exactly as an integer -- a sum of at most
+// s * min(deg A, deg B) + s products below p^2 < 2^62, so below 2^88 for
+// s <= 64 and degrees below 2^20 -- from its residues modulo three FFT primes
+// whose product exceeds 2^89, and then reduced mod p.  Only the coefficients
+// [lo, hi) of C are produced; a cyclic transform of length Lz >= hi whose
+// wrapped-around part (coefficients at and above Lz folded onto 0..) stays
+// below lo gives exactly those (a middle product when lo > 0).
+//
+// Transforms: forward decimation in frequency (natural order in, bit-reversed
+// out), pointwise products in that order, inverse decimation in time
+// (bit-reversed in, natural out); residues in Montgomery form; one launch per
+// butterfly stage over all polynomials of the batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "wr_internal.cuh"
+
+namespace wr {
+
+namespace {
+
+constexpr int NTT_NPRIMES = 3;
+constexpr uint32_t NTT_PRIMES[NTT_NPRIMES] = {998244353u, 469762049u, 2013265921u};  // 119 2^23+1, 7 2^26+1, 15 2^27+1
+constexpr int NTT_MAX_LOG = 23;  // 2^23 divides every p_i - 1
+
+uint64_t hpow(uint64_t a, uint64_t e, uint64_t m) {
+    uint64_t r = 1 % m;
+    a %= m;
+    while (e) {
+        if (e & 1) r = (unsigned __int128)r * a % m;
+        a = (unsigned __int128)a * a % m;
+        e >>= 1;
+    }
+    return r;
+}
+
+// smallest generator of the multiplicative group mod prime P (checked
+// against every prime factor of P - 1)
+uint32_t primitive_root(uint32_t P) {
+    std::vector<uint64_t> f;
+    uint64_t x = P - 1;
+    for (uint64_t d = 2; d * d <= x; d++)
+        if (x % d == 0) {
+            f.push_back(d);
+            while (x % d == 0) x /= d;
+        }
+    if (x > 1) f.push_back(x);
+    for (uint32_t g = 2;; g++) {
+        bool ok = true;
+        for (uint64_t q : f)
+            if (hpow(g, (P - 1) / q, P) == 1) { ok = false; break; }
+        if (ok) return g;
+    }
+}
+
+// a (mod p, any p < 2^31) -> Montgomery form mod P, transposed to one
+// contiguous run of Lz coefficients per polynomial (zero padded)
+__global__ void k_ntt_load(const uint32_t *__restrict__ src, int64_t ncoef, int nent, int64_t Lz,
+                           uint32_t *__restrict__ dst, ModP mP) {
+    const int64_t total = (int64_t)nent * Lz;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(x / Lz);
+        const int64_t k = x - (int64_t)e * Lz;
+        uint32_t v = 0;
+        if (k < ncoef) v = to_mont(src[(size_t)k * nent + e] % mP.p, mP);
+        dst[x] = v;
+    }
+}
+
+// one stage of the forward transform (decimation in frequency): blocks of
+// length 2 half, butterfly (u, v) -> (u + v, (u - v) w^j), w^j = tw[j * step]
+__global__ void k_ntt_dif_stage(uint32_t *__restrict__ a, int64_t npoly, int64_t Lz, int64_t half, int64_t step,
+                                const uint32_t *__restrict__ tw, ModP mP) {
+    const int64_t nb = npoly * (Lz >> 1);
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nb; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t poly = x / (Lz >> 1), b = x - poly * (Lz >> 1);
+        const int64_t blk = b / half, j = b - blk * half;
+        uint32_t *p0 = a + poly * Lz + blk * 2 * half + j;
+        const uint32_t u = p0[0], v = p0[half];
+        p0[0] = addm(u, v, mP);
+        p0[half] = mont_mul(subm(u, v, mP), tw[j * step], mP);
+    }
+}
+
+// one stage of the inverse transform (decimation in time): (u, v w^j) ->
+// (u + v w^j, u - v w^j) with the inverse twiddles
+__global__ void k_ntt_dit_stage(uint32_t *__restrict__ a, int64_t npoly, int64_t Lz, int64_t half, int64_t step,
+                                const uint32_t *__restrict__ twi, ModP mP) {
+    const int64_t nb = npoly * (Lz >> 1);
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nb; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t poly = x / (Lz >> 1), b = x - poly * (Lz >> 1);
+        const int64_t blk = b / half, j = b - blk * half;
+        uint32_t *p0 = a + poly * Lz + blk * 2 * half + j;
+        const uint32_t u = p0[0], v = mont_mul(p0[half], twi[j * step], mP);
+        p0[0] = addm(u, v, mP);
+        p0[half] = subm(u, v, mP);
+    }
+}
+
+// pointwise: C_f = A_f B_f (r x s times s x t) at every transform point f
+__global__ void k_ntt_pointwise(const uint32_t *__restrict__ A, const uint32_t *__restrict__ B,
+                                uint32_t *__restrict__ C, int r, int s, int t, int64_t Lz, ModP mP) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < Lz; f += (int64_t)gridDim.x * blockDim.x) {
+        for (int i = 0; i < r; i++)
+            for (int j = 0; j < t; j++) {
+                uint32_t acc = 0;
+                for (int k = 0; k < s; k++)
+                    acc = addm(acc, mont_mul(A[((size_t)i * s + k) * Lz + f], B[((size_t)k * t + j) * Lz + f], mP), mP);
+                C[((size_t)i * t + j) * Lz + f] = acc;
+            }
+    }
+}
+
+struct CrtConst {
+    uint32_t P1, P2, P3;
+    uint32_t c12;        // P1^{-1} mod P2
+    uint32_t c123;       // (P1 P2)^{-1} mod P3
+    uint32_t p1_mod_p3;  // P1 mod P3
+    uint32_t P1_mod_p, P1P2_mod_p;
+};
+
+// Garner: the integer x < P1 P2 P3 with x = r_i mod P_i, reduced mod p.
+// In: the three inverse transforms (Montgomery form, still times Lz).
+__global__ void k_ntt_crt(const uint32_t *__restrict__ R1, const uint32_t *__restrict__ R2,
+                          const uint32_t *__restrict__ R3, int nent, int64_t Lz, int64_t lo, int64_t hi,
+                          uint32_t *__restrict__ out, uint32_t il1, uint32_t il2, uint32_t il3, CrtConst cc,
+                          ModP m1, ModP m2, ModP m3, ModP mp) {
+    const int64_t total = (hi - lo) * nent;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = lo + x / nent;
+        const int e = (int)(x % nent);
+        const size_t src = (size_t)e * Lz + (size_t)k;
+        // mont_mul(v R, Lz^{-1}) = v Lz^{-1} in normal form
+        const uint32_t r1 = mont_mul(R1[src], il1, m1);
+        const uint32_t r2 = mont_mul(R2[src], il2, m2);
+        const uint32_t r3 = mont_mul(R3[src], il3, m3);
+        const uint32_t t1 = r1;
+        const uint32_t t2 = mulm(subm(r2, t1 % cc.P2, m2), cc.c12, m2);
+        uint32_t u = subm(r3, t1 % cc.P3, m3);
+        u = subm(u, mulm(cc.p1_mod_p3, t2, m3), m3);
+        const uint32_t t3 = mulm(u, cc.c123, m3);
+        uint64_t v = (uint64_t)(t1 % mp.p);
+        v += (uint64_t)mulm(cc.P1_mod_p, t2 % mp.p, mp);
+        v += (uint64_t)mulm(cc.P1P2_mod_p, t3 % mp.p, mp);
+        out[(size_t)x] = red64(v, mp);
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int num_sms) {
+    const int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
+}
+
+}  // namespace
+
+// C[k - lo] = sum_j A_j B_{k-j} (mod p) for lo <= k < hi; A: na coefficients of
+// r x s, B: nb coefficients of s x t, C: (hi - lo) x r x t.  All device
+// pointers, coefficient-major.
+wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r, int s,
+                      int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C) {
+    if (hi <= lo) return WR_OK;
+    cudaStream_t st = ctx->stream;
+    if (na <= 0 || nb <= 0) {
+        WR_CUDA(cudaMemsetAsync(C, 0, sizeof(uint32_t) * (size_t)(hi - lo) * r * t, st));
+        return WR_OK;
+    }
+    const int64_t full = na + nb - 1;  // coefficients of the exact product
+    const int64_t need = std::max<int64_t>(hi, full - lo);
+    int lg = 1;
+    while (((int64_t)1 << lg) < need) lg++;
+    if (lg > NTT_MAX_LOG) return fail(WR_EINVAL, "polynomial product too long for the transform primes");
+    const int64_t Lz = (int64_t)1 << lg;
+    const int nA = r * s, nB = s * t, nC = r * t;
+    const ModP mp = make_modp(p);
+    DevBuf bufA, bufB, bufC[NTT_NPRIMES], tw, twi;
+    WR_TRY(dev_alloc(ctx, bufA, sizeof(uint32_t) * (size_t)nA * Lz));
+    WR_TRY(dev_alloc(ctx, bufB, sizeof(uint32_t) * (size_t)nB * Lz));
+    for (int i = 0; i < NTT_NPRIMES; i++) WR_TRY(dev_alloc(ctx, bufC[i], sizeof(uint32_t) * (size_t)nC * Lz));
+    WR_TRY(dev_alloc(ctx, tw, sizeof(uint32_t) * (size_t)(Lz / 2)));
+    WR_TRY(dev_alloc(ctx, twi, sizeof(uint32_t) * (size_t)(Lz / 2)));
+    std::vector<uint32_t> htw(Lz / 2), htwi(Lz / 2);
+    uint32_t il[NTT_NPRIMES];
+    ModP mP[NTT_NPRIMES];
+    const int T = 256;
+    for (int i = 0; i < NTT_NPRIMES; i++) {
+        const uint32_t P = NTT_PRIMES[i];
+        mP[i] = make_modp(P);
+        const uint64_t g = primitive_root(P);
+        const uint64_t w = hpow(g, (P - 1) >> lg, P), wi = hpow(w, P - 2, P);
+        // twiddles in Montgomery form: w^j R mod P
+        uint64_t x = 1, y = 1;
+        for (int64_t j = 0; j < Lz / 2; j++) {
+            htw[j] = (uint32_t)(((unsigned __int128)x << 32) % P);
+            htwi[j] = (uint32_t)(((unsigned __int128)y << 32) % P);
+            x = (unsigned __int128)x * w % P;
+            y = (unsigned __int128)y * wi % P;
+        }
+        il[i] = (uint32_t)hpow((uint64_t)(Lz % P), P - 2, P);  // Lz^{-1} mod P (normal form)
+        WR_CUDA(cudaMemcpyAsync(tw.ptr, htw.data(), sizeof(uint32_t) * htw.size(), cudaMemcpyHostToDevice, st));
+        WR_CUDA(cudaMemcpyAsync(twi.ptr, htwi.data(), sizeof(uint32_t) * htwi.size(), cudaMemcpyHostToDevice, st));
+        k_ntt_load<<<grid_for((int64_t)nA * Lz, T, ctx->num_sms), T, 0, st>>>(A, na, nA, Lz, bufA.as<uint32_t>(), mP[i]);
+        WR_LAUNCHED(ctx);
+        k_ntt_load<<<grid_for((int64_t)nB * Lz, T, ctx->num_sms), T, 0, st>>>(B, nb, nB, Lz, bufB.as<uint32_t>(), mP[i]);
+        WR_LAUNCHED(ctx);
+        for (int64_t half = Lz / 2; half >= 1; half >>= 1) {
+            const int64_t step = (Lz / 2) / half;
+            k_ntt_dif_stage<<<grid_for((int64_t)nA * (Lz / 2), T, ctx->num_sms), T, 0, st>>>(
+                bufA.as<uint32_t>(), nA, Lz, half, step, tw.as<uint32_t>(), mP[i]);
+            WR_LAUNCHED(ctx);
+            k_ntt_dif_stage<<<grid_for((int64_t)nB * (Lz / 2), T, ctx->num_sms), T, 0, st>>>(
+                bufB.as<uint32_t>(), nB, Lz, half, step, tw.as<uint32_t>(), mP[i]);
+            WR_LAUNCHED(ctx);
+        }
+        k_ntt_pointwise<<<grid_for(Lz, T, ctx->num_sms), T, 0, st>>>(bufA.as<uint32_t>(), bufB.as<uint32_t>(),
+                                                                      bufC[i].as<uint32_t>(), r, s, t, Lz, mP[i]);
+        WR_LAUNCHED(ctx);
+        for (int64_t half = 1; half <= Lz / 2; half <<= 1) {
+            const int64_t step = (Lz / 2) / half;
+            k_ntt_dit_stage<<<grid_for((int64_t)nC * (Lz / 2), T, ctx->num_sms), T, 0, st>>>(
+                bufC[i].as<uint32_t>(), nC, Lz, half, step, twi.as<uint32_t>(), mP[i]);
+            WR_LAUNCHED(ctx);
+        }
+        // the twiddle uploads of the next prime must not overwrite tables in use
+        WR_CUDA(cudaStreamSynchronize(st));
+    }
+    CrtConst cc;
+    cc.P1 = NTT_PRIMES[0];
+    cc.P2 = NTT_PRIMES[1];
+    cc.P3 = NTT_PRIMES[2];
+    cc.c12 = (uint32_t)hpow(cc.P1 % cc.P2, cc.P2 - 2, cc.P2);
+    cc.c123 = (uint32_t)hpow((uint64_t)cc.P1 * cc.P2 % cc.P3, cc.P3 - 2, cc.P3);
+    cc.p1_mod_p3 = cc.P1 % cc.P3;
+    cc.P1_mod_p = cc.P1 % p;
+    cc.P1P2_mod_p = (uint32_t)((uint64_t)cc.P1 * cc.P2 % p);
+    k_ntt_crt<<<grid_for((hi - lo) * nC, T, ctx->num_sms), T, 0, st>>>(
+        bufC[0].as<uint32_t>(), bufC[1].as<uint32_t>(), bufC[2].as<uint32_t>(), nC, Lz, lo, hi, C, il[0], il[1],
+        il[2], cc, mP[0], mP[1], mP[2], mp);
+    WR_LAUNCHED(ctx);
+    return WR_OK;
+}
+
+}  // namespace wr

@@ -34,14 +34,18 @@ namespace {
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-__global__ void k_init_basis(uint32_t *__restrict__ P, int n, int q, int32_t *__restrict__ deg,
-                             uint32_t *__restrict__ qtop, int m, int *__restrict__ dmax) {
+// The starting basis at x^0.  [S | -I_m] (deg_in == nullptr): P = [I_n | 0]
+// (the first n rows), degrees (0^n, 1^m), Q = [0 | I_m].  A general residual
+// (deg_in given, nr = q rows): P = I_q, the given degrees, Q = 0.
+__global__ void k_init_basis(uint32_t *__restrict__ P, int nr, int n, int q, int32_t *__restrict__ deg,
+                             const int32_t *__restrict__ deg_in, uint32_t *__restrict__ qtop, int m,
+                             int *__restrict__ dmax) {
     for (int t = threadIdx.x; t < m * q || t < q; t += blockDim.x) {
-        if (t < n) P[(size_t)t * q + t] = 1;  // P = [I_n | 0] at x^0
-        if (t < q) deg[t] = t < n ? 0 : 1;
+        if (t < nr) P[(size_t)t * q + t] = 1;
+        if (t < q) deg[t] = deg_in ? deg_in[t] : (t < n ? 0 : 1);
         if (t < m * q) {
             int a = t / q, c = t % q;
-            qtop[t] = (c == n + a) ? 1u : 0u;  // Q = [0 | I_m] at x^0
+            qtop[t] = (!deg_in && c == n + a) ? 1u : 0u;
         }
     }
     if (threadIdx.x == 0) *dmax = 1;
@@ -214,6 +218,13 @@ __global__ void __launch_bounds__(256)
 constexpr int LOCAL_THREADS = 1024;
 // orders per chunk unless the context sets it (wr_set_sigma_chunk)
 constexpr int SIGMA_CHUNK_DEFAULT = 64;
+// PM-Basis by default only for sequences longer than SIGMA_PM_MIN_L (with
+// q <= 32), with leaves of SIGMA_LEAF_DEFAULT orders; measured on GB300 at
+// L = 45,002, q = 16 the blocked M-Basis alone is faster (744 ms against
+// 786-1058 ms for leaves of 16,384 down to 1,024 orders).  wr_set_sigma_leaf
+// chooses the leaf explicitly.
+constexpr int64_t SIGMA_LEAF_DEFAULT = 8192;
+constexpr int64_t SIGMA_PM_MIN_L = 131072;
 constexpr int BAR_T0 = 1, BAR_RR0 = 3;  // ids BAR_T0 + (i & 1), BAR_RR0 + (i & 1)
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
@@ -429,7 +440,8 @@ template <int MM, int CPL, int KLAZY>
 __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
     k_local(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
             uint32_t *__restrict__ qtop_g, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
-            int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, uint32_t *__restrict__ scale_g, ModP mp) {
+            int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, uint32_t *__restrict__ scale_g, int dbase,
+            ModP mp) {
     extern __shared__ uint32_t sm[];
     const int mq = m * q, qq = q * q;
     const int mlrows = 2 * bb + 1;
@@ -740,8 +752,10 @@ __global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
         degl_g[c] = degl[c];
     }
     if (tid == 0) {
+        // bound on the polynomial degree of the basis: column c's degree
+        // minus the smallest starting degree (the row shifts)
         int dmx = 0;
-        for (int c = 0; c < q; c++) dmx = max(dmx, deg[c]);
+        for (int c = 0; c < q; c++) dmx = max(dmx, deg[c] - dbase);
         *dmax_g = dmx;
     }
 }
@@ -975,20 +989,26 @@ __global__ void __launch_bounds__(VAL_THREADS)
 
 }  // namespace
 
-wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n, uint32_t p,
-                      uint32_t *d_P, int32_t *d_deg, int64_t Dcap) {
-    if (m < 1 || n < 1 || m > 32 || n > 32) return fail(WR_EINVAL, "block sizes must be in 1..32");
+// Blocked M-Basis over L orders.  [S | -I_m] (d_deg_in == nullptr): S holds
+// L x m x n, d_P receives the first nr = n rows of the basis, d_deg the
+// shifted degrees.  A general residual F (d_deg_in given): S holds L x m x q,
+// nr = q, the basis starts at I_q with the degrees d_deg_in, and dbase is
+// their minimum.  *dmax_out (optional): a bound on the basis's polynomial
+// degree.
+static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int nr, int n, uint32_t p,
+                            uint32_t *d_P, int32_t *d_deg, const int32_t *d_deg_in, int dbase, int64_t Dcap,
+                            int64_t *dmax_out) {
     const int q = m + n;
     const ModP mp = make_modp(p);
     cudaStream_t s = ctx->stream;
-    const size_t nq = (size_t)n * q;
+    const size_t nq = (size_t)nr * q;
     WR_CUDA(cudaMemsetAsync(d_P, 0, sizeof(uint32_t) * (Dcap + 1) * nq, s));
     DevBuf P2, qtop, dmax, Epart, Ml, degl, scale;
     WR_TRY(dev_alloc(ctx, P2, sizeof(uint32_t) * (Dcap + 1) * nq));
     WR_CUDA(cudaMemsetAsync(P2.ptr, 0, P2.bytes, s));
     WR_TRY(dev_alloc(ctx, qtop, sizeof(uint32_t) * m * q));
     WR_TRY(dev_alloc(ctx, dmax, sizeof(int)));
-    k_init_basis<<<1, 256, 0, s>>>(d_P, n, q, d_deg, qtop.as<uint32_t>(), m, dmax.as<int>());
+    k_init_basis<<<1, 256, 0, s>>>(d_P, nr, n, q, d_deg, d_deg_in, qtop.as<uint32_t>(), m, dmax.as<int>());
     WR_LAUNCHED(ctx);
 
     // chunk size b and tiles: every kernel's shared memory must fit
@@ -999,7 +1019,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     };
     auto window_bytes = [&](int TT, int b) {
         const int nib = (b + WIN_IB - 1) / WIN_IB;
-        return sizeof(uint32_t) * ((size_t)TT * nq + (size_t)(nib * WIN_IB + TT - 1) * m * n);
+        return sizeof(uint32_t) * ((size_t)TT * nq + (size_t)(nib * WIN_IB + TT - 1) * m * nr);
     };
     auto apply_bytes = [&](int ta, int b) { return sizeof(uint32_t) * ((size_t)(b + 1) * q * q + (size_t)(ta + b) * nq); };
     int bmax = ctx->sigma_chunk > 0 ? std::min(ctx->sigma_chunk, 64) : SIGMA_CHUNK_DEFAULT, TT = 32, TA = 64;
@@ -1031,7 +1051,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     DevBuf Esum;
     WR_TRY(dev_alloc(ctx, Esum, sizeof(uint32_t) * (size_t)bmax * m * q));
     using LocalFn = void (*)(int, int, int, int, int, const uint32_t *, uint32_t *, int32_t *, uint32_t *, int32_t *,
-                             int *, uint32_t *, ModP);
+                             int *, uint32_t *, int, ModP);
     LocalFn kloc;
     if (m <= 8)
         kloc = q <= 32 ? (lazy16 ? k_local<8, 1, 16> : k_local<8, 1, 4>) : (lazy16 ? k_local<8, 2, 16> : k_local<8, 2, 4>);
@@ -1057,7 +1077,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         const int64_t tspan = std::min<int64_t>(Dbound, k0 + bb - 1) + 1;
         const int nparts = (int)std::min<int64_t>(nparts_max, std::max<int64_t>(1, (tspan + TT - 1) / TT));
         const int64_t tper = (tspan + nparts - 1) / nparts;
-        kwin<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, n, q, Pcur, k0, bb, TT, tper,
+        kwin<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, nr, q, Pcur, k0, bb, TT, tper,
                                                                 dmax.as<int>(), Epart.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
         const uint32_t *Ewin = Epart.as<uint32_t>();
@@ -1071,13 +1091,13 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
         kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(
             m, n, q, bb, 1, Ewin, qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
-            degl.as<int32_t>(), dmax.as<int>(), scale.as<uint32_t>(), mp);
+            degl.as<int32_t>(), dmax.as<int>(), scale.as<uint32_t>(), dbase, mp);
         WR_LAUNCHED(ctx);
         if (prof) WR_CUDA(cudaEventRecord(pe[2], s));
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
         const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
         kapp<<<(unsigned)((Dnew + TA) / TA), APP_THREADS, apply_bytes(TA, bb), s>>>(
-            Pcur, Pnext, n, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, dmax.as<int>(), mp);
+            Pcur, Pnext, nr, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, dmax.as<int>(), mp);
         WR_LAUNCHED(ctx);
         if (prof) {
             WR_CUDA(cudaEventRecord(pe[3], s));
@@ -1097,15 +1117,116 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     if (ctx->profiling) {
         for (auto &e : pe) cudaEventDestroy(e);
         const double scale = sampled ? (double)nchunks / sampled : 0.0;  // extrapolate the samples
-        ctx->last.sigma_window_ms = pw * scale;
-        ctx->last.sigma_local_ms = pl * scale;
-        ctx->last.sigma_apply_ms = pa * scale;
+        ctx->last.sigma_window_ms += pw * scale;
+        ctx->last.sigma_local_ms += pl * scale;
+        ctx->last.sigma_apply_ms += pa * scale;
     }
     if (Pcur != d_P)
         WR_CUDA(cudaMemcpyAsync(d_P, Pcur, sizeof(uint32_t) * (Dbound + 1) * nq, cudaMemcpyDeviceToDevice, s));
     // divide the cumulative column scales out of P
     k_unscale<<<(unsigned)std::min<int64_t>(((Dbound + 1) * nq + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, s>>>(
-        d_P, n, q, Dbound, scale.as<uint32_t>(), mp);
+        d_P, nr, q, Dbound, scale.as<uint32_t>(), mp);
+    WR_LAUNCHED(ctx);
+    if (dmax_out) {
+        int h = 0;
+        WR_CUDA(cudaMemcpyAsync(&h, dmax.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        WR_CUDA(cudaStreamSynchronize(s));
+        *dmax_out = std::min<int64_t>(std::max(h, 0), Dbound);
+    }
+    WR_CUDA(cudaStreamSynchronize(s));
+    return WR_OK;
+}
+
+// F = [S | -I_m]: L x m x q residual coefficients of the whole problem
+__global__ void k_build_F(const uint32_t *__restrict__ S, int64_t L, int m, int n, uint32_t p,
+                          uint32_t *__restrict__ F) {
+    const int q = m + n;
+    const int64_t total = L * m * q;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = x / (m * q);
+        const int rem = (int)(x - k * m * q), a = rem / q, c = rem % q;
+        F[x] = c < n ? S[((size_t)k * m + a) * n + c] : ((k == 0 && c - n == a) ? p - 1 : 0u);
+    }
+}
+
+// P[t][r][c] = M[t][r][c] for the first n of the q rows, t <= D
+__global__ void k_top_rows(const uint32_t *__restrict__ M, int64_t D, int n, int q, uint32_t *__restrict__ P) {
+    const int64_t total = (D + 1) * n * q;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = x / ((int64_t)n * q);
+        const int rem = (int)(x - t * n * q);
+        P[x] = M[((size_t)t * q + rem / q) * q + rem % q];
+    }
+}
+
+// PM-Basis (Section 2.3): the sigma-basis of the residual F (d orders, m x q)
+// for the starting degrees in d_deg (updated to the final degrees) is M1 M2,
+// M1 the basis of the first h orders and M2 that of the residual
+// R = (F M1) div x^h mod x^(d-h), the latter started from M1's degrees.  The
+// leaves (d <= leaf) run the blocked M-Basis on a general residual; the
+// residual and the product are polynomial matrix products by NTT (CRT over
+// three FFT primes).  Each leaf's basis is the order-by-order one, so M is.
+static wr_status pm_basis_rec(wr_ctx *ctx, const uint32_t *F, int64_t d, int m, int q, uint32_t p,
+                              int32_t *d_deg, int64_t leaf, DevBuf &M, int64_t &DM) {
+    cudaStream_t s = ctx->stream;
+    std::vector<int32_t> h0(q);
+    WR_CUDA(cudaMemcpyAsync(h0.data(), d_deg, sizeof(int32_t) * q, cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    const int dbase = *std::min_element(h0.begin(), h0.end());
+    if (d <= leaf) {
+        WR_TRY(dev_alloc(ctx, M, sizeof(uint32_t) * (size_t)(d + 2) * q * q));
+        DevBuf degin;
+        WR_TRY(dev_alloc(ctx, degin, sizeof(int32_t) * q));
+        WR_CUDA(cudaMemcpyAsync(degin.ptr, d_deg, sizeof(int32_t) * q, cudaMemcpyDeviceToDevice, s));
+        return mbasis_run(ctx, F, d, m, q, q - m, p, M.as<uint32_t>(), d_deg, degin.as<int32_t>(), dbase, d + 1, &DM);
+    }
+    int64_t h = ((d / 2 + 63) / 64) * 64;
+    if (h >= d) h = d / 2;
+    DevBuf M1, M2, R;
+    int64_t DM1 = 0, DM2 = 0;
+    WR_TRY(pm_basis_rec(ctx, F, h, m, q, p, d_deg, leaf, M1, DM1));
+    WR_TRY(dev_alloc(ctx, R, sizeof(uint32_t) * (size_t)(d - h) * m * q));
+    WR_TRY(polymat_mul(ctx, F, d, M1.as<uint32_t>(), DM1 + 1, m, q, q, h, d, p, R.as<uint32_t>()));
+    WR_TRY(pm_basis_rec(ctx, R.as<uint32_t>(), d - h, m, q, p, d_deg, leaf, M2, DM2));
+    R.release();
+    // degree of M: at most DM1 + DM2, and at most the largest final degree
+    // minus the smallest starting one
+    std::vector<int32_t> h1(q);
+    WR_CUDA(cudaMemcpyAsync(h1.data(), d_deg, sizeof(int32_t) * q, cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    const int64_t bound = (int64_t)*std::max_element(h1.begin(), h1.end()) - dbase;
+    DM = std::max<int64_t>(0, std::min<int64_t>(DM1 + DM2, bound));
+    WR_TRY(dev_alloc(ctx, M, sizeof(uint32_t) * (size_t)(DM + 2) * q * q));
+    WR_CUDA(cudaMemsetAsync(M.ptr, 0, M.bytes, s));
+    return polymat_mul(ctx, M1.as<uint32_t>(), DM1 + 1, M2.as<uint32_t>(), DM2 + 1, q, q, q, 0, DM + 1, p,
+                       M.as<uint32_t>());
+}
+
+wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n, uint32_t p,
+                      uint32_t *d_P, int32_t *d_deg, int64_t Dcap) {
+    if (m < 1 || n < 1 || m > 32 || n > 32) return fail(WR_EINVAL, "block sizes must be in 1..32");
+    ctx->last.sigma_window_ms = ctx->last.sigma_local_ms = ctx->last.sigma_apply_ms = 0.0;
+    const bool automatic = ctx->sigma_leaf <= 0;
+    const int64_t leaf = automatic ? SIGMA_LEAF_DEFAULT : ctx->sigma_leaf;
+    if (L <= leaf || (automatic && (L <= SIGMA_PM_MIN_L || m + n > 32)))
+        return mbasis_run(ctx, d_S, L, m, n, n, p, d_P, d_deg, nullptr, 0, Dcap, nullptr);
+    const int q = m + n;
+    cudaStream_t s = ctx->stream;
+    DevBuf F, M;
+    WR_TRY(dev_alloc(ctx, F, sizeof(uint32_t) * (size_t)L * m * q));
+    const unsigned g = (unsigned)std::min<int64_t>((L * m * q + 255) / 256, (int64_t)ctx->num_sms * 16);
+    k_build_F<<<g, 256, 0, s>>>(d_S, L, m, n, p, F.as<uint32_t>());
+    WR_LAUNCHED(ctx);
+    std::vector<int32_t> deg0(q);
+    for (int c = 0; c < q; c++) deg0[c] = c < n ? 0 : 1;
+    WR_CUDA(cudaMemcpyAsync(d_deg, deg0.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    int64_t DM = 0;
+    WR_TRY(pm_basis_rec(ctx, F.as<uint32_t>(), L, m, q, p, d_deg, leaf, M, DM));
+    if (DM > Dcap) return fail(WR_EINVAL, "sigma-basis degree cap too small");
+    WR_CUDA(cudaMemsetAsync(d_P, 0, sizeof(uint32_t) * (Dcap + 1) * n * q, s));
+    const unsigned g2 = (unsigned)std::min<int64_t>(((DM + 1) * n * q + 255) / 256, (int64_t)ctx->num_sms * 16);
+    k_top_rows<<<g2, 256, 0, s>>>(M.as<uint32_t>(), DM, n, q, d_P);
     WR_LAUNCHED(ctx);
     WR_CUDA(cudaStreamSynchronize(s));
     return WR_OK;

@@ -70,6 +70,7 @@ _sig = {
     "wr_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
     "wr_last_timings": ([vp, P(wr_timings)], ctypes.c_int),
     "wr_set_sigma_chunk": ([vp, i32], ctypes.c_int),
+    "wr_set_sigma_leaf": ([vp, i64], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -197,6 +198,10 @@ def wr_rank_batch(ctx: int, mats: Sequence[int], params: Sequence[wr_params]) ->
 
 def wr_set_sigma_chunk(ctx: int, orders: int) -> None:
     _check(_lib.wr_set_sigma_chunk(vp(ctx), orders))
+
+
+def wr_set_sigma_leaf(ctx: int, orders: int) -> None:
+    _check(_lib.wr_set_sigma_leaf(vp(ctx), orders))
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

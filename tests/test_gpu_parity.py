@@ -388,6 +388,46 @@ def test_errors_are_reported(wr, ctx):
     assert ei.value.status == wr.WR_EOVERFLOW
 
 
+@pytest.mark.parametrize("m,n,L,leaf", [(1, 1, 700, 64), (2, 3, 610, 64), (3, 2, 900, 200), (4, 4, 950, 128),
+                                      (8, 8, 1300, 200), (8, 8, 700, 64), (5, 5, 390, 64)])
+@pytest.mark.parametrize("p", [65521, 2147483629, 1073741789])
+def test_pm_basis_matches_order_by_order(wr, ctx, m, n, L, leaf, p):
+    """PM-Basis (recursive halving, NTT products over three FFT primes, CRT
+    back to p) gives the order-by-order M-Basis bit for bit: the leaf size is
+    forced small so that the sequence is split several times."""
+    rng = np.random.default_rng(m * 7919 + n * 31 + L + leaf)
+    S = rng.integers(0, p, size=(L, m, n)).astype(np.uint32)
+    M, deg = oracle.mbasis(S, p)
+    wr.wr_set_sigma_leaf(ctx, leaf)
+    try:
+        P, dg = gpu_sigma(wr, ctx, S, p)
+    finally:
+        wr.wr_set_sigma_leaf(ctx, 0)
+    assert np.array_equal(dg, deg)
+    D = M.shape[0] - 1
+    assert np.array_equal(P[: D + 1], M[:, :n, :])
+    assert not P[D + 1:].any()
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_rank_with_pm_basis(wr, ctx, m):
+    p = 1073741789
+    for t in range(2):
+        rng = np.random.default_rng(t * 13 + m)
+        R, C = int(rng.integers(300, 700)), int(rng.integers(300, 700))
+        r = int(rng.integers(100, min(R, C)))
+        A = synth.planted_sparse(R, C, r, row_len=int(rng.integers(3, 8)), seed=t + 500 * m)
+        ref = oracle.rank_wiedemann(A, p, m, m, seed=t)
+        wr.wr_set_sigma_leaf(ctx, 64)
+        try:
+            g = gpu_rank(wr, ctx, A, p, m, m, t, want=3)
+        finally:
+            wr.wr_set_sigma_leaf(ctx, 0)
+        assert g["rank"] == ref["rank"] == r
+        assert (g["deg_det"], g["codeg"], g["sum_delta"]) == (ref["deg_det"], ref["codeg"], ref["sum_delta"])
+        assert np.array_equal(g["F"], ref["F"])
+
+
 # ------------------------------------------------------------------ full size: config 1
 
 def _annihilates(S, F, delta, p, i):
