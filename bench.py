@@ -34,6 +34,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "mod-p SpMM nnz·vec/s, %HBM peak; batched/served vs plain time-to-rank (exact)"
+# DRAM bytes (read + write) per k_spmm launch in the warm loop, from one ncu
+# capture of this kernel: dram__bytes_read.sum + dram__bytes_write.sum, with
+# --cache-control none, launches 2000-2019 of
+# `python bench.py --steps 1 --warmup 0 --no-cpu-baseline` (both passes
+# averaged; profiles/spmm_traffic_config1.md).
+SPMM_TRAFFIC_PER_LAUNCH = 0.58e6
 UNIT = "nnz*vec/s"
 
 
@@ -410,7 +416,9 @@ def main():
         per_launch = spmm_bytes / spmm_launches
         ach = per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak if peak else 6800.0, "unit": "GB/s",
-                "frac": ach / (peak if peak else 6800.0), "traffic": None,
+                "frac": ach / (peak if peak else 6800.0), "traffic": SPMM_TRAFFIC_PER_LAUNCH,
+                "traffic_note": "warm L2: the working set stays resident, so DRAM traffic is far below the "
+                                "algorithmic bytes; the pass is bound by random 32-byte gathers from L2",
                 "peak_source": "measured" if peak else "fallback",
                 "kernel": "k_spmm (both passes of the black box)", "avg_launch_us": avg_s * 1e6,
                 "bytes_per_launch": per_launch, "sampled_launches": spmm_launches}
