@@ -123,6 +123,16 @@ wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
  * (default) = automatic: PM-Basis with 8,192-order leaves for sequences longer
  * than 131,072 orders when m + n <= 32, the blocked M-Basis otherwise. */
 wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders);
+/* SpMM tile shape: the residues each lane gathers from a row of the dense
+ * block (1, 2 or 4; the row's n residues are spread over n / that many lanes).
+ * With autotuning on (default), the first sequence or black-box application
+ * on a matrix with at least 2^20 stored entries times each candidate on that
+ * matrix's two layouts (a few launches each, CUDA events) and keeps the
+ * fastest, per matrix, layout and block width; smaller matrices and autotune
+ * off use the default (2 residues for n <= 8, 4 above).  wr_set_lane_width
+ * forces one (0 = tuned or default).  Results never depend on it. */
+wr_status wr_set_autotune(wr_ctx *ctx, int32_t on);
+wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
 
 /* ---------------------------------------------------------------- matrices */
 

@@ -200,6 +200,20 @@ extern "C" wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders) {
     return WR_OK;
 }
 
+extern "C" wr_status wr_set_autotune(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->autotune = on != 0;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if (residues != 0 && residues != 1 && residues != 2 && residues != 4)
+        return fail(WR_EINVAL, "lane width must be 0 (tuned or default), 1, 2 or 4 residues");
+    ctx->lane_width = residues;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out) {
     if (!ctx || !out) return fail(WR_EINVAL, "null argument");
     *out = ctx->last;

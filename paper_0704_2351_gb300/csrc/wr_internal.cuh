@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <stdint.h>
 
 #include <string>
@@ -299,6 +301,8 @@ struct wr_ctx {
     int batch_slots = 8;    // slots (streams + host threads) of wr_rank_batch
     int sigma_chunk = 0;    // orders per sigma-basis chunk (0: automatic)
     int64_t sigma_leaf = 0; // orders per PM-Basis leaf (0: automatic)
+    bool autotune = true;   // tune the SpMM lane width per matrix and block width
+    int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
     wr_timings last{};
 };
 
@@ -307,6 +311,9 @@ struct wr_matrix {
     int64_t rows = 0, cols = 0, nnz = 0;
     wr::Sell a;    // rows of A
     wr::Sell at;   // rows of A^T
+    // SpMM residues per lane tuned for [layout a / at][log2 block width] (0: not yet)
+    mutable std::mutex tune_mu;
+    mutable int tuned_w[2][6] = {{0}};
 };
 
 struct wr_result {

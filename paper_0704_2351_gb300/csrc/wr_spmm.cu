@@ -29,12 +29,15 @@ namespace {
 // from an L2-resident table run fastest as 4 lanes of 8 bytes (measured on
 // GB300: 10-15% ahead of 2 lanes of 16 bytes, well ahead of one lane of 32
 // bytes); rows of 64 bytes and more take 16 bytes per lane.
-template <int NV>
+template <int NV, int WW = (NV <= 8 ? (NV < 2 ? NV : 2) : 4)>
 struct Lanes {
-    static constexpr int W = NV <= 8 ? (NV < 2 ? NV : 2) : 4;  // residues per lane
-    static constexpr int G = NV / W;           // lanes per row (1, 2, 4, 8)
-    static constexpr int RPW = 32 / G;         // rows (light) or entries (vector) per warp step
+    static constexpr int W = WW;       // residues per lane
+    static constexpr int G = NV / W;   // lanes per row
+    static constexpr int RPW = 32 / G; // rows (light) or entries (vector) per warp step
+    static_assert(NV % W == 0 && G >= 1 && G <= 32, "lane width must divide the block width");
 };
+// default residues per lane for a block width (used when nothing is tuned)
+inline int default_lane_width(int nv) { return nv <= 8 ? (nv < 2 ? nv : 2) : 4; }
 
 template <int W>
 __device__ __forceinline__ void ldv(const uint32_t *p, uint32_t (&v)[W]) {
@@ -103,13 +106,13 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
 // over the segment's contiguous entries, then a shuffle reduction.
 // Blocks [vblocks, ...): G warps per SELL chunk of 32 light rows; warp q of
 // the chunk takes rows [q*RPW, (q+1)*RPW), G lanes per row.
-template <int NV>
+template <int NV, int WL>
 __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__restrict__ x,
                                               uint32_t *__restrict__ y,
                                               const uint32_t *__restrict__ scale,
                                               unsigned long long *__restrict__ acc64, ModP mp,
                                               int *__restrict__ term_counter, int64_t vblocks) {
-    using Ln = Lanes<NV>;
+    using Ln = Lanes<NV, WL>;
     constexpr int W = Ln::W, G = Ln::G, RPW = Ln::RPW;
     if (term_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(term_counter, 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -386,18 +389,33 @@ __global__ void k_unpad(int64_t N, int width, int nv, const uint32_t *__restrict
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+template <int NV, int WL>
+void launch_spmm_kernel(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y, const uint32_t *scale,
+                        unsigned long long *acc64, const ModP &mp, int *term_counter) {
+    const int64_t vblocks = (A.nseg + 7) / 8;
+    const int64_t lblocks = (A.nchunks * Lanes<NV, WL>::G + 7) / 8;
+    const int64_t blocks = std::max<int64_t>(vblocks + lblocks, term_counter ? 1 : 0);
+    if (blocks > 0)
+        k_spmm<NV, WL><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter, vblocks);
+}
+
 template <int NV>
 wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y,
                         const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
-                        int *term_counter) {
-    const int64_t vblocks = (A.nseg + 7) / 8;
-    const int64_t lblocks = (A.nchunks * Lanes<NV>::G + 7) / 8;
-    const int64_t blocks = std::max<int64_t>(vblocks + lblocks, term_counter ? 1 : 0);
-    if (blocks > 0) {
-        k_spmm<NV><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter, vblocks);
-        WR_LAUNCHED(ctx);
+                        int *term_counter, int wl, bool finalize = true) {
+    const int vblocks_any = (A.nseg + A.nchunks) > 0 || term_counter;
+    switch (wl) {
+        case 1: launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter); break;
+        case 2:
+            if constexpr (NV % 2 == 0) { launch_spmm_kernel<NV, 2>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            else return fail(WR_EINVAL, "lane width does not divide the block width");
+        case 4:
+            if constexpr (NV % 4 == 0) { launch_spmm_kernel<NV, 4>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            else return fail(WR_EINVAL, "lane width does not divide the block width");
+        default: return fail(WR_EINVAL, "lane width must be 1, 2 or 4");
     }
-    if (A.nsplit > 0) {
+    if (vblocks_any) WR_LAUNCHED(ctx);
+    if (finalize && A.nsplit > 0) {
         int64_t cnt = A.nsplit * NV;
         k_finalize_split<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
                                                                        y, scale, mp);
@@ -406,18 +424,94 @@ wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
     return WR_OK;
 }
 
+// wl: residues per lane (0 = the default for nv); finalize = false leaves
+// the split rows' sums in acc64 (used by the lane-width tuner only)
 wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
                       const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
-                      int *term_counter) {
+                      int *term_counter, int wl = 0, bool finalize = true) {
+    if (wl <= 0 || wl > nv) wl = default_lane_width(nv);
     switch (nv) {
-        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter);
-        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter);
-        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter);
-        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter);
-        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter);
-        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter);
+        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
         default: return fail(WR_EINVAL, "unsupported padded block width");
     }
+}
+
+// Lane-width tuner: times the candidate residues-per-lane (1, 2, 4) of one
+// SpMM layout on the matrix itself (zero block: the gather addresses, which
+// set the time, do not depend on the values) and keeps the fastest.  The
+// result never depends on the choice.
+int nv_index(int nv) {
+    int k = 0;
+    while ((1 << k) < nv) k++;
+    return k;
+}
+
+static wr_status tune_lane_width(wr_ctx *ctx, const Sell &S, int nv, int *out) {
+    *out = default_lane_width(nv);
+    if (S.nslots + S.nvent < (int64_t)1 << 20) return WR_OK;  // too small to matter
+    cudaStream_t s = ctx->stream;
+    DevBuf x, y, scale, acc;
+    WR_TRY(dev_alloc(ctx, x, sizeof(uint32_t) * (size_t)std::max<int64_t>(S.ncols, 1) * nv));
+    WR_TRY(dev_alloc(ctx, y, sizeof(uint32_t) * (size_t)std::max<int64_t>(S.nrows, 1) * nv));
+    WR_TRY(dev_alloc(ctx, scale, sizeof(uint32_t) * (size_t)std::max<int64_t>(S.nrows, 1)));
+    WR_TRY(dev_alloc(ctx, acc, sizeof(unsigned long long) * (size_t)std::max<int64_t>(S.nsplit, 1) * nv));
+    WR_CUDA(cudaMemsetAsync(x.ptr, 0, x.bytes, s));
+    WR_CUDA(cudaMemsetAsync(scale.ptr, 0, scale.bytes, s));
+    WR_CUDA(cudaMemsetAsync(acc.ptr, 0, acc.bytes, s));
+    const ModP mp = make_modp(2147483629u);
+    const SellView v = view(S);
+    cudaEvent_t e0, e1;
+    WR_CUDA(cudaEventCreate(&e0));
+    WR_CUDA(cudaEventCreate(&e1));
+    float best = 0.0f;
+    for (int wl : {1, 2, 4}) {
+        if (wl > nv || nv % wl != 0 || nv / wl > 32) continue;
+        for (int w = 0; w < 2; w++)
+            WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
+                               acc.as<unsigned long long>(), mp, nullptr, wl, false));
+        WR_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 5; r++)
+            WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
+                               acc.as<unsigned long long>(), mp, nullptr, wl, false));
+        WR_CUDA(cudaEventRecord(e1, s));
+        WR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0.0f || ms < best) {
+            best = ms;
+            *out = wl;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return WR_OK;
+}
+
+// the lane width for a layout: forced by the context, else tuned once per
+// matrix, layout and block width (when the context tunes), else the default
+static wr_status lane_width_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S, int nv, int *out) {
+    if (ctx->lane_width > 0 && ctx->lane_width <= nv && nv % ctx->lane_width == 0) {
+        *out = ctx->lane_width;
+        return WR_OK;
+    }
+    if (!ctx->autotune) {
+        *out = default_lane_width(nv);
+        return WR_OK;
+    }
+    const int layout = &S == &mat->a ? 0 : 1, k = nv_index(nv);
+    std::lock_guard<std::mutex> lk(mat->tune_mu);
+    if (mat->tuned_w[layout][k] == 0) {
+        int w = 0;
+        WR_TRY(tune_lane_width(ctx, S, nv, &w));
+        mat->tuned_w[layout][k] = w;
+    }
+    *out = mat->tuned_w[layout][k];
+    return WR_OK;
 }
 
 template <int NV, bool GRAM>
@@ -471,6 +565,7 @@ struct SeqState {
     ModP mp;
     const Sell *first = nullptr;   // pass 1 layout (output in the other space)
     const Sell *second = nullptr;  // pass 2 layout (output in N-space)
+    int wl1 = 0, wl2 = 0;          // residues per lane of the two passes
     DevBuf T, Wb, D1, D2, d1sq, xh, w2, acc1, acc2, s_raw, counter;
 };
 
@@ -481,6 +576,8 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
     st.first = r.side == 0 ? &mat->a : &mat->at;
     st.second = r.side == 0 ? &mat->at : &mat->a;
     const int nv = r.nv;
+    WR_TRY(lane_width_for(ctx, mat, *st.first, nv, &st.wl1));
+    WR_TRY(lane_width_for(ctx, mat, *st.second, nv, &st.wl2));
     WR_TRY(dev_alloc(ctx, st.T, sizeof(uint32_t) * std::max<int64_t>(r.N * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.Wb, sizeof(uint32_t) * std::max<int64_t>(r.M * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.D1, sizeof(uint32_t) * std::max<int64_t>(r.N, 1)));
@@ -535,10 +632,10 @@ static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
     SellView f = view(*st.first), sc = view(*st.second);
     if (ev) WR_CUDA(cudaEventRecord(ev[0], ctx->stream));
     WR_TRY(launch_spmm(ctx, nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
-                       st.acc1.as<unsigned long long>(), st.mp, st.counter.as<int>()));
+                       st.acc1.as<unsigned long long>(), st.mp, st.counter.as<int>(), st.wl1));
     if (ev) WR_CUDA(cudaEventRecord(ev[1], ctx->stream));
     WR_TRY(launch_spmm(ctx, nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.d1sq.as<uint32_t>(),
-                       st.acc2.as<unsigned long long>(), st.mp, nullptr));
+                       st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
     if (st.r.gram) {
         WR_TRY(launch_project(ctx, st.r.M, st.r.m, st.r.n, nv, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(),
@@ -686,10 +783,10 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
     }
     SellView f = view(*st.first), sc = view(*st.second);
     WR_TRY(launch_spmm(ctx, r.nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
-                       st.acc1.as<unsigned long long>(), st.mp, nullptr));
+                       st.acc1.as<unsigned long long>(), st.mp, nullptr, st.wl1));
     // second pass scaled by D1 (not D1^2): out = D1 A^T D2 A D1 in
     WR_TRY(launch_spmm(ctx, r.nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.D1.as<uint32_t>(),
-                       st.acc2.as<unsigned long long>(), st.mp, nullptr));
+                       st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (r.N > 0) {
         k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out);
         WR_LAUNCHED(ctx);

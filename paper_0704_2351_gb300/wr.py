@@ -71,6 +71,8 @@ _sig = {
     "wr_last_timings": ([vp, P(wr_timings)], ctypes.c_int),
     "wr_set_sigma_chunk": ([vp, i32], ctypes.c_int),
     "wr_set_sigma_leaf": ([vp, i64], ctypes.c_int),
+    "wr_set_autotune": ([vp, i32], ctypes.c_int),
+    "wr_set_lane_width": ([vp, i32], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -202,6 +204,14 @@ def wr_set_sigma_chunk(ctx: int, orders: int) -> None:
 
 def wr_set_sigma_leaf(ctx: int, orders: int) -> None:
     _check(_lib.wr_set_sigma_leaf(vp(ctx), orders))
+
+
+def wr_set_autotune(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_autotune(vp(ctx), 1 if on else 0))
+
+
+def wr_set_lane_width(ctx: int, residues: int) -> None:
+    _check(_lib.wr_set_lane_width(vp(ctx), residues))
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

@@ -226,6 +226,27 @@ def test_sharded_sequence_single_rank_gpu(wr, ctx):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("n", [1, 2, 8, 32])
+def test_lane_widths_give_identical_sequences(wr, ctx, n):
+    """Every SpMM lane width (1, 2, 4 residues per lane where it divides the
+    block width) gives the oracle's sequence; the autotuner only picks
+    among them."""
+    p, m, seed, L = 2147483629, min(n, 4), 5, 40
+    A = heavy_matrix(900, 820, seed=41 + n, heavy=3, heavy_len=500)
+    st = oracle.Setup(A, p, m, n, seed)
+    S_ref = oracle.sequence(A, st, L)
+    try:
+        for wl in [1, 2, 4]:
+            if wl > n or n % wl:
+                continue
+            wr.wr_set_lane_width(ctx, wl)
+            assert np.array_equal(gpu_sequence(wr, ctx, A, p, m, n, seed, L), S_ref), "lane width %d" % wl
+    finally:
+        wr.wr_set_lane_width(ctx, 0)
+    with pytest.raises(wr.WrError):
+        wr.wr_set_lane_width(ctx, 3)
+
+
 # ------------------------------------------------------------------ sigma-basis (A8)
 
 def gpu_sigma(wr, ctx, S, p):
