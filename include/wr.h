@@ -95,6 +95,13 @@ typedef struct {
     double sigma_apply_ms;
 } wr_timings;
 
+/* Device allocator callbacks (for example PyTorch's caching allocator):
+ * alloc(bytes, stream, user) returns device memory usable on `stream` (the
+ * context's stream) or NULL; release(ptr, bytes, stream, user) gives it back,
+ * in stream order (work already queued on `stream` may still use it). */
+typedef void *(*wr_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*wr_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
@@ -132,6 +139,12 @@ wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders);
  * off use the default (2 residues for n <= 8, 4 above).  wr_set_lane_width
  * forces one (0 = tuned or default).  Results never depend on it. */
 wr_status wr_set_autotune(wr_ctx *ctx, int32_t on);
+/* Route the context's device allocations through the caller's allocator
+ * (both callbacks, or NULL, NULL for the default stream-ordered pool).
+ * Matrices keep the allocator they were loaded with until wr_matrix_free;
+ * batch and server slots inherit the context's callbacks, which may then be
+ * called from the library's worker threads. */
+wr_status wr_set_allocator(wr_ctx *ctx, wr_alloc_fn alloc, wr_free_fn release, void *user);
 wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
 
 /* ---------------------------------------------------------------- matrices */

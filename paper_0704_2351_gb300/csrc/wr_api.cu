@@ -27,20 +27,35 @@ wr_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 void DevBuf::release() {
-    if (ptr) cudaFreeAsync(ptr, stream);
+    if (ptr) {
+        if (free_fn) free_fn(ptr, bytes, (void *)stream, free_user);
+        else cudaFreeAsync(ptr, stream);
+    }
     ptr = nullptr;
     bytes = 0;
 }
 
+// Device buffers come from the caller's allocator when one is set
+// (wr_set_allocator), else from the stream-ordered pool (cudaMallocAsync);
+// either way they are used on ctx->stream only and returned on it.
 wr_status dev_alloc(wr_ctx *ctx, DevBuf &b, size_t bytes) {
     b.release();
     if (bytes == 0) bytes = 1;
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(WR_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
-                                   " bytes failed: " + cudaGetErrorString(e));
+    if (ctx->alloc_fn) {
+        p = ctx->alloc_fn(bytes, (void *)ctx->stream, ctx->alloc_user);
+        if (!p) return fail(WR_ENOMEM, "the caller's allocator returned no memory for " + std::to_string(bytes) + " bytes");
+        b.free_fn = ctx->free_fn;
+        b.free_user = ctx->alloc_user;
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(WR_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                       " bytes failed: " + cudaGetErrorString(e));
+        }
+        b.free_fn = nullptr;
+        b.free_user = nullptr;
     }
     b.ptr = p;
     b.bytes = bytes;
@@ -197,6 +212,15 @@ extern "C" wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders) {
     if (!ctx) return fail(WR_EINVAL, "null context");
     if (orders != 0 && orders < 64) return fail(WR_EINVAL, "PM-Basis leaf must be 0 (automatic) or at least 64 orders");
     ctx->sigma_leaf = orders;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_allocator(wr_ctx *ctx, wr_alloc_fn alloc, wr_free_fn release, void *user) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if ((alloc == nullptr) != (release == nullptr)) return fail(WR_EINVAL, "give both allocator callbacks or neither");
+    ctx->alloc_fn = alloc;
+    ctx->free_fn = release;
+    ctx->alloc_user = user;
     return WR_OK;
 }
 
@@ -372,6 +396,14 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
     if (st != WR_OK) {
         delete res;
         return st;
+    }
+    // Monte Carlo consistency: deg det F of a generator of X^T A~^i Y (A~ of
+    // order N) is at most N, and 0 <= codeg <= deg det F
+    if (ro.rank < 0 || ro.rank > r.N || ro.codeg < 0 || ro.deg_det > r.N) {
+        delete res;
+        return fail(WR_EPROBFAIL, "inconsistent readout (rank " + std::to_string(ro.rank) + ", codeg " +
+                                      std::to_string(ro.codeg) + ", deg det " + std::to_string(ro.deg_det) +
+                                      "); retry with another seed");
     }
     res->rank = ro.rank;
     res->deg_det = ro.deg_det;

@@ -211,12 +211,23 @@ struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
+    wr_free_fn free_fn = nullptr;  // caller's allocator (nullptr: cudaFreeAsync)
+    void *free_user = nullptr;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), bytes(o.bytes), stream(o.stream) { o.ptr = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf &&o) noexcept
+        : ptr(o.ptr), bytes(o.bytes), stream(o.stream), free_fn(o.free_fn), free_user(o.free_user) {
+        o.ptr = nullptr;
+        o.bytes = 0;
+    }
     DevBuf &operator=(DevBuf &&o) noexcept {
-        if (this != &o) { release(); ptr = o.ptr; bytes = o.bytes; stream = o.stream; o.ptr = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            ptr = o.ptr; bytes = o.bytes; stream = o.stream; free_fn = o.free_fn; free_user = o.free_user;
+            o.ptr = nullptr;
+            o.bytes = 0;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
@@ -303,6 +314,9 @@ struct wr_ctx {
     int64_t sigma_leaf = 0; // orders per PM-Basis leaf (0: automatic)
     bool autotune = true;   // tune the SpMM lane width per matrix and block width
     int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
+    wr_alloc_fn alloc_fn = nullptr;  // caller's device allocator (nullptr: cudaMallocAsync)
+    wr_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
     wr_timings last{};
 };
 

@@ -48,6 +48,13 @@ size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
 static wr_status make_slot(const wr_ctx *parent, wr_ctx **out) {
     WR_TRY(wr_create(out, parent->device, nullptr));
     (*out)->profiling = parent->profiling;
+    (*out)->autotune = parent->autotune;
+    (*out)->lane_width = parent->lane_width;
+    (*out)->sigma_chunk = parent->sigma_chunk;
+    (*out)->sigma_leaf = parent->sigma_leaf;
+    (*out)->alloc_fn = parent->alloc_fn;
+    (*out)->free_fn = parent->free_fn;
+    (*out)->alloc_user = parent->alloc_user;
     return WR_OK;
 }
 

@@ -72,6 +72,7 @@ _sig = {
     "wr_set_sigma_chunk": ([vp, i32], ctypes.c_int),
     "wr_set_sigma_leaf": ([vp, i64], ctypes.c_int),
     "wr_set_autotune": ([vp, i32], ctypes.c_int),
+    "wr_set_allocator": ([vp, vp, vp, vp], ctypes.c_int),
     "wr_set_lane_width": ([vp, i32], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
@@ -204,6 +205,28 @@ def wr_set_sigma_chunk(ctx: int, orders: int) -> None:
 
 def wr_set_sigma_leaf(ctx: int, orders: int) -> None:
     _check(_lib.wr_set_sigma_leaf(vp(ctx), orders))
+
+
+WR_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+WR_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def wr_set_allocator(ctx: int, alloc=None, release=None, user=None) -> None:
+    """alloc(bytes, stream) -> device pointer (int), release(ptr, bytes, stream):
+    Python callables wrapped as the C callbacks (kept alive on the binding),
+    or None, None for the default pool."""
+    if alloc is None and release is None:
+        _check(_lib.wr_set_allocator(vp(ctx), None, None, None))
+        _allocators.pop(ctx, None)
+        return
+    fa = WR_ALLOC_FN(lambda n, s, u: alloc(n, s or 0) or None) if alloc is not None else None
+    ff = WR_FREE_FN(lambda p, n, s, u: release(p, n, s or 0)) if release is not None else None
+    _check(_lib.wr_set_allocator(vp(ctx), ctypes.cast(fa, vp) if fa else None,
+                                 ctypes.cast(ff, vp) if ff else None, None))
+    _allocators[ctx] = (fa, ff)
+
+
+_allocators = {}
 
 
 def wr_set_autotune(ctx: int, on: bool) -> None:

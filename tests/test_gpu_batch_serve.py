@@ -191,3 +191,38 @@ def test_server_refuses_invalid_requests_and_keeps_serving(wr, ctx):
     wr.wr_server_stop(srv)
     wr.wr_matrix_free(h)
     assert oracle.rank_sparse(A, PRIMES[3]) == 150
+
+
+def test_torch_caching_allocator_owns_the_device_memory(wr, ctx):
+    """With wr_set_allocator every device buffer of the library (matrix
+    layouts, sequence state, sigma-basis, batch slots) comes from PyTorch's
+    caching allocator and goes back to it; the results do not change."""
+    counts = {"alloc": 0, "free": 0}
+
+    def alloc(nbytes, stream):
+        counts["alloc"] += 1
+        return torch.cuda.caching_allocator_alloc(nbytes, device=0, stream=stream)
+
+    def release(ptr, nbytes, stream):
+        counts["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    A = synth.planted_sparse(1500, 1400, 1200, row_len=7, seed=21)
+    c2 = wr.wr_create(0)
+    try:
+        wr.wr_set_allocator(c2, alloc, release)
+        h = _load(wr, c2, A)
+        prm = [_params(wr, PRIMES[k], 8, 50 + k, k == 1) for k in range(3)]
+        got = [_result(wr, wr.wr_rank(c2, h, prm[0]), 8, 8)]
+        got += [_result(wr, o, 8, 8) for o in wr.wr_rank_batch(c2, [h, h], prm[1:])]
+        wr.wr_matrix_free(h)
+        assert counts["alloc"] > 0 and counts["alloc"] == counts["free"]
+    finally:
+        wr.wr_destroy(c2)
+    h0 = _load(wr, ctx, A)
+    for g, p in zip(got, prm):
+        assert _same(g, _result(wr, wr.wr_rank(ctx, h0, p), 8, 8))
+        assert g["rank"] == 1200
+    wr.wr_matrix_free(h0)
+    with pytest.raises(wr.WrError):
+        wr.wr_set_allocator(ctx, alloc, None)
