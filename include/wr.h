@@ -151,10 +151,14 @@ wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
 
 /* Ingest a CSR matrix (Section 2.4 step 1 operates on it as a black box).
  * rowptr: rows + 1 int64, nondecreasing, rowptr[0] = 0; colidx: int32 in
- * [0, cols); vals: small signed integers, |v| <= 127 (the paper's boundary
- * matrices hold 0, +-1 and small integers).  cols < 2^24 and every row and
- * column < 2^24 entries (exact int64 accumulation), else WR_EOVERFLOW.
- * Builds SELL-C-sigma layouts of A and A^T on the device. */
+ * [0, cols); vals: small signed integers (the paper's boundary matrices hold
+ * 0, +-1 and small integers).  rows, cols < 2^31; every row < 2^24 entries.
+ * Entries in [-127, 127] with rows, cols < 2^24 are packed with their column
+ * in one 32-bit word; otherwise (entries up to |v| <= 32767, or a dimension
+ * of 2^24 and more) the layout keeps 32-bit columns with int16 values beside
+ * them, and every row and column must then hold fewer than 65,536 entries
+ * (exact int64 sums); anything else is WR_EOVERFLOW.  Builds SELL-C-sigma
+ * layouts of A and A^T on the device. */
 wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
                              const int32_t *colidx, const int32_t *vals, wr_matrix **out);
 /* Same, from arrays already in device memory (nnz = rowptr[rows]). */

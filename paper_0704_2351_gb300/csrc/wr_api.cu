@@ -252,23 +252,29 @@ static wr_status load_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nn
     if (!ctx || !out) return fail(WR_EINVAL, "null argument");
     *out = nullptr;
     if (rows < 0 || cols < 0 || nnz < 0) return fail(WR_EINVAL, "negative size");
-    if (rows >= (int64_t(1) << 31) || cols >= (int64_t(1) << 24))
-        return fail(WR_EOVERFLOW, "rows must be < 2^31 and cols < 2^24");
+    if (rows >= (int64_t(1) << 31) || cols >= (int64_t(1) << 31))
+        return fail(WR_EOVERFLOW, "rows and cols must be < 2^31");
     if (nnz > 0 && (!d_colidx || !d_vals)) return fail(WR_EINVAL, "null column or value array");
     if (!d_rowptr) return fail(WR_EINVAL, "null row pointer array");
     WR_CUDA(cudaSetDevice(ctx->device));
-    WR_TRY(validate_csr(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals));
+    bool wide = rows >= (int64_t(1) << 24) || cols >= (int64_t(1) << 24);
+    WR_TRY(validate_csr(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, &wide));
     wr_matrix *m = new wr_matrix();
     m->ctx = ctx;
     m->rows = rows;
     m->cols = cols;
     m->nnz = nnz;
-    wr_status st = build_sell(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, m->a);
+    wr_status st = build_sell(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, m->a, wide);
     if (st == WR_OK) {
         DevBuf rpt, cit, vat;
         st = transpose_csr(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, rpt, cit, vat);
+        if (st == WR_OK && wide) {  // column lengths: the rows of A^T
+            bool w2 = true;
+            st = validate_csr(ctx, cols, rows, nnz, rpt.as<int64_t>(), cit.as<int32_t>(), vat.as<int32_t>(), &w2);
+        }
         if (st == WR_OK)
-            st = build_sell(ctx, cols, rows, nnz, rpt.as<int64_t>(), cit.as<int32_t>(), vat.as<int32_t>(), m->at);
+            st = build_sell(ctx, cols, rows, nnz, rpt.as<int64_t>(), cit.as<int32_t>(), vat.as<int32_t>(), m->at,
+                            wide);
     }
     if (st != WR_OK) {
         delete m;

@@ -19,7 +19,7 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-enum : int { ERR_ROWPTR = 1, ERR_COL = 2, ERR_VAL = 4, ERR_ROWLEN = 8 };
+enum : int { ERR_ROWPTR = 1, ERR_COL = 2, ERR_VAL = 4, ERR_ROWLEN = 8, ERR_WIDEVAL = 16, ERR_ROWLEN16 = 32 };
 
 // Block-wide exclusive scan of one value per thread; returns the block total.
 __device__ int64_t block_exclusive_scan(int64_t v, int64_t &excl) {
@@ -98,13 +98,15 @@ __global__ void k_validate(int64_t rows, int64_t cols, int64_t nnz, const int64_
         int64_t a = rowptr[i], b = rowptr[i + 1];
         if (b < a || a < 0 || b > nnz) e |= ERR_ROWPTR;
         else if (b - a >= (int64_t(1) << 24)) e |= ERR_ROWLEN;
+        else if (b - a >= (int64_t(1) << 16)) e |= ERR_ROWLEN16;
     }
     if (tid == 0 && (rowptr[0] != 0 || rowptr[rows] != nnz)) e |= ERR_ROWPTR;
     for (int64_t k = tid; k < nnz; k += stride) {
         int32_t c = colidx[k];
         int32_t v = vals[k];
         if (c < 0 || c >= cols) e |= ERR_COL;
-        if (v < -127 || v > 127) e |= ERR_VAL;
+        if (v < -32767 || v > 32767) e |= ERR_VAL;
+        else if (v < -127 || v > 127) e |= ERR_WIDEVAL;
     }
     if (e) atomicOr(err, e);
 }
@@ -213,7 +215,7 @@ __global__ void k_fill_light(int64_t nchunks, int64_t nlight, const int32_t *__r
                              const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                              const int32_t *__restrict__ vals, const int64_t *__restrict__ chunk_off,
                              const int32_t *__restrict__ chunk_len, uint32_t *__restrict__ entries,
-                             uint32_t *__restrict__ vrow) {
+                             uint32_t *__restrict__ vrow, int16_t *__restrict__ wvals) {
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t pos = tid; pos < nchunks * SELL_C; pos += stride) {
@@ -225,14 +227,22 @@ __global__ void k_fill_light(int64_t nchunks, int64_t nlight, const int32_t *__r
             const int32_t r = sorted[pos];
             const int64_t s = rowptr[r];
             const int l = (int)(rowptr[r + 1] - s);
+            int16_t *wdst = wvals ? wvals + chunk_off[c] + lane : nullptr;
             for (int j = 0; j < clen; j++) {
                 uint32_t w = 0;
-                if (j < l) w = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
+                if (wdst) {  // wide: the column in the entry word, the value beside it
+                    if (j < l) w = (uint32_t)colidx[s + j];
+                    wdst[(int64_t)j * SELL_C] = j < l ? (int16_t)vals[s + j] : (int16_t)0;
+                } else if (j < l) {
+                    w = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
+                }
                 dst[(int64_t)j * SELL_C] = w;
             }
             vrow[pos] = (uint32_t)r;
         } else {
             for (int j = 0; j < clen; j++) dst[(int64_t)j * SELL_C] = 0;
+            if (wvals)
+                for (int j = 0; j < clen; j++) wvals[chunk_off[c] + lane + (int64_t)j * SELL_C] = 0;
             vrow[pos] = VROW_EMPTY;
         }
     }
@@ -245,7 +255,7 @@ __global__ void k_fill_vector(int64_t rows, const int64_t *__restrict__ rowptr, 
                               const int64_t *__restrict__ is_split, const int64_t *__restrict__ split_id,
                               uint32_t *__restrict__ ventries, int64_t *__restrict__ seg_start,
                               int32_t *__restrict__ seg_len, uint32_t *__restrict__ seg_row,
-                              int32_t *__restrict__ split_row) {
+                              int32_t *__restrict__ split_row, int16_t *__restrict__ vwvals) {
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -253,8 +263,15 @@ __global__ void k_fill_vector(int64_t rows, const int64_t *__restrict__ rowptr, 
         const int64_t len = vlen[i];
         if (len == 0) continue;
         const int64_t s = rowptr[i], o = voff[i];
-        for (int64_t j = lane; j < len; j += 32)
-            ventries[o + j] = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
+        if (vwvals) {
+            for (int64_t j = lane; j < len; j += 32) {
+                ventries[o + j] = (uint32_t)colidx[s + j];
+                vwvals[o + j] = (int16_t)vals[s + j];
+            }
+        } else {
+            for (int64_t j = lane; j < len; j += 32)
+                ventries[o + j] = ((uint32_t)colidx[s + j] << 8) | ((uint32_t)vals[s + j] & 0xFFu);
+        }
         const int64_t ns = (len + VSEG - 1) / VSEG;
         const uint32_t tgt = is_split[i] ? (VROW_SPLIT | (uint32_t)split_id[i]) : (uint32_t)i;
         for (int64_t k = lane; k < ns; k += 32) {
@@ -306,8 +323,11 @@ wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, i
     return WR_OK;
 }
 
+// Checks a CSR matrix; *wide (in: already wide because of the dimensions;
+// out: wide) selects the layout with 32-bit columns and int16 values, needed
+// for entries outside [-127, 127] or dimensions of 2^24 and more.
 wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
-                       const int32_t *d_colidx, const int32_t *d_vals) {
+                       const int32_t *d_colidx, const int32_t *d_vals, bool *wide) {
     DevBuf err;
     WR_TRY(dev_alloc(ctx, err, sizeof(int)));
     WR_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), ctx->stream));
@@ -319,8 +339,12 @@ wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, con
     WR_TRY(read_err(ctx, err.as<int>(), &h));
     if (h & ERR_ROWPTR) return fail(WR_EINVAL, "rowptr is not a valid CSR row pointer array");
     if (h & ERR_COL) return fail(WR_EINVAL, "column index out of range");
-    if (h & ERR_VAL) return fail(WR_EOVERFLOW, "matrix entry outside [-127, 127]");
+    if (h & ERR_VAL) return fail(WR_EOVERFLOW, "matrix entry outside [-32767, 32767]");
     if (h & ERR_ROWLEN) return fail(WR_EOVERFLOW, "a row holds 2^24 or more entries");
+    if (h & ERR_WIDEVAL) *wide = true;
+    if (*wide && (h & ERR_ROWLEN16))
+        return fail(WR_EOVERFLOW, "with entries outside [-127, 127] (or a dimension of 2^24 or more) every row and "
+                                  "column must hold fewer than 65,536 entries");
     return WR_OK;
 }
 
@@ -352,10 +376,11 @@ wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, co
 }
 
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
-                     const int32_t *d_colidx, const int32_t *d_vals, Sell &out) {
+                     const int32_t *d_colidx, const int32_t *d_vals, Sell &out, bool wide) {
     (void)nnz;
     out.nrows = rows;
     out.ncols = cols;
+    out.wide = wide;
     const int threads = 256;
     cudaStream_t st = ctx->stream;
     const int64_t R1 = rows + 1;
@@ -405,11 +430,13 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
     WR_TRY(dev_alloc(ctx, out.seg_len, sizeof(int32_t) * std::max<int64_t>(out.nseg, 1)));
     WR_TRY(dev_alloc(ctx, out.seg_row, sizeof(uint32_t) * std::max<int64_t>(out.nseg, 1)));
     WR_TRY(dev_alloc(ctx, out.split_row, sizeof(int32_t) * std::max<int64_t>(out.nsplit, 1)));
+    if (wide) WR_TRY(dev_alloc(ctx, out.vwvals, sizeof(int16_t) * std::max<int64_t>(out.nvent, 1)));
     if (out.nseg > 0) {
         k_fill_vector<<<grid_for(ctx, rows * 32, threads), threads, 0, st>>>(
             rows, d_rowptr, d_colidx, d_vals, vlen.as<int64_t>(), voff.as<int64_t>(), segbase.as<int64_t>(),
             is_split.as<int64_t>(), split_id.as<int64_t>(), out.ventries.as<uint32_t>(), out.seg_start.as<int64_t>(),
-            out.seg_len.as<int32_t>(), out.seg_row.as<uint32_t>(), out.split_row.as<int32_t>());
+            out.seg_len.as<int32_t>(), out.seg_row.as<uint32_t>(), out.split_row.as<int32_t>(),
+            wide ? out.vwvals.as<int16_t>() : nullptr);
         WR_LAUNCHED(ctx);
     }
 
@@ -423,6 +450,7 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
     if (out.nchunks == 0) {
         WR_CUDA(cudaMemsetAsync(out.chunk_off.ptr, 0, sizeof(int64_t), st));
         WR_TRY(dev_alloc(ctx, out.entries, sizeof(uint32_t)));
+        if (wide) WR_TRY(dev_alloc(ctx, out.wvals, sizeof(int16_t)));
         out.nslots = 0;
         WR_CUDA(cudaStreamSynchronize(st));
         return WR_OK;
@@ -440,9 +468,11 @@ wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const
     WR_CUDA(cudaStreamSynchronize(st));
     out.nslots = nslots;
     WR_TRY(dev_alloc(ctx, out.entries, sizeof(uint32_t) * std::max<int64_t>(nslots, 1)));
+    if (wide) WR_TRY(dev_alloc(ctx, out.wvals, sizeof(int16_t) * std::max<int64_t>(nslots, 1)));
     k_fill_light<<<grid_for(ctx, out.nchunks * SELL_C, threads), threads, 0, st>>>(
         out.nchunks, out.nlight, sorted.as<int32_t>(), d_rowptr, d_colidx, d_vals, out.chunk_off.as<int64_t>(),
-        out.chunk_len.as<int32_t>(), out.entries.as<uint32_t>(), out.vrow.as<uint32_t>());
+        out.chunk_len.as<int32_t>(), out.entries.as<uint32_t>(), out.vrow.as<uint32_t>(),
+        wide ? out.wvals.as<int16_t>() : nullptr);
     WR_LAUNCHED(ctx);
     WR_CUDA(cudaStreamSynchronize(st));
     return WR_OK;

@@ -275,6 +275,11 @@ struct Sell {
     DevBuf seg_row;        // uint32 [nseg]
     int64_t nsplit = 0;    // rows with more than one segment
     DevBuf split_row;      // int32  [nsplit]
+    // wide layout (entries outside [-127, 127] or a dimension >= 2^24): the
+    // entry words hold the column alone and the values sit beside them
+    bool wide = false;
+    DevBuf wvals;          // int16  [nslots]
+    DevBuf vwvals;         // int16  [nvent]
 };
 
 struct SellView {
@@ -288,13 +293,16 @@ struct SellView {
     const int32_t *seg_len;
     const uint32_t *seg_row;
     const int32_t *split_row;
+    const int16_t *wvals;   // wide layout only
+    const int16_t *vwvals;
 };
 
 inline SellView view(const Sell &s) {
     return SellView{s.nrows, s.ncols, s.nchunks, s.nseg, s.nsplit, s.entries.as<uint32_t>(),
                     s.chunk_off.as<int64_t>(), s.chunk_len.as<int32_t>(), s.vrow.as<uint32_t>(),
                     s.ventries.as<uint32_t>(), s.seg_start.as<int64_t>(), s.seg_len.as<int32_t>(),
-                    s.seg_row.as<uint32_t>(), s.split_row.as<int32_t>()};
+                    s.seg_row.as<uint32_t>(), s.split_row.as<int32_t>(),
+                    s.wide ? s.wvals.as<int16_t>() : nullptr, s.wide ? s.vwvals.as<int16_t>() : nullptr};
 }
 
 }  // namespace wr
@@ -345,12 +353,12 @@ wr_status dev_alloc(wr_ctx *ctx, DevBuf &b, size_t bytes);
 
 // format (wr_format.cu)
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
-                     const int32_t *d_colidx, const int32_t *d_vals, Sell &out);
+                     const int32_t *d_colidx, const int32_t *d_vals, Sell &out, bool wide);
 wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
                         const int32_t *d_colidx, const int32_t *d_vals, DevBuf &rowptr_t,
                         DevBuf &colidx_t, DevBuf &vals_t);
 wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
-                       const int32_t *d_colidx, const int32_t *d_vals);
+                       const int32_t *d_colidx, const int32_t *d_vals, bool *wide);
 wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n);
 
 // sequence (wr_spmm.cu)

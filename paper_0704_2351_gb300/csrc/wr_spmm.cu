@@ -68,21 +68,28 @@ __device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&v)[W]) {
     }
 }
 
-__device__ __forceinline__ int entry_val(uint32_t e) { return (int)(int8_t)(e & 0xFFu); }
+// Entry words: (column << 8) | (uint8)value in the packed layout, the column
+// alone in the wide one (values from the int16 array beside the entries).
+template <bool WIDE>
+__device__ __forceinline__ uint32_t entry_col(uint32_t e) { return WIDE ? e : (e >> 8); }
+template <bool WIDE>
+__device__ __forceinline__ int entry_val(uint32_t e, const int16_t *wv, int64_t idx) {
+    if constexpr (WIDE) return (int)__ldg(wv + idx);
+    else return (int)(int8_t)(e & 0xFFu);
+}
 
 template <int W>
-__device__ __forceinline__ void mac(int64_t (&acc)[W], uint32_t e, const uint32_t (&v)[W]) {
-    const int a = entry_val(e);
+__device__ __forceinline__ void mac(int64_t (&acc)[W], int a, const uint32_t (&v)[W]) {
 #pragma unroll
     for (int w = 0; w < W; w++) acc[w] += (int64_t)a * (int32_t)v[w];
 }
 
 // Epilogue of a finished row: y[row] = scale[row] * (sum mod p), or, for a
 // row cut into segments, the exact partial sums added into acc64.
-// A direct row has at most VSEG entries, so |sum| < 2^15 p and
-// T = sum + 2^15 p lies in [0, 2^16 p), below p R: one Montgomery reduction
-// gives T R^{-1}; with the scale taken to scale R^2 mod p (two Montgomery
-// products), mont_mul(T R^{-1}, scale R^2) = sum * scale mod p.
+// A direct row has at most VSEG = 256 entries of magnitude below 2^15, so
+// |sum| < 2^23 p and T = sum + 2^23 p lies in [0, 2^24 p), below p R: one
+// Montgomery reduction gives T R^{-1}; with the scale taken to scale R^2 mod p
+// (two Montgomery products), mont_mul(T R^{-1}, scale R^2) = sum * scale mod p.
 template <int W>
 __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], uint32_t *y,
                                         const uint32_t *scale, unsigned long long *acc64, int nv,
@@ -93,7 +100,7 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
         for (int w = 0; w < W; w++) atomicAdd(dst + w, (unsigned long long)acc[w]);
     } else {
         const uint32_t s2 = to_mont(to_mont(__ldg(scale + tgt), mp), mp);
-        const uint64_t off = (uint64_t)mp.p << 15;
+        const uint64_t off = (uint64_t)mp.p << 23;
         uint32_t o[W];
 #pragma unroll
         for (int w = 0; w < W; w++) o[w] = mont_mul(mont_redc((uint64_t)acc[w] + off, mp), s2, mp);
@@ -106,7 +113,7 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
 // over the segment's contiguous entries, then a shuffle reduction.
 // Blocks [vblocks, ...): G warps per SELL chunk of 32 light rows; warp q of
 // the chunk takes rows [q*RPW, (q+1)*RPW), G lanes per row.
-template <int NV, int WL>
+template <int NV, int WL, bool WIDE>
 __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__restrict__ x,
                                               uint32_t *__restrict__ y,
                                               const uint32_t *__restrict__ scale,
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
         const int64_t seg = (int64_t)blockIdx.x * 8 + warp;
         if (seg >= A.nseg) return;
         const uint32_t *e = A.ventries + A.seg_start[seg];
+        const int16_t *ev = WIDE ? A.vwvals + A.seg_start[seg] : nullptr;
         const int len = A.seg_len[seg];
         int64_t acc[W];
 #pragma unroll
@@ -131,20 +139,20 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
             const uint32_t e0 = __ldg(e + j), e1 = __ldg(e + j + RPW);
             const uint32_t e2 = __ldg(e + j + 2 * RPW), e3 = __ldg(e + j + 3 * RPW);
             uint32_t v0[W], v1[W], v2[W], v3[W];
-            ldv<W>(xb + (e0 >> 8) * NV, v0);
-            ldv<W>(xb + (e1 >> 8) * NV, v1);
-            ldv<W>(xb + (e2 >> 8) * NV, v2);
-            ldv<W>(xb + (e3 >> 8) * NV, v3);
-            mac<W>(acc, e0, v0);
-            mac<W>(acc, e1, v1);
-            mac<W>(acc, e2, v2);
-            mac<W>(acc, e3, v3);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e1) * NV, v1);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e2) * NV, v2);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e3) * NV, v3);
+            mac<W>(acc, entry_val<WIDE>(e0, ev, j), v0);
+            mac<W>(acc, entry_val<WIDE>(e1, ev, j + RPW), v1);
+            mac<W>(acc, entry_val<WIDE>(e2, ev, j + 2 * RPW), v2);
+            mac<W>(acc, entry_val<WIDE>(e3, ev, j + 3 * RPW), v3);
         }
         for (; j < len; j += RPW) {
             const uint32_t e0 = __ldg(e + j);
             uint32_t v0[W];
-            ldv<W>(xb + (e0 >> 8) * NV, v0);
-            mac<W>(acc, e0, v0);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
+            mac<W>(acc, entry_val<WIDE>(e0, ev, j), v0);
         }
 #pragma unroll
         for (int off = G; off < 32; off <<= 1)
@@ -161,6 +169,7 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
     {
         const int r = (int)(lw % G) * RPW + sub;
         const uint32_t *e = A.entries + base + r;
+        const int16_t *ev = WIDE ? A.wvals + base + r : nullptr;
         int64_t acc[W];
 #pragma unroll
         for (int w = 0; w < W; w++) acc[w] = 0;
@@ -171,28 +180,28 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
             for (int u = 0; u < 8; u++) ee[u] = __ldg(e + (j + u) * SELL_C);
             uint32_t vv[8][W];
 #pragma unroll
-            for (int u = 0; u < 8; u++) ldv<W>(xb + (ee[u] >> 8) * NV, vv[u]);
+            for (int u = 0; u < 8; u++) ldv<W>(xb + (size_t)entry_col<WIDE>(ee[u]) * NV, vv[u]);
 #pragma unroll
-            for (int u = 0; u < 8; u++) mac<W>(acc, ee[u], vv[u]);
+            for (int u = 0; u < 8; u++) mac<W>(acc, entry_val<WIDE>(ee[u], ev, (int64_t)(j + u) * SELL_C), vv[u]);
         }
         for (; j + 4 <= len; j += 4) {
             const uint32_t e0 = __ldg(e + (j + 0) * SELL_C), e1 = __ldg(e + (j + 1) * SELL_C);
             const uint32_t e2 = __ldg(e + (j + 2) * SELL_C), e3 = __ldg(e + (j + 3) * SELL_C);
             uint32_t v0[W], v1[W], v2[W], v3[W];
-            ldv<W>(xb + (e0 >> 8) * NV, v0);
-            ldv<W>(xb + (e1 >> 8) * NV, v1);
-            ldv<W>(xb + (e2 >> 8) * NV, v2);
-            ldv<W>(xb + (e3 >> 8) * NV, v3);
-            mac<W>(acc, e0, v0);
-            mac<W>(acc, e1, v1);
-            mac<W>(acc, e2, v2);
-            mac<W>(acc, e3, v3);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e1) * NV, v1);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e2) * NV, v2);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e3) * NV, v3);
+            mac<W>(acc, entry_val<WIDE>(e0, ev, (int64_t)(j + 0) * SELL_C), v0);
+            mac<W>(acc, entry_val<WIDE>(e1, ev, (int64_t)(j + 1) * SELL_C), v1);
+            mac<W>(acc, entry_val<WIDE>(e2, ev, (int64_t)(j + 2) * SELL_C), v2);
+            mac<W>(acc, entry_val<WIDE>(e3, ev, (int64_t)(j + 3) * SELL_C), v3);
         }
         for (; j < len; j++) {
             const uint32_t e0 = __ldg(e + j * SELL_C);
             uint32_t v0[W];
-            ldv<W>(xb + (e0 >> 8) * NV, v0);
-            mac<W>(acc, e0, v0);
+            ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
+            mac<W>(acc, entry_val<WIDE>(e0, ev, (int64_t)j * SELL_C), v0);
         }
         const uint32_t vr = A.vrow[chunk * SELL_C + r];
         if (vr != VROW_EMPTY) row_out<W>(vr, acc, y, scale, acc64, NV, part * W, mp);
@@ -395,8 +404,13 @@ void launch_spmm_kernel(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
     const int64_t vblocks = (A.nseg + 7) / 8;
     const int64_t lblocks = (A.nchunks * Lanes<NV, WL>::G + 7) / 8;
     const int64_t blocks = std::max<int64_t>(vblocks + lblocks, term_counter ? 1 : 0);
-    if (blocks > 0)
-        k_spmm<NV, WL><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter, vblocks);
+    if (blocks <= 0) return;
+    if (A.wvals)
+        k_spmm<NV, WL, true><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter,
+                                                                         vblocks);
+    else
+        k_spmm<NV, WL, false><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter,
+                                                                          vblocks);
 }
 
 template <int NV>

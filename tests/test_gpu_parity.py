@@ -104,6 +104,58 @@ def test_blackbox_tiny_and_ragged(wr, ctx):
         wr.wr_matrix_free(mat)
 
 
+def _wide_matrix(seed, R=700, C=640):
+    """heavy_matrix with most values multiplied up to the int16 range."""
+    A = heavy_matrix(R, C, seed=seed, heavy=2, heavy_len=400)
+    rng = np.random.default_rng(seed)
+    v = A.vals.astype(np.int64) * rng.choice([1, 97, 1021, 10007], size=A.nnz)
+    v = np.clip(v, -32767, 32767).astype(np.int32)
+    return synth.CSR(A.rows, A.cols, A.rowptr, A.colidx, v)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("p", [65521, 2147483629])
+def test_wide_values_blackbox_and_sequence(wr, ctx, side, p):
+    """Entries up to +-32767 (the int16 layout): one application on both
+    sides against the oracle, and the sequence."""
+    A = _wide_matrix(60 + side)
+    assert np.abs(A.vals).max() > 127
+    mat = load(wr, ctx, A)
+    N = A.cols if side == 0 else A.rows
+    M = A.rows if side == 0 else A.cols
+    rng = np.random.default_rng(side)
+    v = rng.integers(0, p, size=(N, 4)).astype(np.uint32)
+    dout = torch.empty((N, 4), dtype=torch.int32, device="cuda")
+    wr.wr_blackbox_apply_device(ctx, mat, wr.make_params(p, 1, 4, 9, side=side), to_dev(v), dout, 4)
+    ref = oracle.blackbox_apply(A, p, side, oracle.derive_diag(9, 3, N, p), oracle.derive_diag(9, 4, M, p), v)
+    assert np.array_equal(from_dev(dout), ref)
+    wr.wr_matrix_free(mat)
+    st = oracle.Setup(A, p, 4, 4, seed=3, side=side)
+    assert np.array_equal(gpu_sequence(wr, ctx, A, p, 4, 4, 3, 120, side=side), oracle.sequence(A, st, 120))
+
+
+def test_wide_values_rank_and_limits(wr, ctx):
+    p = 1073741789
+    A = synth.planted_sparse(800, 700, 560, row_len=6, seed=19)
+    B = synth.CSR(A.rows, A.cols, A.rowptr, A.colidx, (A.vals * 257).astype(np.int32))  # rank kept for p != 257
+    assert np.abs(B.vals).max() > 127
+    assert gpu_rank(wr, ctx, B, p, 4, 4, 2)["rank"] == 560
+    # a wide matrix with a column of 65,536 entries is refused
+    R = 65536
+    rows = np.arange(R)
+    cols = np.zeros(R, dtype=np.int64)
+    vals = np.ones(R, dtype=np.int64)
+    vals[0] = 200
+    L = synth.csr_from_coo(R, 2, rows, cols, vals)
+    with pytest.raises(wr.WrError) as ei:
+        load(wr, ctx, L)
+    assert ei.value.status == wr.WR_EOVERFLOW
+    # the same column with small values is fine
+    vals[0] = 1
+    mat = load(wr, ctx, synth.csr_from_coo(R, 2, rows, cols, vals))
+    wr.wr_matrix_free(mat)
+
+
 # ------------------------------------------------------------------ sequence (A2, A3, A6, A7)
 
 def gpu_sequence(wr, ctx, A, p, m, n, seed, L, side=-1, symmetric=False):
@@ -403,7 +455,7 @@ def test_errors_are_reported(wr, ctx):
     with pytest.raises(wr.WrError) as ei:
         load(wr, ctx, bad)
     assert ei.value.status == wr.WR_EINVAL
-    big = synth.CSR(1, 1, np.array([0, 1]), np.array([0], np.int32), np.array([300], np.int32))
+    big = synth.CSR(1, 1, np.array([0, 1]), np.array([0], np.int32), np.array([40000], np.int32))
     with pytest.raises(wr.WrError) as ei:
         load(wr, ctx, big)
     assert ei.value.status == wr.WR_EOVERFLOW
