@@ -146,6 +146,13 @@ wr_status wr_set_autotune(wr_ctx *ctx, int32_t on);
  * called from the library's worker threads. */
 wr_status wr_set_allocator(wr_ctx *ctx, wr_alloc_fn alloc, wr_free_fn release, void *user);
 wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
+/* Generic projection with m = n (on by default): A~ = D1 A^T D2 A D1 is
+ * symmetric, so with U_k = A~^k X and V_k = A~^k Y the terms are
+ * S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k) (A~ symmetric:
+ * Section 2.2).  X and Y are then carried side by side in one block of width 2n
+ * (n <= 16) and one black-box application yields two terms.  Off: one term per
+ * application on a block of width n.  The sequence is the same either way. */
+wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on);
 
 /* ---------------------------------------------------------------- matrices */
 

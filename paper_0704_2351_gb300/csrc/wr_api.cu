@@ -148,6 +148,8 @@ wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r) {
     r.xtag = r.symmetric ? TAG_Y : TAG_X;
     r.xwidth = r.symmetric ? r.n : r.m;
     r.gram = r.symmetric;
+    r.paired = false;
+    r.nvs = r.nv;
     return WR_OK;
 }
 
@@ -235,6 +237,12 @@ extern "C" wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues) {
     if (residues != 0 && residues != 1 && residues != 2 && residues != 4)
         return fail(WR_EINVAL, "lane width must be 0 (tuned or default), 1, 2 or 4 residues");
     ctx->lane_width = residues;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->pair_generic = on != 0;
     return WR_OK;
 }
 
@@ -512,6 +520,7 @@ extern "C" wr_status wr_sequence_slab_device(wr_ctx *ctx, const wr_matrix *mat, 
     ctx->last = wr_timings{};
     r.n = (int)ncols;
     r.nv = padded_width(r.n);
+    r.nvs = r.nv;
     r.ycol0 = (int)col0;
     r.gram = false;  // one term per application: X spans the whole Y, the right block is a slab
     if (r.N == 0) {

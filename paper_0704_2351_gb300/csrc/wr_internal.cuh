@@ -322,6 +322,7 @@ struct wr_ctx {
     int64_t sigma_leaf = 0; // orders per PM-Basis leaf (0: automatic)
     bool autotune = true;   // tune the SpMM lane width per matrix and block width
     int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
+    bool pair_generic = true; // generic projection, m = n: X and Y in one block, two terms per application
     wr_alloc_fn alloc_fn = nullptr;  // caller's device allocator (nullptr: cudaMallocAsync)
     wr_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
@@ -401,6 +402,10 @@ struct Resolved {
     uint64_t xtag;
     int xwidth;
     bool gram;  // two terms per application (symmetric projection, whole Y)
+    // generic projection with m = n: [D1 X | D1 Y] ride side by side, two
+    // terms per application (cross Gram products); nvs = the SpMM width
+    bool paired = false;
+    int nvs = 0;
 };
 wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r);
 wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,

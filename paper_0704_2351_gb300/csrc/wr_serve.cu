@@ -34,7 +34,10 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
 // sequence phase and the sigma-basis + readout phase (the sequence state is
 // released before the sigma-basis starts).
 size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
-    const size_t L = (size_t)r.L, m = (size_t)r.m, n = (size_t)r.n, q = m + n, nv = (size_t)r.nv;
+    // the paired generic block (m = n) runs the SpMM at twice the width
+    const bool pairable = !r.symmetric && r.m == r.n && 2 * r.nv <= 32;
+    const size_t L = (size_t)r.L, m = (size_t)r.m, n = (size_t)r.n, q = m + n,
+                 nv = (size_t)r.nv * (pairable ? 2 : 1);
     const size_t N = (size_t)r.N, M = (size_t)r.M;
     const size_t nsplit = (size_t)(mat->a.nsplit + mat->at.nsplit);
     const size_t seq = 4 * N * nv + 4 * M * nv + 4 * (3 * N + 2 * M) + 4 * N * m + 8 * nv * nsplit + 8 * L * m * n;
@@ -50,6 +53,7 @@ static wr_status make_slot(const wr_ctx *parent, wr_ctx **out) {
     (*out)->profiling = parent->profiling;
     (*out)->autotune = parent->autotune;
     (*out)->lane_width = parent->lane_width;
+    (*out)->pair_generic = parent->pair_generic;
     (*out)->sigma_chunk = parent->sigma_chunk;
     (*out)->sigma_leaf = parent->sigma_leaf;
     (*out)->alloc_fn = parent->alloc_fn;

@@ -229,14 +229,17 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
 // reduced mod p before the exact uint64 atomics, so their sum cannot overflow
 // and does not depend on the order.
 // GRAM: the weighted Gram matrix sum_r wt[r] T[r]^T T[r] (m = n) instead; the
-// symmetric projection X = Y turns every term into one (Section 2.2).
+// symmetric projection X = Y turns every term into one (Section 2.2).  Rows
+// of t are tstride residues apart; GRAM takes its left factor from the first
+// m of them and the right one from yoff on (yoff > 0: the cross products of
+// the paired block [D1 X | D1 Y]).
 constexpr int PROJ_THREADS = 256;
 
 template <int NV, int FOLDK, bool GRAM>
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project(int64_t N, int m, int n, const uint32_t *__restrict__ xh, const uint32_t *__restrict__ t,
               unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, int tmul, int toff,
-              int64_t L, ModP mp) {
+              int64_t L, int tstride, int yoff, ModP mp) {
     const int64_t k_term = (int64_t)tmul * *term_counter + toff;
     if (k_term < 0 || k_term >= L) return;  // the same for every thread
     // red32[w][a][b]: per-warp sums reduced mod p (m divides 32); red: one
@@ -266,8 +269,8 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int64_t ru = r + u * stride;
-                    xs[u] = GRAM ? mont_mul(__ldg(xh + ru), __ldg(t + ru * NV + a), mp) : __ldg(xh + ru * m + a);
-                    ldv<NV>(t + ru * NV, tv[u]);
+                    xs[u] = GRAM ? mont_mul(__ldg(xh + ru), __ldg(t + ru * tstride + a), mp) : __ldg(xh + ru * m + a);
+                    ldv<NV>(t + ru * tstride + yoff, tv[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -281,9 +284,9 @@ __global__ void __launch_bounds__(PROJ_THREADS)
                 }
             }
             for (; r < N; r += stride) {
-                const uint32_t xv = GRAM ? mont_mul(__ldg(xh + r), __ldg(t + r * NV + a), mp) : __ldg(xh + r * m + a);
+                const uint32_t xv = GRAM ? mont_mul(__ldg(xh + r), __ldg(t + r * tstride + a), mp) : __ldg(xh + r * m + a);
                 uint32_t tv[NV];
-                ldv<NV>(t + r * NV, tv);
+                ldv<NV>(t + r * tstride + yoff, tv);
 #pragma unroll
                 for (int b = 0; b < NV; b++) mac2(ac[b], xv, tv[b]);
                 if (++cnt == FOLDK) {
@@ -348,17 +351,27 @@ __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t
 // xwidth columns) or the Gram weights D1^{-2} (symmetric projection X = Y
 // over the whole Y: S_2k = V_k^T V_k with T_k = D1 V_k; Montgomery form).
 __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64_t xtag, int xwidth, int ystride,
-                          int ycol0, int gram, const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
+                          int ycol0, int gram, int paired, const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
                           uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, ModP mp) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint32_t d = d1[i];
     const uint32_t dinv = invm(d, mp);
     d1sq[i] = mulm(d, d, mp);
+    const int tw = paired ? 2 * nv : nv, yo = paired ? nv : 0;
     for (int b = 0; b < nv; b++) {
         uint32_t yv = 0;
         if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, (uint64_t)i * ystride + ycol0 + b) % mp.p);
-        t0[i * nv + b] = mulm(d, yv, mp);
+        t0[i * tw + yo + b] = mulm(d, yv, mp);
+    }
+    if (paired) {  // D1 X beside D1 Y, weights D1^{-2} for the cross Gram products
+        for (int a = 0; a < nv; a++) {
+            uint32_t xv = 0;
+            if (a < m) xv = (uint32_t)(stream_hash(seed, xtag, (uint64_t)i * xwidth + a) % mp.p);
+            t0[i * tw + a] = mulm(d, xv, mp);
+        }
+        xh[i] = to_mont(mulm(dinv, dinv, mp), mp);
+        return;
     }
     if (gram) {
         xh[i] = to_mont(mulm(dinv, dinv, mp), mp);  // Montgomery form for the Gram projection
@@ -531,13 +544,14 @@ static wr_status lane_width_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S
 template <int NV, bool GRAM>
 void launch_project_t(wr_ctx *ctx, unsigned grid, int64_t N, int m, int n, const uint32_t *xh,
                       const uint32_t *t, unsigned long long *s_raw, const int *term_counter, int tmul, int toff,
-                      int64_t L, const ModP &mp) {
+                      int64_t L, int tstride, int yoff, const ModP &mp) {
+    if (tstride <= 0) tstride = NV;
     if (mp.lazy >= 16)  // p < 2^30
         k_project<NV, 14, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
-                                                                         toff, L, mp);
+                                                                         toff, L, tstride, yoff, mp);
     else
         k_project<NV, 2, GRAM><<<grid, PROJ_THREADS, 0, ctx->stream>>>(N, m, n, xh, t, s_raw, term_counter, tmul,
-                                                                        toff, L, mp);
+                                                                        toff, L, tstride, yoff, mp);
 }
 
 // gram = false: S_raw[k] += xh^T t (xh: N x m).  gram = true: S_raw[k] +=
@@ -545,16 +559,16 @@ void launch_project_t(wr_ctx *ctx, unsigned grid, int64_t N, int m, int n, const
 wr_status launch_project(wr_ctx *ctx, int64_t N, int m, int n, int nv, const uint32_t *xh,
                          const uint32_t *t, unsigned long long *s_raw, const int *term_counter,
                          const ModP &mp, bool gram = false, int tmul = 1, int toff = 0,
-                         int64_t L = INT64_MAX) {
+                         int64_t L = INT64_MAX, int tstride = 0, int yoff = 0) {
     const int per = PROJ_THREADS / m;
     const int64_t need = std::max<int64_t>((N + per - 1) / per, 1);
     const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ctx->num_sms * 2);
 #define WR_PROJ_CASE(NVV)                                                                                    \
     case NVV:                                                                                                \
         if (gram)                                                                                            \
-            launch_project_t<NVV, true>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, tmul, toff, L, mp);  \
+            launch_project_t<NVV, true>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, tmul, toff, L, tstride, yoff, mp); \
         else                                                                                                 \
-            launch_project_t<NVV, false>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, tmul, toff, L, mp); \
+            launch_project_t<NVV, false>(ctx, grid, N, m, n, xh, t, s_raw, term_counter, tmul, toff, L, tstride, yoff, mp); \
         break;
     switch (nv) {
         WR_PROJ_CASE(1)
@@ -589,7 +603,7 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
     st.mp = make_modp(r.p);
     st.first = r.side == 0 ? &mat->a : &mat->at;
     st.second = r.side == 0 ? &mat->at : &mat->a;
-    const int nv = r.nv;
+    const int nv = r.nvs;  // SpMM width (2 nv for the paired generic block)
     WR_TRY(lane_width_for(ctx, mat, *st.first, nv, &st.wl1));
     WR_TRY(lane_width_for(ctx, mat, *st.second, nv, &st.wl2));
     WR_TRY(dev_alloc(ctx, st.T, sizeof(uint32_t) * std::max<int64_t>(r.N * nv, 1)));
@@ -614,13 +628,13 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
         WR_LAUNCHED(ctx);
     }
     if (want_projection && r.N > 0) {
-        k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, nv, r.seed, r.xtag, r.xwidth, r.ystride,
-                                                      r.ycol0, r.gram ? 1 : 0, st.D1.as<uint32_t>(),
+        k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, r.nv, r.seed, r.xtag, r.xwidth, r.ystride,
+                                                      r.ycol0, r.gram ? 1 : 0, r.paired ? 1 : 0, st.D1.as<uint32_t>(),
                                                       st.T.as<uint32_t>(), st.xh.as<uint32_t>(),
                                                       st.d1sq.as<uint32_t>(), st.mp);
         WR_LAUNCHED(ctx);
     }
-    if (want_projection && r.gram && r.M > 0) {
+    if (want_projection && (r.gram || r.paired) && r.M > 0) {
         WR_TRY(dev_alloc(ctx, st.w2, sizeof(uint32_t) * r.M));
         k_inv_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.M, st.D2.as<uint32_t>(), st.w2.as<uint32_t>(), st.mp);
         WR_LAUNCHED(ctx);
@@ -634,7 +648,7 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
 // S_2k+1 = (A D1 V_k)^T D2 (A D1 V_k).
 static int64_t seq_applications(const Resolved &r, int64_t L) {
     const int64_t terms = std::max<int64_t>(L - 1, 0);
-    return r.gram ? (terms + 1) / 2 : terms;
+    return (r.gram || r.paired) ? (terms + 1) / 2 : terms;
 }
 
 // One iteration: W = D2 A T, T <- D1^2 A^T W (or the rows-side analogue),
@@ -642,7 +656,7 @@ static int64_t seq_applications(const Resolved &r, int64_t L) {
 // new T into S_raw[2 counter - 1] and S_raw[2 counter] (symmetric; terms past
 // L - 1 are skipped).
 static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
-    const int nv = st.r.nv;
+    const int nv = st.r.nvs;
     SellView f = view(*st.first), sc = view(*st.second);
     if (ev) WR_CUDA(cudaEventRecord(ev[0], ctx->stream));
     WR_TRY(launch_spmm(ctx, nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
@@ -651,13 +665,14 @@ static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
     WR_TRY(launch_spmm(ctx, nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.d1sq.as<uint32_t>(),
                        st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
-    if (st.r.gram) {
-        WR_TRY(launch_project(ctx, st.r.M, st.r.m, st.r.n, nv, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(),
+    if (st.r.gram || st.r.paired) {
+        const int pv = st.r.nv, ts = nv, yo = st.r.paired ? st.r.nv : 0;
+        WR_TRY(launch_project(ctx, st.r.M, st.r.m, st.r.n, pv, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(),
                               st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, -1,
-                              st.r.L));
-        WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
+                              st.r.L, ts, yo));
+        WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, pv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
                               st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, 0,
-                              st.r.L));
+                              st.r.L, ts, yo));
     } else {
         WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
                               st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, false, 1, 0,
@@ -676,6 +691,13 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
                        uint32_t *d_S, double *setup_ms, double *seq_ms) {
     Resolved r;
     WR_TRY(resolve(mat, &prm, r));
+    // generic projection with m = n: A~ is symmetric, so with U_k = A~^k X and
+    // V_k = A~^k Y, S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k);
+    // X and Y ride in one block of twice the width, two terms per application
+    if (!r.symmetric && r.m == r.n && 2 * r.nv <= 32 && ctx->pair_generic) {
+        r.paired = true;
+        r.nvs = 2 * r.nv;
+    }
     return run_sequence_resolved(ctx, mat, r, L, d_S, setup_ms, seq_ms);
 }
 
@@ -695,8 +717,8 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     WR_CUDA(cudaMemsetAsync(st.s_raw.ptr, 0, st.s_raw.bytes, s));
     if (L > 0)
         WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
-                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.gram,
-                              r.gram ? 2 : 1, 0, L));
+                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.gram || r.paired,
+                              (r.gram || r.paired) ? 2 : 1, 0, L, r.nvs, r.paired ? r.nv : 0));
     WR_CUDA(cudaEventRecord(e1, s));
 
     // profiling: every PROF_EVERY-th group of iterations is launched eagerly
@@ -747,8 +769,8 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
                     cudaEventElapsedTime(&b, pev[3 * i + 1], pev[3 * i + 2]);
                     prof_ms += a + b;
                     prof_launches += 2;
-                    ctx->last.spmm_bytes += spmm_pass_bytes(*st.first, r.nv, mat->nnz) +
-                                            spmm_pass_bytes(*st.second, r.nv, mat->nnz);
+                    ctx->last.spmm_bytes += spmm_pass_bytes(*st.first, r.nvs, mat->nnz) +
+                                            spmm_pass_bytes(*st.second, r.nvs, mat->nnz);
                 }
             }
         }

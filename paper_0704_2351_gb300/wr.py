@@ -74,6 +74,7 @@ _sig = {
     "wr_set_autotune": ([vp, i32], ctypes.c_int),
     "wr_set_allocator": ([vp, vp, vp, vp], ctypes.c_int),
     "wr_set_lane_width": ([vp, i32], ctypes.c_int),
+    "wr_set_paired_projection": ([vp, i32], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -235,6 +236,10 @@ def wr_set_autotune(ctx: int, on: bool) -> None:
 
 def wr_set_lane_width(ctx: int, residues: int) -> None:
     _check(_lib.wr_set_lane_width(vp(ctx), residues))
+
+
+def wr_set_paired_projection(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_paired_projection(vp(ctx), 1 if on else 0))
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

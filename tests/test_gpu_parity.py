@@ -218,6 +218,27 @@ def test_sequence_symmetric_two_terms_per_application(wr, ctx, n, L, side, p):
     assert np.array_equal(S, S_ref)
 
 
+@pytest.mark.parametrize("n,L,side", [(1, 41, 0), (1, 40, 1), (3, 57, 0), (8, 97, 0), (8, 96, 1), (16, 33, 1),
+                                      (4, 1, 0), (4, 2, 1), (4, 3, 0)])
+@pytest.mark.parametrize("p", [65521, 2147483629])
+def test_sequence_generic_paired_two_terms_per_application(wr, ctx, n, L, side, p):
+    """Generic projection with m = n: the GPU carries [D1 X | D1 Y] as one
+    block and takes S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k)
+    from one application per two terms; the oracle applies A~ to Y once per
+    term.  The sequence is the same with the pairing switched off.  Odd and
+    even L, L = 1, 2, 3, a padded block width (n = 3) and both sides."""
+    A = heavy_matrix(610, 575, seed=n * 11 + L, heavy=2, heavy_len=330)
+    st = oracle.Setup(A, p, n, n, seed=60 + n, side=side)
+    S_ref = oracle.sequence(A, st, L)
+    S = gpu_sequence(wr, ctx, A, p, n, n, 60 + n, L, side=side)
+    assert np.array_equal(S, S_ref)
+    try:
+        wr.wr_set_paired_projection(ctx, False)
+        assert np.array_equal(gpu_sequence(wr, ctx, A, p, n, n, 60 + n, L, side=side), S_ref)
+    finally:
+        wr.wr_set_paired_projection(ctx, True)
+
+
 @pytest.mark.parametrize("m", [1, 4, 8])
 def test_rank_planted_symmetric(wr, ctx, m):
     p = 1073741789
