@@ -372,7 +372,7 @@ def main():
         spmm_ms += tm["spmm_ms"]
         spmm_bytes += tm["spmm_bytes"]
         spmm_launches += tm["spmm_launches"]
-        phases.append({k: round(tm[k], 3) for k in ["setup_ms", "sequence_ms", "sigma_ms", "readout_ms"]})
+        phases.append({k: round(tm[k], 3) for k in ["setup_ms", "sequence_ms", "sigma_ms", "sigma_tail_ms", "readout_ms"]})
     torch.cuda.synchronize()
     launches = wr.wr_last_timings(ctx)["kernel_launches"] - launches0
     clocks = stop_clock_sampler(sampler, clk_path, local)

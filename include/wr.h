@@ -82,7 +82,7 @@ typedef struct {
 typedef struct {
     double setup_ms;     /* X, Y, D1, D2 derivation and preconditioning set-up             */
     double sequence_ms;  /* the L - 1 black-box applications and projections               */
-    double sigma_ms;     /* sigma-basis                                                   */
+    double sigma_ms;     /* sigma-basis, from its start to its end (host clock)           */
     double readout_ms;   /* generator selection, det valuations, rank                     */
     double total_ms;
     double spmm_ms;      /* when profiling is on: summed duration of the sampled SpMM      */
@@ -93,6 +93,9 @@ typedef struct {
     double sigma_window_ms;  /* when profiling is on: sigma-basis time in the discrepancy    */
     double sigma_local_ms;   /* windows, the per-chunk M-Basis and the transform products    */
     double sigma_apply_ms;
+    double sigma_tail_ms;    /* sigma-basis time after the sequence's end: with the pipeline  */
+                             /* (wr_set_pipeline) sigma_ms overlaps the sequence and only    */
+                             /* this part adds to the time to rank                           */
 } wr_timings;
 
 /* Device allocator callbacks (for example PyTorch's caching allocator):
@@ -146,6 +149,12 @@ wr_status wr_set_autotune(wr_ctx *ctx, int32_t on);
  * called from the library's worker threads. */
 wr_status wr_set_allocator(wr_ctx *ctx, wr_alloc_fn alloc, wr_free_fn release, void *user);
 wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
+/* wr_rank pipeline (on by default): the sigma-basis trails the sequence on a
+ * second stream driven by a second host thread.  M-Basis orders k .. k+b-1
+ * need only S_0 .. S_{k+b-1} (Section 2.3's sigma-basis is computed order by
+ * order), so each chunk starts as soon as the sequence has produced its terms
+ * and the two phases overlap on the device.  Results do not depend on it. */
+wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on);
 /* Generic projection with m = n (on by default): A~ = D1 A^T D2 A D1 is
  * symmetric, so with U_k = A~^k X and V_k = A~^k Y the terms are
  * S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k) (A~ symmetric:

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "wr_internal.cuh"
@@ -189,6 +190,7 @@ extern "C" wr_status wr_create(wr_ctx **out, int device, void *cuda_stream) {
 
 extern "C" void wr_destroy(wr_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->aux) wr_destroy(ctx->aux);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -237,6 +239,12 @@ extern "C" wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues) {
     if (residues != 0 && residues != 1 && residues != 2 && residues != 4)
         return fail(WR_EINVAL, "lane width must be 0 (tuned or default), 1, 2 or 4 residues");
     ctx->lane_width = residues;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->pipeline = on != 0;
     return WR_OK;
 }
 
@@ -345,6 +353,48 @@ extern "C" void wr_matrix_free(wr_matrix *mat) {
 
 namespace wr {
 
+void copy_settings(const wr_ctx *parent, wr_ctx *c) {
+    c->profiling = parent->profiling;
+    c->autotune = parent->autotune;
+    c->lane_width = parent->lane_width;
+    c->pair_generic = parent->pair_generic;
+    c->pipeline = parent->pipeline;
+    c->sigma_chunk = parent->sigma_chunk;
+    c->sigma_leaf = parent->sigma_leaf;
+    c->alloc_fn = parent->alloc_fn;
+    c->free_fn = parent->free_fn;
+    c->alloc_user = parent->alloc_user;
+}
+
+wr_status make_child(const wr_ctx *parent, wr_ctx **out) {
+    WR_TRY(wr_create(out, parent->device, nullptr));
+    copy_settings(parent, *out);
+    return WR_OK;
+}
+
+wr_status feed_wait(wr_ctx *ctx, SeqFeed *feed, int64_t terms) {
+    if (!feed || terms <= 0) return WR_OK;
+    cudaEvent_t ev = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(feed->mu);
+        int64_t i = std::max<int64_t>(feed->waited, 0);
+        for (;;) {
+            while (i < (int64_t)feed->ready.size() && feed->ready[i] >= 0 && feed->ready[i] < terms) i++;
+            if (i < (int64_t)feed->ready.size()) {
+                if (feed->ready[i] < 0) return fail(WR_EDEVICE, "the sequence stopped before its terms were ready");
+                break;
+            }
+            if (feed->closed) return fail(WR_EDEVICE, "the sequence stopped before its terms were ready");
+            feed->cv.wait(lk);
+        }
+        if (i == feed->waited) return WR_OK;  // the stream already waits on that event
+        feed->waited = i;
+        ev = feed->ev[i];
+    }
+    WR_CUDA(cudaStreamWaitEvent(ctx->stream, ev, 0));
+    return WR_OK;
+}
+
 wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out) {
     if (!ctx || !mat || !params || !out) return fail(WR_EINVAL, "null argument");
     *out = nullptr;
@@ -370,18 +420,79 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
     wr_status st = dev_alloc(ctx, dS, sizeof(uint32_t) * L * r.m * r.n);
     if (st == WR_OK) st = dev_alloc(ctx, dP, sizeof(uint32_t) * (Dcap + 1) * r.n * q);
     if (st == WR_OK) st = dev_alloc(ctx, ddeg, sizeof(int32_t) * q);
-    double setup_ms = 0, seq_ms = 0;
-    if (st == WR_OK) st = run_sequence(ctx, mat, *params, L, dS.as<uint32_t>(), &setup_ms, &seq_ms);
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    if (st == WR_OK) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventCreate(&e2);
-        cudaEventRecord(e0, ctx->stream);
-        st = sigma_basis(ctx, dS.as<uint32_t>(), L, r.m, r.n, r.p, dP.as<uint32_t>(), ddeg.as<int32_t>(), Dcap);
+    double setup_ms = 0, seq_ms = 0, sigma_ms = 0, tail_ms = 0;
+    if (st == WR_OK && ctx->pipeline) {
+        // The sigma-basis trails the sequence: a child context (own stream,
+        // own host thread) runs M-Basis chunk k as soon as the sequence
+        // stream has published S_0 .. S_{k+b-1}, so the two overlap on the
+        // device and only the last chunks run after the sequence ends.
+        if (!ctx->aux) st = make_child(ctx, &ctx->aux);
+        wr_ctx *aux = ctx->aux;
+        SeqFeed feed;
+        cudaEvent_t ready0 = nullptr;
+        if (st == WR_OK) {
+            copy_settings(ctx, aux);
+            aux->launches = 0;
+            aux->last = wr_timings{};
+            cudaError_t ce = cudaEventCreateWithFlags(&ready0, cudaEventDisableTiming);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ready0, ctx->stream);  // dS, dP, ddeg allocated
+            if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventRecord");
+        }
+        if (st == WR_OK) {
+            wr_status sst = WR_OK;
+            std::string smsg;
+            std::chrono::steady_clock::time_point t_sig0, t_sig1;
+            aux->feed = &feed;
+            std::thread sig([&] {
+                cudaSetDevice(aux->device);
+                t_sig0 = std::chrono::steady_clock::now();
+                cudaError_t ce = cudaStreamWaitEvent(aux->stream, ready0, 0);
+                sst = ce == cudaSuccess ? WR_OK : cuda_fail(ce, "cudaStreamWaitEvent");
+                if (sst == WR_OK)
+                    sst = sigma_basis(aux, dS.as<uint32_t>(), L, r.m, r.n, r.p, dP.as<uint32_t>(),
+                                      ddeg.as<int32_t>(), Dcap);
+                if (sst == WR_OK) {
+                    ce = cudaStreamSynchronize(aux->stream);
+                    if (ce != cudaSuccess) sst = cuda_fail(ce, "cudaStreamSynchronize");
+                }
+                t_sig1 = std::chrono::steady_clock::now();
+                if (sst != WR_OK) smsg = wr_last_error();
+            });
+            st = run_sequence(ctx, mat, *params, L, dS.as<uint32_t>(), &setup_ms, &seq_ms, &feed);
+            const auto t_seq1 = std::chrono::steady_clock::now();
+            {
+                std::lock_guard<std::mutex> lk(feed.mu);
+                feed.closed = true;
+            }
+            feed.cv.notify_all();
+            sig.join();
+            aux->feed = nullptr;
+            ctx->launches += aux->launches;
+            ctx->last.sigma_window_ms = aux->last.sigma_window_ms;
+            ctx->last.sigma_local_ms = aux->last.sigma_local_ms;
+            ctx->last.sigma_apply_ms = aux->last.sigma_apply_ms;
+            sigma_ms = std::chrono::duration<double, std::milli>(t_sig1 - t_sig0).count();
+            tail_ms = std::max(0.0, std::chrono::duration<double, std::milli>(t_sig1 - t_seq1).count());
+            if (st == WR_OK && sst != WR_OK) st = fail(sst, smsg);
+        }
+        for (cudaEvent_t e : feed.ev) cudaEventDestroy(e);
+        if (ready0) cudaEventDestroy(ready0);
+    } else if (st == WR_OK) {
+        st = run_sequence(ctx, mat, *params, L, dS.as<uint32_t>(), &setup_ms, &seq_ms);
+        const auto t0 = std::chrono::steady_clock::now();
+        if (st == WR_OK)
+            st = sigma_basis(ctx, dS.as<uint32_t>(), L, r.m, r.n, r.p, dP.as<uint32_t>(), ddeg.as<int32_t>(), Dcap);
+        if (st == WR_OK) {
+            cudaError_t ce = cudaStreamSynchronize(ctx->stream);
+            if (ce != cudaSuccess) st = cuda_fail(ce, "cudaStreamSynchronize");
+        }
+        sigma_ms = tail_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     Readout ro;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
     if (st == WR_OK) {
+        cudaEventCreate(&e1);
+        cudaEventCreate(&e2);
         cudaEventRecord(e1, ctx->stream);
         st = rank_readout(ctx, dP.as<uint32_t>(), ddeg.as<int32_t>(), r.m, r.n, r.p, Dcap, ro,
                           (params->want & WR_WANT_GENERATOR) ? &res->gen : nullptr);
@@ -389,15 +500,14 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
     if (st == WR_OK) {
         cudaEventRecord(e2, ctx->stream);
         cudaEventSynchronize(e2);
-        float a = 0, b = 0;
-        cudaEventElapsedTime(&a, e0, e1);
+        float b = 0;
         cudaEventElapsedTime(&b, e1, e2);
         ctx->last.setup_ms = setup_ms;
         ctx->last.sequence_ms = seq_ms;
-        ctx->last.sigma_ms = a;
+        ctx->last.sigma_ms = sigma_ms;
+        ctx->last.sigma_tail_ms = tail_ms;
         ctx->last.readout_ms = b;
     }
-    if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e2) cudaEventDestroy(e2);
     if (st == WR_OK && (params->want & WR_WANT_SEQUENCE)) {

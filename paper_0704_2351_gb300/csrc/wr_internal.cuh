@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <condition_variable>
 #include <mutex>
 #include <stdint.h>
 
@@ -309,6 +310,20 @@ inline SellView view(const Sell &s) {
 
 // ------------------------------------------------------------------ opaque handles
 
+namespace wr {
+// Terms of a sequence that one host thread computes while another consumes
+// them: once ev[i] has completed on the producer's stream, S_0 .. S_{ready[i]-1}
+// are final in the device sequence buffer.  The owner destroys the events.
+struct SeqFeed {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int64_t> ready;
+    bool closed = false;    // the producer has recorded its last event (or stopped)
+    int64_t waited = -1;    // consumer: last event index its stream waits on
+};
+}  // namespace wr
+
 struct wr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -323,6 +338,9 @@ struct wr_ctx {
     bool autotune = true;   // tune the SpMM lane width per matrix and block width
     int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
     bool pair_generic = true; // generic projection, m = n: X and Y in one block, two terms per application
+    bool pipeline = true;   // wr_rank: the sigma-basis trails the sequence on a second stream
+    wr_ctx *aux = nullptr;  // child context (own stream) that runs the trailing sigma-basis
+    wr::SeqFeed *feed = nullptr; // set on a child context while it consumes a sequence in flight
     wr_alloc_fn alloc_fn = nullptr;  // caller's device allocator (nullptr: cudaMallocAsync)
     wr_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
@@ -363,11 +381,16 @@ wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, con
 wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n);
 
 // sequence (wr_spmm.cu)
-struct SeqPlan;
 wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r, int s,
                       int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C);
 wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
-                       uint32_t *d_S, double *setup_ms, double *seq_ms);
+                       uint32_t *d_S, double *setup_ms, double *seq_ms, SeqFeed *feed = nullptr);
+// Make the context's stream wait until S_0 .. S_{terms-1} of the fed sequence
+// are final (blocks the host until the producer has recorded that far).
+wr_status feed_wait(wr_ctx *ctx, SeqFeed *feed, int64_t terms);
+// A context on the parent's device with its own stream and the parent's settings.
+wr_status make_child(const wr_ctx *parent, wr_ctx **out);
+void copy_settings(const wr_ctx *parent, wr_ctx *child);
 wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                          const uint32_t *d_in, uint32_t *d_out, int64_t width);
 wr_status blackbox_apply_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
@@ -409,7 +432,7 @@ struct Resolved {
 };
 wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r);
 wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,
-                                double *setup_ms, double *seq_ms);
+                                double *setup_ms, double *seq_ms, SeqFeed *feed = nullptr);
 
 int padded_width(int n);
 

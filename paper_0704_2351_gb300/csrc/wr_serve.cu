@@ -29,10 +29,10 @@ namespace wr {
 wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out);
 
 // Upper bound of the device memory one rank_one call allocates besides the
-// loaded matrix: the sequence state (blocks, diagonals, split accumulators,
-// exact term sums), the kept sequence and basis, and the larger of the
-// sequence phase and the sigma-basis + readout phase (the sequence state is
-// released before the sigma-basis starts).
+// loaded matrix: the kept sequence and basis, the sequence state (blocks,
+// diagonals, split accumulators, exact term sums) beside the sigma-basis
+// state (the sigma-basis trails the sequence while it runs), then the
+// readout (after both are released).
 size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
     // the paired generic block (m = n) runs the SpMM at twice the width
     const bool pairable = !r.symmetric && r.m == r.n && 2 * r.nv <= 32;
@@ -44,22 +44,7 @@ size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
     const size_t keep = 4 * L * m * n + 4 * (L + 2) * n * q + 4 * q;
     const size_t sigma = 4 * (L + 2) * n * q + 4 * (size_t)(2 * num_sms) * 64 * m * q + 4 * 65 * q * q + 4 * (m * q + 4 * q);
     const size_t readout = 4 * 2 * (L + 2) * n * n + 64;
-    return keep + std::max(seq, sigma + readout) + (1u << 20);
-}
-
-// A slot: a context of its own on the parent's device.
-static wr_status make_slot(const wr_ctx *parent, wr_ctx **out) {
-    WR_TRY(wr_create(out, parent->device, nullptr));
-    (*out)->profiling = parent->profiling;
-    (*out)->autotune = parent->autotune;
-    (*out)->lane_width = parent->lane_width;
-    (*out)->pair_generic = parent->pair_generic;
-    (*out)->sigma_chunk = parent->sigma_chunk;
-    (*out)->sigma_leaf = parent->sigma_leaf;
-    (*out)->alloc_fn = parent->alloc_fn;
-    (*out)->free_fn = parent->free_fn;
-    (*out)->alloc_user = parent->alloc_user;
-    return WR_OK;
+    return keep + std::max(seq + sigma, readout) + (1u << 20);
 }
 
 }  // namespace wr
@@ -102,7 +87,7 @@ extern "C" wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *c
     const int nslots = (int)std::min<size_t>(njobs, (size_t)std::max(1, ctx->batch_slots));
     std::vector<wr_ctx *> slots(nslots, nullptr);
     for (int k = 0; k < nslots; k++) {
-        wr_status st = make_slot(ctx, &slots[k]);
+        wr_status st = make_child(ctx, &slots[k]);
         if (st != WR_OK) {
             for (auto *c : slots) wr_destroy(c);
             return st;
@@ -223,7 +208,7 @@ extern "C" wr_status wr_server_start(wr_ctx *ctx, const wr_server_cfg *cfg, wr_s
     if (s->cfg.queue_cap < 1) s->cfg.queue_cap = 1 << 20;
     for (int k = 0; k < s->cfg.max_slots; k++) {
         wr_ctx *c = nullptr;
-        wr_status st = make_slot(ctx, &c);
+        wr_status st = make_child(ctx, &c);
         if (st != WR_OK) {
             for (auto *x : s->slots) wr_destroy(x);
             delete s;

@@ -1072,6 +1072,10 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
     for (int64_t k0 = 0; k0 < L; k0 += bmax) {
         const int bb = (int)std::min<int64_t>(bmax, L - k0);
         const bool prof = ctx->profiling && ((k0 / bmax) % 16 == 0);
+        // a sequence still in flight: the window reads S rows below k0 + bb
+        // rounded up to its order tile
+        if (ctx->feed && !d_deg_in)
+            WR_TRY(feed_wait(ctx, ctx->feed, std::min<int64_t>(L, k0 + (bb + WIN_IB - 1) / WIN_IB * WIN_IB)));
         if (prof) WR_CUDA(cudaEventRecord(pe[0], s));
         // window: split coefficients [0, min(Dbound, k0 + bb - 1)] over the blocks
         const int64_t tspan = std::min<int64_t>(Dbound, k0 + bb - 1) + 1;
@@ -1212,6 +1216,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         return mbasis_run(ctx, d_S, L, m, n, n, p, d_P, d_deg, nullptr, 0, Dcap, nullptr);
     const int q = m + n;
     cudaStream_t s = ctx->stream;
+    if (ctx->feed) WR_TRY(feed_wait(ctx, ctx->feed, L));  // PM-Basis reads the whole sequence
     DevBuf F, M;
     WR_TRY(dev_alloc(ctx, F, sizeof(uint32_t) * (size_t)L * m * q));
     const unsigned g = (unsigned)std::min<int64_t>((L * m * q + 255) / 256, (int64_t)ctx->num_sms * 16);

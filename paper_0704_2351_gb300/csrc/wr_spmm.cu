@@ -688,7 +688,7 @@ static double spmm_pass_bytes(const Sell &s, int nv, int64_t nnz) {
 }
 
 wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
-                       uint32_t *d_S, double *setup_ms, double *seq_ms) {
+                       uint32_t *d_S, double *setup_ms, double *seq_ms, SeqFeed *feed) {
     Resolved r;
     WR_TRY(resolve(mat, &prm, r));
     // generic projection with m = n: A~ is symmetric, so with U_k = A~^k X and
@@ -698,11 +698,38 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
         r.paired = true;
         r.nvs = 2 * r.nv;
     }
-    return run_sequence_resolved(ctx, mat, r, L, d_S, setup_ms, seq_ms);
+    return run_sequence_resolved(ctx, mat, r, L, d_S, setup_ms, seq_ms, feed);
+}
+
+// Terms final after `done` applications (the initial projection gives S_0).
+static int64_t terms_ready(const Resolved &r, int64_t done, int64_t L) {
+    return std::min<int64_t>((r.gram || r.paired) ? 2 * done + 1 : done + 1, L);
+}
+
+// Fed mode: reduce the terms [from, to) into d_S and publish an event after them.
+static wr_status publish_terms(wr_ctx *ctx, SeqState &st, int64_t from, int64_t to, uint32_t *d_S,
+                               SeqFeed *feed) {
+    const int64_t E = (int64_t)st.r.m * st.r.n;
+    if (to > from) {
+        k_reduce_seq<<<blocks_for((to - from) * E, 256), 256, 0, ctx->stream>>>(
+            (to - from) * E, st.s_raw.as<unsigned long long>() + from * E, d_S + from * E, st.mp);
+        WR_LAUNCHED(ctx);
+    }
+    cudaEvent_t ev;
+    WR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t ce = cudaEventRecord(ev, ctx->stream);
+    {
+        std::lock_guard<std::mutex> lk(feed->mu);
+        feed->ev.push_back(ev);  // the feed's owner destroys it
+        feed->ready.push_back(ce == cudaSuccess ? to : -1);
+    }
+    feed->cv.notify_all();
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventRecord");
+    return WR_OK;
 }
 
 wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,
-                                double *setup_ms, double *seq_ms) {
+                                double *setup_ms, double *seq_ms, SeqFeed *feed) {
     r.L = L;
     cudaStream_t s = ctx->stream;
     cudaEvent_t e0, e1, e2;
@@ -719,6 +746,11 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
         WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
                               st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.gram || r.paired,
                               (r.gram || r.paired) ? 2 : 1, 0, L, r.nvs, r.paired ? r.nv : 0));
+    int64_t published = 0;
+    if (feed) {
+        WR_TRY(publish_terms(ctx, st, 0, terms_ready(r, 0, L), d_S, feed));
+        published = terms_ready(r, 0, L);
+    }
     WR_CUDA(cudaEventRecord(e1, s));
 
     // profiling: every PROF_EVERY-th group of iterations is launched eagerly
@@ -776,12 +808,17 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
         }
         done += todo;
         group++;
+        if (feed && loop_st == WR_OK) {
+            const int64_t t = terms_ready(r, done, L);
+            loop_st = publish_terms(ctx, st, published, t, d_S, feed);
+            published = t;
+        }
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto &e : pev) cudaEventDestroy(e);
     WR_TRY(loop_st);
-    if (L * E > 0) {
+    if (!feed && L * E > 0) {
         k_reduce_seq<<<blocks_for(L * E, 256), 256, 0, s>>>(L * E, st.s_raw.as<unsigned long long>(), d_S,
                                                            st.mp);
         WR_LAUNCHED(ctx);

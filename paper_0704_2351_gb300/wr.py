@@ -43,7 +43,8 @@ class wr_timings(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("spmm_ms", ctypes.c_double),
                 ("spmm_launches", ctypes.c_int64), ("spmm_bytes", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("sigma_window_ms", ctypes.c_double),
-                ("sigma_local_ms", ctypes.c_double), ("sigma_apply_ms", ctypes.c_double)]
+                ("sigma_local_ms", ctypes.c_double), ("sigma_apply_ms", ctypes.c_double),
+                ("sigma_tail_ms", ctypes.c_double)]
 
 
 class wr_server_cfg(ctypes.Structure):
@@ -75,6 +76,7 @@ _sig = {
     "wr_set_allocator": ([vp, vp, vp, vp], ctypes.c_int),
     "wr_set_lane_width": ([vp, i32], ctypes.c_int),
     "wr_set_paired_projection": ([vp, i32], ctypes.c_int),
+    "wr_set_pipeline": ([vp, i32], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -240,6 +242,10 @@ def wr_set_lane_width(ctx: int, residues: int) -> None:
 
 def wr_set_paired_projection(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_paired_projection(vp(ctx), 1 if on else 0))
+
+
+def wr_set_pipeline(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_pipeline(vp(ctx), 1 if on else 0))
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

@@ -239,6 +239,30 @@ def test_sequence_generic_paired_two_terms_per_application(wr, ctx, n, L, side, 
         wr.wr_set_paired_projection(ctx, True)
 
 
+@pytest.mark.parametrize("m,n,sym,chunk", [(8, 8, False, 0), (8, 8, True, 5), (3, 3, False, 64), (4, 7, False, 13),
+                                            (1, 1, False, 0), (16, 16, True, 0)])
+def test_rank_pipeline_matches_sequential(wr, ctx, m, n, sym, chunk):
+    """wr_rank with the sigma-basis trailing the sequence on a second stream
+    (the default) gives the same sequence, generator and rank as the phases
+    run one after the other, and both equal the oracle's; chunk sizes that are
+    not a multiple of the window's order tile make the trailing windows wait
+    for rounded-up term counts."""
+    p = 1073741789
+    A = synth.planted_sparse(1300, 1150, 1020, row_len=7, seed=m * 31 + n + chunk)
+    try:
+        wr.wr_set_sigma_chunk(ctx, chunk)
+        got = gpu_rank(wr, ctx, A, p, m, n, 77, want=3, symmetric=sym)
+        wr.wr_set_pipeline(ctx, False)
+        seq = gpu_rank(wr, ctx, A, p, m, n, 77, want=3, symmetric=sym)
+    finally:
+        wr.wr_set_pipeline(ctx, True)
+        wr.wr_set_sigma_chunk(ctx, 0)
+    assert got["rank"] == seq["rank"] == 1020
+    assert np.array_equal(got["S"], seq["S"]) and np.array_equal(got["F"], seq["F"])
+    ref = oracle.rank_wiedemann(A, p, m, n, seed=77, symmetric=sym)
+    assert np.array_equal(got["S"], ref["S"]) and np.array_equal(got["F"], ref["F"])
+
+
 @pytest.mark.parametrize("m", [1, 4, 8])
 def test_rank_planted_symmetric(wr, ctx, m):
     p = 1073741789
