@@ -4,17 +4,17 @@
  *
  * Method (Dumas, Elbaz-Vincent, Giorgi, Urbanska, "Parallel computation of the
  * rank of large sparse matrices from algebraic K-theory", PASCO 2007):
- * Section 2.4, "Block Wiedemann Rank Algorithm":
+ * Section 2.5, "Block Wiedemann Rank Algorithm":
  *   1. form A~ from A with preconditioners of the form A^T A (Section 2.3):
  *      A~ = D1 A^T D2 A D1 (N = cols) or D1 A D2 A^T D1 (N = rows), D1, D2
  *      random nonsingular diagonals;
- *   2. the sequence S_i = X^T A~^i Y, i = 0 .. L-1 (Section 2.1, Coppersmith's
+ *   2. the sequence S_i = X^T A~^i Y, i = 0 .. L-1 (Section 2.2, Coppersmith's
  *      block Wiedemann), L = ceil(N/m) + ceil(N/n) + 2 by default;
  *   3. the minimal matrix generator F of {S_i} through a sigma-basis
- *      (Section 2.3, "sigma-basis computations"; M-Basis of Giorgi, Jeannerod,
+ *      (Section 2.4, "sigma-basis computations"; M-Basis of Giorgi, Jeannerod,
  *      Villard);
  *   4. r = deg det F - codeg det F.
- * Rank over Q: the maximum of the ranks modulo several primes (Section 2.4,
+ * Rank over Q: the maximum of the ranks modulo several primes (Section 2.5,
  * last paragraph).
  *
  * Conventions for every call:
@@ -72,7 +72,7 @@ typedef struct {
                          /* X, Y entries h mod p (tags 1, 2; idx = row*width + col);      */
                          /* D1, D2 entries 1 + h mod (p - 1) (tags 3, 4; idx = row)       */
     int32_t projection;  /* WR_PROJ_GENERIC (X independent) or WR_PROJ_SYMMETRIC (X = Y,  */
-                         /* m = n; Section 2.2)                                           */
+                         /* m = n; Section 2.3)                                           */
     int32_t side;        /* WR_SIDE_AUTO (N = min(rows, cols)), WR_SIDE_COLS, WR_SIDE_ROWS */
     uint64_t seq_len;    /* 0: L = ceil(N/m) + ceil(N/n) + 2                               */
     uint32_t want;       /* WR_WANT_SEQUENCE | WR_WANT_GENERATOR: keep them in the result */
@@ -125,7 +125,7 @@ wr_status wr_last_timings(const wr_ctx *ctx, wr_timings *out);
  * any chunk size and cost a few launches per chunk. */
 wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
 /* Sigma-bases of more than `orders` orders (>= 64) are computed by PM-Basis
- * (Section 2.3): halved recursively down to leaves of at most `orders`
+ * (Section 2.4): halved recursively down to leaves of at most `orders`
  * orders, which run the blocked M-Basis, with the residuals and the products
  * of the halves' bases done as polynomial matrix products by number-theoretic
  * transforms over three FFT primes and the CRT.  The result is the same basis
@@ -151,21 +151,34 @@ wr_status wr_set_allocator(wr_ctx *ctx, wr_alloc_fn alloc, wr_free_fn release, v
 wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
 /* wr_rank pipeline (on by default): the sigma-basis trails the sequence on a
  * second stream driven by a second host thread.  M-Basis orders k .. k+b-1
- * need only S_0 .. S_{k+b-1} (Section 2.3's sigma-basis is computed order by
+ * need only S_0 .. S_{k+b-1} (Section 2.4's sigma-basis is computed order by
  * order), so each chunk starts as soon as the sequence has produced its terms
  * and the two phases overlap on the device.  Results do not depend on it. */
 wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on);
+/* Early termination of wr_rank (off by default; orders = 0).  The trailing
+ * M-Basis watches the generator candidates (the n basis columns of smallest
+ * shifted degree); once they have had zero discrepancy for `orders`
+ * consecutive orders (counted per whole chunk) the generator is taken as
+ * stable, the sequence stops and the rank is read from the basis so far,
+ * instead of after L = ceil(N/m) + ceil(N/n) + 2 terms (about 2r/n + O(1)
+ * terms suffice for rank r: the iteration count 2 + 2r/p of Table
+ * tab:r-time; Section 4 remarks that early termination needs the
+ * order-by-order basis, which is what runs here).  A false
+ * stop needs orders * m random residues to vanish; 64 is a sensible value.
+ * Needs the pipeline (wr_set_pipeline); the result's seq_len and sequence
+ * then hold the terms actually used, and the run always uses M-Basis. */
+wr_status wr_set_early_termination(wr_ctx *ctx, int64_t orders);
 /* Generic projection with m = n (on by default): A~ = D1 A^T D2 A D1 is
  * symmetric, so with U_k = A~^k X and V_k = A~^k Y the terms are
  * S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k) (A~ symmetric:
- * Section 2.2).  X and Y are then carried side by side in one block of width 2n
+ * Section 2.3).  X and Y are then carried side by side in one block of width 2n
  * (n <= 16) and one black-box application yields two terms.  Off: one term per
  * application on a block of width n.  The sequence is the same either way. */
 wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on);
 
 /* ---------------------------------------------------------------- matrices */
 
-/* Ingest a CSR matrix (Section 2.4 step 1 operates on it as a black box).
+/* Ingest a CSR matrix (Section 2.5 step 1 operates on it as a black box).
  * rowptr: rows + 1 int64, nondecreasing, rowptr[0] = 0; colidx: int32 in
  * [0, cols); vals: small signed integers (the paper's boundary matrices hold
  * 0, +-1 and small integers).  rows, cols < 2^31; every row < 2^24 entries.
@@ -188,7 +201,7 @@ void wr_matrix_free(wr_matrix *mat);
 
 /* ---------------------------------------------------------------- rank */
 
-/* Rank of the matrix modulo params->prime (Section 2.4 steps 1-4). */
+/* Rank of the matrix modulo params->prime (Section 2.5 steps 1-4). */
 wr_status wr_rank(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out);
 
 /* Many jobs in one call (matrices may repeat with different primes or seeds;
@@ -252,7 +265,7 @@ wr_status wr_blackbox_apply_device(wr_ctx *ctx, const wr_matrix *mat, const wr_p
 wr_status wr_blackbox_apply_device_noalloc(wr_ctx *ctx, const wr_matrix *mat,
                                            const wr_params *params, const uint32_t *d_in,
                                            uint32_t *d_out, int64_t width);
-/* The sequence S_i = X^T A~^i Y, i < L (Section 2.4 step 2) into d_S (L*m*n). */
+/* The sequence S_i = X^T A~^i Y, i < L (Section 2.5 step 2) into d_S (L*m*n). */
 wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                              uint32_t *d_S, uint64_t L);
 /* Columns [col0, col0 + ncols) of that sequence, S_i = X^T A~^i Y[:, col0:col0+ncols]
@@ -265,14 +278,14 @@ wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params 
  * Y and one term is computed per application. */
 wr_status wr_sequence_slab_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                                   uint32_t col0, uint32_t ncols, uint32_t *d_S, uint64_t L);
-/* Order-L sigma-basis of [S(x) | -I_m] with shift (0^n, 1^m) (Section 2.3):
+/* Order-L sigma-basis of [S(x) | -I_m] with shift (0^n, 1^m) (Section 2.4):
  * writes its first n rows (the P part) as d_P ((Dcap+1) x n x (m+n), [t][r][c])
  * and the shifted column degrees d_deg (m + n).  d_S: L*m*n residues. */
 wr_status wr_sigma_basis_device(wr_ctx *ctx, const uint32_t *d_S, uint64_t L, uint32_t m,
                                 uint32_t n, uint32_t prime, uint32_t *d_P, int32_t *d_deg,
                                 int64_t Dcap);
 /* x-adic valuation of det G for G (T x n x n, [t][i][j], residues) given by
- * its first T coefficients (Section 2.4 step 4, codeg).  *val = -1 when the
+ * its first T coefficients (Section 2.5 step 4, codeg).  *val = -1 when the
  * precision T does not determine it. */
 wr_status wr_det_valuation_device(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T,
                                   uint32_t prime, int64_t *val);

@@ -10,12 +10,12 @@ The heavy loops are plain C (oracle.c, built by build()); this module holds
 the glue and the rank readout.  What each function computes, and where the
 paper defines it:
 
-* sequence()            S_i = X^T A~^i Y mod p, i < L           (Section 2.1; Section 2.4 step 2)
-* blackbox_apply()      A~ = D1 A^T D2 A D1 (or D1 A D2 A^T D1)   (Section 2.3, Section 2.4 step 1)
+* sequence()            S_i = X^T A~^i Y mod p, i < L           (Section 2.2; Section 2.5 step 2)
+* blackbox_apply()      A~ = D1 A^T D2 A D1 (or D1 A D2 A^T D1)   (Section 2.3, Section 2.5 step 1)
 * blackbox_apply_rows() selected rows of A~ v, one at a time      (same; spot checks at full size)
-* mbasis()              sigma-basis of [S(x) | -I]               (Section 2.3 "sigma-basis computations")
-* generator()           minimal right matrix generator F          (Section 2.4 step 3)
-* rank_readout()        r = deg det F - codeg det F              (Section 2.4 step 4)
+* mbasis()              sigma-basis of [S(x) | -I]               (Section 2.4 "sigma-basis computations")
+* generator()           minimal right matrix generator F          (Section 2.5 step 3)
+* rank_readout()        r = deg det F - codeg det F              (Section 2.5 step 4)
 * rank_dense/sparse()   rank_p by Gaussian elimination (definition of the rank)
 * berlekamp_massey()    scalar minimal polynomial                (Section 1.2, Wiedemann)
 
@@ -168,7 +168,7 @@ def choose_side(rows: int, cols: int, side: Optional[int] = None) -> int:
 
 
 def seq_length(N: int, m: int, n: int) -> int:
-    """L = ceil(N/m) + ceil(N/n) + 2 (Section 2.4 step 2: 2n/s + O(1) terms)."""
+    """L = ceil(N/m) + ceil(N/n) + 2 (Section 2.5 step 2: 2n/s + O(1) terms)."""
     return -(-N // m) + -(-N // n) + 2
 
 
@@ -368,7 +368,7 @@ def det_valuation(G: np.ndarray, p: int, T0: int = 4) -> Optional[int]:
 
 def det_poly(G: np.ndarray, p: int) -> np.ndarray:
     """det G as a polynomial, by evaluation at n*D+1 points and Lagrange
-    interpolation (the paper's evaluation/interpolation fallback, Section 2.4).
+    interpolation (the paper's evaluation/interpolation fallback, Section 2.5).
     Tiny inputs only."""
     G = _c(G, np.uint32)
     D1, n, _ = G.shape
@@ -394,7 +394,7 @@ def det_poly(G: np.ndarray, p: int) -> np.ndarray:
 
 
 def rank_readout(M: np.ndarray, deg: np.ndarray, n: int, p: int) -> dict:
-    """Section 2.4 step 4: r = deg det F - codeg det F.  With
+    """Section 2.5 step 4: r = deg det F - codeg det F.  With
     F_j(x) = x^{delta_j} P_j(1/x):  deg det F = sum delta - v_x(det P) and
     codeg det F = v_x(det F).  (When P(0) is nonsingular F is column reduced
     and deg det F is the sum of its column degrees -- the paper's Popov
@@ -412,7 +412,7 @@ def rank_readout(M: np.ndarray, deg: np.ndarray, n: int, p: int) -> dict:
 
 def rank_wiedemann(A, p: int, m: int, n: int, seed: int, side: Optional[int] = None,
                    symmetric: bool = False, L: Optional[int] = None) -> dict:
-    """The paper's block Wiedemann rank algorithm (Section 2.4, steps 1-4)."""
+    """The paper's block Wiedemann rank algorithm (Section 2.5, steps 1-4)."""
     st = Setup(A, p, m, n, seed, side, symmetric)
     if st.N == 0:
         return dict(rank=0, S=np.zeros((0, m, n), np.uint32))

@@ -71,7 +71,7 @@ uint64_t or_invmod(uint64_t a, uint64_t p) { return invmod(a, p); }
 
 /* ------------------------------------------------------------------------ */
 /* primality: deterministic Miller-Rabin for n < 2^32 (bases 2, 7, 61)        */
-/* (the paper picks random primes for rank over Q, Section 2.4)               */
+/* (the paper picks random primes for rank over Q, Section 2.5)               */
 /* ------------------------------------------------------------------------ */
 
 int or_is_prime_u32(uint64_t n) {
@@ -103,7 +103,7 @@ int or_is_prime_u32(uint64_t n) {
 /* ------------------------------------------------------------------------ */
 /* counter-based random draws (SplitMix64 of Steele, Lea and Flood, 2014)     */
 /* The paper draws X, Y and the preconditioner diagonals at random (Section   */
-/* 2.4, step 2; Section 2.3); here they are derived from a 64-bit seed:       */
+/* 2.5, step 2; Section 2.3); here they are derived from a 64-bit seed:       */
 /*   h(seed, tag, idx) = sm(sm(seed ^ tag*GOLDEN) + idx)                      */
 /* with sm(x) the SplitMix64 output for state x (x + GOLDEN, then the mix).   */
 /* Tags: X = 1, Y = 2, D1 = 3, D2 = 4.  Block entries: h mod p.               */
@@ -211,7 +211,7 @@ static void scale_rows(int64_t n, int64_t w, const uint32_t *d, uint64_t p, uint
 
 /*
  * One application of the preconditioned black box (Section 2.3: the
- * preconditioners "are of the form A^T A"; Section 2.4 step 1 "form A~"):
+ * preconditioners "are of the form A^T A"; Section 2.5 step 1 "form A~"):
  *   side = 0 (N = C):  v <- D1 A^T D2 A D1 v      (D1: C entries, D2: R entries)
  *   side = 1 (N = R):  v <- D1 A D2 A^T D1 v      (D1: R entries, D2: C entries)
  * v is N x w, row-major.  A is given with its transpose At (or_csr_transpose).
@@ -253,7 +253,7 @@ void or_project(int64_t N, int64_t m, int64_t n, const uint32_t *X, const uint32
 }
 
 /*
- * Block Wiedemann sequence (Section 2.1 and Section 2.4 step 2):
+ * Block Wiedemann sequence (Section 2.2 and Section 2.5 step 2):
  *   S_i = X^T A~^i Y mod p, i = 0 .. L-1, S laid out [i][a][b] (L x m x n).
  * Literal definition: v <- Y; for each i: S_i = X^T v; v <- A~ v.
  * If V_out is non-null, the final v (= A~^(L-1) Y) is written there.
@@ -278,7 +278,7 @@ void or_sequence(int64_t R, int64_t C, const int64_t *rowptr, const int32_t *col
 
 /* ------------------------------------------------------------------------ */
 /* rank by Gaussian elimination mod p: the plain definition of rank_p(A)      */
-/* (the paper uses elimination mod p for the smaller matrices, Section 2.5)   */
+/* (the paper uses elimination mod p for the smaller matrices, Section 2.6.3) */
 /* ------------------------------------------------------------------------ */
 
 /* dense: a is rows x cols row-major (any int64 values); destroyed. */
@@ -479,8 +479,8 @@ int64_t or_berlekamp_massey(const uint32_t *s, int64_t len, uint64_t p, uint32_t
 
 /* ------------------------------------------------------------------------ */
 /* sigma-basis by M-Basis (Giorgi, Jeannerod, Villard, ISSAC 2003; the paper  */
-/* computes the minimal matrix generator through sigma-bases, Section 2.3,    */
-/* "sigma-basis computations", and Section 2.4 step 3).                        */
+/* computes the minimal matrix generator through sigma-bases, Section 2.4,    */
+/* "sigma-basis computations", and Section 2.5 step 3).                        */
 /*                                                                             */
 /* Input: S_0..S_{L-1} (m x n).  H(x) = [ S(x) | -I_m ] (m x q, q = m + n).    */
 /* Output: M(x) (q x q, coefficients M[t][r][c], t <= Dcap) with               */
@@ -574,7 +574,7 @@ int or_mbasis(const uint32_t *S, int64_t L, int64_t m, int64_t n, uint64_t p, in
 /* is an entry of least valuation v; it is a unit times x^v, every other row  */
 /* is reduced by a power-series multiple of the pivot row, and the precision  */
 /* drops by v.  Returns the valuation, or -1 when the precision runs out.      */
-/* (The paper needs codeg det F, Section 2.4 step 4.)                          */
+/* (The paper needs codeg det F, Section 2.5 step 4.)                          */
 /* ------------------------------------------------------------------------ */
 
 int64_t or_det_valuation(const uint32_t *G, int64_t n, int64_t T, uint64_t p) {

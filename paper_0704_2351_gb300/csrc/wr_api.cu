@@ -242,6 +242,13 @@ extern "C" wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues) {
     return WR_OK;
 }
 
+extern "C" wr_status wr_set_early_termination(wr_ctx *ctx, int64_t orders) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if (orders < 0) return fail(WR_EINVAL, "early termination: orders must be >= 0 (0: off)");
+    ctx->early_term = orders;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on) {
     if (!ctx) return fail(WR_EINVAL, "null context");
     ctx->pipeline = on != 0;
@@ -359,6 +366,7 @@ void copy_settings(const wr_ctx *parent, wr_ctx *c) {
     c->lane_width = parent->lane_width;
     c->pair_generic = parent->pair_generic;
     c->pipeline = parent->pipeline;
+    c->early_term = parent->early_term;
     c->sigma_chunk = parent->sigma_chunk;
     c->sigma_leaf = parent->sigma_leaf;
     c->alloc_fn = parent->alloc_fn;
@@ -421,6 +429,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
     if (st == WR_OK) st = dev_alloc(ctx, dP, sizeof(uint32_t) * (Dcap + 1) * r.n * q);
     if (st == WR_OK) st = dev_alloc(ctx, ddeg, sizeof(int32_t) * q);
     double setup_ms = 0, seq_ms = 0, sigma_ms = 0, tail_ms = 0;
+    int64_t L_used = L;  // terms the generator was computed from (< L after early termination)
     if (st == WR_OK && ctx->pipeline) {
         // The sigma-basis trails the sequence: a child context (own stream,
         // own host thread) runs M-Basis chunk k as soon as the sequence
@@ -429,6 +438,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
         if (!ctx->aux) st = make_child(ctx, &ctx->aux);
         wr_ctx *aux = ctx->aux;
         SeqFeed feed;
+        feed.throttle = ctx->early_term > 0 ? 3 : 0;
         cudaEvent_t ready0 = nullptr;
         if (st == WR_OK) {
             copy_settings(ctx, aux);
@@ -474,6 +484,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
             sigma_ms = std::chrono::duration<double, std::milli>(t_sig1 - t_sig0).count();
             tail_ms = std::max(0.0, std::chrono::duration<double, std::milli>(t_sig1 - t_seq1).count());
             if (st == WR_OK && sst != WR_OK) st = fail(sst, smsg);
+            if (feed.orders_used >= 0 && feed.orders_used < L) L_used = feed.orders_used;
         }
         for (cudaEvent_t e : feed.ev) cudaEventDestroy(e);
         if (ready0) cudaEventDestroy(ready0);
@@ -510,8 +521,9 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
     }
     if (e1) cudaEventDestroy(e1);
     if (e2) cudaEventDestroy(e2);
+    res->seq_len = L_used;
     if (st == WR_OK && (params->want & WR_WANT_SEQUENCE)) {
-        res->seq.resize((size_t)L * r.m * r.n);
+        res->seq.resize((size_t)L_used * r.m * r.n);
         cudaError_t e = cudaMemcpyAsync(res->seq.data(), dS.ptr, sizeof(uint32_t) * res->seq.size(),
                                         cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

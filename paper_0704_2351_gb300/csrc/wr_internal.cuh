@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <condition_variable>
 #include <mutex>
 #include <stdint.h>
@@ -321,6 +322,12 @@ struct SeqFeed {
     std::vector<int64_t> ready;
     bool closed = false;    // the producer has recorded its last event (or stopped)
     int64_t waited = -1;    // consumer: last event index its stream waits on
+    // early termination: the producer keeps at most `throttle` groups in
+    // flight (0: no limit) and stops once it has published stop_at terms;
+    // the consumer sets orders_used to the orders its sigma-basis took
+    int throttle = 0;
+    std::atomic<int64_t> stop_at{INT64_MAX};
+    int64_t orders_used = -1;
 };
 }  // namespace wr
 
@@ -339,6 +346,7 @@ struct wr_ctx {
     int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
     bool pair_generic = true; // generic projection, m = n: X and Y in one block, two terms per application
     bool pipeline = true;   // wr_rank: the sigma-basis trails the sequence on a second stream
+    int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
     wr_ctx *aux = nullptr;  // child context (own stream) that runs the trailing sigma-basis
     wr::SeqFeed *feed = nullptr; // set on a child context while it consumes a sequence in flight
     wr_alloc_fn alloc_fn = nullptr;  // caller's device allocator (nullptr: cudaMallocAsync)

@@ -1,5 +1,5 @@
 // Products of polynomial matrices mod p by number-theoretic transforms, for
-// the PM-Basis sigma-basis (Section 2.3: "PM-Basis ... reduces this
+// the PM-Basis sigma-basis (Section 2.4: "PM-Basis ... reduces this
 // computation to polynomial matrix multiplication", FFT primes c 2^k + 1, and
 // CRT with several FFT primes when the field itself has no large 2^k-th roots
 // of unity, with prod p_i > d n p^2).

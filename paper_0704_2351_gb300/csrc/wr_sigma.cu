@@ -1,5 +1,5 @@
 // sigma-basis of the block Wiedemann sequence and the rank readout
-// (Section 2.3 "sigma-basis computations", Section 2.4 steps 3 and 4).
+// (Section 2.4 "sigma-basis computations", Section 2.5 steps 3 and 4).
 //
 // M-Basis (Giorgi, Jeannerod, Villard) computes an order-L sigma-basis M(x)
 // of H(x) = [S(x) | -I_m] (m x q, q = m + n) for the shift (0^n, 1^m), one
@@ -49,6 +49,38 @@ __global__ void k_init_basis(uint32_t *__restrict__ P, int nr, int n, int q, int
         }
     }
     if (threadIdx.x == 0) *dmax = 1;
+}
+
+// Early termination test of one chunk.  The generator candidates are the n
+// columns of smallest shifted degree (ties by index); the chunk is quiet when
+// each has degree <= k0 (so its -Q part lies below the chunk's orders and the
+// window's E is its whole discrepancy) and zero discrepancy at every order of
+// the chunk.  Such columns are never touched by the chunk's eliminations.
+// *count: consecutive quiet orders so far, mirrored to a host-mapped slot.
+__global__ void k_quiet(const uint32_t *__restrict__ E, int bb, int m, int n, int q,
+                        const int32_t *__restrict__ deg, int64_t k0, long long *__restrict__ count,
+                        long long *host_slot) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < q; c += blockDim.x) {
+        const int dc = deg[c];
+        int before = 0;
+        for (int c2 = 0; c2 < q; c2++) {
+            const int d2 = deg[c2];
+            before += (d2 < dc || (d2 == dc && c2 < c)) ? 1 : 0;
+        }
+        if (before >= n) continue;
+        bool nz = dc > k0;
+        for (int x = 0; x < bb * m && !nz; x++) nz = E[(size_t)x * q + c] != 0u;
+        if (nz) atomicOr(&bad, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long v = bad ? 0 : *count + bb;
+        *count = v;
+        *(volatile long long *)host_slot = v;
+    }
 }
 
 // ---- window.  Block b takes coefficients t in [b tper, (b+1) tper) and
@@ -1063,19 +1095,55 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
 
     uint32_t *Pcur = d_P, *Pnext = P2.as<uint32_t>();
     int64_t Dbound = 1;
+    // early termination on a sequence in flight: a quiet-order count per
+    // chunk in host-mapped memory; the loop stays ET_LAG chunks ahead of the
+    // device and stops once ctx->early_term consecutive orders were quiet
+    SeqFeed *feed = d_deg_in ? nullptr : ctx->feed;
+    const bool early = feed && ctx->early_term > 0;
+    constexpr int ET_RING = 8, ET_LAG = 2;
+    long long *et_host = nullptr, *et_host_dev = nullptr;
+    cudaEvent_t et_ev[ET_RING] = {};
+    DevBuf et_count;
+    struct EtCleanup {
+        long long *&h;
+        cudaEvent_t *ev;
+        ~EtCleanup() {
+            if (h) cudaFreeHost(h);
+            for (int i = 0; i < ET_RING; i++)
+                if (ev[i]) cudaEventDestroy(ev[i]);
+        }
+    } et_cleanup{et_host, et_ev};
+    if (early) {
+        WR_CUDA(cudaHostAlloc((void **)&et_host, sizeof(long long) * ET_RING, cudaHostAllocMapped));
+        for (int i = 0; i < ET_RING; i++) et_host[i] = -1;
+        WR_CUDA(cudaHostGetDevicePointer((void **)&et_host_dev, et_host, 0));
+        for (int i = 0; i < ET_RING; i++) WR_CUDA(cudaEventCreateWithFlags(&et_ev[i], cudaEventDisableTiming));
+        WR_TRY(dev_alloc(ctx, et_count, sizeof(long long)));
+        WR_CUDA(cudaMemsetAsync(et_count.ptr, 0, sizeof(long long), s));
+    }
+    int64_t Lused = L;
     // profiling: events around the three kernels of every 16th chunk
     cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
     double pw = 0, pl = 0, pa = 0;
-    int64_t nchunks = (L + bmax - 1) / bmax, sampled = 0;
+    int64_t nchunks = (L + bmax - 1) / bmax, sampled = 0;  // (profiling extrapolates to all L orders)
     if (ctx->profiling)
         for (auto &e : pe) WR_CUDA(cudaEventCreate(&e));
     for (int64_t k0 = 0; k0 < L; k0 += bmax) {
         const int bb = (int)std::min<int64_t>(bmax, L - k0);
         const bool prof = ctx->profiling && ((k0 / bmax) % 16 == 0);
+        const int64_t chunk = k0 / bmax;
+        if (early && chunk >= ET_LAG) {
+            const int slot = (int)((chunk - ET_LAG) % ET_RING);
+            WR_CUDA(cudaEventSynchronize(et_ev[slot]));
+            if (*(volatile long long *)(et_host + slot) >= ctx->early_term) {
+                Lused = k0;  // the generator is stable: the chunks so far are the whole basis
+                feed->stop_at.store(k0);
+                break;
+            }
+        }
         // a sequence still in flight: the window reads S rows below k0 + bb
         // rounded up to its order tile
-        if (ctx->feed && !d_deg_in)
-            WR_TRY(feed_wait(ctx, ctx->feed, std::min<int64_t>(L, k0 + (bb + WIN_IB - 1) / WIN_IB * WIN_IB)));
+        if (feed) WR_TRY(feed_wait(ctx, feed, std::min<int64_t>(L, k0 + (bb + WIN_IB - 1) / WIN_IB * WIN_IB)));
         if (prof) WR_CUDA(cudaEventRecord(pe[0], s));
         // window: split coefficients [0, min(Dbound, k0 + bb - 1)] over the blocks
         const int64_t tspan = std::min<int64_t>(Dbound, k0 + bb - 1) + 1;
@@ -1091,6 +1159,11 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
                                                                   Esum.as<uint32_t>(), mp);
             WR_LAUNCHED(ctx);
             Ewin = Esum.as<uint32_t>();
+        }
+        if (early) {
+            k_quiet<<<1, 64, 0, s>>>(Ewin, bb, m, n, q, d_deg, k0, et_count.as<long long>(),
+                                     et_host_dev + chunk % ET_RING);
+            WR_LAUNCHED(ctx);
         }
         if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
         kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(
@@ -1115,9 +1188,11 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
             pa += c;
             sampled++;
         }
+        if (early) WR_CUDA(cudaEventRecord(et_ev[chunk % ET_RING], s));
         std::swap(Pcur, Pnext);
         Dbound = Dnew;
     }
+    if (feed) feed->orders_used = Lused;
     if (ctx->profiling) {
         for (auto &e : pe) cudaEventDestroy(e);
         const double scale = sampled ? (double)nchunks / sampled : 0.0;  // extrapolate the samples
@@ -1163,7 +1238,7 @@ __global__ void k_top_rows(const uint32_t *__restrict__ M, int64_t D, int n, int
     }
 }
 
-// PM-Basis (Section 2.3): the sigma-basis of the residual F (d orders, m x q)
+// PM-Basis (Section 2.4): the sigma-basis of the residual F (d orders, m x q)
 // for the starting degrees in d_deg (updated to the final degrees) is M1 M2,
 // M1 the basis of the first h orders and M2 that of the residual
 // R = (F M1) div x^h mod x^(d-h), the latter started from M1's degrees.  The
@@ -1212,7 +1287,10 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     ctx->last.sigma_window_ms = ctx->last.sigma_local_ms = ctx->last.sigma_apply_ms = 0.0;
     const bool automatic = ctx->sigma_leaf <= 0;
     const int64_t leaf = automatic ? SIGMA_LEAF_DEFAULT : ctx->sigma_leaf;
-    if (L <= leaf || (automatic && (L <= SIGMA_PM_MIN_L || m + n > 32)))
+    // early termination needs the order-by-order basis (PM-Basis splits the
+    // orders in halves and so needs all of them from the start)
+    const bool early = ctx->feed && ctx->early_term > 0;
+    if (early || L <= leaf || (automatic && (L <= SIGMA_PM_MIN_L || m + n > 32)))
         return mbasis_run(ctx, d_S, L, m, n, n, p, d_P, d_deg, nullptr, 0, Dcap, nullptr);
     const int q = m + n;
     cudaStream_t s = ctx->stream;

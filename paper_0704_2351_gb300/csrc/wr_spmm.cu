@@ -1,5 +1,5 @@
-// The block Wiedemann sequence on the device (Section 2.4 step 2 of the paper;
-// Section 2.1 for the block sequence X^T A~^i Y; Section 2.3 for A~).
+// The block Wiedemann sequence on the device (Section 2.5 step 2 of the paper;
+// Section 2.2 for the block sequence X^T A~^i Y; Section 2.3 for A~).
 //
 // With T_k = D1 A~^k Y (stored, N x nv residues) the recurrence is
 //   W       = D2 (A T_k)                    SpMM pass 1 (rows of A, or of A^T)
@@ -229,7 +229,7 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
 // reduced mod p before the exact uint64 atomics, so their sum cannot overflow
 // and does not depend on the order.
 // GRAM: the weighted Gram matrix sum_r wt[r] T[r]^T T[r] (m = n) instead; the
-// symmetric projection X = Y turns every term into one (Section 2.2).  Rows
+// symmetric projection X = Y turns every term into one (Section 2.3).  Rows
 // of t are tstride residues apart; GRAM takes its left factor from the first
 // m of them and the right one from yoff on (yoff > 0: the cross products of
 // the paired block [D1 X | D1 Y]).
@@ -783,6 +783,17 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     int64_t done = 0, group = 0;
     wr_status loop_st = WR_OK;
     while (done < iters && loop_st == WR_OK) {
+        if (feed && feed->throttle > 0) {
+            // early termination: stop once the consumer has enough terms, and
+            // keep few groups in flight so that its decision arrives in time
+            if (published >= feed->stop_at.load()) break;
+            const int64_t w = (int64_t)feed->ev.size() - feed->throttle;  // this thread alone appends
+            if (w >= 0) {
+                cudaError_t ce = cudaEventSynchronize(feed->ev[w]);
+                if (ce != cudaSuccess) { loop_st = cuda_fail(ce, "cudaEventSynchronize"); break; }
+            }
+            if (published >= feed->stop_at.load()) break;
+        }
         const int64_t todo = std::min(G, iters - done);
         if (todo == G && exec && !(ctx->profiling && group % PROF_EVERY == 0)) {
             cudaError_t ce = cudaGraphLaunch(exec, s);

@@ -77,6 +77,7 @@ _sig = {
     "wr_set_lane_width": ([vp, i32], ctypes.c_int),
     "wr_set_paired_projection": ([vp, i32], ctypes.c_int),
     "wr_set_pipeline": ([vp, i32], ctypes.c_int),
+    "wr_set_early_termination": ([vp, i64], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -246,6 +247,10 @@ def wr_set_paired_projection(ctx: int, on: bool) -> None:
 
 def wr_set_pipeline(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_pipeline(vp(ctx), 1 if on else 0))
+
+
+def wr_set_early_termination(ctx: int, orders: int) -> None:
+    _check(_lib.wr_set_early_termination(vp(ctx), orders))
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

@@ -263,6 +263,42 @@ def test_rank_pipeline_matches_sequential(wr, ctx, m, n, sym, chunk):
     assert np.array_equal(got["S"], ref["S"]) and np.array_equal(got["F"], ref["F"])
 
 
+@pytest.mark.parametrize("m,sym,chunk,quiet,R,C,r", [(4, False, 0, 64, 2100, 2000, 600),
+                                                       (8, True, 0, 64, 3000, 2600, 1200),
+                                                       (4, False, 16, 48, 1800, 1700, 400),
+                                                       (1, False, 0, 64, 900, 800, 300),
+                                                       (2, False, 0, 128, 1500, 1400, 1400)])
+def test_rank_early_termination(wr, ctx, m, sym, chunk, quiet, R, C, r):
+    """Early termination: the trailing M-Basis stops the sequence once the
+    generator candidates have been quiet for `quiet` orders.  The rank equals
+    the planted one, the generator equals the oracle's from all L terms (and
+    from the terms actually used), the terms used match the oracle's, and a
+    rank-deficient matrix needs far fewer than L terms (about 2r/n + O(1));
+    a full-rank one (last case) runs to the end or close to it."""
+    p = 1073741789
+    A = synth.planted_sparse(R, C, r, row_len=6, seed=r + m)
+    L = oracle.seq_length(min(R, C), m, m)
+    try:
+        wr.wr_set_sigma_chunk(ctx, chunk)
+        wr.wr_set_early_termination(ctx, quiet)
+        got = gpu_rank(wr, ctx, A, p, m, m, 91, want=3, symmetric=sym)
+    finally:
+        wr.wr_set_early_termination(ctx, 0)
+        wr.wr_set_sigma_chunk(ctx, 0)
+    used = got["seq_len"]
+    assert got["rank"] == r
+    assert 0 < used <= L and got["S"].shape[0] == used
+    ref = oracle.rank_wiedemann(A, p, m, m, seed=91, symmetric=sym)
+    assert np.array_equal(got["S"], ref["S"][:used])
+    assert np.array_equal(got["F"], ref["F"]) and np.array_equal(got["delta"], ref["delta"])
+    short = oracle.rank_wiedemann(A, p, m, m, seed=91, symmetric=sym, L=used)
+    assert short["rank"] == r and np.array_equal(short["F"], got["F"])
+    if r < min(R, C) // 2:
+        assert used < L - (min(R, C) - r) // (2 * m), "early termination saved too little (%d of %d)" % (used, L)
+    with pytest.raises(wr.WrError):
+        wr.wr_set_early_termination(ctx, -1)
+
+
 @pytest.mark.parametrize("m", [1, 4, 8])
 def test_rank_planted_symmetric(wr, ctx, m):
     p = 1073741789

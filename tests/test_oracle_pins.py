@@ -229,7 +229,7 @@ def test_sequence_equals_dense_powers():
 
 
 def test_symmetric_projection_gives_symmetric_terms():
-    """With X = Y the terms Y^T A~^i Y are symmetric because A~ is (Section 2.2)."""
+    """With X = Y the terms Y^T A~^i Y are symmetric because A~ is (Section 2.3)."""
     p = 65521
     A = synth.random_sparse(40, 30, 4, seed=6)
     st = oracle.Setup(A, p, 4, 4, seed=3, symmetric=True)
@@ -392,7 +392,7 @@ def test_det_valuation_matches_interpolated_determinant():
 # ---------------------------------------------------------------- rank
 
 def test_wiedemann_rank_equals_elimination_many_shapes():
-    """The Monte Carlo rank (Section 2.4) equals the elimination rank."""
+    """The Monte Carlo rank (Section 2.5) equals the elimination rank."""
     bad = 0
     for t in range(25):
         rng = np.random.default_rng(300 + t)
