@@ -96,6 +96,8 @@ typedef struct {
     double sigma_tail_ms;    /* sigma-basis time after the sequence's end: with the pipeline  */
                              /* (wr_set_pipeline) sigma_ms overlaps the sequence and only    */
                              /* this part adds to the time to rank                           */
+    int64_t sequence_terms;  /* terms the sequence computed (early termination: at least the */
+                             /* result's seq_len, the terms the generator used)               */
 } wr_timings;
 
 /* Device allocator callbacks (for example PyTorch's caching allocator):

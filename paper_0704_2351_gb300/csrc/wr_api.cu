@@ -192,6 +192,10 @@ extern "C" void wr_destroy(wr_ctx *ctx) {
     if (!ctx) return;
     if (ctx->aux) wr_destroy(ctx->aux);
     cudaSetDevice(ctx->device);
+    if (ctx->seq_stream) {
+        cudaStreamSynchronize(ctx->seq_stream);
+        cudaStreamDestroy(ctx->seq_stream);
+    }
     cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -436,6 +440,14 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
         // stream has published S_0 .. S_{k+b-1}, so the two overlap on the
         // device and only the last chunks run after the sequence ends.
         if (!ctx->aux) st = make_child(ctx, &ctx->aux);
+        if (st == WR_OK && !ctx->seq_stream) {
+            // the sequence's SpMM blocks go first wherever both phases have
+            // blocks waiting; the sigma-basis fills the gaps
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            cudaError_t ce = cudaStreamCreateWithPriority(&ctx->seq_stream, cudaStreamNonBlocking, greatest);
+            if (ce != cudaSuccess) { ctx->seq_stream = nullptr; st = cuda_fail(ce, "cudaStreamCreateWithPriority"); }
+        }
         wr_ctx *aux = ctx->aux;
         SeqFeed feed;
         feed.throttle = ctx->early_term > 0 ? 3 : 0;
@@ -468,7 +480,25 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
                 t_sig1 = std::chrono::steady_clock::now();
                 if (sst != WR_OK) smsg = wr_last_error();
             });
-            st = run_sequence(ctx, mat, *params, L, dS.as<uint32_t>(), &setup_ms, &seq_ms, &feed);
+            // the sequence on the high-priority stream, after what the
+            // caller's stream holds so far (the allocations above)
+            cudaStream_t user = ctx->stream;
+            cudaError_t ce = cudaStreamWaitEvent(ctx->seq_stream, ready0, 0);
+            if (ce != cudaSuccess) {
+                st = cuda_fail(ce, "cudaStreamWaitEvent");
+            } else {
+                ctx->stream = ctx->seq_stream;
+                st = run_sequence(ctx, mat, *params, L, dS.as<uint32_t>(), &setup_ms, &seq_ms, &feed);
+                ctx->stream = user;
+                // run_sequence waited for its last event; order the caller's
+                // stream after the sequence stream all the same
+                cudaEvent_t done_ev = nullptr;
+                if (cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming) == cudaSuccess) {
+                    cudaEventRecord(done_ev, ctx->seq_stream);
+                    cudaStreamWaitEvent(user, done_ev, 0);
+                    cudaEventDestroy(done_ev);
+                }
+            }
             const auto t_seq1 = std::chrono::steady_clock::now();
             {
                 std::lock_guard<std::mutex> lk(feed.mu);

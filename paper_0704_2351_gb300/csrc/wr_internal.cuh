@@ -348,6 +348,7 @@ struct wr_ctx {
     bool pipeline = true;   // wr_rank: the sigma-basis trails the sequence on a second stream
     int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
     wr_ctx *aux = nullptr;  // child context (own stream) that runs the trailing sigma-basis
+    cudaStream_t seq_stream = nullptr; // high-priority stream of the pipelined sequence (lazy)
     wr::SeqFeed *feed = nullptr; // set on a child context while it consumes a sequence in flight
     wr_alloc_fn alloc_fn = nullptr;  // caller's device allocator (nullptr: cudaMallocAsync)
     wr_free_fn free_fn = nullptr;

@@ -841,6 +841,7 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     cudaEventElapsedTime(&b, e1, e2);
     if (setup_ms) *setup_ms = a;
     if (seq_ms) *seq_ms = b;
+    ctx->last.sequence_terms = feed ? published : L;
     ctx->last.spmm_ms += prof_ms;
     ctx->last.spmm_launches += prof_launches;
     cudaEventDestroy(e0);
