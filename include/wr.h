@@ -196,10 +196,35 @@ wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols, const int6
 wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz,
                                     const int64_t *d_rowptr, const int32_t *d_colidx,
                                     const int32_t *d_vals, wr_matrix **out);
-/* rows, cols, nnz, and the padded slot counts of the A and A^T layouts. */
+/* rows, cols, nnz, and the padded slot counts of the A and A^T layouts (of
+ * the reduced matrix when the chain reduction ran). */
 wr_status wr_matrix_info(const wr_matrix *mat, int64_t *rows, int64_t *cols, int64_t *nnz,
                          int64_t *slots_a, int64_t *slots_at);
 void wr_matrix_free(wr_matrix *mat);
+
+/* Chain reduction at read time (Section 2.6.4, off by default): loads through
+ * this context first remove, repeatedly, every row or column whose only
+ * nonzero entry is +-1, together with the column or row of that entry (a
+ * free-face pair; one step of Gaussian elimination that changes nothing
+ * else), and the empty rows and columns.  The matrix held is the reduced one
+ * and wr_rank returns rank_offset + its rank, rank_offset being the number of
+ * pivots taken.  Unit pivots are units modulo every prime, so the reduced
+ * matrix serves any prime; sequences and generators are those of the reduced
+ * matrix.  The reduction is a host pass (a matrix given in device memory is
+ * copied to the host for it). */
+wr_status wr_set_chain_reduction(wr_ctx *ctx, int32_t on);
+/* The input's size and the pivots the chain reduction took (0 without it). */
+wr_status wr_matrix_reduction(const wr_matrix *mat, int64_t *rows_in, int64_t *cols_in, int64_t *rank_offset);
+/* The same reduction on host arrays, without a device: writes the reduced
+ * CSR (rows and columns renumbered in their input order) into arrays sized
+ * for the input (rows + 1 and rowptr[rows] entries) and, when the pointers
+ * are not NULL, each kept row's and column's input index (rows resp. cols
+ * entries at most); rank(input) = *rank_offset + rank(output) over every
+ * prime field.  WR_EINVAL on a malformed CSR. */
+wr_status wr_chain_reduce_csr(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
+                              const int32_t *vals, int64_t *out_rows, int64_t *out_cols, int64_t *out_rowptr,
+                              int32_t *out_colidx, int32_t *out_vals, int32_t *out_row_of, int32_t *out_col_of,
+                              int64_t *rank_offset);
 
 /* ---------------------------------------------------------------- rank */
 

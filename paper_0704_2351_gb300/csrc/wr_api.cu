@@ -316,14 +316,58 @@ static wr_status load_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nn
     return WR_OK;
 }
 
+static wr_status load_host_plain(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
+                                 const int32_t *colidx, const int32_t *vals, wr_matrix **out);
+
+// Chain reduction at read time: reduce on the host, load the reduced matrix.
+static wr_status load_reduced(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
+                              const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
+    ReducedCsr r;
+    WR_TRY(chain_reduce_host(rows, cols, rowptr, colidx, vals, r));
+    WR_TRY(load_host_plain(ctx, r.rows, r.cols, r.rowptr.data(), r.colidx.data(), r.vals.data(), out));
+    (*out)->rows_in = rows;
+    (*out)->cols_in = cols;
+    (*out)->rank_offset = r.rank_offset;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz,
                                                const int64_t *d_rowptr, const int32_t *d_colidx,
                                                const int32_t *d_vals, wr_matrix **out) {
-    return load_device(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, out);
+    if (ctx && ctx->chain_reduce) {
+        // the reduction is a host pass: bring the CSR over first
+        if (!out || !d_rowptr) return fail(WR_EINVAL, "null argument");
+        if (rows < 0 || cols < 0 || nnz < 0) return fail(WR_EINVAL, "negative size");
+        if (nnz > 0 && (!d_colidx || !d_vals)) return fail(WR_EINVAL, "null column or value array");
+        WR_CUDA(cudaSetDevice(ctx->device));
+        std::vector<int64_t> rp(rows + 1);
+        std::vector<int32_t> ci(nnz), va(nnz);
+        WR_CUDA(cudaMemcpyAsync(rp.data(), d_rowptr, sizeof(int64_t) * (rows + 1), cudaMemcpyDeviceToHost, ctx->stream));
+        if (nnz > 0) {
+            WR_CUDA(cudaMemcpyAsync(ci.data(), d_colidx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, ctx->stream));
+            WR_CUDA(cudaMemcpyAsync(va.data(), d_vals, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        WR_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (rp[rows] != nnz) return fail(WR_EINVAL, "rowptr[rows] must equal nnz");
+        return load_reduced(ctx, rows, cols, rp.data(), ci.data(), va.data(), out);
+    }
+    WR_TRY(load_device(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, out));
+    (*out)->rows_in = rows;
+    (*out)->cols_in = cols;
+    return WR_OK;
 }
 
 extern "C" wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
                                         const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
+    if (ctx && ctx->chain_reduce) return load_reduced(ctx, rows, cols, rowptr, colidx, vals, out);
+    WR_TRY(load_host_plain(ctx, rows, cols, rowptr, colidx, vals, out));
+    (*out)->rows_in = rows;
+    (*out)->cols_in = cols;
+    return WR_OK;
+}
+
+static wr_status load_host_plain(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
+                                 const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
     if (!ctx || !out || !rowptr) return fail(WR_EINVAL, "null argument");
     if (rows < 0 || cols < 0) return fail(WR_EINVAL, "negative size");
     const int64_t nnz = rowptr[rows];
@@ -340,6 +384,21 @@ extern "C" wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols,
         WR_CUDA(cudaMemcpyAsync(va.ptr, vals, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
     }
     return load_device(ctx, rows, cols, nnz, rp.as<int64_t>(), ci.as<int32_t>(), va.as<int32_t>(), out);
+}
+
+extern "C" wr_status wr_set_chain_reduction(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->chain_reduce = on != 0;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_matrix_reduction(const wr_matrix *mat, int64_t *rows_in, int64_t *cols_in,
+                                         int64_t *rank_offset) {
+    if (!mat) return fail(WR_EINVAL, "null matrix");
+    if (rows_in) *rows_in = mat->rows_in;
+    if (cols_in) *cols_in = mat->cols_in;
+    if (rank_offset) *rank_offset = mat->rank_offset;
+    return WR_OK;
 }
 
 extern "C" wr_status wr_matrix_info(const wr_matrix *mat, int64_t *rows, int64_t *cols, int64_t *nnz,
@@ -371,6 +430,7 @@ void copy_settings(const wr_ctx *parent, wr_ctx *c) {
     c->pair_generic = parent->pair_generic;
     c->pipeline = parent->pipeline;
     c->early_term = parent->early_term;
+    c->chain_reduce = parent->chain_reduce;
     c->sigma_chunk = parent->sigma_chunk;
     c->sigma_leaf = parent->sigma_leaf;
     c->alloc_fn = parent->alloc_fn;
@@ -421,7 +481,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
     res->n = (uint32_t)r.n;
     res->seq_len = r.L;
     if (r.N == 0) {
-        res->rank = 0;
+        res->rank = mat->rank_offset;
         *out = res;
         return WR_OK;
     }
@@ -571,7 +631,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
                                       std::to_string(ro.codeg) + ", deg det " + std::to_string(ro.deg_det) +
                                       "); retry with another seed");
     }
-    res->rank = ro.rank;
+    res->rank = mat->rank_offset + ro.rank;
     res->deg_det = ro.deg_det;
     res->codeg = ro.codeg;
     res->sum_delta = ro.sum_delta;

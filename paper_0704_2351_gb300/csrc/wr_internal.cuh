@@ -347,6 +347,7 @@ struct wr_ctx {
     bool pair_generic = true; // generic projection, m = n: X and Y in one block, two terms per application
     bool pipeline = true;   // wr_rank: the sigma-basis trails the sequence on a second stream
     int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
+    bool chain_reduce = false; // matrix loads: remove unit singleton rows/columns and empty ones
     wr_ctx *aux = nullptr;  // child context (own stream) that runs the trailing sigma-basis
     cudaStream_t seq_stream = nullptr; // high-priority stream of the pipelined sequence (lazy)
     wr::SeqFeed *feed = nullptr; // set on a child context while it consumes a sequence in flight
@@ -359,6 +360,9 @@ struct wr_ctx {
 struct wr_matrix {
     wr_ctx *ctx = nullptr;
     int64_t rows = 0, cols = 0, nnz = 0;
+    // chain reduction at load: the matrix held is the reduced one, of the
+    // rows_in x cols_in input; rank(input) = rank_offset + rank(held)
+    int64_t rows_in = 0, cols_in = 0, rank_offset = 0;
     wr::Sell a;    // rows of A
     wr::Sell at;   // rows of A^T
     // SpMM residues per lane tuned for [layout a / at][log2 block width] (0: not yet)
@@ -378,6 +382,16 @@ struct wr_result {
 namespace wr {
 
 wr_status dev_alloc(wr_ctx *ctx, DevBuf &b, size_t bytes);
+
+// chain reduction (wr_reduce.cu): the reduced CSR, its rows' and columns'
+// indices in the input, and the number of unit pivots taken
+struct ReducedCsr {
+    int64_t rows = 0, cols = 0, rows_in = 0, cols_in = 0, rank_offset = 0;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colidx, vals, row_of, col_of;
+};
+wr_status chain_reduce_host(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
+                            const int32_t *vals, ReducedCsr &out);
 
 // format (wr_format.cu)
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,

@@ -78,6 +78,9 @@ _sig = {
     "wr_set_paired_projection": ([vp, i32], ctypes.c_int),
     "wr_set_pipeline": ([vp, i32], ctypes.c_int),
     "wr_set_early_termination": ([vp, i64], ctypes.c_int),
+    "wr_set_chain_reduction": ([vp, i32], ctypes.c_int),
+    "wr_matrix_reduction": ([vp, P(i64), P(i64), P(i64)], ctypes.c_int),
+    "wr_chain_reduce_csr": ([i64, i64, vp, vp, vp, P(i64), P(i64), vp, vp, vp, vp, vp, P(i64)], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_load_csr_device": ([vp, i64, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
     "wr_matrix_info": ([vp, P(i64), P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -251,6 +254,39 @@ def wr_set_pipeline(ctx: int, on: bool) -> None:
 
 def wr_set_early_termination(ctx: int, orders: int) -> None:
     _check(_lib.wr_set_early_termination(vp(ctx), orders))
+
+
+def wr_set_chain_reduction(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_chain_reduction(vp(ctx), 1 if on else 0))
+
+
+def wr_matrix_reduction(mat: int) -> dict:
+    a, b, c = i64(), i64(), i64()
+    _check(_lib.wr_matrix_reduction(vp(mat), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(rows_in=a.value, cols_in=b.value, rank_offset=c.value)
+
+
+def wr_chain_reduce_csr(rows: int, cols: int, rowptr, colidx, vals):
+    """Host chain reduction (no device needed): returns (rows, cols, rowptr,
+    colidx, vals, row_of, col_of, rank_offset) of the reduced CSR, row_of and
+    col_of being the kept rows' and columns' input indices."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.int32)
+    nnz = int(rowptr[rows])
+    orp = np.zeros(rows + 1, dtype=np.int64)
+    oci = np.zeros(max(nnz, 1), dtype=np.int32)
+    ova = np.zeros(max(nnz, 1), dtype=np.int32)
+    rof = np.zeros(max(rows, 1), dtype=np.int32)
+    cof = np.zeros(max(cols, 1), dtype=np.int32)
+    r, c, off = i64(), i64(), i64()
+    _check(_lib.wr_chain_reduce_csr(rows, cols, vp(rowptr.ctypes.data), vp(colidx.ctypes.data),
+                                    vp(vals.ctypes.data), ctypes.byref(r), ctypes.byref(c),
+                                    vp(orp.ctypes.data), vp(oci.ctypes.data), vp(ova.ctypes.data),
+                                    vp(rof.ctypes.data), vp(cof.ctypes.data), ctypes.byref(off)))
+    n2 = int(orp[r.value])
+    return (r.value, c.value, orp[: r.value + 1].copy(), oci[:n2].copy(), ova[:n2].copy(),
+            rof[: r.value].copy(), cof[: c.value].copy(), off.value)
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

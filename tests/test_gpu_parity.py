@@ -299,6 +299,49 @@ def test_rank_early_termination(wr, ctx, m, sym, chunk, quiet, R, C, r):
         wr.wr_set_early_termination(ctx, -1)
 
 
+def test_rank_with_chain_reduction(wr, ctx):
+    """Loads with the chain reduction: wr_rank = pivots taken + rank of the
+    reduced matrix = the planted rank (and the oracle's elimination rank);
+    the reduction agrees with the host entry point; device-side loads reduce
+    the same way; a matrix that reduces to nothing has rank = its pivots."""
+    p = 1073741789
+    d_n, d_n1 = synth.chain_pair(2500, seed=5, homology=2)
+    mats = [synth.planted_sparse(1500, 1300, 1111, row_len=6, seed=12), d_n, d_n1,
+            synth.config1(scale=0.03)]
+    n = 40
+    bid = synth.dense_to_csr(np.eye(n, dtype=np.int64) + np.diag(-np.ones(n - 1, dtype=np.int64), 1))
+    bid.rank = n
+    mats.append(bid)
+    try:
+        wr.wr_set_chain_reduction(ctx, True)
+        for A in mats:
+            h = load(wr, ctx, A)
+            red = wr.wr_matrix_reduction(h)
+            r, c, *_rest, off = wr.wr_chain_reduce_csr(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+            assert (red["rows_in"], red["cols_in"], red["rank_offset"]) == (A.rows, A.cols, off)
+            info = wr.wr_matrix_info(h)
+            assert (info["rows"], info["cols"]) == (r, c)
+            for b, sym in [(8, False), (4, True)]:
+                res = wr.wr_rank(ctx, h, wr.make_params(p, b, b, 3, projection=wr.WR_PROJ_SYMMETRIC if sym
+                                                      else wr.WR_PROJ_GENERIC))
+                assert wr.wr_result_rank(res) == A.rank
+                wr.wr_result_free(res)
+            wr.wr_matrix_free(h)
+            # the same from device arrays
+            d_rp = torch.from_numpy(A.rowptr.astype(np.int64)).cuda()
+            d_ci = torch.from_numpy(A.colidx.astype(np.int32)).cuda()
+            d_va = torch.from_numpy(A.vals.astype(np.int32)).cuda()
+            h = wr.wr_matrix_load_csr_device(ctx, A.rows, A.cols, A.nnz, d_rp, d_ci, d_va)
+            assert wr.wr_matrix_reduction(h)["rank_offset"] == off
+            res = wr.wr_rank(ctx, h, wr.make_params(p, 8, 8, 4))
+            assert wr.wr_result_rank(res) == A.rank
+            wr.wr_result_free(res)
+            wr.wr_matrix_free(h)
+    finally:
+        wr.wr_set_chain_reduction(ctx, False)
+    assert oracle.rank_sparse(mats[0], p) == mats[0].rank
+
+
 @pytest.mark.parametrize("m", [1, 4, 8])
 def test_rank_planted_symmetric(wr, ctx, m):
     p = 1073741789
