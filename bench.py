@@ -52,6 +52,19 @@ def workload(rank: int):
         "170000; block Wiedemann m=n=8 mod p=1073741789, L=45002" % A.nnz))
 
 
+def apply_options(wr, ctx, args):
+    """Read-time passes and early termination, when asked for (all off by default)."""
+    wr.wr_set_chain_reduction(ctx, bool(getattr(args, "chain_reduction", False)))
+    wr.wr_set_locality_order(ctx, bool(getattr(args, "locality_order", False)))
+    wr.wr_set_early_termination(ctx, int(getattr(args, "early_termination", 0)))
+
+
+def options_config(args):
+    return {"chain_reduction": bool(getattr(args, "chain_reduction", False)),
+            "locality_order": bool(getattr(args, "locality_order", False)),
+            "early_termination_orders": int(getattr(args, "early_termination", 0))}
+
+
 def applications(L, symmetric):
     return (L // 2) if symmetric else (L - 1)
 
@@ -173,6 +186,7 @@ def run_blackbox_only(args):
         A, cfg = workload(0)
         p, n, seed, name = cfg["p"], cfg["n"], cfg["seed"], cfg["name"]
     ctx = wr.wr_create(0)
+    apply_options(wr, ctx, args)
     mat = wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals)
     N = min(A.rows, A.cols)
     g = torch.Generator().manual_seed(seed)
@@ -194,9 +208,170 @@ def run_blackbox_only(args):
     peak = measured_peaks().get("hbm_gbs")
     line = {"only": "blackbox", "workload": name, "steps": args.steps, "ms_per_application_wall": ms,
             "algorithmic_bytes_per_pass": per_pass,
-            "gbs_per_pass_at_wall_time": 1e-6 * sum(per_pass) / ms, "hbm_peak_gbs": peak}
+            "gbs_per_pass_at_wall_time": 1e-6 * sum(per_pass) / ms, "hbm_peak_gbs": peak,
+            "options": options_config(args)}
     print(json.dumps(line), flush=True)
     wr.wr_matrix_free(mat)
+    wr.wr_destroy(ctx)
+    return 0
+
+
+def run_batch(args):
+    """Batched workload: chain-complex pairs (d_n, d_{n+1}, d_n d_{n+1} = 0)
+    with row counts log-uniform in [5,000, 300,000], each matrix solved
+    modulo 4 primes below 2^30 (rank over Q = the maximum).  Plain = every job
+    through wr_rank one at a time; batched = one wr_rank_batch call.  Both
+    are timed end to end (host clock, results copied back); every batched
+    rank must equal the plain one and the planted rank."""
+    import torch
+    from paper_0704_2351_gb300 import synth, wr
+    pairs = synth.config3_pairs(npairs=args.pairs)
+    mats = [A for pr in pairs for A in pr]
+    primes = []
+    c = (1 << 30) - 1
+    while len(primes) < 4:
+        if all(c % d for d in range(2, int(c ** 0.5) + 1)):
+            primes.append(c)
+        c -= 2
+    ctx = wr.wr_create(0)
+    apply_options(wr, ctx, args)
+    wr.wr_set_batch_slots(ctx, args.slots)
+    handles = [wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals) for A in mats]
+    b = args.block
+    jobs = [(i, p) for i in range(len(mats)) for p in primes]
+    params = [wr.make_params(p, b, b, synth.SEED_BASE + 3 + 7 * i) for (i, p) in jobs]
+    # warm-up (module load, first graph instantiation)
+    small = min(range(len(mats)), key=lambda i: mats[i].nnz)
+    wr.wr_result_free(wr.wr_rank(ctx, handles[small], params[small * 4]))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    plain = []
+    for h, (i, p), prm in zip([handles[i] for i, _ in jobs], jobs, params):
+        res = wr.wr_rank(ctx, h, prm)
+        plain.append(wr.wr_result_rank(res))
+        wr.wr_result_free(res)
+    t_plain = time.perf_counter() - t
+    t = time.perf_counter()
+    outs = wr.wr_rank_batch(ctx, [handles[i] for i, _ in jobs], params)
+    t_batch = time.perf_counter() - t
+    batched = [wr.wr_result_rank(o) for o in outs]
+    for o in outs:
+        wr.wr_result_free(o)
+    assert batched == plain, "batched ranks differ from the plain ones"
+    for k, (i, p) in enumerate(jobs):
+        assert batched[k] == mats[i].rank, "job %d: rank %d != planted %d" % (k, batched[k], mats[i].rank)
+    rank_q = [max(batched[4 * i: 4 * i + 4]) for i in range(len(mats))]
+    chain_ok = all(rank_q[2 * k] + rank_q[2 * k + 1] <= pairs[k][0].cols for k in range(len(pairs)))
+    work = sum(2.0 * mats[i].nnz * b * ((-(-min(mats[i].rows, mats[i].cols) // b)) * 2 + 1) for i, _ in jobs)
+    line = {"metric": METRIC, "workload": "batched", "value": work / t_batch, "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+            "config": {"pairs": args.pairs, "matrices": len(mats), "primes": primes, "jobs": len(jobs),
+                       "block": [b, b], "slots": args.slots, "options": options_config(args),
+                       "rows": [int(min(A.rows for A in mats)), int(max(A.rows for A in mats))],
+                       "nnz_total": int(sum(A.nnz for A in mats))},
+            "plain_s": t_plain, "batched_s": t_batch, "speedup": t_plain / t_batch,
+            "ranks_equal_planted": True, "chain_rank_sum_ok": chain_ok,
+            "gpu_launches_batched": wr.wr_last_timings(ctx)["kernel_launches"]}
+    print(json.dumps(line), flush=True)
+    for h in handles:
+        wr.wr_matrix_free(h)
+    wr.wr_destroy(ctx)
+    return 0
+
+
+def _latency_stats(lat):
+    lat = sorted(lat)
+    pick = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]
+    return {"p50_ms": pick(0.5), "p99_ms": pick(0.99), "mean_ms": sum(lat) / len(lat)}
+
+
+def run_serve(args):
+    """Served workload: a Poisson trace of rank queries (rows log-uniform in
+    [1,000, rows_hi], 10-20 nnz/row, planted rank 0.95 min(R, C), 4 primes
+    below 2^30, m = n = 16).  Plain = one request at a time in arrival order
+    (latency = queueing behind earlier requests + own time, from the measured
+    service times).  Served = the continuous-batching server fed at the
+    trace's arrival times, at the trace rate and at 0.7x the plain capacity."""
+    import torch
+    from paper_0704_2351_gb300 import synth, wr
+    trace = synth.config4_trace(nreq=args.requests, rate=args.rate, hi=args.rows_hi)
+    primes = [1073741789, 1073741783, 1073741741, 1073741723]
+    mats = [synth.config4_matrix(r) for r in trace]
+    ctx = wr.wr_create(0)
+    apply_options(wr, ctx, args)
+    handles = [wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals) for A in mats]
+    b = args.block
+    params = [wr.make_params(primes[r["prime_slot"]], b, b, r["seed"]) for r in trace]
+    wr.wr_result_free(wr.wr_rank(ctx, handles[0], params[0]))
+    torch.cuda.synchronize()
+    service = []
+    ranks = []
+    for h, prm in zip(handles, params):
+        t = time.perf_counter()
+        res = wr.wr_rank(ctx, h, prm)
+        service.append(time.perf_counter() - t)
+        ranks.append(wr.wr_result_rank(res))
+        wr.wr_result_free(res)
+    assert ranks == [r["rank"] for r in trace], "plain ranks differ from the planted ones"
+    cap_plain = len(trace) / sum(service)
+
+    def plain_latency(arrivals):
+        """One request at a time in arrival order: (latencies in ms, completions/s)."""
+        free, lat = 0.0, []
+        for a, s in zip(arrivals, service):
+            start = max(a, free)
+            free = start + s
+            lat.append(1e3 * (free - a))
+        return lat, len(arrivals) / (free - arrivals[0])
+
+    def served(arrivals):
+        srv = wr.wr_server_start(ctx, max_slots=args.slots, hbm_budget=args.hbm_budget, queue_cap=1 << 20)
+        t0 = time.perf_counter()
+        tickets = []
+        for a, h, prm in zip(arrivals, handles[:len(arrivals)], params[:len(arrivals)]):
+            d = a - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets.append(wr.wr_submit(srv, h, prm))
+        got = []
+        for tk in tickets:
+            res = wr.wr_wait(srv, tk, 3600 * 1000)
+            got.append(wr.wr_result_rank(res))
+            wr.wr_result_free(res)
+        st = wr.wr_server_stats(srv)
+        wr.wr_server_stop(srv)
+        assert got == ranks[:len(arrivals)], "served ranks differ from the plain ones"
+        return st
+
+    arr = [r["t"] for r in trace]
+    out = {}
+    for name, scale in [("trace_rate", 1.0), ("rate_0.7x_plain_capacity", None)]:
+        if scale is None:
+            # the first quarter of the trace, arrivals stretched to 0.7x the
+            # plain capacity (the whole trace would take n / (0.7 capacity))
+            k = max(20, len(arr) // 4)
+            lam = 0.7 * cap_plain
+            a = [x * args.rate / lam for x in arr[:k]]
+        else:
+            lam = args.rate
+            a = arr
+        st = served(a)
+        lat, thr = plain_latency(a)
+        out[name] = {"arrival_rate_rps": lam, "requests": len(a),
+                     "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                                "throughput_rps": st["throughput_rps"], "max_resident": st["max_resident"]},
+                     "plain": dict(_latency_stats(lat), throughput_rps=thr)}
+    line = {"metric": METRIC, "workload": "served", "unit": "requests/s", "n_gpus": 1,
+            "value": out["trace_rate"]["served"]["throughput_rps"], "higher_is_better": True,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"requests": len(trace), "rate": args.rate, "rows": [1000, args.rows_hi],
+                       "block": [b, b], "slots": args.slots, "hbm_budget": args.hbm_budget,
+                       "options": options_config(args),
+                       "nnz_total": int(sum(A.nnz for A in mats))},
+            "plain_capacity_rps": cap_plain, "results": out, "ranks_equal_planted": True}
+    print(json.dumps(line), flush=True)
+    for h in handles:
+        wr.wr_matrix_free(h)
     wr.wr_destroy(ctx)
     return 0
 
@@ -291,6 +466,12 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="batch / serve: block width m = n")
     ap.add_argument("--slots", type=int, default=8, help="batch / serve: concurrent slots")
     ap.add_argument("--hbm-budget", type=int, default=0, help="serve: admission budget in bytes (0: none)")
+    ap.add_argument("--chain-reduction", action="store_true",
+                    help="remove unit singleton rows/columns at load (rank = pivots + rank of the rest)")
+    ap.add_argument("--locality-order", action="store_true",
+                    help="renumber rows and columns by decreasing entry count at load (same results)")
+    ap.add_argument("--early-termination", type=int, default=0,
+                    help="quiet orders after which the sequence stops (0: all L terms)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -324,6 +505,7 @@ def main():
     work = nnzvec_per_step(A, n, L, sym)
     stream = torch.cuda.Stream()
     ctx = wr.wr_create(local, stream.cuda_stream)
+    apply_options(wr, ctx, args)
     params = wr.make_params(p, m, n, cfg["seed"],
                             projection=wr.WR_PROJ_SYMMETRIC if sym else wr.WR_PROJ_GENERIC)
     d_rp = torch.from_numpy(A.rowptr.astype(np.int64)).to("cuda")
@@ -429,6 +611,7 @@ def main():
                        "projection": args.projection, "applications": applications(L, sym),
                        "per_rank": "independent matrix per rank (seeded by rank), no collective on the data path",
                        "l2": "working set below L2; a 256 MB buffer is written between timed steps",
+                       "options": options_config(args),
                        "phases_ms": phases},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -213,6 +213,16 @@ void wr_matrix_free(wr_matrix *mat);
  * matrix.  The reduction is a host pass (a matrix given in device memory is
  * copied to the host for it). */
 wr_status wr_set_chain_reduction(wr_ctx *ctx, int32_t on);
+/* Locality order at read time (off by default; the paper's conclusion names
+ * an adapted reordering for clustering the products): loads through this
+ * context renumber the rows and the columns by decreasing entry count, so
+ * that the block rows the SpMM gathers most often sit next to each other.
+ * Everything stays in the loaded order at the boundary: X, Y, D1, D2 are
+ * drawn at the loaded indices, so sequences, generators and ranks are the
+ * same with and without it, and the black-box calls take and return blocks
+ * in the loaded row order.  A host pass (after the chain reduction, when
+ * both are on). */
+wr_status wr_set_locality_order(wr_ctx *ctx, int32_t on);
 /* The input's size and the pivots the chain reduction took (0 without it). */
 wr_status wr_matrix_reduction(const wr_matrix *mat, int64_t *rows_in, int64_t *cols_in, int64_t *rank_offset);
 /* The same reduction on host arrays, without a device: writes the reduced

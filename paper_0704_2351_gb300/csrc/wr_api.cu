@@ -151,6 +151,10 @@ wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r) {
     r.gram = r.symmetric;
     r.paired = false;
     r.nvs = r.nv;
+    const uint32_t *mr = mat->map_rows.ptr ? mat->map_rows.as<uint32_t>() : nullptr;
+    const uint32_t *mc = mat->map_cols.ptr ? mat->map_cols.as<uint32_t>() : nullptr;
+    r.nmap = side == WR_SIDE_COLS ? mc : mr;
+    r.mmap = side == WR_SIDE_COLS ? mr : mc;
     return WR_OK;
 }
 
@@ -319,23 +323,54 @@ static wr_status load_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nn
 static wr_status load_host_plain(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
                                  const int32_t *colidx, const int32_t *vals, wr_matrix **out);
 
-// Chain reduction at read time: reduce on the host, load the reduced matrix.
-static wr_status load_reduced(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
-                              const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
-    ReducedCsr r;
-    WR_TRY(chain_reduce_host(rows, cols, rowptr, colidx, vals, r));
-    WR_TRY(load_host_plain(ctx, r.rows, r.cols, r.rowptr.data(), r.colidx.data(), r.vals.data(), out));
-    (*out)->rows_in = rows;
-    (*out)->cols_in = cols;
-    (*out)->rank_offset = r.rank_offset;
+static wr_status upload_map(wr_ctx *ctx, const std::vector<int32_t> &m, DevBuf &dst) {
+    WR_TRY(dev_alloc(ctx, dst, sizeof(uint32_t) * std::max<size_t>(m.size(), 1)));
+    if (!m.empty())
+        WR_CUDA(cudaMemcpyAsync(dst.ptr, m.data(), sizeof(uint32_t) * m.size(), cudaMemcpyHostToDevice, ctx->stream));
+    WR_CUDA(cudaStreamSynchronize(ctx->stream));
     return WR_OK;
+}
+
+// Read-time passes on the host: the chain reduction, then the locality
+// order; the matrix held is the result, with the reduction's rank offset and
+// the order's index maps.
+static wr_status load_prepared(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
+                               const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
+    ReducedCsr red, ord;
+    int64_t R = rows, C = cols, off = 0;
+    const int64_t *rp = rowptr;
+    const int32_t *ci = colidx, *va = vals;
+    if (ctx->chain_reduce) {
+        WR_TRY(chain_reduce_host(rows, cols, rowptr, colidx, vals, red));
+        R = red.rows, C = red.cols, off = red.rank_offset;
+        rp = red.rowptr.data(), ci = red.colidx.data(), va = red.vals.data();
+    }
+    if (ctx->reorder) {
+        WR_TRY(locality_order_host(R, C, rp, ci, va, ord));
+        rp = ord.rowptr.data(), ci = ord.colidx.data(), va = ord.vals.data();
+    }
+    WR_TRY(load_host_plain(ctx, R, C, rp, ci, va, out));
+    wr_matrix *m = *out;
+    m->rows_in = rows;
+    m->cols_in = cols;
+    m->rank_offset = off;
+    wr_status st = WR_OK;
+    if (ctx->reorder) {
+        st = upload_map(ctx, ord.row_of, m->map_rows);
+        if (st == WR_OK) st = upload_map(ctx, ord.col_of, m->map_cols);
+    }
+    if (st != WR_OK) {
+        delete m;
+        *out = nullptr;
+    }
+    return st;
 }
 
 extern "C" wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz,
                                                const int64_t *d_rowptr, const int32_t *d_colidx,
                                                const int32_t *d_vals, wr_matrix **out) {
-    if (ctx && ctx->chain_reduce) {
-        // the reduction is a host pass: bring the CSR over first
+    if (ctx && (ctx->chain_reduce || ctx->reorder)) {
+        // the read-time passes run on the host: bring the CSR over first
         if (!out || !d_rowptr) return fail(WR_EINVAL, "null argument");
         if (rows < 0 || cols < 0 || nnz < 0) return fail(WR_EINVAL, "negative size");
         if (nnz > 0 && (!d_colidx || !d_vals)) return fail(WR_EINVAL, "null column or value array");
@@ -349,7 +384,7 @@ extern "C" wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_
         }
         WR_CUDA(cudaStreamSynchronize(ctx->stream));
         if (rp[rows] != nnz) return fail(WR_EINVAL, "rowptr[rows] must equal nnz");
-        return load_reduced(ctx, rows, cols, rp.data(), ci.data(), va.data(), out);
+        return load_prepared(ctx, rows, cols, rp.data(), ci.data(), va.data(), out);
     }
     WR_TRY(load_device(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, out));
     (*out)->rows_in = rows;
@@ -359,7 +394,7 @@ extern "C" wr_status wr_matrix_load_csr_device(wr_ctx *ctx, int64_t rows, int64_
 
 extern "C" wr_status wr_matrix_load_csr(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *rowptr,
                                         const int32_t *colidx, const int32_t *vals, wr_matrix **out) {
-    if (ctx && ctx->chain_reduce) return load_reduced(ctx, rows, cols, rowptr, colidx, vals, out);
+    if (ctx && (ctx->chain_reduce || ctx->reorder)) return load_prepared(ctx, rows, cols, rowptr, colidx, vals, out);
     WR_TRY(load_host_plain(ctx, rows, cols, rowptr, colidx, vals, out));
     (*out)->rows_in = rows;
     (*out)->cols_in = cols;
@@ -384,6 +419,12 @@ static wr_status load_host_plain(wr_ctx *ctx, int64_t rows, int64_t cols, const 
         WR_CUDA(cudaMemcpyAsync(va.ptr, vals, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, ctx->stream));
     }
     return load_device(ctx, rows, cols, nnz, rp.as<int64_t>(), ci.as<int32_t>(), va.as<int32_t>(), out);
+}
+
+extern "C" wr_status wr_set_locality_order(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->reorder = on != 0;
+    return WR_OK;
 }
 
 extern "C" wr_status wr_set_chain_reduction(wr_ctx *ctx, int32_t on) {
@@ -431,6 +472,7 @@ void copy_settings(const wr_ctx *parent, wr_ctx *c) {
     c->pipeline = parent->pipeline;
     c->early_term = parent->early_term;
     c->chain_reduce = parent->chain_reduce;
+    c->reorder = parent->reorder;
     c->sigma_chunk = parent->sigma_chunk;
     c->sigma_leaf = parent->sigma_leaf;
     c->alloc_fn = parent->alloc_fn;

@@ -348,6 +348,7 @@ struct wr_ctx {
     bool pipeline = true;   // wr_rank: the sigma-basis trails the sequence on a second stream
     int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
     bool chain_reduce = false; // matrix loads: remove unit singleton rows/columns and empty ones
+    bool reorder = false;      // matrix loads: renumber rows and columns by decreasing degree
     wr_ctx *aux = nullptr;  // child context (own stream) that runs the trailing sigma-basis
     cudaStream_t seq_stream = nullptr; // high-priority stream of the pipelined sequence (lazy)
     wr::SeqFeed *feed = nullptr; // set on a child context while it consumes a sequence in flight
@@ -363,6 +364,10 @@ struct wr_matrix {
     // chain reduction at load: the matrix held is the reduced one, of the
     // rows_in x cols_in input; rank(input) = rank_offset + rank(held)
     int64_t rows_in = 0, cols_in = 0, rank_offset = 0;
+    // locality order: layout row i is row map_rows[i] of the matrix as
+    // loaded (after any chain reduction), column j is column map_cols[j];
+    // empty when the matrix keeps its order
+    wr::DevBuf map_rows, map_cols;
     wr::Sell a;    // rows of A
     wr::Sell at;   // rows of A^T
     // SpMM residues per lane tuned for [layout a / at][log2 block width] (0: not yet)
@@ -392,6 +397,10 @@ struct ReducedCsr {
 };
 wr_status chain_reduce_host(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
                             const int32_t *vals, ReducedCsr &out);
+// Locality order (wr_reduce.cu): rows and columns renumbered by decreasing
+// entry count (ties by index); out.row_of / col_of map back, rank_offset = 0.
+wr_status locality_order_host(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
+                              const int32_t *vals, ReducedCsr &out);
 
 // format (wr_format.cu)
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
@@ -452,6 +461,9 @@ struct Resolved {
     // terms per application (cross Gram products); nvs = the SpMM width
     bool paired = false;
     int nvs = 0;
+    // locality-ordered matrix: loaded-order index of each layout row of the
+    // N-space and of the other space (nullptr: identity)
+    const uint32_t *nmap = nullptr, *mmap = nullptr;
 };
 wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r);
 wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,

@@ -1,5 +1,7 @@
-// Chain-reduction pre-pass at read time (Section 2.6.4 "Chain Reductions").
+// Read-time passes on the host: the chain reduction (Section 2.6.4 "Chain
+// Reductions") and the locality order.
 //
+// Chain reduction.
 // A row whose only nonzero entry is lambda at column b (a free face when
 // lambda = +-1) is removed together with column b: Gaussian elimination on
 // that pivot changes nothing else (the paper's Eq. for the reduced
@@ -149,6 +151,54 @@ wr_status chain_reduce_host(int64_t rows, int64_t cols, const int64_t *rowptr, c
     }
     out.rows = (int64_t)out.row_of.size();
     out.cols = nc;
+    return WR_OK;
+}
+
+// Locality order (Section 4's "adapted reordering technique"): rows and
+// columns renumbered by decreasing entry count, ties by index.  The SpMM
+// gathers a block row per entry; in power-law matrices a few columns (and
+// the dependent rows) carry most entries, and this packs their block rows
+// next to each other, so that the hot ones share cache lines and stay in L1.
+wr_status locality_order_host(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
+                              const int32_t *vals, ReducedCsr &out) {
+    if (rows < 0 || cols < 0) return fail(WR_EINVAL, "negative size");
+    if (!rowptr) return fail(WR_EINVAL, "null row pointer array");
+    const int64_t nnz = rowptr[rows];
+    if (nnz > 0 && (!colidx || !vals)) return fail(WR_EINVAL, "null column or value array");
+    for (int64_t e = 0; e < nnz; e++)
+        if (colidx[e] < 0 || colidx[e] >= cols) return fail(WR_EINVAL, "column index out of range");
+    std::vector<int64_t> cdeg(cols, 0);
+    for (int64_t e = 0; e < nnz; e++) cdeg[colidx[e]]++;
+    out.rows_in = out.rows = rows;
+    out.cols_in = out.cols = cols;
+    out.rank_offset = 0;
+    out.row_of.resize(rows);
+    out.col_of.resize(cols);
+    for (int64_t i = 0; i < rows; i++) out.row_of[i] = (int32_t)i;
+    for (int64_t j = 0; j < cols; j++) out.col_of[j] = (int32_t)j;
+    std::stable_sort(out.row_of.begin(), out.row_of.end(), [&](int32_t a, int32_t b) {
+        return rowptr[a + 1] - rowptr[a] > rowptr[b + 1] - rowptr[b];
+    });
+    std::stable_sort(out.col_of.begin(), out.col_of.end(), [&](int32_t a, int32_t b) { return cdeg[a] > cdeg[b]; });
+    std::vector<int32_t> cnew(cols);
+    for (int64_t j = 0; j < cols; j++) cnew[out.col_of[j]] = (int32_t)j;
+    out.rowptr.assign(rows + 1, 0);
+    out.colidx.resize(nnz);
+    out.vals.resize(nnz);
+    std::vector<std::pair<int32_t, int32_t>> row;
+    int64_t w = 0;
+    for (int64_t i = 0; i < rows; i++) {
+        const int32_t g = out.row_of[i];
+        row.clear();
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; e++) row.emplace_back(cnew[colidx[e]], vals[e]);
+        std::sort(row.begin(), row.end());
+        for (const auto &x : row) {
+            out.colidx[w] = x.first;
+            out.vals[w] = x.second;
+            w++;
+        }
+        out.rowptr[i + 1] = w;
+    }
     return WR_OK;
 }
 

@@ -340,10 +340,17 @@ __global__ void k_reduce_seq(int64_t count, const unsigned long long *__restrict
 }
 
 // random draws (tags: X 1, Y 2, D1 3, D2 4)
+// map (locality-ordered matrix): entry i of the layout is index map[i] of
+// the matrix as loaded, and the draw takes that index, so the sequence does
+// not depend on the order (X^T A~^i Y is invariant under a simultaneous
+// permutation of A~'s rows and columns, X and Y)
 __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t p,
-                              uint32_t *__restrict__ out) {
+                              uint32_t *__restrict__ out, const uint32_t *__restrict__ map) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < len) out[i] = (uint32_t)(1 + stream_hash(seed, tag, (uint64_t)i) % (uint64_t)(p - 1));
+    if (i < len) {
+        const uint64_t gi = map ? (uint64_t)map[i] : (uint64_t)i;
+        out[i] = (uint32_t)(1 + stream_hash(seed, tag, gi) % (uint64_t)(p - 1));
+    }
 }
 
 // T0 = D1 Y (padded to nv columns with zeros; columns ycol0.. of a Y with
@@ -352,22 +359,24 @@ __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t
 // over the whole Y: S_2k = V_k^T V_k with T_k = D1 V_k; Montgomery form).
 __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64_t xtag, int xwidth, int ystride,
                           int ycol0, int gram, int paired, const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
-                          uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, ModP mp) {
+                          uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, const uint32_t *__restrict__ nmap,
+                          ModP mp) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const uint64_t gi = nmap ? (uint64_t)nmap[i] : (uint64_t)i;  // index of the draws
     const uint32_t d = d1[i];
     const uint32_t dinv = invm(d, mp);
     d1sq[i] = mulm(d, d, mp);
     const int tw = paired ? 2 * nv : nv, yo = paired ? nv : 0;
     for (int b = 0; b < nv; b++) {
         uint32_t yv = 0;
-        if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, (uint64_t)i * ystride + ycol0 + b) % mp.p);
+        if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, gi * ystride + ycol0 + b) % mp.p);
         t0[i * tw + yo + b] = mulm(d, yv, mp);
     }
     if (paired) {  // D1 X beside D1 Y, weights D1^{-2} for the cross Gram products
         for (int a = 0; a < nv; a++) {
             uint32_t xv = 0;
-            if (a < m) xv = (uint32_t)(stream_hash(seed, xtag, (uint64_t)i * xwidth + a) % mp.p);
+            if (a < m) xv = (uint32_t)(stream_hash(seed, xtag, gi * xwidth + a) % mp.p);
             t0[i * tw + a] = mulm(d, xv, mp);
         }
         xh[i] = to_mont(mulm(dinv, dinv, mp), mp);
@@ -378,7 +387,7 @@ __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64
         return;
     }
     for (int a = 0; a < m; a++) {
-        uint32_t xv = (uint32_t)(stream_hash(seed, xtag, (uint64_t)i * xwidth + a) % mp.p);
+        uint32_t xv = (uint32_t)(stream_hash(seed, xtag, gi * xwidth + a) % mp.p);
         xh[i * m + a] = mulm(dinv, xv, mp);
     }
 }
@@ -391,22 +400,27 @@ __global__ void k_inv_diag(int64_t len, const uint32_t *__restrict__ d, uint32_t
 }
 
 // out (N x nv, padded) = D1 in (N x width)
+// the caller's block is in the matrix's loaded order: row r of the layout
+// reads (and writes back) row nmap[r] of it
 __global__ void k_scale_pad(int64_t N, int width, int nv, const uint32_t *__restrict__ in,
-                            const uint32_t *__restrict__ d1, uint32_t *__restrict__ out, ModP mp) {
+                            const uint32_t *__restrict__ d1, uint32_t *__restrict__ out,
+                            const uint32_t *__restrict__ nmap, ModP mp) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * nv) return;
     int64_t r = i / nv;
     int b = (int)(i % nv);
-    out[i] = b < width ? mulm(d1[r], in[r * width + b], mp) : 0;
+    const int64_t g = nmap ? (int64_t)nmap[r] : r;
+    out[i] = b < width ? mulm(d1[r], in[g * width + b], mp) : 0;
 }
 
 __global__ void k_unpad(int64_t N, int width, int nv, const uint32_t *__restrict__ in,
-                        uint32_t *__restrict__ out) {
+                        uint32_t *__restrict__ out, const uint32_t *__restrict__ nmap) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * width) return;
     int64_t r = i / width;
     int b = (int)(i % width);
-    out[i] = in[r * nv + b];
+    const int64_t g = nmap ? (int64_t)nmap[r] : r;
+    out[g * width + b] = in[r * nv + b];
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -620,18 +634,18 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
     WR_CUDA(cudaMemsetAsync(st.acc2.ptr, 0, st.acc2.bytes, s));
     WR_CUDA(cudaMemsetAsync(st.counter.ptr, 0, sizeof(int), s));
     if (r.N > 0) {
-        k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, st.D1.as<uint32_t>());
+        k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, st.D1.as<uint32_t>(), r.nmap);
         WR_LAUNCHED(ctx);
     }
     if (r.M > 0) {
-        k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, st.D2.as<uint32_t>());
+        k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, st.D2.as<uint32_t>(), r.mmap);
         WR_LAUNCHED(ctx);
     }
     if (want_projection && r.N > 0) {
         k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, r.nv, r.seed, r.xtag, r.xwidth, r.ystride,
                                                       r.ycol0, r.gram ? 1 : 0, r.paired ? 1 : 0, st.D1.as<uint32_t>(),
                                                       st.T.as<uint32_t>(), st.xh.as<uint32_t>(),
-                                                      st.d1sq.as<uint32_t>(), st.mp);
+                                                      st.d1sq.as<uint32_t>(), r.nmap, st.mp);
         WR_LAUNCHED(ctx);
     }
     if (want_projection && (r.gram || r.paired) && r.M > 0) {
@@ -863,7 +877,8 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
     cudaStream_t s = ctx->stream;
     if (r.N > 0) {
         k_scale_pad<<<blocks_for(r.N * r.nv, 256), 256, 0, s>>>(r.N, (int)width, r.nv, d_in,
-                                                               st.D1.as<uint32_t>(), st.T.as<uint32_t>(), st.mp);
+                                                               st.D1.as<uint32_t>(), st.T.as<uint32_t>(), r.nmap,
+                                                               st.mp);
         WR_LAUNCHED(ctx);
     }
     SellView f = view(*st.first), sc = view(*st.second);
@@ -873,7 +888,8 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
     WR_TRY(launch_spmm(ctx, r.nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.D1.as<uint32_t>(),
                        st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (r.N > 0) {
-        k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out);
+        k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out,
+                                                             r.nmap);
         WR_LAUNCHED(ctx);
     }
     WR_CUDA(cudaStreamSynchronize(s));
@@ -963,21 +979,21 @@ wr_status blackbox_apply_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_par
     if (nA1) WR_CUDA(cudaMemsetAsync(acc1, 0, nA1, s));
     if (nA2) WR_CUDA(cudaMemsetAsync(acc2, 0, nA2, s));
     if (r.N > 0) {
-        k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, D1);
+        k_derive_diag<<<blocks_for(r.N, 256), 256, 0, s>>>(r.seed, TAG_D1, r.N, r.p, D1, r.nmap);
         WR_LAUNCHED(ctx);
     }
     if (r.M > 0) {
-        k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, D2);
+        k_derive_diag<<<blocks_for(r.M, 256), 256, 0, s>>>(r.seed, TAG_D2, r.M, r.p, D2, r.mmap);
         WR_LAUNCHED(ctx);
     }
     if (r.N > 0) {
-        k_scale_pad<<<blocks_for(r.N * nv, 256), 256, 0, s>>>(r.N, (int)width, nv, d_in, D1, T, mp);
+        k_scale_pad<<<blocks_for(r.N * nv, 256), 256, 0, s>>>(r.N, (int)width, nv, d_in, D1, T, r.nmap, mp);
         WR_LAUNCHED(ctx);
     }
     WR_TRY(launch_spmm(ctx, nv, view(*first), T, Wb, D2, acc1, mp, nullptr));
     WR_TRY(launch_spmm(ctx, nv, view(*second), Wb, T, D1, acc2, mp, nullptr));
     if (r.N > 0) {
-        k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, nv, T, d_out);
+        k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, nv, T, d_out, r.nmap);
         WR_LAUNCHED(ctx);
     }
     WR_CUDA(cudaStreamSynchronize(s));

@@ -79,6 +79,7 @@ _sig = {
     "wr_set_pipeline": ([vp, i32], ctypes.c_int),
     "wr_set_early_termination": ([vp, i64], ctypes.c_int),
     "wr_set_chain_reduction": ([vp, i32], ctypes.c_int),
+    "wr_set_locality_order": ([vp, i32], ctypes.c_int),
     "wr_matrix_reduction": ([vp, P(i64), P(i64), P(i64)], ctypes.c_int),
     "wr_chain_reduce_csr": ([i64, i64, vp, vp, vp, P(i64), P(i64), vp, vp, vp, vp, vp, P(i64)], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
@@ -258,6 +259,10 @@ def wr_set_early_termination(ctx: int, orders: int) -> None:
 
 def wr_set_chain_reduction(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_chain_reduction(vp(ctx), 1 if on else 0))
+
+
+def wr_set_locality_order(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_locality_order(vp(ctx), 1 if on else 0))
 
 
 def wr_matrix_reduction(mat: int) -> dict:

@@ -342,6 +342,48 @@ def test_rank_with_chain_reduction(wr, ctx):
     assert oracle.rank_sparse(mats[0], p) == mats[0].rank
 
 
+def test_locality_order_changes_nothing_at_the_boundary(wr, ctx):
+    """Loads with the locality order renumber rows and columns by decreasing
+    entry count; X, Y, D1, D2 are drawn at the loaded indices, so sequences
+    (generic, paired, symmetric, both sides, column slabs), black-box
+    applications (allocating and allocation-free) and ranks equal the
+    oracle's and those of the unordered load."""
+    p = 1073741789
+    A = heavy_matrix(1200, 1000, seed=71, heavy=3, heavy_len=600)
+    P = synth.config1(scale=0.02)
+    try:
+        wr.wr_set_locality_order(ctx, True)
+        for side in [0, 1]:
+            for (m, n, sym) in [(4, 4, False), (3, 5, False), (8, 8, True), (1, 1, False)]:
+                st = oracle.Setup(A, p, m, n, seed=13, side=side, symmetric=sym)
+                S_ref = oracle.sequence(A, st, 90)
+                assert np.array_equal(gpu_sequence(wr, ctx, A, p, m, n, 13, 90, side=side, symmetric=sym), S_ref)
+            N = A.cols if side == 0 else A.rows
+            Mo = A.rows if side == 0 else A.cols
+            v = np.random.default_rng(side).integers(0, p, size=(N, 8)).astype(np.uint32)
+            d1 = oracle.derive_diag(21, oracle.TAG_D1, N, p)
+            d2 = oracle.derive_diag(21, oracle.TAG_D2, Mo, p)
+            ref = oracle.blackbox_apply(A, p, side, d1, d2, v)
+            mat = load(wr, ctx, A)
+            prm = wr.make_params(p, 1, 8, 21, side=side)
+            dout = torch.empty((N, 8), dtype=torch.int32, device="cuda")
+            wr.wr_blackbox_apply_device(ctx, mat, prm, to_dev(v), dout, 8)
+            assert np.array_equal(from_dev(dout), ref)
+            dout2 = torch.empty((N, 8), dtype=torch.int32, device="cuda")
+            wr.wr_blackbox_apply_device_noalloc(ctx, mat, prm, to_dev(v), dout2, 8)
+            assert np.array_equal(from_dev(dout2), ref)
+            wr.wr_matrix_free(mat)
+        g = gpu_rank(wr, ctx, P, p, 8, 8, 5, want=3)
+        wr.wr_set_chain_reduction(ctx, True)
+        g2 = gpu_rank(wr, ctx, P, p, 8, 8, 5)
+    finally:
+        wr.wr_set_locality_order(ctx, False)
+        wr.wr_set_chain_reduction(ctx, False)
+    ref = oracle.rank_wiedemann(P, p, 8, 8, seed=5)
+    assert g["rank"] == ref["rank"] == P.rank == g2["rank"]
+    assert np.array_equal(g["S"], ref["S"]) and np.array_equal(g["F"], ref["F"])
+
+
 @pytest.mark.parametrize("m", [1, 4, 8])
 def test_rank_planted_symmetric(wr, ctx, m):
     p = 1073741789
