@@ -1,19 +1,25 @@
 """Benchmark of the block Wiedemann rank path on GB300.
 
 A step is one pass of the whole path over one synthetic matrix: CSR ingest
-and SELL-C-sigma layout on the device, preconditioner set-up, the L - 1
-black-box applications with their projections, the sigma-basis and the rank
-readout.  The workload is the 200,000 x 180,000 power-law matrix of planted
-rank 170,000, block 8 x 8, p = 1073741789 (L = 45,002 terms).
+and SELL-C-sigma layout on the device, preconditioner set-up, the black-box
+applications with their projections (L = 45,002 terms), the sigma-basis
+(trailing the sequence on a second stream) and the rank readout.  The
+workload is the 200,000 x 180,000 power-law matrix of planted rank 170,000,
+block 8 x 8, p = 1073741789.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wr|reference]
                     [--projection generic|symmetric]
+                    [--chain-reduction] [--locality-order] [--early-termination ORDERS]
+                    [--workload single|batch|serve] [--only-blackbox | --only-sigma]
 
 One JSON line on rank 0.  value = SpMM nnz*vec processed per second over the
-whole step (2 passes x nnz x n per black-box application); ms_per_step = time
-to rank.  The generic projection (independent X) applies the black box L - 1
-times; the symmetric one (X = Y) takes two terms per application, so it
-applies it ceil((L - 1) / 2) times and its value counts only those.
+whole step (2 passes x nnz x block columns per black-box application);
+ms_per_step = time to rank.  The generic projection (independent X, m = n)
+carries X and Y side by side: ceil((L - 1) / 2) applications to a block of
+width 2n, the same nnz*vec as L - 1 applications to Y alone, which is what
+value counts.  The symmetric one (X = Y) takes two terms per application of
+width n, so it applies the black box ceil((L - 1) / 2) times and its value
+counts only those.
 --impl reference times the CPU oracle on the host cores on a bounded sample
 of the same workload (first terms of the sequence).
 """
@@ -37,9 +43,9 @@ METRIC = "mod-p SpMM nnz·vec/s, %HBM peak; batched/served vs plain time-to-rank
 # DRAM bytes (read + write) per k_spmm launch in the warm loop, from one ncu
 # capture of this kernel: dram__bytes_read.sum + dram__bytes_write.sum, with
 # --cache-control none, launches 2000-2019 of
-# `python bench.py --steps 1 --warmup 0 --no-cpu-baseline` (both passes
-# averaged; profiles/spmm_traffic_config1.md).
-SPMM_TRAFFIC_PER_LAUNCH = 0.58e6
+# `python bench.py --steps 1 --warmup 0 --no-cpu-baseline` (both passes of the
+# paired width-16 block averaged; profiles/spmm_traffic_config1.md).
+SPMM_TRAFFIC_PER_LAUNCH = 4.0e6
 UNIT = "nnz*vec/s"
 
 
@@ -599,8 +605,9 @@ def main():
         ach = per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak if peak else 6800.0, "unit": "GB/s",
                 "frac": ach / (peak if peak else 6800.0), "traffic": SPMM_TRAFFIC_PER_LAUNCH,
-                "traffic_note": "warm L2: the working set stays resident, so DRAM traffic is far below the "
-                                "algorithmic bytes; the pass is bound by random 32-byte gathers from L2",
+                "traffic_note": "warm L2: the blocks and layouts stay resident beside the trailing sigma-basis "
+                                "state, so DRAM traffic (4.0 MB) is far below the algorithmic bytes; the pass "
+                                "is bound by random 64-byte gathers from L2",
                 "peak_source": "measured" if peak else "fallback",
                 "kernel": "k_spmm (both passes of the black box)", "avg_launch_us": avg_s * 1e6,
                 "bytes_per_launch": per_launch, "sampled_launches": spmm_launches}
@@ -608,7 +615,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": cfg["name"], "block": [m, n], "prime": p, "seq_len": L,
-                       "projection": args.projection, "applications": applications(L, sym),
+                       "projection": args.projection,
+                       "applications": (L // 2) if (sym or m == n) else L - 1,
+                       "spmm_block_width": n if (sym or m != n) else 2 * n,
                        "per_rank": "independent matrix per rank (seeded by rank), no collective on the data path",
                        "l2": "working set below L2; a 256 MB buffer is written between timed steps",
                        "options": options_config(args),
