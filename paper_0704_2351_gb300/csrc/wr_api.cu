@@ -576,7 +576,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
                     sst = sigma_basis(aux, dS.as<uint32_t>(), L, r.m, r.n, r.p, dP.as<uint32_t>(),
                                       ddeg.as<int32_t>(), Dcap);
                 if (sst == WR_OK) {
-                    ce = cudaStreamSynchronize(aux->stream);
+                    ce = sync_stream_blocking(aux->stream);
                     if (ce != cudaSuccess) sst = cuda_fail(ce, "cudaStreamSynchronize");
                 }
                 t_sig1 = std::chrono::steady_clock::now();

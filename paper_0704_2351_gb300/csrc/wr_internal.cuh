@@ -21,6 +21,22 @@ void set_error(const std::string &msg);
 wr_status fail(wr_status st, const std::string &msg);
 wr_status cuda_fail(cudaError_t e, const char *what);
 
+// Event flags for host waits: the waiting thread sleeps instead of spinning,
+// since the pipelined and batched paths have many host threads waiting at
+// once (two per job) and spinning ones would take the cores that launch work.
+constexpr unsigned WAIT_EVENT_FLAGS = cudaEventBlockingSync | cudaEventDisableTiming;
+
+// Wait, asleep, for everything queued on s so far.
+inline cudaError_t sync_stream_blocking(cudaStream_t s) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, WAIT_EVENT_FLAGS);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev);
+    cudaEventDestroy(ev);
+    return e;
+}
+
 #define WR_CUDA(call)                                              \
     do {                                                           \
         cudaError_t e_ = (call);                                   \

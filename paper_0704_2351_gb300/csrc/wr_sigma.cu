@@ -1117,7 +1117,7 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
         WR_CUDA(cudaHostAlloc((void **)&et_host, sizeof(long long) * ET_RING, cudaHostAllocMapped));
         for (int i = 0; i < ET_RING; i++) et_host[i] = -1;
         WR_CUDA(cudaHostGetDevicePointer((void **)&et_host_dev, et_host, 0));
-        for (int i = 0; i < ET_RING; i++) WR_CUDA(cudaEventCreateWithFlags(&et_ev[i], cudaEventDisableTiming));
+        for (int i = 0; i < ET_RING; i++) WR_CUDA(cudaEventCreateWithFlags(&et_ev[i], WAIT_EVENT_FLAGS));
         WR_TRY(dev_alloc(ctx, et_count, sizeof(long long)));
         WR_CUDA(cudaMemsetAsync(et_count.ptr, 0, sizeof(long long), s));
     }
@@ -1209,10 +1209,10 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
     if (dmax_out) {
         int h = 0;
         WR_CUDA(cudaMemcpyAsync(&h, dmax.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
-        WR_CUDA(cudaStreamSynchronize(s));
+        WR_CUDA(sync_stream_blocking(s));
         *dmax_out = std::min<int64_t>(std::max(h, 0), Dbound);
     }
-    WR_CUDA(cudaStreamSynchronize(s));
+    WR_CUDA(sync_stream_blocking(s));  // (trailing a sequence: as long as the sequence)
     return WR_OK;
 }
 

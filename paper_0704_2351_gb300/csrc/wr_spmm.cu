@@ -730,7 +730,7 @@ static wr_status publish_terms(wr_ctx *ctx, SeqState &st, int64_t from, int64_t 
         WR_LAUNCHED(ctx);
     }
     cudaEvent_t ev;
-    WR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    WR_CUDA(cudaEventCreateWithFlags(&ev, WAIT_EVENT_FLAGS));
     cudaError_t ce = cudaEventRecord(ev, ctx->stream);
     {
         std::lock_guard<std::mutex> lk(feed->mu);
@@ -749,7 +749,7 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     cudaEvent_t e0, e1, e2;
     WR_CUDA(cudaEventCreate(&e0));
     WR_CUDA(cudaEventCreate(&e1));
-    WR_CUDA(cudaEventCreate(&e2));
+    WR_CUDA(cudaEventCreateWithFlags(&e2, cudaEventBlockingSync));  // waited on below, asleep
     WR_CUDA(cudaEventRecord(e0, s));
     SeqState st;
     WR_TRY(seq_setup(ctx, mat, r, st, true));
