@@ -16,6 +16,9 @@ paper defines it:
 * mbasis()              sigma-basis of [S(x) | -I]               (Section 2.4 "sigma-basis computations")
 * generator()           minimal right matrix generator F          (Section 2.5 step 3)
 * rank_readout()        r = deg det F - codeg det F              (Section 2.5 step 4)
+* early_termination_point()  first order count after which the generator
+                        candidates have been quiet for `quiet` orders (Section 4's early
+                        termination; the criterion is a reading, stated in the function)
 * rank_dense/sparse()   rank_p by Gaussian elimination (definition of the rank)
 * berlekamp_massey()    scalar minimal polynomial                (Section 1.2, Wiedemann)
 
@@ -408,6 +411,54 @@ def rank_readout(M: np.ndarray, deg: np.ndarray, n: int, p: int) -> dict:
     deg_det = sd - vP
     return dict(rank=deg_det - vF, deg_det=deg_det, codeg=vF, sum_delta=sd, vP=vP,
                 cols=cols, delta=delta, F=F, P=P)
+
+
+def early_termination_point(S: np.ndarray, p: int, chunk: int, quiet: int) -> Optional[int]:
+    """Early termination (Section 4 mentions it; Table tab:r-time's 2 + 2r/p
+    iterations say how many terms the rank needs; no criterion is given).
+    Reading: the orders are taken in chunks of `chunk`; before the chunk
+    [k0, k0 + b), the generator candidates are the n columns of least
+    (shifted degree, index) of the order-k0 sigma-basis of [S | -I_m]; the
+    chunk is quiet when every candidate has shifted degree <= k0 and zero
+    residual [S(x) | -I_m] col mod p at every order of the chunk.  Quiet
+    orders are counted over consecutive quiet chunks.  Returns the order count
+    k0 + b at which the count first reaches `quiet` (the generator is then
+    taken as final), or None if it never does within the L terms of S."""
+    S = _c(S, np.uint32)
+    L, m, n = S.shape
+    q = m + n
+    So = S.astype(object)
+    count = 0
+    for k0 in range(0, L, chunk):
+        b = min(chunk, L - k0)
+        if k0 == 0:
+            M = np.zeros((1, q, q), dtype=np.uint32)
+            for c in range(q):
+                M[0, c, c] = 1
+            deg = np.array([0] * n + [1] * m, dtype=np.int32)
+        else:
+            M, deg = mbasis(S[:k0], p)
+        cand = sorted(range(q), key=lambda c: (int(deg[c]), c))[:n]
+        quiet_chunk = all(int(deg[c]) <= k0 for c in cand)
+        if quiet_chunk:
+            Mo = M.astype(object)
+            for c in cand:
+                for k in range(k0, k0 + b):
+                    # order-k coefficient of S(x) P_c(x) - Q_c(x)
+                    r = np.zeros(m, dtype=object)
+                    for t in range(min(k, Mo.shape[0] - 1) + 1):
+                        r = r + So[k - t].dot(Mo[t, :n, c])
+                    if k < Mo.shape[0]:
+                        r = r - Mo[k, n:, c]
+                    if any(int(v) % p for v in r):
+                        quiet_chunk = False
+                        break
+                if not quiet_chunk:
+                    break
+        count = count + b if quiet_chunk else 0
+        if count >= quiet:
+            return k0 + b
+    return None
 
 
 def rank_wiedemann(A, p: int, m: int, n: int, seed: int, side: Optional[int] = None,

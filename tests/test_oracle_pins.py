@@ -517,3 +517,60 @@ def test_blackbox_apply_rows_equals_full_application(side):
     full = oracle.blackbox_apply(A, p, side, d1, d2, v)
     rows = rng.choice(N, 25, replace=False)
     assert np.array_equal(oracle.blackbox_apply_rows(A, p, side, d1, d2, v, rows), full[rows])
+
+
+# ---------------------------------------------------------------------------
+# early termination (reading of Section 4's remark; no GPU)
+# ---------------------------------------------------------------------------
+
+def _generator(S, p, n):
+    M, deg = oracle.mbasis(S, p)
+    return oracle.rank_readout(M, deg, n, p)
+
+
+@pytest.mark.parametrize("m,R,C,r,seed", [(1, 70, 60, 25, 1), (2, 90, 80, 30, 2), (4, 160, 150, 50, 3),
+                                          (3, 120, 110, 70, 4), (2, 100, 90, 89, 5)])
+def test_early_termination_gives_the_full_generator(m, R, C, r, seed):
+    """Stopping at the quiet point keeps the generator of all L terms bit for
+    bit: the candidates' columns are final once they annihilate the quiet
+    orders; a rank-deficient matrix reaches the point well before L (about
+    2r/m + quiet orders), a nearly full-rank one may not reach it at all."""
+    p = 1073741789
+    A = synth.planted_sparse(R, C, r, row_len=5, seed=seed)
+    st = oracle.Setup(A, p, m, m, seed=seed)
+    S = oracle.sequence(A, st)
+    L = S.shape[0]
+    k = oracle.early_termination_point(S, p, chunk=8, quiet=8)
+    if k is None:  # no room for the quiet orders before L (nearly full rank): all L terms
+        assert r > min(R, C) - 8
+        k = L
+    assert k <= L
+    full, short = _generator(S, p, m), _generator(S[:k], p, m)
+    assert short["rank"] == full["rank"] == r
+    assert np.array_equal(short["delta"], full["delta"]) and np.array_equal(short["F"], full["F"])
+    if r < min(R, C) // 2:
+        assert k < L - (min(R, C) - r) // (2 * m)
+
+
+def test_early_termination_never_stops_on_a_sequence_without_a_short_generator():
+    """A random sequence has no generator of degree below L/2 per column, so
+    no chunk of the candidates is quiet."""
+    p = 65521
+    rng = np.random.default_rng(9)
+    for m in [1, 2, 4]:
+        S = rng.integers(0, p, size=(64, m, m)).astype(np.uint32)
+        assert oracle.early_termination_point(S, p, chunk=8, quiet=8) is None
+
+
+def test_early_termination_point_is_where_a_planted_mistake_shows():
+    """A pin against a weaker criterion: counting a chunk as quiet without
+    checking the candidates' residuals would stop at the first chunks of any
+    sequence; the reading's check keeps the stop after the generator's degree."""
+    p = 1073741789
+    A = synth.planted_sparse(120, 110, 40, row_len=5, seed=12)
+    st = oracle.Setup(A, p, 2, 2, seed=12)
+    S = oracle.sequence(A, st)
+    k = oracle.early_termination_point(S, p, chunk=4, quiet=4)
+    full = _generator(S, p, 2)
+    # the generator's degree max(delta) orders at least must have been seen
+    assert k >= int(np.max(full["delta"]))
