@@ -223,6 +223,12 @@ wr_status wr_set_chain_reduction(wr_ctx *ctx, int32_t on);
  * in the loaded row order.  A host pass (after the chain reduction, when
  * both are on). */
 wr_status wr_set_locality_order(wr_ctx *ctx, int32_t on);
+/* The locality order on host arrays, without a device: the renumbered CSR
+ * (arrays sized as the input's) and each layout row's and column's input
+ * index (rows resp. cols entries).  WR_EINVAL on a malformed CSR. */
+wr_status wr_locality_order_csr(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
+                                const int32_t *vals, int64_t *out_rowptr, int32_t *out_colidx, int32_t *out_vals,
+                                int32_t *out_row_of, int32_t *out_col_of);
 /* The input's size and the pivots the chain reduction took (0 without it). */
 wr_status wr_matrix_reduction(const wr_matrix *mat, int64_t *rows_in, int64_t *cols_in, int64_t *rank_offset);
 /* The same reduction on host arrays, without a device: writes the reduced

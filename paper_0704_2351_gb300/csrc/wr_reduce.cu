@@ -227,3 +227,21 @@ extern "C" wr_status wr_chain_reduce_csr(int64_t rows, int64_t cols, const int64
     if (out_col_of && r.cols > 0) std::memcpy(out_col_of, r.col_of.data(), sizeof(int32_t) * r.cols);
     return WR_OK;
 }
+
+extern "C" wr_status wr_locality_order_csr(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
+                                           const int32_t *vals, int64_t *out_rowptr, int32_t *out_colidx,
+                                           int32_t *out_vals, int32_t *out_row_of, int32_t *out_col_of) {
+    if (!out_rowptr || !out_row_of || !out_col_of) return fail(WR_EINVAL, "null output argument");
+    ReducedCsr r;
+    WR_TRY(locality_order_host(rows, cols, rowptr, colidx, vals, r));
+    const int64_t nnz = (int64_t)r.colidx.size();
+    if (nnz > 0 && (!out_colidx || !out_vals)) return fail(WR_EINVAL, "null output column or value array");
+    std::memcpy(out_rowptr, r.rowptr.data(), sizeof(int64_t) * (rows + 1));
+    if (nnz > 0) {
+        std::memcpy(out_colidx, r.colidx.data(), sizeof(int32_t) * nnz);
+        std::memcpy(out_vals, r.vals.data(), sizeof(int32_t) * nnz);
+    }
+    if (rows > 0) std::memcpy(out_row_of, r.row_of.data(), sizeof(int32_t) * rows);
+    if (cols > 0) std::memcpy(out_col_of, r.col_of.data(), sizeof(int32_t) * cols);
+    return WR_OK;
+}

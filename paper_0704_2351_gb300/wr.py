@@ -80,6 +80,7 @@ _sig = {
     "wr_set_early_termination": ([vp, i64], ctypes.c_int),
     "wr_set_chain_reduction": ([vp, i32], ctypes.c_int),
     "wr_set_locality_order": ([vp, i32], ctypes.c_int),
+    "wr_locality_order_csr": ([i64, i64, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
     "wr_matrix_reduction": ([vp, P(i64), P(i64), P(i64)], ctypes.c_int),
     "wr_chain_reduce_csr": ([i64, i64, vp, vp, vp, P(i64), P(i64), vp, vp, vp, vp, vp, P(i64)], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
@@ -263,6 +264,24 @@ def wr_set_chain_reduction(ctx: int, on: bool) -> None:
 
 def wr_set_locality_order(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_locality_order(vp(ctx), 1 if on else 0))
+
+
+def wr_locality_order_csr(rows: int, cols: int, rowptr, colidx, vals):
+    """Host locality order (no device needed): returns (rowptr, colidx, vals,
+    row_of, col_of) of the renumbered CSR."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.int32)
+    nnz = int(rowptr[rows])
+    orp = np.zeros(rows + 1, dtype=np.int64)
+    oci = np.zeros(max(nnz, 1), dtype=np.int32)
+    ova = np.zeros(max(nnz, 1), dtype=np.int32)
+    rof = np.zeros(max(rows, 1), dtype=np.int32)
+    cof = np.zeros(max(cols, 1), dtype=np.int32)
+    _check(_lib.wr_locality_order_csr(rows, cols, vp(rowptr.ctypes.data), vp(colidx.ctypes.data),
+                                      vp(vals.ctypes.data), vp(orp.ctypes.data), vp(oci.ctypes.data),
+                                      vp(ova.ctypes.data), vp(rof.ctypes.data), vp(cof.ctypes.data)))
+    return orp, oci[:nnz].copy(), ova[:nnz].copy(), rof[:rows].copy(), cof[:cols].copy()
 
 
 def wr_matrix_reduction(mat: int) -> dict:

@@ -1,9 +1,9 @@
-"""Chain reduction at read time (Section 2.6.4): the host pass of the library
-(wr_chain_reduce_csr, no device needed) checked against the oracle's
-Gaussian elimination.  For every matrix and prime,
+"""Read-time host passes, no device needed.  Chain reduction (Section 2.6.4,
+wr_chain_reduce_csr) checked against the oracle's Gaussian elimination.  For every matrix and prime,
 rank_p(A) = rank_offset + rank_p(reduced), the reduced matrix keeps no unit
 singleton row or column and no empty one, and the remaining rows and columns
-keep their input order."""
+keep their input order.  Locality order (wr_locality_order_csr): a
+simultaneous renumbering of rows and columns by decreasing entry count."""
 import numpy as np
 import pytest
 
@@ -106,3 +106,21 @@ def test_malformed_csr_is_rejected(wr):
     with pytest.raises(wr.WrError):
         wr.wr_chain_reduce_csr(2, 2, np.array([0, 2, 1]), np.array([0, 1], dtype=np.int32),
                                np.array([1, 1], dtype=np.int32))
+
+
+def test_locality_order_is_a_degree_sorted_permutation(wr):
+    for A in _mats() + [synth.config1(scale=0.01)]:
+        rp, ci, va, rof, cof = wr.wr_locality_order_csr(A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+        assert sorted(rof) == list(range(A.rows)) and sorted(cof) == list(range(A.cols))
+        B = synth.CSR(A.rows, A.cols, rp, ci, va)
+        assert np.array_equal(B.to_dense(), A.to_dense()[np.ix_(rof, cof)])
+        rlen = np.diff(A.rowptr)[rof]
+        clen = np.bincount(A.colidx, minlength=A.cols)[cof]
+        for lens, idx in [(rlen, rof), (clen, cof)]:
+            assert np.all(np.diff(lens) <= 0), "not by decreasing entry count"
+            ties = np.diff(lens) == 0
+            assert np.all(np.diff(idx)[ties] > 0), "ties not by index"
+        # columns sorted within each row
+        for i in range(B.rows):
+            assert np.all(np.diff(ci[rp[i]:rp[i + 1]]) > 0)
+        assert oracle.rank_dense(B.to_dense(), 65521) == oracle.rank_dense(A.to_dense(), 65521)
