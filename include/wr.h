@@ -81,7 +81,8 @@ typedef struct {
 /* Phase times of the last wr_rank on a context (milliseconds, CUDA events). */
 typedef struct {
     double setup_ms;     /* X, Y, D1, D2 derivation and preconditioning set-up             */
-    double sequence_ms;  /* the L - 1 black-box applications and projections               */
+    double sequence_ms;  /* the black-box applications and projections (two terms each for */
+                         /* the symmetric projection and the generic one with m = n)     */
     double sigma_ms;     /* sigma-basis, from its start to its end (host clock)           */
     double readout_ms;   /* generator selection, det valuations, rank                     */
     double total_ms;
