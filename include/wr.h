@@ -230,6 +230,29 @@ wr_status wr_set_locality_order(wr_ctx *ctx, int32_t on);
 wr_status wr_locality_order_csr(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
                                 const int32_t *vals, int64_t *out_rowptr, int32_t *out_colidx, int32_t *out_vals,
                                 int32_t *out_row_of, int32_t *out_col_of);
+/* One matrix of a complex for wr_chain_reduce_complex: the input CSR (host
+ * arrays, read only) and the caller's output arrays, sized as the input's
+ * (rows + 1 and rowptr[rows] entries; out_row_of / out_col_of: rows / cols
+ * entries, or NULL); out_rows, out_cols and rank_offset are written. */
+typedef struct {
+    int64_t rows, cols;
+    const int64_t *rowptr;
+    const int32_t *colidx;
+    const int32_t *vals;
+    int64_t out_rows, out_cols, rank_offset;
+    int64_t *out_rowptr;
+    int32_t *out_colidx, *out_vals, *out_row_of, *out_col_of;
+} wr_csr_io;
+/* Chain reduction along a complex (Section 2.6.4, propagation from one matrix
+ * to the next), on the host.  mats[i]'s columns are mats[i+1]'s rows and
+ * mats[i] mats[i+1] = 0 over Z (checked: WR_EINVAL otherwise, and on any
+ * malformed CSR or size mismatch).  Every unit pivot at (r, c) of mats[i]
+ * removes row r and column c there (rank_offset + 1) and, in the
+ * neighbours, column r of mats[i-1] and row c of mats[i+1], lines that the
+ * complex makes zero or dependent; removals cascade.  For every i and every
+ * prime, rank(mats[i]) = rank_offset + rank(reduced mats[i]).  count = 1 is
+ * the single-matrix reduction of wr_chain_reduce_csr. */
+wr_status wr_chain_reduce_complex(int32_t count, wr_csr_io *mats);
 /* The input's size and the pivots the chain reduction took (0 without it). */
 wr_status wr_matrix_reduction(const wr_matrix *mat, int64_t *rows_in, int64_t *cols_in, int64_t *rank_offset);
 /* The same reduction on host arrays, without a device: writes the reduced

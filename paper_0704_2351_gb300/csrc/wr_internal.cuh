@@ -413,6 +413,7 @@ struct ReducedCsr {
 };
 wr_status chain_reduce_host(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
                             const int32_t *vals, ReducedCsr &out);
+wr_status chain_reduce_complex_host(int count, wr_csr_io *io);
 // Locality order (wr_reduce.cu): rows and columns renumbered by decreasing
 // entry count (ties by index); out.row_of / col_of map back, rank_offset = 0.
 wr_status locality_order_host(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,

@@ -202,9 +202,215 @@ wr_status locality_order_host(int64_t rows, int64_t cols, const int64_t *rowptr,
     return WR_OK;
 }
 
+// Chain reduction along a complex (Section 2.6.4: "elimination in one matrix
+// can propagate on the others").  mats[i] has the cells of mats[i+1]'s rows
+// as its columns and mats[i] mats[i+1] = 0 over Z.  A unit pivot at (r, c) of
+// mats[i] is removed as above (rank offset + 1) and, in the neighbours, the
+// line of each shared cell goes too: column r of mats[i-1], row c of
+// mats[i+1].  That line is zero or a combination of the others (d o d = 0
+// with the pivot's row or column a single +-1), so the neighbours' ranks do
+// not change, and the reduced matrices still compose to zero, so the rule
+// applies again.  Removals cascade through all the matrices.
+namespace {
+
+struct ChainMat {
+    int64_t rows = 0, cols = 0;
+    const int64_t *rp = nullptr;
+    const int32_t *ci = nullptr, *va = nullptr;
+    std::vector<int64_t> cptr;
+    std::vector<int32_t> crow;
+    std::vector<int32_t> rcnt, ccnt;
+    std::vector<char> rdead, cdead;
+    int64_t pivots = 0;
+};
+
+}  // namespace
+
+wr_status chain_reduce_complex_host(int count, wr_csr_io *io) {
+    if (count < 1 || !io) return fail(WR_EINVAL, "a complex needs at least one matrix");
+    std::vector<ChainMat> M(count);
+    for (int i = 0; i < count; i++) {
+        ChainMat &a = M[i];
+        a.rows = io[i].rows, a.cols = io[i].cols, a.rp = io[i].rowptr, a.ci = io[i].colidx, a.va = io[i].vals;
+        if (a.rows < 0 || a.cols < 0 || a.rows >= (int64_t(1) << 31) || a.cols >= (int64_t(1) << 31))
+            return fail(WR_EINVAL, "matrix " + std::to_string(i) + ": sizes must be in [0, 2^31)");
+        if (!a.rp || a.rp[0] != 0) return fail(WR_EINVAL, "matrix " + std::to_string(i) + ": bad rowptr");
+        for (int64_t r = 0; r < a.rows; r++)
+            if (a.rp[r + 1] < a.rp[r]) return fail(WR_EINVAL, "matrix " + std::to_string(i) + ": bad rowptr");
+        const int64_t nnz = a.rp[a.rows];
+        if (nnz > 0 && (!a.ci || !a.va)) return fail(WR_EINVAL, "matrix " + std::to_string(i) + ": null arrays");
+        for (int64_t e = 0; e < nnz; e++)
+            if (a.ci[e] < 0 || a.ci[e] >= a.cols)
+                return fail(WR_EINVAL, "matrix " + std::to_string(i) + ": column index out of range");
+        if (i > 0 && M[i - 1].cols != a.rows)
+            return fail(WR_EINVAL, "matrix " + std::to_string(i - 1) + "'s columns must be matrix " +
+                                       std::to_string(i) + "'s rows");
+    }
+    // exactness: mats[i] mats[i+1] = 0 over Z (row by row, dense accumulator)
+    for (int i = 0; i + 1 < count; i++) {
+        const ChainMat &a = M[i], &b = M[i + 1];
+        std::vector<__int128> acc(b.cols, 0);  // exact for any int32 entries
+        std::vector<int32_t> touched;
+        for (int64_t r = 0; r < a.rows; r++) {
+            touched.clear();
+            for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++) {
+                const int64_t j = a.ci[e], x = a.va[e];
+                if (!x) continue;
+                for (int64_t f = b.rp[j]; f < b.rp[j + 1]; f++) {
+                    if (!b.va[f]) continue;
+                    if (acc[b.ci[f]] == 0) touched.push_back(b.ci[f]);
+                    acc[b.ci[f]] += (__int128)x * b.va[f];
+                }
+            }
+            bool zero = true;
+            for (int32_t c : touched) {
+                if (acc[c] != 0) zero = false;
+                acc[c] = 0;
+            }
+            if (!zero)
+                return fail(WR_EINVAL, "matrices " + std::to_string(i) + " and " + std::to_string(i + 1) +
+                                           " do not compose to zero (not a chain complex)");
+        }
+    }
+    for (ChainMat &a : M) {
+        a.rcnt.assign(a.rows, 0);
+        a.ccnt.assign(a.cols, 0);
+        a.cptr.assign(a.cols + 1, 0);
+        for (int64_t r = 0; r < a.rows; r++)
+            for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++)
+                if (a.va[e] != 0) {
+                    a.rcnt[r]++;
+                    a.cptr[a.ci[e] + 1]++;
+                }
+        for (int64_t j = 0; j < a.cols; j++) {
+            a.ccnt[j] = (int32_t)a.cptr[j + 1];
+            a.cptr[j + 1] += a.cptr[j];
+        }
+        a.crow.assign(a.cptr[a.cols], 0);
+        std::vector<int64_t> fill(a.cptr.begin(), a.cptr.end() - 1);
+        for (int64_t r = 0; r < a.rows; r++)
+            for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++)
+                if (a.va[e] != 0) a.crow[fill[a.ci[e]]++] = (int32_t)r;
+        a.rdead.assign(a.rows, 0);
+        a.cdead.assign(a.cols, 0);
+    }
+    // work items: (matrix, line, is_row) with a single live entry
+    std::deque<std::pair<int, int64_t>> rq, cq;
+    for (int i = 0; i < count; i++) {
+        for (int64_t r = 0; r < M[i].rows; r++)
+            if (M[i].rcnt[r] == 1) rq.emplace_back(i, r);
+        for (int64_t j = 0; j < M[i].cols; j++)
+            if (M[i].ccnt[j] == 1) cq.emplace_back(i, j);
+    }
+    auto kill_row = [&](int i, int64_t r) {
+        ChainMat &a = M[i];
+        if (a.rdead[r]) return;
+        a.rdead[r] = 1;
+        for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++) {
+            const int64_t c = a.ci[e];
+            if (a.va[e] != 0 && !a.cdead[c] && --a.ccnt[c] == 1) cq.emplace_back(i, c);
+        }
+    };
+    auto kill_col = [&](int i, int64_t c) {
+        ChainMat &a = M[i];
+        if (a.cdead[c]) return;
+        a.cdead[c] = 1;
+        for (int64_t e = a.cptr[c]; e < a.cptr[c + 1]; e++) {
+            const int64_t r = a.crow[e];
+            if (!a.rdead[r] && --a.rcnt[r] == 1) rq.emplace_back(i, r);
+        }
+    };
+    auto take = [&](int i, int64_t r, int64_t c) {
+        ChainMat &a = M[i];
+        a.pivots++;
+        a.rdead[r] = 1;  // both lines go before the counts of their crossings drop
+        a.cdead[c] = 1;
+        for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++) {
+            const int64_t c2 = a.ci[e];
+            if (a.va[e] != 0 && !a.cdead[c2] && --a.ccnt[c2] == 1) cq.emplace_back(i, c2);
+        }
+        for (int64_t e = a.cptr[c]; e < a.cptr[c + 1]; e++) {
+            const int64_t r2 = a.crow[e];
+            if (!a.rdead[r2] && --a.rcnt[r2] == 1) rq.emplace_back(i, r2);
+        }
+        if (i > 0) kill_col(i - 1, r);
+        if (i + 1 < count) kill_row(i + 1, c);
+    };
+    while (!rq.empty() || !cq.empty()) {
+        while (!rq.empty()) {
+            const auto [i, r] = rq.front();
+            rq.pop_front();
+            ChainMat &a = M[i];
+            if (a.rdead[r] || a.rcnt[r] != 1) continue;
+            for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++)
+                if (a.va[e] != 0 && !a.cdead[a.ci[e]]) {
+                    if (a.va[e] == 1 || a.va[e] == -1) take(i, r, a.ci[e]);
+                    break;
+                }
+        }
+        while (!cq.empty()) {
+            const auto [i, c] = cq.front();
+            cq.pop_front();
+            ChainMat &a = M[i];
+            if (a.cdead[c] || a.ccnt[c] != 1) continue;
+            for (int64_t e = a.cptr[c]; e < a.cptr[c + 1]; e++) {
+                const int64_t r = a.crow[e];
+                if (a.rdead[r]) continue;
+                int32_t v = 0;
+                for (int64_t f = a.rp[r]; f < a.rp[r + 1]; f++)
+                    if (a.ci[f] == c && a.va[f] != 0) {
+                        v = a.va[f];
+                        break;
+                    }
+                if (v == 1 || v == -1) take(i, r, c);
+                break;
+            }
+        }
+    }
+    // compact each matrix: live rows and columns that still hold an entry
+    for (int i = 0; i < count; i++) {
+        ChainMat &a = M[i];
+        wr_csr_io &o = io[i];
+        std::vector<int32_t> cnew(a.cols, -1);
+        int64_t nc = 0;
+        for (int64_t j = 0; j < a.cols; j++)
+            if (!a.cdead[j] && a.ccnt[j] > 0) {
+                if (o.out_col_of) o.out_col_of[nc] = (int32_t)j;
+                cnew[j] = (int32_t)nc++;
+            }
+        int64_t nr = 0, w = 0;
+        o.out_rowptr[0] = 0;
+        for (int64_t r = 0; r < a.rows; r++) {
+            if (a.rdead[r] || a.rcnt[r] == 0) continue;
+            for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++)
+                if (a.va[e] != 0 && cnew[a.ci[e]] >= 0) {
+                    o.out_colidx[w] = cnew[a.ci[e]];
+                    o.out_vals[w] = a.va[e];
+                    w++;
+                }
+            if (o.out_row_of) o.out_row_of[nr] = (int32_t)r;
+            o.out_rowptr[++nr] = w;
+        }
+        o.out_rows = nr;
+        o.out_cols = nc;
+        o.rank_offset = a.pivots;
+    }
+    return WR_OK;
+}
+
 }  // namespace wr
 
 using namespace wr;
+
+extern "C" wr_status wr_chain_reduce_complex(int32_t count, wr_csr_io *mats) {
+    if (!mats) return fail(WR_EINVAL, "null argument");
+    for (int i = 0; i < count; i++) {
+        const int64_t nnz = mats[i].rowptr ? mats[i].rowptr[std::max<int64_t>(mats[i].rows, 0)] : 0;
+        if (!mats[i].out_rowptr || (nnz > 0 && (!mats[i].out_colidx || !mats[i].out_vals)))
+            return fail(WR_EINVAL, "matrix " + std::to_string(i) + ": null output arrays");
+    }
+    return chain_reduce_complex_host(count, mats);
+}
 
 extern "C" wr_status wr_chain_reduce_csr(int64_t rows, int64_t cols, const int64_t *rowptr, const int32_t *colidx,
                                          const int32_t *vals, int64_t *out_rows, int64_t *out_cols,

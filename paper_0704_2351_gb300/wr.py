@@ -37,6 +37,14 @@ class wr_params(ctypes.Structure):
                 ("seq_len", ctypes.c_uint64), ("want", ctypes.c_uint32)]
 
 
+class wr_csr_io(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("out_rows", ctypes.c_int64),
+                ("out_cols", ctypes.c_int64), ("rank_offset", ctypes.c_int64), ("out_rowptr", ctypes.c_void_p),
+                ("out_colidx", ctypes.c_void_p), ("out_vals", ctypes.c_void_p), ("out_row_of", ctypes.c_void_p),
+                ("out_col_of", ctypes.c_void_p)]
+
+
 class wr_timings(ctypes.Structure):
     _fields_ = [("setup_ms", ctypes.c_double), ("sequence_ms", ctypes.c_double),
                 ("sigma_ms", ctypes.c_double), ("readout_ms", ctypes.c_double),
@@ -81,6 +89,7 @@ _sig = {
     "wr_set_chain_reduction": ([vp, i32], ctypes.c_int),
     "wr_set_locality_order": ([vp, i32], ctypes.c_int),
     "wr_locality_order_csr": ([i64, i64, vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+    "wr_chain_reduce_complex": ([i32, vp], ctypes.c_int),
     "wr_matrix_reduction": ([vp, P(i64), P(i64), P(i64)], ctypes.c_int),
     "wr_chain_reduce_csr": ([i64, i64, vp, vp, vp, P(i64), P(i64), vp, vp, vp, vp, vp, P(i64)], ctypes.c_int),
     "wr_matrix_load_csr": ([vp, i64, i64, vp, vp, vp, P(vp)], ctypes.c_int),
@@ -282,6 +291,37 @@ def wr_locality_order_csr(rows: int, cols: int, rowptr, colidx, vals):
                                       vp(vals.ctypes.data), vp(orp.ctypes.data), vp(oci.ctypes.data),
                                       vp(ova.ctypes.data), vp(rof.ctypes.data), vp(cof.ctypes.data)))
     return orp, oci[:nnz].copy(), ova[:nnz].copy(), rof[:rows].copy(), cof[:cols].copy()
+
+
+def wr_chain_reduce_complex(mats):
+    """Host chain reduction along a complex (no device needed).  mats: list of
+    (rows, cols, rowptr, colidx, vals) with mats[i] mats[i+1] = 0.  Returns a
+    list of (rows, cols, rowptr, colidx, vals, row_of, col_of, rank_offset)."""
+    k = len(mats)
+    arr = (wr_csr_io * max(k, 1))()
+    keep = []
+    for i, (rows, cols, rowptr, colidx, vals) in enumerate(mats):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.int32)
+        nnz = int(rowptr[rows])
+        outs = (np.zeros(rows + 1, dtype=np.int64), np.zeros(max(nnz, 1), dtype=np.int32),
+                np.zeros(max(nnz, 1), dtype=np.int32), np.zeros(max(rows, 1), dtype=np.int32),
+                np.zeros(max(cols, 1), dtype=np.int32))
+        keep.append((rowptr, colidx, vals) + outs)
+        a = arr[i]
+        a.rows, a.cols = rows, cols
+        a.rowptr, a.colidx, a.vals = rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data
+        a.out_rowptr, a.out_colidx, a.out_vals, a.out_row_of, a.out_col_of = [o.ctypes.data for o in outs]
+    _check(_lib.wr_chain_reduce_complex(k, ctypes.cast(arr, ctypes.c_void_p)))
+    res = []
+    for i in range(k):
+        a = arr[i]
+        orp, oci, ova, rof, cof = keep[i][3:]
+        n2 = int(orp[a.out_rows])
+        res.append((a.out_rows, a.out_cols, orp[: a.out_rows + 1].copy(), oci[:n2].copy(), ova[:n2].copy(),
+                    rof[: a.out_rows].copy(), cof[: a.out_cols].copy(), a.rank_offset))
+    return res
 
 
 def wr_matrix_reduction(mat: int) -> dict:

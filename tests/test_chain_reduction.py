@@ -124,3 +124,83 @@ def test_locality_order_is_a_degree_sorted_permutation(wr):
         for i in range(B.rows):
             assert np.all(np.diff(ci[rp[i]:rp[i + 1]]) > 0)
         assert oracle.rank_dense(B.to_dense(), 65521) == oracle.rank_dense(A.to_dense(), 65521)
+
+
+# ---------------------------------------------------------------------------
+# along a complex: reductions propagate from one matrix to its neighbours
+# ---------------------------------------------------------------------------
+
+def _csr_tuple(A):
+    return (A.rows, A.cols, A.rowptr, A.colidx, A.vals)
+
+
+def _reduced(t):
+    r, c, rp, ci, va, rof, cof, off = t
+    return synth.CSR(r, c, rp, ci, va), rof, cof, off
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_complex_reduction_keeps_every_rank(wr, seed):
+    d_n, d_n1 = synth.chain_pair(260 + 40 * seed, seed=seed, homology=seed % 3)
+    out = wr.wr_chain_reduce_complex([_csr_tuple(d_n), _csr_tuple(d_n1)])
+    for A, t in zip([d_n, d_n1], out):
+        R, rof, cof, off = _reduced(t)
+        assert np.array_equal(R.to_dense(), A.to_dense()[np.ix_(rof, cof)])
+        for p in [3, 65521, 1073741789]:
+            assert oracle.rank_dense(A.to_dense(), p) == off + oracle.rank_dense(R.to_dense(), p), p
+        assert off + oracle.rank_dense(R.to_dense(), 1073741789) == A.rank
+    # the reduced pair still composes to zero: kept rows of d_n times kept
+    # columns of d_n+1 over the cells kept in both (a cell kept in one only
+    # is an empty line there, which adds nothing to the product)
+    _, rof_n, cof_n, _ = _reduced(out[0])
+    _, rof_n1, cof_n1, _ = _reduced(out[1])
+    common = np.intersect1d(cof_n, rof_n1)
+    prod = d_n.to_dense()[np.ix_(rof_n, common)] @ d_n1.to_dense()[np.ix_(common, cof_n1)]
+    assert not prod.any()
+
+
+def test_complex_reduction_propagates_beyond_the_single_matrix_pass(wr):
+    """A small complex where the neighbour's rule frees new singletons: the
+    boundary of a filled square (2 triangles) -- d1: edges -> vertices,
+    d2: faces -> edges.  Each matrix alone has no unit singleton row or
+    column beyond what the pair unlocks."""
+    # vertices 0..3, edges (0,1),(1,2),(2,3),(3,0),(0,2), faces (0,1,2),(0,2,3)
+    e = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2)]
+    d1 = np.zeros((4, 5), dtype=np.int64)
+    for j, (a, b) in enumerate(e):
+        d1[a, j], d1[b, j] = -1, 1
+    # faces (0,1,2) = e01 + e12 - e02 and (0,2,3) = e02 + e23 + e30
+    d2 = np.array([[1, 0], [1, 0], [0, 1], [0, 1], [-1, 1]], dtype=np.int64)
+    assert not (d1 @ d2).any()
+    A1, A2 = synth.dense_to_csr(d1), synth.dense_to_csr(d2)
+    single = [wr.wr_chain_reduce_csr(*_csr_tuple(A))[-1] for A in (A1, A2)]
+    out = wr.wr_chain_reduce_complex([_csr_tuple(A1), _csr_tuple(A2)])
+    offs = [t[-1] for t in out]
+    # alone, d1 has no unit singleton line and d2 two; along the complex the
+    # pivots of d2 free d1's rows: the contractible square reduces to nothing
+    assert single == [0, 2] and offs == [3, 2]
+    assert all(t[0] == 0 or t[1] == 0 for t in out)
+    for A, t in zip([A1, A2], out):
+        R, _, _, off = _reduced(t)
+        assert oracle.rank_dense(A.to_dense(), 65521) == off + oracle.rank_dense(R.to_dense(), 65521)
+    # the square is contractible: rank d1 = 3, rank d2 = 2
+    assert oracle.rank_dense(d1, 65521) == 3 and oracle.rank_dense(d2, 65521) == 2
+
+
+def test_complex_of_one_matrix_is_the_single_reduction(wr):
+    for A in _mats():
+        a = wr.wr_chain_reduce_csr(*_csr_tuple(A))
+        b = wr.wr_chain_reduce_complex([_csr_tuple(A)])[0]
+        assert a[0] == b[0] and a[1] == b[1] and a[-1] == b[-1]
+        R1, R2 = synth.CSR(a[0], a[1], a[2], a[3], a[4]), synth.CSR(b[0], b[1], b[2], b[3], b[4])
+        assert oracle.rank_dense(R1.to_dense(), 65521) == oracle.rank_dense(R2.to_dense(), 65521)
+
+
+def test_complex_reduction_rejects_a_non_complex(wr):
+    A = synth.dense_to_csr(np.array([[1, 1], [0, 1]]))
+    B = synth.dense_to_csr(np.array([[1, 0], [0, 1]]))
+    with pytest.raises(wr.WrError):
+        wr.wr_chain_reduce_complex([_csr_tuple(A), _csr_tuple(B)])
+    C = synth.dense_to_csr(np.array([[1, 0, 0]]))
+    with pytest.raises(wr.WrError):  # 1 x 3 then 2 x 2: sizes do not chain
+        wr.wr_chain_reduce_complex([_csr_tuple(C), _csr_tuple(B)])
