@@ -574,3 +574,37 @@ def test_early_termination_point_is_where_a_planted_mistake_shows():
     full = _generator(S, p, 2)
     # the generator's degree max(delta) orders at least must have been seen
     assert k >= int(np.max(full["delta"]))
+
+
+# ---------------------------------------------------------------------------
+# two terms per application of A~ (the identities the device's symmetric and
+# paired generic modes compute), from oracle primitives
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("side,m", [(0, 3), (1, 2), (0, 1)])
+def test_two_terms_per_application_identities(side, m):
+    """A~ = D1 A^T D2 A D1 is symmetric, so with U_k = A~^k X, V_k = A~^k Y:
+    X^T A~^(2k) Y = U_k^T V_k and X^T A~^(2k+1) Y = (A D1 U_k)^T D2 (A D1 V_k)
+    (rows side: A^T and A swap).  Checked against the literal sequence for
+    independent X and Y (and X = Y), k = 0..6."""
+    p = 1073741789
+    A = synth.planted_sparse(70, 60, 45, row_len=4, seed=side * 10 + m)
+    for symmetric in [False, True]:
+        st = oracle.Setup(A, p, m, m, seed=5 + m, side=side, symmetric=symmetric)
+        S = oracle.sequence(A, st, 14)
+        U = st.X.astype(np.uint32)
+        V = st.Y.astype(np.uint32)
+
+        def half(W):  # A D1 W (columns side) or A^T D1 W (rows side)
+            D1W = (st.D1.astype(object)[:, None] * W.astype(object)) % p
+            return (oracle.csr_mul(A, D1W.astype(np.uint32), p) if side == 0
+                    else oracle.csr_tmul(A, D1W.astype(np.uint32), p)).astype(object)
+
+        for k in range(7):
+            even = (U.astype(object).T.dot(V.astype(object))) % p
+            assert np.array_equal(even.astype(np.uint64), S[2 * k].astype(np.uint64)), (k, "even")
+            HU, HV = half(U), half(V)
+            odd = (HU.T.dot(st.D2.astype(object)[:, None] * HV)) % p
+            assert np.array_equal(odd.astype(np.uint64), S[2 * k + 1].astype(np.uint64)), (k, "odd")
+            U = oracle.blackbox_apply(A, p, st.side, st.D1, st.D2, U)
+            V = oracle.blackbox_apply(A, p, st.side, st.D1, st.D2, V)
