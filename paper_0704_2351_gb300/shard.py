@@ -1,4 +1,7 @@
-"""Column sharding of the sequence over several GPUs (Section 3.1).
+"""Sharding over several GPUs: columns of the block (Section 3.1) and
+independent jobs.
+
+Column slabs.
 
 The paper gives each process one column of the block Y: column j of
 S_i = X^T A~^i Y depends only on Y[:, j], so the processes never exchange
@@ -9,6 +12,12 @@ wr_sequence_slab_device, and one all-gather assembles the full L x m x n
 sequence in column order on every rank.  The host logic (slab bounds, padding
 of uneven slabs to a common width for the collective, reassembly) is plain
 torch.distributed and runs the same on gloo (CPU) and NCCL (GPU).
+
+Independent jobs.  Batched work (matrices x primes, rank over Q as the
+maximum over primes, Section 2.5) needs no exchange while it runs: jobs are
+dealt to ranks, largest first, so that the ranks' summed costs stay close,
+each rank runs its share (wr_rank_batch on its GPU), and one gather brings
+the ranks of every job back in job order.
 """
 from __future__ import annotations
 
@@ -65,3 +74,41 @@ def gpu_slab(ctx: int, mat: int, params, L: int, device: Optional[torch.device] 
         return out
 
     return run
+
+
+def deal_jobs(costs, world: int):
+    """Job indices per rank: jobs taken largest cost first (ties by index),
+    each to the rank with the least summed cost so far (ties by rank).  Every
+    job lands on exactly one rank; a rank's list is in increasing job order."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0.0] * world
+    share = [[] for _ in range(world)]
+    for j in sorted(range(len(costs)), key=lambda j: (-float(costs[j]), j)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        share[r].append(j)
+        load[r] += float(costs[j])
+    return [sorted(s) for s in share]
+
+
+def gather_job_results(mine, results, njobs: int, world: int, group=None) -> torch.Tensor:
+    """All-gather the int64 results of every rank's jobs (mine: this rank's
+    job indices, results: one value each) into one tensor in job order."""
+    cnt = torch.tensor([len(mine)], dtype=torch.int64)
+    parts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(parts, cnt, group=group)
+    counts = [int(c.item()) for c in parts]
+    width = max(counts + [1])
+    buf = torch.full((2, width), -1, dtype=torch.int64)
+    if mine:
+        buf[0, : len(mine)] = torch.tensor(list(mine), dtype=torch.int64)
+        buf[1, : len(mine)] = torch.tensor(list(results), dtype=torch.int64)
+    bufs = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(bufs, buf, group=group)
+    out = torch.full((njobs,), -1, dtype=torch.int64)
+    for r in range(world):
+        k = counts[r]
+        out[bufs[r][0, :k]] = bufs[r][1, :k]
+    if (out < 0).any():
+        raise RuntimeError("a job's result is missing after the gather")
+    return out

@@ -71,3 +71,53 @@ def test_column_slab_partition():
             assert max(ws) - min(ws) <= 1 and min(ws) >= 1
     with pytest.raises(ValueError):
         shard.column_slab(8, 8, 8)
+
+
+# ---------------------------------------------------------------------------
+# independent jobs (matrices x primes) dealt to ranks, ranks gathered
+# ---------------------------------------------------------------------------
+
+def _jobs():
+    mats = [synth.planted_sparse(60 + 25 * i, 50 + 20 * i, 30 + 10 * i, row_len=4, seed=40 + i) for i in range(5)]
+    primes = [65521, 1073741789, 2147483629]
+    return mats, [(i, p) for i in range(len(mats)) for p in primes]
+
+
+def _jobs_main(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mats, jobs = _jobs()
+        share = shard.deal_jobs([mats[i].nnz for i, _ in jobs], world)[rank]
+        ranks = [oracle.rank_sparse(mats[jobs[j][0]], jobs[j][1]) for j in share]
+        allr = shard.gather_job_results(share, ranks, len(jobs), world)
+        np.save(out_path + ".%d.npy" % rank, allr.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_jobs_dealt_and_gathered_in_job_order(tmp_path, world):
+    out = str(tmp_path / "R")
+    mp.start_processes(_jobs_main, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
+    mats, jobs = _jobs()
+    for r in range(world):
+        got = np.load(out + ".%d.npy" % r)
+        assert got.tolist() == [mats[i].rank for i, _ in jobs], "rank %d" % r
+        # rank over Q = the maximum over the primes
+        for i, A in enumerate(mats):
+            assert max(got[k] for k, (ii, _) in enumerate(jobs) if ii == i) == A.rank
+
+
+def test_deal_jobs_balances_and_covers():
+    costs = [5, 1, 1, 1, 1, 1, 3, 2, 8, 1]
+    for world in [1, 2, 3, 4, 12]:
+        share = shard.deal_jobs(costs, world)
+        flat = sorted(j for s in share for j in s)
+        assert flat == list(range(len(costs)))
+        loads = [sum(costs[j] for j in s) for s in share]
+        if world <= len(costs):
+            assert max(loads) - min(loads) <= max(costs)
+    with pytest.raises(ValueError):
+        shard.deal_jobs(costs, 0)
