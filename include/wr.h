@@ -137,7 +137,8 @@ wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
  * than 131,072 orders when m + n <= 32, the blocked M-Basis otherwise. */
 wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders);
 /* SpMM tile shape: the residues each lane gathers from a row of the dense
- * block (1, 2 or 4; the row's n residues are spread over n / that many lanes).
+ * block (1, 2, 4 or 8; the row's n residues are spread over n / that many
+ * lanes, at most 32).
  * With autotuning on (default), the first sequence or black-box application
  * on a matrix with at least 2^20 stored entries times each candidate on that
  * matrix's two layouts (a few launches each, CUDA events) and keeps the
@@ -175,9 +176,20 @@ wr_status wr_set_early_termination(wr_ctx *ctx, int64_t orders);
  * symmetric, so with U_k = A~^k X and V_k = A~^k Y the terms are
  * S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k) (A~ symmetric:
  * Section 2.3).  X and Y are then carried side by side in one block of width 2n
- * (n <= 16) and one black-box application yields two terms.  Off: one term per
+ * (n <= 32: rows of up to 64 residues) and one black-box application yields
+ * two terms.  Off: one term per
  * application on a block of width n.  The sequence is the same either way. */
 wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on);
+/* Where the Gram projections run (the terms of the symmetric projection and of
+ * the paired generic one, Section 2.3; Table tab:r-opp col. 3 is the paper's
+ * dot-product step): 1 = the tensor cores, 0 = 64-bit integer multiply-adds,
+ * -1 (default) = the tensor cores for blocks of 16 columns and more (m, n >=
+ * 16), the integer path below.  The tensor-core path is exact: every residue
+ * is split into four balanced 8-bit digits (bf16 values), tcgen05 MMAs sum the
+ * 16 digit products per residue product in fp32 over at most 512 rows (every
+ * partial sum an integer below 2^23), and the sums are drained into int64 and
+ * recombined mod p.  The result is the same bit for bit either way. */
+wr_status wr_set_tensor_projection(wr_ctx *ctx, int32_t mode);
 
 /* ---------------------------------------------------------------- matrices */
 
@@ -325,7 +337,10 @@ wr_status wr_blackbox_apply_device(wr_ctx *ctx, const wr_matrix *mat, const wr_p
  * rounded up to a power of two, M the other dimension); larger requests return
  * WR_EINVAL with the sizes in wr_last_error().  The first call on a device
  * looks up the array's device address (with that device current): make that
- * first call before any stream capture.  All calls share the array and find
+ * first call before any stream capture.  The address is kept per device and
+ * primary context; after a device reset (cudaDeviceReset, which also ends
+ * every context, matrix and stream of this library on that device) the next
+ * call looks it up again.  All calls share the array and find
  * what the previous call left in it; calls whose work overlaps on the GPU
  * (other threads, contexts or streams of the same device) race on it and must
  * be serialised by the caller.  The call returns after its work completed. */
@@ -335,6 +350,28 @@ wr_status wr_blackbox_apply_device_noalloc(wr_ctx *ctx, const wr_matrix *mat,
 /* The sequence S_i = X^T A~^i Y, i < L (Section 2.5 step 2) into d_S (L*m*n). */
 wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
                              uint32_t *d_S, uint64_t L);
+/* The sequence of wr_sequence_device, plus the block the iteration carries,
+ * for spot checks of any step at full size (Section 2.5 step 2).  The block
+ * after k applications of A~ is written in the matrix's row order, unscaled:
+ * with the paired generic projection (m = n, wr_set_paired_projection) the
+ * N x (m + n) block [A~^k X | A~^k Y] (*paired = 1), otherwise the N x n block
+ * A~^k Y (*paired = 0).  One application yields two terms in the paired and
+ * symmetric modes (S_2k = X^T A~^2k Y from the block after k applications),
+ * one term otherwise.  d_snap (may be NULL) receives the block after snap_at
+ * applications, d_last (may be NULL) the block after the last application;
+ * *applications (may be NULL) receives the number of applications done.
+ * snap_at beyond that number is WR_EINVAL. */
+wr_status wr_sequence_state_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                   uint32_t *d_S, uint64_t L, int64_t snap_at, uint32_t *d_snap,
+                                   uint32_t *d_last, int64_t *applications, int32_t *paired);
+/* One Gram projection of the sequence (Section 2.3), through the kernels the
+ * sequence uses (wr_set_tensor_projection chooses them):
+ * d_G (m x n) = sum_{r < N} w_r t[r][0 .. m)^T t[r][yoff .. yoff + n) mod p.
+ * d_t: N rows of tstride residues (16-byte aligned; nv = n rounded up to a
+ * power of two; tstride a multiple of nv with tstride >= m and >= yoff + nv;
+ * yoff a multiple of nv); d_w: N residues.  All residues must be below p. */
+wr_status wr_gram_device(wr_ctx *ctx, uint32_t prime, int64_t N, uint32_t m, uint32_t n, const uint32_t *d_t,
+                         int32_t tstride, int32_t yoff, const uint32_t *d_w, uint32_t *d_G);
 /* Columns [col0, col0 + ncols) of that sequence, S_i = X^T A~^i Y[:, col0:col0+ncols]
  * (L x m x ncols residues into d_S), with X, Y, D1, D2 drawn exactly as for
  * the whole sequence (params->n is the width of the whole Y).  The paper
@@ -356,6 +393,17 @@ wr_status wr_sigma_basis_device(wr_ctx *ctx, const uint32_t *d_S, uint64_t L, ui
  * precision T does not determine it. */
 wr_status wr_det_valuation_device(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T,
                                   uint32_t prime, int64_t *val);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Tensor-core rate and layout probe (a measurement helper; the paper has no
+ * counterpart): `blocks` thread blocks (one per SM at most) each issue
+ * iters chains of four tcgen05 bf16 MMAs (M = 128, N = 256, K = 16 each, fp32
+ * accumulators in tensor memory) on tiles held in shared memory; *ms is the
+ * kernel's duration (CUDA events).  With d_out != NULL, block 0 writes its
+ * 128 x 256 fp32 accumulator: entry (r, c) = iters * sum_{k < 64} a(r, k) b(c, k)
+ * with a(r, k) = (7r + 3k) mod 17 - 8 and b(c, k) = (5c + 11k) mod 13 - 6. */
+wr_status wr_probe_mma(wr_ctx *ctx, int64_t iters, int32_t blocks, float *d_out, double *ms);
 
 /* ---------------------------------------------------------------- serving */
 

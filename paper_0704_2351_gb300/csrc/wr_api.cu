@@ -244,8 +244,8 @@ extern "C" wr_status wr_set_autotune(wr_ctx *ctx, int32_t on) {
 
 extern "C" wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues) {
     if (!ctx) return fail(WR_EINVAL, "null context");
-    if (residues != 0 && residues != 1 && residues != 2 && residues != 4)
-        return fail(WR_EINVAL, "lane width must be 0 (tuned or default), 1, 2 or 4 residues");
+    if (residues != 0 && residues != 1 && residues != 2 && residues != 4 && residues != 8)
+        return fail(WR_EINVAL, "lane width must be 0 (tuned or default), 1, 2, 4 or 8 residues");
     ctx->lane_width = residues;
     return WR_OK;
 }
@@ -266,6 +266,13 @@ extern "C" wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on) {
 extern "C" wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on) {
     if (!ctx) return fail(WR_EINVAL, "null context");
     ctx->pair_generic = on != 0;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_tensor_projection(wr_ctx *ctx, int32_t mode) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    if (mode < -1 || mode > 1) return fail(WR_EINVAL, "tensor projection mode must be -1 (automatic), 0 or 1");
+    ctx->tensor_proj = mode;
     return WR_OK;
 }
 
@@ -761,6 +768,47 @@ extern "C" wr_status wr_sequence_device(wr_ctx *ctx, const wr_matrix *mat, const
     ctx->last.setup_ms = a;
     ctx->last.sequence_ms = b;
     return WR_OK;
+}
+
+extern "C" wr_status wr_sequence_state_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,
+                                              uint32_t *d_S, uint64_t L, int64_t snap_at, uint32_t *d_snap,
+                                              uint32_t *d_last, int64_t *applications, int32_t *paired) {
+    if (!ctx || !mat || !params || !d_S) return fail(WR_EINVAL, "null argument");
+    if (d_snap && snap_at < 0) return fail(WR_EINVAL, "snap_at must be >= 0 when d_snap is given");
+    Resolved r;
+    WR_TRY(resolve(mat, params, r));
+    if (r.N == 0) return fail(WR_EINVAL, "the matrix has no rows or no columns");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    ctx->last = wr_timings{};
+    StateOut so;
+    so.snap_at = d_snap ? snap_at : -1;
+    so.d_snap = d_snap;
+    so.d_last = d_last;
+    double a = 0, b = 0;
+    WR_TRY(run_sequence(ctx, mat, *params, (int64_t)L, d_S, &a, &b, nullptr, &so));
+    if (d_snap && so.snap_at > so.applications)
+        return fail(WR_EINVAL, "snap_at is beyond the applications of this sequence");
+    ctx->last.setup_ms = a;
+    ctx->last.sequence_ms = b;
+    if (applications) *applications = so.applications;
+    if (paired) *paired = so.paired ? 1 : 0;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_gram_device(wr_ctx *ctx, uint32_t prime, int64_t N, uint32_t m, uint32_t n,
+                                    const uint32_t *d_t, int32_t tstride, int32_t yoff, const uint32_t *d_w,
+                                    uint32_t *d_G) {
+    if (!ctx || (N > 0 && (!d_t || !d_w)) || !d_G) return fail(WR_EINVAL, "null argument");
+    if (prime <= 2 || prime >= (1u << 31) || !is_prime_u32(prime)) return fail(WR_ENOTPRIME, "bad prime");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    return gram_device(ctx, prime, N, (int)m, (int)n, d_t, tstride, yoff, d_w, d_G);
+}
+
+extern "C" wr_status wr_probe_mma(wr_ctx *ctx, int64_t iters, int32_t blocks, float *d_out, double *ms) {
+    if (!ctx || !ms) return fail(WR_EINVAL, "null argument");
+    if (iters < 1 || blocks < 1 || blocks > 4096) return fail(WR_EINVAL, "iters >= 1 and blocks in 1..4096");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    return probe_mma(ctx, iters, blocks, d_out, ms);
 }
 
 extern "C" wr_status wr_sequence_slab_device(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,

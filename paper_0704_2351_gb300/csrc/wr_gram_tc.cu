@@ -1,0 +1,436 @@
+// The projection's weighted Gram products on the tensor cores.
+//
+// Two terms per application of A~ (Section 2.3: A~ = D1 A^T D2 A D1 is
+// symmetric; Table tab:r-opp col. 3 is the paper's dot-product step) come from
+// products of the form
+//
+//   G = sum_r w_r L_r^T R_r  mod p,   L_r = t[r][0 .. m),  R_r = t[r][yoff .. yoff + n)
+//
+// over the N rows of a block t (the symmetric projection: L = R; X beside Y:
+// the X and Y halves of the paired block).  They are computed exactly from
+// bf16 products of 8-bit digits.  A residue x < 2^31 is written in balanced
+// digits x = sum_i d_i 2^{8i}: with y = x + 0x808080, d_i = byte_i(y) - 128 for
+// i < 3 and d_3 = byte_3(y) in [0, 128].  Every digit is an integer of
+// magnitude <= 128 (exact in bf16), a digit product is at most 2^14, so the
+// fp32 sums of GT_DRAIN * 64 = 512 rows stay below 2^23 and are exact.
+//
+// Per tile of 64 rows (the MMA's K), one tcgen05 MMA chain computes
+//   D[i*32 + a][j*NB + b] = sum_r d_i(w_r L_r[a]) d_j(R_r[b])
+// (M = 128 = 4 digits x 32 left columns, N = 4 digits x NB right columns, fp32
+// in tensor memory); every 512 rows each thread of the first four warps
+// drains its TMEM lane (digit i = warp, column a = lane) into exact int64 sums
+// acc[b] += sum_j 2^{8j} D[i*32 + a][j*NB + b], and at the end
+//   G[a][b] = sum_i 2^{8i} acc_i[a][b]  mod p.
+// The rows of t reach shared memory by 1-D bulk copies (four tiles in flight),
+// the threads rewrite them as digit tiles in the MMA's swizzled layout, and
+// one thread issues the MMAs and commits them to an mbarrier; operand tiles
+// are double-buffered.  Every wait is bounded: after WAIT_NS the block records
+// an error, waits (bounded) for its copies and MMAs in flight, frees its
+// tensor memory and returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "wr_internal.cuh"
+#include "wr_tc.cuh"
+
+namespace wr {
+
+namespace {
+
+constexpr int GT_THREADS = 256;
+constexpr int GT_KT = 64;     // rows per tile
+constexpr int GT_NS = 4;      // raw tiles in flight
+constexpr int GT_DRAIN = 8;   // tiles per drain of the accumulator (512 rows)
+constexpr uint64_t GT_WAIT_NS = 2000000000ull;
+constexpr int GT_ERR_TIMEOUT = 1;
+
+template <int NB, int RB>
+struct GramShape {
+    static constexpr int TN = 4 * NB;                      // B rows (N of the MMA)
+    static constexpr uint32_t ABYTES = 128u * 128u;        // A tile: 128 rows x 128 bytes
+    static constexpr uint32_t BBYTES = (uint32_t)TN * 128u;
+    static constexpr uint32_t OPB = ABYTES + BBYTES;       // one operand stage
+    static constexpr uint32_t RAWB = (uint32_t)GT_KT * RB; // one raw tile
+    static constexpr uint32_t TMEM_COLS = TN < 32 ? 32 : TN;
+    static constexpr size_t SMEM = 1024 + 2 * (size_t)OPB + GT_NS * (size_t)RAWB + 128;
+    static_assert(NB == 8 || NB == 16 || NB == 32, "NB");
+    static_assert(RB % 16 == 0 && RB >= 32 && RB <= 256, "RB");
+    static_assert(4u * 32u * NB * 4u <= GT_NS * RAWB, "reduction area");
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    // cvt packs its first source into the upper half
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// digit i (0..3) of the balanced digits of x, as a float: y = x + 0x808080,
+// byte i of y placed in the mantissa of 2^23 (bits 0x4B0000ee = 2^23 + e)
+template <int I>
+__device__ __forceinline__ float digit_f(uint32_t y) {
+    const float f = __uint_as_float(__byte_perm(y, 0x4B000000u, 0x7440u + I));
+    return I < 3 ? f - 8388736.0f : f - 8388608.0f;  // 2^23 + 128, 2^23
+}
+
+// the 4 digit rows (row0 + i * stride) of 8 consecutive K values into
+// 16-byte chunk c of a swizzled tile
+__device__ __forceinline__ void put_digits(unsigned char *tile, int row0, int stride, int c, const uint32_t (&x)[8]) {
+    uint32_t y[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) y[u] = x[u] + 0x808080u;
+#define WR_DIGIT_ROW(I)                                                                              \
+    {                                                                                                \
+        uint4 q;                                                                                     \
+        q.x = pack_bf16x2(digit_f<I>(y[0]), digit_f<I>(y[1]));                                       \
+        q.y = pack_bf16x2(digit_f<I>(y[2]), digit_f<I>(y[3]));                                       \
+        q.z = pack_bf16x2(digit_f<I>(y[4]), digit_f<I>(y[5]));                                       \
+        q.w = pack_bf16x2(digit_f<I>(y[6]), digit_f<I>(y[7]));                                       \
+        *reinterpret_cast<uint4 *>(tile + tc::sw128_chunk((uint32_t)(row0 + I * stride), (uint32_t)c)) = q; \
+    }
+    WR_DIGIT_ROW(0)
+    WR_DIGIT_ROW(1)
+    WR_DIGIT_ROW(2)
+    WR_DIGIT_ROW(3)
+#undef WR_DIGIT_ROW
+}
+
+// G into s_raw[k] (k = tmul * counter + toff; skipped unless 0 <= k < L): the
+// per-block result reduced mod p, then added with exact uint64 atomics.
+// w: the N weights in Montgomery form (mont_mul(w_r, x) = w_r x mod p).
+template <int NB, int RB>
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    k_gram_tc(int64_t N, int m, int n, const uint32_t *__restrict__ w, const uint32_t *__restrict__ t, int yoff,
+              unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, int tmul, int toff,
+              int64_t L, ModP mp, int *__restrict__ err) {
+    using S = GramShape<NB, RB>;
+    constexpr int RW = RB / 4;  // residues per raw row
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, S::TN);
+    const int64_t k_term = term_counter ? (int64_t)tmul * *term_counter + toff : (int64_t)toff;
+    if (k_term < 0 || k_term >= L) return;  // the same for every block
+
+    extern __shared__ unsigned char gsm[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
+    unsigned char *raw = base + 2 * S::OPB;
+    uint64_t *bar_raw = reinterpret_cast<uint64_t *>(raw + GT_NS * S::RAWB);
+    uint64_t *bar_mma = bar_raw + GT_NS;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_mma + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tiles = (N + GT_KT - 1) / GT_KT;
+    const int64_t t_begin = tiles * blockIdx.x / gridDim.x;
+    const int64_t ntile = tiles * (blockIdx.x + 1) / gridDim.x - t_begin;
+
+    // both operand stages start at zero: digit rows of absent columns stay zero
+    for (uint32_t i = (uint32_t)tid * 16u; i < 2u * S::OPB; i += GT_THREADS * 16u)
+        *reinterpret_cast<uint4 *>(base + i) = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int s = 0; s < GT_NS; s++) tc::mbar_init(&bar_raw[s], 1);
+        tc::mbar_init(&bar_mma[0], 1);
+        tc::mbar_init(&bar_mma[1], 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, S::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int64_t issued = 0;  // raw tiles whose copies were issued (thread 0)
+    auto issue = [&](int64_t tl) {
+        const int s = (int)(tl % GT_NS);
+        const int64_t r0 = (t_begin + tl) * GT_KT;
+        const uint32_t rows = (uint32_t)min64(GT_KT, N - r0);
+        tc::mbar_arrive_expect_tx(&bar_raw[s], rows * (uint32_t)RB);
+        tc::bulk_g2s(raw + s * S::RAWB, t + r0 * RW, rows * (uint32_t)RB, &bar_raw[s]);
+    };
+    if (tid == 0) {
+        for (; issued < ntile && issued < GT_NS; issued++) issue(issued);
+    }
+
+    long long acc[NB];
+#pragma unroll
+    for (int b = 0; b < NB; b++) acc[b] = 0;
+    int64_t committed = 0;  // MMA commits (one per tile)
+    bool bad = false;       // this thread's waits
+    bool aborted = false;   // some thread's wait ran out (the same in every thread)
+
+    for (int64_t tl = 0; tl < ntile; tl++) {
+        const int sr = (int)(tl % GT_NS), so = (int)(tl & 1);
+        const int g = (int)(tl % GT_DRAIN);
+        unsigned char *opA = base + so * S::OPB, *opB = opA + S::ABYTES;
+        // the raw rows have landed; the operand stage's previous MMAs are done
+        if (!tc::mbar_wait(&bar_raw[sr], (uint32_t)((tl / GT_NS) & 1), GT_WAIT_NS)) bad = true;
+        if (tl >= 2 && !tc::mbar_wait(&bar_mma[so], (uint32_t)(((tl >> 1) - 1) & 1), GT_WAIT_NS)) bad = true;
+        const int64_t r0 = (t_begin + tl) * GT_KT;
+        const int rows = (int)min64(GT_KT, N - r0);
+        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + sr * S::RAWB);
+        {
+            // left factor: chunk c = warp (rows 8c .. 8c + 7), column a = lane, weighted
+            const int c = warp, a = lane;
+            if (a < m) {
+                uint32_t x[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int rr = 8 * c + u;
+                    x[u] = rr < rows ? mont_mul(__ldg(w + r0 + rr), rw[rr * RW + a], mp) : 0u;
+                }
+                put_digits(opA, a, 32, c, x);
+            }
+        }
+        if (tid < 8 * NB) {
+            // right factor: chunk c, column b
+            const int c = tid / NB, b = tid % NB;
+            if (b < n) {
+                uint32_t x[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int rr = 8 * c + u;
+                    x[u] = rr < rows ? rw[rr * RW + yoff + b] : 0u;
+                }
+                put_digits(opB, b, NB, c, x);
+            }
+        }
+        tc::fence_proxy_async_smem();
+        aborted = __syncthreads_or(bad) != 0;
+        if (tid == 0 && !aborted) {
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_addr(opA), b0 = tc::smem_addr(opB);
+#pragma unroll
+            for (int ks = 0; ks < GT_KT / 16; ks++)
+                tc::mma_bf16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
+                             (ks > 0 || g > 0) ? 1u : 0u);
+            tc::mma_commit(&bar_mma[so]);
+            committed++;
+            // the raw stage of this tile is free again (every thread is past the barrier)
+            if (issued < ntile) {
+                tc::fence_proxy_async_smem();
+                issue(issued);
+                issued++;
+            }
+        }
+        if (aborted) break;
+        if (g == GT_DRAIN - 1 || tl == ntile - 1) {
+            // drain: the accumulator of this group into the int64 sums
+            if (!tc::mbar_wait(&bar_mma[so], (uint32_t)((tl >> 1) & 1), GT_WAIT_NS)) bad = true;
+            tc::tc_fence_after();
+            if (warp < 4) {
+#pragma unroll
+                for (int ch = 0; ch < S::TN / 32; ch++) {
+                    uint32_t v[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int cc = 0; cc < 32; cc++) {
+                        const int col = ch * 32 + cc, j = col / NB, b = col % NB;
+                        acc[b] += (long long)__float2int_rn(__uint_as_float(v[cc])) << (8 * j);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            aborted = __syncthreads_or(bad) != 0;
+            if (aborted) break;
+        }
+    }
+
+    if (aborted) {
+        // record the error, let the copies and MMAs in flight finish (bounded)
+        if (tid == 0) {
+            atomicExch(err, GT_ERR_TIMEOUT);
+            for (int64_t tl = max64(0, issued - GT_NS); tl < issued; tl++)
+                tc::mbar_wait(&bar_raw[tl % GT_NS], (uint32_t)((tl / GT_NS) & 1), GT_WAIT_NS);
+            if (committed > 0) {
+                const int64_t last = committed - 1;
+                tc::mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1), GT_WAIT_NS);
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+    } else {
+        // G[a][b] = sum_i 2^{8i} acc_i[a][b] mod p: per digit row reduced and
+        // scaled in the first four warps, summed over the digits below
+        uint32_t *red = reinterpret_cast<uint32_t *>(raw);
+        if (warp < 4) {
+            const uint32_t sc = powm(256u % mp.p, (uint32_t)warp, mp);  // 2^{8 warp} mod p
+#pragma unroll
+            for (int b = 0; b < NB; b++) red[(warp * 32 + lane) * NB + b] = mulm(red_s64(acc[b], mp), sc, mp);
+        }
+        __syncthreads();
+        unsigned long long *dst = s_raw + (size_t)k_term * m * n;
+        for (int e = tid; e < m * n; e += GT_THREADS) {
+            const int a = e / n, b = e % n;
+            unsigned long long v = 0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) v += red[(i * 32 + a) * NB + b];
+            const uint32_t r = red64(v, mp);
+            if (r) atomicAdd(dst + e, (unsigned long long)r);
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, S::TMEM_COLS);
+    }
+}
+
+template <int NB, int RB>
+wr_status launch_gram_tc_t(wr_ctx *ctx, int64_t N, int m, int n, const uint32_t *w, const uint32_t *t, int yoff,
+                           unsigned long long *s_raw, const int *term_counter, int tmul, int toff, int64_t L,
+                           const ModP &mp, int *err) {
+    using S = GramShape<NB, RB>;
+    static std::once_flag once[8];
+    static cudaError_t attr_err[8];
+    const int dev = ctx->device & 7;
+    std::call_once(once[dev], [&] {
+        attr_err[dev] = cudaFuncSetAttribute(k_gram_tc<NB, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::SMEM);
+    });
+    WR_CUDA(attr_err[dev]);
+    const int64_t tiles = (N + GT_KT - 1) / GT_KT;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctx->num_sms);
+    if (grid == 0) return WR_OK;
+    k_gram_tc<NB, RB><<<grid, GT_THREADS, S::SMEM, ctx->stream>>>(N, m, n, w, t, yoff, s_raw, term_counter, tmul,
+                                                                  toff, L, mp, err);
+    WR_LAUNCHED(ctx);
+    return WR_OK;
+}
+
+// ------------------------------------------------------------------ tensor-core rate and layout probe
+//
+// Every block fills a 128 x 64 A tile and a PN x 64 B tile (bf16, the same
+// swizzled layout) with small integers, then one thread issues iters chains
+// of 4 MMAs (M = 128, N = PN, K = 64) into one accumulator and commits.  With
+// out != nullptr block 0 writes D (128 x PN fp32) after its MMAs: the layout
+// check compares it with the integer product of the same tiles.
+constexpr int PN = 256;
+
+__device__ __forceinline__ int probe_a(int r, int k) { return ((r * 7 + k * 3) % 17) - 8; }
+__device__ __forceinline__ int probe_b(int r, int k) { return ((r * 5 + k * 11) % 13) - 6; }
+
+__global__ void __launch_bounds__(128, 1) k_probe_mma(int64_t iters, float *__restrict__ out, int *__restrict__ err) {
+    extern __shared__ unsigned char psm[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(psm) + 1023) & ~uintptr_t(1023));
+    unsigned char *A = base, *B = base + 128 * 128;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(B + PN * 128);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int e = tid; e < 128 * 64; e += 128) {
+        const int r = e / 64, k = e % 64;
+        *reinterpret_cast<unsigned short *>(A + tc::sw128_chunk(r, k / 8) + (k % 8) * 2) =
+            (unsigned short)(__float_as_uint((float)probe_a(r, k)) >> 16);
+    }
+    for (int e = tid; e < PN * 64; e += 128) {
+        const int r = e / 64, k = e % 64;
+        *reinterpret_cast<unsigned short *>(B + tc::sw128_chunk(r, k / 8) + (k % 8) * 2) =
+            (unsigned short)(__float_as_uint((float)probe_b(r, k)) >> 16);
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, PN);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *slot;
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, PN);
+    if (tid == 0) {
+        const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+        for (int64_t it = 0; it < iters; it++)
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++)
+                tc::mma_bf16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
+                             (it > 0 || ks > 0) ? 1u : 0u);
+        tc::mma_commit(bar);
+    }
+    const bool ok = tc::mbar_wait(bar, 0, GT_WAIT_NS);
+    if (!ok && tid == 0) atomicExch(err, GT_ERR_TIMEOUT);
+    tc::tc_fence_after();
+    if (ok && out && blockIdx.x == 0) {
+        for (int ch = 0; ch < PN / 32; ch++) {
+            uint32_t v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+            tc::tmem_ld_wait();
+            for (int cc = 0; cc < 32; cc++) out[(size_t)(warp * 32 + (tid & 31)) * PN + ch * 32 + cc] = __uint_as_float(v[cc]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, PN);
+    }
+}
+
+}  // namespace
+
+bool gram_tc_supported(int m, int n, int tstride, int yoff) {
+    if (m < 1 || m > 32 || n < 1 || n > 32) return false;
+    const int rb = 4 * tstride;
+    if (rb != 32 && rb != 64 && rb != 128 && rb != 256) return false;
+    const int nb = n <= 8 ? 8 : (n <= 16 ? 16 : 32);
+    if (m > tstride || yoff + n > tstride) return false;
+    if (nb == 8 && rb > 64) return false;
+    if (nb == 16 && (rb < 64 || rb > 128)) return false;
+    if (nb == 32 && rb < 128) return false;
+    return true;
+}
+
+wr_status launch_gram_tc(wr_ctx *ctx, int64_t N, int m, int n, const uint32_t *w, const uint32_t *t, int tstride,
+                         int yoff, unsigned long long *s_raw, const int *term_counter, int tmul, int toff, int64_t L,
+                         const ModP &mp, int *err) {
+    if (!gram_tc_supported(m, n, tstride, yoff)) return fail(WR_EINVAL, "tensor-core Gram: unsupported shape");
+    if (N <= 0) return WR_OK;
+    const int rb = 4 * tstride;
+    const int nb = n <= 8 ? 8 : (n <= 16 ? 16 : 32);
+#define WR_GT(NBV, RBV)                                                                                        \
+    if (nb == NBV && rb == RBV)                                                                                \
+        return launch_gram_tc_t<NBV, RBV>(ctx, N, m, n, w, t, yoff, s_raw, term_counter, tmul, toff, L, mp, err);
+    WR_GT(8, 32)
+    WR_GT(8, 64)
+    WR_GT(16, 64)
+    WR_GT(16, 128)
+    WR_GT(32, 128)
+    WR_GT(32, 256)
+#undef WR_GT
+    return fail(WR_EINVAL, "tensor-core Gram: unsupported shape");
+}
+
+wr_status probe_mma(wr_ctx *ctx, int64_t iters, int blocks, float *d_out, double *ms) {
+    // (more shared memory than the tiles need: one block per SM)
+    const size_t smem = std::max<size_t>(1024 + 128 * 128 + PN * 128 + 64, 120 * 1024);
+    WR_CUDA(cudaFuncSetAttribute(k_probe_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DevBuf err;
+    WR_TRY(dev_alloc(ctx, err, sizeof(int)));
+    WR_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), ctx->stream));
+    cudaEvent_t e0, e1;
+    WR_CUDA(cudaEventCreate(&e0));
+    WR_CUDA(cudaEventCreate(&e1));
+    WR_CUDA(cudaEventRecord(e0, ctx->stream));
+    k_probe_mma<<<blocks, 128, smem, ctx->stream>>>(iters, d_out, err.as<int>());
+    WR_LAUNCHED(ctx);
+    WR_CUDA(cudaEventRecord(e1, ctx->stream));
+    WR_CUDA(cudaEventSynchronize(e1));
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int h = 0;
+    WR_CUDA(cudaMemcpy(&h, err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(WR_ETIMEDOUT, "tensor-core probe: an MMA wait ran out");
+    return WR_OK;
+}
+
+}  // namespace wr

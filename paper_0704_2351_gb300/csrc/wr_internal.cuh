@@ -361,6 +361,7 @@ struct wr_ctx {
     bool autotune = true;   // tune the SpMM lane width per matrix and block width
     int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
     bool pair_generic = true; // generic projection, m = n: X and Y in one block, two terms per application
+    int tensor_proj = -1;   // Gram projections on the tensor cores: 1 on, 0 off, -1 automatic
     bool pipeline = true;   // wr_rank: the sigma-basis trails the sequence on a second stream
     int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
     bool chain_reduce = false; // matrix loads: remove unit singleton rows/columns and empty ones
@@ -388,7 +389,7 @@ struct wr_matrix {
     wr::Sell at;   // rows of A^T
     // SpMM residues per lane tuned for [layout a / at][log2 block width] (0: not yet)
     mutable std::mutex tune_mu;
-    mutable int tuned_w[2][6] = {{0}};
+    mutable int tuned_w[2][7] = {{0}};
 };
 
 struct wr_result {
@@ -430,10 +431,21 @@ wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, con
 wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n);
 
 // sequence (wr_spmm.cu)
+// Optional exports of the iterated block (the matrix's row order, unscaled:
+// [A~^k X | A~^k Y] with the paired block, A~^k Y otherwise): after `snap_at`
+// applications into d_snap, after the last one into d_last (either may be null).
+struct StateOut {
+    int64_t snap_at = -1;
+    uint32_t *d_snap = nullptr;
+    uint32_t *d_last = nullptr;
+    int64_t applications = 0;  // written: applications done
+    bool paired = false;       // written: whether the block carried X beside Y
+};
 wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r, int s,
                       int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C);
 wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
-                       uint32_t *d_S, double *setup_ms, double *seq_ms, SeqFeed *feed = nullptr);
+                       uint32_t *d_S, double *setup_ms, double *seq_ms, SeqFeed *feed = nullptr,
+                       StateOut *out = nullptr);
 // Make the context's stream wait until S_0 .. S_{terms-1} of the fed sequence
 // are final (blocks the host until the producer has recorded that far).
 wr_status feed_wait(wr_ctx *ctx, SeqFeed *feed, int64_t terms);
@@ -442,6 +454,15 @@ wr_status make_child(const wr_ctx *parent, wr_ctx **out);
 void copy_settings(const wr_ctx *parent, wr_ctx *child);
 wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                          const uint32_t *d_in, uint32_t *d_out, int64_t width);
+// tensor-core Gram products (wr_gram_tc.cu): S_raw[k] += sum_r w_r t[r][0..m)^T
+// t[r][yoff..yoff+n) mod p, w in Montgomery form, k = tmul * counter + toff
+bool gram_tc_supported(int m, int n, int tstride, int yoff);
+wr_status launch_gram_tc(wr_ctx *ctx, int64_t N, int m, int n, const uint32_t *w, const uint32_t *t, int tstride,
+                         int yoff, unsigned long long *s_raw, const int *term_counter, int tmul, int toff, int64_t L,
+                         const ModP &mp, int *err);
+wr_status probe_mma(wr_ctx *ctx, int64_t iters, int blocks, float *d_out, double *ms);
+wr_status gram_device(wr_ctx *ctx, uint32_t p, int64_t N, int m, int n, const uint32_t *t, int tstride, int yoff,
+                      const uint32_t *w, uint32_t *G);
 wr_status blackbox_apply_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                                  const uint32_t *d_in, uint32_t *d_out, int64_t width);
 
@@ -483,8 +504,11 @@ struct Resolved {
     const uint32_t *nmap = nullptr, *mmap = nullptr;
 };
 wr_status resolve(const wr_matrix *mat, const wr_params *prm, Resolved &r);
+
 wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,
-                                double *setup_ms, double *seq_ms, SeqFeed *feed = nullptr);
+                                double *setup_ms, double *seq_ms, SeqFeed *feed = nullptr, StateOut *out = nullptr);
+// whether the generic projection pairs X with Y in one block (m = n)
+bool pairs_generic(const wr_ctx *ctx, const Resolved &r);
 
 int padded_width(int n);
 

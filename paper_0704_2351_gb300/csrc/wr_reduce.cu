@@ -202,8 +202,9 @@ wr_status locality_order_host(int64_t rows, int64_t cols, const int64_t *rowptr,
     return WR_OK;
 }
 
-// Chain reduction along a complex (Section 2.6.4: "elimination in one matrix
-// can propagate on the others").  mats[i] has the cells of mats[i+1]'s rows
+// Chain reduction along a complex (Section 2.6.4, where a pivot taken in one
+// boundary matrix also removes lines of the neighbouring ones).  mats[i] has
+// the cells of mats[i+1]'s rows
 // as its columns and mats[i] mats[i+1] = 0 over Z.  A unit pivot at (r, c) of
 // mats[i] is removed as above (rank offset + 1) and, in the neighbours, the
 // line of each shared cell goes too: column r of mats[i-1], row c of
@@ -367,21 +368,33 @@ wr_status chain_reduce_complex_host(int count, wr_csr_io *io) {
             }
         }
     }
-    // compact each matrix: live rows and columns that still hold an entry
+    // Compact each matrix.  A cell between mats[i] and mats[i+1] (a column of
+    // the one, a row of the other) is kept in both while it is live and holds
+    // an entry on either side, so that the reduced matrices still compose
+    // (out_cols of mats[i] = out_rows of mats[i+1]) and the reduction can run
+    // again on its own output; the outer lines (rows of the first matrix,
+    // columns of the last) are kept when live and not empty.
+    std::vector<std::vector<char>> keep(count > 1 ? count - 1 : 0);
+    for (int i = 0; i + 1 < count; i++) {
+        const ChainMat &a = M[i], &b = M[i + 1];
+        keep[i].assign(a.cols, 0);
+        for (int64_t c = 0; c < a.cols; c++)
+            keep[i][c] = !a.cdead[c] && !b.rdead[c] && (a.ccnt[c] > 0 || b.rcnt[c] > 0);
+    }
     for (int i = 0; i < count; i++) {
         ChainMat &a = M[i];
         wr_csr_io &o = io[i];
         std::vector<int32_t> cnew(a.cols, -1);
         int64_t nc = 0;
         for (int64_t j = 0; j < a.cols; j++)
-            if (!a.cdead[j] && a.ccnt[j] > 0) {
+            if (i + 1 < count ? keep[i][j] != 0 : (!a.cdead[j] && a.ccnt[j] > 0)) {
                 if (o.out_col_of) o.out_col_of[nc] = (int32_t)j;
                 cnew[j] = (int32_t)nc++;
             }
         int64_t nr = 0, w = 0;
         o.out_rowptr[0] = 0;
         for (int64_t r = 0; r < a.rows; r++) {
-            if (a.rdead[r] || a.rcnt[r] == 0) continue;
+            if (i > 0 ? keep[i - 1][r] == 0 : (a.rdead[r] || a.rcnt[r] == 0)) continue;
             for (int64_t e = a.rp[r]; e < a.rp[r + 1]; e++)
                 if (a.va[e] != 0 && cnew[a.ci[e]] >= 0) {
                     o.out_colidx[w] = cnew[a.ci[e]];

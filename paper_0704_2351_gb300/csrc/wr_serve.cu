@@ -35,7 +35,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
 // readout (after both are released).
 size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
     // the paired generic block (m = n) runs the SpMM at twice the width
-    const bool pairable = !r.symmetric && r.m == r.n && 2 * r.nv <= 32;
+    const bool pairable = !r.symmetric && r.m == r.n && 2 * r.nv <= 64;
     const size_t L = (size_t)r.L, m = (size_t)r.m, n = (size_t)r.n, q = m + n,
                  nv = (size_t)r.nv * (pairable ? 2 : 1);
     const size_t N = (size_t)r.N, M = (size_t)r.M;

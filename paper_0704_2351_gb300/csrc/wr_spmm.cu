@@ -423,6 +423,25 @@ __global__ void k_unpad(int64_t N, int width, int nv, const uint32_t *__restrict
     out[g * width + b] = in[r * nv + b];
 }
 
+// The iterated block in the matrix's row order, unscaled (T = D1 V): from the
+// paired block [D1 A~^k X | D1 A~^k Y] the N x (m + n) block [A~^k X | A~^k Y],
+// otherwise A~^k Y (N x n).
+__global__ void k_export_state(int64_t N, int m, int n, int nv, int paired, const uint32_t *__restrict__ T,
+                               const uint32_t *__restrict__ d1, uint32_t *__restrict__ out,
+                               const uint32_t *__restrict__ nmap, ModP mp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t dinv = invm(d1[i], mp);
+    const int64_t g = nmap ? (int64_t)nmap[i] : i;
+    const int tw = paired ? 2 * nv : nv, w = paired ? m + n : n;
+    if (paired) {
+        for (int a = 0; a < m; a++) out[g * w + a] = mulm(dinv, T[i * tw + a], mp);
+        for (int b = 0; b < n; b++) out[g * w + m + b] = mulm(dinv, T[i * tw + nv + b], mp);
+    } else {
+        for (int b = 0; b < n; b++) out[g * w + b] = mulm(dinv, T[i * tw + b], mp);
+    }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <int NV, int WL>
@@ -446,14 +465,19 @@ wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
                         int *term_counter, int wl, bool finalize = true) {
     const int vblocks_any = (A.nseg + A.nchunks) > 0 || term_counter;
     switch (wl) {
-        case 1: launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter); break;
+        case 1:
+            if constexpr (NV <= 32) { launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            else return fail(WR_EINVAL, "lane width too small for the block width");
         case 2:
             if constexpr (NV % 2 == 0) { launch_spmm_kernel<NV, 2>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         case 4:
             if constexpr (NV % 4 == 0) { launch_spmm_kernel<NV, 4>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
-        default: return fail(WR_EINVAL, "lane width must be 1, 2 or 4");
+        case 8:
+            if constexpr (NV % 8 == 0) { launch_spmm_kernel<NV, 8>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            else return fail(WR_EINVAL, "lane width does not divide the block width");
+        default: return fail(WR_EINVAL, "lane width must be 1, 2, 4 or 8");
     }
     if (vblocks_any) WR_LAUNCHED(ctx);
     if (finalize && A.nsplit > 0) {
@@ -470,7 +494,7 @@ wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
 wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
                       const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
                       int *term_counter, int wl = 0, bool finalize = true) {
-    if (wl <= 0 || wl > nv) wl = default_lane_width(nv);
+    if (wl <= 0 || wl > nv || nv / wl > 32) wl = default_lane_width(nv);
     switch (nv) {
         case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
         case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
@@ -478,12 +502,13 @@ wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x,
         case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
         case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
         case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 64: return launch_spmm_t<64>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
         default: return fail(WR_EINVAL, "unsupported padded block width");
     }
 }
 
-// Lane-width tuner: times the candidate residues-per-lane (1, 2, 4) of one
-// SpMM layout on the matrix itself (zero block: the gather addresses, which
+// Lane-width tuner: times the candidate residues-per-lane (1, 2, 4, 8; at
+// most 32 lanes per gathered row) of one SpMM layout on the matrix itself (zero block: the gather addresses, which
 // set the time, do not depend on the values) and keeps the fastest.  The
 // result never depends on the choice.
 int nv_index(int nv) {
@@ -510,7 +535,7 @@ static wr_status tune_lane_width(wr_ctx *ctx, const Sell &S, int nv, int *out) {
     WR_CUDA(cudaEventCreate(&e0));
     WR_CUDA(cudaEventCreate(&e1));
     float best = 0.0f;
-    for (int wl : {1, 2, 4}) {
+    for (int wl : {1, 2, 4, 8}) {
         if (wl > nv || nv % wl != 0 || nv / wl > 32) continue;
         for (int w = 0; w < 2; w++)
             WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
@@ -536,7 +561,7 @@ static wr_status tune_lane_width(wr_ctx *ctx, const Sell &S, int nv, int *out) {
 // the lane width for a layout: forced by the context, else tuned once per
 // matrix, layout and block width (when the context tunes), else the default
 static wr_status lane_width_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S, int nv, int *out) {
-    if (ctx->lane_width > 0 && ctx->lane_width <= nv && nv % ctx->lane_width == 0) {
+    if (ctx->lane_width > 0 && ctx->lane_width <= nv && nv % ctx->lane_width == 0 && nv / ctx->lane_width <= 32) {
         *out = ctx->lane_width;
         return WR_OK;
     }
@@ -608,8 +633,26 @@ struct SeqState {
     const Sell *first = nullptr;   // pass 1 layout (output in the other space)
     const Sell *second = nullptr;  // pass 2 layout (output in N-space)
     int wl1 = 0, wl2 = 0;          // residues per lane of the two passes
-    DevBuf T, Wb, D1, D2, d1sq, xh, w2, acc1, acc2, s_raw, counter;
+    DevBuf T, Wb, D1, D2, d1sq, xh, w2, acc1, acc2, s_raw, counter, err;
 };
+
+// A Gram projection S_raw[tmul * counter + toff] += sum_r w_r t[r][0..m)^T
+// t[r][yoff..yoff+n): on the tensor cores (bf16 digit products, exact) when
+// the context asks for them, or automatically for blocks of 16 columns and
+// more; otherwise with 64-bit integer multiply-adds.  Same result either way.
+static bool use_tc_gram(const wr_ctx *ctx, int m, int n, int tstride, int yoff) {
+    if (ctx->tensor_proj == 0 || !gram_tc_supported(m, n, tstride, yoff)) return false;
+    return ctx->tensor_proj == 1 || (m >= 16 && n >= 16);
+}
+
+static wr_status launch_gram(wr_ctx *ctx, SeqState &st, int64_t rows, const uint32_t *w, const uint32_t *t,
+                             int tmul, int toff, int tstride, int yoff) {
+    if (use_tc_gram(ctx, st.r.m, st.r.n, tstride, yoff))
+        return launch_gram_tc(ctx, rows, st.r.m, st.r.n, w, t, tstride, yoff, st.s_raw.as<unsigned long long>(),
+                              st.counter.as<int>(), tmul, toff, st.r.L, st.mp, st.err.as<int>());
+    return launch_project(ctx, rows, st.r.m, st.r.n, st.r.nv, w, t, st.s_raw.as<unsigned long long>(),
+                          st.counter.as<int>(), st.mp, true, tmul, toff, st.r.L, tstride, yoff);
+}
 
 static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r, SeqState &st,
                            bool want_projection) {
@@ -629,7 +672,9 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
     WR_TRY(dev_alloc(ctx, st.acc1, sizeof(unsigned long long) * std::max<int64_t>(st.first->nsplit * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.acc2, sizeof(unsigned long long) * std::max<int64_t>(st.second->nsplit * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.counter, sizeof(int)));
+    WR_TRY(dev_alloc(ctx, st.err, sizeof(int)));
     cudaStream_t s = ctx->stream;
+    WR_CUDA(cudaMemsetAsync(st.err.ptr, 0, sizeof(int), s));
     WR_CUDA(cudaMemsetAsync(st.acc1.ptr, 0, st.acc1.bytes, s));
     WR_CUDA(cudaMemsetAsync(st.acc2.ptr, 0, st.acc2.bytes, s));
     WR_CUDA(cudaMemsetAsync(st.counter.ptr, 0, sizeof(int), s));
@@ -680,13 +725,9 @@ static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
                        st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
     if (st.r.gram || st.r.paired) {
-        const int pv = st.r.nv, ts = nv, yo = st.r.paired ? st.r.nv : 0;
-        WR_TRY(launch_project(ctx, st.r.M, st.r.m, st.r.n, pv, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(),
-                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, -1,
-                              st.r.L, ts, yo));
-        WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, pv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
-                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, true, 2, 0,
-                              st.r.L, ts, yo));
+        const int ts = nv, yo = st.r.paired ? st.r.nv : 0;
+        WR_TRY(launch_gram(ctx, st, st.r.M, st.w2.as<uint32_t>(), st.Wb.as<uint32_t>(), 2, -1, ts, yo));
+        WR_TRY(launch_gram(ctx, st, st.r.N, st.xh.as<uint32_t>(), st.T.as<uint32_t>(), 2, 0, ts, yo));
     } else {
         WR_TRY(launch_project(ctx, st.r.N, st.r.m, st.r.n, nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
                               st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, false, 1, 0,
@@ -701,18 +742,23 @@ static double spmm_pass_bytes(const Sell &s, int nv, int64_t nnz) {
     return 4.0 * (double)nnz + 4.0 * nv * (double)(s.ncols + s.nrows) + 4.0 * (double)s.nrows;
 }
 
+// generic projection with m = n: A~ is symmetric, so with U_k = A~^k X and
+// V_k = A~^k Y, S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k);
+// X and Y ride in one block of twice the width (up to 64 residues per row),
+// two terms per application
+bool pairs_generic(const wr_ctx *ctx, const Resolved &r) {
+    return !r.symmetric && r.m == r.n && 2 * r.nv <= 64 && ctx->pair_generic;
+}
+
 wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, int64_t L,
-                       uint32_t *d_S, double *setup_ms, double *seq_ms, SeqFeed *feed) {
+                       uint32_t *d_S, double *setup_ms, double *seq_ms, SeqFeed *feed, StateOut *out) {
     Resolved r;
     WR_TRY(resolve(mat, &prm, r));
-    // generic projection with m = n: A~ is symmetric, so with U_k = A~^k X and
-    // V_k = A~^k Y, S_2k = U_k^T V_k and S_2k+1 = (A D1 U_k)^T D2 (A D1 V_k);
-    // X and Y ride in one block of twice the width, two terms per application
-    if (!r.symmetric && r.m == r.n && 2 * r.nv <= 32 && ctx->pair_generic) {
+    if (pairs_generic(ctx, r)) {
         r.paired = true;
         r.nvs = 2 * r.nv;
     }
-    return run_sequence_resolved(ctx, mat, r, L, d_S, setup_ms, seq_ms, feed);
+    return run_sequence_resolved(ctx, mat, r, L, d_S, setup_ms, seq_ms, feed, out);
 }
 
 // Terms final after `done` applications (the initial projection gives S_0).
@@ -742,8 +788,17 @@ static wr_status publish_terms(wr_ctx *ctx, SeqState &st, int64_t from, int64_t 
     return WR_OK;
 }
 
+static wr_status export_state(wr_ctx *ctx, const SeqState &st, uint32_t *dst) {
+    if (!dst || st.r.N <= 0) return WR_OK;
+    k_export_state<<<blocks_for(st.r.N, 128), 128, 0, ctx->stream>>>(st.r.N, st.r.m, st.r.n, st.r.nv,
+                                                                      st.r.paired ? 1 : 0, st.T.as<uint32_t>(),
+                                                                      st.D1.as<uint32_t>(), dst, st.r.nmap, st.mp);
+    WR_LAUNCHED(ctx);
+    return WR_OK;
+}
+
 wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, int64_t L, uint32_t *d_S,
-                                double *setup_ms, double *seq_ms, SeqFeed *feed) {
+                                double *setup_ms, double *seq_ms, SeqFeed *feed, StateOut *out) {
     r.L = L;
     cudaStream_t s = ctx->stream;
     cudaEvent_t e0, e1, e2;
@@ -756,10 +811,16 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     const int64_t E = (int64_t)r.m * r.n;
     WR_TRY(dev_alloc(ctx, st.s_raw, sizeof(unsigned long long) * std::max<int64_t>(L * E, 1)));
     WR_CUDA(cudaMemsetAsync(st.s_raw.ptr, 0, st.s_raw.bytes, s));
-    if (L > 0)
-        WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
-                              st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, r.gram || r.paired,
-                              (r.gram || r.paired) ? 2 : 1, 0, L, r.nvs, r.paired ? r.nv : 0));
+    if (L > 0) {
+        if (r.gram || r.paired)
+            WR_TRY(launch_gram(ctx, st, r.N, st.xh.as<uint32_t>(), st.T.as<uint32_t>(), 2, 0, r.nvs,
+                               r.paired ? r.nv : 0));
+        else
+            WR_TRY(launch_project(ctx, r.N, r.m, r.n, r.nv, st.xh.as<uint32_t>(), st.T.as<uint32_t>(),
+                                  st.s_raw.as<unsigned long long>(), st.counter.as<int>(), st.mp, false, 1, 0, L,
+                                  r.nvs, 0));
+    }
+    if (out && out->snap_at == 0) WR_TRY(export_state(ctx, st, out->d_snap));
     int64_t published = 0;
     if (feed) {
         WR_TRY(publish_terms(ctx, st, 0, terms_ready(r, 0, L), d_S, feed));
@@ -808,7 +869,9 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
             }
             if (published >= feed->stop_at.load()) break;
         }
-        const int64_t todo = std::min(G, iters - done);
+        // a snapshot of the block ends the group at its application count
+        const int64_t lim = (out && out->d_snap && out->snap_at > done) ? std::min(out->snap_at, iters) : iters;
+        const int64_t todo = std::min(G, lim - done);
         if (todo == G && exec && !(ctx->profiling && group % PROF_EVERY == 0)) {
             cudaError_t ce = cudaGraphLaunch(exec, s);
             if (ce != cudaSuccess) loop_st = cuda_fail(ce, "cudaGraphLaunch");
@@ -833,6 +896,7 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
         }
         done += todo;
         group++;
+        if (out && out->d_snap && done == out->snap_at && loop_st == WR_OK) loop_st = export_state(ctx, st, out->d_snap);
         if (feed && loop_st == WR_OK) {
             const int64_t t = terms_ready(r, done, L);
             loop_st = publish_terms(ctx, st, published, t, d_S, feed);
@@ -843,16 +907,29 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     if (graph) cudaGraphDestroy(graph);
     for (auto &e : pev) cudaEventDestroy(e);
     WR_TRY(loop_st);
+    if (out) {
+        WR_TRY(export_state(ctx, st, out->d_last));
+        out->applications = done;
+        out->paired = r.paired;
+    }
     if (!feed && L * E > 0) {
         k_reduce_seq<<<blocks_for(L * E, 256), 256, 0, s>>>(L * E, st.s_raw.as<unsigned long long>(), d_S,
                                                            st.mp);
         WR_LAUNCHED(ctx);
     }
+    int herr = 0;
+    WR_CUDA(cudaMemcpyAsync(&herr, st.err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     WR_CUDA(cudaEventRecord(e2, s));
     WR_CUDA(cudaEventSynchronize(e2));
     float a = 0, b = 0;
     cudaEventElapsedTime(&a, e0, e1);
     cudaEventElapsedTime(&b, e1, e2);
+    if (herr) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        return fail(WR_ETIMEDOUT, "tensor-core projection: a bounded wait ran out");
+    }
     if (setup_ms) *setup_ms = a;
     if (seq_ms) *seq_ms = b;
     ctx->last.sequence_terms = feed ? published : L;
@@ -861,6 +938,51 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
+    return WR_OK;
+}
+
+__global__ void k_to_mont_vec(int64_t len, const uint32_t *__restrict__ in, uint32_t *__restrict__ out, ModP mp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = to_mont(in[i], mp);
+}
+
+// G (m x n) = sum_r w_r t[r][0..m)^T t[r][yoff..yoff+n) mod p, through the
+// same kernels as the sequence's Gram projections
+wr_status gram_device(wr_ctx *ctx, uint32_t p, int64_t N, int m, int n, const uint32_t *t, int tstride, int yoff,
+                      const uint32_t *w, uint32_t *G) {
+    if (m < 1 || m > 32 || n < 1 || n > 32) return fail(WR_EINVAL, "m and n must be in 1..32");
+    const int nv = padded_width(n);
+    if (N < 0 || tstride < m || yoff < 0 || yoff % nv != 0 || tstride % nv != 0 || yoff + nv > tstride)
+        return fail(WR_EINVAL, "rows of t: tstride residues, a multiple of the padded width nv >= m and >= yoff + nv, "
+                               "yoff a multiple of nv");
+    if (reinterpret_cast<uintptr_t>(t) % 16 != 0) return fail(WR_EINVAL, "t must be 16-byte aligned");
+    SeqState st;
+    st.mp = make_modp(p);
+    st.r.m = m;
+    st.r.n = n;
+    st.r.nv = nv;
+    st.r.L = 1;
+    cudaStream_t s = ctx->stream;
+    DevBuf wm;
+    WR_TRY(dev_alloc(ctx, wm, sizeof(uint32_t) * std::max<int64_t>(N, 1)));
+    WR_TRY(dev_alloc(ctx, st.s_raw, sizeof(unsigned long long) * m * n));
+    WR_TRY(dev_alloc(ctx, st.counter, sizeof(int)));
+    WR_TRY(dev_alloc(ctx, st.err, sizeof(int)));
+    WR_CUDA(cudaMemsetAsync(st.s_raw.ptr, 0, st.s_raw.bytes, s));
+    WR_CUDA(cudaMemsetAsync(st.counter.ptr, 0, sizeof(int), s));
+    WR_CUDA(cudaMemsetAsync(st.err.ptr, 0, sizeof(int), s));
+    if (N > 0) {
+        k_to_mont_vec<<<blocks_for(N, 256), 256, 0, s>>>(N, w, wm.as<uint32_t>(), st.mp);
+        WR_LAUNCHED(ctx);
+        WR_TRY(launch_gram(ctx, st, N, wm.as<uint32_t>(), t, 1, 0, tstride, yoff));
+    }
+    k_reduce_seq<<<blocks_for((int64_t)m * n, 256), 256, 0, s>>>((int64_t)m * n, st.s_raw.as<unsigned long long>(),
+                                                                G, st.mp);
+    WR_LAUNCHED(ctx);
+    int herr = 0;
+    WR_CUDA(cudaMemcpyAsync(&herr, st.err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(WR_ETIMEDOUT, "tensor-core projection: a bounded wait ran out");
     return WR_OK;
 }
 
@@ -918,19 +1040,53 @@ namespace wr {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = sizeof(wr_noalloc_scratch);
 
-// Device address of the scratch array, looked up once per device (the first
-// call on a device does it, with that device current).
+// Device address of the scratch array, looked up once per device and
+// context (the first call on a device does it, with that device current).
+// The address belongs to the device's primary context: if the caller resets
+// the device (cudaDeviceReset), the context that follows gets a new copy of
+// the array, so the lookup is keyed by the context's unique ID (cuCtxGetId,
+// through the runtime's driver entry points) and repeated when it changes.
+// Where that ID is not available the address is looked up on every call.
 static void *g_noalloc_addr[128];
+static unsigned long long g_noalloc_ctx[128];
 static std::mutex g_noalloc_mu;
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// unique ID of the calling thread's current context, 0 if unknown
+static unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    void *c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == 0 && c && get_id(c, &id) == 0) return id;
+    return 0;
+}
 
 static wr_status noalloc_scratch_address(int device, void **out) {
     if (device < 0 || device >= 128) return fail(WR_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
+    const unsigned long long id = current_context_id();
+    if (!g_noalloc_addr[device] || id == 0 || g_noalloc_ctx[device] != id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, wr_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
         g_noalloc_addr[device] = p;
+        g_noalloc_ctx[device] = current_context_id();  // the context exists now
     }
     *out = g_noalloc_addr[device];
     return WR_OK;

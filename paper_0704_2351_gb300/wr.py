@@ -84,6 +84,10 @@ _sig = {
     "wr_set_allocator": ([vp, vp, vp, vp], ctypes.c_int),
     "wr_set_lane_width": ([vp, i32], ctypes.c_int),
     "wr_set_paired_projection": ([vp, i32], ctypes.c_int),
+    "wr_set_tensor_projection": ([vp, i32], ctypes.c_int),
+    "wr_sequence_state_device": ([vp, vp, P(wr_params), vp, u64, i64, vp, vp, P(i64), P(i32)], ctypes.c_int),
+    "wr_gram_device": ([vp, u32, i64, u32, u32, vp, i32, i32, vp, vp], ctypes.c_int),
+    "wr_probe_mma": ([vp, i64, i32, vp, P(ctypes.c_double)], ctypes.c_int),
     "wr_set_pipeline": ([vp, i32], ctypes.c_int),
     "wr_set_early_termination": ([vp, i64], ctypes.c_int),
     "wr_set_chain_reduction": ([vp, i32], ctypes.c_int),
@@ -255,6 +259,10 @@ def wr_set_lane_width(ctx: int, residues: int) -> None:
     _check(_lib.wr_set_lane_width(vp(ctx), residues))
 
 
+def wr_set_tensor_projection(ctx: int, mode: int) -> None:
+    _check(_lib.wr_set_tensor_projection(vp(ctx), mode))
+
+
 def wr_set_paired_projection(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_paired_projection(vp(ctx), 1 if on else 0))
 
@@ -409,6 +417,27 @@ def wr_blackbox_apply_device_noalloc(ctx: int, mat: int, params: wr_params, d_in
 
 def wr_sequence_device(ctx: int, mat: int, params: wr_params, d_S, L: int) -> None:
     _check(_lib.wr_sequence_device(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_S)), L))
+
+
+def wr_sequence_state_device(ctx: int, mat: int, params: wr_params, d_S, L: int, snap_at: int = -1,
+                             d_snap=None, d_last=None):
+    """Returns (applications, paired)."""
+    k, pr = i64(), i32()
+    _check(_lib.wr_sequence_state_device(vp(ctx), vp(mat), ctypes.byref(params), vp(_dptr(d_S)), L, snap_at,
+                                         vp(_dptr(d_snap)), vp(_dptr(d_last)), ctypes.byref(k), ctypes.byref(pr)))
+    return k.value, bool(pr.value)
+
+
+def wr_gram_device(ctx: int, prime: int, N: int, m: int, n: int, d_t, tstride: int, yoff: int, d_w, d_G) -> None:
+    _check(_lib.wr_gram_device(vp(ctx), prime, N, m, n, vp(_dptr(d_t)), tstride, yoff, vp(_dptr(d_w)),
+                               vp(_dptr(d_G))))
+
+
+def wr_probe_mma(ctx: int, iters: int, blocks: int, d_out=None) -> float:
+    """Kernel time in ms of the tensor-core probe (see include/wr.h)."""
+    ms = ctypes.c_double()
+    _check(_lib.wr_probe_mma(vp(ctx), iters, blocks, vp(_dptr(d_out)), ctypes.byref(ms)))
+    return ms.value
 
 
 def wr_sequence_slab_device(ctx: int, mat: int, params: wr_params, col0: int, ncols: int, d_S, L: int) -> None:

@@ -149,14 +149,18 @@ def test_complex_reduction_keeps_every_rank(wr, seed):
         for p in [3, 65521, 1073741789]:
             assert oracle.rank_dense(A.to_dense(), p) == off + oracle.rank_dense(R.to_dense(), p), p
         assert off + oracle.rank_dense(R.to_dense(), 1073741789) == A.rank
-    # the reduced pair still composes to zero: kept rows of d_n times kept
-    # columns of d_n+1 over the cells kept in both (a cell kept in one only
-    # is an empty line there, which adds nothing to the product)
-    _, rof_n, cof_n, _ = _reduced(out[0])
-    _, rof_n1, cof_n1, _ = _reduced(out[1])
-    common = np.intersect1d(cof_n, rof_n1)
-    prod = d_n.to_dense()[np.ix_(rof_n, common)] @ d_n1.to_dense()[np.ix_(common, cof_n1)]
-    assert not prod.any()
+    # the reduced pair is still a complex over the same cells: d_n keeps as
+    # columns exactly the cells d_n+1 keeps as rows, and the product is zero
+    R_n, rof_n, cof_n, _ = _reduced(out[0])
+    R_n1, rof_n1, cof_n1, off_n1 = _reduced(out[1])
+    assert R_n.cols == R_n1.rows and np.array_equal(cof_n, rof_n1)
+    assert not (R_n.to_dense() @ R_n1.to_dense()).any()
+    # so the reduction runs again on its own output, and finds nothing more
+    again = wr.wr_chain_reduce_complex([_csr_tuple(R_n), _csr_tuple(R_n1)])
+    for R, t in zip([R_n, R_n1], again):
+        R2, _, _, off2 = _reduced(t)
+        assert off2 == 0 and (R2.rows, R2.cols) == (R.rows, R.cols)
+        assert np.array_equal(R2.to_dense(), R.to_dense())
 
 
 def test_complex_reduction_propagates_beyond_the_single_matrix_pass(wr):

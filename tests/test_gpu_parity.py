@@ -219,7 +219,7 @@ def test_sequence_symmetric_two_terms_per_application(wr, ctx, n, L, side, p):
 
 
 @pytest.mark.parametrize("n,L,side", [(1, 41, 0), (1, 40, 1), (3, 57, 0), (8, 97, 0), (8, 96, 1), (16, 33, 1),
-                                      (4, 1, 0), (4, 2, 1), (4, 3, 0)])
+                                      (4, 1, 0), (4, 2, 1), (4, 3, 0), (32, 65, 0), (32, 64, 1), (24, 29, 1)])
 @pytest.mark.parametrize("p", [65521, 2147483629])
 def test_sequence_generic_paired_two_terms_per_application(wr, ctx, n, L, side, p):
     """Generic projection with m = n: the GPU carries [D1 X | D1 Y] as one
@@ -444,17 +444,18 @@ def test_sharded_sequence_single_rank_gpu(wr, ctx):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("n", [1, 2, 8, 32])
-def test_lane_widths_give_identical_sequences(wr, ctx, n):
-    """Every SpMM lane width (1, 2, 4 residues per lane where it divides the
-    block width) gives the oracle's sequence; the autotuner only picks
-    among them."""
-    p, m, seed, L = 2147483629, min(n, 4), 5, 40
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 2), (4, 8), (4, 32), (32, 32)])
+def test_lane_widths_give_identical_sequences(wr, ctx, m, n):
+    """Every SpMM lane width (1, 2, 4, 8 residues per lane where it divides
+    the block width, at most 32 lanes per row) gives the oracle's sequence;
+    the autotuner only picks among them.  m = n = 32 runs the paired block of
+    width 64."""
+    p, seed, L = 2147483629, 5, 40
     A = heavy_matrix(900, 820, seed=41 + n, heavy=3, heavy_len=500)
     st = oracle.Setup(A, p, m, n, seed)
     S_ref = oracle.sequence(A, st, L)
     try:
-        for wl in [1, 2, 4]:
+        for wl in [1, 2, 4, 8]:
             if wl > n or n % wl:
                 continue
             wr.wr_set_lane_width(ctx, wl)
@@ -687,11 +688,50 @@ def _annihilates(S, F, delta, p, i):
     return True
 
 
-def test_config1_full_size(wr, ctx):
+def _deep_step_check(wr, ctx, A, mat, st, seed, k):
+    """Spot check of the graph-replayed loop at depth k (Section 2.5 step 2,
+    two terms per application of the symmetric A~, Section 2.3).  The GPU runs
+    k + 1 applications of the paired block [D1 X | D1 Y] and exports the block
+    after k of them, [U_k | V_k] = [A~^k X | A~^k Y], and after k + 1.  From
+    [U_k | V_k] the oracle recomputes S_2k = U_k^T V_k, the next block
+    [A~ U_k | A~ V_k], S_2k+1 = U_k^T A~ V_k and S_2k+2 = (A~ U_k)^T (A~ V_k),
+    which must equal the GPU's own terms and block bit for bit."""
+    p, m, n, N = st.p, st.m, st.n, st.N
+    L = 2 * k + 3
+    prm = wr.make_params(p, m, n, seed)
+    dS = torch.empty((L, m, n), dtype=torch.int32, device="cuda")
+    snap = torch.empty((N, m + n), dtype=torch.int32, device="cuda")
+    last = torch.empty((N, m + n), dtype=torch.int32, device="cuda")
+    apps, paired = wr.wr_sequence_state_device(ctx, mat, prm, dS, L, k, snap, last)
+    assert paired and apps == k + 1
+    S = from_dev(dS)
+    UV = from_dev(snap)
+    if k == 0:
+        assert np.array_equal(UV[:, :m], st.X) and np.array_equal(UV[:, m:], st.Y)
+    assert np.array_equal(oracle.project(UV[:, :m], UV[:, m:], p), S[2 * k])
+    nxt = oracle.blackbox_apply(A, p, st.side, st.D1, st.D2, UV)
+    assert np.array_equal(from_dev(last), nxt)
+    assert np.array_equal(oracle.project(UV[:, :m], np.ascontiguousarray(nxt[:, m:]), p), S[2 * k + 1])
+    assert np.array_equal(oracle.project(np.ascontiguousarray(nxt[:, :m]), np.ascontiguousarray(nxt[:, m:]), p),
+                          S[2 * k + 2])
+    return S
+
+
+@pytest.fixture(scope="module")
+def config1():
+    return synth.config1()
+
+
+@pytest.fixture(scope="module")
+def config2():
+    return synth.config2()
+
+
+def test_config1_full_size(wr, ctx, config1):
     """200,000 x 180,000, block 8 x 8, p = 1073741789: planted rank, the first
     terms against the oracle, the generator annihilates the sequence at
     sampled offsets, and one black-box application at full size."""
-    A = synth.config1()
+    A = config1
     p, m, n, seed = synth.PRIME_C1, 8, 8, synth.SEED_BASE + 1
     g = gpu_rank(wr, ctx, A, p, m, n, seed, want=3)
     assert g["rank"] == A.rank == 170000
@@ -711,27 +751,68 @@ def test_config1_full_size(wr, ctx):
     wr.wr_matrix_free(mat)
 
 
+@pytest.mark.parametrize("k", [0, 1000, 20001, 22499])
+def test_config1_deep_steps(wr, ctx, config1, k):
+    """Config 1 at depth k of its 22,501 applications (k = 22,499: the last
+    graph group is partial), each step checked by the oracle from the GPU's
+    own block; the terms S_2k .. S_2k+2 also sit in the full wr_rank sequence."""
+    A = config1
+    p, m, n, seed = synth.PRIME_C1, 8, 8, synth.SEED_BASE + 1
+    st = oracle.Setup(A, p, m, n, seed)
+    mat = load(wr, ctx, A)
+    try:
+        _deep_step_check(wr, ctx, A, mat, st, seed, k)
+    finally:
+        wr.wr_matrix_free(mat)
+
+
 # ------------------------------------------------------------------ full size: config 2
 
-def test_config2_full_size_spot_checks(wr, ctx):
-    """1,900,000 x 1,950,000, ~37M nnz, block 32 x 32, p = 2147483629 (rows
+def test_config2_full_size_spot_checks(wr, ctx, config2):
+    """1,900,000 x 1,950,000, ~40.7M nnz, block 32 x 32, p = 2147483629 (rows
     side, N = 1.9M): one black-box application at full size checked on 64
-    sampled output rows computed one by one, and the first two terms of the
-    sequence against the oracle's literal loop."""
-    A = synth.config2()
+    sampled output rows computed one by one, the first three terms of the
+    sequence against the oracle's literal loop, and the loop at depth 0 and
+    4,100 (paired block of width 64, Gram projections on the tensor cores)
+    checked step by step against the oracle."""
+    A = config2
     p, m, n, seed = 2147483629, 32, 32, synth.SEED_BASE + 2
     st = oracle.Setup(A, p, m, n, seed)
     assert st.side == 1 and st.N == 1900000
     mat = load(wr, ctx, A)
-    rng = np.random.default_rng(2)
-    v = rng.integers(0, p, size=(st.N, n)).astype(np.uint32)
-    dout = torch.empty((st.N, n), dtype=torch.int32, device="cuda")
-    wr.wr_blackbox_apply_device(ctx, mat, wr.make_params(p, 1, n, seed), to_dev(v), dout, n)
-    got = from_dev(dout)
-    rows = np.sort(rng.choice(st.N, 64, replace=False))
-    assert np.array_equal(got[rows], oracle.blackbox_apply_rows(A, p, st.side, st.D1, st.D2, v, rows))
-    L = 2
-    dS = torch.empty((L, m, n), dtype=torch.int32, device="cuda")
-    wr.wr_sequence_device(ctx, mat, wr.make_params(p, m, n, seed), dS, L)
-    assert np.array_equal(from_dev(dS).reshape(L, m, n), oracle.sequence(A, st, L))
-    wr.wr_matrix_free(mat)
+    try:
+        rng = np.random.default_rng(2)
+        v = rng.integers(0, p, size=(st.N, n)).astype(np.uint32)
+        dout = torch.empty((st.N, n), dtype=torch.int32, device="cuda")
+        wr.wr_blackbox_apply_device(ctx, mat, wr.make_params(p, 1, n, seed), to_dev(v), dout, n)
+        got = from_dev(dout)
+        rows = np.sort(rng.choice(st.N, 64, replace=False))
+        assert np.array_equal(got[rows], oracle.blackbox_apply_rows(A, p, st.side, st.D1, st.D2, v, rows))
+        del got, v, dout
+        S0 = _deep_step_check(wr, ctx, A, mat, st, seed, 0)
+        assert np.array_equal(S0, oracle.sequence(A, st, 3))
+        _deep_step_check(wr, ctx, A, mat, st, seed, 4100)
+    finally:
+        wr.wr_matrix_free(mat)
+
+
+def test_config2_rank(wr, ctx, config2):
+    """The one-prime time to rank of config 2: wr_rank over all L = 118,752
+    terms (59,376 applications of the width-64 paired block) and the M-Basis
+    at q = 64 gives the planted rank 1,805,000; the generator annihilates the
+    sequence at sampled offsets and the first terms equal the oracle's."""
+    A = config2
+    p, m, n, seed = 2147483629, 32, 32, synth.SEED_BASE + 2
+    wr.wr_set_profiling(ctx, True)
+    try:
+        g = gpu_rank(wr, ctx, A, p, m, n, seed, want=3)
+        tm = wr.wr_last_timings(ctx)
+    finally:
+        wr.wr_set_profiling(ctx, False)
+    print("config 2 time to rank: %.1f s (sequence %.1f s, sigma-basis %.1f s, tail %.1f s)" % (
+        tm["total_ms"] / 1e3, tm["sequence_ms"] / 1e3, tm["sigma_ms"] / 1e3, tm["sigma_tail_ms"] / 1e3))
+    assert g["rank"] == A.rank == 1805000
+    assert g["seq_len"] == 118752
+    rng = np.random.default_rng(5)
+    for i in [0] + list(rng.integers(0, 50000, size=2)):
+        assert _annihilates(g["S"], g["F"], g["delta"], p, int(i))
