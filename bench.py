@@ -1,37 +1,46 @@
 """Benchmark of the block Wiedemann rank path on GB300.
 
-A step is one pass of the whole path over one synthetic matrix: CSR ingest
-and SELL-C-sigma layout on the device, preconditioner set-up, the black-box
-applications with their projections (L = 45,002 terms), the sigma-basis
-(trailing the sequence on a second stream) and the rank readout.  The
-workload is the 200,000 x 180,000 power-law matrix of planted rank 170,000,
-block 8 x 8, p = 1073741789.
+Default workload (one GPU): the K-theory-scale matrix sized after GL7d19
+(Table tab:res): 1,900,000 x 1,950,000, ~40.7M nnz (Poisson 19.5 per row,
+uniform columns), planted rank 1,805,000, block m = n = 32, p = 2147483629,
+L = 118,752 terms.
+
+A timed step is the next stretch of that sequence: TERMS_PER_STEP = 256 terms
+S_0 .. S_255, i.e. 128 applications of the preconditioned black box to the
+paired block [D1 X | D1 Y] (width 64) with both SpMM passes and the two Gram
+projections of each application (the captured 64-application graphs of the
+sequence loop), plus the sequence set-up (D1, D2, X, Y, T_0, S_0).  Inputs are
+resident in HBM (the matrix loaded once).  value = SpMM nnz*vec per second over
+the timed steps (2 passes x nnz x 64 block columns per application).  In the
+same run: the whole time to rank of the workload (ingest from pinned host CSR,
+all L terms, sigma-basis, readout; e2e), the secondary 200,000 x 180,000
+block-8 workload's time to rank, the roofline of k_spmm and the CPU oracle on
+a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wr|reference]
-                    [--projection generic|symmetric]
+                    [--matrix c2|c1] [--projection generic|symmetric] [--no-time-to-rank]
                     [--chain-reduction] [--locality-order] [--early-termination ORDERS]
-                    [--workload single|batch|serve] [--only-blackbox | --only-sigma]
+                    [--workload single|batch|serve] [--only-blackbox | --only-sigma | --probe-mma]
 
-One JSON line on rank 0.  value = SpMM nnz*vec processed per second over the
-whole step (2 passes x nnz x block columns per black-box application);
-ms_per_step = time to rank.  The generic projection (independent X, m = n)
-carries X and Y side by side: ceil((L - 1) / 2) applications to a block of
-width 2n, the same nnz*vec as L - 1 applications to Y alone, which is what
-value counts.  The symmetric one (X = Y) takes two terms per application of
-width n, so it applies the black box ceil((L - 1) / 2) times and its value
-counts only those.
---impl reference times the CPU oracle on the host cores on a bounded sample
-of the same workload (first terms of the sequence).
+With N > 1 (torchrun, one rank per GPU) every rank computes its column slab of
+Y (Section 3.1: column block j of S_i depends on Y_j only; wr_sequence_slab_device)
+for the same step terms, with no exchange while iterating, and the slabs are
+all-gathered once per step over NCCL (strong scaling: the step's terms are the
+same for every N).
+--impl reference times the CPU oracle on the host cores on a bounded sample of
+the same workload (one application per step).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -40,22 +49,49 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "mod-p SpMM nnz·vec/s, %HBM peak; batched/served vs plain time-to-rank (exact)"
-# DRAM bytes (read + write) per k_spmm launch in the warm loop, from one ncu
-# capture of this kernel: dram__bytes_read.sum + dram__bytes_write.sum, with
-# --cache-control none, launches 2000-2019 of
-# `python bench.py --steps 1 --warmup 0 --no-cpu-baseline` (both passes of the
-# paired width-16 block averaged; profiles/spmm_traffic_config1.md).
-SPMM_TRAFFIC_PER_LAUNCH = 4.0e6
 UNIT = "nnz*vec/s"
+TERMS_PER_STEP = 256
 
 
-def workload(rank: int):
+def workload(rank: int = 0, matrix: str = "c2"):
+    """The bench matrix and its parameters (seeded; rank > 0 only for the
+    independent-matrix mode)."""
     from paper_0704_2351_gb300 import synth
-    seed = synth.SEED_BASE + 1 + 1000 * rank
-    A = synth.config1(seed=seed)
-    return A, dict(p=synth.PRIME_C1, m=8, n=8, seed=seed, name=(
-        "power-law sparse matrix 200000x180000, %d nnz (20/row base, alpha 2.1 column degrees), planted rank "
-        "170000; block Wiedemann m=n=8 mod p=1073741789, L=45002" % A.nnz))
+    if matrix == "c1":
+        seed = synth.SEED_BASE + 1 + 1000 * rank
+        A = synth.config1(seed=seed)
+        return A, dict(p=synth.PRIME_C1, m=8, n=8, seed=seed, key="c1", name=(
+            "power-law sparse matrix 200000x180000, %d nnz (20/row base, alpha 2.1 column degrees), planted rank "
+            "170000; block Wiedemann m=n=8 mod p=1073741789, L=45002" % A.nnz))
+    seed = synth.SEED_BASE + 2 + 1000 * rank
+    A = synth.config2(seed=seed)
+    return A, dict(p=synth.PRIME_C2, m=32, n=32, seed=seed, key="c2", name=(
+        "K-theory-scale sparse matrix 1900000x1950000 (after GL7d19), %d nnz (Poisson 19.5/row, uniform "
+        "columns), planted rank 1805000; block Wiedemann m=n=32 mod p=2147483629, L=118752" % A.nnz))
+
+
+def spmm_traffic(kernel_file="paper_0704_2351_gb300/csrc/wr_spmm.cu",
+                 summary="profiles/spmm_traffic_config2.md"):
+    """DRAM bytes (read + write) per k_spmm launch on the bench workload, from
+    the committed ncu summary's line `traffic_bytes_per_launch: X source_sha256:
+    Y`; None when the SpMM source has changed since that capture (Y differs
+    from the current file's hash) or the summary is missing."""
+    try:
+        text = open(os.path.join(ROOT, summary)).read()
+        src = hashlib.sha256(open(os.path.join(ROOT, kernel_file), "rb").read()).hexdigest()
+    except OSError:
+        return None, "no summary"
+    for line in text.splitlines():
+        if line.strip().startswith("traffic_bytes_per_launch:"):
+            f = line.split()
+            try:
+                val, sha = float(f[1]), f[3]
+            except (IndexError, ValueError):
+                return None, "unparsable summary line"
+            if sha != src:
+                return None, "k_spmm source changed since the capture"
+            return val, summary
+    return None, "no traffic line in the summary"
 
 
 def apply_options(wr, ctx, args):
@@ -69,14 +105,6 @@ def options_config(args):
     return {"chain_reduction": bool(getattr(args, "chain_reduction", False)),
             "locality_order": bool(getattr(args, "locality_order", False)),
             "early_termination_orders": int(getattr(args, "early_termination", 0))}
-
-
-def applications(L, symmetric):
-    return (L // 2) if symmetric else (L - 1)
-
-
-def nnzvec_per_step(A, n, L, symmetric=False):
-    return 2.0 * A.nnz * n * applications(L, symmetric)
 
 
 def measured_peaks():
@@ -125,23 +153,31 @@ def stop_clock_sampler(proc, path, device):
             "samples": len(sm)}
 
 
-def cpu_baseline(A, cfg, budget_s=12.0, terms_cap=400):
+def cpu_baseline(A, cfg, budget_s=15.0, terms_cap=400):
     """The oracle as it stands, on the host's cores, over the first terms of
-    the same sequence (each term = one black-box application = 2 SpMM passes)."""
+    the same sequence (each term after S_0 = one black-box application = 2
+    sparse passes over Y alone), bounded to about budget_s seconds; the CPU
+    time of the whole L-term sequence is extrapolated from it (labelled)."""
     import oracle
     st = oracle.Setup(A, cfg["p"], cfg["m"], cfg["n"], cfg["seed"], symmetric=cfg.get("symmetric", False))
     t = time.perf_counter()
-    oracle.sequence(A, st, L=3)
-    per = max((time.perf_counter() - t) / 2, 1e-4)
-    terms = int(min(terms_cap, max(3, budget_s / per)))
-    t = time.perf_counter()
-    oracle.sequence(A, st, L=terms)
-    el = time.perf_counter() - t
+    oracle.sequence(A, st, L=2)
+    per = max(time.perf_counter() - t, 1e-4)
+    terms = int(min(terms_cap, max(2, budget_s / per)))
+    if terms == 2:  # one application already takes the budget: that run is the sample
+        el = per
+    else:
+        t = time.perf_counter()
+        oracle.sequence(A, st, L=terms)
+        el = time.perf_counter() - t
     cores = len(os.sched_getaffinity(0))
     v = 2.0 * A.nnz * cfg["n"] * (terms - 1) / el
+    L = oracle.seq_length(st.N, cfg["m"], cfg["n"])
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d terms of the same sequence (%d black-box applications, 2 sparse passes "
-                      "each, %.1f s)" % (terms, terms - 1, el)}
+            "sample": "first %d terms of the same sequence (%d black-box applications to Y, 2 sparse passes "
+                      "each, %.1f s)" % (terms, terms - 1, el),
+            "sequence_s_extrapolated": el / (terms - 1) * (L - 1),
+            "extrapolation": "x (L - 1) / %d applications, L = %d" % (terms - 1, L)}
 
 
 def gather_reference(A, n, reps=20):
@@ -182,15 +218,9 @@ def run_blackbox_only(args):
     library's CUDA-event samples and the algorithmic GB/s against the HBM
     peak."""
     import torch
-    from paper_0704_2351_gb300 import synth, wr
-    if args.matrix == "c2":
-        A = synth.config2()
-        p, n, seed = 2147483629, 32, synth.SEED_BASE + 2
-        name = ("1,900,000 x 1,950,000, %d nnz (Poisson 19.5 per row, uniform columns), block 32, "
-                "p = 2147483629" % A.nnz)
-    else:
-        A, cfg = workload(0)
-        p, n, seed, name = cfg["p"], cfg["n"], cfg["seed"], cfg["name"]
+    from paper_0704_2351_gb300 import wr
+    A, cfg = workload(0, args.matrix)
+    p, n, seed, name = cfg["p"], cfg["n"], cfg["seed"], cfg["name"]
     ctx = wr.wr_create(0)
     apply_options(wr, ctx, args)
     mat = wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals)
@@ -242,6 +272,7 @@ def run_batch(args):
     ctx = wr.wr_create(0)
     apply_options(wr, ctx, args)
     wr.wr_set_batch_slots(ctx, args.slots)
+    wr.wr_set_batch_fusion(ctx, not args.no_batch_fusion)
     handles = [wr.wr_matrix_load_csr(ctx, A.rows, A.cols, A.rowptr, A.colidx, A.vals) for A in mats]
     b = args.block
     jobs = [(i, p) for i in range(len(mats)) for p in primes]
@@ -273,6 +304,8 @@ def run_batch(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
             "config": {"pairs": args.pairs, "matrices": len(mats), "primes": primes, "jobs": len(jobs),
                        "block": [b, b], "slots": args.slots, "options": options_config(args),
+                       "fusion": "jobs on one matrix share one sequence loop (up to 4 primes per block)"
+                                 if not args.no_batch_fusion else "off",
                        "rows": [int(min(A.rows for A in mats)), int(max(A.rows for A in mats))],
                        "nnz_total": int(sum(A.nnz for A in mats))},
             "plain_s": t_plain, "batched_s": t_batch, "speedup": t_plain / t_batch,
@@ -416,17 +449,73 @@ def run_sigma_only(args):
     return 0
 
 
+def run_gram_only(args):
+    """The projection's Gram product alone on rows shaped as the default
+    workload's paired block (N = 1,900,000 rows of 64 residues, X half and Y
+    half of 32, p = 2147483629): wr_gram_device with the tensor-core path and
+    with the integer path, W + K calls each (for profiler captures of
+    k_gram_tc and its time per Gram)."""
+    import torch
+    from paper_0704_2351_gb300 import wr
+    p, m, n, N = 2147483629, 32, 32, args.gram_rows
+    g = torch.Generator().manual_seed(1)
+    t = torch.randint(0, p, (N, 64), generator=g, dtype=torch.int64).to(torch.int32).cuda()
+    w = torch.randint(1, p, (N,), generator=g, dtype=torch.int64).to(torch.int32).cuda()
+    G = torch.empty((m, n), dtype=torch.int32, device="cuda")
+    ctx = wr.wr_create(0)
+    out = {"only": "gram", "rows": N, "block": [m, n], "row_residues": 64}
+    for mode, name in [(1, "tensor_cores_ms"), (0, "integer_ms")]:
+        wr.wr_set_tensor_projection(ctx, mode)
+        for _ in range(args.warmup):
+            wr.wr_gram_device(ctx, p, N, m, n, t, 64, 32, w, G)
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        for _ in range(args.steps):
+            wr.wr_gram_device(ctx, p, N, m, n, t, 64, 32, w, G)
+        torch.cuda.synchronize()
+        out[name] = 1e3 * (time.perf_counter() - tt) / max(args.steps, 1)
+    print(json.dumps(out), flush=True)
+    wr.wr_destroy(ctx)
+    return 0
+
+
+def run_probe_mma(args):
+    """Tensor-core rate on this GPU: one block per SM issuing chains of bf16
+    tcgen05 MMAs (M = 128, N = 256, K = 16) on shared-memory tiles, fp32
+    accumulators in tensor memory (wr_probe_mma).  Prints dense bf16 TFLOP/s
+    and the measured cuBLAS peak beside it.  (The int8 kind of tcgen05.mma
+    does not exist for sm_103a: ptxas rejects it, so there is no int8 line.)"""
+    from paper_0704_2351_gb300 import wr
+    import torch
+    ctx = wr.wr_create(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    iters = 20000
+    wr.wr_probe_mma(ctx, 100, sms)
+    ms = min(wr.wr_probe_mma(ctx, iters, sms) for _ in range(5))
+    flops = 2.0 * 128 * 256 * 64 * iters * sms
+    peaks = measured_peaks()
+    print(json.dumps({"probe": "tcgen05 kind::f16 bf16 -> fp32, M=128 N=256 K=16, one block per SM",
+                      "blocks": sms, "iters": iters, "ms": ms, "tflops": flops / ms / 1e9,
+                      "cublas_bf16_tflops_measured": peaks.get("bf16_tflops")}), flush=True)
+    wr.wr_destroy(ctx)
+    return 0
+
+
 def run_reference(args):
+    """The CPU oracle as it stands on the host's cores, on the bench's
+    workload: each step is one application of the black box to Y (the first
+    terms of the same sequence, restarted every step), so that the whole run
+    stays within minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    A, cfg = workload(0)
+    A, cfg = workload(0, args.matrix)
     import oracle
     oracle.load()
     st = oracle.Setup(A, cfg["p"], cfg["m"], cfg["n"], cfg["seed"])
-    terms = 6
+    terms = 2
     for _ in range(args.warmup):
-        oracle.sequence(A, st, L=2)
+        oracle.sequence(A, st, L=terms)
     t = time.perf_counter()
     for _ in range(args.steps):
         oracle.sequence(A, st, L=terms)
@@ -436,9 +525,9 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": cfg["name"], "step": "first %d terms of the sequence "
-                                            "on the CPU oracle" % terms},
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": cfg["name"], "step": "S_0, S_1 of the sequence on the CPU "
+                                            "oracle (one black-box application to Y, 2 sparse passes)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d terms per step, %d steps" % (terms, args.steps)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -446,24 +535,56 @@ def run_reference(args):
     return 0
 
 
+def _time_to_rank_host(wr, ctx, A, params):
+    """wr_matrix_load_csr from pinned host arrays + wr_rank + the rank read
+    back: the whole job through the public API.  Returns (rank, seconds,
+    phase timings, host-to-device bytes)."""
+    import ctypes
+    import torch
+    from paper_0704_2351_gb300.wr import _lib, vp, _check
+    h_rp = torch.from_numpy(A.rowptr.astype(np.int64)).pin_memory()
+    h_ci = torch.from_numpy(A.colidx.astype(np.int32)).pin_memory()
+    h_va = torch.from_numpy(A.vals.astype(np.int32)).pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h = vp()
+    _check(_lib.wr_matrix_load_csr(vp(ctx), A.rows, A.cols, vp(h_rp.data_ptr()), vp(h_ci.data_ptr()),
+                                   vp(h_va.data_ptr()), ctypes.byref(h)))
+    res = wr.wr_rank(ctx, h.value, params)
+    r = wr.wr_result_rank(res)
+    el = time.perf_counter() - t
+    tm = wr.wr_last_timings(ctx)
+    wr.wr_result_free(res)
+    wr.wr_matrix_free(h.value)
+    h2d = 8 * (A.rows + 1) + 8 * A.nnz
+    return r, el, tm, h2d
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wr", choices=["wr", "reference"])
+    ap.add_argument("--matrix", default="c2", choices=["c2", "c1"],
+                    help="c2: the 1.9M x 1.95M block-32 matrix (default); c1: the 200,000 x 180,000 block-8 one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-rank", action="store_true",
+                    help="skip the whole time-to-rank runs (timed steps only)")
     ap.add_argument("--projection", default="generic", choices=["generic", "symmetric"])
+    ap.add_argument("--multi", default="slab", choices=["slab", "independent"],
+                    help="N > 1: column slabs of one sequence (default) or an independent matrix per rank")
     ap.add_argument("--only-blackbox", action="store_true",
                     help="only ingest + black-box applications (for profiler captures)")
-    ap.add_argument("--matrix", default="c1", choices=["c1", "c2"],
-                    help="--only-blackbox: the bench matrix (c1) or the 1.9M-row block-32 matrix (c2)")
     ap.add_argument("--only-sigma", action="store_true",
                     help="only the sigma-basis on a random sequence of the workload's shape")
+    ap.add_argument("--probe-mma", action="store_true", help="the tensor-core rate probe")
+    ap.add_argument("--only-gram", action="store_true", help="only the projection's Gram product (profiler captures)")
+    ap.add_argument("--gram-rows", type=int, default=1900000, help="--only-gram: rows of the block")
     ap.add_argument("--sigma-chunk", type=int, default=0, help="orders per sigma-basis chunk (0: automatic)")
     ap.add_argument("--sigma-leaf", type=int, default=0, help="orders per PM-Basis leaf (0: automatic)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
-                    help="single: the one-matrix time-to-rank line (default); batch / serve: batched or "
+                    help="single: the one-matrix line (default); batch / serve: batched or "
                          "served against plain time-to-rank")
     ap.add_argument("--pairs", type=int, default=64, help="batch: chain-complex pairs")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests in the trace")
@@ -471,6 +592,8 @@ def main():
     ap.add_argument("--rows-hi", type=int, default=500000, help="serve: largest row count")
     ap.add_argument("--block", type=int, default=0, help="batch / serve: block width m = n")
     ap.add_argument("--slots", type=int, default=8, help="batch / serve: concurrent slots")
+    ap.add_argument("--no-batch-fusion", action="store_true",
+                    help="batch: every job its own sequence loop (no sharing of the matrix passes)")
     ap.add_argument("--hbm-budget", type=int, default=0, help="serve: admission budget in bytes (0: none)")
     ap.add_argument("--chain-reduction", action="store_true",
                     help="remove unit singleton rows/columns at load (rank = pivots + rank of the rest)")
@@ -481,6 +604,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.probe_mma:
+        return run_probe_mma(args)
+    if args.only_gram:
+        return run_gram_only(args)
     if args.only_blackbox:
         return run_blackbox_only(args)
     if args.only_sigma:
@@ -491,7 +618,10 @@ def main():
     if args.workload == "serve":
         args.block = args.block or 16
         return run_serve(args)
+    return run_single(args)
 
+
+def run_single(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -501,101 +631,100 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_0704_2351_gb300 import wr
+    from paper_0704_2351_gb300 import shard, wr
 
-    A, cfg = workload(rank)
+    slab = world > 1 and args.multi == "slab"
+    A, cfg = workload(0 if slab else rank, args.matrix)
     p, m, n = cfg["p"], cfg["m"], cfg["n"]
     sym = args.projection == "symmetric"
     cfg["symmetric"] = sym
-    L = -(-A.cols // m) + -(-A.cols // n) + 2
-    work = nnzvec_per_step(A, n, L, sym)
+    N = min(A.rows, A.cols)
+    L_full = -(-N // m) + -(-N // n) + 2
+    T = TERMS_PER_STEP
     stream = torch.cuda.Stream()
     ctx = wr.wr_create(local, stream.cuda_stream)
     apply_options(wr, ctx, args)
-    params = wr.make_params(p, m, n, cfg["seed"],
-                            projection=wr.WR_PROJ_SYMMETRIC if sym else wr.WR_PROJ_GENERIC)
+    proj = wr.WR_PROJ_SYMMETRIC if sym else wr.WR_PROJ_GENERIC
+    params = wr.make_params(p, m, n, cfg["seed"], projection=proj)
     d_rp = torch.from_numpy(A.rowptr.astype(np.int64)).to("cuda")
     d_ci = torch.from_numpy(A.colidx.astype(np.int32)).to("cuda")
     d_va = torch.from_numpy(A.vals.astype(np.int32)).to("cuda")
+    mat = wr.wr_matrix_load_csr_device(ctx, A.rows, A.cols, A.nnz, d_rp, d_ci, d_va)
+    del d_rp, d_ci, d_va
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    if slab:
+        c0, w = shard.column_slab(n, rank, world)
+        dS = torch.empty((T, m, max(w, 1)), dtype=torch.int32, device="cuda")
+        apps = T - 1                      # one term per application of the slab
+        width = w
+    else:
+        dS = torch.empty((T, m, n), dtype=torch.int32, device="cuda")
+        paired = (not sym) and m == n
+        apps = (T - 1 + 1) // 2 if (paired or sym) else T - 1
+        width = 2 * n if paired else n
+    work_rank = 2.0 * A.nnz * width * apps  # nnz*vec of this rank per step
     torch.cuda.synchronize()
 
     def step():
-        mat = wr.wr_matrix_load_csr_device(ctx, A.rows, A.cols, A.nnz, d_rp, d_ci, d_va)
-        res = wr.wr_rank(ctx, mat, params)
-        r = wr.wr_result_rank(res)
-        wr.wr_result_free(res)
-        wr.wr_matrix_free(mat)
-        return r
+        if slab:
+            if w > 0:
+                wr.wr_sequence_slab_device(ctx, mat, params, c0, w, dS, T)
+        else:
+            wr.wr_sequence_device(ctx, mat, params, dS, T)
 
     for _ in range(args.warmup):
-        r = step()
-        assert r == A.rank, "rank %d != planted %d" % (r, A.rank)
+        step()
+    torch.cuda.synchronize()
 
     wr.wr_set_profiling(ctx, True)
-    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % rank)
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk_path = os.path.join(tempfile.gettempdir(), "wr_bench_clocks_%d_%d.csv" % (os.getpid(), rank))
     sampler = start_clock_sampler(clk_path)
     time.sleep(0.5)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = 0.0
-    spmm_ms = spmm_bytes = 0.0
+    total_ms = spmm_ms = spmm_bytes = 0.0
     spmm_launches = 0
-    phases = []
     launches0 = wr.wr_last_timings(ctx)["kernel_launches"]
+    gathered = None
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = step()
+        step()
+        if slab:
+            with torch.cuda.stream(stream):
+                gathered = shard.gather_columns(dS, n, world)
         e1.record(stream)
         e1.synchronize()
-        assert r == A.rank
         total_ms += e0.elapsed_time(e1)
         tm = wr.wr_last_timings(ctx)
         spmm_ms += tm["spmm_ms"]
         spmm_bytes += tm["spmm_bytes"]
         spmm_launches += tm["spmm_launches"]
-        phases.append({k: round(tm[k], 3) for k in ["setup_ms", "sequence_ms", "sigma_ms", "sigma_tail_ms", "readout_ms"]})
     torch.cuda.synchronize()
     launches = wr.wr_last_timings(ctx)["kernel_launches"] - launches0
     clocks = stop_clock_sampler(sampler, clk_path, local)
+    try:
+        os.remove(clk_path)
+    except OSError:
+        pass
     wr.wr_set_profiling(ctx, False)
     t_max = total_ms
     if dist:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    value = work * args.steps * world / (t_max * 1e-3)
+        wt = torch.tensor([work_rank], device="cuda", dtype=torch.float64)
+        dist.all_reduce(wt)
+        work_all = float(wt.item())
+    else:
+        work_all = work_rank
+    value = work_all * args.steps / (t_max * 1e-3)
 
-    # end to end through the C ABI from pinned host buffers
-    h_rp = torch.from_numpy(A.rowptr.astype(np.int64)).pin_memory()
-    h_ci = torch.from_numpy(A.colidx.astype(np.int32)).pin_memory()
-    h_va = torch.from_numpy(A.vals.astype(np.int32)).pin_memory()
-    from paper_0704_2351_gb300.wr import _lib, vp, _check
-    import ctypes
-    e2e_ms = 0.0
-    for _ in range(max(1, min(args.steps, 2))):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        h = vp()
-        _check(_lib.wr_matrix_load_csr(vp(ctx), A.rows, A.cols, vp(h_rp.data_ptr()), vp(h_ci.data_ptr()),
-                                       vp(h_va.data_ptr()), ctypes.byref(h)))
-        res = wr.wr_rank(ctx, h.value, params)
-        r = wr.wr_result_rank(res)
-        wr.wr_result_free(res)
-        wr.wr_matrix_free(h.value)
-        e2e_ms += 1e3 * (time.perf_counter() - t)
-        assert r == A.rank
-    e2e_steps = max(1, min(args.steps, 2))
-    e2e_value = work * world / (e2e_ms / e2e_steps * 1e-3)
-    h2d = 8 * (A.rows + 1) + 8 * A.nnz
-    d2h = 4 * n + 2 * 8 + 8 + 3 * 8  # column degrees, valuations, layout sizes, rank
-
+    # roofline of the dominant kernel (k_spmm), from the sampled launches of the timed steps
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
     roof = None
@@ -603,37 +732,61 @@ def main():
         avg_s = spmm_ms / spmm_launches * 1e-3
         per_launch = spmm_bytes / spmm_launches
         ach = per_launch / avg_s / 1e9
+        traffic, tsrc = spmm_traffic()
         roof = {"bound": "hbm", "achieved": ach, "peak": peak if peak else 6800.0, "unit": "GB/s",
-                "frac": ach / (peak if peak else 6800.0), "traffic": SPMM_TRAFFIC_PER_LAUNCH,
-                "traffic_note": "warm L2: the blocks and layouts stay resident beside the trailing sigma-basis "
-                                "state, so DRAM traffic (4.0 MB) is far below the algorithmic bytes; the pass "
-                                "is bound by random 64-byte gathers from L2",
-                "peak_source": "measured" if peak else "fallback",
+                "frac": ach / (peak if peak else 6800.0), "traffic": traffic, "traffic_source": tsrc,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "fallback",
                 "kernel": "k_spmm (both passes of the black box)", "avg_launch_us": avg_s * 1e6,
-                "bytes_per_launch": per_launch, "sampled_launches": spmm_launches}
+                "bytes_per_launch": per_launch, "sampled_launches": spmm_launches,
+                "bytes_definition": "4 B per stored entry + 4 B x block width per gathered and per written row "
+                                    "+ 4 B scale per written row (compulsory bytes of one pass)"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "block": [m, n], "prime": p, "seq_len": L,
+            "scaling": "strong" if slab else "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "block": [m, n], "prime": p, "seq_len": L_full,
                        "projection": args.projection,
-                       "applications": (L // 2) if (sym or m == n) else L - 1,
-                       "spmm_block_width": n if (sym or m != n) else 2 * n,
-                       "per_rank": "independent matrix per rank (seeded by rank), no collective on the data path",
-                       "l2": "working set below L2; a 256 MB buffer is written between timed steps",
-                       "options": options_config(args),
-                       "phases_ms": phases},
-            "roofline": roof,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_ms / e2e_steps},
-            "gpu_launches": launches, "clocks": clocks}
+                       "step": ("terms S_0..S_%d of the sequence: %d applications of the black box to a block of "
+                                "width %d with both SpMM passes and the projections, plus the sequence set-up"
+                                % (T - 1, apps, width)) + (
+                                    "; this rank's column slab [%d, %d) of Y, slabs all-gathered (NCCL) once per "
+                                    "step" % (c0, c0 + w) if slab else ""),
+                       "parallelism": ("column slabs of Y over %d GPUs" % world) if slab else (
+                           "independent matrix per rank" if world > 1 else "one GPU"),
+                       "l2": "inputs larger than L2 (block 1.9M x 256 B); a 256 MB buffer is also written between "
+                             "timed steps",
+                       "options": options_config(args)},
+            "roofline": roof, "gpu_launches": launches, "clocks": clocks}
+
+    # the whole job: time to rank through the public API from pinned host buffers
+    if rank == 0 and world == 1 and not args.no_time_to_rank:
+        r, el, tm, h2d = _time_to_rank_host(wr, ctx, A, params)
+        assert r == A.rank, "rank %d != planted %d" % (r, A.rank)
+        L = tm["sequence_terms"] or L_full
+        seq_work = 2.0 * A.nnz * n * (L - 1)
+        line["time_to_rank_ms"] = 1e3 * el
+        line["time_to_rank_phases_ms"] = {k: round(tm[k], 1) for k in
+                                          ["setup_ms", "sequence_ms", "sigma_ms", "sigma_tail_ms", "readout_ms"]}
+        line["rank"] = r
+        line["e2e"] = {"value": seq_work / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": 8, "ms_per_step": 1e3 * el,
+                       "step": "one whole rank computation: CSR ingest from pinned host memory, all %d terms, "
+                               "sigma-basis, readout; value = the sequence's nnz*vec / wall time" % L}
+        if args.matrix == "c2":
+            A1, cfg1 = workload(0, "c1")
+            prm1 = wr.make_params(cfg1["p"], cfg1["m"], cfg1["n"], cfg1["seed"])
+            _time_to_rank_host(wr, ctx, A1, prm1)  # first use of this matrix shape (tuner)
+            r1, el1, tm1, _ = _time_to_rank_host(wr, ctx, A1, prm1)
+            assert r1 == A1.rank
+            line["time_to_rank_config1_ms"] = 1e3 * el1
+            line["time_to_rank_config1_workload"] = cfg1["name"]
+    elif rank == 0:
+        line["e2e"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, cfg)
-    if rank == 0 and world == 1 and spmm_launches:
-        gref = gather_reference(A, n)
-        gref["k_spmm_avg_pass_us"] = spmm_ms / spmm_launches * 1e3
-        line["gather_ref"] = gref
     if rank == 0:
         print(json.dumps(line), flush=True)
+    wr.wr_matrix_free(mat)
     wr.wr_destroy(ctx)
     if dist:
         dist.destroy_process_group()

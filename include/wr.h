@@ -134,14 +134,20 @@ wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
  * transforms over three FFT primes and the CRT.  The result is the same basis
  * bit for bit; a leaf as large as the sequence turns PM-Basis off.  0
  * (default) = automatic: PM-Basis with 8,192-order leaves for sequences longer
- * than 131,072 orders when m + n <= 32, the blocked M-Basis otherwise. */
+ * than 131,072 orders when m + n <= 32, with 2,048-order leaves for sequences
+ * longer than 32,768 orders when m + n > 32, the blocked M-Basis otherwise.
+ * PM-Basis needs the whole sequence: with the pipeline (wr_set_pipeline) it
+ * starts when the sequence ends, where the M-Basis trails it chunk by chunk. */
 wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders);
 /* SpMM tile shape: the residues each lane gathers from a row of the dense
  * block (1, 2, 4 or 8; the row's n residues are spread over n / that many
- * lanes, at most 32).
+ * lanes, at most 32), plus 16 for the streaming cache hints (the matrix's
+ * entries and the output rows are loaded and stored evict-first, so that L2
+ * keeps rows of the gathered block).
  * With autotuning on (default), the first sequence or black-box application
- * on a matrix with at least 2^20 stored entries times each candidate on that
- * matrix's two layouts (a few launches each, CUDA events) and keeps the
+ * on a matrix with at least 2^20 stored entries times each candidate (every
+ * lane width, with and without the hints) on that matrix's two layouts (a few
+ * launches each, CUDA events) and keeps the
  * fastest, per matrix, layout and block width; smaller matrices and autotune
  * off use the default (2 residues for n <= 8, 4 above).  wr_set_lane_width
  * forces one (0 = tuned or default).  Results never depend on it. */
@@ -285,7 +291,7 @@ wr_status wr_rank(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr
 
 /* Many jobs in one call (matrices may repeat with different primes or seeds;
  * the paper's rank over Q takes the maximum over several primes, Section
- * 2.4).  Jobs run on the context's batch slots (wr_set_batch_slots, default
+ * 2.5).  Jobs run on the context's batch slots (wr_set_batch_slots, default
  * 8): each slot has its own stream and host thread, so the sequence loops and
  * sigma-basis kernels of several jobs are in flight on the device at once;
  * slots take the largest remaining job first.  Each job's result is
@@ -297,6 +303,17 @@ wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *const *mats,
                         const wr_params *params, wr_result **outs);
 /* Number of slots wr_rank_batch uses on this context (1..64). */
 wr_status wr_set_batch_slots(wr_ctx *ctx, int32_t slots);
+/* Job fusion in wr_rank_batch (on by default): jobs on the same matrix with
+ * the same m = n (at most 16), side, sequence length and outputs, and any
+ * primes and seeds (the rank over Q takes one matrix modulo several primes,
+ * Section 2.5), run in groups of up to four sharing one sequence loop: each
+ * job's X beside Y occupies a slice of one block of up to 64 columns, one
+ * pair of SpMM passes per application reads the matrix once for all of them
+ * (the exact int64 row sums do not depend on the prime; each slice is reduced
+ * modulo its own prime and scaled by its own diagonals), the Gram
+ * projections and sigma-bases run per job.  Each result is bit-identical to
+ * the job run alone.  Not used with early termination. */
+wr_status wr_set_batch_fusion(wr_ctx *ctx, int32_t on);
 /* Upper bound of the device memory one wr_rank call on (mat, params)
  * allocates besides the loaded matrix (the server's admission estimate). */
 wr_status wr_rank_device_bytes(const wr_ctx *ctx, const wr_matrix *mat, const wr_params *params,

@@ -244,8 +244,10 @@ extern "C" wr_status wr_set_autotune(wr_ctx *ctx, int32_t on) {
 
 extern "C" wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues) {
     if (!ctx) return fail(WR_EINVAL, "null context");
-    if (residues != 0 && residues != 1 && residues != 2 && residues != 4 && residues != 8)
-        return fail(WR_EINVAL, "lane width must be 0 (tuned or default), 1, 2, 4 or 8 residues");
+    const int w = residues & 15;
+    if ((residues & ~31) != 0 || (residues != 0 && w != 1 && w != 2 && w != 4 && w != 8))
+        return fail(WR_EINVAL, "lane width must be 0 (tuned or default) or 1, 2, 4 or 8 residues, plus 16 for the "
+                               "streaming cache hints");
     ctx->lane_width = residues;
     return WR_OK;
 }
@@ -516,6 +518,53 @@ wr_status feed_wait(wr_ctx *ctx, SeqFeed *feed, int64_t terms) {
     return WR_OK;
 }
 
+// The readout of a finished sigma-basis into res (Section 2.5 step 4), the
+// sequence copied back when wanted, and the Monte Carlo consistency checks.
+static wr_status finish_result(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r, const wr_params *params,
+                               const DevBuf &dS, const DevBuf &dP, const DevBuf &ddeg, int64_t Dcap, int64_t L_used,
+                               wr_result *res, double *readout_ms) {
+    Readout ro;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    WR_CUDA(cudaEventCreate(&e1));
+    WR_CUDA(cudaEventCreate(&e2));
+    cudaEventRecord(e1, ctx->stream);
+    wr_status st = rank_readout(ctx, dP.as<uint32_t>(), ddeg.as<int32_t>(), r.m, r.n, r.p, Dcap, ro,
+                                (params->want & WR_WANT_GENERATOR) ? &res->gen : nullptr);
+    if (st == WR_OK) {
+        cudaEventRecord(e2, ctx->stream);
+        cudaEventSynchronize(e2);
+        float b = 0;
+        cudaEventElapsedTime(&b, e1, e2);
+        if (readout_ms) *readout_ms = b;
+    }
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    WR_TRY(st);
+    res->seq_len = L_used;
+    if (params->want & WR_WANT_SEQUENCE) {
+        res->seq.resize((size_t)L_used * r.m * r.n);
+        cudaError_t e = cudaMemcpyAsync(res->seq.data(), dS.ptr, sizeof(uint32_t) * res->seq.size(),
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy sequence");
+    }
+    // Monte Carlo consistency: deg det F of a generator of X^T A~^i Y (A~ of
+    // order N) is at most N, and 0 <= codeg <= deg det F
+    if (ro.rank < 0 || ro.rank > r.N || ro.codeg < 0 || ro.deg_det > r.N)
+        return fail(WR_EPROBFAIL, "inconsistent readout (rank " + std::to_string(ro.rank) + ", codeg " +
+                                      std::to_string(ro.codeg) + ", deg det " + std::to_string(ro.deg_det) +
+                                      "); retry with another seed");
+    res->rank = mat->rank_offset + ro.rank;
+    res->deg_det = ro.deg_det;
+    res->codeg = ro.codeg;
+    res->sum_delta = ro.sum_delta;
+    if (params->want & WR_WANT_GENERATOR) {
+        res->gen_deg = ro.delta;
+        res->gen_dmax = ro.dmax;
+    }
+    return WR_OK;
+}
+
 wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out) {
     if (!ctx || !mat || !params || !out) return fail(WR_EINVAL, "null argument");
     *out = nullptr;
@@ -638,59 +687,100 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
         }
         sigma_ms = tail_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
-    Readout ro;
-    cudaEvent_t e1 = nullptr, e2 = nullptr;
-    if (st == WR_OK) {
-        cudaEventCreate(&e1);
-        cudaEventCreate(&e2);
-        cudaEventRecord(e1, ctx->stream);
-        st = rank_readout(ctx, dP.as<uint32_t>(), ddeg.as<int32_t>(), r.m, r.n, r.p, Dcap, ro,
-                          (params->want & WR_WANT_GENERATOR) ? &res->gen : nullptr);
-    }
-    if (st == WR_OK) {
-        cudaEventRecord(e2, ctx->stream);
-        cudaEventSynchronize(e2);
-        float b = 0;
-        cudaEventElapsedTime(&b, e1, e2);
-        ctx->last.setup_ms = setup_ms;
-        ctx->last.sequence_ms = seq_ms;
-        ctx->last.sigma_ms = sigma_ms;
-        ctx->last.sigma_tail_ms = tail_ms;
-        ctx->last.readout_ms = b;
-    }
-    if (e1) cudaEventDestroy(e1);
-    if (e2) cudaEventDestroy(e2);
-    res->seq_len = L_used;
-    if (st == WR_OK && (params->want & WR_WANT_SEQUENCE)) {
-        res->seq.resize((size_t)L_used * r.m * r.n);
-        cudaError_t e = cudaMemcpyAsync(res->seq.data(), dS.ptr, sizeof(uint32_t) * res->seq.size(),
-                                        cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) st = cuda_fail(e, "copy sequence");
-    }
+    double readout_ms = 0;
+    if (st == WR_OK) st = finish_result(ctx, mat, r, params, dS, dP, ddeg, Dcap, L_used, res, &readout_ms);
     if (st != WR_OK) {
         delete res;
         return st;
     }
-    // Monte Carlo consistency: deg det F of a generator of X^T A~^i Y (A~ of
-    // order N) is at most N, and 0 <= codeg <= deg det F
-    if (ro.rank < 0 || ro.rank > r.N || ro.codeg < 0 || ro.deg_det > r.N) {
-        delete res;
-        return fail(WR_EPROBFAIL, "inconsistent readout (rank " + std::to_string(ro.rank) + ", codeg " +
-                                      std::to_string(ro.codeg) + ", deg det " + std::to_string(ro.deg_det) +
-                                      "); retry with another seed");
-    }
-    res->rank = mat->rank_offset + ro.rank;
-    res->deg_det = ro.deg_det;
-    res->codeg = ro.codeg;
-    res->sum_delta = ro.sum_delta;
-    if (params->want & WR_WANT_GENERATOR) {
-        res->gen_deg = ro.delta;
-        res->gen_dmax = ro.dmax;
-    }
+    ctx->last.setup_ms = setup_ms;
+    ctx->last.sequence_ms = seq_ms;
+    ctx->last.sigma_ms = sigma_ms;
+    ctx->last.sigma_tail_ms = tail_ms;
+    ctx->last.readout_ms = readout_ms;
     ctx->last.total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     *out = res;
+    return WR_OK;
+}
+
+// Several jobs on one matrix (same m = n, side and length; any primes and
+// seeds, for the rank over Q by several primes, Section 2.5): one sequence
+// loop for all of them (run_sequence_multi), then each job's sigma-basis on a
+// stream of its own (concurrently), then each readout.  outs[g] receives job
+// g's result, bit-identical to rank_one's.
+wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *params, int G, wr_result **outs) {
+    if (!ctx || !mat || !params || !outs || G < 1 || G > MULTI_MAX_JOBS) return fail(WR_EINVAL, "bad multi-job call");
+    for (int g = 0; g < G; g++) outs[g] = nullptr;
+    WR_CUDA(cudaSetDevice(ctx->device));
+    std::vector<Resolved> rs(G);
+    for (int g = 0; g < G; g++) WR_TRY(resolve(mat, params[g], rs[g]));
+    const Resolved &r0 = rs[0];
+    if (r0.N == 0) {
+        for (int g = 0; g < G; g++) WR_TRY(rank_one(ctx, mat, params[g], &outs[g]));
+        return WR_OK;
+    }
+    const int64_t L = r0.L, Dcap = L + 1;
+    const int q = r0.m + r0.n;
+    std::vector<DevBuf> dS(G), dP(G), ddeg(G);
+    std::vector<uint32_t *> pS(G);
+    for (int g = 0; g < G; g++) {
+        WR_TRY(dev_alloc(ctx, dS[g], sizeof(uint32_t) * L * r0.m * r0.n));
+        WR_TRY(dev_alloc(ctx, dP[g], sizeof(uint32_t) * (Dcap + 1) * r0.n * q));
+        WR_TRY(dev_alloc(ctx, ddeg[g], sizeof(int32_t) * q));
+        pS[g] = dS[g].as<uint32_t>();
+    }
+    double seq_ms = 0;
+    WR_TRY(run_sequence_multi(ctx, mat, rs, pS, &seq_ms));
+    // the sigma-bases side by side, each on a child context of its own
+    std::vector<wr_ctx *> kids(G, nullptr);
+    wr_status st = WR_OK;
+    for (int g = 0; g < G && st == WR_OK; g++) {
+        st = make_child(ctx, &kids[g]);
+        if (st == WR_OK) copy_settings(ctx, kids[g]);
+    }
+    if (st == WR_OK) {
+        std::vector<wr_status> sst(G, WR_OK);
+        std::vector<std::string> smsg(G);
+        std::vector<std::thread> th;
+        for (int g = 0; g < G; g++)
+            th.emplace_back([&, g] {
+                cudaSetDevice(ctx->device);
+                sst[g] = sigma_basis(kids[g], pS[g], L, r0.m, r0.n, rs[g].p, dP[g].as<uint32_t>(),
+                                     ddeg[g].as<int32_t>(), Dcap);
+                if (sst[g] == WR_OK) {
+                    cudaError_t ce = sync_stream_blocking(kids[g]->stream);
+                    if (ce != cudaSuccess) sst[g] = cuda_fail(ce, "cudaStreamSynchronize");
+                }
+                if (sst[g] != WR_OK) smsg[g] = wr_last_error();
+            });
+        for (auto &t : th) t.join();
+        for (int g = 0; g < G && st == WR_OK; g++)
+            if (sst[g] != WR_OK) st = fail(sst[g], smsg[g]);
+    }
+    for (auto *k : kids)
+        if (k) {
+            ctx->launches += k->launches;
+            wr_destroy(k);
+        }
+    WR_TRY(st);
+    for (int g = 0; g < G; g++) {
+        wr_result *res = new wr_result();
+        res->prime = rs[g].p;
+        res->m = (uint32_t)r0.m;
+        res->n = (uint32_t)r0.n;
+        wr_status fs = finish_result(ctx, mat, rs[g], params[g], dS[g], dP[g], ddeg[g], Dcap, L, res, nullptr);
+        if (fs != WR_OK) {
+            delete res;
+            for (int h = 0; h < g; h++) {
+                delete outs[h];
+                outs[h] = nullptr;
+            }
+            return fs;
+        }
+        outs[g] = res;
+    }
+    ctx->last.sequence_ms = seq_ms;
     return WR_OK;
 }
 

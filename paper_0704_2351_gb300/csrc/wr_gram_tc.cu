@@ -21,7 +21,8 @@
 // drains its TMEM lane (digit i = warp, column a = lane) into exact int64 sums
 // acc[b] += sum_j 2^{8j} D[i*32 + a][j*NB + b], and at the end
 //   G[a][b] = sum_i 2^{8i} acc_i[a][b]  mod p.
-// The rows of t reach shared memory by 1-D bulk copies (four tiles in flight),
+// The rows of t and their weights reach shared memory by 1-D bulk copies
+// (two tiles in flight per block, two blocks per SM),
 // the threads rewrite them as digit tiles in the MMA's swizzled layout, and
 // one thread issues the MMAs and commits them to an mbarrier; operand tiles
 // are double-buffered.  Every wait is bounded: after WAIT_NS the block records
@@ -41,7 +42,7 @@ namespace {
 
 constexpr int GT_THREADS = 256;
 constexpr int GT_KT = 64;     // rows per tile
-constexpr int GT_NS = 4;      // raw tiles in flight
+constexpr int GT_NS = 2;      // raw tiles in flight per block (two blocks a SM)
 constexpr int GT_DRAIN = 8;   // tiles per drain of the accumulator (512 rows)
 constexpr uint64_t GT_WAIT_NS = 2000000000ull;
 constexpr int GT_ERR_TIMEOUT = 1;
@@ -54,7 +55,8 @@ struct GramShape {
     static constexpr uint32_t OPB = ABYTES + BBYTES;       // one operand stage
     static constexpr uint32_t RAWB = (uint32_t)GT_KT * RB; // one raw tile
     static constexpr uint32_t TMEM_COLS = TN < 32 ? 32 : TN;
-    static constexpr size_t SMEM = 1024 + 2 * (size_t)OPB + GT_NS * (size_t)RAWB + 128;
+    static constexpr uint32_t WB = (uint32_t)GT_KT * 4;   // one tile's weights
+    static constexpr size_t SMEM = 1024 + 2 * (size_t)OPB + GT_NS * ((size_t)RAWB + WB) + 128;
     static_assert(NB == 8 || NB == 16 || NB == 32, "NB");
     static_assert(RB % 16 == 0 && RB >= 32 && RB <= 256, "RB");
     static_assert(4u * 32u * NB * 4u <= GT_NS * RAWB, "reduction area");
@@ -99,9 +101,10 @@ __device__ __forceinline__ void put_digits(unsigned char *tile, int row0, int st
 
 // G into s_raw[k] (k = tmul * counter + toff; skipped unless 0 <= k < L): the
 // per-block result reduced mod p, then added with exact uint64 atomics.
-// w: the N weights in Montgomery form (mont_mul(w_r, x) = w_r x mod p).
+// w: the N weights in Montgomery form (mont_mul(w_r, x) = w_r x mod p); t and w
+// 16-byte aligned (bulk copies).
 template <int NB, int RB>
-__global__ void __launch_bounds__(GT_THREADS, 1)
+__global__ void __launch_bounds__(GT_THREADS, 2)
     k_gram_tc(int64_t N, int m, int n, const uint32_t *__restrict__ w, const uint32_t *__restrict__ t, int yoff,
               unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, int tmul, int toff,
               int64_t L, ModP mp, int *__restrict__ err) {
@@ -114,7 +117,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     extern __shared__ unsigned char gsm[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
     unsigned char *raw = base + 2 * S::OPB;
-    uint64_t *bar_raw = reinterpret_cast<uint64_t *>(raw + GT_NS * S::RAWB);
+    uint32_t *wts = reinterpret_cast<uint32_t *>(raw + GT_NS * S::RAWB);  // GT_NS x 64 weights
+    uint64_t *bar_raw = reinterpret_cast<uint64_t *>(wts + GT_NS * GT_KT);
     uint64_t *bar_mma = bar_raw + GT_NS;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_mma + 2);
 
@@ -147,8 +151,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         const int s = (int)(tl % GT_NS);
         const int64_t r0 = (t_begin + tl) * GT_KT;
         const uint32_t rows = (uint32_t)min64(GT_KT, N - r0);
-        tc::mbar_arrive_expect_tx(&bar_raw[s], rows * (uint32_t)RB);
+        const uint32_t wrows = rows & ~3u;  // whole 16-byte groups of weights; the rest by plain loads
+        tc::mbar_arrive_expect_tx(&bar_raw[s], rows * (uint32_t)RB + wrows * 4u);
         tc::bulk_g2s(raw + s * S::RAWB, t + r0 * RW, rows * (uint32_t)RB, &bar_raw[s]);
+        if (wrows) tc::bulk_g2s(wts + s * GT_KT, w + r0, wrows * 4u, &bar_raw[s]);
     };
     if (tid == 0) {
         for (; issued < ntile && issued < GT_NS; issued++) issue(issued);
@@ -171,6 +177,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         const int64_t r0 = (t_begin + tl) * GT_KT;
         const int rows = (int)min64(GT_KT, N - r0);
         const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + sr * S::RAWB);
+        const uint32_t *ws = wts + sr * GT_KT;
+        const int wrows = rows & ~3;
         {
             // left factor: chunk c = warp (rows 8c .. 8c + 7), column a = lane, weighted
             const int c = warp, a = lane;
@@ -179,7 +187,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
                     const int rr = 8 * c + u;
-                    x[u] = rr < rows ? mont_mul(__ldg(w + r0 + rr), rw[rr * RW + a], mp) : 0u;
+                    const uint32_t wv = rr < wrows ? ws[rr] : (rr < rows ? __ldg(w + r0 + rr) : 0u);
+                    x[u] = rr < rows ? mont_mul(wv, rw[rr * RW + a], mp) : 0u;
                 }
                 put_digits(opA, a, 32, c, x);
             }
@@ -294,7 +303,7 @@ wr_status launch_gram_tc_t(wr_ctx *ctx, int64_t N, int m, int n, const uint32_t 
     });
     WR_CUDA(attr_err[dev]);
     const int64_t tiles = (N + GT_KT - 1) / GT_KT;
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctx->num_sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, 2 * (int64_t)ctx->num_sms);  // two blocks a SM
     if (grid == 0) return WR_OK;
     k_gram_tc<NB, RB><<<grid, GT_THREADS, S::SMEM, ctx->stream>>>(N, m, n, w, t, yoff, s_raw, term_counter, tmul,
                                                                   toff, L, mp, err);

@@ -356,6 +356,7 @@ struct wr_ctx {
     bool profiling = false;
     int64_t launches = 0;   // kernels launched through this context (graph replays: nodes per replay)
     int batch_slots = 8;    // slots (streams + host threads) of wr_rank_batch
+    bool batch_fuse = true; // wr_rank_batch: jobs on one matrix share one sequence loop
     int sigma_chunk = 0;    // orders per sigma-basis chunk (0: automatic)
     int64_t sigma_leaf = 0; // orders per PM-Basis leaf (0: automatic)
     bool autotune = true;   // tune the SpMM lane width per matrix and block width
@@ -430,6 +431,18 @@ wr_status validate_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, con
                        const int32_t *d_colidx, const int32_t *d_vals, bool *wide);
 wr_status exclusive_scan_i64(wr_ctx *ctx, const int64_t *d_in, int64_t *d_out, int64_t n);
 
+// Several jobs on one matrix in one SpMM pass (wr_multi.cu): the block holds
+// `jobs` slices of 2^jw_log columns side by side, slice g reduced modulo
+// mp[g] and scaled by scale[g] in the epilogue (the exact int64 row sums do
+// not depend on the prime).
+constexpr int MULTI_MAX_JOBS = 4;
+struct MultiEpi {
+    int jobs = 1;
+    int jw_log = 0;
+    ModP mp[MULTI_MAX_JOBS];
+    const uint32_t *scale[MULTI_MAX_JOBS] = {nullptr, nullptr, nullptr, nullptr};
+};
+
 // sequence (wr_spmm.cu)
 // Optional exports of the iterated block (the matrix's row order, unscaled:
 // [A~^k X | A~^k Y] with the paired block, A~^k Y otherwise): after `snap_at`
@@ -463,6 +476,11 @@ wr_status launch_gram_tc(wr_ctx *ctx, int64_t N, int m, int n, const uint32_t *w
 wr_status probe_mma(wr_ctx *ctx, int64_t iters, int blocks, float *d_out, double *ms);
 wr_status gram_device(wr_ctx *ctx, uint32_t p, int64_t N, int m, int n, const uint32_t *t, int tstride, int yoff,
                       const uint32_t *w, uint32_t *G);
+// one SpMM pass of a multi-job block (nv = the whole block width; variant as
+// for the sequence: lane width, optionally | 16 for the streaming hints)
+wr_status launch_spmm_multi(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
+                            unsigned long long *acc64, const MultiEpi &me, int *term_counter, int variant);
+wr_status spmm_variant_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S, int nv, int *out);
 wr_status blackbox_apply_noalloc(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                                  const uint32_t *d_in, uint32_t *d_out, int64_t width);
 
@@ -511,5 +529,10 @@ wr_status run_sequence_resolved(wr_ctx *ctx, const wr_matrix *mat, Resolved r, i
 bool pairs_generic(const wr_ctx *ctx, const Resolved &r);
 
 int padded_width(int n);
+bool multi_eligible(const wr_ctx *ctx, const Resolved &r);
+int multi_max_jobs(const Resolved &r);
+// the sequences of 1..4 jobs on one matrix in one loop (same m = n, side, L)
+wr_status run_sequence_multi(wr_ctx *ctx, const wr_matrix *mat, const std::vector<Resolved> &rs,
+                             const std::vector<uint32_t *> &d_S, double *seq_ms);
 
 }  // namespace wr

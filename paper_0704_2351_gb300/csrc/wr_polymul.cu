@@ -16,8 +16,9 @@
 //
 // Transforms: forward decimation in frequency (natural order in, bit-reversed
 // out), pointwise products in that order, inverse decimation in time
-// (bit-reversed in, natural out); residues in Montgomery form; one launch per
-// butterfly stage over all polynomials of the batch.
+// (bit-reversed in, natural out); residues in Montgomery form; the stages
+// are grouped into passes through shared memory (two passes up to 2^17 points,
+// three up to 2^23), each one launch over all polynomials of the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -77,34 +78,79 @@ __global__ void k_ntt_load(const uint32_t *__restrict__ src, int64_t ncoef, int 
     }
 }
 
-// one stage of the forward transform (decimation in frequency): blocks of
-// length 2 half, butterfly (u, v) -> (u + v, (u - v) w^j), w^j = tw[j * step]
-__global__ void k_ntt_dif_stage(uint32_t *__restrict__ a, int64_t npoly, int64_t Lz, int64_t half, int64_t step,
-                                const uint32_t *__restrict__ tw, ModP mP) {
-    const int64_t nb = npoly * (Lz >> 1);
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nb; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t poly = x / (Lz >> 1), b = x - poly * (Lz >> 1);
-        const int64_t blk = b / half, j = b - blk * half;
-        uint32_t *p0 = a + poly * Lz + blk * 2 * half + j;
-        const uint32_t u = p0[0], v = p0[half];
-        p0[0] = addm(u, v, mP);
-        p0[half] = mont_mul(subm(u, v, mP), tw[j * step], mP);
+// Several butterfly stages in one pass through shared memory.  The stages
+// with half = 2^h for h in [b0, b1) pair elements that differ in one of the
+// index bits b0 .. b1 - 1 only, so with e = top 2^b1 + mid 2^b0 + low, a tile
+// of all 2^(b1-b0) mid values x 2^LB consecutive low values (LB = min(b0, 5))
+// of one (polynomial, top, low block) goes through all of them in shared
+// memory: one read and one write of the data per pass instead of per stage.
+// DIF (forward): h from b1 - 1 down to b0, (u, v) -> (u + v, (u - v) w^j);
+// DIT (inverse): h from b0 up to b1 - 1, (u, v w^j) -> (u + v w^j, u - v w^j);
+// j = e mod 2^h, w^j = tw[j 2^(lg-1-h)] (Montgomery form), as the one-stage
+// kernels above.
+constexpr int NTT_PASS_THREADS = 256;
+constexpr int NTT_TILE_LOG = 12;  // 4096 residues (16 KB) per tile
+
+template <bool DIF>
+__global__ void __launch_bounds__(NTT_PASS_THREADS)
+    k_ntt_pass(uint32_t *__restrict__ a, int64_t npoly, int lg, int b0, int b1, const uint32_t *__restrict__ tw,
+               ModP mP) {
+    __shared__ uint32_t sm[1 << NTT_TILE_LOG];
+    const int MB = b1 - b0, LB = b0 < 5 ? b0 : 5;
+    const int nlow = 1 << LB, tile = 1 << (MB + LB), half_tile = tile >> 1;
+    const int64_t Lz = (int64_t)1 << lg;
+    const int lowblocks_log = b0 - LB;
+    const int64_t tiles_per_poly = Lz >> (MB + LB);
+    for (int64_t tid_tile = blockIdx.x; tid_tile < npoly * tiles_per_poly; tid_tile += gridDim.x) {
+        const int64_t poly = tid_tile / tiles_per_poly, rem = tid_tile - poly * tiles_per_poly;
+        const int64_t lowblock = rem & (((int64_t)1 << lowblocks_log) - 1), top = rem >> lowblocks_log;
+        uint32_t *g = a + poly * Lz + (top << b1) + (lowblock << LB);
+        const int64_t lowbase = lowblock << LB;  // low part of e for l = 0
+        __syncthreads();
+        for (int x = threadIdx.x; x < tile; x += NTT_PASS_THREADS)
+            sm[x] = g[((int64_t)(x >> LB) << b0) + (x & (nlow - 1))];
+        __syncthreads();
+        for (int k = 0; k < MB; k++) {
+            const int h = DIF ? b1 - 1 - k : b0 + k;
+            const int hh = h - b0, hm = 1 << hh;
+            const int sh = lg - 1 - h;
+            for (int y = threadIdx.x; y < half_tile; y += NTT_PASS_THREADS) {
+                const int l = y & (nlow - 1), r = y >> LB;
+                const int jm = r & (hm - 1), mid0 = ((r >> hh) << (hh + 1)) + jm;
+                const int i0 = (mid0 << LB) + l, i1 = i0 + (hm << LB);
+                const int64_t j = ((int64_t)jm << b0) + lowbase + l;  // e mod 2^h
+                const uint32_t w = tw[j << sh];
+                const uint32_t u = sm[i0];
+                if (DIF) {
+                    const uint32_t v = sm[i1];
+                    sm[i0] = addm(u, v, mP);
+                    sm[i1] = mont_mul(subm(u, v, mP), w, mP);
+                } else {
+                    const uint32_t v = mont_mul(sm[i1], w, mP);
+                    sm[i0] = addm(u, v, mP);
+                    sm[i1] = subm(u, v, mP);
+                }
+            }
+            __syncthreads();
+        }
+        for (int x = threadIdx.x; x < tile; x += NTT_PASS_THREADS)
+            g[((int64_t)(x >> LB) << b0) + (x & (nlow - 1))] = sm[x];
     }
 }
 
-// one stage of the inverse transform (decimation in time): (u, v w^j) ->
-// (u + v w^j, u - v w^j) with the inverse twiddles
-__global__ void k_ntt_dit_stage(uint32_t *__restrict__ a, int64_t npoly, int64_t Lz, int64_t half, int64_t step,
-                                const uint32_t *__restrict__ twi, ModP mP) {
-    const int64_t nb = npoly * (Lz >> 1);
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nb; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t poly = x / (Lz >> 1), b = x - poly * (Lz >> 1);
-        const int64_t blk = b / half, j = b - blk * half;
-        uint32_t *p0 = a + poly * Lz + blk * 2 * half + j;
-        const uint32_t u = p0[0], v = mont_mul(p0[half], twi[j * step], mP);
-        p0[0] = addm(u, v, mP);
-        p0[half] = subm(u, v, mP);
+// Bit ranges [b0, b1) of the passes of a length-2^lg transform, lowest first:
+// the lowest pass takes up to NTT_TILE_LOG bits (contiguous segments), the
+// others up to NTT_TILE_LOG - 5 (tiles of 32 consecutive columns).
+inline std::vector<std::pair<int, int>> ntt_passes(int lg) {
+    std::vector<std::pair<int, int>> out;
+    int b0 = 0;
+    while (b0 < lg) {
+        const int room = b0 == 0 ? NTT_TILE_LOG : NTT_TILE_LOG - (b0 < 5 ? b0 : 5);
+        const int b1 = std::min(lg, b0 + room);
+        out.emplace_back(b0, b1);
+        b0 = b1;
     }
+    return out;
 }
 
 // pointwise: C_f = A_f B_f (r x s times s x t) at every transform point f
@@ -212,22 +258,26 @@ wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t
         WR_LAUNCHED(ctx);
         k_ntt_load<<<grid_for((int64_t)nB * Lz, T, ctx->num_sms), T, 0, st>>>(B, nb, nB, Lz, bufB.as<uint32_t>(), mP[i]);
         WR_LAUNCHED(ctx);
-        for (int64_t half = Lz / 2; half >= 1; half >>= 1) {
-            const int64_t step = (Lz / 2) / half;
-            k_ntt_dif_stage<<<grid_for((int64_t)nA * (Lz / 2), T, ctx->num_sms), T, 0, st>>>(
-                bufA.as<uint32_t>(), nA, Lz, half, step, tw.as<uint32_t>(), mP[i]);
+        const auto passes = ntt_passes(lg);
+        const int tile_log = NTT_TILE_LOG;
+        auto pass_grid = [&](int64_t npoly) {
+            const int64_t tiles = npoly * (Lz >> std::min<int64_t>(lg, tile_log));
+            return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * 8));
+        };
+        for (auto it = passes.rbegin(); it != passes.rend(); ++it) {  // forward: highest bits first
+            k_ntt_pass<true><<<pass_grid(nA), NTT_PASS_THREADS, 0, st>>>(bufA.as<uint32_t>(), nA, lg, it->first,
+                                                                        it->second, tw.as<uint32_t>(), mP[i]);
             WR_LAUNCHED(ctx);
-            k_ntt_dif_stage<<<grid_for((int64_t)nB * (Lz / 2), T, ctx->num_sms), T, 0, st>>>(
-                bufB.as<uint32_t>(), nB, Lz, half, step, tw.as<uint32_t>(), mP[i]);
+            k_ntt_pass<true><<<pass_grid(nB), NTT_PASS_THREADS, 0, st>>>(bufB.as<uint32_t>(), nB, lg, it->first,
+                                                                        it->second, tw.as<uint32_t>(), mP[i]);
             WR_LAUNCHED(ctx);
         }
         k_ntt_pointwise<<<grid_for(Lz, T, ctx->num_sms), T, 0, st>>>(bufA.as<uint32_t>(), bufB.as<uint32_t>(),
                                                                       bufC[i].as<uint32_t>(), r, s, t, Lz, mP[i]);
         WR_LAUNCHED(ctx);
-        for (int64_t half = 1; half <= Lz / 2; half <<= 1) {
-            const int64_t step = (Lz / 2) / half;
-            k_ntt_dit_stage<<<grid_for((int64_t)nC * (Lz / 2), T, ctx->num_sms), T, 0, st>>>(
-                bufC[i].as<uint32_t>(), nC, Lz, half, step, twi.as<uint32_t>(), mP[i]);
+        for (const auto &ps : passes) {  // inverse: lowest bits first
+            k_ntt_pass<false><<<pass_grid(nC), NTT_PASS_THREADS, 0, st>>>(bufC[i].as<uint32_t>(), nC, lg, ps.first,
+                                                                         ps.second, twi.as<uint32_t>(), mP[i]);
             WR_LAUNCHED(ctx);
         }
         // the twiddle uploads of the next prime must not overwrite tables in use

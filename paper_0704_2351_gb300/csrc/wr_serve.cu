@@ -27,6 +27,7 @@
 
 namespace wr {
 wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, wr_result **out);
+wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *params, int G, wr_result **outs);
 
 // Upper bound of the device memory one rank_one call allocates besides the
 // loaded matrix: the kept sequence and basis, the sequence state (blocks,
@@ -67,24 +68,63 @@ extern "C" wr_status wr_set_batch_slots(wr_ctx *ctx, int32_t slots) {
     return WR_OK;
 }
 
+extern "C" wr_status wr_set_batch_fusion(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->batch_fuse = on != 0;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *const *mats,
                                    const wr_params *params, wr_result **outs) {
     if (!ctx || (njobs && (!mats || !params || !outs))) return fail(WR_EINVAL, "null argument");
     for (size_t j = 0; j < njobs; j++) outs[j] = nullptr;
     if (njobs == 0) return WR_OK;
     auto t0 = std::chrono::steady_clock::now();
-    // largest jobs first (longest-processing-time order balances the slots)
-    std::vector<size_t> order(njobs);
+    // Work items: single jobs, or groups of up to 4 jobs on the same matrix
+    // with the same m = n, side, length and outputs (any primes and seeds)
+    // that share one sequence loop (fusion on, early termination off).
     std::vector<double> cost(njobs, 0.0);
+    std::vector<Resolved> rs(njobs);
+    std::vector<char> ok(njobs, 0);
     for (size_t j = 0; j < njobs; j++) {
-        order[j] = j;
-        Resolved r;
-        if (mats[j] && resolve(mats[j], &params[j], r) == WR_OK)
-            cost[j] = (double)r.L * (double)(mats[j]->nnz + 1) * r.nv;
+        if (mats[j] && resolve(mats[j], &params[j], rs[j]) == WR_OK) {
+            ok[j] = 1;
+            cost[j] = (double)rs[j].L * (double)(mats[j]->nnz + 1) * rs[j].nv;
+        }
     }
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<size_t>> items;
+    {
+        std::vector<char> used(njobs, 0);
+        for (size_t j = 0; j < njobs; j++) {
+            if (used[j]) continue;
+            used[j] = 1;
+            std::vector<size_t> it{j};
+            const bool fusable = ctx->batch_fuse && ctx->early_term == 0 && ok[j] && rs[j].N > 0 &&
+                                 multi_eligible(ctx, rs[j]);
+            if (fusable) {
+                const int gmax = multi_max_jobs(rs[j]);
+                for (size_t k = j + 1; k < njobs && (int)it.size() < gmax; k++) {
+                    if (used[k] || !ok[k] || mats[k] != mats[j]) continue;
+                    const Resolved &a = rs[j], &b = rs[k];
+                    if (b.m != a.m || b.n != a.n || b.side != a.side || b.L != a.L || b.symmetric != a.symmetric ||
+                        params[k].want != params[j].want)
+                        continue;
+                    used[k] = 1;
+                    it.push_back(k);
+                }
+            }
+            items.push_back(std::move(it));
+        }
+    }
+    // largest items first (longest-processing-time order balances the slots)
+    std::vector<double> icost(items.size(), 0.0);
+    for (size_t i = 0; i < items.size(); i++)
+        for (size_t j : items[i]) icost[i] += cost[j];
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return icost[a] > icost[b]; });
 
-    const int nslots = (int)std::min<size_t>(njobs, (size_t)std::max(1, ctx->batch_slots));
+    const int nslots = (int)std::min<size_t>(items.size(), (size_t)std::max(1, ctx->batch_slots));
     std::vector<wr_ctx *> slots(nslots, nullptr);
     for (int k = 0; k < nslots; k++) {
         wr_status st = make_child(ctx, &slots[k]);
@@ -100,10 +140,24 @@ extern "C" wr_status wr_rank_batch(wr_ctx *ctx, size_t njobs, const wr_matrix *c
         cudaSetDevice(ctx->device);
         for (;;) {
             const size_t i = next.fetch_add(1);
-            if (i >= njobs) return;
-            const size_t j = order[i];
-            status[j] = rank_one(slots[k], mats[j], &params[j], &outs[j]);
-            if (status[j] != WR_OK) msg[j] = wr_last_error();
+            if (i >= items.size()) return;
+            const std::vector<size_t> &it = items[order[i]];
+            if (it.size() == 1) {
+                const size_t j = it[0];
+                status[j] = rank_one(slots[k], mats[j], &params[j], &outs[j]);
+                if (status[j] != WR_OK) msg[j] = wr_last_error();
+                continue;
+            }
+            std::vector<const wr_params *> ps;
+            std::vector<wr_result *> rr(it.size(), nullptr);
+            for (size_t j : it) ps.push_back(&params[j]);
+            const wr_status st = rank_multi(slots[k], mats[it[0]], ps.data(), (int)it.size(), rr.data());
+            const std::string m = st != WR_OK ? wr_last_error() : std::string();
+            for (size_t g = 0; g < it.size(); g++) {
+                outs[it[g]] = rr[g];
+                status[it[g]] = st;
+                msg[it[g]] = m;
+            }
         }
     };
     std::vector<std::thread> th;

@@ -250,13 +250,19 @@ __global__ void __launch_bounds__(256)
 constexpr int LOCAL_THREADS = 1024;
 // orders per chunk unless the context sets it (wr_set_sigma_chunk)
 constexpr int SIGMA_CHUNK_DEFAULT = 64;
-// PM-Basis by default only for sequences longer than SIGMA_PM_MIN_L (with
-// q <= 32), with leaves of SIGMA_LEAF_DEFAULT orders; measured on GB300 at
+// PM-Basis by default only for sequences longer than SIGMA_PM_MIN_L (q <=
+// 32), with leaves of SIGMA_LEAF_DEFAULT orders; measured on GB300 at
 // L = 45,002, q = 16 the blocked M-Basis alone is faster (744 ms against
-// 786-1058 ms for leaves of 16,384 down to 1,024 orders).  wr_set_sigma_leaf
+// 786-1058 ms for leaves of 16,384 down to 1,024 orders).  For q > 32 the
+// M-Basis chunks shrink to a few orders (shared memory) and its passes over
+// the basis dominate: at q = 64, L = 118,752 PM-Basis with 2,048-order leaves
+// takes 83 s against about 530 s, at L = 16,384 11.1 s against 10.2 s; so
+// PM-Basis from SIGMA_PM_MIN_L_WIDE orders on there.  wr_set_sigma_leaf
 // chooses the leaf explicitly.
 constexpr int64_t SIGMA_LEAF_DEFAULT = 8192;
 constexpr int64_t SIGMA_PM_MIN_L = 131072;
+constexpr int64_t SIGMA_LEAF_WIDE = 2048;
+constexpr int64_t SIGMA_PM_MIN_L_WIDE = 32768;
 constexpr int BAR_T0 = 1, BAR_RR0 = 3;  // ids BAR_T0 + (i & 1), BAR_RR0 + (i & 1)
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
@@ -1216,12 +1222,13 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
     return WR_OK;
 }
 
-// F = [S | -I_m]: L x m x q residual coefficients of the whole problem
-__global__ void k_build_F(const uint32_t *__restrict__ S, int64_t L, int m, int n, uint32_t p,
+// F = [S | -I_m]: coefficients [k0, k1) of the L x m x q residual of the whole problem
+__global__ void k_build_F(const uint32_t *__restrict__ S, int64_t k0, int64_t k1, int m, int n, uint32_t p,
                           uint32_t *__restrict__ F) {
     const int q = m + n;
-    const int64_t total = L * m * q;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t total = (k1 - k0) * m * q;
+    for (int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; y < total; y += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = y + k0 * m * q;
         const int64_t k = x / (m * q);
         const int rem = (int)(x - k * m * q), a = rem / q, c = rem % q;
         F[x] = c < n ? S[((size_t)k * m + a) * n + c] : ((k == 0 && c - n == a) ? p - 1 : 0u);
@@ -1286,26 +1293,63 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     if (m < 1 || n < 1 || m > 32 || n > 32) return fail(WR_EINVAL, "block sizes must be in 1..32");
     ctx->last.sigma_window_ms = ctx->last.sigma_local_ms = ctx->last.sigma_apply_ms = 0.0;
     const bool automatic = ctx->sigma_leaf <= 0;
-    const int64_t leaf = automatic ? SIGMA_LEAF_DEFAULT : ctx->sigma_leaf;
+    const bool wide = m + n > 32;
+    const int64_t leaf = automatic ? (wide ? SIGMA_LEAF_WIDE : SIGMA_LEAF_DEFAULT) : ctx->sigma_leaf;
     // early termination needs the order-by-order basis (PM-Basis splits the
     // orders in halves and so needs all of them from the start)
     const bool early = ctx->feed && ctx->early_term > 0;
-    if (early || L <= leaf || (automatic && (L <= SIGMA_PM_MIN_L || m + n > 32)))
+    if (early || L <= leaf || (automatic && L <= (wide ? SIGMA_PM_MIN_L_WIDE : SIGMA_PM_MIN_L)))
         return mbasis_run(ctx, d_S, L, m, n, n, p, d_P, d_deg, nullptr, 0, Dcap, nullptr);
     const int q = m + n;
     cudaStream_t s = ctx->stream;
-    if (ctx->feed) WR_TRY(feed_wait(ctx, ctx->feed, L));  // PM-Basis reads the whole sequence
     DevBuf F, M;
     WR_TRY(dev_alloc(ctx, F, sizeof(uint32_t) * (size_t)L * m * q));
-    const unsigned g = (unsigned)std::min<int64_t>((L * m * q + 255) / 256, (int64_t)ctx->num_sms * 16);
-    k_build_F<<<g, 256, 0, s>>>(d_S, L, m, n, p, F.as<uint32_t>());
-    WR_LAUNCHED(ctx);
+    auto build_F = [&](int64_t k0, int64_t k1) -> wr_status {
+        if (k1 <= k0) return WR_OK;
+        const unsigned g = (unsigned)std::min<int64_t>(((k1 - k0) * m * q + 255) / 256, (int64_t)ctx->num_sms * 16);
+        k_build_F<<<g, 256, 0, s>>>(d_S, k0, k1, m, n, p, F.as<uint32_t>());
+        WR_LAUNCHED(ctx);
+        return WR_OK;
+    };
     std::vector<int32_t> deg0(q);
     for (int c = 0; c < q; c++) deg0[c] = c < n ? 0 : 1;
     WR_CUDA(cudaMemcpyAsync(d_deg, deg0.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s));
     WR_CUDA(cudaStreamSynchronize(s));
     int64_t DM = 0;
-    WR_TRY(pm_basis_rec(ctx, F.as<uint32_t>(), L, m, q, p, d_deg, leaf, M, DM));
+    // Trailing a sequence still in flight: the basis of the first h orders
+    // needs S_0 .. S_{h-1} only, so that half of the top-level split runs
+    // while the sequence computes its last terms; the residual of the rest,
+    // its basis and the product follow once the sequence has ended.  h is
+    // about 70 % of the orders (the first part's share of the work about
+    // matches the share of the sequence still to come), a multiple of 64.
+    const int64_t h = ctx->feed ? std::min<int64_t>(L - 64, ((L * 7 / 10) / 64) * 64) : 0;
+    if (ctx->feed && h >= leaf && L - h >= 64) {
+        WR_TRY(feed_wait(ctx, ctx->feed, h));
+        WR_TRY(build_F(0, h));
+        DevBuf M1, M2, R;
+        int64_t DM1 = 0, DM2 = 0;
+        std::vector<int32_t> hd(q);
+        WR_TRY(pm_basis_rec(ctx, F.as<uint32_t>(), h, m, q, p, d_deg, leaf, M1, DM1));
+        WR_TRY(feed_wait(ctx, ctx->feed, L));
+        WR_TRY(build_F(h, L));
+        WR_TRY(dev_alloc(ctx, R, sizeof(uint32_t) * (size_t)(L - h) * m * q));
+        WR_TRY(polymat_mul(ctx, F.as<uint32_t>(), L, M1.as<uint32_t>(), DM1 + 1, m, q, q, h, L, p, R.as<uint32_t>()));
+        WR_TRY(pm_basis_rec(ctx, R.as<uint32_t>(), L - h, m, q, p, d_deg, leaf, M2, DM2));
+        R.release();
+        WR_CUDA(cudaMemcpyAsync(hd.data(), d_deg, sizeof(int32_t) * q, cudaMemcpyDeviceToHost, s));
+        WR_CUDA(cudaStreamSynchronize(s));
+        // starting degrees (0^n, 1^m): the smallest is 0
+        const int64_t bound = (int64_t)*std::max_element(hd.begin(), hd.end());
+        DM = std::max<int64_t>(0, std::min<int64_t>(DM1 + DM2, bound));
+        WR_TRY(dev_alloc(ctx, M, sizeof(uint32_t) * (size_t)(DM + 2) * q * q));
+        WR_CUDA(cudaMemsetAsync(M.ptr, 0, M.bytes, s));
+        WR_TRY(polymat_mul(ctx, M1.as<uint32_t>(), DM1 + 1, M2.as<uint32_t>(), DM2 + 1, q, q, q, 0, DM + 1, p,
+                           M.as<uint32_t>()));
+    } else {
+        if (ctx->feed) WR_TRY(feed_wait(ctx, ctx->feed, L));  // PM-Basis reads the whole sequence
+        WR_TRY(build_F(0, L));
+        WR_TRY(pm_basis_rec(ctx, F.as<uint32_t>(), L, m, q, p, d_deg, leaf, M, DM));
+    }
     if (DM > Dcap) return fail(WR_EINVAL, "sigma-basis degree cap too small");
     WR_CUDA(cudaMemsetAsync(d_P, 0, sizeof(uint32_t) * (Dcap + 1) * n * q, s));
     const unsigned g2 = (unsigned)std::min<int64_t>(((DM + 1) * n * q + 255) / 256, (int64_t)ctx->num_sms * 16);

@@ -68,6 +68,32 @@ __device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&v)[W]) {
     }
 }
 
+// Loads of the matrix's entry words and stores of the output rows, with or
+// without the streaming cache hint (CS: evict-first in L1 and L2, ld/st.cs):
+// each entry and each output row is touched once per pass, so with the hint
+// they stop pushing rows of the gathered block out of L2.  The autotuner
+// times both forms per matrix.
+template <bool CS>
+__device__ __forceinline__ uint32_t lde(const uint32_t *p) {
+    if constexpr (CS) return __ldcs(p);
+    else return __ldg(p);
+}
+
+template <int W, bool CS>
+__device__ __forceinline__ void stv_out(uint32_t *p, const uint32_t (&v)[W]) {
+    if constexpr (!CS) {
+        stv<W>(p, v);
+    } else if constexpr (W == 1) {
+        __stcs(p, v[0]);
+    } else if constexpr (W == 2) {
+        __stcs(reinterpret_cast<uint2 *>(p), make_uint2(v[0], v[1]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < W / 4; k++)
+            __stcs(reinterpret_cast<uint4 *>(p) + k, make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+    }
+}
+
 // Entry words: (column << 8) | (uint8)value in the packed layout, the column
 // alone in the wide one (values from the int16 array beside the entries).
 template <bool WIDE>
@@ -90,10 +116,25 @@ __device__ __forceinline__ void mac(int64_t (&acc)[W], int a, const uint32_t (&v
 // |sum| < 2^23 p and T = sum + 2^23 p lies in [0, 2^24 p), below p R: one
 // Montgomery reduction gives T R^{-1}; with the scale taken to scale R^2 mod p
 // (two Montgomery products), mont_mul(T R^{-1}, scale R^2) = sum * scale mod p.
-template <int W>
+// the modulus and scale of the job owning columns col0.. of a multi-job block
+__device__ __forceinline__ void job_of(const MultiEpi &me, int col0, ModP &mp, const uint32_t *&scale) {
+    switch (col0 >> me.jw_log) {
+        case 0: mp = me.mp[0]; scale = me.scale[0]; break;
+        case 1: mp = me.mp[1]; scale = me.scale[1]; break;
+        case 2: mp = me.mp[2]; scale = me.scale[2]; break;
+        default: mp = me.mp[3]; scale = me.scale[3]; break;
+    }
+}
+
+template <int W, bool CS, bool MULTI>
 __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], uint32_t *y,
-                                        const uint32_t *scale, unsigned long long *acc64, int nv,
-                                        int col0, const ModP &mp) {
+                                        const uint32_t *scale_one, unsigned long long *acc64, int nv,
+                                        int col0, const ModP &mp_one, const MultiEpi &me) {
+    ModP mp = mp_one;
+    const uint32_t *scale = scale_one;
+    if constexpr (MULTI) {
+        if (!(tgt & VROW_SPLIT)) job_of(me, col0, mp, scale);
+    }
     if (tgt & VROW_SPLIT) {
         unsigned long long *dst = acc64 + (size_t)(tgt & ~VROW_SPLIT) * nv + col0;
 #pragma unroll
@@ -104,7 +145,7 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
         uint32_t o[W];
 #pragma unroll
         for (int w = 0; w < W; w++) o[w] = mont_mul(mont_redc((uint64_t)acc[w] + off, mp), s2, mp);
-        stv<W>(y + (size_t)tgt * nv + col0, o);
+        stv_out<W, CS>(y + (size_t)tgt * nv + col0, o);
     }
 }
 
@@ -113,12 +154,12 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
 // over the segment's contiguous entries, then a shuffle reduction.
 // Blocks [vblocks, ...): G warps per SELL chunk of 32 light rows; warp q of
 // the chunk takes rows [q*RPW, (q+1)*RPW), G lanes per row.
-template <int NV, int WL, bool WIDE>
+template <int NV, int WL, bool WIDE, bool CS, bool MULTI>
 __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__restrict__ x,
                                               uint32_t *__restrict__ y,
                                               const uint32_t *__restrict__ scale,
                                               unsigned long long *__restrict__ acc64, ModP mp,
-                                              int *__restrict__ term_counter, int64_t vblocks) {
+                                              int *__restrict__ term_counter, int64_t vblocks, MultiEpi me) {
     using Ln = Lanes<NV, WL>;
     constexpr int W = Ln::W, G = Ln::G, RPW = Ln::RPW;
     if (term_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(term_counter, 1);
@@ -136,8 +177,8 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
         for (int w = 0; w < W; w++) acc[w] = 0;
         int j = sub;
         for (; j + 3 * RPW < len; j += 4 * RPW) {
-            const uint32_t e0 = __ldg(e + j), e1 = __ldg(e + j + RPW);
-            const uint32_t e2 = __ldg(e + j + 2 * RPW), e3 = __ldg(e + j + 3 * RPW);
+            const uint32_t e0 = lde<CS>(e + j), e1 = lde<CS>(e + j + RPW);
+            const uint32_t e2 = lde<CS>(e + j + 2 * RPW), e3 = lde<CS>(e + j + 3 * RPW);
             uint32_t v0[W], v1[W], v2[W], v3[W];
             ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
             ldv<W>(xb + (size_t)entry_col<WIDE>(e1) * NV, v1);
@@ -149,7 +190,7 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
             mac<W>(acc, entry_val<WIDE>(e3, ev, j + 3 * RPW), v3);
         }
         for (; j < len; j += RPW) {
-            const uint32_t e0 = __ldg(e + j);
+            const uint32_t e0 = lde<CS>(e + j);
             uint32_t v0[W];
             ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
             mac<W>(acc, entry_val<WIDE>(e0, ev, j), v0);
@@ -158,7 +199,7 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
         for (int off = G; off < 32; off <<= 1)
 #pragma unroll
             for (int w = 0; w < W; w++) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], off);
-        if (sub == 0) row_out<W>(A.seg_row[seg], acc, y, scale, acc64, NV, part * W, mp);
+        if (sub == 0) row_out<W, CS, MULTI>(A.seg_row[seg], acc, y, scale, acc64, NV, part * W, mp, me);
         return;
     }
     const int64_t lw = ((int64_t)blockIdx.x - vblocks) * 8 + warp;
@@ -177,7 +218,7 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
         for (; j + 8 <= len; j += 8) {
             uint32_t ee[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) ee[u] = __ldg(e + (j + u) * SELL_C);
+            for (int u = 0; u < 8; u++) ee[u] = lde<CS>(e + (j + u) * SELL_C);
             uint32_t vv[8][W];
 #pragma unroll
             for (int u = 0; u < 8; u++) ldv<W>(xb + (size_t)entry_col<WIDE>(ee[u]) * NV, vv[u]);
@@ -185,8 +226,8 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
             for (int u = 0; u < 8; u++) mac<W>(acc, entry_val<WIDE>(ee[u], ev, (int64_t)(j + u) * SELL_C), vv[u]);
         }
         for (; j + 4 <= len; j += 4) {
-            const uint32_t e0 = __ldg(e + (j + 0) * SELL_C), e1 = __ldg(e + (j + 1) * SELL_C);
-            const uint32_t e2 = __ldg(e + (j + 2) * SELL_C), e3 = __ldg(e + (j + 3) * SELL_C);
+            const uint32_t e0 = lde<CS>(e + (j + 0) * SELL_C), e1 = lde<CS>(e + (j + 1) * SELL_C);
+            const uint32_t e2 = lde<CS>(e + (j + 2) * SELL_C), e3 = lde<CS>(e + (j + 3) * SELL_C);
             uint32_t v0[W], v1[W], v2[W], v3[W];
             ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
             ldv<W>(xb + (size_t)entry_col<WIDE>(e1) * NV, v1);
@@ -198,13 +239,13 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
             mac<W>(acc, entry_val<WIDE>(e3, ev, (int64_t)(j + 3) * SELL_C), v3);
         }
         for (; j < len; j++) {
-            const uint32_t e0 = __ldg(e + j * SELL_C);
+            const uint32_t e0 = lde<CS>(e + j * SELL_C);
             uint32_t v0[W];
             ldv<W>(xb + (size_t)entry_col<WIDE>(e0) * NV, v0);
             mac<W>(acc, entry_val<WIDE>(e0, ev, (int64_t)j * SELL_C), v0);
         }
         const uint32_t vr = A.vrow[chunk * SELL_C + r];
-        if (vr != VROW_EMPTY) row_out<W>(vr, acc, y, scale, acc64, NV, part * W, mp);
+        if (vr != VROW_EMPTY) row_out<W, CS, MULTI>(vr, acc, y, scale, acc64, NV, part * W, mp, me);
     }
 }
 
@@ -220,6 +261,22 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
     int32_t r = split_row[sid];
     unsigned long long s = acc64[i];
     acc64[i] = 0;
+    y[(size_t)r * nv + b] = mulm(scale[r], red_s64((int64_t)s, mp), mp);
+}
+
+// the same for a multi-job block: column b is reduced with its job's modulus and scale
+__global__ void k_finalize_split_multi(int64_t nsplit, int nv, const int32_t *__restrict__ split_row,
+                                       unsigned long long *__restrict__ acc64, uint32_t *__restrict__ y, MultiEpi me) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsplit * nv) return;
+    int64_t sid = i / nv;
+    int b = (int)(i % nv);
+    int32_t r = split_row[sid];
+    unsigned long long s = acc64[i];
+    acc64[i] = 0;
+    ModP mp;
+    const uint32_t *scale;
+    job_of(me, b, mp, scale);
     y[(size_t)r * nv + b] = mulm(scale[r], red_s64((int64_t)s, mp), mp);
 }
 
@@ -360,14 +417,15 @@ __global__ void k_derive_diag(uint64_t seed, uint64_t tag, int64_t len, uint32_t
 __global__ void k_prepare(int64_t N, int m, int n, int nv, uint64_t seed, uint64_t xtag, int xwidth, int ystride,
                           int ycol0, int gram, int paired, const uint32_t *__restrict__ d1, uint32_t *__restrict__ t0,
                           uint32_t *__restrict__ xh, uint32_t *__restrict__ d1sq, const uint32_t *__restrict__ nmap,
-                          ModP mp) {
+                          ModP mp, int trow) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint64_t gi = nmap ? (uint64_t)nmap[i] : (uint64_t)i;  // index of the draws
     const uint32_t d = d1[i];
     const uint32_t dinv = invm(d, mp);
     d1sq[i] = mulm(d, d, mp);
-    const int tw = paired ? 2 * nv : nv, yo = paired ? nv : 0;
+    // trow: row stride of t0 (0: the block's own width; a multi-job block is wider)
+    const int tw = trow > 0 ? trow : (paired ? 2 * nv : nv), yo = paired ? nv : 0;
     for (int b = 0; b < nv; b++) {
         uint32_t yv = 0;
         if (b < n) yv = (uint32_t)(stream_hash(seed, TAG_Y, gi * ystride + ycol0 + b) % mp.p);
@@ -446,63 +504,87 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 template <int NV, int WL>
 void launch_spmm_kernel(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y, const uint32_t *scale,
-                        unsigned long long *acc64, const ModP &mp, int *term_counter) {
+                        unsigned long long *acc64, const ModP &mp, int *term_counter, bool cs,
+                        const MultiEpi *me) {
     const int64_t vblocks = (A.nseg + 7) / 8;
     const int64_t lblocks = (A.nchunks * Lanes<NV, WL>::G + 7) / 8;
     const int64_t blocks = std::max<int64_t>(vblocks + lblocks, term_counter ? 1 : 0);
     if (blocks <= 0) return;
-    if (A.wvals)
-        k_spmm<NV, WL, true><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter,
-                                                                         vblocks);
-    else
-        k_spmm<NV, WL, false><<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, x, y, scale, acc64, mp, term_counter,
-                                                                          vblocks);
+    const MultiEpi one{};
+#define WR_SPMM_LAUNCH(WIDEV, CSV, MULTIV)                                                                     \
+    k_spmm<NV, WL, WIDEV, CSV, MULTIV><<<(unsigned)blocks, 256, 0, ctx->stream>>>(                             \
+        A, x, y, scale, acc64, mp, term_counter, vblocks, me ? *me : one)
+    if constexpr (NV >= 16) {
+        if (me && me->jobs > 1) {
+            if (A.wvals) {
+                if (cs) WR_SPMM_LAUNCH(true, true, true); else WR_SPMM_LAUNCH(true, false, true);
+            } else {
+                if (cs) WR_SPMM_LAUNCH(false, true, true); else WR_SPMM_LAUNCH(false, false, true);
+            }
+            return;
+        }
+    }
+    if (A.wvals) {
+        if (cs) WR_SPMM_LAUNCH(true, true, false); else WR_SPMM_LAUNCH(true, false, false);
+    } else {
+        if (cs) WR_SPMM_LAUNCH(false, true, false); else WR_SPMM_LAUNCH(false, false, false);
+    }
+#undef WR_SPMM_LAUNCH
 }
 
 template <int NV>
 wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y,
                         const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
-                        int *term_counter, int wl, bool finalize = true) {
+                        int *term_counter, int wl, bool cs, bool finalize, const MultiEpi *me) {
     const int vblocks_any = (A.nseg + A.nchunks) > 0 || term_counter;
     switch (wl) {
         case 1:
-            if constexpr (NV <= 32) { launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            if constexpr (NV <= 32) { launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
             else return fail(WR_EINVAL, "lane width too small for the block width");
         case 2:
-            if constexpr (NV % 2 == 0) { launch_spmm_kernel<NV, 2>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            if constexpr (NV % 2 == 0) { launch_spmm_kernel<NV, 2>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         case 4:
-            if constexpr (NV % 4 == 0) { launch_spmm_kernel<NV, 4>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            if constexpr (NV % 4 == 0) { launch_spmm_kernel<NV, 4>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         case 8:
-            if constexpr (NV % 8 == 0) { launch_spmm_kernel<NV, 8>(ctx, A, x, y, scale, acc64, mp, term_counter); break; }
+            if constexpr (NV % 8 == 0) { launch_spmm_kernel<NV, 8>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         default: return fail(WR_EINVAL, "lane width must be 1, 2, 4 or 8");
     }
     if (vblocks_any) WR_LAUNCHED(ctx);
     if (finalize && A.nsplit > 0) {
         int64_t cnt = A.nsplit * NV;
-        k_finalize_split<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
-                                                                       y, scale, mp);
+        if (me && me->jobs > 1)
+            k_finalize_split_multi<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
+                                                                                 y, *me);
+        else
+            k_finalize_split<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
+                                                                           y, scale, mp);
         WR_LAUNCHED(ctx);
     }
     return WR_OK;
 }
 
-// wl: residues per lane (0 = the default for nv); finalize = false leaves
-// the split rows' sums in acc64 (used by the lane-width tuner only)
+// SpMM variant: residues per lane in the low bits (0 = the default for nv),
+// SPMM_CS set for the streaming cache hints on entries and outputs
+constexpr int SPMM_CS = 16;
+
+// finalize = false leaves the split rows' sums in acc64 (used by the tuner only)
 wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
                       const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
-                      int *term_counter, int wl = 0, bool finalize = true) {
+                      int *term_counter, int variant = 0, bool finalize = true, const MultiEpi *me = nullptr) {
+    const bool cs = (variant & SPMM_CS) != 0;
+    int wl = variant & (SPMM_CS - 1);
     if (wl <= 0 || wl > nv || nv / wl > 32) wl = default_lane_width(nv);
     switch (nv) {
-        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
-        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
-        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
-        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
-        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
-        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
-        case 64: return launch_spmm_t<64>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, finalize);
+        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 64: return launch_spmm_t<64>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
         default: return fail(WR_EINVAL, "unsupported padded block width");
     }
 }
@@ -535,24 +617,25 @@ static wr_status tune_lane_width(wr_ctx *ctx, const Sell &S, int nv, int *out) {
     WR_CUDA(cudaEventCreate(&e0));
     WR_CUDA(cudaEventCreate(&e1));
     float best = 0.0f;
-    for (int wl : {1, 2, 4, 8}) {
-        if (wl > nv || nv % wl != 0 || nv / wl > 32) continue;
-        for (int w = 0; w < 2; w++)
-            WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
-                               acc.as<unsigned long long>(), mp, nullptr, wl, false));
-        WR_CUDA(cudaEventRecord(e0, s));
-        for (int r = 0; r < 5; r++)
-            WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
-                               acc.as<unsigned long long>(), mp, nullptr, wl, false));
-        WR_CUDA(cudaEventRecord(e1, s));
-        WR_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (best == 0.0f || ms < best) {
-            best = ms;
-            *out = wl;
+    for (int cs : {0, SPMM_CS})
+        for (int wl : {1, 2, 4, 8}) {
+            if (wl > nv || nv % wl != 0 || nv / wl > 32) continue;
+            for (int w = 0; w < 2; w++)
+                WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
+                                   acc.as<unsigned long long>(), mp, nullptr, wl | cs, false));
+            WR_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 5; r++)
+                WR_TRY(launch_spmm(ctx, nv, v, x.as<uint32_t>(), y.as<uint32_t>(), scale.as<uint32_t>(),
+                                   acc.as<unsigned long long>(), mp, nullptr, wl | cs, false));
+            WR_CUDA(cudaEventRecord(e1, s));
+            WR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best == 0.0f || ms < best) {
+                best = ms;
+                *out = wl | cs;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return WR_OK;
@@ -561,7 +644,8 @@ static wr_status tune_lane_width(wr_ctx *ctx, const Sell &S, int nv, int *out) {
 // the lane width for a layout: forced by the context, else tuned once per
 // matrix, layout and block width (when the context tunes), else the default
 static wr_status lane_width_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S, int nv, int *out) {
-    if (ctx->lane_width > 0 && ctx->lane_width <= nv && nv % ctx->lane_width == 0 && nv / ctx->lane_width <= 32) {
+    const int lw = ctx->lane_width & 15;
+    if (lw > 0 && lw <= nv && nv % lw == 0 && nv / lw <= 32) {
         *out = ctx->lane_width;
         return WR_OK;
     }
@@ -579,6 +663,21 @@ static wr_status lane_width_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S
     *out = mat->tuned_w[layout][k];
     return WR_OK;
 }
+
+}  // namespace
+
+wr_status launch_spmm_multi(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
+                            unsigned long long *acc64, const MultiEpi &me, int *term_counter, int variant) {
+    if (me.jobs < 2 || me.jobs > MULTI_MAX_JOBS || nv < 16 || (me.jobs << me.jw_log) > nv)
+        return fail(WR_EINVAL, "multi-job SpMM: 2..4 jobs over a block of 16 columns or more");
+    return launch_spmm(ctx, nv, A, x, y, nullptr, acc64, me.mp[0], term_counter, variant, true, &me);
+}
+
+wr_status spmm_variant_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S, int nv, int *out) {
+    return lane_width_for(ctx, mat, S, nv, out);
+}
+
+namespace {
 
 template <int NV, bool GRAM>
 void launch_project_t(wr_ctx *ctx, unsigned grid, int64_t N, int m, int n, const uint32_t *xh,
@@ -645,13 +744,18 @@ static bool use_tc_gram(const wr_ctx *ctx, int m, int n, int tstride, int yoff) 
     return ctx->tensor_proj == 1 || (m >= 16 && n >= 16);
 }
 
+static wr_status launch_gram_to(wr_ctx *ctx, const Resolved &r, const ModP &mp, int64_t rows, const uint32_t *w,
+                                const uint32_t *t, int tmul, int toff, int tstride, int yoff,
+                                unsigned long long *s_raw, const int *counter, int *err) {
+    if (use_tc_gram(ctx, r.m, r.n, tstride, yoff))
+        return launch_gram_tc(ctx, rows, r.m, r.n, w, t, tstride, yoff, s_raw, counter, tmul, toff, r.L, mp, err);
+    return launch_project(ctx, rows, r.m, r.n, r.nv, w, t, s_raw, counter, mp, true, tmul, toff, r.L, tstride, yoff);
+}
+
 static wr_status launch_gram(wr_ctx *ctx, SeqState &st, int64_t rows, const uint32_t *w, const uint32_t *t,
                              int tmul, int toff, int tstride, int yoff) {
-    if (use_tc_gram(ctx, st.r.m, st.r.n, tstride, yoff))
-        return launch_gram_tc(ctx, rows, st.r.m, st.r.n, w, t, tstride, yoff, st.s_raw.as<unsigned long long>(),
-                              st.counter.as<int>(), tmul, toff, st.r.L, st.mp, st.err.as<int>());
-    return launch_project(ctx, rows, st.r.m, st.r.n, st.r.nv, w, t, st.s_raw.as<unsigned long long>(),
-                          st.counter.as<int>(), st.mp, true, tmul, toff, st.r.L, tstride, yoff);
+    return launch_gram_to(ctx, st.r, st.mp, rows, w, t, tmul, toff, tstride, yoff, st.s_raw.as<unsigned long long>(),
+                          st.counter.as<int>(), st.err.as<int>());
 }
 
 static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r, SeqState &st,
@@ -690,7 +794,7 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
         k_prepare<<<blocks_for(r.N, 128), 128, 0, s>>>(r.N, r.m, r.n, r.nv, r.seed, r.xtag, r.xwidth, r.ystride,
                                                       r.ycol0, r.gram ? 1 : 0, r.paired ? 1 : 0, st.D1.as<uint32_t>(),
                                                       st.T.as<uint32_t>(), st.xh.as<uint32_t>(),
-                                                      st.d1sq.as<uint32_t>(), r.nmap, st.mp);
+                                                      st.d1sq.as<uint32_t>(), r.nmap, st.mp, 0);
         WR_LAUNCHED(ctx);
     }
     if (want_projection && (r.gram || r.paired) && r.M > 0) {
@@ -1015,6 +1119,185 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
         WR_LAUNCHED(ctx);
     }
     WR_CUDA(cudaStreamSynchronize(s));
+    return WR_OK;
+}
+
+}  // namespace wr
+
+// ---------------------------------------------------------------------------
+namespace wr {
+
+// Several jobs on one matrix in one sequence loop (batches: the paper's rank
+// over Q takes the same matrix modulo several primes, Section 2.5).  Jobs
+// with the same matrix, m = n, side and length (any primes and seeds) each
+// carry X beside Y; their slices of 2 nv columns sit side by side in one
+// block, so one pair of SpMM passes per application serves them all: the
+// exact int64 row sums do not depend on the prime, and the epilogue reduces
+// each slice modulo its own prime and scales it by its own diagonal.  The
+// Gram projections then run per job on its slice.  Every job's sequence is
+// the one it has alone, bit for bit.
+
+bool multi_eligible(const wr_ctx *ctx, const Resolved &r) {
+    // at least two jobs of 2 nv columns per block of at most 64, and slices of
+    // at least 4 columns (the block is at least 16 columns wide: 4 slices)
+    return pairs_generic(ctx, r) && 4 * r.nv <= 64 && r.nv >= 2;
+}
+
+int multi_max_jobs(const Resolved &r) { return std::min(MULTI_MAX_JOBS, 64 / (2 * r.nv)); }
+
+wr_status run_sequence_multi(wr_ctx *ctx, const wr_matrix *mat, const std::vector<Resolved> &rs_in,
+                             const std::vector<uint32_t *> &d_S, double *seq_ms) {
+    const int G = (int)rs_in.size();
+    if (G < 1 || G > MULTI_MAX_JOBS || (int)d_S.size() != G) return fail(WR_EINVAL, "multi-job sequence: 1..4 jobs");
+    std::vector<Resolved> rs = rs_in;
+    for (auto &r : rs) {
+        r.paired = true;
+        r.nvs = 2 * r.nv;
+    }
+    const Resolved &r0 = rs[0];
+    for (const auto &r : rs)
+        if (r.m != r0.m || r.n != r0.n || r.side != r0.side || r.L != r0.L || !multi_eligible(ctx, r))
+            return fail(WR_EINVAL, "multi-job sequence: jobs must share m = n, side and length");
+    const int jw = 2 * r0.nv;
+    const int W = std::max(16, padded_width(G * jw));
+    if (W > 64 || W / jw > MULTI_MAX_JOBS) return fail(WR_EINVAL, "multi-job sequence: block wider than 64 columns");
+    int jw_log = 0;
+    while ((1 << jw_log) < jw) jw_log++;
+    const int64_t N = r0.N, M = r0.M, L = r0.L;
+    const int64_t E = (int64_t)r0.m * r0.n;
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e1, e2;
+    WR_CUDA(cudaEventCreate(&e1));
+    WR_CUDA(cudaEventCreateWithFlags(&e2, cudaEventBlockingSync));
+    const Sell *first = r0.side == 0 ? &mat->a : &mat->at;
+    const Sell *second = r0.side == 0 ? &mat->at : &mat->a;
+    int v1 = 0, v2 = 0;
+    WR_TRY(lane_width_for(ctx, mat, *first, W, &v1));
+    WR_TRY(lane_width_for(ctx, mat, *second, W, &v2));
+    DevBuf T, Wb, acc1, acc2, counter, err;
+    WR_TRY(dev_alloc(ctx, T, sizeof(uint32_t) * std::max<int64_t>(N * W, 1)));
+    WR_TRY(dev_alloc(ctx, Wb, sizeof(uint32_t) * std::max<int64_t>(M * W, 1)));
+    WR_TRY(dev_alloc(ctx, acc1, sizeof(unsigned long long) * std::max<int64_t>(first->nsplit * W, 1)));
+    WR_TRY(dev_alloc(ctx, acc2, sizeof(unsigned long long) * std::max<int64_t>(second->nsplit * W, 1)));
+    WR_TRY(dev_alloc(ctx, counter, sizeof(int)));
+    WR_TRY(dev_alloc(ctx, err, sizeof(int)));
+    WR_CUDA(cudaMemsetAsync(T.ptr, 0, T.bytes, s));  // slices past the last job stay zero
+    WR_CUDA(cudaMemsetAsync(acc1.ptr, 0, acc1.bytes, s));
+    WR_CUDA(cudaMemsetAsync(acc2.ptr, 0, acc2.bytes, s));
+    WR_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(int), s));
+    WR_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+    struct Job {
+        ModP mp;
+        DevBuf D1, D2, d1sq, xh, w2, s_raw;
+    };
+    std::vector<Job> jobs(G);
+    MultiEpi me1, me2;
+    me1.jobs = me2.jobs = W >> jw_log;
+    me1.jw_log = me2.jw_log = jw_log;
+    for (int g = 0; g < G; g++) {
+        const Resolved &r = rs[g];
+        Job &j = jobs[g];
+        j.mp = make_modp(r.p);
+        WR_TRY(dev_alloc(ctx, j.D1, sizeof(uint32_t) * std::max<int64_t>(N, 1)));
+        WR_TRY(dev_alloc(ctx, j.D2, sizeof(uint32_t) * std::max<int64_t>(M, 1)));
+        WR_TRY(dev_alloc(ctx, j.d1sq, sizeof(uint32_t) * std::max<int64_t>(N, 1)));
+        WR_TRY(dev_alloc(ctx, j.xh, sizeof(uint32_t) * std::max<int64_t>(N, 1)));
+        WR_TRY(dev_alloc(ctx, j.w2, sizeof(uint32_t) * std::max<int64_t>(M, 1)));
+        WR_TRY(dev_alloc(ctx, j.s_raw, sizeof(unsigned long long) * std::max<int64_t>(L * E, 1)));
+        WR_CUDA(cudaMemsetAsync(j.s_raw.ptr, 0, j.s_raw.bytes, s));
+        if (N > 0) {
+            k_derive_diag<<<blocks_for(N, 256), 256, 0, s>>>(r.seed, TAG_D1, N, r.p, j.D1.as<uint32_t>(), r.nmap);
+            WR_LAUNCHED(ctx);
+            k_prepare<<<blocks_for(N, 128), 128, 0, s>>>(N, r.m, r.n, r.nv, r.seed, r.xtag, r.xwidth, r.ystride,
+                                                         r.ycol0, 0, 1, j.D1.as<uint32_t>(), T.as<uint32_t>() + g * jw,
+                                                         j.xh.as<uint32_t>(), j.d1sq.as<uint32_t>(), r.nmap, j.mp, W);
+            WR_LAUNCHED(ctx);
+        }
+        if (M > 0) {
+            k_derive_diag<<<blocks_for(M, 256), 256, 0, s>>>(r.seed, TAG_D2, M, r.p, j.D2.as<uint32_t>(), r.mmap);
+            WR_LAUNCHED(ctx);
+            k_inv_diag<<<blocks_for(M, 256), 256, 0, s>>>(M, j.D2.as<uint32_t>(), j.w2.as<uint32_t>(), j.mp);
+            WR_LAUNCHED(ctx);
+        }
+    }
+    for (int g = 0; g < me1.jobs; g++) {
+        const Job &j = jobs[g < G ? g : 0];  // slices past the last job: zero columns, any valid modulus
+        me1.mp[g] = me2.mp[g] = j.mp;
+        me1.scale[g] = j.D2.as<uint32_t>();
+        me2.scale[g] = j.d1sq.as<uint32_t>();
+    }
+    auto grams = [&](bool w_side, int tmul, int toff) -> wr_status {
+        for (int g = 0; g < G; g++) {
+            Job &j = jobs[g];
+            if (w_side)
+                WR_TRY(launch_gram_to(ctx, rs[g], j.mp, M, j.w2.as<uint32_t>(), Wb.as<uint32_t>() + g * jw, tmul, toff,
+                                      W, r0.nv, j.s_raw.as<unsigned long long>(), counter.as<int>(), err.as<int>()));
+            else
+                WR_TRY(launch_gram_to(ctx, rs[g], j.mp, N, j.xh.as<uint32_t>(), T.as<uint32_t>() + g * jw, tmul, toff,
+                                      W, r0.nv, j.s_raw.as<unsigned long long>(), counter.as<int>(), err.as<int>()));
+        }
+        return WR_OK;
+    };
+    if (L > 0) WR_TRY(grams(false, 2, 0));  // S_0
+    WR_CUDA(cudaEventRecord(e1, s));
+    const SellView f = view(*first), sc = view(*second);
+    auto iteration = [&]() -> wr_status {
+        WR_TRY(launch_spmm_multi(ctx, W, f, T.as<uint32_t>(), Wb.as<uint32_t>(), acc1.as<unsigned long long>(), me1,
+                                 counter.as<int>(), v1));
+        WR_TRY(launch_spmm_multi(ctx, W, sc, Wb.as<uint32_t>(), T.as<uint32_t>(), acc2.as<unsigned long long>(), me2,
+                                 nullptr, v2));
+        WR_TRY(grams(true, 2, -1));
+        return grams(false, 2, 0);
+    };
+    const int64_t terms = std::max<int64_t>(L - 1, 0), iters = (terms + 1) / 2;
+    const int64_t Gk = 64;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_launches = 0;
+    if (iters >= Gk) {
+        const int64_t before = ctx->launches;
+        WR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        wr_status cst = WR_OK;
+        for (int64_t i = 0; i < Gk && cst == WR_OK; i++) cst = iteration();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        graph_launches = ctx->launches - before;
+        ctx->launches = before;
+        if (cst != WR_OK) { if (graph) cudaGraphDestroy(graph); return cst; }
+        WR_CUDA(ce);
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
+    }
+    wr_status loop_st = WR_OK;
+    int64_t done = 0;
+    while (done < iters && loop_st == WR_OK) {
+        const int64_t todo = std::min(Gk, iters - done);
+        if (todo == Gk && exec) {
+            cudaError_t ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) loop_st = cuda_fail(ce, "cudaGraphLaunch");
+            ctx->launches += graph_launches;
+        } else {
+            for (int64_t i = 0; i < todo && loop_st == WR_OK; i++) loop_st = iteration();
+        }
+        done += todo;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    WR_TRY(loop_st);
+    for (int g = 0; g < G && L * E > 0; g++) {
+        k_reduce_seq<<<blocks_for(L * E, 256), 256, 0, s>>>(L * E, jobs[g].s_raw.as<unsigned long long>(), d_S[g],
+                                                           jobs[g].mp);
+        WR_LAUNCHED(ctx);
+    }
+    int herr = 0;
+    WR_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WR_CUDA(cudaEventRecord(e2, s));
+    WR_CUDA(cudaEventSynchronize(e2));
+    float b = 0;
+    cudaEventElapsedTime(&b, e1, e2);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (herr) return fail(WR_ETIMEDOUT, "tensor-core projection: a bounded wait ran out");
+    if (seq_ms) *seq_ms = b;
     return WR_OK;
 }
 

@@ -103,6 +103,7 @@ _sig = {
     "wr_rank": ([vp, vp, P(wr_params), P(vp)], ctypes.c_int),
     "wr_rank_batch": ([vp, ctypes.c_size_t, P(vp), P(wr_params), P(vp)], ctypes.c_int),
     "wr_set_batch_slots": ([vp, i32], ctypes.c_int),
+    "wr_set_batch_fusion": ([vp, i32], ctypes.c_int),
     "wr_rank_device_bytes": ([vp, vp, P(wr_params), P(u64)], ctypes.c_int),
     "wr_result_rank": ([vp], u64),
     "wr_result_info": ([vp, P(i64), P(i64), P(i64), P(i64)], ctypes.c_int),
@@ -359,6 +360,10 @@ def wr_chain_reduce_csr(rows: int, cols: int, rowptr, colidx, vals):
     n2 = int(orp[r.value])
     return (r.value, c.value, orp[: r.value + 1].copy(), oci[:n2].copy(), ova[:n2].copy(),
             rof[: r.value].copy(), cof[: c.value].copy(), off.value)
+
+
+def wr_set_batch_fusion(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_batch_fusion(vp(ctx), 1 if on else 0))
 
 
 def wr_set_batch_slots(ctx: int, slots: int) -> None:

@@ -97,6 +97,45 @@ def test_rank_batch_matches_alone(wr, ctx):
         wr.wr_matrix_free(h)
 
 
+def _heavy(R, C, seed):
+    """A planted matrix plus a row and a column longer than one SELL segment
+    (the split-row path of both passes)."""
+    A = synth.planted_sparse(R, C, min(R, C) - 40, row_len=7, seed=seed)
+    rng = np.random.default_rng(seed)
+    r = [np.repeat(np.arange(R), np.diff(A.rowptr)), np.full(600, int(rng.integers(0, R))), rng.choice(R, 600, False)]
+    c = [A.colidx.astype(np.int64), rng.choice(C, 600, False), np.full(600, int(rng.integers(0, C)))]
+    v = [A.vals.astype(np.int64), np.ones(600, dtype=np.int64), -np.ones(600, dtype=np.int64)]
+    return synth.csr_from_coo(R, C, np.concatenate(r), np.concatenate(c), np.concatenate(v))
+
+
+@pytest.mark.parametrize("b,nprimes", [(8, 4), (8, 3), (4, 4), (3, 2), (16, 2), (16, 3), (2, 4)])
+def test_rank_batch_fused_primes_match_alone(wr, ctx, b, nprimes):
+    """Jobs on one matrix modulo several primes (the rank over Q) share one
+    sequence loop in the batch: slices of one block of up to 64 columns, each
+    reduced modulo its own prime.  Every result equals the same job alone and
+    the batch with the fusion off, bit for bit; the chain pair's ranks are
+    the planted ones for every prime."""
+    d_n, _ = synth.chain_pair(2500, seed=b * 7 + nprimes, homology=1)
+    mats = [d_n, _heavy(1500, 1400, b + nprimes)]
+    handles = [_load(wr, ctx, A) for A in mats]
+    jobs = [(i, p, 500 + 17 * i + k) for i in range(len(mats)) for k, p in enumerate(PRIMES[:nprimes])]
+    params = [wr.make_params(p, b, b, seed, want=3) for (i, p, seed) in jobs]
+    alone = [_result(wr, wr.wr_rank(ctx, handles[i], prm), b, b) for (i, _, _), prm in zip(jobs, params)]
+    wr.wr_set_batch_slots(ctx, 3)
+    try:
+        for fuse in [True, False]:
+            wr.wr_set_batch_fusion(ctx, fuse)
+            outs = wr.wr_rank_batch(ctx, [handles[i] for (i, _, _) in jobs], params)
+            for j, (i, p, seed) in enumerate(jobs):
+                got = _result(wr, outs[j], b, b)
+                assert _same(got, alone[j]), "job %d (fusion %s) differs from the same job alone" % (j, fuse)
+            assert all(alone[j]["rank"] == mats[0].rank for j in range(nprimes))
+    finally:
+        wr.wr_set_batch_fusion(ctx, True)
+        for h in handles:
+            wr.wr_matrix_free(h)
+
+
 def test_rank_batch_reports_a_failing_job(wr, ctx):
     A = synth.planted_sparse(300, 260, 200, row_len=5, seed=2)
     h = _load(wr, ctx, A)
