@@ -416,13 +416,19 @@ def run_serve(args):
 
 
 def run_sigma_only(args):
-    """The sigma-basis alone on a random sequence with the bench workload's
-    shape (L = 45,002 terms of 8 x 8 residues mod 1073741789; a random
-    sequence has the generic degree profile of a full-rank one), W + K times
-    (for profiler captures and timing of the sigma-basis kernels)."""
+    """The sigma-basis alone on a random sequence (default: L = 45,002 terms
+    of 8 x 8 residues mod 1073741789, the 200,000 x 180,000 workload's shape;
+    --sigma-block 32 --sigma-L 118752: the default workload's shape); a
+    random sequence has the generic degree profile of a full-rank one.  W + K
+    times, for profiler captures and timing of the sigma-basis kernels."""
     import torch
     from paper_0704_2351_gb300 import wr
     p, m, n, L = 1073741789, 8, 8, 45002
+    if args.sigma_block:
+        m = n = args.sigma_block
+        p = 2147483629
+    if args.sigma_L:
+        L = args.sigma_L
     g = torch.Generator().manual_seed(7)
     S = torch.randint(0, p, (L, m, n), generator=g, dtype=torch.int64).to(torch.int32).cuda()
     q = m + n
@@ -583,6 +589,9 @@ def main():
     ap.add_argument("--gram-rows", type=int, default=1900000, help="--only-gram: rows of the block")
     ap.add_argument("--sigma-chunk", type=int, default=0, help="orders per sigma-basis chunk (0: automatic)")
     ap.add_argument("--sigma-leaf", type=int, default=0, help="orders per PM-Basis leaf (0: automatic)")
+    ap.add_argument("--sigma-block", type=int, default=0,
+                    help="--only-sigma: block m = n (with p = 2147483629; 0: 8 x 8 mod 1073741789)")
+    ap.add_argument("--sigma-L", type=int, default=0, help="--only-sigma: sequence length (0: 45,002)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the one-matrix line (default); batch / serve: batched or "
                          "served against plain time-to-rank")

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -731,14 +732,36 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
         pS[g] = dS[g].as<uint32_t>();
     }
     double seq_ms = 0;
-    WR_TRY(run_sequence_multi(ctx, mat, rs, pS, &seq_ms));
-    // the sigma-bases side by side, each on a child context of its own
+    // The sigma-bases, each on a child context of its own; with the pipeline
+    // they trail the shared sequence (each fed by its job's published terms)
+    // while it runs on the high-priority sequence stream.
     std::vector<wr_ctx *> kids(G, nullptr);
     wr_status st = WR_OK;
     for (int g = 0; g < G && st == WR_OK; g++) {
         st = make_child(ctx, &kids[g]);
         if (st == WR_OK) copy_settings(ctx, kids[g]);
     }
+    const bool piped = ctx->pipeline;
+    if (st == WR_OK && piped && !ctx->seq_stream) {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        cudaError_t ce = cudaStreamCreateWithPriority(&ctx->seq_stream, cudaStreamNonBlocking, greatest);
+        if (ce != cudaSuccess) { ctx->seq_stream = nullptr; st = cuda_fail(ce, "cudaStreamCreateWithPriority"); }
+    }
+    std::vector<std::unique_ptr<SeqFeed>> feeds;
+    std::vector<SeqFeed *> fptr;
+    cudaEvent_t ready0 = nullptr;
+    if (st == WR_OK && piped) {
+        for (int g = 0; g < G; g++) {
+            feeds.emplace_back(new SeqFeed());
+            fptr.push_back(feeds.back().get());
+            kids[g]->feed = fptr.back();
+        }
+        cudaError_t ce = cudaEventCreateWithFlags(&ready0, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventRecord(ready0, ctx->stream);  // the buffers above are allocated
+        if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventRecord");
+    }
+    if (st == WR_OK && !piped) st = run_sequence_multi(ctx, mat, rs, pS, &seq_ms);
     if (st == WR_OK) {
         std::vector<wr_status> sst(G, WR_OK);
         std::vector<std::string> smsg(G);
@@ -746,6 +769,10 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
         for (int g = 0; g < G; g++)
             th.emplace_back([&, g] {
                 cudaSetDevice(ctx->device);
+                if (piped) {
+                    cudaError_t ce = cudaStreamWaitEvent(kids[g]->stream, ready0, 0);
+                    if (ce != cudaSuccess) { sst[g] = cuda_fail(ce, "cudaStreamWaitEvent"); smsg[g] = wr_last_error(); return; }
+                }
                 sst[g] = sigma_basis(kids[g], pS[g], L, r0.m, r0.n, rs[g].p, dP[g].as<uint32_t>(),
                                      ddeg[g].as<int32_t>(), Dcap);
                 if (sst[g] == WR_OK) {
@@ -754,6 +781,30 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
                 }
                 if (sst[g] != WR_OK) smsg[g] = wr_last_error();
             });
+        if (piped) {
+            cudaStream_t user = ctx->stream;
+            cudaError_t ce = cudaStreamWaitEvent(ctx->seq_stream, ready0, 0);
+            if (ce != cudaSuccess) {
+                st = cuda_fail(ce, "cudaStreamWaitEvent");
+            } else {
+                ctx->stream = ctx->seq_stream;
+                st = run_sequence_multi(ctx, mat, rs, pS, &seq_ms, &fptr);
+                ctx->stream = user;
+                cudaEvent_t done_ev = nullptr;
+                if (cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming) == cudaSuccess) {
+                    cudaEventRecord(done_ev, ctx->seq_stream);
+                    cudaStreamWaitEvent(user, done_ev, 0);
+                    cudaEventDestroy(done_ev);
+                }
+            }
+            for (auto *fd : fptr) {
+                {
+                    std::lock_guard<std::mutex> lk(fd->mu);
+                    fd->closed = true;
+                }
+                fd->cv.notify_all();
+            }
+        }
         for (auto &t : th) t.join();
         for (int g = 0; g < G && st == WR_OK; g++)
             if (sst[g] != WR_OK) st = fail(sst[g], smsg[g]);
@@ -761,8 +812,12 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
     for (auto *k : kids)
         if (k) {
             ctx->launches += k->launches;
+            k->feed = nullptr;
             wr_destroy(k);
         }
+    for (auto *fd : fptr)
+        for (cudaEvent_t e : fd->ev) cudaEventDestroy(e);
+    if (ready0) cudaEventDestroy(ready0);
     WR_TRY(st);
     for (int g = 0; g < G; g++) {
         wr_result *res = new wr_result();

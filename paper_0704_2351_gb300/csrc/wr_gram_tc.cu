@@ -8,16 +8,16 @@
 //
 // over the N rows of a block t (the symmetric projection: L = R; X beside Y:
 // the X and Y halves of the paired block).  They are computed exactly from
-// bf16 products of 8-bit digits.  A residue x < 2^31 is written in balanced
-// digits x = sum_i d_i 2^{8i}: with y = x + 0x808080, d_i = byte_i(y) - 128 for
-// i < 3 and d_3 = byte_3(y) in [0, 128].  Every digit is an integer of
-// magnitude <= 128 (exact in bf16), a digit product is at most 2^14, so the
+// half-precision products of 8-bit digits.  A residue x < 2^31 is written in
+// balanced digits x = sum_i d_i 2^{8i}: with y = x + 0x808080, d_i = byte_i(y) -
+// 128 for i < 3 and d_3 = byte_3(y) in [0, 128].  Every digit is an integer of
+// magnitude <= 128 (exact in fp16), a digit product is at most 2^14, so the
 // fp32 sums of GT_DRAIN * 64 = 512 rows stay below 2^23 and are exact.
 //
 // Per tile of 64 rows (the MMA's K), one tcgen05 MMA chain computes
 //   D[i*32 + a][j*NB + b] = sum_r d_i(w_r L_r[a]) d_j(R_r[b])
-// (M = 128 = 4 digits x 32 left columns, N = 4 digits x NB right columns, fp32
-// in tensor memory); every 512 rows each thread of the first four warps
+// (kind::f16 with fp16 operands, M = 128 = 4 digits x 32 left columns, N = 4
+// digits x NB right columns, fp32 in tensor memory); every 512 rows each thread of the first four warps
 // drains its TMEM lane (digit i = warp, column a = lane) into exact int64 sums
 // acc[b] += sum_j 2^{8j} D[i*32 + a][j*NB + b], and at the end
 //   G[a][b] = sum_i 2^{8i} acc_i[a][b]  mod p.
@@ -62,19 +62,18 @@ struct GramShape {
     static_assert(4u * 32u * NB * 4u <= GT_NS * RAWB, "reduction area");
 };
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    uint32_t r;
-    // cvt packs its first source into the upper half
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-}
-
-// digit i (0..3) of the balanced digits of x, as a float: y = x + 0x808080,
-// byte i of y placed in the mantissa of 2^23 (bits 0x4B0000ee = 2^23 + e)
+// Digit I of two consecutive values (y = x + 0x808080 each) as an fp16 pair:
+// the two bytes are placed under 0x64 (fp16 bits 0x64ee = 1024 + e, exact for
+// e < 1024) and 1024 + 128 (digits 0..2) or 1024 (digit 3) is subtracted in
+// one packed half-precision subtraction; every result is an integer of
+// magnitude <= 128, exact.  The lower K index goes to the lower half.
 template <int I>
-__device__ __forceinline__ float digit_f(uint32_t y) {
-    const float f = __uint_as_float(__byte_perm(y, 0x4B000000u, 0x7440u + I));
-    return I < 3 ? f - 8388736.0f : f - 8388608.0f;  // 2^23 + 128, 2^23
+__device__ __forceinline__ uint32_t digit_h2(uint32_t y0, uint32_t y1) {
+    const uint32_t t = __byte_perm(y0, y1, I | ((I + 4) << 4));  // [b_I(y0), b_I(y1), ., .]
+    const uint32_t h = __byte_perm(t, 0x64646464u, 0x4140);      // [b_I(y0), 0x64, b_I(y1), 0x64]
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(h), "r"(I < 3 ? 0x64806480u : 0x64006400u));
+    return r;
 }
 
 // the 4 digit rows (row0 + i * stride) of 8 consecutive K values into
@@ -86,10 +85,10 @@ __device__ __forceinline__ void put_digits(unsigned char *tile, int row0, int st
 #define WR_DIGIT_ROW(I)                                                                              \
     {                                                                                                \
         uint4 q;                                                                                     \
-        q.x = pack_bf16x2(digit_f<I>(y[0]), digit_f<I>(y[1]));                                       \
-        q.y = pack_bf16x2(digit_f<I>(y[2]), digit_f<I>(y[3]));                                       \
-        q.z = pack_bf16x2(digit_f<I>(y[4]), digit_f<I>(y[5]));                                       \
-        q.w = pack_bf16x2(digit_f<I>(y[6]), digit_f<I>(y[7]));                                       \
+        q.x = digit_h2<I>(y[0], y[1]);                                                               \
+        q.y = digit_h2<I>(y[2], y[3]);                                                               \
+        q.z = digit_h2<I>(y[4], y[5]);                                                               \
+        q.w = digit_h2<I>(y[6], y[7]);                                                               \
         *reinterpret_cast<uint4 *>(tile + tc::sw128_chunk((uint32_t)(row0 + I * stride), (uint32_t)c)) = q; \
     }
     WR_DIGIT_ROW(0)
@@ -110,7 +109,7 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
               int64_t L, ModP mp, int *__restrict__ err) {
     using S = GramShape<NB, RB>;
     constexpr int RW = RB / 4;  // residues per raw row
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, S::TN);
+    constexpr uint32_t IDESC = tc::idesc_f16_f32(128, S::TN);
     const int64_t k_term = term_counter ? (int64_t)tmul * *term_counter + toff : (int64_t)toff;
     if (k_term < 0 || k_term >= L) return;  // the same for every block
 
@@ -213,7 +212,7 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
             const uint32_t a0 = tc::smem_addr(opA), b0 = tc::smem_addr(opB);
 #pragma unroll
             for (int ks = 0; ks < GT_KT / 16; ks++)
-                tc::mma_bf16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
+                tc::mma_f16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
                              (ks > 0 || g > 0) ? 1u : 0u);
             tc::mma_commit(&bar_mma[so]);
             committed++;
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(128, 1) k_probe_mma(int64_t iters, float *__re
         for (int64_t it = 0; it < iters; it++)
 #pragma unroll
             for (int ks = 0; ks < 4; ks++)
-                tc::mma_bf16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
+                tc::mma_f16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
                              (it > 0 || ks > 0) ? 1u : 0u);
         tc::mma_commit(bar);
     }

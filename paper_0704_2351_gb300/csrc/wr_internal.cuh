@@ -532,7 +532,9 @@ int padded_width(int n);
 bool multi_eligible(const wr_ctx *ctx, const Resolved &r);
 int multi_max_jobs(const Resolved &r);
 // the sequences of 1..4 jobs on one matrix in one loop (same m = n, side, L)
+struct SeqFeed;
 wr_status run_sequence_multi(wr_ctx *ctx, const wr_matrix *mat, const std::vector<Resolved> &rs,
-                             const std::vector<uint32_t *> &d_S, double *seq_ms);
+                             const std::vector<uint32_t *> &d_S, double *seq_ms,
+                             const std::vector<SeqFeed *> *feeds = nullptr);
 
 }  // namespace wr

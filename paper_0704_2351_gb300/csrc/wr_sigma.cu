@@ -248,6 +248,13 @@ __global__ void __launch_bounds__(256)
 // holds its coefficient s at row base[c] + s; the other warps use per-order
 // snapshots of sh and base.
 constexpr int LOCAL_THREADS = 1024;
+// threads of k_local: all 32 warps for m <= 8; 16 for m > 8; 8 when q > 32,
+// so that the elimination warp keeps its two columns per lane (about 200
+// residues) in registers -- at 16 warps (128 registers a thread) it spilled
+// to local memory and an order took several times longer
+__host__ __device__ constexpr int local_threads(int MM, int CPL) {
+    return CPL > 1 ? LOCAL_THREADS / 4 : (MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS);
+}
 // orders per chunk unless the context sets it (wr_set_sigma_chunk)
 constexpr int SIGMA_CHUNK_DEFAULT = 64;
 // PM-Basis by default only for sequences longer than SIGMA_PM_MIN_L (q <=
@@ -475,7 +482,7 @@ __device__ __forceinline__ void local_warp0_two_lane(int m, int q, int bb, const
 }
 
 template <int MM, int CPL, int KLAZY>
-__global__ void __launch_bounds__(MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS)
+__global__ void __launch_bounds__(local_threads(MM, CPL))
     k_local(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
             uint32_t *__restrict__ qtop_g, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
             int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, uint32_t *__restrict__ scale_g, int dbase,
@@ -1172,7 +1179,7 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
             WR_LAUNCHED(ctx);
         }
         if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
-        kloc<<<1, m <= 8 ? LOCAL_THREADS : LOCAL_THREADS / 2, local_bytes(bb), s>>>(
+        kloc<<<1, local_threads(m <= 8 ? 8 : 32, q <= 32 ? 1 : 2), local_bytes(bb), s>>>(
             m, n, q, bb, 1, Ewin, qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
             degl.as<int32_t>(), dmax.as<int>(), scale.as<uint32_t>(), dbase, mp);
         WR_LAUNCHED(ctx);

@@ -1146,7 +1146,7 @@ bool multi_eligible(const wr_ctx *ctx, const Resolved &r) {
 int multi_max_jobs(const Resolved &r) { return std::min(MULTI_MAX_JOBS, 64 / (2 * r.nv)); }
 
 wr_status run_sequence_multi(wr_ctx *ctx, const wr_matrix *mat, const std::vector<Resolved> &rs_in,
-                             const std::vector<uint32_t *> &d_S, double *seq_ms) {
+                             const std::vector<uint32_t *> &d_S, double *seq_ms, const std::vector<SeqFeed *> *feeds) {
     const int G = (int)rs_in.size();
     if (G < 1 || G > MULTI_MAX_JOBS || (int)d_S.size() != G) return fail(WR_EINVAL, "multi-job sequence: 1..4 jobs");
     std::vector<Resolved> rs = rs_in;
@@ -1239,6 +1239,33 @@ wr_status run_sequence_multi(wr_ctx *ctx, const wr_matrix *mat, const std::vecto
         return WR_OK;
     };
     if (L > 0) WR_TRY(grams(false, 2, 0));  // S_0
+    // fed mode: after every group the terms it finished are reduced into
+    // each job's sequence and an event published to that job's sigma-basis
+    int64_t published = 0;
+    auto publish = [&](int64_t to) -> wr_status {
+        for (int g = 0; g < G; g++) {
+            if (to > published) {
+                k_reduce_seq<<<blocks_for((to - published) * E, 256), 256, 0, s>>>(
+                    (to - published) * E, jobs[g].s_raw.as<unsigned long long>() + published * E,
+                    d_S[g] + published * E, jobs[g].mp);
+                WR_LAUNCHED(ctx);
+            }
+            SeqFeed *fd = (*feeds)[g];
+            cudaEvent_t ev;
+            WR_CUDA(cudaEventCreateWithFlags(&ev, WAIT_EVENT_FLAGS));
+            cudaError_t ce = cudaEventRecord(ev, s);
+            {
+                std::lock_guard<std::mutex> lk(fd->mu);
+                fd->ev.push_back(ev);  // the feed's owner destroys it
+                fd->ready.push_back(ce == cudaSuccess ? to : -1);
+            }
+            fd->cv.notify_all();
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventRecord");
+        }
+        published = to;
+        return WR_OK;
+    };
+    if (feeds) WR_TRY(publish(std::min<int64_t>(1, L)));
     WR_CUDA(cudaEventRecord(e1, s));
     const SellView f = view(*first), sc = view(*second);
     auto iteration = [&]() -> wr_status {
@@ -1279,11 +1306,12 @@ wr_status run_sequence_multi(wr_ctx *ctx, const wr_matrix *mat, const std::vecto
             for (int64_t i = 0; i < todo && loop_st == WR_OK; i++) loop_st = iteration();
         }
         done += todo;
+        if (feeds && loop_st == WR_OK) loop_st = publish(std::min<int64_t>(2 * done + 1, L));
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     WR_TRY(loop_st);
-    for (int g = 0; g < G && L * E > 0; g++) {
+    for (int g = 0; g < G && L * E > 0 && !feeds; g++) {
         k_reduce_seq<<<blocks_for(L * E, 256), 256, 0, s>>>(L * E, jobs[g].s_raw.as<unsigned long long>(), d_S[g],
                                                            jobs[g].mp);
         WR_LAUNCHED(ctx);

@@ -1,10 +1,11 @@
 // Blackwell (sm_103a) primitives for the tensor-core kernels, as inline PTX:
 // mbarriers with bounded waits, 1-D bulk copies (cp.async.bulk, the TMA
 // engine's untiled form), tensor memory (TMEM) allocation and loads, and the
-// tcgen05 MMA on bf16 operands with fp32 accumulators in TMEM.
+// tcgen05 MMA of kind::f16 (bf16 or fp16 operands) with fp32 accumulators in
+// TMEM.
 //
 // Operand tiles live in shared memory in the K-major 128-byte-swizzle layout:
-// a row of the operand (one M or N index) holds 64 bf16 values of K, 128
+// a row of the operand (one M or N index) holds 64 16-bit values of K, 128
 // bytes; rows come in atoms of 8 (1024 bytes, 1024-byte aligned), and the
 // 16-byte chunk c of row r of an atom sits at chunk position c ^ (r % 8).
 #pragma once
@@ -133,8 +134,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// one thread: D (TMEM) = A B^T (+ D if accumulate), A: M x 16, B: N x 16, bf16
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// The same with fp16 A and B (bits 7-9, 10-12 = 0).
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// one thread: D (TMEM) = A B^T (+ D if accumulate), A: M x 16, B: N x 16, bf16 or fp16
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -153,7 +159,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 }
 
 // byte offset of element (row, k) (k < 64) in a K-major 128-byte-swizzled
-// bf16 tile, and of the 16-byte chunk holding k = 8 c .. 8 c + 7
+// 16-bit tile, and of the 16-byte chunk holding k = 8 c .. 8 c + 7
 __host__ __device__ __forceinline__ uint32_t sw128_chunk(uint32_t row, uint32_t c) {
     return (row >> 3) * 1024u + (row & 7u) * 128u + ((c ^ (row & 7u)) << 4);
 }
