@@ -95,16 +95,22 @@ def spmm_traffic(kernel_file="paper_0704_2351_gb300/csrc/wr_spmm.cu",
 
 
 def apply_options(wr, ctx, args):
-    """Read-time passes and early termination, when asked for (all off by default)."""
+    """Read-time passes and early termination, when asked for (all off by
+    default), and the column-slab size of the SpMM passes (0: the library's
+    default)."""
     wr.wr_set_chain_reduction(ctx, bool(getattr(args, "chain_reduction", False)))
     wr.wr_set_locality_order(ctx, bool(getattr(args, "locality_order", False)))
     wr.wr_set_early_termination(ctx, int(getattr(args, "early_termination", 0)))
+    wr.wr_set_column_slabs(ctx, int(getattr(args, "slab_bytes", 0)))
 
 
 def options_config(args):
-    return {"chain_reduction": bool(getattr(args, "chain_reduction", False)),
-            "locality_order": bool(getattr(args, "locality_order", False)),
-            "early_termination_orders": int(getattr(args, "early_termination", 0))}
+    out = {"chain_reduction": bool(getattr(args, "chain_reduction", False)),
+           "locality_order": bool(getattr(args, "locality_order", False)),
+           "early_termination_orders": int(getattr(args, "early_termination", 0))}
+    if int(getattr(args, "slab_bytes", 0)) != 0:
+        out["column_slab_bytes"] = int(args.slab_bytes)
+    return out
 
 
 def measured_peaks():
@@ -178,34 +184,6 @@ def cpu_baseline(A, cfg, budget_s=15.0, terms_cap=400):
                       "each, %.1f s)" % (terms, terms - 1, el),
             "sequence_s_extrapolated": el / (terms - 1) * (L - 1),
             "extrapolation": "x (L - 1) / %d applications, L = %d" % (terms - 1, L)}
-
-
-def gather_reference(A, n, reps=20):
-    """The same gather pattern through a library kernel: a float32 gather-sum
-    (torch.nn.functional.embedding_bag, mode "sum") of rows of the same width,
-    once over the rows of A (pass 1 shape) and once over the rows of A^T (pass
-    2 shape), timed with CUDA events after warm-up (inputs L2-resident, as in
-    the loop)."""
-    import torch
-    import torch.nn.functional as F
-    At = A.transpose()
-    out = {}
-    for name, M, cols in [("pass1", A, A.cols), ("pass2", At, At.cols)]:
-        tab = torch.rand(cols, n, device="cuda", dtype=torch.float32)
-        idx = torch.from_numpy(M.colidx.astype(np.int64)).cuda()
-        off = torch.from_numpy(M.rowptr[:-1].astype(np.int64)).cuda()
-        for _ in range(3):
-            F.embedding_bag(idx, tab, off, mode="sum")
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            F.embedding_bag(idx, tab, off, mode="sum")
-        e1.record()
-        e1.synchronize()
-        out[name + "_us"] = 1e3 * e0.elapsed_time(e1) / reps
-    out["impl"] = "torch.nn.functional.embedding_bag, mode sum, float32 rows of %d values, same index pattern" % n
-    return out
 
 
 def run_blackbox_only(args):
@@ -283,10 +261,14 @@ def run_batch(args):
     torch.cuda.synchronize()
     t = time.perf_counter()
     plain = []
+    phases = {"sequence_ms": 0.0, "sigma_ms": 0.0, "sigma_tail_ms": 0.0, "readout_ms": 0.0}
     for h, (i, p), prm in zip([handles[i] for i, _ in jobs], jobs, params):
         res = wr.wr_rank(ctx, h, prm)
         plain.append(wr.wr_result_rank(res))
         wr.wr_result_free(res)
+        tm = wr.wr_last_timings(ctx)
+        for k in phases:
+            phases[k] += tm[k]
     t_plain = time.perf_counter() - t
     t = time.perf_counter()
     outs = wr.wr_rank_batch(ctx, [handles[i] for i, _ in jobs], params)
@@ -309,6 +291,7 @@ def run_batch(args):
                        "rows": [int(min(A.rows for A in mats)), int(max(A.rows for A in mats))],
                        "nnz_total": int(sum(A.nnz for A in mats))},
             "plain_s": t_plain, "batched_s": t_batch, "speedup": t_plain / t_batch,
+            "plain_phases_ms_summed": {k: round(v, 1) for k, v in phases.items()},
             "ranks_equal_planted": True, "chain_rank_sum_ok": chain_ok,
             "gpu_launches_batched": wr.wr_last_timings(ctx)["kernel_launches"]}
     print(json.dumps(line), flush=True)
@@ -608,6 +591,8 @@ def main():
                     help="remove unit singleton rows/columns at load (rank = pivots + rank of the rest)")
     ap.add_argument("--locality-order", action="store_true",
                     help="renumber rows and columns by decreasing entry count at load (same results)")
+    ap.add_argument("--slab-bytes", type=int, default=0,
+                    help="gathered block bytes per column slab of the SpMM passes (0: no slabs, the default)")
     ap.add_argument("--early-termination", type=int, default=0,
                     help="quiet orders after which the sequence stops (0: all L terms)")
     args = ap.parse_args()

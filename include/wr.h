@@ -196,6 +196,20 @@ wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on);
  * partial sum an integer below 2^23), and the sums are drained into int64 and
  * recombined mod p.  The result is the same bit for bit either way. */
 wr_status wr_set_tensor_projection(wr_ctx *ctx, int32_t mode);
+/* Column slabs of the SpMM passes (Section 4 names reordering for locality;
+ * this is the blocking counterpart): a pass whose gathered block (gathered
+ * rows x block width x 4 bytes) is larger than `bytes` runs as S launches over
+ * column ranges of the matrix, S = ceil(block bytes / bytes) (at most 64), so
+ * that the block rows one launch gathers stay in L2; each launch adds its
+ * exact row sums, reduced mod p, to the output rows, the last one applies the
+ * diagonal.  The slab layouts are built on first use from a copy of the CSR
+ * that matrices loaded while slabs are on keep on the device (others run
+ * without slabs).  0 or negative (default) = no slabs: on the
+ * 1.9M x 1.95M block-32 matrix (paired block of 64 residues, 486 MB gathered
+ * per pass) a pass takes 1.48 ms without slabs and 2.1-5.3 ms with 4-16 of
+ * them, because every slab reads and writes all output rows.  Results never
+ * depend on it. */
+wr_status wr_set_column_slabs(wr_ctx *ctx, int64_t bytes);
 
 /* ---------------------------------------------------------------- matrices */
 

@@ -272,6 +272,12 @@ extern "C" wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on) {
     return WR_OK;
 }
 
+extern "C" wr_status wr_set_column_slabs(wr_ctx *ctx, int64_t bytes) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->slab_bytes = bytes;
+    return WR_OK;
+}
+
 extern "C" wr_status wr_set_tensor_projection(wr_ctx *ctx, int32_t mode) {
     if (!ctx) return fail(WR_EINVAL, "null context");
     if (mode < -1 || mode > 1) return fail(WR_EINVAL, "tensor projection mode must be -1 (automatic), 0 or 1");
@@ -305,6 +311,7 @@ static wr_status load_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nn
     m->rows = rows;
     m->cols = cols;
     m->nnz = nnz;
+    m->wide = wide;
     wr_status st = build_sell(ctx, rows, cols, nnz, d_rowptr, d_colidx, d_vals, m->a, wide);
     if (st == WR_OK) {
         DevBuf rpt, cit, vat;
@@ -316,6 +323,28 @@ static wr_status load_device(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nn
         if (st == WR_OK)
             st = build_sell(ctx, cols, rows, nnz, rpt.as<int64_t>(), cit.as<int32_t>(), vat.as<int32_t>(), m->at,
                             wide);
+        // with column slabs on, both CSRs stay on the device for the slab
+        // layouts built on first use
+        const bool keep = ctx->slab_bytes > 0;
+        if (st == WR_OK && keep) st = dev_alloc(ctx, m->csr_rp[0], sizeof(int64_t) * (rows + 1));
+        if (st == WR_OK && keep) st = dev_alloc(ctx, m->csr_ci[0], sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+        if (st == WR_OK && keep) st = dev_alloc(ctx, m->csr_va[0], sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+        if (st == WR_OK && keep) {
+            cudaError_t e = cudaMemcpyAsync(m->csr_rp[0].ptr, d_rowptr, sizeof(int64_t) * (rows + 1),
+                                            cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e == cudaSuccess && nnz > 0)
+                e = cudaMemcpyAsync(m->csr_ci[0].ptr, d_colidx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice,
+                                    ctx->stream);
+            if (e == cudaSuccess && nnz > 0)
+                e = cudaMemcpyAsync(m->csr_va[0].ptr, d_vals, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice,
+                                    ctx->stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "keep CSR");
+        }
+        if (st == WR_OK && keep) {
+            m->csr_rp[1] = std::move(rpt);
+            m->csr_ci[1] = std::move(cit);
+            m->csr_va[1] = std::move(vat);
+        }
     }
     if (st != WR_OK) {
         delete m;
@@ -485,6 +514,9 @@ void copy_settings(const wr_ctx *parent, wr_ctx *c) {
     c->reorder = parent->reorder;
     c->sigma_chunk = parent->sigma_chunk;
     c->sigma_leaf = parent->sigma_leaf;
+    c->tensor_proj = parent->tensor_proj;
+    c->slab_bytes = parent->slab_bytes;
+    c->batch_fuse = parent->batch_fuse;
     c->alloc_fn = parent->alloc_fn;
     c->free_fn = parent->free_fn;
     c->alloc_user = parent->alloc_user;

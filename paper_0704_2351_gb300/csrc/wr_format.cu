@@ -375,6 +375,66 @@ wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, co
     return WR_OK;
 }
 
+// entries of each row whose column lies in [c0, c1)
+__global__ void k_slab_count(int64_t rows, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                             int32_t c0, int32_t c1, int64_t *__restrict__ cnt) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    int64_t k = 0;
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
+        const int32_t c = colidx[e];
+        k += (c >= c0 && c < c1) ? 1 : 0;
+    }
+    cnt[r] = k;
+}
+
+__global__ void k_slab_fill(int64_t rows, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                            const int32_t *__restrict__ vals, int32_t c0, int32_t c1,
+                            const int64_t *__restrict__ rowptr_s, int32_t *__restrict__ colidx_s,
+                            int32_t *__restrict__ vals_s) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    int64_t w = rowptr_s[r];
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
+        const int32_t c = colidx[e];
+        if (c >= c0 && c < c1) {
+            colidx_s[w] = c;
+            vals_s[w] = vals[e];
+            w++;
+        }
+    }
+}
+
+// The layout of the entries of a CSR whose columns lie in [c0, c1) (columns
+// keep their numbers; every row of the matrix has a row in the layout, empty
+// ones included, so that a pass over this slab writes every output row).
+wr_status build_sell_slab(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *d_rowptr, const int32_t *d_colidx,
+                          const int32_t *d_vals, int32_t c0, int32_t c1, Sell &out, bool wide) {
+    cudaStream_t st = ctx->stream;
+    DevBuf cnt, rp;
+    WR_TRY(dev_alloc(ctx, cnt, sizeof(int64_t) * (rows + 1)));
+    WR_TRY(dev_alloc(ctx, rp, sizeof(int64_t) * (rows + 1)));
+    if (rows > 0) {
+        k_slab_count<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(rows, d_rowptr, d_colidx, c0, c1,
+                                                                      cnt.as<int64_t>());
+        WR_LAUNCHED(ctx);
+    }
+    WR_TRY(exclusive_scan_i64(ctx, cnt.as<int64_t>(), rp.as<int64_t>(), rows));
+    int64_t nnz = 0;
+    WR_CUDA(cudaMemcpyAsync(&nnz, rp.as<int64_t>() + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    WR_CUDA(cudaStreamSynchronize(st));
+    DevBuf ci, va;
+    WR_TRY(dev_alloc(ctx, ci, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    WR_TRY(dev_alloc(ctx, va, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    if (rows > 0) {
+        k_slab_fill<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(rows, d_rowptr, d_colidx, d_vals, c0, c1,
+                                                                     rp.as<int64_t>(), ci.as<int32_t>(),
+                                                                     va.as<int32_t>());
+        WR_LAUNCHED(ctx);
+    }
+    return build_sell(ctx, rows, cols, nnz, rp.as<int64_t>(), ci.as<int32_t>(), va.as<int32_t>(), out, wide);
+}
+
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
                      const int32_t *d_colidx, const int32_t *d_vals, Sell &out, bool wide) {
     (void)nnz;

@@ -367,6 +367,7 @@ struct wr_ctx {
     int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
     bool chain_reduce = false; // matrix loads: remove unit singleton rows/columns and empty ones
     bool reorder = false;      // matrix loads: renumber rows and columns by decreasing degree
+    int64_t slab_bytes = 0;    // column slabs: gathered block bytes per slab (<= 0: off)
     wr_ctx *aux = nullptr;  // child context (own stream) that runs the trailing sigma-basis
     cudaStream_t seq_stream = nullptr; // high-priority stream of the pipelined sequence (lazy)
     wr::SeqFeed *feed = nullptr; // set on a child context while it consumes a sequence in flight
@@ -388,6 +389,13 @@ struct wr_matrix {
     wr::DevBuf map_rows, map_cols;
     wr::Sell a;    // rows of A
     wr::Sell at;   // rows of A^T
+    bool wide = false;
+    // the CSR of A ([0]) and of A^T ([1]), kept on the device for column slabs
+    wr::DevBuf csr_rp[2], csr_ci[2], csr_va[2];
+    // column-slab layouts of A ([0]) and A^T ([1]), built on first use for the
+    // slab count in slab_n (the last one asked for)
+    mutable std::vector<wr::Sell> slabs[2];
+    mutable int slab_n[2] = {0, 0};
     // SpMM residues per lane tuned for [layout a / at][log2 block width] (0: not yet)
     mutable std::mutex tune_mu;
     mutable int tuned_w[2][7] = {{0}};
@@ -424,6 +432,8 @@ wr_status locality_order_host(int64_t rows, int64_t cols, const int64_t *rowptr,
 // format (wr_format.cu)
 wr_status build_sell(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
                      const int32_t *d_colidx, const int32_t *d_vals, Sell &out, bool wide);
+wr_status build_sell_slab(wr_ctx *ctx, int64_t rows, int64_t cols, const int64_t *d_rowptr, const int32_t *d_colidx,
+                          const int32_t *d_vals, int32_t c0, int32_t c1, Sell &out, bool wide);
 wr_status transpose_csr(wr_ctx *ctx, int64_t rows, int64_t cols, int64_t nnz, const int64_t *d_rowptr,
                         const int32_t *d_colidx, const int32_t *d_vals, DevBuf &rowptr_t,
                         DevBuf &colidx_t, DevBuf &vals_t);

@@ -68,6 +68,24 @@ __device__ __forceinline__ void stv(uint32_t *p, const uint32_t (&v)[W]) {
     }
 }
 
+// W residues from memory this kernel also writes (the partial output of the
+// previous column slab): plain loads
+template <int W>
+__device__ __forceinline__ void ldv_rw(const uint32_t *p, uint32_t (&v)[W]) {
+    if constexpr (W == 1) {
+        v[0] = p[0];
+    } else if constexpr (W == 2) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < W / 4; k++) {
+            const uint4 t = reinterpret_cast<const uint4 *>(p)[k];
+            v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+        }
+    }
+}
+
 // Loads of the matrix's entry words and stores of the output rows, with or
 // without the streaming cache hint (CS: evict-first in L1 and L2, ld/st.cs):
 // each entry and each output row is touched once per pass, so with the hint
@@ -126,10 +144,15 @@ __device__ __forceinline__ void job_of(const MultiEpi &me, int col0, ModP &mp, c
     }
 }
 
+// part: 0 the whole pass (y = scale (A x)); with column slabs of the matrix
+// (passes split by ranges of the gathered rows, so that the rows of x that a
+// slab gathers stay in L2) 1 the first slab (y = its sum mod p), 2 a middle
+// one (y += its sum), 3 the last (y = scale (y + its sum)); y holds residues
+// in between.
 template <int W, bool CS, bool MULTI>
 __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], uint32_t *y,
                                         const uint32_t *scale_one, unsigned long long *acc64, int nv,
-                                        int col0, const ModP &mp_one, const MultiEpi &me) {
+                                        int col0, const ModP &mp_one, const MultiEpi &me, int part) {
     ModP mp = mp_one;
     const uint32_t *scale = scale_one;
     if constexpr (MULTI) {
@@ -140,12 +163,30 @@ __device__ __forceinline__ void row_out(uint32_t tgt, const int64_t (&acc)[W], u
 #pragma unroll
         for (int w = 0; w < W; w++) atomicAdd(dst + w, (unsigned long long)acc[w]);
     } else {
-        const uint32_t s2 = to_mont(to_mont(__ldg(scale + tgt), mp), mp);
         const uint64_t off = (uint64_t)mp.p << 23;
         uint32_t o[W];
+        uint32_t *yr = y + (size_t)tgt * nv + col0;
+        if (part == 0) {
+            const uint32_t s2 = to_mont(to_mont(__ldg(scale + tgt), mp), mp);
 #pragma unroll
-        for (int w = 0; w < W; w++) o[w] = mont_mul(mont_redc((uint64_t)acc[w] + off, mp), s2, mp);
-        stv_out<W, CS>(y + (size_t)tgt * nv + col0, o);
+            for (int w = 0; w < W; w++) o[w] = mont_mul(mont_redc((uint64_t)acc[w] + off, mp), s2, mp);
+        } else {
+            // mont_mul(T R^{-1}, R^2) = T mod p
+#pragma unroll
+            for (int w = 0; w < W; w++) o[w] = mont_mul(mont_redc((uint64_t)acc[w] + off, mp), mp.r2, mp);
+            if (part >= 2) {
+                uint32_t prev[W];
+                ldv_rw<W>(yr, prev);
+#pragma unroll
+                for (int w = 0; w < W; w++) o[w] = addm(o[w], prev[w], mp);
+            }
+            if (part == 3) {
+                const uint32_t s1 = to_mont(__ldg(scale + tgt), mp);
+#pragma unroll
+                for (int w = 0; w < W; w++) o[w] = mont_mul(o[w], s1, mp);
+            }
+        }
+        stv_out<W, CS>(yr, o);
     }
 }
 
@@ -159,13 +200,14 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
                                               uint32_t *__restrict__ y,
                                               const uint32_t *__restrict__ scale,
                                               unsigned long long *__restrict__ acc64, ModP mp,
-                                              int *__restrict__ term_counter, int64_t vblocks, MultiEpi me) {
+                                              int *__restrict__ term_counter, int64_t vblocks, MultiEpi me,
+                                              int part) {
     using Ln = Lanes<NV, WL>;
     constexpr int W = Ln::W, G = Ln::G, RPW = Ln::RPW;
     if (term_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(term_counter, 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sub = lane / G, part = lane % G;
-    const uint32_t *xb = x + part * W;
+    const int sub = lane / G, lanepart = lane % G;
+    const uint32_t *xb = x + lanepart * W;
     if ((int64_t)blockIdx.x < vblocks) {
         const int64_t seg = (int64_t)blockIdx.x * 8 + warp;
         if (seg >= A.nseg) return;
@@ -199,7 +241,7 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
         for (int off = G; off < 32; off <<= 1)
 #pragma unroll
             for (int w = 0; w < W; w++) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], off);
-        if (sub == 0) row_out<W, CS, MULTI>(A.seg_row[seg], acc, y, scale, acc64, NV, part * W, mp, me);
+        if (sub == 0) row_out<W, CS, MULTI>(A.seg_row[seg], acc, y, scale, acc64, NV, lanepart * W, mp, me, part);
         return;
     }
     const int64_t lw = ((int64_t)blockIdx.x - vblocks) * 8 + warp;
@@ -245,15 +287,16 @@ __global__ void __launch_bounds__(256) k_spmm(SellView A, const uint32_t *__rest
             mac<W>(acc, entry_val<WIDE>(e0, ev, (int64_t)j * SELL_C), v0);
         }
         const uint32_t vr = A.vrow[chunk * SELL_C + r];
-        if (vr != VROW_EMPTY) row_out<W, CS, MULTI>(vr, acc, y, scale, acc64, NV, part * W, mp, me);
+        if (vr != VROW_EMPTY) row_out<W, CS, MULTI>(vr, acc, y, scale, acc64, NV, lanepart * W, mp, me, part);
     }
 }
 
 // Rows that were cut into segments: their exact int64 sums were added into
 // acc64; reduce, scale, store, and clear the accumulator for the next pass.
+// (part: as in row_out)
 __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restrict__ split_row,
                                  unsigned long long *__restrict__ acc64, uint32_t *__restrict__ y,
-                                 const uint32_t *__restrict__ scale, ModP mp) {
+                                 const uint32_t *__restrict__ scale, ModP mp, int part) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nsplit * nv) return;
     int64_t sid = i / nv;
@@ -261,7 +304,11 @@ __global__ void k_finalize_split(int64_t nsplit, int nv, const int32_t *__restri
     int32_t r = split_row[sid];
     unsigned long long s = acc64[i];
     acc64[i] = 0;
-    y[(size_t)r * nv + b] = mulm(scale[r], red_s64((int64_t)s, mp), mp);
+    uint32_t *yr = y + (size_t)r * nv + b;
+    uint32_t v = red_s64((int64_t)s, mp);
+    if (part >= 2) v = addm(v, *yr, mp);
+    if (part == 0 || part == 3) v = mulm(scale[r], v, mp);
+    *yr = v;
 }
 
 // the same for a multi-job block: column b is reduced with its job's modulus and scale
@@ -505,7 +552,7 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 template <int NV, int WL>
 void launch_spmm_kernel(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y, const uint32_t *scale,
                         unsigned long long *acc64, const ModP &mp, int *term_counter, bool cs,
-                        const MultiEpi *me) {
+                        const MultiEpi *me, int part) {
     const int64_t vblocks = (A.nseg + 7) / 8;
     const int64_t lblocks = (A.nchunks * Lanes<NV, WL>::G + 7) / 8;
     const int64_t blocks = std::max<int64_t>(vblocks + lblocks, term_counter ? 1 : 0);
@@ -513,7 +560,7 @@ void launch_spmm_kernel(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
     const MultiEpi one{};
 #define WR_SPMM_LAUNCH(WIDEV, CSV, MULTIV)                                                                     \
     k_spmm<NV, WL, WIDEV, CSV, MULTIV><<<(unsigned)blocks, 256, 0, ctx->stream>>>(                             \
-        A, x, y, scale, acc64, mp, term_counter, vblocks, me ? *me : one)
+        A, x, y, scale, acc64, mp, term_counter, vblocks, me ? *me : one, part)
     if constexpr (NV >= 16) {
         if (me && me->jobs > 1) {
             if (A.wvals) {
@@ -535,20 +582,20 @@ void launch_spmm_kernel(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
 template <int NV>
 wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint32_t *y,
                         const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
-                        int *term_counter, int wl, bool cs, bool finalize, const MultiEpi *me) {
+                        int *term_counter, int wl, bool cs, bool finalize, const MultiEpi *me, int part) {
     const int vblocks_any = (A.nseg + A.nchunks) > 0 || term_counter;
     switch (wl) {
         case 1:
-            if constexpr (NV <= 32) { launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
+            if constexpr (NV <= 32) { launch_spmm_kernel<NV, 1>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me, part); break; }
             else return fail(WR_EINVAL, "lane width too small for the block width");
         case 2:
-            if constexpr (NV % 2 == 0) { launch_spmm_kernel<NV, 2>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
+            if constexpr (NV % 2 == 0) { launch_spmm_kernel<NV, 2>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me, part); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         case 4:
-            if constexpr (NV % 4 == 0) { launch_spmm_kernel<NV, 4>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
+            if constexpr (NV % 4 == 0) { launch_spmm_kernel<NV, 4>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me, part); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         case 8:
-            if constexpr (NV % 8 == 0) { launch_spmm_kernel<NV, 8>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me); break; }
+            if constexpr (NV % 8 == 0) { launch_spmm_kernel<NV, 8>(ctx, A, x, y, scale, acc64, mp, term_counter, cs, me, part); break; }
             else return fail(WR_EINVAL, "lane width does not divide the block width");
         default: return fail(WR_EINVAL, "lane width must be 1, 2, 4 or 8");
     }
@@ -560,7 +607,7 @@ wr_status launch_spmm_t(wr_ctx *ctx, const SellView &A, const uint32_t *x, uint3
                                                                                  y, *me);
         else
             k_finalize_split<<<blocks_for(cnt, 256), 256, 0, ctx->stream>>>(A.nsplit, NV, A.split_row, acc64,
-                                                                           y, scale, mp);
+                                                                           y, scale, mp, part);
         WR_LAUNCHED(ctx);
     }
     return WR_OK;
@@ -573,18 +620,19 @@ constexpr int SPMM_CS = 16;
 // finalize = false leaves the split rows' sums in acc64 (used by the tuner only)
 wr_status launch_spmm(wr_ctx *ctx, int nv, const SellView &A, const uint32_t *x, uint32_t *y,
                       const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
-                      int *term_counter, int variant = 0, bool finalize = true, const MultiEpi *me = nullptr) {
+                      int *term_counter, int variant = 0, bool finalize = true, const MultiEpi *me = nullptr,
+                      int part = 0) {
     const bool cs = (variant & SPMM_CS) != 0;
     int wl = variant & (SPMM_CS - 1);
     if (wl <= 0 || wl > nv || nv / wl > 32) wl = default_lane_width(nv);
     switch (nv) {
-        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
-        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
-        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
-        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
-        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
-        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
-        case 64: return launch_spmm_t<64>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me);
+        case 1: return launch_spmm_t<1>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
+        case 2: return launch_spmm_t<2>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
+        case 4: return launch_spmm_t<4>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
+        case 8: return launch_spmm_t<8>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
+        case 16: return launch_spmm_t<16>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
+        case 32: return launch_spmm_t<32>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
+        case 64: return launch_spmm_t<64>(ctx, A, x, y, scale, acc64, mp, term_counter, wl, cs, finalize, me, part);
         default: return fail(WR_EINVAL, "unsupported padded block width");
     }
 }
@@ -732,8 +780,66 @@ struct SeqState {
     const Sell *first = nullptr;   // pass 1 layout (output in the other space)
     const Sell *second = nullptr;  // pass 2 layout (output in N-space)
     int wl1 = 0, wl2 = 0;          // residues per lane of the two passes
+    // column slabs of the two passes (empty: one launch over the whole layout)
+    const std::vector<Sell> *slabs1 = nullptr, *slabs2 = nullptr;
     DevBuf T, Wb, D1, D2, d1sq, xh, w2, acc1, acc2, s_raw, counter, err;
 };
+
+// Column slabs (off unless the context sets a slab size, ctx->slab_bytes > 0):
+// a pass whose gathered block is larger than the slab size runs as S launches
+// over column ranges of the matrix, S = ceil(block bytes / slab size), so
+// that the block rows one launch gathers stay in L2; the output rows carry
+// residues from one launch to the next (k_spmm's part argument).  The layouts
+// are built from the CSR kept with the matrix on first use.  Measured on the
+// 1.9M x 1.95M matrix at width 64 they are slower (a pass 1.48 ms without,
+// 2.1-5.3 ms with 4-16 slabs): every slab reads and writes all output rows.
+constexpr int SLAB_MAX = 64;
+
+static wr_status slabs_for(wr_ctx *ctx, const wr_matrix *mat, const Sell &S, int nv,
+                           const std::vector<Sell> **out) {
+    *out = nullptr;
+    if (ctx->slab_bytes <= 0 || !mat->csr_rp[0].ptr) return WR_OK;
+    const int64_t target = ctx->slab_bytes;
+    const int64_t block = S.ncols * (int64_t)nv * 4;
+    if (block <= target || S.ncols < 2) return WR_OK;
+    const int n = (int)std::min<int64_t>(std::min<int64_t>((block + target - 1) / target, SLAB_MAX), S.ncols);
+    const int layout = &S == &mat->a ? 0 : 1;
+    std::lock_guard<std::mutex> lk(mat->tune_mu);
+    if (mat->slab_n[layout] != n) {
+        std::vector<Sell> v(n);
+        const int64_t width = (S.ncols + n - 1) / n;
+        for (int s = 0; s < n; s++) {
+            const int64_t c0 = std::min<int64_t>(s * width, S.ncols), c1 = std::min<int64_t>(c0 + width, S.ncols);
+            WR_TRY(build_sell_slab(ctx, S.nrows, S.ncols, mat->csr_rp[layout].as<int64_t>(),
+                                   mat->csr_ci[layout].as<int32_t>(), mat->csr_va[layout].as<int32_t>(), (int32_t)c0,
+                                   (int32_t)c1, v[s], mat->wide));
+        }
+        mat->slabs[layout] = std::move(v);
+        mat->slab_n[layout] = n;
+    }
+    *out = &mat->slabs[layout];
+    return WR_OK;
+}
+
+// one pass over the whole layout, or over its column slabs
+static wr_status launch_pass(wr_ctx *ctx, int nv, const Sell &S, const std::vector<Sell> *slabs, const uint32_t *x,
+                             uint32_t *y, const uint32_t *scale, unsigned long long *acc64, const ModP &mp,
+                             int *term_counter, int variant) {
+    if (!slabs || slabs->size() < 2)
+        return launch_spmm(ctx, nv, view(S), x, y, scale, acc64, mp, term_counter, variant);
+    const int n = (int)slabs->size();
+    for (int s = 0; s < n; s++)
+        WR_TRY(launch_spmm(ctx, nv, view((*slabs)[s]), x, y, scale, acc64, mp, s == 0 ? term_counter : nullptr,
+                           variant, true, nullptr, s == 0 ? 1 : (s == n - 1 ? 3 : 2)));
+    return WR_OK;
+}
+
+static int64_t max_split(const Sell &S, const std::vector<Sell> *slabs) {
+    int64_t m = S.nsplit;
+    if (slabs)
+        for (const auto &x : *slabs) m = std::max<int64_t>(m, x.nsplit);
+    return m;
+}
 
 // A Gram projection S_raw[tmul * counter + toff] += sum_r w_r t[r][0..m)^T
 // t[r][yoff..yoff+n): on the tensor cores (bf16 digit products, exact) when
@@ -767,14 +873,18 @@ static wr_status seq_setup(wr_ctx *ctx, const wr_matrix *mat, const Resolved &r,
     const int nv = r.nvs;  // SpMM width (2 nv for the paired generic block)
     WR_TRY(lane_width_for(ctx, mat, *st.first, nv, &st.wl1));
     WR_TRY(lane_width_for(ctx, mat, *st.second, nv, &st.wl2));
+    WR_TRY(slabs_for(ctx, mat, *st.first, nv, &st.slabs1));
+    WR_TRY(slabs_for(ctx, mat, *st.second, nv, &st.slabs2));
     WR_TRY(dev_alloc(ctx, st.T, sizeof(uint32_t) * std::max<int64_t>(r.N * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.Wb, sizeof(uint32_t) * std::max<int64_t>(r.M * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.D1, sizeof(uint32_t) * std::max<int64_t>(r.N, 1)));
     WR_TRY(dev_alloc(ctx, st.D2, sizeof(uint32_t) * std::max<int64_t>(r.M, 1)));
     WR_TRY(dev_alloc(ctx, st.d1sq, sizeof(uint32_t) * std::max<int64_t>(r.N, 1)));
     WR_TRY(dev_alloc(ctx, st.xh, sizeof(uint32_t) * std::max<int64_t>(r.N * r.m, 1)));
-    WR_TRY(dev_alloc(ctx, st.acc1, sizeof(unsigned long long) * std::max<int64_t>(st.first->nsplit * nv, 1)));
-    WR_TRY(dev_alloc(ctx, st.acc2, sizeof(unsigned long long) * std::max<int64_t>(st.second->nsplit * nv, 1)));
+    WR_TRY(dev_alloc(ctx, st.acc1,
+                     sizeof(unsigned long long) * std::max<int64_t>(max_split(*st.first, st.slabs1) * nv, 1)));
+    WR_TRY(dev_alloc(ctx, st.acc2,
+                     sizeof(unsigned long long) * std::max<int64_t>(max_split(*st.second, st.slabs2) * nv, 1)));
     WR_TRY(dev_alloc(ctx, st.counter, sizeof(int)));
     WR_TRY(dev_alloc(ctx, st.err, sizeof(int)));
     cudaStream_t s = ctx->stream;
@@ -820,13 +930,12 @@ static int64_t seq_applications(const Resolved &r, int64_t L) {
 // L - 1 are skipped).
 static wr_status seq_iteration(wr_ctx *ctx, SeqState &st, cudaEvent_t *ev) {
     const int nv = st.r.nvs;
-    SellView f = view(*st.first), sc = view(*st.second);
     if (ev) WR_CUDA(cudaEventRecord(ev[0], ctx->stream));
-    WR_TRY(launch_spmm(ctx, nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
+    WR_TRY(launch_pass(ctx, nv, *st.first, st.slabs1, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
                        st.acc1.as<unsigned long long>(), st.mp, st.counter.as<int>(), st.wl1));
     if (ev) WR_CUDA(cudaEventRecord(ev[1], ctx->stream));
-    WR_TRY(launch_spmm(ctx, nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.d1sq.as<uint32_t>(),
-                       st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
+    WR_TRY(launch_pass(ctx, nv, *st.second, st.slabs2, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(),
+                       st.d1sq.as<uint32_t>(), st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (ev) WR_CUDA(cudaEventRecord(ev[2], ctx->stream));
     if (st.r.gram || st.r.paired) {
         const int ts = nv, yo = st.r.paired ? st.r.nv : 0;
@@ -1107,12 +1216,11 @@ wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm
                                                                st.mp);
         WR_LAUNCHED(ctx);
     }
-    SellView f = view(*st.first), sc = view(*st.second);
-    WR_TRY(launch_spmm(ctx, r.nv, f, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(), st.D2.as<uint32_t>(),
-                       st.acc1.as<unsigned long long>(), st.mp, nullptr, st.wl1));
+    WR_TRY(launch_pass(ctx, r.nv, *st.first, st.slabs1, st.T.as<uint32_t>(), st.Wb.as<uint32_t>(),
+                       st.D2.as<uint32_t>(), st.acc1.as<unsigned long long>(), st.mp, nullptr, st.wl1));
     // second pass scaled by D1 (not D1^2): out = D1 A^T D2 A D1 in
-    WR_TRY(launch_spmm(ctx, r.nv, sc, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(), st.D1.as<uint32_t>(),
-                       st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
+    WR_TRY(launch_pass(ctx, r.nv, *st.second, st.slabs2, st.Wb.as<uint32_t>(), st.T.as<uint32_t>(),
+                       st.D1.as<uint32_t>(), st.acc2.as<unsigned long long>(), st.mp, nullptr, st.wl2));
     if (r.N > 0) {
         k_unpad<<<blocks_for(r.N * width, 256), 256, 0, s>>>(r.N, (int)width, r.nv, st.T.as<uint32_t>(), d_out,
                                                              r.nmap);

@@ -85,6 +85,7 @@ _sig = {
     "wr_set_lane_width": ([vp, i32], ctypes.c_int),
     "wr_set_paired_projection": ([vp, i32], ctypes.c_int),
     "wr_set_tensor_projection": ([vp, i32], ctypes.c_int),
+    "wr_set_column_slabs": ([vp, i64], ctypes.c_int),
     "wr_sequence_state_device": ([vp, vp, P(wr_params), vp, u64, i64, vp, vp, P(i64), P(i32)], ctypes.c_int),
     "wr_gram_device": ([vp, u32, i64, u32, u32, vp, i32, i32, vp, vp], ctypes.c_int),
     "wr_probe_mma": ([vp, i64, i32, vp, P(ctypes.c_double)], ctypes.c_int),
@@ -258,6 +259,10 @@ def wr_set_autotune(ctx: int, on: bool) -> None:
 
 def wr_set_lane_width(ctx: int, residues: int) -> None:
     _check(_lib.wr_set_lane_width(vp(ctx), residues))
+
+
+def wr_set_column_slabs(ctx: int, nbytes: int) -> None:
+    _check(_lib.wr_set_column_slabs(vp(ctx), nbytes))
 
 
 def wr_set_tensor_projection(ctx: int, mode: int) -> None:

@@ -444,6 +444,35 @@ def test_sharded_sequence_single_rank_gpu(wr, ctx):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("m,n,sym,side", [(8, 8, False, 0), (8, 8, False, 1), (4, 4, True, 0), (3, 5, False, 1),
+                                          (32, 32, False, 0), (1, 1, False, 1)])
+@pytest.mark.parametrize("slab_bytes,wide", [(4096, False), (20000, False), (12000, True)])
+def test_sequence_with_column_slabs(wr, ctx, m, n, sym, side, slab_bytes, wide):
+    """Passes split into column slabs (several launches, each adding its exact
+    row sums mod p to the output rows, the last applying the diagonal): the
+    sequence and one black-box application equal the oracle's, with rows
+    longer than a segment (split rows) cut across slabs, both sides, the
+    paired, symmetric and unpaired projections."""
+    p = 2147483629
+    A = heavy_matrix(900, 820, seed=m * 31 + n + side, heavy=3, heavy_len=600)
+    if wide:  # entries beyond int8: the layout with int16 values beside the columns
+        A = synth.CSR(A.rows, A.cols, A.rowptr, A.colidx, (A.vals * 257).astype(np.int32))
+    st = oracle.Setup(A, p, m, n, seed=13, side=side, symmetric=sym)
+    L = 41
+    S_ref = oracle.sequence(A, st, L)
+    wr.wr_set_column_slabs(ctx, slab_bytes)  # before the loads: the matrices keep their CSR for the slabs
+    try:
+        assert np.array_equal(gpu_sequence(wr, ctx, A, p, m, n, 13, L, side=side, symmetric=sym), S_ref)
+        mat = load(wr, ctx, A)
+        v = np.random.default_rng(3).integers(0, p, size=(st.N, n)).astype(np.uint32)
+        dout = torch.empty((st.N, n), dtype=torch.int32, device="cuda")
+        wr.wr_blackbox_apply_device(ctx, mat, wr.make_params(p, 1, n, 13, side=side), to_dev(v), dout, n)
+        assert np.array_equal(from_dev(dout), oracle.blackbox_apply(A, p, st.side, st.D1, st.D2, v))
+        wr.wr_matrix_free(mat)
+    finally:
+        wr.wr_set_column_slabs(ctx, 0)
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (2, 2), (4, 8), (4, 32), (32, 32)])
 def test_lane_widths_give_identical_sequences(wr, ctx, m, n):
     """Every SpMM lane width (1, 2, 4, 8 residues per lane where it divides
