@@ -99,6 +99,8 @@ typedef struct {
                              /* this part adds to the time to rank                           */
     int64_t sequence_terms;  /* terms the sequence computed (early termination: at least the */
                              /* result's seq_len, the terms the generator used)               */
+    double sigma_product_ms; /* when profiling is on: PM-Basis polynomial matrix products   */
+                             /* (residuals and basis products, CUDA events)                  */
 } wr_timings;
 
 /* Device allocator callbacks (for example PyTorch's caching allocator):
@@ -134,10 +136,14 @@ wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
  * transforms over three FFT primes and the CRT.  The result is the same basis
  * bit for bit; a leaf as large as the sequence turns PM-Basis off.  0
  * (default) = automatic: PM-Basis with 8,192-order leaves for sequences longer
- * than 131,072 orders when m + n <= 32, with 2,048-order leaves for sequences
- * longer than 32,768 orders when m + n > 32, the blocked M-Basis otherwise.
- * PM-Basis needs the whole sequence: with the pipeline (wr_set_pipeline) it
- * starts when the sequence ends, where the M-Basis trails it chunk by chunk. */
+ * than 131,072 orders when m + n <= 32, with 512-order leaves for sequences
+ * longer than 2,048 orders when m + n > 32, the blocked M-Basis otherwise.
+ * With the pipeline (wr_set_pipeline) PM-Basis trails the sequence in
+ * segments, each about half of the orders still to come (down to two
+ * leaves): a segment's residual against the basis so far, its own basis and
+ * the product start as soon as its terms are published, so that one short
+ * segment is left when the sequence ends; the M-Basis trails it chunk by
+ * chunk. */
 wr_status wr_set_sigma_leaf(wr_ctx *ctx, int64_t orders);
 /* SpMM tile shape: the residues each lane gathers from a row of the dense
  * block (1, 2, 4 or 8; the row's n residues are spread over n / that many

@@ -202,6 +202,8 @@ extern "C" void wr_destroy(wr_ctx *ctx) {
         cudaStreamDestroy(ctx->seq_stream);
     }
     cudaStreamSynchronize(ctx->stream);
+    ctx->ntt_tw.release();
+    cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -702,6 +704,7 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
             ctx->last.sigma_window_ms = aux->last.sigma_window_ms;
             ctx->last.sigma_local_ms = aux->last.sigma_local_ms;
             ctx->last.sigma_apply_ms = aux->last.sigma_apply_ms;
+            ctx->last.sigma_product_ms = aux->last.sigma_product_ms;
             sigma_ms = std::chrono::duration<double, std::milli>(t_sig1 - t_sig0).count();
             tail_ms = std::max(0.0, std::chrono::duration<double, std::milli>(t_sig1 - t_seq1).count());
             if (st == WR_OK && sst != WR_OK) st = fail(sst, smsg);

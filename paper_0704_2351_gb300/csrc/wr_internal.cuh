@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <condition_variable>
 #include <mutex>
@@ -76,6 +77,17 @@ struct ModP {
 
 ModP make_modp(uint32_t p);
 
+// Products below (p-1)^2 that fit in a 64-bit accumulator on top of what
+// fold2 by c = 2^32 mod p leaves (at most c^2 + 2^32 - 1): the fold interval
+// of the lazily reduced sums (at least 2 for p < 2^31, 14 for p < 2^30).
+inline int fold_products(uint32_t p) {
+    const unsigned __int128 c = ((unsigned __int128)1 << 32) % p;
+    const unsigned __int128 after = c * c + (((unsigned __int128)1 << 32) - 1);
+    const unsigned __int128 room = (((unsigned __int128)1 << 64) - 1) - after;
+    const unsigned __int128 prod = (unsigned __int128)(p - 1) * (p - 1);
+    return prod ? (int)std::min<unsigned __int128>(room / prod, 1000) : 1000;
+}
+
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 #ifdef __CUDA_ARCH__
     return __umul64hi(a, b);
@@ -101,9 +113,10 @@ __device__ __forceinline__ unsigned long long madw(uint32_t a, uint32_t b, unsig
 }
 
 // x = hi 2^32 + lo is congruent to hi (2^32 mod p) + lo; folded twice a 64-bit
-// accumulator drops below 2^60 + 2^33 (p < 2^30) or 2^62 + 2^33 (p < 2^31),
-// leaving room for 14 (p < 2^30) or 2 (p < 2^31) more products below p^2 before the next
-// fold.  Two 32x32+64-bit multiply-adds instead of a reduction mod p.
+// accumulator drops to at most c^2 + 2^32 - 1 (c = 2^32 mod p), leaving room
+// for fold_products(p) more products below p^2 before the next fold (at
+// least 14 for p < 2^30, 2 for p < 2^31).  Two 32x32+64-bit multiply-adds
+// instead of a reduction mod p.
 __device__ __forceinline__ unsigned long long fold2(unsigned long long x, uint32_t c) {
     x = madw((uint32_t)(x >> 32), c, (unsigned long long)(uint32_t)x);
     return madw((uint32_t)(x >> 32), c, (unsigned long long)(uint32_t)x);
@@ -375,6 +388,10 @@ struct wr_ctx {
     wr_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
     wr_timings last{};
+    // PM-Basis products: twiddle tables of the transform primes for lengths
+    // up to 2^ntt_lg (0: none yet), released before the stream
+    wr::DevBuf ntt_tw;
+    int ntt_lg = 0;
 };
 
 struct wr_matrix {

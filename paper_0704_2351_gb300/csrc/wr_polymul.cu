@@ -65,16 +65,48 @@ uint32_t primitive_root(uint32_t P) {
 }
 
 // a (mod p, any p < 2^31) -> Montgomery form mod P, transposed to one
-// contiguous run of Lz coefficients per polynomial (zero padded)
-__global__ void k_ntt_load(const uint32_t *__restrict__ src, int64_t ncoef, int nent, int64_t Lz,
-                           uint32_t *__restrict__ dst, ModP mP) {
-    const int64_t total = (int64_t)nent * Lz;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        const int e = (int)(x / Lz);
-        const int64_t k = x - (int64_t)e * Lz;
-        uint32_t v = 0;
-        if (k < ncoef) v = to_mont(src[(size_t)k * nent + e] % mP.p, mP);
-        dst[x] = v;
+// contiguous run of Lz coefficients per polynomial (zero padded).  Tiles of
+// 32 coefficients x 32 entries go through shared memory, so that both the
+// reads (along the entries of a coefficient) and the writes (along the
+// coefficients of an entry) are coalesced.
+constexpr int TR_TILE = 32, TR_ROWS = 8;  // tile edge; thread rows of a 32 x 8 block
+
+__global__ void __launch_bounds__(TR_TILE * TR_ROWS)
+    k_ntt_load(const uint32_t *__restrict__ src, int64_t ncoef, int nent, int64_t Lz, uint32_t *__restrict__ dst,
+               ModP mP) {
+    __shared__ uint32_t tile[TR_TILE][TR_TILE + 1];
+    const int tx = threadIdx.x & (TR_TILE - 1), ty = threadIdx.x / TR_TILE;
+    const int64_t ktiles = (Lz + TR_TILE - 1) / TR_TILE, etiles = (nent + TR_TILE - 1) / TR_TILE;
+    for (int64_t tl = blockIdx.x; tl < ktiles * etiles; tl += gridDim.x) {
+        const int64_t k0 = (tl % ktiles) * TR_TILE;
+        const int e0 = (int)(tl / ktiles) * TR_TILE;
+        __syncthreads();
+        if (k0 < ncoef) {
+            for (int y = ty; y < TR_TILE; y += TR_ROWS) {
+                const int64_t k = k0 + y;
+                const int e = e0 + tx;
+                tile[y][tx] = (k < ncoef && e < nent) ? to_mont(src[(size_t)k * nent + e] % mP.p, mP) : 0u;
+            }
+        }
+        __syncthreads();
+        for (int y = ty; y < TR_TILE; y += TR_ROWS) {
+            const int e = e0 + y;
+            const int64_t k = k0 + tx;
+            if (e < nent && k < Lz) dst[(size_t)e * Lz + k] = k0 < ncoef ? tile[tx][y] : 0u;
+        }
+    }
+}
+
+// tw[j] = w^j (Montgomery form, w_m = w R mod P) for j < count, by square
+// and multiply
+__global__ void k_twiddles(uint32_t w_m, int64_t count, uint32_t *__restrict__ tw, ModP mP) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t r = mP.r1, b = w_m;
+        for (int64_t e = j; e; e >>= 1) {
+            if (e & 1) r = mont_mul(r, b, mP);
+            b = mont_mul(b, b, mP);
+        }
+        tw[j] = r;
     }
 }
 
@@ -86,15 +118,15 @@ __global__ void k_ntt_load(const uint32_t *__restrict__ src, int64_t ncoef, int 
 // memory: one read and one write of the data per pass instead of per stage.
 // DIF (forward): h from b1 - 1 down to b0, (u, v) -> (u + v, (u - v) w^j);
 // DIT (inverse): h from b0 up to b1 - 1, (u, v w^j) -> (u + v w^j, u - v w^j);
-// j = e mod 2^h, w^j = tw[j 2^(lg-1-h)] (Montgomery form), as the one-stage
-// kernels above.
+// j = e mod 2^h, w the 2^(h+1)-th root of unity: w^j = tw[j 2^(lg-1-h+tshift)]
+// in a table of the powers of a 2^(lg+tshift)-th root (Montgomery form).
 constexpr int NTT_PASS_THREADS = 256;
 constexpr int NTT_TILE_LOG = 12;  // 4096 residues (16 KB) per tile
 
 template <bool DIF>
 __global__ void __launch_bounds__(NTT_PASS_THREADS)
     k_ntt_pass(uint32_t *__restrict__ a, int64_t npoly, int lg, int b0, int b1, const uint32_t *__restrict__ tw,
-               ModP mP) {
+               int tshift, ModP mP) {
     __shared__ uint32_t sm[1 << NTT_TILE_LOG];
     const int MB = b1 - b0, LB = b0 < 5 ? b0 : 5;
     const int nlow = 1 << LB, tile = 1 << (MB + LB), half_tile = tile >> 1;
@@ -113,7 +145,7 @@ __global__ void __launch_bounds__(NTT_PASS_THREADS)
         for (int k = 0; k < MB; k++) {
             const int h = DIF ? b1 - 1 - k : b0 + k;
             const int hh = h - b0, hm = 1 << hh;
-            const int sh = lg - 1 - h;
+            const int sh = lg - 1 - h + tshift;
             for (int y = threadIdx.x; y < half_tile; y += NTT_PASS_THREADS) {
                 const int l = y & (nlow - 1), r = y >> LB;
                 const int jm = r & (hm - 1), mid0 = ((r >> hh) << (hh + 1)) + jm;
@@ -153,18 +185,81 @@ inline std::vector<std::pair<int, int>> ntt_passes(int lg) {
     return out;
 }
 
-// pointwise: C_f = A_f B_f (r x s times s x t) at every transform point f
-__global__ void k_ntt_pointwise(const uint32_t *__restrict__ A, const uint32_t *__restrict__ B,
-                                uint32_t *__restrict__ C, int r, int s, int t, int64_t Lz, ModP mP) {
-    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < Lz; f += (int64_t)gridDim.x * blockDim.x) {
-        for (int i = 0; i < r; i++)
-            for (int j = 0; j < t; j++) {
-                uint32_t acc = 0;
-                for (int k = 0; k < s; k++)
-                    acc = addm(acc, mont_mul(A[((size_t)i * s + k) * Lz + f], B[((size_t)k * t + j) * Lz + f], mP), mP);
-                C[((size_t)i * t + j) * Lz + f] = acc;
-            }
+// pointwise: C_f = A_f B_f (r x s times s x t) at every transform point f.
+// A thread owns one transform point f (consecutive f across a warp, so every
+// load is one coalesced row segment) and a PW_RT x PW_CT tile of C; a
+// block's eight warps take eight tiles of
+// the same 32 points.  The sums sum_k A_ik B_kj run on 64-bit accumulators
+// (one 32 x 32 + 64-bit multiply-add per product) folded by 2^32 = r1 (mod P)
+// every FOLDK products, reduced mod P and brought to Montgomery form
+// (A_ik B_kj R^-1) once at the end.
+constexpr int PW_RT = 4, PW_CT = 8, PW_WARPS = 8;
+
+template <int FOLDK>
+__global__ void __launch_bounds__(32 * PW_WARPS)
+    k_ntt_pointwise_tiled(const uint32_t *__restrict__ A, const uint32_t *__restrict__ B, uint32_t *__restrict__ C,
+                          int r, int s, int t, int64_t Lz, ModP mP) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t f = (int64_t)blockIdx.x * 32 + lane;
+    const int ntj = (t + PW_CT - 1) / PW_CT, nti = (r + PW_RT - 1) / PW_RT;
+    const int tile = blockIdx.y * PW_WARPS + warp;
+    if (tile >= nti * ntj || f >= Lz) return;
+    const int i0 = (tile / ntj) * PW_RT, j0 = (tile % ntj) * PW_CT;
+    const uint32_t fc = mP.r1;  // 2^32 mod P
+    bool iv[PW_RT], jv[PW_CT];
+    const uint32_t *pa[PW_RT];
+    const uint32_t *pb[PW_CT];
+#pragma unroll
+    for (int u = 0; u < PW_RT; u++) {
+        iv[u] = i0 + u < r;
+        pa[u] = A + ((size_t)(iv[u] ? i0 + u : 0) * s) * Lz + f;  // row i0 + u, k = 0
     }
+#pragma unroll
+    for (int v = 0; v < PW_CT; v++) {
+        jv[v] = j0 + v < t;
+        pb[v] = B + (size_t)(jv[v] ? j0 + v : 0) * Lz + f;  // column j0 + v, k = 0
+    }
+    const size_t bstep = (size_t)t * Lz;
+    unsigned long long acc[PW_RT][PW_CT];
+#pragma unroll
+    for (int u = 0; u < PW_RT; u++)
+#pragma unroll
+        for (int v = 0; v < PW_CT; v++) acc[u][v] = 0ull;
+    int k = 0;
+    for (; k + FOLDK <= s; k += FOLDK) {
+#pragma unroll
+        for (int kk = 0; kk < FOLDK; kk++) {
+            uint32_t a[PW_RT], b[PW_CT];
+#pragma unroll
+            for (int u = 0; u < PW_RT; u++) a[u] = iv[u] ? __ldg(pa[u] + (size_t)(k + kk) * Lz) : 0u;
+#pragma unroll
+            for (int v = 0; v < PW_CT; v++) b[v] = jv[v] ? __ldg(pb[v] + (size_t)(k + kk) * bstep) : 0u;
+#pragma unroll
+            for (int u = 0; u < PW_RT; u++)
+#pragma unroll
+                for (int v = 0; v < PW_CT; v++) acc[u][v] = madw(a[u], b[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < PW_RT; u++)
+#pragma unroll
+            for (int v = 0; v < PW_CT; v++) acc[u][v] = fold2(acc[u][v], fc);
+    }
+    for (; k < s; k++) {  // fewer than FOLDK products after the last fold
+        uint32_t a[PW_RT], b[PW_CT];
+#pragma unroll
+        for (int u = 0; u < PW_RT; u++) a[u] = iv[u] ? __ldg(pa[u] + (size_t)k * Lz) : 0u;
+#pragma unroll
+        for (int v = 0; v < PW_CT; v++) b[v] = jv[v] ? __ldg(pb[v] + (size_t)k * bstep) : 0u;
+#pragma unroll
+        for (int u = 0; u < PW_RT; u++)
+#pragma unroll
+            for (int v = 0; v < PW_CT; v++) acc[u][v] = madw(a[u], b[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < PW_RT; u++)
+#pragma unroll
+        for (int v = 0; v < PW_CT; v++)
+            if (iv[u] && jv[v]) C[((size_t)(i0 + u) * t + j0 + v) * Lz + f] = mont_redc(red64(acc[u][v], mP), mP);
 }
 
 struct CrtConst {
@@ -176,44 +271,116 @@ struct CrtConst {
 };
 
 // Garner: the integer x < P1 P2 P3 with x = r_i mod P_i, reduced mod p.
-// In: the three inverse transforms (Montgomery form, still times Lz).
-__global__ void k_ntt_crt(const uint32_t *__restrict__ R1, const uint32_t *__restrict__ R2,
-                          const uint32_t *__restrict__ R3, int nent, int64_t Lz, int64_t lo, int64_t hi,
-                          uint32_t *__restrict__ out, uint32_t il1, uint32_t il2, uint32_t il3, CrtConst cc,
-                          ModP m1, ModP m2, ModP m3, ModP mp) {
-    const int64_t total = (hi - lo) * nent;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = lo + x / nent;
-        const int e = (int)(x % nent);
-        const size_t src = (size_t)e * Lz + (size_t)k;
-        // mont_mul(v R, Lz^{-1}) = v Lz^{-1} in normal form
-        const uint32_t r1 = mont_mul(R1[src], il1, m1);
-        const uint32_t r2 = mont_mul(R2[src], il2, m2);
-        const uint32_t r3 = mont_mul(R3[src], il3, m3);
-        const uint32_t t1 = r1;
-        const uint32_t t2 = mulm(subm(r2, t1 % cc.P2, m2), cc.c12, m2);
-        uint32_t u = subm(r3, t1 % cc.P3, m3);
-        u = subm(u, mulm(cc.p1_mod_p3, t2, m3), m3);
-        const uint32_t t3 = mulm(u, cc.c123, m3);
-        uint64_t v = (uint64_t)(t1 % mp.p);
-        v += (uint64_t)mulm(cc.P1_mod_p, t2 % mp.p, mp);
-        v += (uint64_t)mulm(cc.P1P2_mod_p, t3 % mp.p, mp);
-        out[(size_t)x] = red64(v, mp);
+// In: the three inverse transforms (Montgomery form, still times Lz), one
+// run of Lz coefficients per entry; out: coefficient-major.  Tiles of 32
+// coefficients x 32 entries: coalesced reads along the coefficients of an
+// entry, Garner in registers, a shared-memory transpose, coalesced writes
+// along the entries of a coefficient.
+__global__ void __launch_bounds__(TR_TILE * TR_ROWS)
+    k_ntt_crt(const uint32_t *__restrict__ R1, const uint32_t *__restrict__ R2, const uint32_t *__restrict__ R3,
+              int nent, int64_t Lz, int64_t lo, int64_t hi, uint32_t *__restrict__ out, uint32_t il1, uint32_t il2,
+              uint32_t il3, CrtConst cc, ModP m1, ModP m2, ModP m3, ModP mp) {
+    __shared__ uint32_t tile[TR_TILE][TR_TILE + 1];
+    const int tx = threadIdx.x & (TR_TILE - 1), ty = threadIdx.x / TR_TILE;
+    const int64_t nk = hi - lo;
+    const int64_t ktiles = (nk + TR_TILE - 1) / TR_TILE, etiles = (nent + TR_TILE - 1) / TR_TILE;
+    for (int64_t tl = blockIdx.x; tl < ktiles * etiles; tl += gridDim.x) {
+        const int64_t k0 = lo + (tl % ktiles) * TR_TILE;
+        const int e0 = (int)(tl / ktiles) * TR_TILE;
+        __syncthreads();
+        for (int y = ty; y < TR_TILE; y += TR_ROWS) {
+            const int e = e0 + y;
+            const int64_t k = k0 + tx;
+            uint32_t v = 0;
+            if (e < nent && k < hi) {
+                const size_t src = (size_t)e * Lz + (size_t)k;
+                // mont_mul(v R, Lz^{-1}) = v Lz^{-1} in normal form
+                const uint32_t r1 = mont_mul(R1[src], il1, m1);
+                const uint32_t r2 = mont_mul(R2[src], il2, m2);
+                const uint32_t r3 = mont_mul(R3[src], il3, m3);
+                const uint32_t t1 = r1;
+                const uint32_t t2 = mulm(subm(r2, t1 % cc.P2, m2), cc.c12, m2);
+                uint32_t u = subm(r3, t1 % cc.P3, m3);
+                u = subm(u, mulm(cc.p1_mod_p3, t2, m3), m3);
+                const uint32_t t3 = mulm(u, cc.c123, m3);
+                uint64_t w = (uint64_t)(t1 % mp.p);
+                w += (uint64_t)mulm(cc.P1_mod_p, t2 % mp.p, mp);
+                w += (uint64_t)mulm(cc.P1P2_mod_p, t3 % mp.p, mp);
+                v = red64(w, mp);
+            }
+            tile[y][tx] = v;
+        }
+        __syncthreads();
+        for (int y = ty; y < TR_TILE; y += TR_ROWS) {
+            const int64_t k = k0 + y;
+            const int e = e0 + tx;
+            if (k < hi && e < nent) out[(size_t)(k - lo) * nent + e] = tile[tx][y];
+        }
     }
 }
 
-inline unsigned grid_for(int64_t n, int threads, int num_sms) {
-    const int64_t b = (n + threads - 1) / threads;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
+// blocks of the tiled transposes: one per 32 x 32 tile, at most 16 per SM
+// (grid-stride beyond)
+inline unsigned tr_grid(int64_t nk, int64_t nent, int num_sms) {
+    const int64_t tiles = ((nk + TR_TILE - 1) / TR_TILE) * ((nent + TR_TILE - 1) / TR_TILE);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms * 16));
 }
 
 }  // namespace
 
+// The context's twiddle tables, kept across products: for each transform
+// prime, the powers w^j and w^-j (j < 2^(LG-1)) of a 2^LG-th root of unity,
+// LG >= lg (a shorter transform takes every 2^(LG-lg)-th entry); built on
+// the device when a longer transform than the tables serve is first needed.
+static wr_status ensure_twiddles(wr_ctx *ctx, int lg) {
+    if (ctx->ntt_lg >= lg) return WR_OK;
+    const int LG = std::max(lg, 14);
+    const int64_t half = (int64_t)1 << (LG - 1);
+    WR_TRY(dev_alloc(ctx, ctx->ntt_tw, sizeof(uint32_t) * (size_t)(2 * NTT_NPRIMES) * half));
+    for (int i = 0; i < NTT_NPRIMES; i++) {
+        const uint32_t P = NTT_PRIMES[i];
+        const ModP mP = make_modp(P);
+        const uint64_t g = primitive_root(P);
+        const uint64_t w = hpow(g, (P - 1) >> LG, P), wi = hpow(w, P - 2, P);
+        const uint32_t wm = (uint32_t)(((unsigned __int128)w << 32) % P), wim = (uint32_t)(((unsigned __int128)wi << 32) % P);
+        uint32_t *tw = ctx->ntt_tw.as<uint32_t>() + (size_t)(2 * i) * half;
+        const unsigned g2 = (unsigned)std::min<int64_t>((half + 255) / 256, (int64_t)ctx->num_sms * 16);
+        k_twiddles<<<g2, 256, 0, ctx->stream>>>(wm, half, tw, mP);
+        WR_LAUNCHED(ctx);
+        k_twiddles<<<g2, 256, 0, ctx->stream>>>(wim, half, tw + half, mP);
+        WR_LAUNCHED(ctx);
+    }
+    ctx->ntt_lg = LG;
+    return WR_OK;
+}
+
 // C[k - lo] = sum_j A_j B_{k-j} (mod p) for lo <= k < hi; A: na coefficients of
 // r x s, B: nb coefficients of s x t, C: (hi - lo) x r x t.  All device
 // pointers, coefficient-major.
+static wr_status polymat_mul_run(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r,
+                                 int s, int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C);
+
 wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r, int s,
                       int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C) {
+    if (!ctx->profiling) return polymat_mul_run(ctx, A, na, B, nb, r, s, t, lo, hi, p, C);
+    // profiling: the product's device time, summed over the sigma-basis
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    WR_CUDA(cudaEventCreate(&e0));
+    WR_CUDA(cudaEventCreate(&e1));
+    WR_CUDA(cudaEventRecord(e0, ctx->stream));
+    const wr_status st = polymat_mul_run(ctx, A, na, B, nb, r, s, t, lo, hi, p, C);
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->last.sigma_product_ms += ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+static wr_status polymat_mul_run(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t *B, int64_t nb, int r,
+                                 int s, int t, int64_t lo, int64_t hi, uint32_t p, uint32_t *C) {
     if (hi <= lo) return WR_OK;
     cudaStream_t st = ctx->stream;
     if (na <= 0 || nb <= 0) {
@@ -228,35 +395,23 @@ wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t
     const int64_t Lz = (int64_t)1 << lg;
     const int nA = r * s, nB = s * t, nC = r * t;
     const ModP mp = make_modp(p);
-    DevBuf bufA, bufB, bufC[NTT_NPRIMES], tw, twi;
+    DevBuf bufA, bufB, bufC[NTT_NPRIMES];
     WR_TRY(dev_alloc(ctx, bufA, sizeof(uint32_t) * (size_t)nA * Lz));
     WR_TRY(dev_alloc(ctx, bufB, sizeof(uint32_t) * (size_t)nB * Lz));
     for (int i = 0; i < NTT_NPRIMES; i++) WR_TRY(dev_alloc(ctx, bufC[i], sizeof(uint32_t) * (size_t)nC * Lz));
-    WR_TRY(dev_alloc(ctx, tw, sizeof(uint32_t) * (size_t)(Lz / 2)));
-    WR_TRY(dev_alloc(ctx, twi, sizeof(uint32_t) * (size_t)(Lz / 2)));
-    std::vector<uint32_t> htw(Lz / 2), htwi(Lz / 2);
+    WR_TRY(ensure_twiddles(ctx, lg));
+    const int LG = ctx->ntt_lg, tshift = LG - lg;  // the length-2^lg twiddle j is table entry j << tshift
     uint32_t il[NTT_NPRIMES];
     ModP mP[NTT_NPRIMES];
-    const int T = 256;
     for (int i = 0; i < NTT_NPRIMES; i++) {
         const uint32_t P = NTT_PRIMES[i];
         mP[i] = make_modp(P);
-        const uint64_t g = primitive_root(P);
-        const uint64_t w = hpow(g, (P - 1) >> lg, P), wi = hpow(w, P - 2, P);
-        // twiddles in Montgomery form: w^j R mod P
-        uint64_t x = 1, y = 1;
-        for (int64_t j = 0; j < Lz / 2; j++) {
-            htw[j] = (uint32_t)(((unsigned __int128)x << 32) % P);
-            htwi[j] = (uint32_t)(((unsigned __int128)y << 32) % P);
-            x = (unsigned __int128)x * w % P;
-            y = (unsigned __int128)y * wi % P;
-        }
+        const uint32_t *tw = ctx->ntt_tw.as<uint32_t>() + (size_t)(2 * i) * ((size_t)1 << (LG - 1));
+        const uint32_t *twi = tw + ((size_t)1 << (LG - 1));
         il[i] = (uint32_t)hpow((uint64_t)(Lz % P), P - 2, P);  // Lz^{-1} mod P (normal form)
-        WR_CUDA(cudaMemcpyAsync(tw.ptr, htw.data(), sizeof(uint32_t) * htw.size(), cudaMemcpyHostToDevice, st));
-        WR_CUDA(cudaMemcpyAsync(twi.ptr, htwi.data(), sizeof(uint32_t) * htwi.size(), cudaMemcpyHostToDevice, st));
-        k_ntt_load<<<grid_for((int64_t)nA * Lz, T, ctx->num_sms), T, 0, st>>>(A, na, nA, Lz, bufA.as<uint32_t>(), mP[i]);
+        k_ntt_load<<<tr_grid(Lz, nA, ctx->num_sms), TR_TILE * TR_ROWS, 0, st>>>(A, na, nA, Lz, bufA.as<uint32_t>(), mP[i]);
         WR_LAUNCHED(ctx);
-        k_ntt_load<<<grid_for((int64_t)nB * Lz, T, ctx->num_sms), T, 0, st>>>(B, nb, nB, Lz, bufB.as<uint32_t>(), mP[i]);
+        k_ntt_load<<<tr_grid(Lz, nB, ctx->num_sms), TR_TILE * TR_ROWS, 0, st>>>(B, nb, nB, Lz, bufB.as<uint32_t>(), mP[i]);
         WR_LAUNCHED(ctx);
         const auto passes = ntt_passes(lg);
         const int tile_log = NTT_TILE_LOG;
@@ -266,22 +421,26 @@ wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t
         };
         for (auto it = passes.rbegin(); it != passes.rend(); ++it) {  // forward: highest bits first
             k_ntt_pass<true><<<pass_grid(nA), NTT_PASS_THREADS, 0, st>>>(bufA.as<uint32_t>(), nA, lg, it->first,
-                                                                        it->second, tw.as<uint32_t>(), mP[i]);
+                                                                        it->second, tw, tshift, mP[i]);
             WR_LAUNCHED(ctx);
             k_ntt_pass<true><<<pass_grid(nB), NTT_PASS_THREADS, 0, st>>>(bufB.as<uint32_t>(), nB, lg, it->first,
-                                                                        it->second, tw.as<uint32_t>(), mP[i]);
+                                                                        it->second, tw, tshift, mP[i]);
             WR_LAUNCHED(ctx);
         }
-        k_ntt_pointwise<<<grid_for(Lz, T, ctx->num_sms), T, 0, st>>>(bufA.as<uint32_t>(), bufB.as<uint32_t>(),
-                                                                      bufC[i].as<uint32_t>(), r, s, t, Lz, mP[i]);
-        WR_LAUNCHED(ctx);
+        {
+            const int fk = fold_products(NTT_PRIMES[i]);
+            auto *kpw = fk >= 14 ? k_ntt_pointwise_tiled<14> : (fk >= 4 ? k_ntt_pointwise_tiled<4> : k_ntt_pointwise_tiled<2>);
+            const int tiles = ((r + PW_RT - 1) / PW_RT) * ((t + PW_CT - 1) / PW_CT);
+            const dim3 g((unsigned)((Lz + 31) / 32), (unsigned)((tiles + PW_WARPS - 1) / PW_WARPS));
+            kpw<<<g, 32 * PW_WARPS, 0, st>>>(bufA.as<uint32_t>(), bufB.as<uint32_t>(), bufC[i].as<uint32_t>(), r, s,
+                                              t, Lz, mP[i]);
+            WR_LAUNCHED(ctx);
+        }
         for (const auto &ps : passes) {  // inverse: lowest bits first
             k_ntt_pass<false><<<pass_grid(nC), NTT_PASS_THREADS, 0, st>>>(bufC[i].as<uint32_t>(), nC, lg, ps.first,
-                                                                         ps.second, twi.as<uint32_t>(), mP[i]);
+                                                                         ps.second, twi, tshift, mP[i]);
             WR_LAUNCHED(ctx);
         }
-        // the twiddle uploads of the next prime must not overwrite tables in use
-        WR_CUDA(cudaStreamSynchronize(st));
     }
     CrtConst cc;
     cc.P1 = NTT_PRIMES[0];
@@ -292,7 +451,7 @@ wr_status polymat_mul(wr_ctx *ctx, const uint32_t *A, int64_t na, const uint32_t
     cc.p1_mod_p3 = cc.P1 % cc.P3;
     cc.P1_mod_p = cc.P1 % p;
     cc.P1P2_mod_p = (uint32_t)((uint64_t)cc.P1 * cc.P2 % p);
-    k_ntt_crt<<<grid_for((hi - lo) * nC, T, ctx->num_sms), T, 0, st>>>(
+    k_ntt_crt<<<tr_grid(hi - lo, nC, ctx->num_sms), TR_TILE * TR_ROWS, 0, st>>>(
         bufC[0].as<uint32_t>(), bufC[1].as<uint32_t>(), bufC[2].as<uint32_t>(), nC, Lz, lo, hi, C, il[0], il[1],
         il[2], cc, mP[0], mP[1], mP[2], mp);
     WR_LAUNCHED(ctx);

@@ -87,9 +87,9 @@ __global__ void k_quiet(const uint32_t *__restrict__ E, int bb, int m, int n, in
 // writes its partial E_i = sum_t S[k0+i-t] P[t] (mod p) for all i < bb into
 // Epart[b]; k_sum_parts adds the partials.
 constexpr int WIN_THREADS = 256;
-constexpr int WIN_IB = 8;  // orders per thread
+constexpr int WIN_IB = 8;  // orders per thread (IB = 4 for chunks of at most 4 orders)
 constexpr int WIN_CB = 4;  // columns per thread
-static_assert(WIN_IB == 8 && WIN_CB == 4, "the register window and 16-byte loads assume an 8 x 4 tile");
+static_assert(WIN_CB == 4, "the 16-byte loads assume tiles of 4 columns");
 
 // Four consecutive residues from shared memory (one 16-byte load when VEC),
 // zero where the column is out of range.
@@ -111,16 +111,17 @@ __device__ __forceinline__ void ld4(const uint32_t *p, const bool (&cv)[4], uint
 // r it walks the coefficients t of the tile: the S residues the tile needs at
 // step t+1 are those of step t shifted by one order, so they live in a
 // circular register window that takes one new shared-memory load per step
-// (slot indices are compile-time in an 8-fold unrolled loop), and the
+// (slot indices are compile-time in an IB-fold unrolled loop), and the
 // WIN_CB residues of P are one 16-byte load (VEC: q a multiple of 4).
-template <int FOLDK, bool VEC>
+template <int FOLDK, bool VEC, int IB>
 __global__ void __launch_bounds__(WIN_THREADS, 1)
     k_window(const uint32_t *__restrict__ S, int64_t L, int m, int n, int q, const uint32_t *__restrict__ P,
              int64_t k0, int bb, int TT, int64_t tper, const int *__restrict__ dmax_dev,
              uint32_t *__restrict__ Epart, ModP mp) {
     extern __shared__ uint32_t sm[];
     const int mn = m * n, nq = n * q, mq = m * q;
-    const int nib = (bb + WIN_IB - 1) / WIN_IB, ncb = (q + WIN_CB - 1) / WIN_CB;
+    static_assert(IB == 4 || IB == 8, "order tiles of 4 or 8");
+    const int nib = (bb + IB - 1) / IB, ncb = (q + WIN_CB - 1) / WIN_CB;
     const int items = nib * m * ncb;
     const uint32_t fc = mp.r1;  // 2^32 mod p
     uint32_t *out = Epart + (size_t)blockIdx.x * bb * mq;
@@ -128,27 +129,27 @@ __global__ void __launch_bounds__(WIN_THREADS, 1)
     const int64_t tb0 = (int64_t)blockIdx.x * tper;
     const int64_t tb1 = min64(tb0 + tper, tmax + 1);
     uint32_t *Ps = sm;                          // [TT][n][q]
-    uint32_t *Ss = sm + (size_t)TT * nq;        // [nib*WIN_IB + TT - 1][m][n]
+    uint32_t *Ss = sm + (size_t)TT * nq;        // [nib*IB + TT - 1][m][n]
     for (int round = 0; round * WIN_THREADS < items; round++) {
         const int it = round * WIN_THREADS + threadIdx.x;
         const bool act = it < items;
         const int cb = act ? it % ncb : 0;
         const int a = act ? (it / ncb) % m : 0;
-        const int i0 = act ? (it / (ncb * m)) * WIN_IB : 0;
+        const int i0 = act ? (it / (ncb * m)) * IB : 0;
         const int c0 = cb * WIN_CB;
         bool cv[WIN_CB];
 #pragma unroll
         for (int u = 0; u < WIN_CB; u++) cv[u] = c0 + u < q;
-        Acc2 acc[WIN_IB][WIN_CB];
+        Acc2 acc[IB][WIN_CB];
 #pragma unroll
-        for (int k = 0; k < WIN_IB; k++)
+        for (int k = 0; k < IB; k++)
 #pragma unroll
             for (int u = 0; u < WIN_CB; u++) acc[k][u] = Acc2{0u, 0u};
         int cnt = 0;
         for (int64_t t0 = tb0; t0 < tb1; t0 += TT) {
             const int tt_n = (int)min64(TT, tb1 - t0);
             const int64_t smin = k0 - (t0 + tt_n - 1);
-            const int srows = nib * WIN_IB + tt_n - 1;
+            const int srows = nib * IB + tt_n - 1;
             __syncthreads();
             for (int x = threadIdx.x; x < tt_n * nq; x += WIN_THREADS) Ps[x] = P[(size_t)t0 * nq + x];
             for (int x = threadIdx.x; x < srows * mn; x += WIN_THREADS) {
@@ -162,24 +163,24 @@ __global__ void __launch_bounds__(WIN_THREADS, 1)
             for (int r = 0; r < n; r++) {
                 const uint32_t *scol = Ss + a * n + r;      // row u at scol[u * mn]
                 const uint32_t *pcol = Ps + r * q + c0;     // coefficient s at pcol[s * nq]
-                uint32_t sw[WIN_IB];                        // row top - s + k in slot (k - s) & 7
+                uint32_t sw[IB];                            // row top - s + k in slot (k - s) mod IB
 #pragma unroll
-                for (int k = 0; k < WIN_IB; k++) sw[k] = scol[(size_t)(top + k) * mn];
-                for (int s0 = 0; s0 < tt_n; s0 += 8) {
+                for (int k = 0; k < IB; k++) sw[k] = scol[(size_t)(top + k) * mn];
+                for (int s0 = 0; s0 < tt_n; s0 += IB) {
 #pragma unroll
-                    for (int j = 0; j < 8; j++) {
+                    for (int j = 0; j < IB; j++) {
                         const int st = s0 + j;
                         if (st < tt_n) {
-                            if (st > 0) sw[(8 - j) & 7] = scol[(size_t)(top - st) * mn];
+                            if (st > 0) sw[(IB - j) & (IB - 1)] = scol[(size_t)(top - st) * mn];
                             uint32_t pv[WIN_CB];
                             ld4<VEC>(pcol + (size_t)st * nq, cv, pv);
 #pragma unroll
-                            for (int k = 0; k < WIN_IB; k++)
+                            for (int k = 0; k < IB; k++)
 #pragma unroll
-                                for (int u = 0; u < WIN_CB; u++) mac2(acc[k][u], sw[(k - j) & 7], pv[u]);
+                                for (int u = 0; u < WIN_CB; u++) mac2(acc[k][u], sw[(k - j) & (IB - 1)], pv[u]);
                             if (++cnt == FOLDK) {
 #pragma unroll
-                                for (int k = 0; k < WIN_IB; k++)
+                                for (int k = 0; k < IB; k++)
 #pragma unroll
                                     for (int u = 0; u < WIN_CB; u++) fold2w(acc[k][u], fc);
                                 cnt = 0;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 1)
         }
         if (act) {
 #pragma unroll
-            for (int k = 0; k < WIN_IB; k++) {
+            for (int k = 0; k < IB; k++) {
                 const int i = i0 + k;
 #pragma unroll
                 for (int u = 0; u < WIN_CB; u++)
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(256)
 // at the end.
 //
 // Warp 0 runs the critical path: per order it eliminates the discrepancy with
-// one column per lane (two for q > 32), right-looking and fraction-free in
+// one column per lane (q <= 32; k_local_wide takes wider blocks), right-looking and fraction-free in
 // Montgomery form -- when the current column (in (degree, index) order) is
 // nonzero it becomes a pivot and every later column is reduced by it at once,
 // so each column is reduced by exactly the pivots created before it.  It
@@ -248,10 +249,9 @@ __global__ void __launch_bounds__(256)
 // holds its coefficient s at row base[c] + s; the other warps use per-order
 // snapshots of sh and base.
 constexpr int LOCAL_THREADS = 1024;
-// threads of k_local: all 32 warps for m <= 8; 16 for m > 8; 8 when q > 32,
-// so that the elimination warp keeps its two columns per lane (about 200
-// residues) in registers -- at 16 warps (128 registers a thread) it spilled
-// to local memory and an order took several times longer
+// threads of k_local: all 32 warps for m <= 8; 16 for m > 8; 8 with two
+// columns per lane (CPL = 2), so that the elimination warp keeps its columns
+// (about 200 residues) in registers
 __host__ __device__ constexpr int local_threads(int MM, int CPL) {
     return CPL > 1 ? LOCAL_THREADS / 4 : (MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS);
 }
@@ -261,15 +261,15 @@ constexpr int SIGMA_CHUNK_DEFAULT = 64;
 // 32), with leaves of SIGMA_LEAF_DEFAULT orders; measured on GB300 at
 // L = 45,002, q = 16 the blocked M-Basis alone is faster (744 ms against
 // 786-1058 ms for leaves of 16,384 down to 1,024 orders).  For q > 32 the
-// M-Basis chunks shrink to a few orders (shared memory) and its passes over
-// the basis dominate: at q = 64, L = 118,752 PM-Basis with 2,048-order leaves
-// takes 83 s against about 530 s, at L = 16,384 11.1 s against 10.2 s; so
-// PM-Basis from SIGMA_PM_MIN_L_WIDE orders on there.  wr_set_sigma_leaf
-// chooses the leaf explicitly.
+// M-Basis chunks are a few orders long (shared memory) and the window and
+// apply passes over the basis grow with its degree, so PM-Basis with short
+// leaves takes over early: at q = 64, L = 8,192, 1,648 / 1,453 / 1,413 ms for
+// leaves of 2,048 / 512 / 256 orders, and at L = 118,752 21.5 s with 512
+// (46 s with 2,048).  wr_set_sigma_leaf chooses the leaf explicitly.
 constexpr int64_t SIGMA_LEAF_DEFAULT = 8192;
 constexpr int64_t SIGMA_PM_MIN_L = 131072;
-constexpr int64_t SIGMA_LEAF_WIDE = 2048;
-constexpr int64_t SIGMA_PM_MIN_L_WIDE = 32768;
+constexpr int64_t SIGMA_LEAF_WIDE = 512;
+constexpr int64_t SIGMA_PM_MIN_L_WIDE = 2048;
 constexpr int BAR_T0 = 1, BAR_RR0 = 3;  // ids BAR_T0 + (i & 1), BAR_RR0 + (i & 1)
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
@@ -805,6 +805,283 @@ __global__ void __launch_bounds__(local_threads(MM, CPL))
     }
 }
 
+// ---- local M-Basis for wide blocks (q = m + n > 32; m <= 32, q <= 64): one
+// block of LW_THREADS threads, every warp taking part in every phase of an
+// order, with barriers between the phases.
+//
+//   ranks : the (degree, index) order of the columns, and the discrepancy
+//           column registers: warp w holds columns w, w + 16, w + 32, w + 48,
+//           lane a row a of each (and coefficient a of its transform);
+//   elim  : one step per column in that order, ended once m pivots are found
+//           (then every remaining column is zero on all m rows).  The owner
+//           warp of the step's column finds its first nonzero row and, if
+//           there is one, publishes the pivot column through a double-buffered
+//           shared slot; after a barrier every warp reduces its later columns
+//           by it, fraction-free as in k_local;
+//   publish: the transform (normal form) and the local degree bounds;
+//   rows  : every row of the window (orders i ..), of Qtop and of the chunk
+//           transform Ml (coefficients 0 .. dl) times the transform, one row
+//           per warp, the pivot residues read as shared-memory broadcasts;
+//   shift : the pivot columns times x, moved in place: window orders i+1 ..
+//           and Ml coefficients 1 .. dl+1 take the column's values one order /
+//           one coefficient down, so that rows stay plain (no per-column
+//           offsets).
+// The pivots, the transforms, P and the degrees are those of k_local.
+constexpr int LW_THREADS = 512;
+constexpr int LW_WARPS = LW_THREADS / 32;
+constexpr int LW_CPW = 64 / LW_WARPS;  // columns per warp in the elimination
+constexpr int LW_SLOT = 68;            // pivot slot: 32 residues, 32 transform coefficients, fr, dc, scale
+
+// dynamic shared memory of k_local_wide for chunks of b orders; the rows of
+// the window and of the transform are padded to q + 1 words, so that a
+// column (one residue per lane, rows apart) falls on distinct banks
+__host__ __device__ constexpr size_t local_wide_bytes(int b, int m, int q) {
+    return sizeof(uint32_t) * ((size_t)b * m * (q + 1) + (size_t)(b + 1) * q * q + (size_t)m * (q + 1) + (size_t)m * q +
+                               64 + 2 * LW_SLOT) +
+           sizeof(int) * (5 * 64 + 32 + 8);
+}
+
+template <int FOLDK>
+__global__ void __launch_bounds__(LW_THREADS, 1)
+    k_local_wide(int m, int n, int q, int bb, int nparts, const uint32_t *__restrict__ Epart,
+                 uint32_t *__restrict__ qtop_g, int32_t *__restrict__ deg_g, uint32_t *__restrict__ Ml_g,
+                 int32_t *__restrict__ degl_g, int *__restrict__ dmax_g, uint32_t *__restrict__ scale_g, int dbase,
+                 ModP mp) {
+    extern __shared__ uint32_t sm[];
+    const int mq = m * q, qq = q * q, qs = q + 1;
+    uint32_t *Es = sm;                            // [bb][m][qs]
+    uint32_t *Ml = Es + (size_t)bb * m * qs;      // [bb+1][q][q]
+    uint32_t *F = Ml + (size_t)(bb + 1) * qq;     // [m][qs] transform of the order
+    uint32_t *qt = F + (size_t)m * qs;            // [m][q]
+    uint32_t *dg = qt + mq;                       // [64]
+    uint32_t *slot = dg + 64;                     // [2][LW_SLOT]
+    int *deg = (int *)(slot + 2 * LW_SLOT);       // [64]
+    int *degl = deg + 64;                         // [64] local degrees
+    int *dln = degl + 64;                         // [64] local degrees after the transform
+    int *colof = dln + 64;                        // [64] column of each rank
+    int *isp = colof + 64;                        // [64] pivot flags of the order
+    int *pcs = isp + 64;                          // [32] pivot columns in order
+    int *misc = pcs + 32;                         // [0]: max local degree after the transform
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t fc = mp.r1;  // 2^32 mod p
+    (void)n;
+
+    for (int x = tid; x < mq; x += LW_THREADS) qt[x] = qtop_g[x];
+    __syncthreads();
+    const int E = bb * mq;
+    for (int x = tid; x < E; x += LW_THREADS) {
+        unsigned long long v = 0;
+        for (int b = 0; b < nparts; b++) v += Epart[(size_t)b * E + x];
+        uint32_t e = red64(v, mp);
+        if (x < mq) e = subm(e, qt[x], mp);
+        Es[(x / q) * qs + x % q] = e;
+    }
+    for (int x = tid; x < (bb + 1) * qq; x += LW_THREADS) Ml[x] = (x < qq && x / q == x % q) ? 1u : 0u;
+    for (int c = tid; c < 64; c += LW_THREADS) {
+        deg[c] = c < q ? deg_g[c] : 0;
+        degl[c] = 0;
+    }
+    uint32_t scum[LW_CPW];  // cumulative column scales over the chunk (Montgomery form)
+#pragma unroll
+    for (int k = 0; k < LW_CPW; k++) scum[k] = mp.r1;
+    __syncthreads();
+
+    for (int i = 0; i < bb; i++) {
+        // ---- ranks and the discrepancy registers
+        uint32_t d[LW_CPW], tp[LW_CPW], sc[LW_CPW];
+        int rk[LW_CPW];
+        {
+            const int la = lane, lb = lane + 32;
+            const int da = la < q ? deg[la] : 0, db = lb < q ? deg[lb] : 0;
+#pragma unroll
+            for (int k = 0; k < LW_CPW; k++) {
+                const int c = warp + LW_WARPS * k;
+                const bool cv = c < q;
+                const int dc = cv ? deg[c] : 0;
+                const bool xa = cv && la < q && (da < dc || (da == dc && la < c));
+                const bool xb = cv && lb < q && (db < dc || (db == dc && lb < c));
+                const int r = __popc(__ballot_sync(FULL, xa)) + __popc(__ballot_sync(FULL, xb));
+                rk[k] = cv ? r : (1 << 20);
+                d[k] = (cv && lane < m) ? to_mont(Es[((size_t)i * m + lane) * qs + c], mp) : 0u;
+                tp[k] = 0u;
+                sc[k] = mp.r1;
+                if (cv && lane == 0) {
+                    colof[r] = c;
+                    isp[c] = 0;
+                }
+            }
+        }
+        if (tid == 0) misc[0] = 0;
+        __syncthreads();
+        // ---- elimination
+        int np = 0;
+        for (int step = 0; step < q && np < m; step++) {
+            const int c = colof[step];
+            uint32_t *sl = slot + (step & 1) * LW_SLOT;
+            if ((c & (LW_WARPS - 1)) == warp) {
+                const int kk = c / LW_WARPS;
+                uint32_t v = 0, t = 0, s = 0;
+#pragma unroll
+                for (int k = 0; k < LW_CPW; k++)
+                    if (k == kk) {
+                        v = d[k];
+                        t = tp[k];
+                        s = sc[k];
+                    }
+                const int fr = __ffs(__ballot_sync(FULL, v != 0u)) - 1;
+                if (fr >= 0) {
+                    const uint32_t dcv = __shfl_sync(FULL, v, fr);
+                    sl[lane] = v;
+                    sl[32 + lane] = t;
+                    if (lane == 0) {
+                        sl[64] = (uint32_t)fr;
+                        sl[65] = dcv;
+                        sl[66] = s;
+                        pcs[np] = c;
+                        isp[c] = 1;
+                    }
+                } else if (lane == 0) {
+                    sl[64] = 0xffffffffu;
+                }
+            }
+            __syncthreads();
+            const int fr = (int)sl[64];
+            if (fr < 0) continue;
+            const uint32_t pv = sl[lane], pt = sl[32 + lane], dcv = sl[65], scc = sl[66];
+#pragma unroll
+            for (int k = 0; k < LW_CPW; k++) {
+                if (rk[k] > step && rk[k] < (1 << 20)) {
+                    const uint32_t dj = __shfl_sync(FULL, d[k], fr);
+                    if (dj != 0u) {
+                        // col <- dc col - dj pivot: dc x + (p - dj) y < 2 p^2 < p 2^32
+                        const uint32_t ndj = mp.p - dj;
+                        d[k] = mont_redc(madw(ndj, pv, (unsigned long long)dcv * d[k]), mp);
+                        if (lane < np) tp[k] = mont_redc(madw(ndj, pt, (unsigned long long)dcv * tp[k]), mp);
+                        else if (lane == np) tp[k] = mont_redc((unsigned long long)ndj * scc, mp);
+                        sc[k] = mont_mul(sc[k], dcv, mp);
+                    }
+                }
+            }
+            np++;
+        }
+        // ---- publish the transform (normal form) and the local degree bounds
+#pragma unroll
+        for (int k = 0; k < LW_CPW; k++) {
+            const int c = warp + LW_WARPS * k;
+            if (c < q) {
+                const uint32_t fv = lane < np ? from_mont(tp[k], mp) : 0u;
+                if (lane < np) F[lane * qs + c] = fv;
+                const int v = __reduce_max_sync(FULL, fv != 0u ? degl[pcs[lane]] : 0);
+                const int dl = max(degl[c], v);
+                if (lane == 0) {
+                    dg[c] = from_mont(sc[k], mp);
+                    dln[c] = dl;
+                    atomicMax(misc, dl);
+                }
+                scum[k] = mont_mul(scum[k], sc[k], mp);
+            }
+        }
+        __syncthreads();
+        const int dl = misc[0];
+        // ---- rows times the transform
+        if (np > 0) {
+            const int ja = lane, jb = lane + 32;
+            const bool vb = jb < q;
+            uint32_t fa[32], fb[32];
+#pragma unroll
+            for (int t = 0; t < 32; t++) {
+                fa[t] = t < np ? F[t * qs + ja] : 0u;
+                fb[t] = (t < np && vb) ? F[t * qs + jb] : 0u;
+            }
+            const uint32_t ga = dg[ja], gb = vb ? dg[jb] : 0u;
+            const int pcl = lane < np ? pcs[lane] : 0;  // lane t fetches the row's residue at pivot column t
+            const int nwin = (bb - i) * m;
+            const int nrows = nwin + m + (dl + 1) * q;
+            for (int row = warp; row < nrows; row += LW_WARPS) {
+                uint32_t *rp = row < nwin ? Es + ((size_t)i * m + row) * qs
+                                          : (row < nwin + m ? qt + (row - nwin) * q : Ml + (size_t)(row - nwin - m) * q);
+                const uint32_t xa = rp[ja], xb = vb ? rp[jb] : 0u, g = rp[pcl];
+                // two accumulators per column (even and odd t), each folded
+                // after FOLDK of its own products
+                unsigned long long a0 = (unsigned long long)ga * xa, b0 = (unsigned long long)gb * xb;
+                unsigned long long a1 = 0ull, b1 = 0ull;
+#pragma unroll
+                for (int t = 0; t < 32; t++) {
+                    if (t < np) {
+                        const uint32_t v = __shfl_sync(FULL, g, t);
+                        if ((t & 1) == 0) {
+                            a0 = madw(fa[t], v, a0);
+                            b0 = madw(fb[t], v, b0);
+                            if ((t / 2 + 2) % FOLDK == 0) {
+                                a0 = fold2(a0, fc);
+                                b0 = fold2(b0, fc);
+                            }
+                        } else {
+                            a1 = madw(fa[t], v, a1);
+                            b1 = madw(fb[t], v, b1);
+                            if (((t + 1) / 2) % FOLDK == 0) {
+                                a1 = fold2(a1, fc);
+                                b1 = fold2(b1, fc);
+                            }
+                        }
+                    }
+                }
+                // folded, each is below 2^62 + 2^32: their sum fits
+                uint32_t ra = red64(fold2(a0, fc) + fold2(a1, fc), mp), rb = red64(fold2(b0, fc) + fold2(b1, fc), mp);
+                if (row >= nwin && row < nwin + m) {  // the next Qtop keeps the pivot columns of Qtop T
+                    if (!isp[ja]) ra = 0u;
+                    if (vb && !isp[jb]) rb = 0u;
+                }
+                __syncwarp();
+                rp[ja] = ra;
+                if (vb) rp[jb] = rb;
+                __syncwarp();
+            }
+        } else {
+            for (int x = tid; x < mq; x += LW_THREADS) qt[x] = 0u;  // no pivot: the next Qtop is zero
+        }
+        __syncthreads();
+        // ---- pivot columns times x (consecutive threads: the pivots of one
+        // row, distinct columns)
+        for (int w = tid; w < np * m; w += LW_THREADS) {
+            const int a = w / np, c = pcs[w - a * np];
+            for (int ip = bb - 1; ip > i; ip--)
+                Es[((size_t)ip * m + a) * qs + c] = Es[((size_t)(ip - 1) * m + a) * qs + c];
+        }
+        for (int w = tid; w < np * q; w += LW_THREADS) {
+            const int y = w / np, c = pcs[w - y * np];
+            for (int s = dl + 1; s > 0; s--) Ml[((size_t)s * q + y) * q + c] = Ml[((size_t)(s - 1) * q + y) * q + c];
+            Ml[(size_t)y * q + c] = 0u;
+        }
+        for (int c = tid; c < q; c += LW_THREADS) {
+            degl[c] = dln[c] + isp[c];
+            deg[c] += isp[c];
+        }
+        __syncthreads();
+    }
+    for (int x = tid; x < (bb + 1) * qq; x += LW_THREADS) Ml_g[x] = Ml[x];
+    for (int x = tid; x < mq; x += LW_THREADS) qtop_g[x] = qt[x];
+    for (int c = tid; c < q; c += LW_THREADS) {
+        deg_g[c] = deg[c];
+        degl_g[c] = degl[c];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < LW_CPW; k++) {
+            const int c = warp + LW_WARPS * k;
+            if (c < q) scale_g[c] = mont_mul(scale_g[c], scum[k], mp);
+        }
+    }
+    if (tid == 0) {
+        // bound on the polynomial degree of the basis: column c's degree
+        // minus the smallest starting degree (the row shifts)
+        int dmx = 0;
+        for (int c = 0; c < q; c++) dmx = max(dmx, deg[c] - dbase);
+        *dmax_g = dmx;
+    }
+}
+
 // P[t][r][c] /= S[c] (S in Montgomery form), t <= D
 __global__ void k_unscale(uint32_t *__restrict__ P, int n, int q, int64_t D, const uint32_t *__restrict__ scale_g,
                           ModP mp) {
@@ -908,6 +1185,111 @@ __global__ void __launch_bounds__(APP_THREADS)
 #pragma unroll
             for (int u = 0; u < APP_CB; u++)
                 if (tl < ta && cv[u]) Pn[(size_t)(t0 + tl) * nq + r * q + c0 + u] = red64(acc2_u64(acc[k][u]), mp);
+        }
+    }
+}
+
+// Four consecutive residues through the read-only data cache (one 16-byte
+// load when VEC), zero where the column is out of range.
+template <bool VEC>
+__device__ __forceinline__ void ldg4(const uint32_t *p, const bool (&cv)[4], uint32_t (&v)[4]) {
+    if constexpr (VEC) {
+        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = cv[u] ? __ldg(p + u) : 0u;
+    }
+}
+
+// P' = P Ml for wide blocks (q > 32), where Ml and whole coefficients of P
+// do not fit in shared memory together: block (coefficient tile of APW_TA,
+// group of APW_RB rows of P); the tile's rows of P (with the bb coefficients
+// below it) in shared memory, Ml through the read-only cache (it is shared by
+// all blocks).  The thread tiles and the register window are those of k_apply.
+constexpr int APW_RB = 4, APW_TA = 32;
+
+__host__ __device__ constexpr size_t apply_wide_bytes(int b, int q) {
+    return sizeof(uint32_t) * (size_t)(APW_TA + b) * APW_RB * q;
+}
+
+template <int FOLDK, bool VEC>
+__global__ void __launch_bounds__(APP_THREADS, 2)
+    k_apply_wide(const uint32_t *__restrict__ P, uint32_t *__restrict__ Pn, int n, int q,
+                 const uint32_t *__restrict__ Ml_g, const int32_t *__restrict__ degl_g, int bb, int64_t Dbound,
+                 const int *__restrict__ dmax_dev, ModP mp) {
+    extern __shared__ uint32_t sm[];
+    __shared__ int degl[64];
+    const int64_t dlim = min64(Dbound, (int64_t)*dmax_dev);
+    const int64_t t0 = (int64_t)blockIdx.x * APW_TA;
+    if (t0 > dlim) return;
+    const int ta = (int)min64(APW_TA, dlim + 1 - t0);
+    const int r0 = blockIdx.y * APW_RB, rn = min(APW_RB, n - r0);
+    const int nq = n * q, rq = APW_RB * q, qq = q * q;
+    const uint32_t fc = mp.r1;  // 2^32 mod p
+    for (int x = threadIdx.x; x < q; x += APP_THREADS) degl[x] = degl_g[x];
+    const int64_t pbase = t0 - bb;  // sm[u rq + rl q + x] holds P[pbase + u][r0 + rl][x]
+    for (int x = threadIdx.x; x < (ta + bb) * rq; x += APP_THREADS) {
+        const int u = x / rq, rem = x - u * rq, rl = rem / q;
+        const int64_t t = pbase + u;
+        sm[x] = (t >= 0 && rl < rn) ? P[(size_t)t * nq + (size_t)(r0 + rl) * q + (rem - rl * q)] : 0u;
+    }
+    __syncthreads();
+    const int ntb = (ta + APP_TB - 1) / APP_TB, ncb = (q + APP_CB - 1) / APP_CB;
+    for (int it = threadIdx.x; it < ntb * APW_RB * ncb; it += APP_THREADS) {
+        const int cb = it % ncb, rl = (it / ncb) % APW_RB, tb = it / (ncb * APW_RB);
+        if (rl >= rn) continue;
+        const int c0 = cb * APP_CB, tl0 = tb * APP_TB;
+        bool cv[APP_CB];
+        int smax = 0;
+#pragma unroll
+        for (int u = 0; u < APP_CB; u++) {
+            cv[u] = c0 + u < q;
+            if (cv[u]) smax = max(smax, degl[c0 + u]);
+        }
+        Acc2 acc[APP_TB][APP_CB];
+#pragma unroll
+        for (int k = 0; k < APP_TB; k++)
+#pragma unroll
+            for (int u = 0; u < APP_CB; u++) acc[k][u] = Acc2{0u, 0u};
+        int cnt = 0;
+        const int top = tl0 + bb;  // coefficient t0 + tl0 + k - s of P is slab row top - s + k
+        for (int x = 0; x < q; x++) {
+            const uint32_t *pc = sm + rl * q + x;       // slab row u at pc[u * rq]
+            const uint32_t *mc = Ml_g + (size_t)x * q + c0;  // coefficient s at mc[s * qq]
+            uint32_t pw[APP_TB];                        // slab row top - s + k in slot (k - s) & 7
+#pragma unroll
+            for (int k = 0; k < APP_TB; k++) pw[k] = pc[(size_t)(top + k) * rq];
+            for (int s0 = 0; s0 <= smax; s0 += 8) {
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int st = s0 + j;
+                    if (st <= smax) {
+                        if (st > 0) pw[(8 - j) & 7] = pc[(size_t)(top - st) * rq];
+                        uint32_t mv[APP_CB];
+                        ldg4<VEC>(mc + (size_t)st * qq, cv, mv);
+#pragma unroll
+                        for (int k = 0; k < APP_TB; k++)
+#pragma unroll
+                            for (int u = 0; u < APP_CB; u++) mac2(acc[k][u], pw[(k - j) & 7], mv[u]);
+                        if (++cnt == FOLDK) {
+#pragma unroll
+                            for (int k = 0; k < APP_TB; k++)
+#pragma unroll
+                                for (int u = 0; u < APP_CB; u++) fold2w(acc[k][u], fc);
+                            cnt = 0;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < APP_TB; k++) {
+            const int tl = tl0 + k;
+#pragma unroll
+            for (int u = 0; u < APP_CB; u++)
+                if (tl < ta && cv[u])
+                    Pn[(size_t)(t0 + tl) * nq + (size_t)(r0 + rl) * q + c0 + u] = red64(acc2_u64(acc[k][u]), mp);
         }
     }
 }
@@ -1067,16 +1449,22 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
         return sizeof(uint32_t) * ((size_t)TT * nq + (size_t)(nib * WIN_IB + TT - 1) * m * nr);
     };
     auto apply_bytes = [&](int ta, int b) { return sizeof(uint32_t) * ((size_t)(b + 1) * q * q + (size_t)(ta + b) * nq); };
+    // wide blocks (q > 32): k_local_wide and k_apply_wide, and chunks one
+    // order shorter at a time (their shared memory grows in steps of a few KB)
+    const bool wide = q > 32;
+    auto local_need = [&](int b) { return wide ? local_wide_bytes(b, m, q) : local_bytes(b); };
+    auto apply_need = [&](int ta, int b) { return wide ? apply_wide_bytes(b, q) : apply_bytes(ta, b); };
     int bmax = ctx->sigma_chunk > 0 ? std::min(ctx->sigma_chunk, 64) : SIGMA_CHUNK_DEFAULT, TT = 32, TA = 64;
     for (;;) {
         while (TT > 4 && window_bytes(TT, bmax) > budget) TT /= 2;
-        while (TA > APP_TB && apply_bytes(TA, bmax) > budget) TA /= 2;
-        if (local_bytes(bmax) <= budget && window_bytes(TT, bmax) <= budget && apply_bytes(TA, bmax) <= budget) break;
+        while (TA > APP_TB && apply_need(TA, bmax) > budget) TA /= 2;
+        if (local_need(bmax) <= budget && window_bytes(TT, bmax) <= budget && apply_need(TA, bmax) <= budget) break;
         if (bmax == 1) return fail(WR_EINVAL, "block sizes too large for shared memory");
-        bmax /= 2;
+        bmax = wide ? bmax - 1 : bmax / 2;
         TT = 32;
         TA = 64;
     }
+    if (wide) TA = APW_TA;
     const int nparts_max = std::max(1, 2 * ctx->num_sms);
     WR_TRY(dev_alloc(ctx, Epart, sizeof(uint32_t) * (size_t)nparts_max * bmax * m * q));
     WR_TRY(dev_alloc(ctx, Ml, sizeof(uint32_t) * (size_t)(bmax + 1) * q * q));
@@ -1089,22 +1477,43 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
     }
     const bool lazy16 = mp.lazy >= 16;
     const bool vec = q % 4 == 0;
-    auto *kwin = lazy16 ? (vec ? k_window<14, true> : k_window<14, false>)
-                        : (vec ? k_window<2, true> : k_window<2, false>);
-    auto *kapp = lazy16 ? (vec ? k_apply<14, true> : k_apply<14, false>)
-                        : (vec ? k_apply<2, true> : k_apply<2, false>);
+    // fold interval of the lazily reduced sums: 14 (p < 2^30), 3 (2^32 mod p
+    // small, as for p = 2^31 - 19), else 2
+    const int fk = fold_products(p), fold = fk >= 14 ? 14 : (fk >= 3 ? 3 : 2);
+    // order tiles of 4 for chunks of at most 4 orders (8 would idle half the tile)
+    auto win_for = [&](int b) {
+        if (b <= 4)
+            return fold == 14 ? (vec ? k_window<14, true, 4> : k_window<14, false, 4>)
+                   : fold == 3 ? (vec ? k_window<3, true, 4> : k_window<3, false, 4>)
+                               : (vec ? k_window<2, true, 4> : k_window<2, false, 4>);
+        return fold == 14 ? (vec ? k_window<14, true, 8> : k_window<14, false, 8>)
+               : fold == 3 ? (vec ? k_window<3, true, 8> : k_window<3, false, 8>)
+                           : (vec ? k_window<2, true, 8> : k_window<2, false, 8>);
+    };
+    auto *kwin = win_for(bmax);
+    auto *kwin_tail = win_for(std::min<int64_t>(bmax, L % bmax ? L % bmax : bmax));
+    auto *kapp = fold == 14 ? (vec ? k_apply<14, true> : k_apply<14, false>)
+                 : fold == 3 ? (vec ? k_apply<3, true> : k_apply<3, false>)
+                             : (vec ? k_apply<2, true> : k_apply<2, false>);
+    auto *kapp_w = fold == 14 ? (vec ? k_apply_wide<14, true> : k_apply_wide<14, false>)
+                   : fold == 3 ? (vec ? k_apply_wide<3, true> : k_apply_wide<3, false>)
+                               : (vec ? k_apply_wide<2, true> : k_apply_wide<2, false>);
     DevBuf Esum;
     WR_TRY(dev_alloc(ctx, Esum, sizeof(uint32_t) * (size_t)bmax * m * q));
     using LocalFn = void (*)(int, int, int, int, int, const uint32_t *, uint32_t *, int32_t *, uint32_t *, int32_t *,
                              int *, uint32_t *, int, ModP);
     LocalFn kloc;
-    if (m <= 8)
-        kloc = q <= 32 ? (lazy16 ? k_local<8, 1, 16> : k_local<8, 1, 4>) : (lazy16 ? k_local<8, 2, 16> : k_local<8, 2, 4>);
+    if (wide)
+        kloc = fold == 14 ? k_local_wide<14> : (fold == 3 ? k_local_wide<3> : k_local_wide<2>);
+    else if (m <= 8)
+        kloc = lazy16 ? k_local<8, 1, 16> : k_local<8, 1, 4>;
     else
-        kloc = q <= 32 ? (lazy16 ? k_local<32, 1, 16> : k_local<32, 1, 4>) : (lazy16 ? k_local<32, 2, 16> : k_local<32, 2, 4>);
+        kloc = lazy16 ? k_local<32, 1, 16> : k_local<32, 1, 4>;
     WR_CUDA(cudaFuncSetAttribute(kwin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+    WR_CUDA(cudaFuncSetAttribute(kwin_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     WR_CUDA(cudaFuncSetAttribute(kloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     WR_CUDA(cudaFuncSetAttribute(kapp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+    WR_CUDA(cudaFuncSetAttribute(kapp_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
 
     uint32_t *Pcur = d_P, *Pnext = P2.as<uint32_t>();
     int64_t Dbound = 1;
@@ -1162,7 +1571,7 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
         const int64_t tspan = std::min<int64_t>(Dbound, k0 + bb - 1) + 1;
         const int nparts = (int)std::min<int64_t>(nparts_max, std::max<int64_t>(1, (tspan + TT - 1) / TT));
         const int64_t tper = (tspan + nparts - 1) / nparts;
-        kwin<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, nr, q, Pcur, k0, bb, TT, tper,
+        (bb == bmax ? kwin : kwin_tail)<<<nparts, WIN_THREADS, window_bytes(TT, bb), s>>>(d_S, L, m, nr, q, Pcur, k0, bb, TT, tper,
                                                                 dmax.as<int>(), Epart.as<uint32_t>(), mp);
         WR_LAUNCHED(ctx);
         const uint32_t *Ewin = Epart.as<uint32_t>();
@@ -1179,15 +1588,20 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
             WR_LAUNCHED(ctx);
         }
         if (prof) WR_CUDA(cudaEventRecord(pe[1], s));
-        kloc<<<1, local_threads(m <= 8 ? 8 : 32, q <= 32 ? 1 : 2), local_bytes(bb), s>>>(
+        kloc<<<1, wide ? LW_THREADS : local_threads(m <= 8 ? 8 : 32, 1), local_need(bb), s>>>(
             m, n, q, bb, 1, Ewin, qtop.as<uint32_t>(), d_deg, Ml.as<uint32_t>(),
             degl.as<int32_t>(), dmax.as<int>(), scale.as<uint32_t>(), dbase, mp);
         WR_LAUNCHED(ctx);
         if (prof) WR_CUDA(cudaEventRecord(pe[2], s));
         if (Dbound + bb > Dcap + 1) return fail(WR_EINVAL, "sigma-basis degree cap too small");
         const int64_t Dnew = std::min<int64_t>(Dbound + bb, Dcap);
-        kapp<<<(unsigned)((Dnew + TA) / TA), APP_THREADS, apply_bytes(TA, bb), s>>>(
-            Pcur, Pnext, nr, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, dmax.as<int>(), mp);
+        if (wide)
+            kapp_w<<<dim3((unsigned)((Dnew + TA) / TA), (unsigned)((nr + APW_RB - 1) / APW_RB)), APP_THREADS,
+                     apply_need(TA, bb), s>>>(Pcur, Pnext, nr, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew,
+                                              dmax.as<int>(), mp);
+        else
+            kapp<<<(unsigned)((Dnew + TA) / TA), APP_THREADS, apply_bytes(TA, bb), s>>>(
+                Pcur, Pnext, nr, q, Ml.as<uint32_t>(), degl.as<int32_t>(), bb, Dnew, TA, dmax.as<int>(), mp);
         WR_LAUNCHED(ctx);
         if (prof) {
             WR_CUDA(cudaEventRecord(pe[3], s));
@@ -1299,6 +1713,7 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
                       uint32_t *d_P, int32_t *d_deg, int64_t Dcap) {
     if (m < 1 || n < 1 || m > 32 || n > 32) return fail(WR_EINVAL, "block sizes must be in 1..32");
     ctx->last.sigma_window_ms = ctx->last.sigma_local_ms = ctx->last.sigma_apply_ms = 0.0;
+    ctx->last.sigma_product_ms = 0.0;
     const bool automatic = ctx->sigma_leaf <= 0;
     const bool wide = m + n > 32;
     const int64_t leaf = automatic ? (wide ? SIGMA_LEAF_WIDE : SIGMA_LEAF_DEFAULT) : ctx->sigma_leaf;
@@ -1323,35 +1738,57 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     WR_CUDA(cudaMemcpyAsync(d_deg, deg0.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s));
     WR_CUDA(cudaStreamSynchronize(s));
     int64_t DM = 0;
-    // Trailing a sequence still in flight: the basis of the first h orders
-    // needs S_0 .. S_{h-1} only, so that half of the top-level split runs
-    // while the sequence computes its last terms; the residual of the rest,
-    // its basis and the product follow once the sequence has ended.  h is
-    // about 70 % of the orders (the first part's share of the work about
-    // matches the share of the sequence still to come), a multiple of 64.
-    const int64_t h = ctx->feed ? std::min<int64_t>(L - 64, ((L * 7 / 10) / 64) * 64) : 0;
-    if (ctx->feed && h >= leaf && L - h >= 64) {
-        WR_TRY(feed_wait(ctx, ctx->feed, h));
-        WR_TRY(build_F(0, h));
-        DevBuf M1, M2, R;
-        int64_t DM1 = 0, DM2 = 0;
+    // Trailing a sequence still in flight: the orders are taken in segments
+    // [h_{k-1}, h_k) as the sequence publishes them.  A segment's residual is
+    // R_k = (F M) div x^h_{k-1} mod x^(h_k - h_{k-1}) (F's first h_k
+    // coefficients times the basis M of the orders before it, a middle
+    // product), its sigma-basis M_k starts from M's degrees, and M <- M M_k:
+    // PM-Basis's split at h_{k-1}, applied once per segment.  Each segment is
+    // about half of the orders still to come, down to 2 leaves, so that what
+    // is left after the sequence's last term (the time it adds to the rank)
+    // is one short segment and two products.
+    if (ctx->feed && L > 2 * leaf) {
+        std::vector<int64_t> hs;
+        const int64_t seg_min = 2 * leaf;
+        for (int64_t h = 0; h < L;) {
+            const int64_t rem = L - h;
+            h += rem <= 2 * seg_min ? rem : std::max<int64_t>(seg_min, ((rem / 2 + 63) / 64) * 64);
+            hs.push_back(h);
+        }
         std::vector<int32_t> hd(q);
-        WR_TRY(pm_basis_rec(ctx, F.as<uint32_t>(), h, m, q, p, d_deg, leaf, M1, DM1));
-        WR_TRY(feed_wait(ctx, ctx->feed, L));
-        WR_TRY(build_F(h, L));
-        WR_TRY(dev_alloc(ctx, R, sizeof(uint32_t) * (size_t)(L - h) * m * q));
-        WR_TRY(polymat_mul(ctx, F.as<uint32_t>(), L, M1.as<uint32_t>(), DM1 + 1, m, q, q, h, L, p, R.as<uint32_t>()));
-        WR_TRY(pm_basis_rec(ctx, R.as<uint32_t>(), L - h, m, q, p, d_deg, leaf, M2, DM2));
-        R.release();
-        WR_CUDA(cudaMemcpyAsync(hd.data(), d_deg, sizeof(int32_t) * q, cudaMemcpyDeviceToHost, s));
-        WR_CUDA(cudaStreamSynchronize(s));
-        // starting degrees (0^n, 1^m): the smallest is 0
-        const int64_t bound = (int64_t)*std::max_element(hd.begin(), hd.end());
-        DM = std::max<int64_t>(0, std::min<int64_t>(DM1 + DM2, bound));
-        WR_TRY(dev_alloc(ctx, M, sizeof(uint32_t) * (size_t)(DM + 2) * q * q));
-        WR_CUDA(cudaMemsetAsync(M.ptr, 0, M.bytes, s));
-        WR_TRY(polymat_mul(ctx, M1.as<uint32_t>(), DM1 + 1, M2.as<uint32_t>(), DM2 + 1, q, q, q, 0, DM + 1, p,
-                           M.as<uint32_t>()));
+        int64_t hprev = 0;
+        for (size_t k = 0; k < hs.size(); k++) {
+            const int64_t hk = hs[k], d = hk - hprev;
+            WR_TRY(feed_wait(ctx, ctx->feed, hk));
+            WR_TRY(build_F(hprev, hk));
+            DevBuf R, Mk;
+            int64_t DMk = 0;
+            if (k > 0) {
+                WR_TRY(dev_alloc(ctx, R, sizeof(uint32_t) * (size_t)d * m * q));
+                WR_TRY(polymat_mul(ctx, F.as<uint32_t>(), hk, M.as<uint32_t>(), DM + 1, m, q, q, hprev, hk, p,
+                                   R.as<uint32_t>()));
+            }
+            WR_TRY(pm_basis_rec(ctx, k > 0 ? R.as<uint32_t>() : F.as<uint32_t>(), d, m, q, p, d_deg, leaf, Mk, DMk));
+            R.release();
+            if (k == 0) {
+                M = std::move(Mk);
+                DM = DMk;
+            } else {
+                WR_CUDA(cudaMemcpyAsync(hd.data(), d_deg, sizeof(int32_t) * q, cudaMemcpyDeviceToHost, s));
+                WR_CUDA(cudaStreamSynchronize(s));
+                // starting degrees (0^n, 1^m): the smallest is 0
+                const int64_t bound = (int64_t)*std::max_element(hd.begin(), hd.end());
+                const int64_t DMn = std::max<int64_t>(0, std::min<int64_t>(DM + DMk, bound));
+                DevBuf Mn;
+                WR_TRY(dev_alloc(ctx, Mn, sizeof(uint32_t) * (size_t)(DMn + 2) * q * q));
+                WR_CUDA(cudaMemsetAsync(Mn.ptr, 0, Mn.bytes, s));
+                WR_TRY(polymat_mul(ctx, M.as<uint32_t>(), DM + 1, Mk.as<uint32_t>(), DMk + 1, q, q, q, 0, DMn + 1, p,
+                                   Mn.as<uint32_t>()));
+                M = std::move(Mn);
+                DM = DMn;
+            }
+            hprev = hk;
+        }
     } else {
         if (ctx->feed) WR_TRY(feed_wait(ctx, ctx->feed, L));  // PM-Basis reads the whole sequence
         WR_TRY(build_F(0, L));

@@ -52,7 +52,8 @@ class wr_timings(ctypes.Structure):
                 ("spmm_launches", ctypes.c_int64), ("spmm_bytes", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("sigma_window_ms", ctypes.c_double),
                 ("sigma_local_ms", ctypes.c_double), ("sigma_apply_ms", ctypes.c_double),
-                ("sigma_tail_ms", ctypes.c_double), ("sequence_terms", ctypes.c_int64)]
+                ("sigma_tail_ms", ctypes.c_double), ("sequence_terms", ctypes.c_int64),
+                ("sigma_product_ms", ctypes.c_double)]
 
 
 class wr_server_cfg(ctypes.Structure):

@@ -263,6 +263,30 @@ def test_rank_pipeline_matches_sequential(wr, ctx, m, n, sym, chunk):
     assert np.array_equal(got["S"], ref["S"]) and np.array_equal(got["F"], ref["F"])
 
 
+@pytest.mark.parametrize("m,leaf,R,C,r", [(4, 64, 1300, 1150, 1020), (8, 64, 1300, 1150, 900),
+                                          (32, 64, 4400, 4200, 4000), (20, 64, 3000, 2900, 2700)])
+def test_rank_pipeline_pm_segments(wr, ctx, m, leaf, R, C, r):
+    """PM-Basis trailing the sequence in segments (each about half of the
+    orders still to come, down to two leaves; leaves forced short so that a
+    small case has several segments, wide blocks included): the same
+    generator and rank as PM-Basis on the whole sequence, and both equal the
+    oracle's."""
+    p = 2147483629
+    A = synth.planted_sparse(R, C, r, row_len=6, seed=m * 7 + leaf)
+    try:
+        wr.wr_set_sigma_leaf(ctx, leaf)
+        got = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
+        wr.wr_set_pipeline(ctx, False)
+        seq = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
+    finally:
+        wr.wr_set_pipeline(ctx, True)
+        wr.wr_set_sigma_leaf(ctx, 0)
+    assert got["rank"] == seq["rank"] == r
+    assert np.array_equal(got["S"], seq["S"]) and np.array_equal(got["F"], seq["F"])
+    ref = oracle.rank_wiedemann(A, p, m, m, seed=5)
+    assert np.array_equal(got["F"], ref["F"]) and got["rank"] == ref["rank"]
+
+
 @pytest.mark.parametrize("m,sym,chunk,quiet,R,C,r", [(4, False, 0, 64, 2100, 2000, 600),
                                                        (8, True, 0, 64, 3000, 2600, 1200),
                                                        (4, False, 16, 48, 1800, 1700, 400),
@@ -510,7 +534,8 @@ def gpu_sigma(wr, ctx, S, p):
 
 
 @pytest.mark.parametrize("m,n,L", [(1, 1, 50), (2, 3, 77), (3, 2, 130), (8, 8, 200), (5, 5, 65),
-                                   (16, 16, 70), (32, 32, 40)])
+                                   (16, 16, 70), (32, 32, 40), (24, 20, 61), (32, 16, 50), (17, 32, 45),
+                                   (32, 31, 39), (32, 1, 90)])
 @pytest.mark.parametrize("p", [65521, 2147483629])
 def test_sigma_basis_random_sequence(wr, ctx, m, n, L, p):
     rng = np.random.default_rng(m * 1000 + n * 10 + L)
@@ -523,7 +548,7 @@ def test_sigma_basis_random_sequence(wr, ctx, m, n, L, p):
     assert not P[D + 1:].any()
 
 
-@pytest.mark.parametrize("m,n", [(1, 1), (4, 4), (2, 6)])
+@pytest.mark.parametrize("m,n", [(1, 1), (4, 4), (2, 6), (20, 24), (32, 32)])
 def test_sigma_basis_wiedemann_sequence(wr, ctx, m, n):
     """Structured (rank-deficient) sequences: degenerate discrepancies."""
     p = 65521
@@ -534,6 +559,50 @@ def test_sigma_basis_wiedemann_sequence(wr, ctx, m, n):
     P, dg = gpu_sigma(wr, ctx, S, p)
     assert np.array_equal(dg, deg)
     assert np.array_equal(P[: M.shape[0]], M[:, :n, :])
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 3, 5, 7])
+@pytest.mark.parametrize("p", [65521, 2147483629])
+def test_sigma_basis_wide_chunks(wr, ctx, chunk, p):
+    """Wide blocks (q = 64 and q = 45) with the chunk length forced: every
+    chunk length up to the largest that fits, and ragged last chunks."""
+    for m, n, L in [(32, 32, 37), (25, 20, 43)]:
+        rng = np.random.default_rng(m * 100 + chunk)
+        S = rng.integers(0, p, size=(L, m, n)).astype(np.uint32)
+        M, deg = oracle.mbasis(S, p)
+        wr.wr_set_sigma_chunk(ctx, chunk)
+        try:
+            P, dg = gpu_sigma(wr, ctx, S, p)
+        finally:
+            wr.wr_set_sigma_chunk(ctx, 0)
+        assert np.array_equal(dg, deg)
+        D = M.shape[0] - 1
+        assert np.array_equal(P[: D + 1], M[:, :n, :])
+        assert not P[D + 1:].any()
+
+
+def test_sigma_basis_wide_rank_deficient_discrepancies(wr, ctx):
+    """q = 64 with discrepancies of rank below m (sequences of a rank-5
+    matrix, and one with zero columns): non-pivot columns before the m-th
+    pivot, and orders with no pivot at all."""
+    p = 1073741789
+    rng = np.random.default_rng(11)
+    m = n = 32
+    U = rng.integers(0, p, size=(m, 5)).astype(object)
+    V = rng.integers(0, p, size=(5, n)).astype(object)
+    L = 40
+    S = np.zeros((L, m, n), np.uint32)
+    for k in range(L):
+        Dk = np.diag(rng.integers(0, p, size=5).astype(object))
+        S[k] = ((U.dot(Dk).dot(V)) % p).astype(np.uint32)
+    S2 = S.copy()
+    S2[:, :, 7] = 0
+    S2[3] = 0
+    for T in [S, S2]:
+        M, deg = oracle.mbasis(T, p)
+        P, dg = gpu_sigma(wr, ctx, T, p)
+        assert np.array_equal(dg, deg)
+        assert np.array_equal(P[: M.shape[0]], M[:, :n, :])
 
 
 def test_sigma_basis_degenerate_sequences(wr, ctx):
@@ -661,7 +730,7 @@ def test_errors_are_reported(wr, ctx):
 
 @pytest.mark.parametrize("m,n,L,leaf", [(1, 1, 700, 64), (2, 3, 610, 64), (3, 2, 900, 200), (4, 4, 950, 128),
                                       (8, 8, 1300, 200), (8, 8, 700, 64), (5, 5, 390, 64), (1, 1, 9000, 512),
-                                      (2, 2, 6100, 256), (16, 16, 500, 64), (32, 32, 200, 64)])
+                                      (2, 2, 6100, 256), (16, 16, 500, 64), (32, 32, 200, 64), (24, 20, 200, 64)])
 @pytest.mark.parametrize("p", [65521, 2147483629, 1073741789])
 def test_pm_basis_matches_order_by_order(wr, ctx, m, n, L, leaf, p):
     """PM-Basis (recursive halving, NTT products over three FFT primes, CRT
