@@ -6,19 +6,24 @@ uniform columns), planted rank 1,805,000, block m = n = 32, p = 2147483629,
 L = 118,752 terms.
 
 A timed step is the next stretch of that sequence: TERMS_PER_STEP = 256 terms
-S_0 .. S_255, i.e. 128 applications of the preconditioned black box to the
-paired block [D1 X | D1 Y] (width 64) with both SpMM passes and the two Gram
-projections of each application (the captured 64-application graphs of the
-sequence loop), plus the sequence set-up (D1, D2, X, Y, T_0, S_0).  Inputs are
-resident in HBM (the matrix loaded once).  value = SpMM nnz*vec per second over
-the timed steps (2 passes x nnz x 64 block columns per application).  In the
-same run: the whole time to rank of the workload (ingest from pinned host CSR,
-all L terms, sigma-basis, readout; e2e), the secondary 200,000 x 180,000
+S_0 .. S_255 with the symmetric projection of Section 2.3 (X = Y^T; the
+paper's own choice), i.e. 128 applications of the preconditioned black box to
+the block D1 Y (width 32) with both SpMM passes and the two Gram projections
+of each application (S_2k = V_k^T V_k after pass 2, S_2k+1 from pass 1's
+output; the captured 64-application graphs of the sequence loop), plus the
+sequence set-up (D1, D2, Y, T_0, S_0).  Inputs are resident in HBM (the matrix
+loaded once).  value = SpMM nnz*vec per second over the timed steps (2 passes
+x nnz x 32 block columns per application; --projection generic: the paired
+block [D1 X | D1 Y] of width 64).  In the same run: the whole time to rank of
+the workload (ingest from pinned host CSR, all L terms, sigma-basis trailing
+the sequence with its stream first, readout; e2e), the same with the generic
+projection (an independent X, Section 2.5), the secondary 200,000 x 180,000
 block-8 workload's time to rank, the roofline of k_spmm and the CPU oracle on
 a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wr|reference]
-                    [--matrix c2|c1] [--projection generic|symmetric] [--no-time-to-rank]
+                    [--matrix c2|c1] [--projection symmetric|generic] [--pipeline 0|1|2]
+                    [--no-time-to-rank] [--no-generic-time-to-rank]
                     [--chain-reduction] [--locality-order] [--early-termination ORDERS]
                     [--workload single|batch|serve] [--only-blackbox | --only-sigma | --probe-mma]
 
@@ -70,28 +75,33 @@ def workload(rank: int = 0, matrix: str = "c2"):
         "columns), planted rank 1805000; block Wiedemann m=n=32 mod p=2147483629, L=118752" % A.nnz))
 
 
-def spmm_traffic(kernel_file="paper_0704_2351_gb300/csrc/wr_spmm.cu",
+def spmm_traffic(width, kernel_file="paper_0704_2351_gb300/csrc/wr_spmm.cu",
                  summary="profiles/spmm_traffic_config2.md"):
-    """DRAM bytes (read + write) per k_spmm launch on the bench workload, from
-    the committed ncu summary's line `traffic_bytes_per_launch: X source_sha256:
-    Y`; None when the SpMM source has changed since that capture (Y differs
-    from the current file's hash) or the summary is missing."""
+    """DRAM bytes (read + write) per k_spmm launch on the bench workload at
+    the given block width, from the committed ncu summary's line
+    `traffic_bytes_per_launch: X source_sha256: Y width: W`; None when the
+    SpMM source has changed since that capture (Y differs from the current
+    file's hash) or there is no line for that width."""
     try:
         text = open(os.path.join(ROOT, summary)).read()
         src = hashlib.sha256(open(os.path.join(ROOT, kernel_file), "rb").read()).hexdigest()
     except OSError:
         return None, "no summary"
+    stale = False
     for line in text.splitlines():
         if line.strip().startswith("traffic_bytes_per_launch:"):
             f = line.split()
             try:
-                val, sha = float(f[1]), f[3]
+                val, sha, w = float(f[1]), f[3], int(f[5])
             except (IndexError, ValueError):
-                return None, "unparsable summary line"
+                continue
+            if w != width:
+                continue
             if sha != src:
-                return None, "k_spmm source changed since the capture"
+                stale = True
+                continue
             return val, summary
-    return None, "no traffic line in the summary"
+    return None, ("k_spmm source changed since the capture" if stale else "no traffic line for width %d" % width)
 
 
 def apply_options(wr, ctx, args):
@@ -101,6 +111,7 @@ def apply_options(wr, ctx, args):
     wr.wr_set_chain_reduction(ctx, bool(getattr(args, "chain_reduction", False)))
     wr.wr_set_locality_order(ctx, bool(getattr(args, "locality_order", False)))
     wr.wr_set_early_termination(ctx, int(getattr(args, "early_termination", 0)))
+    wr.wr_set_pipeline(ctx, int(getattr(args, "pipeline", 2)))
     wr.wr_set_column_slabs(ctx, int(getattr(args, "slab_bytes", 0)))
 
 
@@ -110,6 +121,7 @@ def options_config(args):
            "early_termination_orders": int(getattr(args, "early_termination", 0))}
     if int(getattr(args, "slab_bytes", 0)) != 0:
         out["column_slab_bytes"] = int(args.slab_bytes)
+    out["pipeline"] = {0: "off", 1: "sequence first", 2: "sigma-basis first"}[int(getattr(args, "pipeline", 2))]
     return out
 
 
@@ -531,7 +543,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": cfg["name"], "step": "one sparse pass mod p of the CPU "
+            "data": "synthetic", "config": {"workload": cfg["name"], "projection": args.projection,
+                                            "step": "one sparse pass mod p of the CPU "
                                             "oracle: an eighth of the rows times the %d-column block" % cfg["n"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d row slices of one eighth of the matrix, one pass each" % args.steps},
@@ -576,7 +589,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-rank", action="store_true",
                     help="skip the whole time-to-rank runs (timed steps only)")
-    ap.add_argument("--projection", default="generic", choices=["generic", "symmetric"])
+    ap.add_argument("--no-generic-time-to-rank", action="store_true",
+                    help="skip the second time to rank with the generic projection")
+    ap.add_argument("--projection", default="symmetric", choices=["generic", "symmetric"],
+                    help="symmetric: X = Y^T (Section 2.3), two terms per application of the width-n block "
+                         "(default); generic: independent X, paired with Y in one width-2n block when m = n")
     ap.add_argument("--multi", default="slab", choices=["slab", "independent"],
                     help="N > 1: column slabs of one sequence (default) or an independent matrix per rank")
     ap.add_argument("--only-blackbox", action="store_true",
@@ -607,6 +624,9 @@ def main():
                     help="remove unit singleton rows/columns at load (rank = pivots + rank of the rest)")
     ap.add_argument("--locality-order", action="store_true",
                     help="renumber rows and columns by decreasing entry count at load (same results)")
+    ap.add_argument("--pipeline", type=int, default=2, choices=[0, 1, 2],
+                    help="time to rank: sigma-basis after the sequence (0), trailing it with the sequence's "
+                         "stream first (1) or with its own stream first (2)")
     ap.add_argument("--slab-bytes", type=int, default=0,
                     help="gathered block bytes per column slab of the SpMM passes (0: no slabs, the default)")
     ap.add_argument("--early-termination", type=int, default=0,
@@ -742,7 +762,7 @@ def run_single(args):
         avg_s = spmm_ms / spmm_launches * 1e-3
         per_launch = spmm_bytes / spmm_launches
         ach = per_launch / avg_s / 1e9
-        traffic, tsrc = spmm_traffic()
+        traffic, tsrc = spmm_traffic(width)
         roof = {"bound": "hbm", "achieved": ach, "peak": peak if peak else 6800.0, "unit": "GB/s",
                 "frac": ach / (peak if peak else 6800.0), "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "fallback",
@@ -782,6 +802,16 @@ def run_single(args):
                        "d2h_bytes_per_step": 8, "ms_per_step": 1e3 * el,
                        "step": "one whole rank computation: CSR ingest from pinned host memory, all %d terms, "
                                "sigma-basis, readout; value = the sequence's nnz*vec / wall time" % L}
+        if args.matrix == "c2" and sym and not args.no_generic_time_to_rank:
+            # the other projection on the same matrix (the independent X of
+            # Section 2.5, paired with Y in one width-64 block)
+            prm_g = wr.make_params(p, m, n, cfg["seed"], projection=wr.WR_PROJ_GENERIC)
+            rg, elg, tmg, _ = _time_to_rank_host(wr, ctx, A, prm_g)
+            assert rg == A.rank, "rank %d != planted %d" % (rg, A.rank)
+            line["time_to_rank_generic_ms"] = 1e3 * elg
+            line["time_to_rank_generic_phases_ms"] = {k: round(tmg[k], 1) for k in
+                                                      ["setup_ms", "sequence_ms", "sigma_ms", "sigma_tail_ms",
+                                                       "readout_ms"]}
         if args.matrix == "c2":
             A1, cfg1 = workload(0, "c1")
             prm1 = wr.make_params(cfg1["p"], cfg1["m"], cfg1["n"], cfg1["seed"])

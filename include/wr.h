@@ -169,8 +169,13 @@ wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
  * second stream driven by a second host thread.  M-Basis orders k .. k+b-1
  * need only S_0 .. S_{k+b-1} (Section 2.4's sigma-basis is computed order by
  * order), so each chunk starts as soon as the sequence has produced its terms
- * and the two phases overlap on the device.  Results do not depend on it. */
-wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on);
+ * and the two phases overlap on the device.  Results do not depend on it.
+ * mode 0: off (the sigma-basis after the sequence); 1 (default): on, the
+ * sequence's stream at the greatest priority (its SpMM blocks go first, the
+ * sigma-basis fills the gaps); 2: on, the sigma-basis's stream at the greatest
+ * priority (it keeps up with the terms as they are published and the SpMM
+ * takes the rest of the device).  Other values: WR_EINVAL. */
+wr_status wr_set_pipeline(wr_ctx *ctx, int32_t mode);
 /* Early termination of wr_rank (off by default; orders = 0).  The trailing
  * M-Basis watches the generator candidates (the n basis columns of smallest
  * shifted degree); once they have had zero discrepancy for `orders`

@@ -262,9 +262,10 @@ extern "C" wr_status wr_set_early_termination(wr_ctx *ctx, int64_t orders) {
     return WR_OK;
 }
 
-extern "C" wr_status wr_set_pipeline(wr_ctx *ctx, int32_t on) {
+extern "C" wr_status wr_set_pipeline(wr_ctx *ctx, int32_t mode) {
     if (!ctx) return fail(WR_EINVAL, "null context");
-    ctx->pipeline = on != 0;
+    if (mode < 0 || mode > 2) return fail(WR_EINVAL, "pipeline mode must be 0 (off), 1 (sequence first) or 2 (sigma-basis first)");
+    ctx->pipeline = mode;
     return WR_OK;
 }
 
@@ -524,9 +525,47 @@ void copy_settings(const wr_ctx *parent, wr_ctx *c) {
     c->alloc_user = parent->alloc_user;
 }
 
-wr_status make_child(const wr_ctx *parent, wr_ctx **out) {
-    WR_TRY(wr_create(out, parent->device, nullptr));
+// The greatest (high) or least stream priority of the device.
+static int stream_priority(bool high) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    return high ? greatest : least;
+}
+
+wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool sigma_role) {
+    // a sigma-basis child of a pipeline that puts the sigma-basis first
+    // (wr_set_pipeline(ctx, 2)) gets a stream of the greatest priority
+    const bool high = sigma_role && parent->pipeline == 2;
+    cudaStream_t s = nullptr;
+    WR_CUDA(cudaSetDevice(parent->device));
+    WR_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, stream_priority(high)));
+    const wr_status st = wr_create(out, parent->device, s);
+    if (st != WR_OK) {
+        cudaStreamDestroy(s);
+        return st;
+    }
+    (*out)->own_stream = true;
+    (*out)->high_priority = high;
     copy_settings(parent, *out);
+    return WR_OK;
+}
+
+// The pipeline's sequence stream: the greatest priority when the sequence
+// goes first (mode 1), the least when the sigma-basis does (mode 2).
+static wr_status ensure_seq_stream(wr_ctx *ctx) {
+    const bool high = ctx->pipeline != 2;
+    if (ctx->seq_stream && ctx->seq_high == high) return WR_OK;
+    if (ctx->seq_stream) {
+        cudaStreamSynchronize(ctx->seq_stream);
+        cudaStreamDestroy(ctx->seq_stream);
+        ctx->seq_stream = nullptr;
+    }
+    cudaError_t ce = cudaStreamCreateWithPriority(&ctx->seq_stream, cudaStreamNonBlocking, stream_priority(high));
+    if (ce != cudaSuccess) {
+        ctx->seq_stream = nullptr;
+        return cuda_fail(ce, "cudaStreamCreateWithPriority");
+    }
+    ctx->seq_high = high;
     return WR_OK;
 }
 
@@ -632,15 +671,15 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
         // own host thread) runs M-Basis chunk k as soon as the sequence
         // stream has published S_0 .. S_{k+b-1}, so the two overlap on the
         // device and only the last chunks run after the sequence ends.
-        if (!ctx->aux) st = make_child(ctx, &ctx->aux);
-        if (st == WR_OK && !ctx->seq_stream) {
-            // the sequence's SpMM blocks go first wherever both phases have
-            // blocks waiting; the sigma-basis fills the gaps
-            int least = 0, greatest = 0;
-            cudaDeviceGetStreamPriorityRange(&least, &greatest);
-            cudaError_t ce = cudaStreamCreateWithPriority(&ctx->seq_stream, cudaStreamNonBlocking, greatest);
-            if (ce != cudaSuccess) { ctx->seq_stream = nullptr; st = cuda_fail(ce, "cudaStreamCreateWithPriority"); }
+        // mode 1: the sequence's SpMM blocks go first wherever both phases
+        // have blocks waiting and the sigma-basis fills the gaps; mode 2:
+        // the sigma-basis first (its streams at the greatest priority)
+        if (ctx->aux && ctx->aux->high_priority != (ctx->pipeline == 2)) {
+            wr_destroy(ctx->aux);
+            ctx->aux = nullptr;
         }
+        if (!ctx->aux) st = make_child(ctx, &ctx->aux, true);
+        if (st == WR_OK) st = ensure_seq_stream(ctx);
         wr_ctx *aux = ctx->aux;
         SeqFeed feed;
         feed.throttle = ctx->early_term > 0 ? 3 : 0;
@@ -773,16 +812,11 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
     std::vector<wr_ctx *> kids(G, nullptr);
     wr_status st = WR_OK;
     for (int g = 0; g < G && st == WR_OK; g++) {
-        st = make_child(ctx, &kids[g]);
+        st = make_child(ctx, &kids[g], true);
         if (st == WR_OK) copy_settings(ctx, kids[g]);
     }
-    const bool piped = ctx->pipeline;
-    if (st == WR_OK && piped && !ctx->seq_stream) {
-        int least = 0, greatest = 0;
-        cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        cudaError_t ce = cudaStreamCreateWithPriority(&ctx->seq_stream, cudaStreamNonBlocking, greatest);
-        if (ce != cudaSuccess) { ctx->seq_stream = nullptr; st = cuda_fail(ce, "cudaStreamCreateWithPriority"); }
-    }
+    const bool piped = ctx->pipeline != 0;
+    if (st == WR_OK && piped) st = ensure_seq_stream(ctx);
     std::vector<std::unique_ptr<SeqFeed>> feeds;
     std::vector<SeqFeed *> fptr;
     cudaEvent_t ready0 = nullptr;

@@ -274,8 +274,9 @@ def wr_set_paired_projection(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_paired_projection(vp(ctx), 1 if on else 0))
 
 
-def wr_set_pipeline(ctx: int, on: bool) -> None:
-    _check(_lib.wr_set_pipeline(vp(ctx), 1 if on else 0))
+def wr_set_pipeline(ctx: int, mode: int) -> None:
+    """0 off, 1 (True) the sequence's stream first, 2 the sigma-basis's first."""
+    _check(_lib.wr_set_pipeline(vp(ctx), int(mode)))
 
 
 def wr_set_early_termination(ctx: int, orders: int) -> None:

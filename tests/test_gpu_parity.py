@@ -276,13 +276,19 @@ def test_rank_pipeline_pm_segments(wr, ctx, m, leaf, R, C, r):
     try:
         wr.wr_set_sigma_leaf(ctx, leaf)
         got = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
+        wr.wr_set_pipeline(ctx, 2)  # the sigma-basis's stream first
+        got2 = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
         wr.wr_set_pipeline(ctx, False)
         seq = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
+        for bad in [3, -1]:
+            with pytest.raises(wr.WrError):
+                wr.wr_set_pipeline(ctx, bad)
     finally:
         wr.wr_set_pipeline(ctx, True)
         wr.wr_set_sigma_leaf(ctx, 0)
-    assert got["rank"] == seq["rank"] == r
+    assert got["rank"] == seq["rank"] == got2["rank"] == r
     assert np.array_equal(got["S"], seq["S"]) and np.array_equal(got["F"], seq["F"])
+    assert np.array_equal(got2["S"], seq["S"]) and np.array_equal(got2["F"], seq["F"])
     ref = oracle.rank_wiedemann(A, p, m, m, seed=5)
     assert np.array_equal(got["F"], ref["F"]) and got["rank"] == ref["rank"]
 
@@ -941,3 +947,24 @@ def test_config2_rank(wr, ctx, config2):
     rng = np.random.default_rng(5)
     for i in [0] + list(rng.integers(0, 50000, size=2)):
         assert _annihilates(g["S"], g["F"], g["delta"], p, int(i))
+
+
+def test_config2_rank_symmetric(wr, ctx, config2):
+    """Config 2 with the symmetric projection of Section 2.3 (X = Y^T: two
+    terms per application of the width-32 block) and the sigma-basis's stream
+    first: the planted rank 1,805,000, the generator annihilates the sequence
+    at sampled offsets, and S_0 .. S_2 equal the oracle's literal loop."""
+    A = config2
+    p, m, n, seed = 2147483629, 32, 32, synth.SEED_BASE + 2
+    wr.wr_set_pipeline(ctx, 2)
+    try:
+        g = gpu_rank(wr, ctx, A, p, m, n, seed, want=3, symmetric=True)
+    finally:
+        wr.wr_set_pipeline(ctx, 1)
+    assert g["rank"] == A.rank == 1805000
+    assert g["seq_len"] == 118752
+    rng = np.random.default_rng(6)
+    for i in [0] + list(rng.integers(0, 50000, size=2)):
+        assert _annihilates(g["S"], g["F"], g["delta"], p, int(i))
+    st = oracle.Setup(A, p, m, n, seed=seed, symmetric=True)
+    assert np.array_equal(g["S"][:3], oracle.sequence(A, st, 3))
