@@ -16,13 +16,13 @@ loaded once).  value = SpMM nnz*vec per second over the timed steps (2 passes
 x nnz x 32 block columns per application; --projection generic: the paired
 block [D1 X | D1 Y] of width 64).  In the same run: the whole time to rank of
 the workload (ingest from pinned host CSR, all L terms, sigma-basis trailing
-the sequence with its stream first, readout; e2e), the same with the generic
+the sequence, readout; e2e), the same with the generic
 projection (an independent X, Section 2.5), the secondary 200,000 x 180,000
 block-8 workload's time to rank, the roofline of k_spmm and the CPU oracle on
 a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wr|reference]
-                    [--matrix c2|c1] [--projection symmetric|generic] [--pipeline 0|1|2]
+                    [--matrix c2|c1] [--projection symmetric|generic] [--pipeline 0|1|2|3]
                     [--no-time-to-rank] [--no-generic-time-to-rank]
                     [--chain-reduction] [--locality-order] [--early-termination ORDERS]
                     [--workload single|batch|serve] [--only-blackbox | --only-sigma | --probe-mma]
@@ -75,7 +75,7 @@ def workload(rank: int = 0, matrix: str = "c2"):
         "columns), planted rank 1805000; block Wiedemann m=n=32 mod p=2147483629, L=118752" % A.nnz))
 
 
-def spmm_traffic(width, kernel_file="paper_0704_2351_gb300/csrc/wr_spmm.cu",
+def spmm_traffic(width, kernel_file="paper_0704_2351_gb300/csrc/wr_spmm_kernel.cuh",
                  summary="profiles/spmm_traffic_config2.md"):
     """DRAM bytes (read + write) per k_spmm launch on the bench workload at
     the given block width, from the committed ncu summary's line
@@ -111,7 +111,8 @@ def apply_options(wr, ctx, args):
     wr.wr_set_chain_reduction(ctx, bool(getattr(args, "chain_reduction", False)))
     wr.wr_set_locality_order(ctx, bool(getattr(args, "locality_order", False)))
     wr.wr_set_early_termination(ctx, int(getattr(args, "early_termination", 0)))
-    wr.wr_set_pipeline(ctx, int(getattr(args, "pipeline", 2)))
+    wr.wr_set_pipeline(ctx, int(getattr(args, "pipeline", 1)))
+    wr.wr_set_projection_overlap(ctx, bool(getattr(args, "projection_overlap", False)))
     wr.wr_set_column_slabs(ctx, int(getattr(args, "slab_bytes", 0)))
 
 
@@ -121,7 +122,10 @@ def options_config(args):
            "early_termination_orders": int(getattr(args, "early_termination", 0))}
     if int(getattr(args, "slab_bytes", 0)) != 0:
         out["column_slab_bytes"] = int(args.slab_bytes)
-    out["pipeline"] = {0: "off", 1: "sequence first", 2: "sigma-basis first"}[int(getattr(args, "pipeline", 2))]
+    out["pipeline"] = {0: "off", 1: "automatic", 2: "sigma-basis first",
+                       3: "sequence first"}[int(getattr(args, "pipeline", 1))]
+    if bool(getattr(args, "projection_overlap", False)):
+        out["projection_overlap"] = True
     return out
 
 
@@ -455,27 +459,30 @@ def run_sigma_only(args):
 
 def run_gram_only(args):
     """The projection's Gram product alone on rows shaped as the default
-    workload's paired block (N = 1,900,000 rows of 64 residues, X half and Y
-    half of 32, p = 2147483629): wr_gram_device with the tensor-core path and
-    with the integer path, W + K calls each (for profiler captures of
-    k_gram_tc and its time per Gram)."""
+    workload's block (N = 1,900,000 rows of 32 residues, L = R = the row,
+    p = 2147483629; --gram-width 64: the paired generic block, X half and Y
+    half of 32): wr_gram_device with the tensor-core path and with the
+    integer path, W + K calls each (for profiler captures of k_gram_tc and
+    its time per Gram)."""
     import torch
     from paper_0704_2351_gb300 import wr
     p, m, n, N = 2147483629, 32, 32, args.gram_rows
     g = torch.Generator().manual_seed(1)
-    t = torch.randint(0, p, (N, 64), generator=g, dtype=torch.int64).to(torch.int32).cuda()
+    rw = args.gram_width
+    yoff = 0 if rw == 32 else 32
+    t = torch.randint(0, p, (N, rw), generator=g, dtype=torch.int64).to(torch.int32).cuda()
     w = torch.randint(1, p, (N,), generator=g, dtype=torch.int64).to(torch.int32).cuda()
     G = torch.empty((m, n), dtype=torch.int32, device="cuda")
     ctx = wr.wr_create(0)
-    out = {"only": "gram", "rows": N, "block": [m, n], "row_residues": 64}
+    out = {"only": "gram", "rows": N, "block": [m, n], "row_residues": rw}
     for mode, name in [(1, "tensor_cores_ms"), (0, "integer_ms")]:
         wr.wr_set_tensor_projection(ctx, mode)
         for _ in range(args.warmup):
-            wr.wr_gram_device(ctx, p, N, m, n, t, 64, 32, w, G)
+            wr.wr_gram_device(ctx, p, N, m, n, t, rw, yoff, w, G)
         torch.cuda.synchronize()
         tt = time.perf_counter()
         for _ in range(args.steps):
-            wr.wr_gram_device(ctx, p, N, m, n, t, 64, 32, w, G)
+            wr.wr_gram_device(ctx, p, N, m, n, t, rw, yoff, w, G)
         torch.cuda.synchronize()
         out[name] = 1e3 * (time.perf_counter() - tt) / max(args.steps, 1)
     print(json.dumps(out), flush=True)
@@ -603,6 +610,8 @@ def main():
     ap.add_argument("--probe-mma", action="store_true", help="the tensor-core rate probe")
     ap.add_argument("--only-gram", action="store_true", help="only the projection's Gram product (profiler captures)")
     ap.add_argument("--gram-rows", type=int, default=1900000, help="--only-gram: rows of the block")
+    ap.add_argument("--gram-width", type=int, default=32, choices=[32, 64],
+                    help="--only-gram: residues per row (32: symmetric block; 64: paired generic block)")
     ap.add_argument("--sigma-chunk", type=int, default=0, help="orders per sigma-basis chunk (0: automatic)")
     ap.add_argument("--sigma-leaf", type=int, default=0, help="orders per PM-Basis leaf (0: automatic)")
     ap.add_argument("--sigma-block", type=int, default=0,
@@ -624,9 +633,11 @@ def main():
                     help="remove unit singleton rows/columns at load (rank = pivots + rank of the rest)")
     ap.add_argument("--locality-order", action="store_true",
                     help="renumber rows and columns by decreasing entry count at load (same results)")
-    ap.add_argument("--pipeline", type=int, default=2, choices=[0, 1, 2],
-                    help="time to rank: sigma-basis after the sequence (0), trailing it with the sequence's "
-                         "stream first (1) or with its own stream first (2)")
+    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="time to rank: sigma-basis after the sequence (0), trailing it with automatic stream "
+                         "priorities (1), with its own stream first (2) or with the sequence's first (3)")
+    ap.add_argument("--projection-overlap", action="store_true",
+                    help="the Gram projections beside the passes on a side stream (measured slower)")
     ap.add_argument("--slab-bytes", type=int, default=0,
                     help="gathered block bytes per column slab of the SpMM passes (0: no slabs, the default)")
     ap.add_argument("--early-termination", type=int, default=0,

@@ -170,11 +170,14 @@ wr_status wr_set_lane_width(wr_ctx *ctx, int32_t residues);
  * need only S_0 .. S_{k+b-1} (Section 2.4's sigma-basis is computed order by
  * order), so each chunk starts as soon as the sequence has produced its terms
  * and the two phases overlap on the device.  Results do not depend on it.
- * mode 0: off (the sigma-basis after the sequence); 1 (default): on, the
- * sequence's stream at the greatest priority (its SpMM blocks go first, the
- * sigma-basis fills the gaps); 2: on, the sigma-basis's stream at the greatest
- * priority (it keeps up with the terms as they are published and the SpMM
- * takes the rest of the device).  Other values: WR_EINVAL. */
+ * mode 0: off (the sigma-basis after the sequence); 2: on, the
+ * sigma-basis's stream at the greatest priority (it keeps up with the terms
+ * as they are published and the SpMM takes the rest of the device); 3: on,
+ * the sequence's stream at the greatest priority (its SpMM blocks go first,
+ * the sigma-basis fills the gaps); 1 (default): on, 2 when the sigma-basis
+ * trails in PM-Basis segments (whose kernels need most of an SM and would
+ * fall behind) and 3 when the blocked M-Basis trails chunk by chunk.  Other
+ * values: WR_EINVAL. */
 wr_status wr_set_pipeline(wr_ctx *ctx, int32_t mode);
 /* Early termination of wr_rank (off by default; orders = 0).  The trailing
  * M-Basis watches the generator candidates (the n basis columns of smallest
@@ -197,6 +200,18 @@ wr_status wr_set_early_termination(wr_ctx *ctx, int64_t orders);
  * two terms.  Off: one term per
  * application on a block of width n.  The sequence is the same either way. */
 wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on);
+/* Gram projections beside the passes (off by default): with two terms per
+ * application (the symmetric projection, or the paired generic one) the
+ * Gram product of W = D2 A D1 V_k runs on a second stream beside the pass
+ * that produces the next T, and the Gram product of T beside the next
+ * application's first pass; each pass waits only for the Gram product that
+ * still reads the buffer it overwrites, and every group of applications
+ * joins the sequence stream at its end.  The sequence is the same either
+ * way (Section 2.3's terms, summed in the same order).  Measured on GB300 on
+ * the 1.9M x 1.95M block-32 matrix it is slower: the tensor-core Gram blocks
+ * take SM resources from the SpMM's gathers (a width-32 pass 741 -> 940 us),
+ * which costs more than the Gram products it hides. */
+wr_status wr_set_projection_overlap(wr_ctx *ctx, int32_t on);
 /* Where the Gram projections run (the terms of the symmetric projection and of
  * the paired generic one, Section 2.3; Table tab:r-opp col. 3 is the paper's
  * dot-product step): 1 = the tensor cores, 0 = 64-bit integer multiply-adds,

@@ -264,8 +264,15 @@ extern "C" wr_status wr_set_early_termination(wr_ctx *ctx, int64_t orders) {
 
 extern "C" wr_status wr_set_pipeline(wr_ctx *ctx, int32_t mode) {
     if (!ctx) return fail(WR_EINVAL, "null context");
-    if (mode < 0 || mode > 2) return fail(WR_EINVAL, "pipeline mode must be 0 (off), 1 (sequence first) or 2 (sigma-basis first)");
+    if (mode < 0 || mode > 3)
+        return fail(WR_EINVAL, "pipeline mode must be 0 (off), 1 (automatic), 2 (sigma-basis first) or 3 (sequence first)");
     ctx->pipeline = mode;
+    return WR_OK;
+}
+
+extern "C" wr_status wr_set_projection_overlap(wr_ctx *ctx, int32_t on) {
+    if (!ctx) return fail(WR_EINVAL, "null context");
+    ctx->proj_overlap = on != 0;
     return WR_OK;
 }
 
@@ -512,6 +519,7 @@ void copy_settings(const wr_ctx *parent, wr_ctx *c) {
     c->lane_width = parent->lane_width;
     c->pair_generic = parent->pair_generic;
     c->pipeline = parent->pipeline;
+    c->proj_overlap = parent->proj_overlap;
     c->early_term = parent->early_term;
     c->chain_reduce = parent->chain_reduce;
     c->reorder = parent->reorder;
@@ -532,10 +540,7 @@ static int stream_priority(bool high) {
     return high ? greatest : least;
 }
 
-wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool sigma_role) {
-    // a sigma-basis child of a pipeline that puts the sigma-basis first
-    // (wr_set_pipeline(ctx, 2)) gets a stream of the greatest priority
-    const bool high = sigma_role && parent->pipeline == 2;
+wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool high) {
     cudaStream_t s = nullptr;
     WR_CUDA(cudaSetDevice(parent->device));
     WR_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, stream_priority(high)));
@@ -550,10 +555,20 @@ wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool sigma_role) {
     return WR_OK;
 }
 
-// The pipeline's sequence stream: the greatest priority when the sequence
-// goes first (mode 1), the least when the sigma-basis does (mode 2).
-static wr_status ensure_seq_stream(wr_ctx *ctx) {
-    const bool high = ctx->pipeline != 2;
+// Which stream of a pipelined rank goes first: mode 2 the sigma-basis's, 3
+// the sequence's, 1 (automatic) the sigma-basis's when it trails in PM-Basis
+// segments (their kernels need most of an SM and wait long for SMs to drain
+// of SpMM blocks, so without the priority they fall behind the terms) and
+// the sequence's when the blocked M-Basis trails chunk by chunk (its kernels
+// fill the gaps between the SpMM's).
+static bool sigma_goes_first(const wr_ctx *ctx, int64_t L, int m, int n) {
+    if (ctx->pipeline == 2) return true;
+    if (ctx->pipeline == 3) return false;
+    return sigma_pm_trailing(ctx, L, m, n);
+}
+
+// The pipeline's sequence stream at the greatest priority or at the least.
+static wr_status ensure_seq_stream(wr_ctx *ctx, bool high) {
     if (ctx->seq_stream && ctx->seq_high == high) return WR_OK;
     if (ctx->seq_stream) {
         cudaStreamSynchronize(ctx->seq_stream);
@@ -674,12 +689,13 @@ wr_status rank_one(wr_ctx *ctx, const wr_matrix *mat, const wr_params *params, w
         // mode 1: the sequence's SpMM blocks go first wherever both phases
         // have blocks waiting and the sigma-basis fills the gaps; mode 2:
         // the sigma-basis first (its streams at the greatest priority)
-        if (ctx->aux && ctx->aux->high_priority != (ctx->pipeline == 2)) {
+        const bool sfirst = sigma_goes_first(ctx, L, r.m, r.n);
+        if (ctx->aux && ctx->aux->high_priority != sfirst) {
             wr_destroy(ctx->aux);
             ctx->aux = nullptr;
         }
-        if (!ctx->aux) st = make_child(ctx, &ctx->aux, true);
-        if (st == WR_OK) st = ensure_seq_stream(ctx);
+        if (!ctx->aux) st = make_child(ctx, &ctx->aux, sfirst);
+        if (st == WR_OK) st = ensure_seq_stream(ctx, !sfirst);
         wr_ctx *aux = ctx->aux;
         SeqFeed feed;
         feed.throttle = ctx->early_term > 0 ? 3 : 0;
@@ -811,12 +827,13 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
     // while it runs on the high-priority sequence stream.
     std::vector<wr_ctx *> kids(G, nullptr);
     wr_status st = WR_OK;
+    const bool piped = ctx->pipeline != 0;
+    const bool sfirst = piped && sigma_goes_first(ctx, L, r0.m, r0.n);
     for (int g = 0; g < G && st == WR_OK; g++) {
-        st = make_child(ctx, &kids[g], true);
+        st = make_child(ctx, &kids[g], sfirst);
         if (st == WR_OK) copy_settings(ctx, kids[g]);
     }
-    const bool piped = ctx->pipeline != 0;
-    if (st == WR_OK && piped) st = ensure_seq_stream(ctx);
+    if (st == WR_OK && piped) st = ensure_seq_stream(ctx, !sfirst);
     std::vector<std::unique_ptr<SeqFeed>> feeds;
     std::vector<SeqFeed *> fptr;
     cudaEvent_t ready0 = nullptr;

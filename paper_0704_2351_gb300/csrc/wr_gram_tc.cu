@@ -22,7 +22,7 @@
 // acc[b] += sum_j 2^{8j} D[i*32 + a][j*NB + b], and at the end
 //   G[a][b] = sum_i 2^{8i} acc_i[a][b]  mod p.
 // The rows of t and their weights reach shared memory by 1-D bulk copies
-// (two tiles in flight per block, two blocks per SM),
+// (up to five tiles in flight per block, two blocks per SM),
 // the threads rewrite them as digit tiles in the MMA's swizzled layout, and
 // one thread issues the MMAs and commits them to an mbarrier; operand tiles
 // are double-buffered.  Every wait is bounded: after WAIT_NS the block records
@@ -42,7 +42,6 @@ namespace {
 
 constexpr int GT_THREADS = 256;
 constexpr int GT_KT = 64;     // rows per tile
-constexpr int GT_NS = 2;      // raw tiles in flight per block (two blocks a SM)
 constexpr int GT_DRAIN = 8;   // tiles per drain of the accumulator (512 rows)
 constexpr uint64_t GT_WAIT_NS = 2000000000ull;
 constexpr int GT_ERR_TIMEOUT = 1;
@@ -56,10 +55,15 @@ struct GramShape {
     static constexpr uint32_t RAWB = (uint32_t)GT_KT * RB; // one raw tile
     static constexpr uint32_t TMEM_COLS = TN < 32 ? 32 : TN;
     static constexpr uint32_t WB = (uint32_t)GT_KT * 4;   // one tile's weights
-    static constexpr size_t SMEM = 1024 + 2 * (size_t)OPB + GT_NS * ((size_t)RAWB + WB) + 128;
+    // raw tiles in flight per block (two blocks a SM): five for rows of up to
+    // 128 bytes (32 KB in flight a block, what the shared memory of two
+    // blocks allows), two for the wider rows
+    static constexpr int NS = RB <= 128 ? 5 : 2;
+    static constexpr size_t SMEM = 1024 + 2 * (size_t)OPB + NS * ((size_t)RAWB + WB) + 128;
     static_assert(NB == 8 || NB == 16 || NB == 32, "NB");
     static_assert(RB % 16 == 0 && RB >= 32 && RB <= 256, "RB");
-    static_assert(4u * 32u * NB * 4u <= GT_NS * RAWB, "reduction area");
+    static_assert(4u * 32u * NB * 4u <= NS * RAWB, "reduction area");
+    static_assert(2 * (SMEM + 1024) <= 228 * 1024, "two blocks a SM");
 };
 
 // Digit I of two consecutive values (y = x + 0x808080 each) as an fp16 pair:
@@ -116,9 +120,9 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
     extern __shared__ unsigned char gsm[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
     unsigned char *raw = base + 2 * S::OPB;
-    uint32_t *wts = reinterpret_cast<uint32_t *>(raw + GT_NS * S::RAWB);  // GT_NS x 64 weights
-    uint64_t *bar_raw = reinterpret_cast<uint64_t *>(wts + GT_NS * GT_KT);
-    uint64_t *bar_mma = bar_raw + GT_NS;
+    uint32_t *wts = reinterpret_cast<uint32_t *>(raw + S::NS * S::RAWB);  // NS x 64 weights
+    uint64_t *bar_raw = reinterpret_cast<uint64_t *>(wts + S::NS * GT_KT);
+    uint64_t *bar_mma = bar_raw + S::NS;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_mma + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
     for (uint32_t i = (uint32_t)tid * 16u; i < 2u * S::OPB; i += GT_THREADS * 16u)
         *reinterpret_cast<uint4 *>(base + i) = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        for (int s = 0; s < GT_NS; s++) tc::mbar_init(&bar_raw[s], 1);
+        for (int s = 0; s < S::NS; s++) tc::mbar_init(&bar_raw[s], 1);
         tc::mbar_init(&bar_mma[0], 1);
         tc::mbar_init(&bar_mma[1], 1);
         tc::fence_mbar_init();
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
 
     int64_t issued = 0;  // raw tiles whose copies were issued (thread 0)
     auto issue = [&](int64_t tl) {
-        const int s = (int)(tl % GT_NS);
+        const int s = (int)(tl % S::NS);
         const int64_t r0 = (t_begin + tl) * GT_KT;
         const uint32_t rows = (uint32_t)min64(GT_KT, N - r0);
         const uint32_t wrows = rows & ~3u;  // whole 16-byte groups of weights; the rest by plain loads
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
         if (wrows) tc::bulk_g2s(wts + s * GT_KT, w + r0, wrows * 4u, &bar_raw[s]);
     };
     if (tid == 0) {
-        for (; issued < ntile && issued < GT_NS; issued++) issue(issued);
+        for (; issued < ntile && issued < S::NS; issued++) issue(issued);
     }
 
     long long acc[NB];
@@ -167,11 +171,11 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
     bool aborted = false;   // some thread's wait ran out (the same in every thread)
 
     for (int64_t tl = 0; tl < ntile; tl++) {
-        const int sr = (int)(tl % GT_NS), so = (int)(tl & 1);
+        const int sr = (int)(tl % S::NS), so = (int)(tl & 1);
         const int g = (int)(tl % GT_DRAIN);
         unsigned char *opA = base + so * S::OPB, *opB = opA + S::ABYTES;
         // the raw rows have landed; the operand stage's previous MMAs are done
-        if (!tc::mbar_wait(&bar_raw[sr], (uint32_t)((tl / GT_NS) & 1), GT_WAIT_NS)) bad = true;
+        if (!tc::mbar_wait(&bar_raw[sr], (uint32_t)((tl / S::NS) & 1), GT_WAIT_NS)) bad = true;
         if (tl >= 2 && !tc::mbar_wait(&bar_mma[so], (uint32_t)(((tl >> 1) - 1) & 1), GT_WAIT_NS)) bad = true;
         const int64_t r0 = (t_begin + tl) * GT_KT;
         const int rows = (int)min64(GT_KT, N - r0);
@@ -251,8 +255,8 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
         // record the error, let the copies and MMAs in flight finish (bounded)
         if (tid == 0) {
             atomicExch(err, GT_ERR_TIMEOUT);
-            for (int64_t tl = max64(0, issued - GT_NS); tl < issued; tl++)
-                tc::mbar_wait(&bar_raw[tl % GT_NS], (uint32_t)((tl / GT_NS) & 1), GT_WAIT_NS);
+            for (int64_t tl = max64(0, issued - S::NS); tl < issued; tl++)
+                tc::mbar_wait(&bar_raw[tl % S::NS], (uint32_t)((tl / S::NS) & 1), GT_WAIT_NS);
             if (committed > 0) {
                 const int64_t last = committed - 1;
                 tc::mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1), GT_WAIT_NS);

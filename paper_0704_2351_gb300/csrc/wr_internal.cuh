@@ -376,8 +376,10 @@ struct wr_ctx {
     int lane_width = 0;     // forced SpMM residues per lane (0: tuned or default)
     bool pair_generic = true; // generic projection, m = n: X and Y in one block, two terms per application
     int tensor_proj = -1;   // Gram projections on the tensor cores: 1 on, 0 off, -1 automatic
+    bool proj_overlap = false; // Gram projections on a side stream beside the SpMM passes
     int pipeline = 1;       // wr_rank: the sigma-basis trails the sequence on a second stream
-                            // (0 off, 1 the sequence's stream first, 2 the sigma-basis's first)
+                            // (0 off, 1 automatic priority, 2 the sigma-basis's stream first,
+                            // 3 the sequence's first)
     bool high_priority = false; // this context's own stream has the greatest priority
     bool seq_high = false;      // seq_stream has the greatest priority
     int64_t early_term = 0; // quiet orders that end the sequence early (0: the full L terms)
@@ -494,9 +496,11 @@ wr_status run_sequence(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm, 
 wr_status feed_wait(wr_ctx *ctx, SeqFeed *feed, int64_t terms);
 // A context on the parent's device with its own stream and the parent's settings.
 // A context on the parent's device with the parent's settings and a stream
-// of its own; sigma_role: it runs a pipeline's sigma-basis (its stream then
-// follows the pipeline mode's priority).
-wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool sigma_role = false);
+// of its own, of the greatest priority when high (else the least).
+wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool high = false);
+// Whether sigma_basis, trailing a sequence of L terms with blocks m x n,
+// runs PM-Basis in segments (else the blocked M-Basis chunk by chunk).
+bool sigma_pm_trailing(const wr_ctx *ctx, int64_t L, int m, int n);
 void copy_settings(const wr_ctx *parent, wr_ctx *child);
 wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                          const uint32_t *d_in, uint32_t *d_out, int64_t width);

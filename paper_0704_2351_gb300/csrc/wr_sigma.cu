@@ -1709,18 +1709,31 @@ static wr_status pm_basis_rec(wr_ctx *ctx, const uint32_t *F, int64_t d, int m, 
                        M.as<uint32_t>());
 }
 
+static int64_t sigma_leaf_for(const wr_ctx *ctx, int m, int n) {
+    return ctx->sigma_leaf > 0 ? ctx->sigma_leaf : (m + n > 32 ? SIGMA_LEAF_WIDE : SIGMA_LEAF_DEFAULT);
+}
+
+// PM-Basis (else the blocked M-Basis) for L orders; early termination needs
+// the order-by-order basis (PM-Basis splits the orders in halves and so needs
+// all of them from the start)
+static bool sigma_uses_pm(const wr_ctx *ctx, int64_t L, int m, int n, bool early) {
+    const int64_t leaf = sigma_leaf_for(ctx, m, n);
+    const bool automatic = ctx->sigma_leaf <= 0;
+    return !(early || L <= leaf || (automatic && L <= (m + n > 32 ? SIGMA_PM_MIN_L_WIDE : SIGMA_PM_MIN_L)));
+}
+
+bool sigma_pm_trailing(const wr_ctx *ctx, int64_t L, int m, int n) {
+    return sigma_uses_pm(ctx, L, m, n, ctx->early_term > 0) && L > 2 * sigma_leaf_for(ctx, m, n);
+}
+
 wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n, uint32_t p,
                       uint32_t *d_P, int32_t *d_deg, int64_t Dcap) {
     if (m < 1 || n < 1 || m > 32 || n > 32) return fail(WR_EINVAL, "block sizes must be in 1..32");
     ctx->last.sigma_window_ms = ctx->last.sigma_local_ms = ctx->last.sigma_apply_ms = 0.0;
     ctx->last.sigma_product_ms = 0.0;
-    const bool automatic = ctx->sigma_leaf <= 0;
-    const bool wide = m + n > 32;
-    const int64_t leaf = automatic ? (wide ? SIGMA_LEAF_WIDE : SIGMA_LEAF_DEFAULT) : ctx->sigma_leaf;
-    // early termination needs the order-by-order basis (PM-Basis splits the
-    // orders in halves and so needs all of them from the start)
+    const int64_t leaf = sigma_leaf_for(ctx, m, n);
     const bool early = ctx->feed && ctx->early_term > 0;
-    if (early || L <= leaf || (automatic && L <= (wide ? SIGMA_PM_MIN_L_WIDE : SIGMA_PM_MIN_L)))
+    if (!sigma_uses_pm(ctx, L, m, n, early))
         return mbasis_run(ctx, d_S, L, m, n, n, p, d_P, d_deg, nullptr, 0, Dcap, nullptr);
     const int q = m + n;
     cudaStream_t s = ctx->stream;
@@ -1740,33 +1753,36 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     int64_t DM = 0;
     // Trailing a sequence still in flight: the orders are taken in segments
     // [h_{k-1}, h_k) as the sequence publishes them.  A segment's residual is
-    // R_k = (F M) div x^h_{k-1} mod x^(h_k - h_{k-1}) (F's first h_k
-    // coefficients times the basis M of the orders before it, a middle
-    // product), its sigma-basis M_k starts from M's degrees, and M <- M M_k:
+    // R_k = (F M) div x^h_{k-1} mod x^(h_k - h_{k-1}) (a middle product of F's
+    // coefficients [h_{k-1} - deg M, h_k) and the basis M of the orders before
+    // it), its sigma-basis M_k starts from M's degrees, and M <- M M_k:
     // PM-Basis's split at h_{k-1}, applied once per segment.  Each segment is
-    // about half of the orders still to come, down to 2 leaves, so that what
-    // is left after the sequence's last term (the time it adds to the rank)
-    // is one short segment and two products.
+    // about half of the orders still to come, down to two leaves, so that
+    // what is left after the sequence's last term is one short segment and two
+    // products.  (Segments that take every term finished meanwhile, from the
+    // first sixteenth on, were measured slower on the 1.9M x 1.95M block-32
+    // matrix: their kernels ran beside the SpMM for the whole sequence, each
+    // segment with its two products, and cost the SpMM more than the shorter
+    // tail saved.)
     if (ctx->feed && L > 2 * leaf) {
-        std::vector<int64_t> hs;
         const int64_t seg_min = 2 * leaf;
-        for (int64_t h = 0; h < L;) {
-            const int64_t rem = L - h;
-            h += rem <= 2 * seg_min ? rem : std::max<int64_t>(seg_min, ((rem / 2 + 63) / 64) * 64);
-            hs.push_back(h);
-        }
         std::vector<int32_t> hd(q);
         int64_t hprev = 0;
-        for (size_t k = 0; k < hs.size(); k++) {
-            const int64_t hk = hs[k], d = hk - hprev;
+        for (int k = 0; hprev < L; k++) {
+            const int64_t rem = L - hprev;
+            const int64_t hk =
+                hprev + (rem <= 2 * seg_min ? rem : std::max<int64_t>(seg_min, ((rem / 2 + 63) / 64) * 64));
+            const int64_t d = hk - hprev;
             WR_TRY(feed_wait(ctx, ctx->feed, hk));
             WR_TRY(build_F(hprev, hk));
             DevBuf R, Mk;
             int64_t DMk = 0;
             if (k > 0) {
+                // R_i = sum_j F_j M_{i-j}, j in [i - DM, i]: F from hprev - DM on
+                const int64_t off = std::max<int64_t>(0, hprev - DM);
                 WR_TRY(dev_alloc(ctx, R, sizeof(uint32_t) * (size_t)d * m * q));
-                WR_TRY(polymat_mul(ctx, F.as<uint32_t>(), hk, M.as<uint32_t>(), DM + 1, m, q, q, hprev, hk, p,
-                                   R.as<uint32_t>()));
+                WR_TRY(polymat_mul(ctx, F.as<uint32_t>() + (size_t)off * m * q, hk - off, M.as<uint32_t>(), DM + 1, m,
+                                   q, q, hprev - off, hk - off, p, R.as<uint32_t>()));
             }
             WR_TRY(pm_basis_rec(ctx, k > 0 ? R.as<uint32_t>() : F.as<uint32_t>(), d, m, q, p, d_deg, leaf, Mk, DMk));
             R.release();

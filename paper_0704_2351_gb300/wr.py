@@ -90,6 +90,7 @@ _sig = {
     "wr_sequence_state_device": ([vp, vp, P(wr_params), vp, u64, i64, vp, vp, P(i64), P(i32)], ctypes.c_int),
     "wr_gram_device": ([vp, u32, i64, u32, u32, vp, i32, i32, vp, vp], ctypes.c_int),
     "wr_probe_mma": ([vp, i64, i32, vp, P(ctypes.c_double)], ctypes.c_int),
+    "wr_set_projection_overlap": ([vp, i32], ctypes.c_int),
     "wr_set_pipeline": ([vp, i32], ctypes.c_int),
     "wr_set_early_termination": ([vp, i64], ctypes.c_int),
     "wr_set_chain_reduction": ([vp, i32], ctypes.c_int),
@@ -272,6 +273,10 @@ def wr_set_tensor_projection(ctx: int, mode: int) -> None:
 
 def wr_set_paired_projection(ctx: int, on: bool) -> None:
     _check(_lib.wr_set_paired_projection(vp(ctx), 1 if on else 0))
+
+
+def wr_set_projection_overlap(ctx: int, on: bool) -> None:
+    _check(_lib.wr_set_projection_overlap(vp(ctx), 1 if on else 0))
 
 
 def wr_set_pipeline(ctx: int, mode: int) -> None:

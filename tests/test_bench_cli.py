@@ -29,7 +29,7 @@ def test_options_config_defaults_off():
     b = _bench()
     cfg = b.options_config(argparse.Namespace())
     assert cfg == {"chain_reduction": False, "locality_order": False, "early_termination_orders": 0,
-                   "pipeline": "sigma-basis first"}
+                   "pipeline": "automatic"}
 
 
 def test_spmm_traffic_reads_the_line_of_its_width(tmp_path):

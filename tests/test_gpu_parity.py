@@ -278,17 +278,19 @@ def test_rank_pipeline_pm_segments(wr, ctx, m, leaf, R, C, r):
         got = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
         wr.wr_set_pipeline(ctx, 2)  # the sigma-basis's stream first
         got2 = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
+        wr.wr_set_pipeline(ctx, 3)  # the sequence's stream first
+        got3 = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
         wr.wr_set_pipeline(ctx, False)
         seq = gpu_rank(wr, ctx, A, p, m, m, 5, want=3)
-        for bad in [3, -1]:
+        for bad in [4, -1]:
             with pytest.raises(wr.WrError):
                 wr.wr_set_pipeline(ctx, bad)
     finally:
         wr.wr_set_pipeline(ctx, True)
         wr.wr_set_sigma_leaf(ctx, 0)
-    assert got["rank"] == seq["rank"] == got2["rank"] == r
-    assert np.array_equal(got["S"], seq["S"]) and np.array_equal(got["F"], seq["F"])
-    assert np.array_equal(got2["S"], seq["S"]) and np.array_equal(got2["F"], seq["F"])
+    assert got["rank"] == seq["rank"] == got2["rank"] == got3["rank"] == r
+    for g in [got, got2, got3]:
+        assert np.array_equal(g["S"], seq["S"]) and np.array_equal(g["F"], seq["F"])
     ref = oracle.rank_wiedemann(A, p, m, m, seed=5)
     assert np.array_equal(got["F"], ref["F"]) and got["rank"] == ref["rank"]
 
@@ -501,6 +503,25 @@ def test_sequence_with_column_slabs(wr, ctx, m, n, sym, side, slab_bytes, wide):
         wr.wr_matrix_free(mat)
     finally:
         wr.wr_set_column_slabs(ctx, 0)
+
+
+@pytest.mark.parametrize("m,n,sym,side,L", [(8, 8, False, 0, 331), (8, 8, True, 1, 300), (32, 32, True, 0, 261),
+                                            (32, 32, False, 1, 140), (16, 16, True, 0, 2), (4, 4, False, 0, 3)])
+def test_projection_overlap_gives_the_same_sequence(wr, ctx, m, n, sym, side, L):
+    """The Gram projections beside the passes (side stream, forked and joined
+    around each pass, captured into the 64-application graphs) give the
+    oracle's sequence, as with the projections after the passes: lengths with
+    several captured groups and an eager tail, odd and even L, L = 2 and 3."""
+    p = 2147483629
+    A = heavy_matrix(1200, 1100, seed=m + 3 * side + (7 if sym else 0), heavy=2, heavy_len=500)
+    st = oracle.Setup(A, p, m, n, seed=21, side=side, symmetric=sym)
+    S_ref = oracle.sequence(A, st, L)
+    try:
+        for on in [True, False]:
+            wr.wr_set_projection_overlap(ctx, on)
+            assert np.array_equal(gpu_sequence(wr, ctx, A, p, m, n, 21, L, side=side, symmetric=sym), S_ref), on
+    finally:
+        wr.wr_set_projection_overlap(ctx, False)
 
 
 @pytest.mark.parametrize("m,n", [(1, 1), (2, 2), (4, 8), (4, 32), (32, 32)])
@@ -951,16 +972,11 @@ def test_config2_rank(wr, ctx, config2):
 
 def test_config2_rank_symmetric(wr, ctx, config2):
     """Config 2 with the symmetric projection of Section 2.3 (X = Y^T: two
-    terms per application of the width-32 block) and the sigma-basis's stream
-    first: the planted rank 1,805,000, the generator annihilates the sequence
+    terms per application of the width-32 block): the planted rank 1,805,000, the generator annihilates the sequence
     at sampled offsets, and S_0 .. S_2 equal the oracle's literal loop."""
     A = config2
     p, m, n, seed = 2147483629, 32, 32, synth.SEED_BASE + 2
-    wr.wr_set_pipeline(ctx, 2)
-    try:
-        g = gpu_rank(wr, ctx, A, p, m, n, seed, want=3, symmetric=True)
-    finally:
-        wr.wr_set_pipeline(ctx, 1)
+    g = gpu_rank(wr, ctx, A, p, m, n, seed, want=3, symmetric=True)
     assert g["rank"] == A.rank == 1805000
     assert g["seq_len"] == 118752
     rng = np.random.default_rng(6)
