@@ -17,17 +17,19 @@
 // Per tile of 64 rows (the MMA's K), one tcgen05 MMA chain computes
 //   D[i*32 + a][j*NB + b] = sum_r d_i(w_r L_r[a]) d_j(R_r[b])
 // (kind::f16 with fp16 operands, M = 128 = 4 digits x 32 left columns, N = 4
-// digits x NB right columns, fp32 in tensor memory); every 512 rows each thread of the first four warps
-// drains its TMEM lane (digit i = warp, column a = lane) into exact int64 sums
+// digits x NB right columns, fp32 in tensor memory); every 512 rows the eight
+// converter warps drain the accumulator (TMEM lane: digit i = warp % 4, column
+// a = lane; half warp / 4 of the right columns) into exact int64 sums
 // acc[b] += sum_j 2^{8j} D[i*32 + a][j*NB + b], and at the end
 //   G[a][b] = sum_i 2^{8i} acc_i[a][b]  mod p.
 // The rows of t and their weights reach shared memory by 1-D bulk copies
-// (up to five tiles in flight per block, two blocks per SM),
-// the threads rewrite them as digit tiles in the MMA's swizzled layout, and
-// one thread issues the MMAs and commits them to an mbarrier; operand tiles
-// are double-buffered.  Every wait is bounded: after WAIT_NS the block records
-// an error, waits (bounded) for its copies and MMAs in flight, frees its
-// tensor memory and returns.
+// (up to five tiles in flight per block, two blocks per SM), eight warps
+// rewrite them as digit tiles in the MMA's swizzled layout, and a ninth warp
+// issues the MMAs, commits them to an mbarrier and requests the next rows, so
+// that issuing never holds up the conversion; operand tiles are
+// double-buffered.  Every wait is bounded: after WAIT_NS the block records an
+// error, waits (bounded) for its copies and MMAs in flight, frees its tensor
+// memory and returns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +42,8 @@ namespace wr {
 
 namespace {
 
-constexpr int GT_THREADS = 256;
+constexpr int GT_CONV = 256;              // converter threads (warps 0-7)
+constexpr int GT_THREADS = GT_CONV + 32;  // and the issuer warp
 constexpr int GT_KT = 64;     // rows per tile
 constexpr int GT_DRAIN = 8;   // tiles per drain of the accumulator (512 rows)
 constexpr uint64_t GT_WAIT_NS = 2000000000ull;
@@ -106,13 +109,26 @@ __device__ __forceinline__ void put_digits(unsigned char *tile, int row0, int st
 // per-block result reduced mod p, then added with exact uint64 atomics.
 // w: the N weights in Montgomery form (mont_mul(w_r, x) = w_r x mod p); t and w
 // 16-byte aligned (bulk copies).
+//
+// Roles: warps 0-7 convert (tile tl: wait for its raw rows and for the MMAs
+// that last read its operand stage, write the digit tiles, one arrival per
+// warp on conv[stage]); warp 8's first lane issues (wait on conv[stage],
+// the four MMAs of the tile, the commit to mma[stage], the bulk copies of the
+// tile GT_NS ahead into the raw stage just converted), so that the issue
+// never holds up a converter.  Every GT_DRAIN tiles the converters drain the
+// accumulator (warp w: digit row w % 4 of the left factor, half w / 4 of the
+// right factor's columns) and arrive on drained, which the issuer waits for
+// before the next group overwrites the accumulator.  All waits are bounded
+// mbarrier waits; a wait that runs out sets a shared flag that every role
+// polls, and the issuer then lets the copies and MMAs in flight finish.
 template <int NB, int RB>
 __global__ void __launch_bounds__(GT_THREADS, 2)
     k_gram_tc(int64_t N, int m, int n, const uint32_t *__restrict__ w, const uint32_t *__restrict__ t, int yoff,
               unsigned long long *__restrict__ s_raw, const int *__restrict__ term_counter, int tmul, int toff,
               int64_t L, ModP mp, int *__restrict__ err) {
     using S = GramShape<NB, RB>;
-    constexpr int RW = RB / 4;  // residues per raw row
+    constexpr int RW = RB / 4;      // residues per raw row
+    constexpr int HB = NB / 2;      // right-factor columns a draining thread holds
     constexpr uint32_t IDESC = tc::idesc_f16_f32(128, S::TN);
     const int64_t k_term = term_counter ? (int64_t)tmul * *term_counter + toff : (int64_t)toff;
     if (k_term < 0 || k_term >= L) return;  // the same for every block
@@ -122,10 +138,14 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
     unsigned char *raw = base + 2 * S::OPB;
     uint32_t *wts = reinterpret_cast<uint32_t *>(raw + S::NS * S::RAWB);  // NS x 64 weights
     uint64_t *bar_raw = reinterpret_cast<uint64_t *>(wts + S::NS * GT_KT);
-    uint64_t *bar_mma = bar_raw + S::NS;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_mma + 2);
+    uint64_t *bar_mma = bar_raw + S::NS;   // [2] MMAs of an operand stage done
+    uint64_t *bar_conv = bar_mma + 2;      // [2] operand stage converted
+    uint64_t *bar_drain = bar_conv + 2;    // accumulator drained
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar_drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool issuer = warp == GT_CONV / 32;
     const int64_t tiles = (N + GT_KT - 1) / GT_KT;
     const int64_t t_begin = tiles * blockIdx.x / gridDim.x;
     const int64_t ntile = tiles * (blockIdx.x + 1) / gridDim.x - t_begin;
@@ -137,6 +157,10 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
         for (int s = 0; s < S::NS; s++) tc::mbar_init(&bar_raw[s], 1);
         tc::mbar_init(&bar_mma[0], 1);
         tc::mbar_init(&bar_mma[1], 1);
+        tc::mbar_init(&bar_conv[0], GT_CONV / 32);
+        tc::mbar_init(&bar_conv[1], GT_CONV / 32);
+        tc::mbar_init(bar_drain, GT_CONV / 32);
+        *abort_flag = 0;
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -149,7 +173,7 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    int64_t issued = 0;  // raw tiles whose copies were issued (thread 0)
+    int64_t issued = 0, committed = 0;  // (issuer) raw tiles requested, MMA commits
     auto issue = [&](int64_t tl) {
         const int s = (int)(tl % S::NS);
         const int64_t r0 = (t_begin + tl) * GT_KT;
@@ -159,101 +183,121 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
         tc::bulk_g2s(raw + s * S::RAWB, t + r0 * RW, rows * (uint32_t)RB, &bar_raw[s]);
         if (wrows) tc::bulk_g2s(wts + s * GT_KT, w + r0, wrows * 4u, &bar_raw[s]);
     };
-    if (tid == 0) {
-        for (; issued < ntile && issued < S::NS; issued++) issue(issued);
-    }
 
-    long long acc[NB];
+    long long acc[HB];
 #pragma unroll
-    for (int b = 0; b < NB; b++) acc[b] = 0;
-    int64_t committed = 0;  // MMA commits (one per tile)
-    bool bad = false;       // this thread's waits
-    bool aborted = false;   // some thread's wait ran out (the same in every thread)
+    for (int b = 0; b < HB; b++) acc[b] = 0;
 
-    for (int64_t tl = 0; tl < ntile; tl++) {
-        const int sr = (int)(tl % S::NS), so = (int)(tl & 1);
-        const int g = (int)(tl % GT_DRAIN);
-        unsigned char *opA = base + so * S::OPB, *opB = opA + S::ABYTES;
-        // the raw rows have landed; the operand stage's previous MMAs are done
-        if (!tc::mbar_wait(&bar_raw[sr], (uint32_t)((tl / S::NS) & 1), GT_WAIT_NS)) bad = true;
-        if (tl >= 2 && !tc::mbar_wait(&bar_mma[so], (uint32_t)(((tl >> 1) - 1) & 1), GT_WAIT_NS)) bad = true;
-        const int64_t r0 = (t_begin + tl) * GT_KT;
-        const int rows = (int)min64(GT_KT, N - r0);
-        const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + sr * S::RAWB);
-        const uint32_t *ws = wts + sr * GT_KT;
-        const int wrows = rows & ~3;
-        {
-            // left factor: chunk c = warp (rows 8c .. 8c + 7), column a = lane, weighted
-            const int c = warp, a = lane;
-            if (a < m) {
-                uint32_t x[8];
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int rr = 8 * c + u;
-                    const uint32_t wv = rr < wrows ? ws[rr] : (rr < rows ? __ldg(w + r0 + rr) : 0u);
-                    x[u] = rr < rows ? mont_mul(wv, rw[rr * RW + a], mp) : 0u;
+    if (issuer) {
+        if (lane == 0) {
+            for (; issued < ntile && issued < S::NS; issued++) issue(issued);
+            for (int64_t tl = 0; tl < ntile; tl++) {
+                const int so = (int)(tl & 1), g = (int)(tl % GT_DRAIN);
+                if (*abort_flag) break;
+                bool ok = tc::mbar_wait(&bar_conv[so], (uint32_t)((tl >> 1) & 1), GT_WAIT_NS);
+                // a new group overwrites the accumulator: the last one's drain must be done
+                if (ok && g == 0 && tl > 0)
+                    ok = tc::mbar_wait(bar_drain, (uint32_t)(((tl / GT_DRAIN) - 1) & 1), GT_WAIT_NS);
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
                 }
-                put_digits(opA, a, 32, c, x);
-            }
-        }
-        if (tid < 8 * NB) {
-            // right factor: chunk c, column b
-            const int c = tid / NB, b = tid % NB;
-            if (b < n) {
-                uint32_t x[8];
+                tc::tc_fence_after();
+                unsigned char *opA = base + so * S::OPB, *opB = opA + S::ABYTES;
+                const uint32_t a0 = tc::smem_addr(opA), b0 = tc::smem_addr(opB);
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int rr = 8 * c + u;
-                    x[u] = rr < rows ? rw[rr * RW + yoff + b] : 0u;
+                for (int ks = 0; ks < GT_KT / 16; ks++)
+                    tc::mma_f16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
+                                 (ks > 0 || g > 0) ? 1u : 0u);
+                tc::mma_commit(&bar_mma[so]);
+                committed++;
+                // the raw stage of this tile has been converted: refill it
+                if (issued < ntile) {
+                    tc::fence_proxy_async_smem();
+                    issue(issued);
+                    issued++;
                 }
-                put_digits(opB, b, NB, c, x);
             }
         }
-        tc::fence_proxy_async_smem();
-        aborted = __syncthreads_or(bad) != 0;
-        if (tid == 0 && !aborted) {
-            tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_addr(opA), b0 = tc::smem_addr(opB);
-#pragma unroll
-            for (int ks = 0; ks < GT_KT / 16; ks++)
-                tc::mma_f16(tmem, tc::sdesc_k_sw128(a0 + 32u * ks), tc::sdesc_k_sw128(b0 + 32u * ks), IDESC,
-                             (ks > 0 || g > 0) ? 1u : 0u);
-            tc::mma_commit(&bar_mma[so]);
-            committed++;
-            // the raw stage of this tile is free again (every thread is past the barrier)
-            if (issued < ntile) {
-                tc::fence_proxy_async_smem();
-                issue(issued);
-                issued++;
+        __syncwarp();
+    } else {
+        for (int64_t tl = 0; tl < ntile; tl++) {
+            const int sr = (int)(tl % S::NS), so = (int)(tl & 1);
+            const int g = (int)(tl % GT_DRAIN);
+            if (*abort_flag) break;
+            unsigned char *opA = base + so * S::OPB, *opB = opA + S::ABYTES;
+            // the raw rows have landed; the operand stage's previous MMAs are done
+            bool ok = tc::mbar_wait(&bar_raw[sr], (uint32_t)((tl / S::NS) & 1), GT_WAIT_NS);
+            if (ok && tl >= 2) ok = tc::mbar_wait(&bar_mma[so], (uint32_t)(((tl >> 1) - 1) & 1), GT_WAIT_NS);
+            if (!ok) {
+                *abort_flag = 1;
+                break;
             }
-        }
-        if (aborted) break;
-        if (g == GT_DRAIN - 1 || tl == ntile - 1) {
-            // drain: the accumulator of this group into the int64 sums
-            if (!tc::mbar_wait(&bar_mma[so], (uint32_t)((tl >> 1) & 1), GT_WAIT_NS)) bad = true;
-            tc::tc_fence_after();
-            if (warp < 4) {
+            const int64_t r0 = (t_begin + tl) * GT_KT;
+            const int rows = (int)min64(GT_KT, N - r0);
+            const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + sr * S::RAWB);
+            const uint32_t *ws = wts + sr * GT_KT;
+            const int wrows = rows & ~3;
+            {
+                // left factor: chunk c = warp (rows 8c .. 8c + 7), column a = lane, weighted
+                const int c = warp, a = lane;
+                if (a < m) {
+                    uint32_t x[8];
 #pragma unroll
-                for (int ch = 0; ch < S::TN / 32; ch++) {
-                    uint32_t v[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+                    for (int u = 0; u < 8; u++) {
+                        const int rr = 8 * c + u;
+                        const uint32_t wv = rr < wrows ? ws[rr] : (rr < rows ? __ldg(w + r0 + rr) : 0u);
+                        x[u] = rr < rows ? mont_mul(wv, rw[rr * RW + a], mp) : 0u;
+                    }
+                    put_digits(opA, a, 32, c, x);
+                }
+            }
+            if (tid < 8 * NB) {
+                // right factor: chunk c, column b
+                const int c = tid / NB, b = tid % NB;
+                if (b < n) {
+                    uint32_t x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int rr = 8 * c + u;
+                        x[u] = rr < rows ? rw[rr * RW + yoff + b] : 0u;
+                    }
+                    put_digits(opB, b, NB, c, x);
+                }
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_conv[so]);
+            if (g == GT_DRAIN - 1 || tl == ntile - 1) {
+                // drain: the accumulator of this group into the int64 sums
+                // (the commit of this tile covers every earlier MMA)
+                if (!tc::mbar_wait(&bar_mma[so], (uint32_t)((tl >> 1) & 1), GT_WAIT_NS)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+                const int hf = warp >> 2;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    uint32_t v[HB];
+                    tc::tmem_ldn<HB>(tmem + lanes + (uint32_t)(j * NB + hf * HB), v);
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int cc = 0; cc < 32; cc++) {
-                        const int col = ch * 32 + cc, j = col / NB, b = col % NB;
-                        acc[b] += (long long)__float2int_rn(__uint_as_float(v[cc])) << (8 * j);
-                    }
+                    for (int b = 0; b < HB; b++) acc[b] += (long long)__float2int_rn(__uint_as_float(v[b])) << (8 * j);
                 }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(bar_drain);
             }
-            tc::tc_fence_before();
-            aborted = __syncthreads_or(bad) != 0;
-            if (aborted) break;
         }
     }
 
+    __syncthreads();
+    const bool aborted = *abort_flag != 0;
     if (aborted) {
         // record the error, let the copies and MMAs in flight finish (bounded)
-        if (tid == 0) {
+        if (issuer && lane == 0) {
             atomicExch(err, GT_ERR_TIMEOUT);
             for (int64_t tl = max64(0, issued - S::NS); tl < issued; tl++)
                 tc::mbar_wait(&bar_raw[tl % S::NS], (uint32_t)((tl / S::NS) & 1), GT_WAIT_NS);
@@ -266,12 +310,13 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
         __syncthreads();
     } else {
         // G[a][b] = sum_i 2^{8i} acc_i[a][b] mod p: per digit row reduced and
-        // scaled in the first four warps, summed over the digits below
+        // scaled by the converters, summed over the digits below
         uint32_t *red = reinterpret_cast<uint32_t *>(raw);
-        if (warp < 4) {
-            const uint32_t sc = powm(256u % mp.p, (uint32_t)warp, mp);  // 2^{8 warp} mod p
+        if (!issuer) {
+            const int i = warp & 3, hf = warp >> 2;
+            const uint32_t sc = powm(256u % mp.p, (uint32_t)i, mp);  // 2^{8 i} mod p
 #pragma unroll
-            for (int b = 0; b < NB; b++) red[(warp * 32 + lane) * NB + b] = mulm(red_s64(acc[b], mp), sc, mp);
+            for (int b = 0; b < HB; b++) red[(i * 32 + lane) * NB + hf * HB + b] = mulm(red_s64(acc[b], mp), sc, mp);
         }
         __syncthreads();
         unsigned long long *dst = s_raw + (size_t)k_term * m * n;
