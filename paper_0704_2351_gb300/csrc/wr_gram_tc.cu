@@ -83,9 +83,15 @@ __device__ __forceinline__ uint32_t digit_h2(uint32_t y0, uint32_t y1) {
     return r;
 }
 
-// the 4 digit rows (row0 + i * stride) of 8 consecutive K values into
-// 16-byte chunk c of a swizzled tile
-__device__ __forceinline__ void put_digits(unsigned char *tile, int row0, int stride, int c, const uint32_t (&x)[8]) {
+// byte offsets in a swizzled tile of the 16-byte chunk c of the 4 digit rows
+// row0 + i * stride (the same for every tile a thread converts)
+__device__ __forceinline__ void digit_offsets(int row0, int stride, int c, uint32_t (&off)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) off[i] = tc::sw128_chunk((uint32_t)(row0 + i * stride), (uint32_t)c);
+}
+
+// the 4 digit rows of 8 consecutive K values into their chunks (off)
+__device__ __forceinline__ void put_digits(unsigned char *tile, const uint32_t (&off)[4], const uint32_t (&x)[8]) {
     uint32_t y[8];
 #pragma unroll
     for (int u = 0; u < 8; u++) y[u] = x[u] + 0x808080u;
@@ -96,7 +102,7 @@ __device__ __forceinline__ void put_digits(unsigned char *tile, int row0, int st
         q.y = digit_h2<I>(y[2], y[3]);                                                               \
         q.z = digit_h2<I>(y[4], y[5]);                                                               \
         q.w = digit_h2<I>(y[6], y[7]);                                                               \
-        *reinterpret_cast<uint4 *>(tile + tc::sw128_chunk((uint32_t)(row0 + I * stride), (uint32_t)c)) = q; \
+        *reinterpret_cast<uint4 *>(tile + off[I]) = q;                                               \
     }
     WR_DIGIT_ROW(0)
     WR_DIGIT_ROW(1)
@@ -221,6 +227,13 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
         }
         __syncwarp();
     } else {
+        // this thread's chunks: left factor chunk c = warp (rows 8c .. 8c + 7),
+        // column a = lane; right factor chunk tid / NB, column tid % NB
+        const int ca = warp, a = lane, cb = tid / NB, b = tid % NB;
+        const bool do_l = a < m, do_r = tid < 8 * NB && b < n;
+        uint32_t offL[4], offR[4];
+        digit_offsets(a, 32, ca, offL);
+        digit_offsets(b, NB, cb & 7, offR);
         for (int64_t tl = 0; tl < ntile; tl++) {
             const int sr = (int)(tl % S::NS), so = (int)(tl & 1);
             const int g = (int)(tl % GT_DRAIN);
@@ -238,31 +251,40 @@ __global__ void __launch_bounds__(GT_THREADS, 2)
             const uint32_t *rw = reinterpret_cast<const uint32_t *>(raw + sr * S::RAWB);
             const uint32_t *ws = wts + sr * GT_KT;
             const int wrows = rows & ~3;
-            {
-                // left factor: chunk c = warp (rows 8c .. 8c + 7), column a = lane, weighted
-                const int c = warp, a = lane;
-                if (a < m) {
+            if (rows == GT_KT) {
+                // a whole tile: every row and weight is in shared memory
+                if (do_l) {
+                    uint32_t x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) x[u] = mont_mul(ws[8 * ca + u], rw[(8 * ca + u) * RW + a], mp);
+                    put_digits(opA, offL, x);
+                }
+                if (do_r) {
+                    uint32_t x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) x[u] = rw[(8 * cb + u) * RW + yoff + b];
+                    put_digits(opB, offR, x);
+                }
+            } else {
+                if (do_l) {
+                    // left factor, weighted (the last weights past a 16-byte group by plain loads)
                     uint32_t x[8];
 #pragma unroll
                     for (int u = 0; u < 8; u++) {
-                        const int rr = 8 * c + u;
+                        const int rr = 8 * ca + u;
                         const uint32_t wv = rr < wrows ? ws[rr] : (rr < rows ? __ldg(w + r0 + rr) : 0u);
                         x[u] = rr < rows ? mont_mul(wv, rw[rr * RW + a], mp) : 0u;
                     }
-                    put_digits(opA, a, 32, c, x);
+                    put_digits(opA, offL, x);
                 }
-            }
-            if (tid < 8 * NB) {
-                // right factor: chunk c, column b
-                const int c = tid / NB, b = tid % NB;
-                if (b < n) {
+                if (do_r) {
                     uint32_t x[8];
 #pragma unroll
                     for (int u = 0; u < 8; u++) {
-                        const int rr = 8 * c + u;
+                        const int rr = 8 * cb + u;
                         x[u] = rr < rows ? rw[rr * RW + yoff + b] : 0u;
                     }
-                    put_digits(opB, b, NB, c, x);
+                    put_digits(opB, offR, x);
                 }
             }
             tc::fence_proxy_async_smem();
