@@ -139,8 +139,9 @@ wr_status wr_set_sigma_chunk(wr_ctx *ctx, int32_t orders);
  * than 131,072 orders when m + n <= 32, with 512-order leaves for sequences
  * longer than 2,048 orders when m + n > 32, the blocked M-Basis otherwise.
  * With the pipeline (wr_set_pipeline) PM-Basis trails the sequence in
- * segments, each about half of the orders still to come (down to two
- * leaves): a segment's residual against the basis so far, its own basis and
+ * segments, each about half of the orders still to come but at most a
+ * quarter of all (down to two leaves): a segment's residual against the
+ * basis so far, its own basis and
  * the product start as soon as its terms are published, so that one short
  * segment is left when the sequence ends; the M-Basis trails it chunk by
  * chunk. */

@@ -255,8 +255,12 @@ constexpr int LOCAL_THREADS = 1024;
 __host__ __device__ constexpr int local_threads(int MM, int CPL) {
     return CPL > 1 ? LOCAL_THREADS / 4 : (MM > 8 ? LOCAL_THREADS / 2 : LOCAL_THREADS);
 }
-// orders per chunk unless the context sets it (wr_set_sigma_chunk)
+// orders per chunk unless the context sets it (wr_set_sigma_chunk); for
+// q > 32 (k_local_wide, whose row work per order grows with the chunk) 4:
+// measured at q = 64, L = 8,192, 512-order leaves: 1,678 / 1,518 / 1,299 /
+// 1,496 / 1,415 ms for chunks of 2 / 3 / 4 / 5 / 7 orders
 constexpr int SIGMA_CHUNK_DEFAULT = 64;
+constexpr int SIGMA_CHUNK_WIDE = 4;
 // PM-Basis by default only for sequences longer than SIGMA_PM_MIN_L (q <=
 // 32), with leaves of SIGMA_LEAF_DEFAULT orders; measured on GB300 at
 // L = 45,002, q = 16 the blocked M-Basis alone is faster (744 ms against
@@ -1454,7 +1458,8 @@ static wr_status mbasis_run(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, 
     const bool wide = q > 32;
     auto local_need = [&](int b) { return wide ? local_wide_bytes(b, m, q) : local_bytes(b); };
     auto apply_need = [&](int ta, int b) { return wide ? apply_wide_bytes(b, q) : apply_bytes(ta, b); };
-    int bmax = ctx->sigma_chunk > 0 ? std::min(ctx->sigma_chunk, 64) : SIGMA_CHUNK_DEFAULT, TT = 32, TA = 64;
+    int bmax = ctx->sigma_chunk > 0 ? std::min(ctx->sigma_chunk, 64) : (wide ? SIGMA_CHUNK_WIDE : SIGMA_CHUNK_DEFAULT),
+        TT = 32, TA = 64;
     for (;;) {
         while (TT > 4 && window_bytes(TT, bmax) > budget) TT /= 2;
         while (TA > APP_TB && apply_need(TA, bmax) > budget) TA /= 2;
@@ -1757,9 +1762,10 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
     // coefficients [h_{k-1} - deg M, h_k) and the basis M of the orders before
     // it), its sigma-basis M_k starts from M's degrees, and M <- M M_k:
     // PM-Basis's split at h_{k-1}, applied once per segment.  Each segment is
-    // about half of the orders still to come, down to two leaves, so that
-    // what is left after the sequence's last term is one short segment and two
-    // products.  (Segments that take every term finished meanwhile, from the
+    // about half of the orders still to come but at most a quarter of all
+    // (the first starts when a quarter of the terms are in), down to two
+    // leaves, so that what is left after the sequence's last term is one short
+    // segment and two products.  (Segments that take every term finished meanwhile, from the
     // first sixteenth on, were measured slower on the 1.9M x 1.95M block-32
     // matrix: their kernels ran beside the SpMM for the whole sequence, each
     // segment with its two products, and cost the SpMM more than the shorter
@@ -1770,8 +1776,9 @@ wr_status sigma_basis(wr_ctx *ctx, const uint32_t *d_S, int64_t L, int m, int n,
         int64_t hprev = 0;
         for (int k = 0; hprev < L; k++) {
             const int64_t rem = L - hprev;
+            const int64_t half = std::min<int64_t>(rem / 2, L / 4);
             const int64_t hk =
-                hprev + (rem <= 2 * seg_min ? rem : std::max<int64_t>(seg_min, ((rem / 2 + 63) / 64) * 64));
+                hprev + (rem <= 2 * seg_min ? rem : std::max<int64_t>(seg_min, ((half + 63) / 64) * 64));
             const int64_t d = hk - hprev;
             WR_TRY(feed_wait(ctx, ctx->feed, hk));
             WR_TRY(build_F(hprev, hk));
