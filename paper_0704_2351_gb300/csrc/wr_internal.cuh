@@ -501,6 +501,9 @@ wr_status make_child(const wr_ctx *parent, wr_ctx **out, bool high = false);
 // Whether sigma_basis, trailing a sequence of L terms with blocks m x n,
 // runs PM-Basis in segments (else the blocked M-Basis chunk by chunk).
 bool sigma_pm_trailing(const wr_ctx *ctx, int64_t L, int m, int n);
+// Whether sigma_basis runs PM-Basis for L orders (else the blocked M-Basis;
+// early: early termination asked for, which needs the M-Basis).
+bool sigma_uses_pm(const wr_ctx *ctx, int64_t L, int m, int n, bool early = false);
 void copy_settings(const wr_ctx *parent, wr_ctx *child);
 wr_status blackbox_apply(wr_ctx *ctx, const wr_matrix *mat, const wr_params &prm,
                          const uint32_t *d_in, uint32_t *d_out, int64_t width);

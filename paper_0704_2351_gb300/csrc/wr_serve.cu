@@ -34,7 +34,7 @@ wr_status rank_multi(wr_ctx *ctx, const wr_matrix *mat, const wr_params *const *
 // diagonals, split accumulators, exact term sums) beside the sigma-basis
 // state (the sigma-basis trails the sequence while it runs), then the
 // readout (after both are released).
-size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
+size_t rank_device_bytes(const wr_ctx *ctx, const wr_matrix *mat, const Resolved &r, int num_sms) {
     // the paired generic block (m = n) runs the SpMM at twice the width
     const bool pairable = !r.symmetric && r.m == r.n && 2 * r.nv <= 64;
     const size_t L = (size_t)r.L, m = (size_t)r.m, n = (size_t)r.n, q = m + n,
@@ -43,7 +43,16 @@ size_t rank_device_bytes(const wr_matrix *mat, const Resolved &r, int num_sms) {
     const size_t nsplit = (size_t)(mat->a.nsplit + mat->at.nsplit);
     const size_t seq = 4 * N * nv + 4 * M * nv + 4 * (3 * N + 2 * M) + 4 * N * m + 8 * nv * nsplit + 8 * L * m * n;
     const size_t keep = 4 * L * m * n + 4 * (L + 2) * n * q + 4 * q;
-    const size_t sigma = 4 * (L + 2) * n * q + 4 * (size_t)(2 * num_sms) * 64 * m * q + 4 * 65 * q * q + 4 * (m * q + 4 * q);
+    size_t sigma = 4 * (L + 2) * n * q + 4 * (size_t)(2 * num_sms) * 64 * m * q + 4 * 65 * q * q + 4 * (m * q + 4 * q);
+    if (sigma_uses_pm(ctx, (int64_t)L, (int)m, (int)n)) {
+        // PM-Basis: the residual F, three bases of up to L/2 + 2 coefficients
+        // (the basis so far, a segment's or half's, their product), one
+        // product's transform buffers (operands and three outputs of Lz
+        // points, Lz <= the power of two >= L) and the twiddle tables
+        size_t Lz = 1;
+        while (Lz < L) Lz <<= 1;
+        sigma += 4 * L * m * q + 3 * 4 * (L / 2 + 2) * q * q + 4 * 5 * q * q * Lz + 4 * 6 * (Lz / 2);
+    }
     const size_t readout = 4 * 2 * (L + 2) * n * n + 64;
     return keep + std::max(seq + sigma, readout) + (1u << 20);
 }
@@ -57,7 +66,7 @@ extern "C" wr_status wr_rank_device_bytes(const wr_ctx *ctx, const wr_matrix *ma
     if (!ctx || !mat || !params || !bytes) return fail(WR_EINVAL, "null argument");
     Resolved r;
     WR_TRY(resolve(mat, params, r));
-    *bytes = r.N == 0 ? 0 : (uint64_t)rank_device_bytes(mat, r, ctx->num_sms);
+    *bytes = r.N == 0 ? 0 : (uint64_t)rank_device_bytes(ctx, mat, r, ctx->num_sms);
     return WR_OK;
 }
 
@@ -279,7 +288,7 @@ extern "C" wr_status wr_submit(wr_server *srv, const wr_matrix *mat, const wr_pa
     if (!srv || !mat || !params || !ticket) return fail(WR_EINVAL, "null argument");
     Resolved r;
     WR_TRY(resolve(mat, params, r));
-    const uint64_t bytes = r.N == 0 ? 0 : (uint64_t)rank_device_bytes(mat, r, srv->slots[0]->num_sms);
+    const uint64_t bytes = r.N == 0 ? 0 : (uint64_t)rank_device_bytes(srv->slots[0], mat, r, srv->slots[0]->num_sms);
     if (srv->cfg.hbm_budget && bytes > srv->cfg.hbm_budget)
         return fail(WR_EINVAL, "request needs up to " + std::to_string(bytes) + " bytes of device memory, above the "
                                "server's budget of " + std::to_string(srv->cfg.hbm_budget));

@@ -1721,7 +1721,7 @@ static int64_t sigma_leaf_for(const wr_ctx *ctx, int m, int n) {
 // PM-Basis (else the blocked M-Basis) for L orders; early termination needs
 // the order-by-order basis (PM-Basis splits the orders in halves and so needs
 // all of them from the start)
-static bool sigma_uses_pm(const wr_ctx *ctx, int64_t L, int m, int n, bool early) {
+bool sigma_uses_pm(const wr_ctx *ctx, int64_t L, int m, int n, bool early) {
     const int64_t leaf = sigma_leaf_for(ctx, m, n);
     const bool automatic = ctx->sigma_leaf <= 0;
     return !(early || L <= leaf || (automatic && L <= (m + n > 32 ? SIGMA_PM_MIN_L_WIDE : SIGMA_PM_MIN_L)));
