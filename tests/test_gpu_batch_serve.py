@@ -216,6 +216,26 @@ def test_server_memory_admission(wr, ctx):
     wr.wr_matrix_free(h)
 
 
+def test_memory_estimate_covers_pm_basis(wr, ctx):
+    """The admission bound grows by the PM-Basis buffers (residual, bases,
+    transform buffers) when the sigma-basis runs PM-Basis (q = 64, L > 2,048)
+    and not when a leaf as long as the sequence keeps it on the M-Basis."""
+    A = synth.planted_sparse(40000, 39000, 38000, row_len=4, seed=12)
+    h = _load(wr, ctx, A)
+    prm = wr.make_params(PRIMES[2], 32, 32, 4)
+    L = 2 * -(-39000 // 32) + 2
+    try:
+        pm = wr.wr_rank_device_bytes(ctx, h, prm)
+        wr.wr_set_sigma_leaf(ctx, L + 10)
+        mb = wr.wr_rank_device_bytes(ctx, h, prm)
+    finally:
+        wr.wr_set_sigma_leaf(ctx, 0)
+        wr.wr_matrix_free(h)
+    q = 64
+    Lz = 1 << (L - 1).bit_length()
+    assert pm - mb >= 4 * L * 32 * q + 3 * 4 * (L // 2) * q * q + 4 * 5 * q * q * Lz
+
+
 def test_server_refuses_invalid_requests_and_keeps_serving(wr, ctx):
     A = synth.planted_sparse(200, 180, 150, row_len=4, seed=3)
     h = _load(wr, ctx, A)
