@@ -209,9 +209,11 @@ wr_status wr_set_paired_projection(wr_ctx *ctx, int32_t on);
  * still reads the buffer it overwrites, and every group of applications
  * joins the sequence stream at its end.  The sequence is the same either
  * way (Section 2.3's terms, summed in the same order).  Measured on GB300 on
- * the 1.9M x 1.95M block-32 matrix it is slower: the tensor-core Gram blocks
- * take SM resources from the SpMM's gathers (a width-32 pass 741 -> 940 us),
- * which costs more than the Gram products it hides. */
+ * the 1.9M x 1.95M block-32 matrix it is slower: the Gram products take SM
+ * resources from the SpMM's gathers and stream their rows through the L2 that
+ * holds the gathered block (a width-32 pass 741 -> 940 us; with the Gram
+ * grid capped at half a block per SM 1,257 us), which costs more than the
+ * Gram products it hides. */
 wr_status wr_set_projection_overlap(wr_ctx *ctx, int32_t on);
 /* Where the Gram projections run (the terms of the symmetric projection and of
  * the paired generic one, Section 2.3; Table tab:r-opp col. 3 is the paper's
