@@ -113,6 +113,8 @@ def apply_options(wr, ctx, args):
     wr.wr_set_early_termination(ctx, int(getattr(args, "early_termination", 0)))
     wr.wr_set_pipeline(ctx, int(getattr(args, "pipeline", 1)))
     wr.wr_set_projection_overlap(ctx, bool(getattr(args, "projection_overlap", False)))
+    if int(getattr(args, "lane_width", 0)):
+        wr.wr_set_lane_width(ctx, int(args.lane_width))
     wr.wr_set_column_slabs(ctx, int(getattr(args, "slab_bytes", 0)))
 
 
@@ -126,6 +128,8 @@ def options_config(args):
                        3: "sequence first"}[int(getattr(args, "pipeline", 1))]
     if bool(getattr(args, "projection_overlap", False)):
         out["projection_overlap"] = True
+    if int(getattr(args, "lane_width", 0)):
+        out["lane_width"] = int(args.lane_width)
     return out
 
 
@@ -636,6 +640,8 @@ def main():
     ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1, 2, 3],
                     help="time to rank: sigma-basis after the sequence (0), trailing it with automatic stream "
                          "priorities (1), with its own stream first (2) or with the sequence's first (3)")
+    ap.add_argument("--lane-width", type=int, default=0,
+                    help="SpMM residues per lane, + 16 for streaming cache hints (0: tuned per matrix)")
     ap.add_argument("--projection-overlap", action="store_true",
                     help="the Gram projections beside the passes on a side stream (measured slower)")
     ap.add_argument("--slab-bytes", type=int, default=0,
