@@ -115,6 +115,7 @@ def apply_options(wr, ctx, args):
     wr.wr_set_projection_overlap(ctx, bool(getattr(args, "projection_overlap", False)))
     if int(getattr(args, "lane_width", 0)):
         wr.wr_set_lane_width(ctx, int(args.lane_width))
+    wr.wr_set_tensor_projection(ctx, int(getattr(args, "tensor_projection", -1)))
     wr.wr_set_column_slabs(ctx, int(getattr(args, "slab_bytes", 0)))
 
 
@@ -130,6 +131,8 @@ def options_config(args):
         out["projection_overlap"] = True
     if int(getattr(args, "lane_width", 0)):
         out["lane_width"] = int(args.lane_width)
+    if int(getattr(args, "tensor_projection", -1)) != -1:
+        out["tensor_projection"] = int(args.tensor_projection)
     return out
 
 
@@ -640,6 +643,8 @@ def main():
     ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1, 2, 3],
                     help="time to rank: sigma-basis after the sequence (0), trailing it with automatic stream "
                          "priorities (1), with its own stream first (2) or with the sequence's first (3)")
+    ap.add_argument("--tensor-projection", type=int, default=-1, choices=[-1, 0, 1],
+                    help="Gram products on the tensor cores: 1 on, 0 off, -1 automatic (blocks of 16 and more)")
     ap.add_argument("--lane-width", type=int, default=0,
                     help="SpMM residues per lane, + 16 for streaming cache hints (0: tuned per matrix)")
     ap.add_argument("--projection-overlap", action="store_true",
