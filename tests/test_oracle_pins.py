@@ -608,3 +608,45 @@ def test_two_terms_per_application_identities(side, m):
             assert np.array_equal(odd.astype(np.uint64), S[2 * k + 1].astype(np.uint64)), (k, "odd")
             U = oracle.blackbox_apply(A, p, st.side, st.D1, st.D2, U)
             V = oracle.blackbox_apply(A, p, st.side, st.D1, st.D2, V)
+
+
+def _poly_eval(P, x0, p):
+    """P(x0) mod p for a polynomial matrix P ([deg+1, r, c]) by Horner's rule."""
+    acc = np.zeros(P.shape[1:], dtype=object)
+    for k in range(P.shape[0] - 1, -1, -1):
+        acc = (acc * x0 + P[k].astype(object)) % p
+    return acc
+
+
+@pytest.mark.parametrize("p", [65521, 1073741789, 2147483629])
+def test_polymat_mul_is_a_ring_homomorphism_image(p):
+    """polymat_mul (the product PM-Basis needs): at random points x0 the
+    product's value is the product of the values, C(x0) = A(x0) B(x0) mod p
+    (a wrong shift, a dropped or transposed term breaks it at almost every
+    point); the identity and x^k are neutral and shifting factors; and the
+    scalar powers of (1 + x) give the binomial coefficients mod p."""
+    rng = np.random.default_rng(p % 97)
+    for (da, db, r, s, t) in [(1, 1, 1, 1, 1), (5, 3, 2, 3, 4), (17, 9, 3, 2, 3), (4, 12, 1, 5, 2)]:
+        A = rng.integers(0, p, size=(da, r, s))
+        B = rng.integers(0, p, size=(db, s, t))
+        C = oracle.polymat_mul(A, B, p)
+        assert C.shape == (da + db - 1, r, t)
+        for x0 in rng.integers(0, p, size=4):
+            lhs = _poly_eval(C, int(x0), p)
+            rhs = _poly_eval(A, int(x0), p).dot(_poly_eval(B, int(x0), p)) % p
+            assert np.array_equal(lhs, rhs)
+        # truncation keeps the low coefficients
+        assert np.array_equal(oracle.polymat_mul(A, B, p, trunc=3)[:3], C[:3])
+    A = rng.integers(0, p, size=(6, 3, 3))
+    I = np.eye(3, dtype=np.int64)[None]
+    assert np.array_equal(oracle.polymat_mul(A, I, p), A % p)
+    xk = np.zeros((4, 3, 3), np.int64)
+    xk[3] = np.eye(3, dtype=np.int64)
+    assert np.array_equal(oracle.polymat_mul(A, xk, p)[3:], A % p)
+    assert not oracle.polymat_mul(A, xk, p)[:3].any()
+    P = np.ones((1, 1, 1), np.int64)
+    one_x = np.ones((2, 1, 1), np.int64)
+    for _ in range(10):
+        P = oracle.polymat_mul(P, one_x, p)
+    import math
+    assert [int(v) for v in P[:, 0, 0]] == [math.comb(10, k) % p for k in range(11)]
