@@ -454,6 +454,24 @@ wr_status wr_sigma_basis_device(wr_ctx *ctx, const uint32_t *d_S, uint64_t L, ui
 wr_status wr_det_valuation_device(wr_ctx *ctx, const uint32_t *d_G, int64_t n, int64_t T,
                                   uint32_t prime, int64_t *val);
 
+/* The polynomial matrix product of PM-Basis (Section 2.4: the sigma-basis of
+ * order L is the product of two of order L/2, and the second is computed from
+ * the middle coefficients of S(x) times the first):
+ * C[k - lo] = sum_j A_j B_{k-j} mod prime for lo <= k < hi (coefficients past
+ * the exact product's na + nb - 2 are 0).  d_A: na coefficients of r x s,
+ * d_B: nb coefficients of s x t, d_C: (hi - lo) x r x t, all device pointers
+ * to residues below prime, coefficient-major and row-major inside a
+ * coefficient; the caller owns every buffer.  Returns once d_C is written
+ * (the context's stream is synchronised).  Computed as three number-theoretic
+ * transforms over 998244353, 469762049 and 2013265921 and a Chinese remainder
+ * step, so s * min(na, nb) * (prime - 1)^2 must stay below their product and
+ * max(hi, na + nb - 1 - lo) at most 2^23; WR_EINVAL otherwise, and for
+ * lo > hi, a negative size, r, s or t outside 1..1024, or a null pointer
+ * with work to do. */
+wr_status wr_polymat_mul_device(wr_ctx *ctx, uint32_t prime, const uint32_t *d_A, int64_t na,
+                                const uint32_t *d_B, int64_t nb, uint32_t r, uint32_t s, uint32_t t,
+                                int64_t lo, int64_t hi, uint32_t *d_C);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Tensor-core rate and layout probe (a measurement helper; the paper has no

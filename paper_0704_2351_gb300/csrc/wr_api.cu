@@ -1035,6 +1035,20 @@ extern "C" wr_status wr_gram_device(wr_ctx *ctx, uint32_t prime, int64_t N, uint
     return gram_device(ctx, prime, N, (int)m, (int)n, d_t, tstride, yoff, d_w, d_G);
 }
 
+extern "C" wr_status wr_polymat_mul_device(wr_ctx *ctx, uint32_t prime, const uint32_t *d_A, int64_t na,
+                                           const uint32_t *d_B, int64_t nb, uint32_t r, uint32_t s, uint32_t t,
+                                           int64_t lo, int64_t hi, uint32_t *d_C) {
+    if (!ctx) return fail(WR_EINVAL, "null argument");
+    if (na < 0 || nb < 0 || lo < 0 || lo > hi) return fail(WR_EINVAL, "na, nb >= 0 and 0 <= lo <= hi");
+    if (r < 1 || s < 1 || t < 1 || r > 1024 || s > 1024 || t > 1024) return fail(WR_EINVAL, "r, s, t in 1..1024");
+    if (prime <= 2 || prime >= (1u << 31) || !is_prime_u32(prime)) return fail(WR_ENOTPRIME, "bad prime");
+    if (hi > lo && (!d_C || (na > 0 && nb > 0 && (!d_A || !d_B)))) return fail(WR_EINVAL, "null argument");
+    WR_CUDA(cudaSetDevice(ctx->device));
+    WR_TRY(polymat_mul(ctx, d_A, na, d_B, nb, (int)r, (int)s, (int)t, lo, hi, prime, d_C));
+    WR_CUDA(cudaStreamSynchronize(ctx->stream));
+    return WR_OK;
+}
+
 extern "C" wr_status wr_probe_mma(wr_ctx *ctx, int64_t iters, int32_t blocks, float *d_out, double *ms) {
     if (!ctx || !ms) return fail(WR_EINVAL, "null argument");
     if (iters < 1 || blocks < 1 || blocks > 4096) return fail(WR_EINVAL, "iters >= 1 and blocks in 1..4096");

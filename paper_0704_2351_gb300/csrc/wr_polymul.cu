@@ -387,6 +387,11 @@ static wr_status polymat_mul_run(wr_ctx *ctx, const uint32_t *A, int64_t na, con
         WR_CUDA(cudaMemsetAsync(C, 0, sizeof(uint32_t) * (size_t)(hi - lo) * r * t, st));
         return WR_OK;
     }
+    // the exact coefficients, at most s min(na, nb) (p - 1)^2, must lie below
+    // the product of the transform primes for the remainder step to recover them
+    const double bound = (double)s * (double)std::min(na, nb) * (double)(p - 1) * (double)(p - 1);
+    if (bound >= 0.999 * (double)NTT_PRIMES[0] * (double)NTT_PRIMES[1] * (double)NTT_PRIMES[2])
+        return fail(WR_EINVAL, "polynomial product coefficients exceed the transform primes' product");
     const int64_t full = na + nb - 1;  // coefficients of the exact product
     const int64_t need = std::max<int64_t>(hi, full - lo);
     int lg = 1;

@@ -90,6 +90,7 @@ _sig = {
     "wr_sequence_state_device": ([vp, vp, P(wr_params), vp, u64, i64, vp, vp, P(i64), P(i32)], ctypes.c_int),
     "wr_gram_device": ([vp, u32, i64, u32, u32, vp, i32, i32, vp, vp], ctypes.c_int),
     "wr_probe_mma": ([vp, i64, i32, vp, P(ctypes.c_double)], ctypes.c_int),
+    "wr_polymat_mul_device": ([vp, u32, vp, i64, vp, i64, u32, u32, u32, i64, i64, vp], ctypes.c_int),
     "wr_set_projection_overlap": ([vp, i32], ctypes.c_int),
     "wr_set_pipeline": ([vp, i32], ctypes.c_int),
     "wr_set_early_termination": ([vp, i64], ctypes.c_int),
@@ -448,6 +449,12 @@ def wr_sequence_state_device(ctx: int, mat: int, params: wr_params, d_S, L: int,
 def wr_gram_device(ctx: int, prime: int, N: int, m: int, n: int, d_t, tstride: int, yoff: int, d_w, d_G) -> None:
     _check(_lib.wr_gram_device(vp(ctx), prime, N, m, n, vp(_dptr(d_t)), tstride, yoff, vp(_dptr(d_w)),
                                vp(_dptr(d_G))))
+
+
+def wr_polymat_mul_device(ctx: int, prime: int, d_A, na: int, d_B, nb: int, r: int, s: int, t: int, lo: int,
+                          hi: int, d_C) -> None:
+    _check(_lib.wr_polymat_mul_device(vp(ctx), prime, vp(_dptr(d_A)), na, vp(_dptr(d_B)), nb, r, s, t, lo, hi,
+                                      vp(_dptr(d_C))))
 
 
 def wr_probe_mma(ctx: int, iters: int, blocks: int, d_out=None) -> float:
