@@ -648,5 +648,39 @@ def test_polymat_mul_is_a_ring_homomorphism_image(p):
     one_x = np.ones((2, 1, 1), np.int64)
     for _ in range(10):
         P = oracle.polymat_mul(P, one_x, p)
-    import math
     assert [int(v) for v in P[:, 0, 0]] == [math.comb(10, k) % p for k in range(11)]
+
+
+@pytest.mark.parametrize("p", [65521, 2147483629, 2147483647])
+def test_project_is_the_exact_product_reduced(p):
+    """project(X, V) = X^T V mod p (Section 2.3's dot products), against Python
+    integers: with every residue p - 1 a 64-bit accumulator that is not reduced
+    wraps after 4 rows at p near 2^31, so the row counts here would show it;
+    a transposed operand changes the shape or the values."""
+    rng = np.random.default_rng(p % 101)
+    for N, m, n in [(1, 1, 1), (5, 3, 2), (4097, 4, 7), (70001, 2, 3)]:
+        for kind in ["random", "top"]:
+            X = rng.integers(0, p, size=(N, m)) if kind == "random" else np.full((N, m), p - 1)
+            V = rng.integers(0, p, size=(N, n)) if kind == "random" else np.full((N, n), p - 1)
+            S = oracle.project(X.astype(np.uint32), V.astype(np.uint32), p)
+            ref = (X.astype(object).T.dot(V.astype(object))) % p
+            assert S.shape == (m, n)
+            assert np.array_equal(S.astype(np.int64), ref.astype(np.int64))
+    # all p - 1: (p - 1)^2 N = N mod p
+    N = 70001
+    S = oracle.project(np.full((N, 2), p - 1, np.uint32), np.full((N, 2), p - 1, np.uint32), p)
+    assert (S == N % p).all()
+
+
+def test_side_choice_makes_N_the_smaller_dimension():
+    """Section 2.3: A~ is formed on the smaller side, so N = min(rows, cols)
+    under the automatic choice; an explicit side is kept."""
+    assert oracle.choose_side(10, 7) == oracle.SIDE_COLS
+    assert oracle.choose_side(7, 10) == oracle.SIDE_ROWS
+    assert oracle.choose_side(8, 8) == oracle.SIDE_COLS
+    assert oracle.choose_side(10, 7, oracle.SIDE_ROWS) == oracle.SIDE_ROWS
+    for R, C in [(60, 45), (45, 60)]:
+        A = synth.random_sparse(R, C, 4, seed=R)
+        st = oracle.Setup(A, 65521, 2, 3, seed=1)
+        assert st.N == min(R, C) and st.M == max(R, C)
+        assert st.Y.shape == (st.N, 3)
